@@ -1,0 +1,204 @@
+"""Plain CPU oracle of the flow-interpolation event simulator.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product path (the CUDA library and its binding) never imports, links or calls
+it, and the two share no code: this package holds its own C source
+(``evsim_oracle.c``), its own LUT, its own fixed-point helpers.
+
+``run()`` is a ctypes wrapper of ``orc_run`` (the whole per-stream method of
+Sec. III-A / III-B of Ziegler et al., arXiv 2209.04634, as restated in
+``evsim_oracle.c``).  ``exact.py`` is a second, pixel-major restatement in
+pure Python integers for tiny inputs.
+
+Parity status of each function is pinned by ``tests/test_oracle_pins.py``
+(closed forms, invariants, the Kaiser difference-frame special case,
+exhaustive 1x1 enumeration, exact integer translations, plane images).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "evsim_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+EVENT_DTYPE = np.dtype([("t", "<u4"), ("x", "<u2"), ("yp", "<u2")])
+
+DENSE, SPARSE = 0, 1
+LOG, LINEAR = 0, 1
+ACCUM, RESET = 0, 1
+
+
+class OrcConfig(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("channels", ctypes.c_int32),
+        ("mode", ctypes.c_int32),
+        ("substeps", ctypes.c_int32),
+        ("max_substeps", ctypes.c_int32),
+        ("intensity", ctypes.c_int32),
+        ("ref_mode", ctypes.c_int32),
+        ("c_pos_q16", ctypes.c_int32),
+        ("c_neg_q16", ctypes.c_int32),
+        ("c_act_q16", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(_SO) >= os.path.getmtime(os.path.join(_HERE, "evsim_oracle.h"))):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+           "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def use_library(path: str | None) -> None:
+    """Point the wrapper at another build of the oracle source (the mutation
+    tests load deliberately broken copies); None restores the default."""
+    global _lib, _override
+    with _lock:
+        _override = path
+        _lib = None
+
+
+_override = None
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(_override or build())
+            lib.orc_lut.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+            lib.orc_luma.argtypes = [ctypes.c_int32] * 3
+            lib.orc_luma.restype = ctypes.c_int32
+            lib.orc_flow_q16.argtypes = [ctypes.c_float, ctypes.POINTER(ctypes.c_int32)]
+            lib.orc_flow_q16.restype = ctypes.c_int32
+            lib.orc_bilinear.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int64, ctypes.c_int64]
+            lib.orc_bilinear.restype = ctypes.c_int32
+            lib.orc_adaptive_substeps.argtypes = [ctypes.c_int64, ctypes.c_int32]
+            lib.orc_adaptive_substeps.restype = ctypes.c_int32
+            vp = ctypes.c_void_p
+            lib.orc_run.argtypes = [ctypes.POINTER(OrcConfig), ctypes.c_int32, vp, vp, vp,
+                                    vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+            lib.orc_run.restype = ctypes.c_int64
+            _lib = lib
+    return _lib
+
+
+def lut(intensity: int = LOG) -> np.ndarray:
+    out = (ctypes.c_int32 * 256)()
+    _load().orc_lut(intensity, out)
+    return np.frombuffer(out, dtype=np.int32).copy()
+
+
+def luma(r: int, g: int, b: int) -> int:
+    return int(_load().orc_luma(r, g, b))
+
+
+def flow_q16(f: float) -> tuple[int, bool]:
+    cl = ctypes.c_int32(0)
+    v = _load().orc_flow_q16(ctypes.c_float(f), ctypes.byref(cl))
+    return int(v), bool(cl.value)
+
+
+def bilinear(L: np.ndarray, px: int, py: int) -> int:
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    H, W = L.shape
+    return int(_load().orc_bilinear(L.ctypes.data, W, H, px, py))
+
+
+def adaptive_substeps(max_f2: int, max_substeps: int) -> int:
+    return int(_load().orc_adaptive_substeps(max_f2, max_substeps))
+
+
+def q16(c: float) -> int:
+    """Host conversion of a threshold in log (or 8-bit) units to Q16."""
+    return int(round(abs(float(c)) * 65536.0))
+
+
+def run(frames: np.ndarray, flows: np.ndarray | None, t_us, *, mode: int = DENSE,
+        substeps: int = 8, max_substeps: int = 64, intensity: int = LOG,
+        ref_mode: int = ACCUM, c_pos_q16: int = 13107, c_neg_q16: int = 13107,
+        c_act_q16: int = -1, cpos_map: np.ndarray | None = None,
+        cneg_map: np.ndarray | None = None, cap: int | None = None) -> dict:
+    """Run the oracle over a whole sequence.
+
+    frames: (F, H, W) uint8 luma or (F, H, W, 3) uint8 RGB.
+    flows : (F, H, W, 2) float32, index i holds the flow of frame i-1 -> i
+            (entry 0 unused); may be None when F == 1.
+    Returns a dict with 'events' (structured array, EVENT_DTYPE), 'R' (H, W)
+    int32, 'n_per_frame', 'ev_per_frame', 'active_per_frame', 'clamped'.
+    """
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    F = frames.shape[0]
+    H, W = frames.shape[1], frames.shape[2]
+    ch = 3 if frames.ndim == 4 else 1
+    t = np.ascontiguousarray(np.asarray(t_us, dtype=np.int64))
+    assert t.shape == (F,)
+    if flows is not None:
+        flows = np.ascontiguousarray(flows, dtype=np.float32)
+        assert flows.shape == (F, H, W, 2), flows.shape
+    cfg = OrcConfig(W, H, ch, mode, substeps, max_substeps, intensity, ref_mode,
+                    c_pos_q16, c_neg_q16, c_act_q16)
+    maps = []
+    for m in (cpos_map, cneg_map):
+        if m is None:
+            maps.append(None)
+        else:
+            m = np.ascontiguousarray(m, dtype=np.uint16)
+            assert m.shape == (H, W)
+            maps.append(m)
+    R = np.zeros((H, W), dtype=np.int32)
+    npf = np.zeros(F, dtype=np.int32)
+    epf = np.zeros(F, dtype=np.int64)
+    apf = np.zeros(F, dtype=np.int64)
+    clamped = ctypes.c_int64(0)
+    if cap is None:
+        cap = 1 << 16
+    lib = _load()
+
+    def call(capacity):
+        ev = np.zeros(max(capacity, 1), dtype=EVENT_DTYPE)
+        n = lib.orc_run(ctypes.byref(cfg), F, frames.ctypes.data,
+                        None if flows is None else flows.ctypes.data, t.ctypes.data,
+                        None if maps[0] is None else maps[0].ctypes.data,
+                        None if maps[1] is None else maps[1].ctypes.data,
+                        ev.ctypes.data, capacity, R.ctypes.data, npf.ctypes.data,
+                        epf.ctypes.data, apf.ctypes.data, ctypes.byref(clamped))
+        return n, ev
+
+    n, ev = call(cap)
+    if n > cap:
+        n, ev = call(int(n))
+    if n < 0:
+        raise ValueError(f"oracle rejected the input (code {n})")
+    return {"events": ev[:n].copy(), "R": R, "n_per_frame": npf, "ev_per_frame": epf,
+            "active_per_frame": apf, "clamped": int(clamped.value)}
+
+
+def unpack(events: np.ndarray):
+    """Split packed events into (t, x, y, p) arrays with p in {+1, -1}."""
+    t = events["t"].astype(np.int64)
+    x = events["x"].astype(np.int64)
+    y = (events["yp"] >> 1).astype(np.int64)
+    p = np.where(events["yp"] & 1, 1, -1).astype(np.int64)
+    return t, x, y, p

@@ -1,0 +1,261 @@
+/*
+ * Plain CPU oracle for the flow-interpolation event simulator.
+ * TEST INFRASTRUCTURE ONLY: see evsim_oracle.h.  Every step is written in the
+ * order the method defines it: substep-major, then rows, then columns, then
+ * repeated crossings.  No blocking, no fusion, no SIMD, no threads.
+ *
+ * Paper: Ziegler et al., "Real-time event simulation with frame-based
+ * cameras" (arXiv 2209.04634), Sec. III, III-A, III-B, Table I.
+ */
+#include "evsim_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* floor(a / b) for b > 0, rounding toward minus infinity. */
+static int64_t floordiv(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  if ((a % b != 0) && (a < 0)) q -= 1;
+  return q;
+}
+
+/*
+ * Intensity table.  Sec. III states the paper differences linear intensity;
+ * the log reading takes the event-camera model of Sec. I (log-scale changes).
+ *   ORC_LOG   : LUT[v] = round-half-even(65536 * ln(v + 1)); the +1 keeps
+ *               v = 0 finite (the paper is silent on it).
+ *   ORC_LINEAR: LUT[v] = v * 65536, thresholds then in 8-bit units as in
+ *               Table I (C_pos = 2 / 10 / 20).
+ */
+void orc_lut(int32_t intensity, int32_t lut[256]) {
+  for (int v = 0; v < 256; ++v) {
+    if (intensity == ORC_LINEAR) {
+      lut[v] = v * 65536;
+    } else {
+      double exact = 65536.0 * log((double)v + 1.0);
+      lut[v] = (int32_t)nearbyint(exact); /* default rounding: ties to even */
+    }
+  }
+}
+
+/* BT.601 integer luma (the paper's inputs are grey-scale frames, Fig. 5a). */
+int32_t orc_luma(int32_t r, int32_t g, int32_t b) {
+  return (77 * r + 150 * g + 29 * b + 128) >> 8;
+}
+
+/* Flow to Q16: NaN -> 0; clamp to +-1024 px; nearest, ties to even. */
+int32_t orc_flow_q16(float f, int32_t* clamped) {
+  double d = (double)f;
+  if (d != d) return 0;
+  if (d > 1024.0) { d = 1024.0; if (clamped) *clamped = 1; }
+  if (d < -1024.0) { d = -1024.0; if (clamped) *clamped = 1; }
+  return (int32_t)nearbyint(d * 65536.0);
+}
+
+/* Linear blend of two Q16 values with a Q12 weight w in [0, 4096]:
+ * a + floor(((b - a) * w + 2048) / 4096), i.e. round half up. */
+static int64_t lerp_q12(int64_t a, int64_t b, int64_t w) {
+  return a + floordiv((b - a) * w + 2048, 4096);
+}
+
+/*
+ * Bilinear sample of a Q16 image at a Q16 position, the sampling step of the
+ * "simple but fast linear interpolation" along the flow (Sec. III, III-A).
+ * Borders (the paper is silent): the position is clamped to the image.
+ * The fraction is the top 12 of the 16 fractional bits.
+ */
+int32_t orc_bilinear(const int32_t* L, int32_t W, int32_t H, int64_t px, int64_t py) {
+  int64_t maxx = (int64_t)(W - 1) * 65536, maxy = (int64_t)(H - 1) * 65536;
+  if (px < 0) px = 0;
+  if (px > maxx) px = maxx;
+  if (py < 0) py = 0;
+  if (py > maxy) py = maxy;
+  int64_t ix = px >> 16, iy = py >> 16;
+  int64_t fx = (px & 0xFFFF) >> 4, fy = (py & 0xFFFF) >> 4;
+  int64_t x1 = ix + 1 < W ? ix + 1 : W - 1;
+  int64_t y1 = iy + 1 < H ? iy + 1 : H - 1;
+  int64_t l00 = L[iy * W + ix], l01 = L[iy * W + x1];
+  int64_t l10 = L[y1 * W + ix], l11 = L[y1 * W + x1];
+  int64_t top = lerp_q12(l00, l01, fx);
+  int64_t bot = lerp_q12(l10, l11, fx);
+  return (int32_t)lerp_q12(top, bot, fy);
+}
+
+/* Smallest N >= 1 with N^2 * 2^32 >= max(Fx^2 + Fy^2), i.e. N = ceil(max|F|)
+ * in pixels, capped at max_substeps.  The paper fixes N per data set
+ * (Table I: 10; Sec. IV-A: 20 for the driving sequence); this is the
+ * configuration's adaptive reading. */
+int32_t orc_adaptive_substeps(int64_t max_f2, int32_t max_substeps) {
+  int32_t n = 1;
+  while (n < max_substeps && (int64_t)n * n * 4294967296LL < max_f2) ++n;
+  return n;
+}
+
+static int32_t pixel_threshold(const uint16_t* map, int32_t uniform, int64_t i) {
+  return map ? (int32_t)map[i] : uniform;
+}
+
+static void emit(orc_event* out, int64_t cap, int64_t* n, uint32_t t, int32_t x,
+                 int32_t y, int32_t pos) {
+  if (*n < cap) {
+    out[*n].t = t;
+    out[*n].x = (uint16_t)x;
+    out[*n].yp = (uint16_t)((y << 1) | (pos ? 1 : 0));
+  }
+  *n += 1;
+}
+
+static void frame_to_log(const orc_config* c, const int32_t lut[256], const uint8_t* f,
+                         int32_t* L) {
+  int64_t P = (int64_t)c->width * c->height;
+  for (int64_t i = 0; i < P; ++i) {
+    int32_t v;
+    if (c->channels == 3)
+      v = orc_luma(f[3 * i], f[3 * i + 1], f[3 * i + 2]);
+    else
+      v = f[i];
+    L[i] = lut[v];
+  }
+}
+
+int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
+                const float* flows, const int64_t* t_us,
+                const uint16_t* cpos_map, const uint16_t* cneg_map,
+                orc_event* out, int64_t cap, int32_t* R_final,
+                int32_t* n_per_frame, int64_t* ev_per_frame,
+                int64_t* active_per_frame, int64_t* clamped_total) {
+  if (!c || n_frames < 1 || !frames || !t_us || c->width < 1 || c->height < 1) return -1;
+  if (c->channels != 1 && c->channels != 3) return -1;
+  if (c->substeps < 0 || (c->substeps == 0 && c->max_substeps < 1)) return -1;
+  if (n_frames > 1 && !flows) return -1;
+  const int32_t W = c->width, H = c->height;
+  const int64_t P = (int64_t)W * H;
+  const int64_t fbytes = P * c->channels;
+
+  int32_t lut[256];
+  orc_lut(c->intensity, lut);
+
+  int32_t* Lprev = (int32_t*)malloc(P * sizeof(int32_t));
+  int32_t* Lcur = (int32_t*)malloc(P * sizeof(int32_t));
+  int32_t* R = (int32_t*)malloc(P * sizeof(int32_t));
+  int32_t* Fx = (int32_t*)malloc(P * sizeof(int32_t));
+  int32_t* Fy = (int32_t*)malloc(P * sizeof(int32_t));
+  uint8_t* act = (uint8_t*)malloc(P);
+  if (!Lprev || !Lcur || !R || !Fx || !Fy || !act) {
+    free(Lprev); free(Lcur); free(R); free(Fx); free(Fy); free(act);
+    return -4;
+  }
+
+  /* Frame 0 sets the reference and emits nothing. */
+  frame_to_log(c, lut, frames, Lprev);
+  memcpy(R, Lprev, P * sizeof(int32_t));
+  if (n_per_frame) n_per_frame[0] = 0;
+  if (ev_per_frame) ev_per_frame[0] = 0;
+  if (active_per_frame) active_per_frame[0] = 0;
+  int64_t clamped = 0;
+
+  int64_t n = 0;
+  int64_t rc = 0;
+  for (int32_t i = 1; i < n_frames; ++i) {
+    int64_t t_prev = t_us[i - 1] - t_us[0];
+    int64_t dt = t_us[i] - t_us[i - 1];
+    if (dt <= 0) { rc = -2; break; }
+    if (t_us[i] - t_us[0] > 4294967295LL) { rc = -3; break; }
+    int64_t n_before = n;
+    frame_to_log(c, lut, frames + (int64_t)i * fbytes, Lcur);
+
+    /* Flow of frame i (i-1 -> i), read at the target pixel. */
+    const float* fl = flows + (int64_t)i * P * 2;
+    for (int64_t p = 0; p < P; ++p) {
+      int32_t cl = 0;
+      Fx[p] = orc_flow_q16(fl[2 * p], &cl);
+      Fy[p] = orc_flow_q16(fl[2 * p + 1], &cl);
+      clamped += cl;
+    }
+
+    /* Sec. III-B: pixels whose change from frame i-1 to frame i stays under
+     * the activity threshold are disregarded (dense: every pixel counts). */
+    int64_t n_active = 0;
+    for (int64_t p = 0; p < P; ++p) {
+      int32_t a = 1;
+      if (c->mode == ORC_SPARSE) {
+        int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);
+        int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);
+        int32_t cact = c->c_act_q16 >= 0 ? c->c_act_q16 : (cp < cn ? cp : cn);
+        int64_t d = (int64_t)Lcur[p] - Lprev[p];
+        if (d < 0) d = -d;
+        a = d >= cact;
+      }
+      act[p] = (uint8_t)a;
+      n_active += a;
+    }
+
+    int32_t N = c->substeps;
+    if (N == 0) {
+      int64_t m = 0;
+      for (int64_t p = 0; p < P; ++p) {
+        if (!act[p]) continue;
+        int64_t f2 = (int64_t)Fx[p] * Fx[p] + (int64_t)Fy[p] * Fy[p];
+        if (f2 > m) m = f2;
+      }
+      N = orc_adaptive_substeps(m, c->max_substeps);
+    }
+
+    /* RESET mode differences consecutive interpolated frames: the frame
+     * before substep 1 is frame i-1 itself (Sec. III-A). */
+    if (c->ref_mode == ORC_RESET) memcpy(R, Lprev, P * sizeof(int32_t));
+
+    for (int32_t k = 1; k <= N; ++k) {
+      /* Q12 blend weight round-half-up(4096 k / N); w_N = 4096. */
+      int64_t w = ((int64_t)k * 8192 + N) / (2 * (int64_t)N);
+      uint32_t tk = (uint32_t)(t_prev + floordiv((int64_t)k * dt, N));
+      for (int32_t y = 0; y < H; ++y) {
+        for (int32_t x = 0; x < W; ++x) {
+          int64_t p = (int64_t)y * W + x;
+          if (!act[p]) continue;
+          /* Interpolated frame k of N (Sec. III-A): the pixel's trajectory
+           * passes x - (k/N) F in frame i-1 and x + (1 - k/N) F in frame i. */
+          int64_t offx = floordiv((int64_t)Fx[p] * k, N);
+          int64_t offy = floordiv((int64_t)Fy[p] * k, N);
+          int64_t p0x = (int64_t)x * 65536 - offx, p0y = (int64_t)y * 65536 - offy;
+          int64_t p1x = p0x + Fx[p], p1y = p0y + Fy[p];
+          int64_t s0 = orc_bilinear(Lprev, W, H, p0x, p0y);
+          int64_t s1 = orc_bilinear(Lcur, W, H, p1x, p1y);
+          int64_t I = lerp_q12(s0, s1, w);
+
+          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);
+          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);
+          int64_t D = I - R[p];
+          if (c->ref_mode == ORC_RESET) {
+            /* The two-case threshold equations of Sec. III-A, strict. */
+            if (D > cp) emit(out, cap, &n, tk, x, y, 1);
+            else if (D < -(int64_t)cn) emit(out, cap, &n, tk, x, y, 0);
+            R[p] = (int32_t)I;
+          } else {
+            /* Reference-accumulating reading: every whole threshold crossed
+             * by the difference is one event; the reference moves by it. */
+            if (D >= cp) {
+              int64_t m = D / cp;
+              R[p] = (int32_t)(R[p] + m * cp);
+              for (int64_t j = 0; j < m; ++j) emit(out, cap, &n, tk, x, y, 1);
+            } else if (-D >= cn) {
+              int64_t m = (-D) / cn;
+              R[p] = (int32_t)(R[p] - m * cn);
+              for (int64_t j = 0; j < m; ++j) emit(out, cap, &n, tk, x, y, 0);
+            }
+          }
+        }
+      }
+    }
+    if (n_per_frame) n_per_frame[i] = N;
+    if (ev_per_frame) ev_per_frame[i] = n - n_before;
+    if (active_per_frame) active_per_frame[i] = n_active;
+    int32_t* tmp = Lprev; Lprev = Lcur; Lcur = tmp;
+  }
+
+  if (R_final) memcpy(R_final, R, P * sizeof(int32_t));
+  if (clamped_total) *clamped_total = clamped;
+  free(Lprev); free(Lcur); free(R); free(Fx); free(Fy); free(act);
+  return rc < 0 ? rc : n;
+}

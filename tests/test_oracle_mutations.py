@@ -1,0 +1,124 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a temporary copy of the oracle's C source (a
+dropped rounding term, a flipped sign, a transposed operand, an off-by-one
+comparison ...), builds it, points the oracle wrapper at the broken build and
+runs the pin battery of test_oracle_pins.py.  At least one pin must fail for
+every planted mistake.  The cross-check against the Python restatement is
+left out of the battery on purpose: the pins alone must catch each mistake.
+Everything here runs on the CPU.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+
+from . import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "evsim_oracle.c")
+
+MUTATIONS = {
+    "offset_sign": ("(int64_t)x * 65536 - offx", "(int64_t)x * 65536 + offx"),
+    "flow_components_swapped": ("p1x = p0x + Fx[p], p1y = p0y + Fy[p]",
+                                "p1x = p0x + Fy[p], p1y = p0y + Fx[p]"),
+    "rounding_term_dropped": ("(b - a) * w + 2048, 4096", "(b - a) * w, 4096"),
+    "accum_strict_compare": ("if (D >= cp) {", "if (D > cp) {"),
+    "weight_floor_not_rounded": ("((int64_t)k * 8192 + N) / (2 * (int64_t)N)",
+                                 "((int64_t)k * 4096) / (int64_t)N - (k < N ? 0 : 0) + 0 * N"),
+    "taps_transposed": ("int64_t l00 = L[iy * W + ix], l01 = L[iy * W + x1];",
+                        "int64_t l00 = L[iy * W + ix], l01 = L[y1 * W + ix];"),
+    "time_rounded_not_floored": ("floordiv((int64_t)k * dt, N)", "(((int64_t)k * dt + N / 2) / N)"),
+    "fraction_before_clamp": [("  if (px < 0) px = 0;", "  int64_t fx0 = (px & 0xFFFF) >> 4;\n  if (px < 0) px = 0;"),
+                              ("int64_t fx = (px & 0xFFFF) >> 4,", "int64_t fx = fx0,")],
+    "offset_truncated": ("floordiv((int64_t)Fx[p] * k, N)", "(((int64_t)Fx[p] * k) / N)"),
+    "reset_non_strict": ("if (D > cp) emit(out, cap, &n, tk, x, y, 1);",
+                         "if (D >= cp) emit(out, cap, &n, tk, x, y, 1);"),
+    "log_base_2": ("65536.0 * log((double)v + 1.0)", "65536.0 * log2((double)v + 1.0)"),
+    "luma_weights_swapped": ("77 * r + 150 * g + 29 * b", "29 * r + 150 * g + 77 * b"),
+    "reference_moves_one_step": ("R[p] = (int32_t)(R[p] + m * cp);", "R[p] = (int32_t)(R[p] + cp);"),
+    "activity_strict": ("a = d >= cact;", "a = d > cact;"),
+    "adaptive_off_by_one": ("(int64_t)n * n * 4294967296LL < max_f2",
+                            "(int64_t)n * n * 4294967296LL <= max_f2"),
+    "y_fraction_from_x": ("fy = (py & 0xFFFF) >> 4", "fy = (px & 0xFFFF) >> 4"),
+    "column_major_order": ("for (int32_t y = 0; y < H; ++y) {\n        for (int32_t x = 0; x < W; ++x) {",
+                           "for (int32_t x = 0; x < W; ++x) {\n        for (int32_t y = 0; y < H; ++y) {"),
+    "polarity_bit_inverted": ("(y << 1) | (pos ? 1 : 0)", "(y << 1) | (pos ? 0 : 1)"),
+    "flow_floored": ("(int32_t)nearbyint(d * 65536.0)", "(int32_t)floor(d * 65536.0)"),
+    "reset_starts_from_new_frame": ("if (c->ref_mode == ORC_RESET) memcpy(R, Lprev,",
+                                    "if (c->ref_mode == ORC_RESET) memcpy(R, Lcur,"),
+    "negative_reference_step": ("R[p] = (int32_t)(R[p] - m * cn);", "R[p] = (int32_t)(R[p] - m * cp);"),
+    "clamp_y_one_row_short": ("maxy = (int64_t)(H - 1) * 65536", "maxy = (int64_t)(H - 2) * 65536"),
+    "time_base_from_current_frame": ("int64_t t_prev = t_us[i - 1] - t_us[0];",
+                                     "int64_t t_prev = t_us[i] - t_us[0] - (t_us[1] - t_us[0]);"),
+}
+
+
+def battery():
+    """The pins, each with fixed arguments."""
+    yield pins.test_lut_log_closed_form
+    yield pins.test_lut_linear
+    yield pins.test_luma_bt601
+    yield pins.test_flow_q16
+    for a, b, c in [(20, 1, 2), (200, -1, -1), (40, 2, 1), (100, 0, -2)]:
+        yield lambda a=a, b=b, c=c: pins.test_bilinear_of_a_plane(a, b, c)
+    yield pins.test_bilinear_at_integer_positions_is_indexing
+    yield pins.test_adaptive_substeps_is_ceil_of_max_flow
+    yield lambda: pins.test_identical_frames_zero_flow_no_events(oracle.SPARSE, oracle.ACCUM, oracle.LOG)
+    yield lambda: pins.test_identical_frames_zero_flow_no_events(oracle.DENSE, oracle.RESET, oracle.LINEAR)
+    for N in (1, 5, 8):
+        yield lambda N=N: pins.test_uniform_step_gives_floor_of_difference_over_C(N, 9000, 17000)
+    yield pins.test_alternating_steps_give_alternating_bursts
+    yield lambda: pins.test_exhaustive_one_pixel_pairs(7, oracle.LOG, 3001)
+    yield lambda: pins.test_exhaustive_one_pixel_pairs(1, oracle.LINEAR, 7 * 65536 + 5)
+    for m, N in [((1, 0), 3), ((0, -1), 4), ((1, -1), 2), ((-2, 1), 3)]:
+        for ref in (oracle.ACCUM, oracle.RESET):
+            yield lambda m=m, N=N, ref=ref: pins.test_integer_translation_reproduces_shifted_samples(m, N, ref)
+    for N in (3, 8):
+        yield lambda N=N: pins.test_plane_images_with_fractional_flow(N)
+    for N in (2, 5, 8):
+        yield lambda N=N: pins.test_plane_with_subpixel_flow_at_unit_resolution(N)
+    yield pins.test_blend_is_within_half_a_unit_of_the_exact_line
+    yield pins.test_conservation_and_band_invariant
+    yield pins.test_kaiser_difference_frame_special_case
+    yield pins.test_sparse_with_zero_activity_threshold_equals_dense
+    yield pins.test_sparse_misses_pixels_just_under_the_activity_threshold
+    yield pins.test_time_order_and_raster_order
+    yield pins.test_rgb_input_uses_bt601_luma
+    yield pins.test_per_pixel_threshold_maps
+    yield pins.test_adaptive_substeps_per_frame
+
+
+def test_battery_passes_on_the_real_oracle():
+    for pin in battery():
+        pin()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    subs = MUTATIONS[name]
+    if isinstance(subs, tuple):
+        subs = [subs]
+    bad = open(SRC).read()
+    for old, new in subs:
+        assert bad.count(old) >= 1, f"mutation anchor missing: {name}"
+        bad = bad.replace(old, new, 1)
+    c_path = tmp_path / "mutant.c"
+    c_path.write_text(bad)
+    so = tmp_path / "libmutant.so"
+    inc = os.path.dirname(SRC)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-I", inc, "-o", str(so), str(c_path), "-lm"], check=True)
+    oracle.use_library(str(so))
+    caught = []
+    try:
+        for pin in battery():
+            try:
+                pin()
+            except (AssertionError, ValueError):
+                caught.append(getattr(pin, "__name__", "pin"))
+                break
+    finally:
+        oracle.use_library(None)
+    assert caught, f"no pin caught the planted mistake '{name}'"
