@@ -1,0 +1,186 @@
+/*
+ * evsim: GB300-native frame-to-event simulator (C ABI).
+ *
+ * Implements the data-parallel core of the dense and sparse frame
+ * interpolation methods of Ziegler et al., "Real-time event simulation with
+ * frame-based cameras" (arXiv 2209.04634):
+ *   - Sec. III:   consecutive frames are differenced and thresholded; optical
+ *                 flow plus linear interpolation raises the temporal rate.
+ *   - Sec. III-A: dense frame interpolation.  N frames are interpolated along
+ *                 the flow between camera frames i-1 and i; each interpolated
+ *                 frame is compared with a reference and thresholded with
+ *                 C_pos / C_neg (the two-case equations of III-A); the output
+ *                 is a stream of events <x, y, t, p> (Fig. 1 caption).
+ *   - Sec. III-B: sparse frame interpolation.  Only pixels whose change from
+ *                 frame i-1 to frame i reaches an activity threshold are
+ *                 interpolated; the others emit nothing.
+ * The flow itself is an input (the paper computes it with OpenCV; it is not
+ * part of this library).
+ *
+ * Arithmetic (all integer, bit-exact across runs and devices):
+ *   - intensity: Q16 log table LUT[v] = round(65536 ln(v + 1)) (SIM_LOG), or
+ *     LUT[v] = 65536 v (SIM_LINEAR, the paper's linear differences of Sec. III
+ *     with thresholds in 8-bit units as in Table I);
+ *   - flow: float px -> Q16 (NaN -> 0, clamped to +-1024 px, ties to even);
+ *   - substep k of N: offset floor(F k / N); samples at x - offset in frame
+ *     i-1 and x + F - offset in frame i (flow read at the target pixel),
+ *     clamp-to-edge bilinear with 12-bit fractions, blended with the Q12
+ *     weight round-half-up(4096 k / N); substep time t_{i-1} + floor(k dt / N);
+ *   - SIM_REF_ACCUM: per-pixel reference R; D = I - R; D >= Cp emits floor(D/Cp)
+ *     positive events and moves R by that many Cp (likewise for -D >= Cn);
+ *     SIM_REF_RESET: the paper's consecutive difference, strict > Cp / < -Cn,
+ *     at most one event per substep;
+ *   - output order: frame, substep, row, column, repeated crossings adjacent.
+ *
+ * Threading and streams: one handle must not be used from two host threads
+ * at once.  All device work of a handle is ordered on its CUDA stream.
+ *
+ * Errors: functions return SIM_OK (0), SIM_MORE (1, informational) or a
+ * negative SIM_ERR_* code.  Nothing aborts or throws across this boundary.
+ */
+#ifndef EVSIM_H
+#define EVSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define SIM_OK 0
+#define SIM_MORE 1                 /* pop: more events remain */
+#define SIM_ERR_ARG (-1)           /* invalid argument or configuration */
+#define SIM_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define SIM_ERR_OOM (-3)           /* device or host allocation failed */
+#define SIM_ERR_TIME (-4)          /* timestamp not strictly increasing */
+#define SIM_ERR_TIME_RANGE (-5)    /* more than 2^32-1 us after the first frame */
+#define SIM_ERR_EVENT_OVERFLOW (-6)/* a frame's events did not fit; not committed */
+#define SIM_ERR_DEVICE_TIMEOUT (-7)/* a bounded device-side wait gave up */
+#define SIM_ERR_STATE (-8)         /* call not valid in the handle's state */
+#define SIM_ERR_ADMIT (-9)         /* batch: admission refused (memory budget / slots) */
+#define SIM_ERR_NO_DEVICE (-10)    /* no usable CUDA device / kernel image */
+
+/* ---- enumerations ------------------------------------------------------- */
+enum { SIM_LUMA8 = 1, SIM_RGB8 = 3 };          /* bytes per input pixel */
+enum { SIM_DENSE = 0, SIM_SPARSE = 1 };
+enum { SIM_LOG = 0, SIM_LINEAR = 1 };
+enum { SIM_REF_ACCUM = 0, SIM_REF_RESET = 1 };
+enum { SIM_HOST = 0, SIM_DEVICE = 1 };         /* where a buffer lives */
+
+#define SIM_MAX_DIM 8192
+#define SIM_MAX_SUBSTEPS 64
+
+typedef struct sim_s sim_t;   /* opaque, owned by the library */
+
+/* One event, 8 bytes: t = microseconds since the stream's first frame;
+ * yp = (y << 1) | (polarity > 0). */
+typedef struct {
+  uint32_t t_us;
+  uint16_t x;
+  uint16_t yp;
+} sim_event;
+
+typedef struct {
+  int32_t width, height;     /* 1..SIM_MAX_DIM */
+  int32_t pixel_format;      /* SIM_LUMA8 | SIM_RGB8 (BT.601 luma on device) */
+  int32_t mode;              /* SIM_DENSE | SIM_SPARSE */
+  int32_t substeps;          /* > 0: fixed N; 0: N = ceil(max |flow|) per frame */
+  int32_t max_substeps;      /* cap, 1..SIM_MAX_SUBSTEPS */
+  int32_t intensity;         /* SIM_LOG | SIM_LINEAR */
+  int32_t ref_mode;          /* SIM_REF_ACCUM | SIM_REF_RESET */
+  int32_t c_pos_q16;         /* uniform C_pos, Q16 (0.2 log units = 13107) */
+  int32_t c_neg_q16;         /* uniform |C_neg|, Q16 */
+  int32_t c_act_q16;         /* sparse activity threshold, Q16; < 0: min(Cp(x), Cn(x)) */
+  int32_t reserved0;
+  const uint16_t* c_pos_map; /* optional host W*H Q16 per-pixel C_pos (copied at create) */
+  const uint16_t* c_neg_map; /* optional host W*H Q16 per-pixel |C_neg| */
+  int64_t event_capacity;    /* device event buffer (events); 0: default max(2^20, 8 W H) */
+  void* cuda_stream;         /* cudaStream_t to order work on; NULL: library-owned stream */
+} sim_config;
+
+typedef struct {
+  int64_t frames_pushed;     /* frames accepted by sim_push_frame */
+  int64_t frames_committed;  /* frames whose events and state are committed */
+  int64_t events_pending;    /* committed events not yet popped */
+  int64_t events_popped;     /* events returned by sim_pop_events so far */
+  int64_t last_active;       /* sparse: active pixels of the last committed frame */
+  int64_t last_frame_events; /* events of the last committed frame */
+  int64_t flow_clamped;      /* flow components clamped to +-1024 px so far */
+  int32_t last_substeps;     /* N of the last committed frame */
+  int32_t reserved0;
+} sim_stats;
+
+/* Kernel kinds for sim_kernel_time. */
+enum { SIM_K_INIT = 0, SIM_K_FLOWMAX = 1, SIM_K_DENSE = 2, SIM_K_MASK = 3,
+       SIM_K_SPARSE = 4, SIM_K_ORDER = 5, SIM_K_COPY = 6, SIM_K_COUNT = 7 };
+
+/* Fill *cfg with defaults for a width x height luma stream: dense, N = 8,
+ * log intensity, accumulate mode, C = 0.2, library-owned stream. */
+int sim_config_default(sim_config* cfg, int32_t width, int32_t height);
+
+/* Create a simulator.  Allocates all device state (frame ring, reference,
+ * staging and event buffers) and copies the optional threshold maps.
+ * Thresholds must be >= 1; in accumulate mode they must also be at least
+ * (LUT[255] - LUT[0]) / 32766 (12 for SIM_LOG, 511 for SIM_LINEAR) so that one
+ * substep emits at most 32767 events per pixel.  *out is set on SIM_OK only. */
+int sim_create(const sim_config* cfg, sim_t** out);
+
+/* Push camera frame i with the flow from frame i-1 to frame i.
+ *   frame : height rows of pitch_bytes bytes, width * pixel_format bytes used.
+ *   flow  : height * width * 2 floats (dx, dy) in px per frame interval,
+ *           row-major, 8-byte aligned; ignored (may be NULL) on the first push.
+ *   t_us  : timestamp; strictly increasing; < 2^32 us after the first frame.
+ *   mem   : SIM_HOST (copied before return) or SIM_DEVICE (must stay valid
+ *           until the handle's stream has passed this push: sim_sync or the
+ *           next sim_pop_events).
+ * Asynchronous: returns once the work is enqueued.  The first push sets the
+ * reference from frame 0 and emits no events.  A device-side failure (event
+ * overflow) is reported by the next sim_sync / sim_pop_events; the failing
+ * frame and any frame pushed after it are then not committed. */
+int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float* flow,
+                   int64_t t_us, int32_t mem);
+
+/* Copy up to cap committed events, in output order, into out (host or device
+ * memory per mem) and set *n_out.  Returns SIM_MORE if events remain (the next
+ * call continues where this one stopped).  Waits for the handle's stream.
+ * If a pushed frame failed on the device, returns that error code after
+ * delivering the events of the frames committed before it; the handle then
+ * continues from the last committed frame (see sim_stats.frames_committed). */
+int sim_pop_events(sim_t* s, sim_event* out, int64_t cap, int64_t* n_out, int32_t mem);
+
+/* Wait for all work of the handle; returns (and clears) a pending device error. */
+int sim_sync(sim_t* s);
+
+/* Statistics (waits for the handle's stream). */
+int sim_get_stats(sim_t* s, sim_stats* st);
+
+/* Copy the committed per-pixel reference R (Q16, W*H int32, row-major) to
+ * host memory.  In reset mode the library keeps no reference: SIM_ERR_STATE. */
+int sim_get_reference(sim_t* s, int32_t* out_host);
+
+/* Enable (1) or disable (0) per-kernel device timing with CUDA events. */
+int sim_set_profiling(sim_t* s, int32_t enable);
+
+/* Accumulated device time (ms) and launch count of one kernel kind since
+ * profiling was enabled or last reset (reset = 1 clears after reading). */
+int sim_kernel_time(sim_t* s, int32_t kind, double* ms, int64_t* launches, int32_t reset);
+
+/* Restart the stream: drop all committed state, pending events and any
+ * pending error, keep the allocations.  The next push is a first frame.
+ * Waits for the handle's stream. */
+int sim_reset(sim_t* s);
+
+/* Release every resource of the handle (waits for its stream). */
+int sim_destroy(sim_t* s);
+
+/* Static English description of a return code. */
+const char* sim_strerror(int code);
+
+/* Library version, "major.minor.patch". */
+const char* sim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVSIM_H */

@@ -1,0 +1,112 @@
+// Internal structures shared by the kernels (kernels.cu) and the host
+// runtime (runtime.cu) of the evsim library.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace evsim {
+
+// Dense tile: TW x TH pixels, NT threads, 4 pixels per thread (two rows of a
+// warp, columns lane and lane + 32).
+constexpr int TW = 64;
+constexpr int TH = 16;
+constexpr int NT = 256;
+constexpr int NWARP = NT / 32;
+// Largest per-tile flow reach (pixels) served from the shared-memory halo;
+// tiles whose flow reaches further sample global memory instead.
+constexpr int HMAX = 16;
+constexpr int SW = TW + 2 * HMAX;  // shared tile stride (int32 elements)
+constexpr int SH = TH + 2 * HMAX;
+constexpr int MAXN = 64;           // largest substep count
+// Sparse: active pixels per chunk (one per thread).
+constexpr int SCHUNK = NT;
+// Order kernel: segments per chunk.
+constexpr int OCHUNK = 4 * NT;
+// Activity mask: pixels per chunk (8 per thread).
+constexpr int MCHUNK = 8 * NT;
+
+// Look-back status word: [epoch:32][flag:2][value:30].
+constexpr unsigned long long LB_AGG = 1ull << 30;
+constexpr unsigned long long LB_INC = 2ull << 30;
+constexpr unsigned long long LB_VALUE = (1ull << 30) - 1;
+constexpr int MAX_EVENTS_PER_FRAME = (1 << 30) - 1;
+// Bounded spin: polls before a look-back gives up and flags a timeout.
+constexpr int SPIN_LIMIT = 1 << 22;
+
+// Device-resident control block of one stream.  Fields marked "committed"
+// change only when a frame commits; the others are per-frame scratch that the
+// order kernel resets when it finishes a frame.
+struct Ctl {
+  int err;                       // sticky error (0 or a SIM_ERR_* code)
+  int sel;                       // committed: bit0 reference ping-pong, bit1 frame ring
+  int n_frame;                   // substeps of the frame in flight / last frame
+  int frame_fail;                // staging overflow seen while simulating this frame
+  unsigned long long maxf2;      // adaptive: max squared Q16 flow of processed pixels
+  long long t_prev;              // committed: t_{i-1} - t_0 (us)
+  long long cursor;              // committed: events held in the event buffer
+  long long committed;           // committed: frames
+  long long frame_events;        // committed: events of the last committed frame
+  long long active;              // sparse: active pixels of the frame in flight
+  unsigned long long clamped;    // flow components clamped so far
+  unsigned long long stage_top;  // staging bump allocator (events)
+  unsigned int order_ticket;     // order kernel: chunk tickets
+  unsigned int order_done;       // order kernel: chunks finished
+  unsigned int order_exit;       // order kernel: blocks that left the ticket loop
+  unsigned int mask_ticket;      // mask kernel: chunk tickets
+};
+
+struct Ev {  // same layout as sim_event
+  unsigned int t;
+  unsigned int xyp;  // x | (yp << 16)
+};
+
+// Everything a kernel needs for one stream and one pushed frame.
+struct SimParams {
+  int W, H, ch;
+  int tiles_x, tiles_y;
+  int mode, ref_mode, intensity;
+  int n_fixed, n_max;
+  int cp, cn, cact;
+  int pad0;
+  const unsigned short* cpmap;
+  const unsigned short* cnmap;
+  const int* lut;               // 256 Q16 entries (device)
+  const unsigned char* frame;   // current input frame (device)
+  long long pitch;              // bytes per input row
+  const float2* flow;           // H*W (dx, dy)
+  unsigned char* ring0;         // luma frame ring, W bytes per row
+  unsigned char* ring1;
+  int* R0;                      // reference (dense: ping-pong pair; sparse: R0 only)
+  int* R1;
+  int* Rsave;                   // sparse: previous reference of active pixels
+  Ctl* ctl;
+  Ev* staging;
+  unsigned int stage_cap;
+  int pad1;
+  int2* seg;                    // (count, staging offset) per (substep, segment)
+  unsigned long long* order_status;
+  Ev* events;
+  long long event_cap;
+  int* idx;                     // sparse: active pixel indices, raster order
+  unsigned long long* mask_status;
+  long long t_rel;              // t_i - t_0 of this frame (us)
+  unsigned int serial;          // push serial: epoch of the look-back words
+  int pad2;
+};
+
+// Shared-memory bytes of the dense kernel for a substep cap.
+size_t dense_smem_bytes(int n_max);
+size_t sparse_smem_bytes(int n_max);
+
+// Launchers (kernels.cu).  Each returns the cudaError_t of the launch.
+cudaError_t launch_init(const SimParams& p, cudaStream_t st);
+cudaError_t launch_flowmax(const SimParams& p, cudaStream_t st);
+cudaError_t launch_dense(const SimParams& p, cudaStream_t st);
+cudaError_t launch_mask(const SimParams& p, cudaStream_t st, int grid);
+cudaError_t launch_sparse(const SimParams& p, cudaStream_t st, int grid);
+cudaError_t launch_order(const SimParams& p, cudaStream_t st, int grid);
+cudaError_t configure_kernels(int n_max);
+int device_sm_count();
+
+}  // namespace evsim

@@ -1,0 +1,997 @@
+// CUDA kernels of the evsim library (sm_103a).
+//
+// One pushed frame runs, on the handle's stream:
+//   dense : [flowmax, adaptive N only] -> dense -> order
+//   sparse: mask -> sparse -> order
+// The method (Ziegler et al., arXiv 2209.04634, Sec. III-A / III-B) and its
+// integer arithmetic are described in include/evsim.h.  Every kernel checks
+// the stream's sticky error word first and does nothing once it is set.
+//
+// Event order.  Within a frame, events are ordered by (substep, row, column,
+// repeat).  The simulating kernels work pixel-major, so they record each
+// pixel's per-substep count in shared memory, write their events to a
+// staging area in their own local order and publish one (count, staging
+// offset) entry per "segment" (dense: one tile row; sparse: one chunk of
+// active pixels).  The order kernel scans the segment counts in output order
+// (a single-pass scan with decoupled look-back) and gathers the events into
+// the stream's event buffer; its last block commits the frame.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/evsim.h"
+#include "internal.h"
+
+namespace evsim {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *(const volatile unsigned long long*)p;
+}
+__device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
+  *(volatile unsigned long long*)p = v;
+}
+
+// Block-uniform read of the stream's sticky error word (one read per block,
+// so that every thread of a block takes the same early exit).
+__device__ __forceinline__ bool block_error(const int* err) {
+  __shared__ int s_err;
+  if (threadIdx.x == 0) s_err = ld_volatile(err);
+  __syncthreads();
+  return s_err != 0;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Flow component (px, float) -> Q16: NaN -> 0, clamp to +-1024 px, nearest
+// with ties to even.  The scaling by 2^16 is exact in float.
+__device__ __forceinline__ int flow_q16(float f, int& clamped) {
+  if (!(f == f)) return 0;
+  if (f > 1024.f) { f = 1024.f; ++clamped; }
+  if (f < -1024.f) { f = -1024.f; ++clamped; }
+  return __float2int_rn(f * 65536.0f);
+}
+
+// Smallest N >= 1 with N^2 2^32 >= m (= ceil of the largest flow in px), capped.
+__device__ __forceinline__ int adaptive_n(unsigned long long m, int nmax) {
+  int n = 1;
+  while (n < nmax && (unsigned long long)n * n * 4294967296ull < m) ++n;
+  return n;
+}
+
+// a + floor(((b - a) f + 2048) / 4096): Q12-weighted blend, round half up.
+// LOG values span 19 bits so 32-bit products suffice; LINEAR needs 64 bits.
+template <bool WIDE>
+__device__ __forceinline__ int lerp12(int a, int b, int f) {
+  if (WIDE) return a + (int)(((long long)(b - a) * f + 2048) >> 12);
+  return a + (((b - a) * f + 2048) >> 12);
+}
+
+__device__ __forceinline__ int load_luma(const unsigned char* f, long long pitch, int ch,
+                                         int y, int x) {
+  const unsigned char* q = f + (long long)y * pitch + (long long)x * ch;
+  if (ch == 1) return q[0];
+  return (77 * q[0] + 150 * q[1] + 29 * q[2] + 128) >> 8;
+}
+
+// Bilinear tap from a replicate-padded shared tile at a tile-relative Q16
+// position (always inside the filled region).
+template <bool WIDE>
+__device__ __forceinline__ int tap_shared(const int* s, int px, int py) {
+  const int ix = px >> 16, iy = py >> 16;
+  const int fx = (px >> 4) & 0xFFF, fy = (py >> 4) & 0xFFF;
+  const int* q = s + iy * SW + ix;
+  const int top = lerp12<WIDE>(q[0], q[1], fx);
+  const int bot = lerp12<WIDE>(q[SW], q[SW + 1], fx);
+  return lerp12<WIDE>(top, bot, fy);
+}
+
+// Bilinear tap from an 8-bit image in global memory at an absolute Q16
+// position, clamped to the image (clamp-to-edge).
+template <bool WIDE>
+__device__ __forceinline__ int tap_global(const unsigned char* img, long long pitch, int ch,
+                                          int W, int H, const int* slut, int px, int py) {
+  px = min(max(px, 0), (W - 1) << 16);
+  py = min(max(py, 0), (H - 1) << 16);
+  const int ix = px >> 16, iy = py >> 16;
+  const int fx = (px >> 4) & 0xFFF, fy = (py >> 4) & 0xFFF;
+  const int x1 = min(ix + 1, W - 1), y1 = min(iy + 1, H - 1);
+  const int l00 = slut[load_luma(img, pitch, ch, iy, ix)];
+  const int l01 = slut[load_luma(img, pitch, ch, iy, x1)];
+  const int l10 = slut[load_luma(img, pitch, ch, y1, ix)];
+  const int l11 = slut[load_luma(img, pitch, ch, y1, x1)];
+  const int top = lerp12<WIDE>(l00, l01, fx);
+  const int bot = lerp12<WIDE>(l10, l11, fx);
+  return lerp12<WIDE>(top, bot, fy);
+}
+
+// Threshold test of one interpolated value against the reference.
+// ACCUM: every whole threshold crossed is one event and moves R by it.
+// RESET: the paper's consecutive difference, strict comparisons.
+template <bool RESET>
+__device__ __forceinline__ int threshold_step(int I, int& R, int cp, int cn) {
+  const int D = I - R;
+  int n = 0;
+  if (RESET) {
+    n = D > cp ? 1 : (D < -cn ? -1 : 0);
+    R = I;
+  } else {
+    if (D >= cp) {
+      n = D < 2 * cp ? 1 : D / cp;
+      R += n * cp;
+    } else if (D <= -cn) {
+      const int m = -D < 2 * cn ? 1 : (-D) / cn;
+      R -= m * cn;
+      n = -m;
+    }
+  }
+  return n;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive scan of one int per thread over the block; *total gets the sum.
+// s_warp needs NWARP + 1 ints.  Contains barriers: call from all threads.
+__device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int incl = warp_incl_scan(v);
+  if (lane == 31) s_warp[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int s = lane < NWARP ? s_warp[lane] : 0;
+    const int si = warp_incl_scan(s);
+    if (lane < NWARP) s_warp[lane] = si - s;
+    if (lane == NWARP - 1) s_warp[NWARP] = si;
+  }
+  __syncthreads();
+  *total = s_warp[NWARP];
+  const int r = incl - v + s_warp[w];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(FULL, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+// Single-pass scan across chunks with decoupled look-back.  Publishes chunk
+// c's aggregate, walks back over its predecessors (bounded spin) and
+// publishes its inclusive prefix.  Returns the exclusive prefix of chunk c.
+// Values saturate at LB_VALUE, which callers treat as an overflow.
+__device__ long long lookback(unsigned long long* status, int c, unsigned epoch,
+                              long long agg, int* err) {
+  const unsigned long long hi = (unsigned long long)epoch << 32;
+  if (agg > (long long)LB_VALUE) agg = LB_VALUE;
+  if (c == 0) {
+    __threadfence();
+    st_volatile(&status[0], hi | LB_INC | (unsigned long long)agg);
+    return 0;
+  }
+  __threadfence();
+  st_volatile(&status[c], hi | LB_AGG | (unsigned long long)agg);
+  long long excl = 0;
+  int j = c - 1;
+  int spins = 0;
+  while (j >= 0) {
+    const unsigned long long w = ld_volatile(&status[j]);
+    if ((unsigned)(w >> 32) == epoch && (w & (LB_AGG | LB_INC))) {
+      excl += (long long)(w & LB_VALUE);
+      if (w & LB_INC) break;
+      --j;
+    } else {
+      if (++spins > SPIN_LIMIT) {
+        atomicCAS(err, 0, SIM_ERR_DEVICE_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  long long inc = excl + agg;
+  if (inc > (long long)LB_VALUE) inc = LB_VALUE;
+  __threadfence();
+  st_volatile(&status[c], hi | LB_INC | (unsigned long long)inc);
+  return excl;
+}
+
+__device__ __forceinline__ Ev make_event(unsigned t, int x, int y, bool pos) {
+  Ev e;
+  e.t = t;
+  e.xyp = (unsigned)x | ((unsigned)((y << 1) | (pos ? 1 : 0)) << 16);
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// frame 0: fill the frame ring and the reference
+
+__global__ void k_init(SimParams p) {
+  const long long P = (long long)p.W * p.H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
+    const int v = load_luma(p.frame, p.pitch, p.ch, y, x);
+    p.ring0[i] = (unsigned char)v;
+    if (p.ref_mode == SIM_REF_ACCUM) p.R0[i] = p.lut[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// adaptive N (dense): max over all pixels of the squared Q16 flow
+
+__global__ void __launch_bounds__(NT) k_flowmax(SimParams p) {
+  if (block_error(&p.ctl->err)) return;
+  __shared__ unsigned long long s_m[NWARP];
+  const long long P = (long long)p.W * p.H;
+  unsigned long long m = 0;
+  int dummy = 0;
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+    const float2 f = p.flow[i];
+    const long long fx = flow_q16(f.x, dummy), fy = flow_q16(f.y, dummy);
+    const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
+    m = f2 > m ? f2 : m;
+  }
+  m = warp_max_u64(m);
+  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < NWARP; ++w) b = s_m[w] > b ? s_m[w] : b;
+    if (b) atomicMax(&p.ctl->maxf2, b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dense simulation of one 64 x 16 tile
+
+struct DenseLayout {
+  int* sL0;
+  int* sL1;
+  int* slut;
+  int* srow;   // [N][TH] events per (substep, tile row)
+  int* soff;   // [N][TH] tile-local exclusive offsets
+  unsigned* stk;
+  int* swk;
+  short* snk;  // [N][TH][TW] signed event count per pixel-substep
+};
+
+__device__ __forceinline__ DenseLayout dense_layout(unsigned char* raw, int nmax) {
+  DenseLayout L;
+  L.sL0 = (int*)raw;
+  L.sL1 = L.sL0 + SH * SW;
+  L.slut = L.sL1 + SH * SW;
+  L.srow = L.slut + 256;
+  L.soff = L.srow + nmax * TH;
+  L.stk = (unsigned*)(L.soff + nmax * TH);
+  L.swk = (int*)(L.stk + nmax);
+  L.snk = (short*)(L.swk + nmax);
+  return L;
+}
+
+// The four pixels of a thread: columns lane, lane + 32 of rows 2 warp, 2 warp + 1.
+template <bool RESET, bool WIDE, bool FAST>
+__device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLayout& L, int N,
+                                               int tx0, int ty0, const int (&Fx)[4],
+                                               const int (&Fy)[4], int (&R)[4],
+                                               const int (&Cp)[4], const int (&Cn)[4],
+                                               const bool (&inb)[4],
+                                               const unsigned char* ringp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int px[4], py[4], ax[4], ay[4], qx[4], rx[4], qy[4], ry[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
+    // FAST: positions relative to the shared tile origin (tx0 - HMAX, ty0 - HMAX);
+    // otherwise absolute image positions.
+    px[j] = FAST ? (lx + HMAX) << 16 : (tx0 + lx) << 16;
+    py[j] = FAST ? (ly + HMAX) << 16 : (ty0 + ly) << 16;
+    // F = q N + r with 0 <= r < N: offset_k = q k + floor(r k / N)
+    qx[j] = Fx[j] / N;
+    rx[j] = Fx[j] - qx[j] * N;
+    if (rx[j] < 0) { rx[j] += N; qx[j] -= 1; }
+    qy[j] = Fy[j] / N;
+    ry[j] = Fy[j] - qy[j] * N;
+    if (ry[j] < 0) { ry[j] += N; qy[j] -= 1; }
+    ax[j] = 0;
+    ay[j] = 0;
+  }
+  short* nkrow = L.snk + (2 * warp) * TW + lane;
+  for (int k = 0; k < N; ++k) {
+    const int w = L.swk[k];
+    int n[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      px[j] -= qx[j];
+      ax[j] += rx[j];
+      if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
+      py[j] -= qy[j];
+      ay[j] += ry[j];
+      if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
+      int s0, s1;
+      if (FAST) {
+        s0 = tap_shared<WIDE>(L.sL0, px[j], py[j]);
+        s1 = tap_shared<WIDE>(L.sL1, px[j] + Fx[j], py[j] + Fy[j]);
+      } else {
+        s0 = tap_global<WIDE>(ringp, p.W, 1, p.W, p.H, L.slut, px[j], py[j]);
+        s1 = tap_global<WIDE>(p.frame, p.pitch, p.ch, p.W, p.H, L.slut, px[j] + Fx[j],
+                              py[j] + Fy[j]);
+      }
+      const int I = lerp12<WIDE>(s0, s1, w);
+      n[j] = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
+      if (!inb[j]) n[j] = 0;
+    }
+    short* q = nkrow + k * (TH * TW);
+    q[0] = (short)n[0];
+    q[32] = (short)n[1];
+    q[TW] = (short)n[2];
+    q[TW + 32] = (short)n[3];
+    int c0 = abs(n[0]) + abs(n[1]), c1 = abs(n[2]) + abs(n[3]);
+    if (__any_sync(FULL, (c0 | c1) != 0)) {
+      c0 = __reduce_add_sync(FULL, c0);
+      c1 = __reduce_add_sync(FULL, c1);
+      if (lane == 0) {
+        L.srow[k * TH + 2 * warp] = c0;
+        L.srow[k * TH + 2 * warp + 1] = c1;
+      }
+    }
+  }
+}
+
+template <bool RESET, bool MAPS, bool WIDE>
+__global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_warp[NWARP + 1];
+  __shared__ int s_fx, s_fy, s_clamp, s_base, s_fail;
+  Ctl* ctl = p.ctl;
+  if (block_error(&ctl->err)) return;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nmax = p.n_max;
+  const DenseLayout L = dense_layout(smem_raw, nmax);
+  const int tile = blockIdx.x;
+  const int tcx = tile % p.tiles_x, tcy = tile / p.tiles_x;
+  const int tx0 = tcx * TW, ty0 = tcy * TH;
+  const int W = p.W, H = p.H;
+
+  L.slut[tid] = p.lut[tid];
+  if (tid == 0) { s_fx = 0; s_fy = 0; s_clamp = 0; }
+  const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(ctl->maxf2, nmax);
+  const int sel = ctl->sel;
+  const int* Rin = (sel & 1) ? p.R1 : p.R0;
+  int* Rout = (sel & 1) ? p.R0 : p.R1;
+  const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
+  unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
+  if (tile == 0 && tid == 0) ctl->n_frame = N;
+  const long long tprev = ctl->t_prev;
+
+  int Fx[4], Fy[4], R[4], Cp[4], Cn[4];
+  bool inb[4];
+  int clamps = 0;
+  unsigned mfx = 0, mfy = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+    inb[j] = x < W && y < H;
+    Fx[j] = 0; Fy[j] = 0; R[j] = 0; Cp[j] = p.cp; Cn[j] = p.cn;
+    if (inb[j]) {
+      const long long i = (long long)y * W + x;
+      const float2 f = p.flow[i];
+      Fx[j] = flow_q16(f.x, clamps);
+      Fy[j] = flow_q16(f.y, clamps);
+      if (!RESET) R[j] = Rin[i];
+      if (MAPS) { Cp[j] = p.cpmap[i]; Cn[j] = p.cnmap[i]; }
+      mfx = max(mfx, (unsigned)abs(Fx[j]));
+      mfy = max(mfy, (unsigned)abs(Fy[j]));
+    }
+  }
+  mfx = __reduce_max_sync(FULL, mfx);
+  mfy = __reduce_max_sync(FULL, mfy);
+  clamps = __reduce_add_sync(FULL, clamps);
+  if (tid < N) {
+    const int k = tid + 1;
+    L.swk[tid] = (k * 8192 + N) / (2 * N);
+    const long long dt = p.t_rel - tprev;
+    L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
+  }
+  for (int e = tid; e < N * TH; e += NT) L.srow[e] = 0;
+  __syncthreads();
+  if (lane == 0) {
+    atomicMax(&s_fx, (int)mfx);
+    atomicMax(&s_fy, (int)mfy);
+    if (clamps) atomicAdd(&s_clamp, clamps);
+  }
+  __syncthreads();
+  if (tid == 0 && s_clamp) atomicAdd(&ctl->clamped, (unsigned long long)s_clamp);
+  // Reach of every tap of the tile: floor(max |F|) + 1 pixels on each side.
+  const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
+  const bool fast = hx <= HMAX && hy <= HMAX;
+
+  if (fast) {
+    // Replicate-padded halo tiles of both log frames; the tile interior of the
+    // new frame also goes to the frame ring for the next push.
+    const int c0 = HMAX - hx, c1 = HMAX + TW + hx;
+    const int r0 = HMAX - hy, r1 = HMAX + TH + hy;
+    for (int sr = r0 + warp; sr < r1; sr += NWARP) {
+      const int ry = ty0 - HMAX + sr;
+      const int gy = min(max(ry, 0), H - 1);
+      for (int sc = c0 + lane; sc < c1; sc += 32) {
+        const int rxx = tx0 - HMAX + sc;
+        const int gx = min(max(rxx, 0), W - 1);
+        const int vp = ringp[(long long)gy * W + gx];
+        const int vc = load_luma(p.frame, p.pitch, p.ch, gy, gx);
+        L.sL0[sr * SW + sc] = L.slut[vp];
+        L.sL1[sr * SW + sc] = L.slut[vc];
+        if (ry == gy && rxx == gx && sr >= HMAX && sr < HMAX + TH && sc >= HMAX &&
+            sc < HMAX + TW)
+          ringn[(long long)gy * W + gx] = (unsigned char)vc;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!inb[j]) continue;
+      const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+      ringn[(long long)y * W + x] = (unsigned char)load_luma(p.frame, p.pitch, p.ch, y, x);
+    }
+  }
+  __syncthreads();
+  if (RESET) {
+    // Consecutive differences start from frame i-1 itself.
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!inb[j]) continue;
+      const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+      R[j] = L.slut[ringp[(long long)y * W + x]];
+    }
+  }
+
+  if (fast)
+    dense_substeps<RESET, WIDE, true>(p, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
+  else
+    dense_substeps<RESET, WIDE, false>(p, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
+
+  if (!RESET) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!inb[j]) continue;
+      const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+      Rout[(long long)y * W + x] = R[j];
+    }
+  }
+  __syncthreads();
+
+  // Tile-local offsets of the (substep, row) segments, substep-major.
+  const int E = N * TH;
+  int v[4], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = 4 * tid + q;
+    v[q] = e < E ? L.srow[e] : 0;
+    sum += v[q];
+  }
+  int total;
+  int ex = block_excl_scan(sum, s_warp, &total);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = 4 * tid + q;
+    if (e < E) L.soff[e] = ex;
+    ex += v[q];
+  }
+  if (tid == 0) {
+    unsigned long long base = 0;
+    int fail = 0;
+    if (total > 0) {
+      base = atomicAdd(&ctl->stage_top, (unsigned long long)total);
+      if (base + (unsigned long long)total > (unsigned long long)p.stage_cap) {
+        fail = 1;
+        atomicExch(&ctl->frame_fail, 1);
+      }
+    }
+    s_base = fail ? 0 : (int)base;
+    s_fail = fail;
+  }
+  __syncthreads();
+  const int base = s_base;
+  const bool fail = s_fail != 0;
+  for (int e = tid; e < E; e += NT) {
+    const int k = e / TH, ty = e % TH, y = ty0 + ty;
+    if (y < H)
+      p.seg[((long long)k * H + y) * p.tiles_x + tcx] =
+          make_int2(fail ? 0 : L.srow[e], base + L.soff[e]);
+  }
+  if (fail || total == 0) return;
+
+  // Emission: each warp writes the events of its two rows, substep by substep.
+  const unsigned lt = lanemask_lt();
+  for (int k = 0; k < N; ++k) {
+    const unsigned tk = L.stk[k];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int ty = 2 * warp + r;
+      const int e = k * TH + ty;
+      if (L.srow[e] == 0) continue;
+      const int y = ty0 + ty;
+      const unsigned o = (unsigned)base + (unsigned)L.soff[e];
+      const int na = L.snk[e * TW + lane], nb = L.snk[e * TW + lane + 32];
+      const int aa = abs(na), ab = abs(nb);
+      const int xa = tx0 + lane, xb = tx0 + lane + 32;
+      if (__all_sync(FULL, (aa | ab) <= 1)) {
+        const unsigned ba = __ballot_sync(FULL, aa != 0), bb = __ballot_sync(FULL, ab != 0);
+        if (aa) p.staging[o + __popc(ba & lt)] = make_event(tk, xa, y, na > 0);
+        if (ab) p.staging[o + __popc(ba) + __popc(bb & lt)] = make_event(tk, xb, y, nb > 0);
+      } else {
+        const int ia = warp_incl_scan(aa);
+        const int ta = __shfl_sync(FULL, ia, 31);
+        const int ib = warp_incl_scan(ab);
+        const Ev ea = make_event(tk, xa, y, na > 0), eb = make_event(tk, xb, y, nb > 0);
+        const unsigned oa = o + ia - aa, ob = o + ta + ib - ab;
+        for (int m = 0; m < aa; ++m) p.staging[oa + m] = ea;
+        for (int m = 0; m < ab; ++m) p.staging[ob + m] = eb;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sparse: activity mask and order-preserving compaction of active pixels
+
+__global__ void __launch_bounds__(NT) k_mask(SimParams p) {
+  __shared__ int slut[256];
+  __shared__ int s_warp[NWARP + 1];
+  __shared__ int s_c;
+  __shared__ long long s_prefix;
+  __shared__ unsigned long long s_m[NWARP];
+  Ctl* ctl = p.ctl;
+  if (block_error(&ctl->err)) return;
+  const int tid = threadIdx.x;
+  slut[tid] = p.lut[tid];
+  const int sel = ctl->sel;
+  const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
+  unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
+  const long long P = (long long)p.W * p.H;
+  const int nchunks = (int)((P + MCHUNK - 1) / MCHUNK);
+  const bool adaptive = p.n_fixed == 0;
+  unsigned long long mloc = 0;
+  int dummy = 0;
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) s_c = (int)atomicAdd(&ctl->mask_ticket, 1u);
+    __syncthreads();
+    const int c = s_c;
+    if (c >= nchunks) break;
+    const long long i0 = (long long)c * MCHUNK + 8 * tid;
+    unsigned flags = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const long long i = i0 + q;
+      if (i >= P) break;
+      const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
+      const int vp = ringp[i];
+      const int vc = load_luma(p.frame, p.pitch, p.ch, y, x);
+      ringn[i] = (unsigned char)vc;
+      const int d = abs(slut[vc] - slut[vp]);
+      int ca = p.cact;
+      if (ca < 0) {
+        const int a = p.cpmap ? p.cpmap[i] : p.cp;
+        const int b = p.cnmap ? p.cnmap[i] : p.cn;
+        ca = min(a, b);
+      }
+      if (d >= ca) {
+        flags |= 1u << q;
+        ++cnt;
+        if (adaptive) {
+          const float2 f = p.flow[i];
+          const long long fx = flow_q16(f.x, dummy), fy = flow_q16(f.y, dummy);
+          const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
+          mloc = f2 > mloc ? f2 : mloc;
+        }
+      }
+    }
+    int total;
+    int ex = block_excl_scan(cnt, s_warp, &total);
+    if (tid == 0) s_prefix = lookback(p.mask_status, c, p.serial, total, &ctl->err);
+    __syncthreads();
+    long long o = s_prefix + ex;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (flags & (1u << q)) p.idx[o++] = (int)(i0 + q);
+    if (c == nchunks - 1 && tid == 0) ctl->active = s_prefix + total;
+    __syncthreads();
+  }
+  if (adaptive) {
+    mloc = warp_max_u64(mloc);
+    if ((tid & 31) == 0) s_m[tid >> 5] = mloc;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long b = 0;
+      for (int w = 0; w < NWARP; ++w) b = s_m[w] > b ? s_m[w] : b;
+      if (b) atomicMax(&ctl->maxf2, b);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sparse simulation: one active pixel per thread, chunks of NT active pixels
+
+template <bool RESET, bool MAPS, bool WIDE>
+__global__ void __launch_bounds__(NT) k_sparse(SimParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_warp[NWARP + 1];
+  __shared__ int s_base, s_fail, s_clamp;
+  Ctl* ctl = p.ctl;
+  if (block_error(&ctl->err)) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nmax = p.n_max;
+  int* slut = (int*)smem_raw;
+  int* swk = slut + 256;
+  unsigned* stk = (unsigned*)(swk + nmax);
+  int* swpre = (int*)(stk + nmax);     // [N][NWARP] per-warp counts -> prefixes
+  int* skoff = swpre + nmax * NWARP;   // [N] chunk-local offset of each substep
+  short* snk = (short*)(skoff + nmax); // [N][NT]
+
+  slut[tid] = p.lut[tid];
+  if (tid == 0) s_clamp = 0;
+  const long long A = ctl->active;
+  const int S = (int)((A + SCHUNK - 1) / SCHUNK);
+  const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(ctl->maxf2, nmax);
+  if (blockIdx.x == 0 && tid == 0) ctl->n_frame = N;
+  const int sel = ctl->sel;
+  const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
+  const unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
+  const long long tprev = ctl->t_prev;
+  if (tid < N) {
+    const int k = tid + 1;
+    swk[tid] = (k * 8192 + N) / (2 * N);
+    const long long dt = p.t_rel - tprev;
+    stk[tid] = (unsigned)(tprev + (k * dt) / N);
+  }
+  const int W = p.W, H = p.H;
+  const unsigned lt = lanemask_lt();
+  int clamps = 0;
+
+  for (int c = blockIdx.x; c < S; c += gridDim.x) {
+    for (int e = tid; e < N * NWARP; e += NT) swpre[e] = 0;
+    __syncthreads();
+    const long long j = (long long)c * SCHUNK + tid;
+    const bool act = j < A;
+    const int i = act ? p.idx[j] : 0;
+    const int y = i / W, x = i - y * W;
+    int Fx = 0, Fy = 0, R = 0, cp = p.cp, cn = p.cn;
+    if (act) {
+      const float2 f = p.flow[i];
+      Fx = flow_q16(f.x, clamps);
+      Fy = flow_q16(f.y, clamps);
+      if (MAPS) { cp = p.cpmap[i]; cn = p.cnmap[i]; }
+      if (RESET) {
+        R = slut[ringp[i]];
+      } else {
+        R = p.R0[i];
+        p.Rsave[j] = R;
+      }
+    }
+    int qx = Fx / N, rx = Fx - qx * N;
+    if (rx < 0) { rx += N; qx -= 1; }
+    int qy = Fy / N, ry = Fy - qy * N;
+    if (ry < 0) { ry += N; qy -= 1; }
+    int px = x << 16, py = y << 16, ax = 0, ay = 0;
+    for (int k = 0; k < N; ++k) {
+      px -= qx;
+      ax += rx;
+      if (ax >= N) { ax -= N; px -= 1; }
+      py -= qy;
+      ay += ry;
+      if (ay >= N) { ay -= N; py -= 1; }
+      const int s0 = tap_global<WIDE>(ringp, W, 1, W, H, slut, px, py);
+      const int s1 = tap_global<WIDE>(ringn, W, 1, W, H, slut, px + Fx, py + Fy);
+      const int I = lerp12<WIDE>(s0, s1, swk[k]);
+      int n = threshold_step<RESET>(I, R, cp, cn);
+      if (!act) n = 0;
+      snk[k * NT + tid] = (short)n;
+      if (__any_sync(FULL, n != 0)) {
+        const int cw = __reduce_add_sync(FULL, abs(n));
+        if (lane == 0) swpre[k * NWARP + warp] = cw;
+      }
+    }
+    if (!RESET && act) p.R0[i] = R;
+    __syncthreads();
+    int tot = 0;
+    if (tid < N) {
+      for (int w = 0; w < NWARP; ++w) {
+        const int v = swpre[tid * NWARP + w];
+        swpre[tid * NWARP + w] = tot;
+        tot += v;
+      }
+    }
+    int T;
+    const int ex = block_excl_scan(tot, s_warp, &T);
+    if (tid < N) skoff[tid] = ex;
+    if (tid == 0) {
+      unsigned long long base = 0;
+      int fail = 0;
+      if (T > 0) {
+        base = atomicAdd(&ctl->stage_top, (unsigned long long)T);
+        if (base + (unsigned long long)T > (unsigned long long)p.stage_cap) {
+          fail = 1;
+          atomicExch(&ctl->frame_fail, 1);
+        }
+      }
+      s_base = fail ? 0 : (int)base;
+      s_fail = fail;
+    }
+    __syncthreads();
+    const int base = s_base;
+    const bool fail = s_fail != 0;
+    if (tid < N) p.seg[(long long)tid * S + c] = make_int2(fail ? 0 : tot, base + skoff[tid]);
+    if (!fail && T > 0) {
+      for (int k = 0; k < N; ++k) {
+        const int n = snk[k * NT + tid];
+        const int a = abs(n);
+        if (!__any_sync(FULL, a != 0)) continue;
+        const unsigned o = (unsigned)base + (unsigned)skoff[k] + (unsigned)swpre[k * NWARP + warp];
+        const Ev ev = make_event(stk[k], x, y, n > 0);
+        if (__all_sync(FULL, a <= 1)) {
+          const unsigned b = __ballot_sync(FULL, a != 0);
+          if (a) p.staging[o + __popc(b & lt)] = ev;
+        } else {
+          const int ia = warp_incl_scan(a);
+          for (int m = 0; m < a; ++m) p.staging[o + ia - a + m] = ev;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  clamps = __reduce_add_sync(FULL, clamps);
+  if (lane == 0 && clamps) atomicAdd(&s_clamp, clamps);
+  __syncthreads();
+  if (tid == 0 && s_clamp) atomicAdd(&ctl->clamped, (unsigned long long)s_clamp);
+}
+
+// ---------------------------------------------------------------------------
+// order: scan segment counts in output order, gather events, commit the frame
+
+__global__ void __launch_bounds__(NT) k_order(SimParams p) {
+  __shared__ int s_ex[OCHUNK];
+  __shared__ int s_src[OCHUNK];
+  __shared__ int s_warp[NWARP + 1];
+  __shared__ int s_c, s_last;
+  __shared__ long long s_prefix;
+  Ctl* ctl = p.ctl;
+  if (block_error(&ctl->err)) return;
+  const int tid = threadIdx.x;
+  const int N = ctl->n_frame;
+  const bool sparse = p.mode == SIM_SPARSE;
+  const long long A = sparse ? ctl->active : 0;
+  const long long S = sparse ? (A + SCHUNK - 1) / SCHUNK : (long long)p.H * p.tiles_x;
+  const long long nseg = (long long)N * S;
+  const int nchunks = (int)max(1LL, (nseg + OCHUNK - 1) / OCHUNK);
+  const long long cursor = ctl->cursor;
+
+  for (;;) {
+    if (tid == 0) s_c = (int)atomicAdd(&ctl->order_ticket, 1u);
+    __syncthreads();
+    const int c = s_c;
+    if (c >= nchunks) break;
+    const long long s0 = (long long)c * OCHUNK;
+    int cnt[4], src[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long si = s0 + 4 * tid + q;
+      cnt[q] = 0;
+      src[q] = 0;
+      if (si < nseg) {
+        const int2 e = p.seg[si];
+        cnt[q] = e.x;
+        src[q] = e.y;
+      }
+      sum += cnt[q];
+    }
+    int total;
+    int ex = block_excl_scan(sum, s_warp, &total);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s_ex[4 * tid + q] = ex;
+      s_src[4 * tid + q] = src[q];
+      ex += cnt[q];
+    }
+    if (tid == 0) s_prefix = lookback(p.order_status, c, p.serial, total, &ctl->err);
+    __syncthreads();
+    const long long base = cursor + s_prefix;
+    for (int jj = tid; jj < total; jj += NT) {
+      int lo = 0, hi = OCHUNK;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_ex[mid] <= jj) lo = mid; else hi = mid;
+      }
+      const long long dst = base + jj;
+      if (dst < p.event_cap) p.events[dst] = p.staging[s_src[lo] + (jj - s_ex[lo])];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const unsigned d = atomicAdd(&ctl->order_done, 1u);
+      s_last = d == (unsigned)(nchunks - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      // This block finished the frame's last chunk: commit or fail the frame.
+      __shared__ int s_ok;
+      if (tid == 0) {
+        __threadfence();
+        const unsigned long long w = ld_volatile(&p.order_status[nchunks - 1]);
+        const long long tot = (long long)(w & LB_VALUE);
+        const bool over = ctl->frame_fail != 0 || tot >= (long long)LB_VALUE ||
+                          cursor + tot > p.event_cap;
+        int ok = 0;
+        if (ld_volatile(&ctl->err) == 0) {
+          if (over) {
+            atomicCAS(&ctl->err, 0, SIM_ERR_EVENT_OVERFLOW);
+          } else {
+            int flip = 2;
+            if (!sparse && p.ref_mode == SIM_REF_ACCUM) flip |= 1;
+            ctl->cursor = cursor + tot;
+            ctl->sel ^= flip;
+            ctl->t_prev = p.t_rel;
+            ctl->committed += 1;
+            ctl->frame_events = tot;
+            ok = 1;
+          }
+        }
+        ctl->stage_top = 0;
+        ctl->order_done = 0;
+        ctl->mask_ticket = 0;
+        ctl->maxf2 = 0;
+        ctl->frame_fail = 0;
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok && sparse && p.ref_mode == SIM_REF_ACCUM) {
+        // Roll back the in-place reference of the active pixels.
+        for (long long jj = tid; jj < A; jj += NT) p.R0[p.idx[jj]] = p.Rsave[jj];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const unsigned e = atomicAdd(&ctl->order_exit, 1u);
+    if (e == gridDim.x - 1) {  // every block has left the ticket loop
+      ctl->order_ticket = 0;
+      ctl->order_exit = 0;
+    }
+  }
+}
+
+template <bool RESET, bool MAPS, bool WIDE>
+void set_dense_attr(size_t bytes) {
+  cudaFuncSetAttribute(k_dense<RESET, MAPS, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bytes);
+}
+
+template <bool RESET, bool MAPS, bool WIDE>
+void set_sparse_attr(size_t bytes) {
+  cudaFuncSetAttribute(k_sparse<RESET, MAPS, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bytes);
+}
+
+}  // namespace
+
+size_t dense_smem_bytes(int n_max) {
+  return (size_t)(2 * SH * SW + 256 + 2 * n_max * TH + 2 * n_max) * 4 +
+         (size_t)n_max * TH * TW * 2;
+}
+
+size_t sparse_smem_bytes(int n_max) {
+  return (size_t)(256 + 2 * n_max + n_max * NWARP + n_max) * 4 + (size_t)n_max * NT * 2;
+}
+
+int device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t configure_kernels(int n_max) {
+  const size_t d = dense_smem_bytes(n_max), s = sparse_smem_bytes(n_max);
+  set_dense_attr<false, false, false>(d);
+  set_dense_attr<false, true, false>(d);
+  set_dense_attr<false, false, true>(d);
+  set_dense_attr<false, true, true>(d);
+  set_dense_attr<true, false, false>(d);
+  set_dense_attr<true, true, false>(d);
+  set_dense_attr<true, false, true>(d);
+  set_dense_attr<true, true, true>(d);
+  set_sparse_attr<false, false, false>(s);
+  set_sparse_attr<false, true, false>(s);
+  set_sparse_attr<false, false, true>(s);
+  set_sparse_attr<false, true, true>(s);
+  set_sparse_attr<true, false, false>(s);
+  set_sparse_attr<true, true, false>(s);
+  set_sparse_attr<true, false, true>(s);
+  set_sparse_attr<true, true, true>(s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const SimParams& p, cudaStream_t st) {
+  const long long P = (long long)p.W * p.H;
+  const int grid = (int)std::min<long long>((P + NT - 1) / NT, 4096);
+  k_init<<<grid, NT, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flowmax(const SimParams& p, cudaStream_t st) {
+  const long long P = (long long)p.W * p.H;
+  const int sms = device_sm_count();
+  const int grid = (int)std::max(1LL, std::min<long long>((P + NT - 1) / NT, (long long)sms * 4));
+  k_flowmax<<<grid, NT, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense(const SimParams& p, cudaStream_t st) {
+  const int grid = p.tiles_x * p.tiles_y;
+  const size_t sm = dense_smem_bytes(p.n_max);
+  const bool reset = p.ref_mode == SIM_REF_RESET;
+  const bool maps = p.cpmap != nullptr;
+  const bool wide = p.intensity == SIM_LINEAR;
+#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NT, sm, st>>>(p)
+  if (!reset && !maps && !wide) EVSIM_DENSE(false, false, false);
+  else if (!reset && maps && !wide) EVSIM_DENSE(false, true, false);
+  else if (!reset && !maps && wide) EVSIM_DENSE(false, false, true);
+  else if (!reset && maps && wide) EVSIM_DENSE(false, true, true);
+  else if (reset && !maps && !wide) EVSIM_DENSE(true, false, false);
+  else if (reset && maps && !wide) EVSIM_DENSE(true, true, false);
+  else if (reset && !maps && wide) EVSIM_DENSE(true, false, true);
+  else EVSIM_DENSE(true, true, true);
+#undef EVSIM_DENSE
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask(const SimParams& p, cudaStream_t st, int grid) {
+  k_mask<<<grid, NT, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sparse(const SimParams& p, cudaStream_t st, int grid) {
+  const size_t sm = sparse_smem_bytes(p.n_max);
+  const bool reset = p.ref_mode == SIM_REF_RESET;
+  const bool maps = p.cpmap != nullptr;
+  const bool wide = p.intensity == SIM_LINEAR;
+#define EVSIM_SPARSE(R, M, Wd) k_sparse<R, M, Wd><<<grid, NT, sm, st>>>(p)
+  if (!reset && !maps && !wide) EVSIM_SPARSE(false, false, false);
+  else if (!reset && maps && !wide) EVSIM_SPARSE(false, true, false);
+  else if (!reset && !maps && wide) EVSIM_SPARSE(false, false, true);
+  else if (!reset && maps && wide) EVSIM_SPARSE(false, true, true);
+  else if (reset && !maps && !wide) EVSIM_SPARSE(true, false, false);
+  else if (reset && maps && !wide) EVSIM_SPARSE(true, true, false);
+  else if (reset && !maps && wide) EVSIM_SPARSE(true, false, true);
+  else EVSIM_SPARSE(true, true, true);
+#undef EVSIM_SPARSE
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const SimParams& p, cudaStream_t st, int grid) {
+  k_order<<<grid, NT, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace evsim

@@ -1,0 +1,566 @@
+// Host runtime and C ABI of the evsim library: handle state, device
+// allocation, per-push launch sequence, event pop, error recovery, profiling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/evsim.h"
+#include "internal.h"
+
+using evsim::Ctl;
+using evsim::Ev;
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct sim_s {
+  sim_config cfg{};
+  int W = 0, H = 0, ch = 1;
+  long long P = 0;
+  int n_max = 0;
+  int tiles_x = 0, tiles_y = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int sms = 1;
+
+  int* d_lut = nullptr;
+  unsigned short* d_cpmap = nullptr;
+  unsigned short* d_cnmap = nullptr;
+  unsigned char* d_ring[2] = {nullptr, nullptr};
+  int* d_R[2] = {nullptr, nullptr};
+  int* d_Rsave = nullptr;
+  Ctl* d_ctl = nullptr;
+  Ev* d_staging = nullptr;
+  Ev* d_events = nullptr;
+  int2* d_seg = nullptr;
+  unsigned long long* d_order_status = nullptr;
+  unsigned long long* d_mask_status = nullptr;
+  int* d_idx = nullptr;
+  unsigned char* d_frame_stage = nullptr;
+  float2* d_flow_stage = nullptr;
+  long long event_cap = 0;
+  unsigned stage_cap = 0;
+  long long seg_cap = 0;
+  int order_grid = 1, mask_grid = 1, sparse_grid = 1;
+
+  // host shadow of the stream
+  bool have_first = false;
+  long long t0 = 0, t_last = 0;
+  long long pushed = 0;
+  unsigned serial = 0;
+  long long popped = 0;
+  long long popped_total = 0;
+
+  bool prof = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[SIM_K_COUNT] = {};
+  long long prof_n[SIM_K_COUNT] = {};
+};
+
+namespace {
+
+std::mutex g_attr_mu;
+int g_attr_nmax = 0;
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void build_lut(int intensity, int lut[256]) {
+  for (int v = 0; v < 256; ++v) {
+    if (intensity == SIM_LINEAR)
+      lut[v] = v * 65536;
+    else
+      lut[v] = (int)std::nearbyint(65536.0 * std::log((double)v + 1.0));
+  }
+}
+
+void free_all(sim_t* s) {
+  cudaFree(s->d_lut);
+  cudaFree(s->d_cpmap);
+  cudaFree(s->d_cnmap);
+  cudaFree(s->d_ring[0]);
+  cudaFree(s->d_ring[1]);
+  cudaFree(s->d_R[0]);
+  cudaFree(s->d_R[1]);
+  cudaFree(s->d_Rsave);
+  cudaFree(s->d_ctl);
+  cudaFree(s->d_staging);
+  cudaFree(s->d_events);
+  cudaFree(s->d_seg);
+  cudaFree(s->d_order_status);
+  cudaFree(s->d_mask_status);
+  cudaFree(s->d_idx);
+  cudaFree(s->d_frame_stage);
+  cudaFree(s->d_flow_stage);
+  for (auto& r : s->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : s->pool) cudaEventDestroy(e);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+}
+
+evsim::SimParams make_params(const sim_t* s) {
+  evsim::SimParams p{};
+  p.W = s->W;
+  p.H = s->H;
+  p.ch = s->ch;
+  p.tiles_x = s->tiles_x;
+  p.tiles_y = s->tiles_y;
+  p.mode = s->cfg.mode;
+  p.ref_mode = s->cfg.ref_mode;
+  p.intensity = s->cfg.intensity;
+  p.n_fixed = s->cfg.substeps;
+  p.n_max = s->n_max;
+  p.cp = s->cfg.c_pos_q16;
+  p.cn = s->cfg.c_neg_q16;
+  p.cact = s->cfg.c_act_q16;
+  p.cpmap = s->d_cpmap;
+  p.cnmap = s->d_cnmap;
+  p.lut = s->d_lut;
+  p.ring0 = s->d_ring[0];
+  p.ring1 = s->d_ring[1];
+  p.R0 = s->d_R[0];
+  p.R1 = s->d_R[1];
+  p.Rsave = s->d_Rsave;
+  p.ctl = s->d_ctl;
+  p.staging = s->d_staging;
+  p.stage_cap = s->stage_cap;
+  p.seg = s->d_seg;
+  p.order_status = s->d_order_status;
+  p.events = s->d_events;
+  p.event_cap = s->event_cap;
+  p.idx = s->d_idx;
+  p.mask_status = s->d_mask_status;
+  return p;
+}
+
+int cuda_rc(cudaError_t e) {
+  if (e == cudaSuccess) return SIM_OK;
+  if (e == cudaErrorMemoryAllocation) return SIM_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver || e == cudaErrorNoKernelImageForDevice)
+    return SIM_ERR_NO_DEVICE;
+  return SIM_ERR_CUDA;
+}
+
+cudaEvent_t pool_get(sim_t* s) {
+  if (!s->pool.empty()) {
+    cudaEvent_t e = s->pool.back();
+    s->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch wrapper: records a CUDA event pair around the launch when profiling.
+template <class F>
+cudaError_t timed(sim_t* s, int kind, F&& launch) {
+  if (!s->prof) return launch();
+  ProfRec r{kind, pool_get(s), pool_get(s)};
+  cudaEventRecord(r.a, s->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(r.b, s->stream);
+  s->pending.push_back(r);
+  return e;
+}
+
+void prof_collect(sim_t* s) {
+  if (s->pending.empty()) return;
+  cudaStreamSynchronize(s->stream);
+  for (auto& r : s->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      s->prof_ms[r.kind] += ms;
+      s->prof_n[r.kind] += 1;
+    }
+    s->pool.push_back(r.a);
+    s->pool.push_back(r.b);
+  }
+  s->pending.clear();
+}
+
+// Read the control block (after the stream is idle).
+int read_ctl(sim_t* s, Ctl* c) {
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_rc(e);
+  e = cudaMemcpy(c, s->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+  return cuda_rc(e);
+}
+
+// After a device-side failure: clear the error and the per-frame scratch, and
+// roll the host shadow back to the last committed frame.
+int recover(sim_t* s, Ctl* c) {
+  c->err = 0;
+  c->frame_fail = 0;
+  c->maxf2 = 0;
+  c->stage_top = 0;
+  c->order_ticket = 0;
+  c->order_done = 0;
+  c->order_exit = 0;
+  c->mask_ticket = 0;
+  s->t_last = s->t0 + c->t_prev;
+  cudaError_t e = cudaMemcpy(s->d_ctl, c, sizeof(Ctl), cudaMemcpyHostToDevice);
+  return cuda_rc(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sim_version(void) { return "0.1.0"; }
+
+const char* sim_strerror(int code) {
+  switch (code) {
+    case SIM_OK: return "ok";
+    case SIM_MORE: return "more events remain";
+    case SIM_ERR_ARG: return "invalid argument";
+    case SIM_ERR_CUDA: return "CUDA runtime error";
+    case SIM_ERR_OOM: return "out of memory";
+    case SIM_ERR_TIME: return "timestamp not strictly increasing";
+    case SIM_ERR_TIME_RANGE: return "timestamp more than 2^32-1 us after the first frame";
+    case SIM_ERR_EVENT_OVERFLOW: return "event buffer overflow; frame not committed";
+    case SIM_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case SIM_ERR_STATE: return "call not valid in this state";
+    case SIM_ERR_ADMIT: return "admission refused";
+    case SIM_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown error";
+  }
+}
+
+int sim_config_default(sim_config* cfg, int32_t width, int32_t height) {
+  if (!cfg) return SIM_ERR_ARG;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->width = width;
+  cfg->height = height;
+  cfg->pixel_format = SIM_LUMA8;
+  cfg->mode = SIM_DENSE;
+  cfg->substeps = 8;
+  cfg->max_substeps = 16;
+  cfg->intensity = SIM_LOG;
+  cfg->ref_mode = SIM_REF_ACCUM;
+  cfg->c_pos_q16 = 13107;
+  cfg->c_neg_q16 = 13107;
+  cfg->c_act_q16 = -1;
+  return SIM_OK;
+}
+
+int sim_create(const sim_config* cfg, sim_t** out) {
+  if (!cfg || !out) return SIM_ERR_ARG;
+  const sim_config& c = *cfg;
+  if (c.width < 1 || c.height < 1 || c.width > SIM_MAX_DIM || c.height > SIM_MAX_DIM) return SIM_ERR_ARG;
+  if (c.pixel_format != SIM_LUMA8 && c.pixel_format != SIM_RGB8) return SIM_ERR_ARG;
+  if (c.mode != SIM_DENSE && c.mode != SIM_SPARSE) return SIM_ERR_ARG;
+  if (c.intensity != SIM_LOG && c.intensity != SIM_LINEAR) return SIM_ERR_ARG;
+  if (c.ref_mode != SIM_REF_ACCUM && c.ref_mode != SIM_REF_RESET) return SIM_ERR_ARG;
+  if (c.substeps < 0 || c.substeps > SIM_MAX_SUBSTEPS) return SIM_ERR_ARG;
+  if (c.substeps == 0 && (c.max_substeps < 1 || c.max_substeps > SIM_MAX_SUBSTEPS)) return SIM_ERR_ARG;
+  if (c.event_capacity < 0 || c.event_capacity > evsim::MAX_EVENTS_PER_FRAME - 1) return SIM_ERR_ARG;
+
+  int lut[256];
+  build_lut(c.intensity, lut);
+  // Thresholds: >= 1, < 2^30; accumulate mode also bounds the events of one
+  // pixel-substep to 32767 (they are counted in 16 bits).
+  const long long range = (long long)lut[255] - lut[0];
+  const long long cmin = c.ref_mode == SIM_REF_ACCUM ? (range + 32765) / 32766 : 1;
+  auto bad_c = [&](long long v) { return v < cmin || v >= (1LL << 30); };
+  const long long P = (long long)c.width * c.height;
+  if (!c.c_pos_map && bad_c(c.c_pos_q16)) return SIM_ERR_ARG;
+  if (!c.c_neg_map && bad_c(c.c_neg_q16)) return SIM_ERR_ARG;
+  if ((c.c_pos_map == nullptr) != (c.c_neg_map == nullptr)) return SIM_ERR_ARG;
+  if (c.c_pos_map) {
+    for (long long i = 0; i < P; ++i)
+      if (bad_c(c.c_pos_map[i]) || bad_c(c.c_neg_map[i])) return SIM_ERR_ARG;
+  }
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SIM_ERR_NO_DEVICE;
+
+  sim_t* s = new (std::nothrow) sim_t();
+  if (!s) return SIM_ERR_OOM;
+  s->cfg = c;
+  s->cfg.c_pos_map = nullptr;
+  s->cfg.c_neg_map = nullptr;
+  s->W = c.width;
+  s->H = c.height;
+  s->ch = c.pixel_format;
+  s->P = P;
+  s->n_max = c.substeps > 0 ? c.substeps : c.max_substeps;
+  s->tiles_x = (c.width + evsim::TW - 1) / evsim::TW;
+  s->tiles_y = (c.height + evsim::TH - 1) / evsim::TH;
+  cudaGetDevice(&s->device);
+  s->sms = std::max(1, evsim::device_sm_count());
+
+  long long cap = c.event_capacity > 0 ? c.event_capacity : std::max<long long>(1LL << 20, 8 * P);
+  cap = std::min<long long>(cap, evsim::MAX_EVENTS_PER_FRAME - 1);
+  s->event_cap = cap;
+  s->stage_cap = (unsigned)cap;
+  const bool sparse = c.mode == SIM_SPARSE;
+  const long long segs_per_k = sparse ? (P + evsim::SCHUNK - 1) / evsim::SCHUNK
+                                      : (long long)c.height * s->tiles_x;
+  s->seg_cap = segs_per_k * s->n_max;
+  const long long ochunks = std::max(1LL, (s->seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
+  const long long mchunks = std::max(1LL, (P + evsim::MCHUNK - 1) / evsim::MCHUNK);
+
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  if (c.cuda_stream) {
+    s->stream = (cudaStream_t)c.cuda_stream;
+  } else {
+    chk(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  chk(dalloc(&s->d_lut, 256));
+  chk(dalloc(&s->d_ring[0], P));
+  chk(dalloc(&s->d_ring[1], P));
+  if (c.ref_mode == SIM_REF_ACCUM) {
+    chk(dalloc(&s->d_R[0], P));
+    if (!sparse) chk(dalloc(&s->d_R[1], P));
+    if (sparse) chk(dalloc(&s->d_Rsave, P));
+  }
+  chk(dalloc(&s->d_ctl, 1));
+  chk(dalloc(&s->d_staging, cap));
+  chk(dalloc(&s->d_events, cap));
+  chk(dalloc(&s->d_seg, s->seg_cap));
+  chk(dalloc(&s->d_order_status, ochunks));
+  if (sparse) {
+    chk(dalloc(&s->d_mask_status, mchunks));
+    chk(dalloc(&s->d_idx, P));
+  }
+  chk(dalloc(&s->d_frame_stage, P * s->ch));
+  chk(dalloc(&s->d_flow_stage, P));
+  if (c.c_pos_map) {
+    chk(dalloc(&s->d_cpmap, P));
+    chk(dalloc(&s->d_cnmap, P));
+    if (e == cudaSuccess) {
+      chk(cudaMemcpy(s->d_cpmap, c.c_pos_map, P * 2, cudaMemcpyHostToDevice));
+      chk(cudaMemcpy(s->d_cnmap, c.c_neg_map, P * 2, cudaMemcpyHostToDevice));
+    }
+  }
+  if (e == cudaSuccess) {
+    chk(cudaMemcpy(s->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice));
+    chk(cudaMemset(s->d_ctl, 0, sizeof(Ctl)));
+    chk(cudaMemset(s->d_order_status, 0, ochunks * sizeof(unsigned long long)));
+    if (sparse) chk(cudaMemset(s->d_mask_status, 0, mchunks * sizeof(unsigned long long)));
+  }
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> g(g_attr_mu);
+    if (s->n_max > g_attr_nmax) {
+      chk(evsim::configure_kernels(s->n_max));
+      if (e == cudaSuccess) g_attr_nmax = s->n_max;
+    }
+  }
+  if (e != cudaSuccess) {
+    const int rc = cuda_rc(e);
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  s->order_grid = (int)std::min<long long>(ochunks, (long long)s->sms * 4);
+  s->mask_grid = (int)std::min<long long>(mchunks, (long long)s->sms * 4);
+  s->sparse_grid = (int)std::min<long long>((P + evsim::SCHUNK - 1) / evsim::SCHUNK,
+                                            (long long)s->sms * 4);
+  *out = s;
+  return SIM_OK;
+}
+
+int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float* flow,
+                   int64_t t_us, int32_t mem) {
+  if (!s || !frame) return SIM_ERR_ARG;
+  if (mem != SIM_HOST && mem != SIM_DEVICE) return SIM_ERR_ARG;
+  const long long row = (long long)s->W * s->ch;
+  if (pitch_bytes < row) return SIM_ERR_ARG;
+  if (s->have_first) {
+    if (!flow) return SIM_ERR_ARG;
+    if (t_us <= s->t_last) return SIM_ERR_TIME;
+    if (t_us - s->t0 > 4294967295LL) return SIM_ERR_TIME_RANGE;
+  }
+  cudaError_t e = cudaSuccess;
+  const unsigned char* dframe = (const unsigned char*)frame;
+  const float2* dflow = (const float2*)flow;
+  long long pitch = pitch_bytes;
+  if (mem == SIM_HOST) {
+    e = cudaMemcpy2DAsync(s->d_frame_stage, row, frame, pitch_bytes, row, s->H,
+                          cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    dframe = s->d_frame_stage;
+    pitch = row;
+    if (s->have_first) {
+      e = cudaMemcpyAsync(s->d_flow_stage, flow, s->P * sizeof(float2), cudaMemcpyHostToDevice,
+                          s->stream);
+      if (e != cudaSuccess) return cuda_rc(e);
+      dflow = s->d_flow_stage;
+    }
+  }
+  evsim::SimParams p = make_params(s);
+  p.frame = dframe;
+  p.pitch = pitch;
+  p.flow = dflow;
+  if (!s->have_first) {
+    p.t_rel = 0;
+    e = timed(s, SIM_K_INIT, [&] { return evsim::launch_init(p, s->stream); });
+    if (e != cudaSuccess) return cuda_rc(e);
+    Ctl c{};
+    c.committed = 1;
+    e = cudaMemcpyAsync(s->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    // the source is a stack object: make sure the copy has left it
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    s->have_first = true;
+    s->t0 = t_us;
+    s->t_last = t_us;
+    s->pushed += 1;
+    return SIM_OK;
+  }
+  p.t_rel = t_us - s->t0;
+  p.serial = ++s->serial;
+  if (s->cfg.mode == SIM_DENSE) {
+    if (s->cfg.substeps == 0) {
+      e = timed(s, SIM_K_FLOWMAX, [&] { return evsim::launch_flowmax(p, s->stream); });
+      if (e != cudaSuccess) return cuda_rc(e);
+    }
+    e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, s->stream); });
+  } else {
+    e = timed(s, SIM_K_MASK, [&] { return evsim::launch_mask(p, s->stream, s->mask_grid); });
+    if (e != cudaSuccess) return cuda_rc(e);
+    e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, s->stream, s->sparse_grid); });
+  }
+  if (e != cudaSuccess) return cuda_rc(e);
+  e = timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, s->stream, s->order_grid); });
+  if (e != cudaSuccess) return cuda_rc(e);
+  s->t_last = t_us;
+  s->pushed += 1;
+  return SIM_OK;
+}
+
+int sim_sync(sim_t* s) {
+  if (!s) return SIM_ERR_ARG;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc) return rc;
+  if (c.err) {
+    const int err = c.err;
+    rc = recover(s, &c);
+    return rc ? rc : err;
+  }
+  return SIM_OK;
+}
+
+int sim_pop_events(sim_t* s, sim_event* out, int64_t cap, int64_t* n_out, int32_t mem) {
+  if (!s || !n_out || cap < 0 || (cap > 0 && !out)) return SIM_ERR_ARG;
+  if (mem != SIM_HOST && mem != SIM_DEVICE) return SIM_ERR_ARG;
+  *n_out = 0;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc) return rc;
+  int status = SIM_OK;
+  if (c.err) {
+    status = c.err;
+    rc = recover(s, &c);
+    if (rc) return rc;
+  }
+  const long long avail = c.cursor - s->popped;
+  const long long m = std::min<long long>(avail, cap);
+  if (m > 0) {
+    cudaError_t e = cudaMemcpy(out, s->d_events + s->popped, (size_t)m * sizeof(Ev),
+                               mem == SIM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) return cuda_rc(e);
+  }
+  s->popped += m;
+  s->popped_total += m;
+  *n_out = m;
+  if (s->popped == c.cursor && c.cursor > 0) {
+    const long long zero = 0;
+    cudaError_t e = cudaMemcpy(&s->d_ctl->cursor, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_rc(e);
+    s->popped = 0;
+  }
+  if (status == SIM_OK && avail > m) status = SIM_MORE;
+  return status;
+}
+
+int sim_get_stats(sim_t* s, sim_stats* st) {
+  if (!s || !st) return SIM_ERR_ARG;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc) return rc;
+  std::memset(st, 0, sizeof(*st));
+  st->frames_pushed = s->pushed;
+  st->frames_committed = c.committed;
+  st->events_pending = c.cursor - s->popped;
+  st->events_popped = s->popped_total;
+  st->last_active = s->cfg.mode == SIM_SPARSE ? c.active : s->P;
+  st->last_frame_events = c.frame_events;
+  st->flow_clamped = (int64_t)c.clamped;
+  st->last_substeps = c.n_frame;
+  return SIM_OK;
+}
+
+int sim_get_reference(sim_t* s, int32_t* out_host) {
+  if (!s || !out_host) return SIM_ERR_ARG;
+  if (s->cfg.ref_mode != SIM_REF_ACCUM) return SIM_ERR_STATE;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc) return rc;
+  const int* src = (s->cfg.mode == SIM_DENSE && (c.sel & 1)) ? s->d_R[1] : s->d_R[0];
+  cudaError_t e = cudaMemcpy(out_host, src, s->P * sizeof(int), cudaMemcpyDeviceToHost);
+  return cuda_rc(e);
+}
+
+int sim_set_profiling(sim_t* s, int32_t enable) {
+  if (!s) return SIM_ERR_ARG;
+  if (!enable) prof_collect(s);
+  s->prof = enable != 0;
+  return SIM_OK;
+}
+
+int sim_kernel_time(sim_t* s, int32_t kind, double* ms, int64_t* launches, int32_t reset) {
+  if (!s || kind < 0 || kind >= SIM_K_COUNT) return SIM_ERR_ARG;
+  prof_collect(s);
+  if (ms) *ms = s->prof_ms[kind];
+  if (launches) *launches = s->prof_n[kind];
+  if (reset) {
+    s->prof_ms[kind] = 0;
+    s->prof_n[kind] = 0;
+  }
+  return SIM_OK;
+}
+
+int sim_reset(sim_t* s) {
+  if (!s) return SIM_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) e = cudaMemset(s->d_ctl, 0, sizeof(Ctl));
+  if (e != cudaSuccess) return cuda_rc(e);
+  s->have_first = false;
+  s->t0 = s->t_last = 0;
+  s->pushed = 0;
+  s->popped = 0;
+  return SIM_OK;
+}
+
+int sim_destroy(sim_t* s) {
+  if (!s) return SIM_ERR_ARG;
+  cudaStreamSynchronize(s->stream);
+  free_all(s);
+  delete s;
+  return SIM_OK;
+}
+
+}  // extern "C"

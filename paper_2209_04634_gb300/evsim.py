@@ -1,0 +1,264 @@
+"""Thin ctypes binding of the evsim C ABI (include/evsim.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library ``_build/libevsim.so``.  Loading fails loudly when that library is
+missing; there is no CPU fallback.
+
+The functions keep the C names (``sim_create``, ``sim_push_frame``,
+``sim_pop_events`` ...).  ``Simulator`` wraps one handle for convenience and
+accepts numpy arrays (host) or torch CUDA tensors (device).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SIM_OK, SIM_MORE = 0, 1
+SIM_ERR_ARG, SIM_ERR_CUDA, SIM_ERR_OOM, SIM_ERR_TIME = -1, -2, -3, -4
+SIM_ERR_TIME_RANGE, SIM_ERR_EVENT_OVERFLOW, SIM_ERR_DEVICE_TIMEOUT = -5, -6, -7
+SIM_ERR_STATE, SIM_ERR_ADMIT, SIM_ERR_NO_DEVICE = -8, -9, -10
+SIM_LUMA8, SIM_RGB8 = 1, 3
+SIM_DENSE, SIM_SPARSE = 0, 1
+SIM_LOG, SIM_LINEAR = 0, 1
+SIM_REF_ACCUM, SIM_REF_RESET = 0, 1
+SIM_HOST, SIM_DEVICE = 0, 1
+SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
+KERNEL_NAMES = ["init", "flowmax", "dense", "mask", "sparse", "order", "copy"]
+
+EVENT_DTYPE = np.dtype([("t", "<u4"), ("x", "<u2"), ("yp", "<u2")])
+
+
+class sim_config(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("pixel_format", ctypes.c_int32), ("mode", ctypes.c_int32),
+        ("substeps", ctypes.c_int32), ("max_substeps", ctypes.c_int32),
+        ("intensity", ctypes.c_int32), ("ref_mode", ctypes.c_int32),
+        ("c_pos_q16", ctypes.c_int32), ("c_neg_q16", ctypes.c_int32),
+        ("c_act_q16", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("c_pos_map", ctypes.c_void_p), ("c_neg_map", ctypes.c_void_p),
+        ("event_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class sim_stats(ctypes.Structure):
+    _fields_ = [
+        ("frames_pushed", ctypes.c_int64), ("frames_committed", ctypes.c_int64),
+        ("events_pending", ctypes.c_int64), ("events_popped", ctypes.c_int64),
+        ("last_active", ctypes.c_int64), ("last_frame_events", ctypes.c_int64),
+        ("flow_clamped", ctypes.c_int64), ("last_substeps", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+    ]
+
+
+# (name, restype, argtypes) of every function that include/evsim.h declares
+_VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+SIGNATURES = [
+    ("sim_config_default", ctypes.c_int, [ctypes.POINTER(sim_config), _I32, _I32]),
+    ("sim_create", ctypes.c_int, [ctypes.POINTER(sim_config), ctypes.POINTER(_VP)]),
+    ("sim_push_frame", ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I32]),
+    ("sim_pop_events", ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(_I64), _I32]),
+    ("sim_sync", ctypes.c_int, [_VP]),
+    ("sim_get_stats", ctypes.c_int, [_VP, ctypes.POINTER(sim_stats)]),
+    ("sim_get_reference", ctypes.c_int, [_VP, _VP]),
+    ("sim_set_profiling", ctypes.c_int, [_VP, _I32]),
+    ("sim_kernel_time", ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(_I64), _I32]),
+    ("sim_reset", ctypes.c_int, [_VP]),
+    ("sim_destroy", ctypes.c_int, [_VP]),
+    ("sim_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("sim_version", ctypes.c_char_p, []),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libevsim.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _build.LIB
+            if not os.path.exists(p):
+                raise RuntimeError(f"evsim CUDA library not built ({p}); run "
+                                   "paper_2209_04634_gb300.build.build() first")
+            lib = ctypes.CDLL(p)
+            for name, res, args in SIGNATURES:
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+def strerror(code: int) -> str:
+    return load().sim_strerror(code).decode()
+
+
+def check(code: int, what: str) -> int:
+    if code < 0:
+        raise SimError(code, what)
+    return code
+
+
+def q16(c: float) -> int:
+    """Threshold in log (or 8-bit) units -> Q16 integer."""
+    return int(round(abs(float(c)) * 65536.0))
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    return int(a.ctypes.data)
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+class Simulator:
+    """One simulator handle.
+
+    Frames: (H, W) or (H, W, 3) uint8; flow: (H, W, 2) float32.  numpy arrays
+    are pushed as host memory, torch CUDA tensors as device memory (they must
+    stay alive until the stream passes the push; pop() and sync() wait)."""
+
+    def __init__(self, width: int, height: int, *, pixel_format: int = SIM_LUMA8,
+                 mode: int = SIM_DENSE, substeps: int = 8, max_substeps: int = 16,
+                 intensity: int = SIM_LOG, ref_mode: int = SIM_REF_ACCUM,
+                 c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
+                 c_pos_map=None, c_neg_map=None, event_capacity: int = 0, stream=None):
+        lib = load()
+        cfg = sim_config()
+        check(lib.sim_config_default(ctypes.byref(cfg), width, height), "sim_config_default")
+        cfg.pixel_format = pixel_format
+        cfg.mode = mode
+        cfg.substeps = substeps
+        cfg.max_substeps = max_substeps
+        cfg.intensity = intensity
+        cfg.ref_mode = ref_mode
+        cfg.c_pos_q16 = c_pos_q16
+        cfg.c_neg_q16 = c_neg_q16
+        cfg.c_act_q16 = c_act_q16
+        self._maps = None
+        if c_pos_map is not None:
+            cp = np.ascontiguousarray(c_pos_map, dtype=np.uint16)
+            cn = np.ascontiguousarray(c_neg_map, dtype=np.uint16)
+            self._maps = (cp, cn)
+            cfg.c_pos_map = cp.ctypes.data
+            cfg.c_neg_map = cn.ctypes.data
+        cfg.event_capacity = event_capacity
+        if stream is not None:
+            cfg.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+        h = ctypes.c_void_p()
+        check(lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)), "sim_create")
+        self._maps = None
+        self.h = h
+        self.width, self.height, self.channels = width, height, pixel_format
+        self._lib = lib
+
+    def push(self, frame, flow, t_us: int, pitch: int | None = None) -> None:
+        dev = _is_device(frame)
+        if not dev:
+            frame = np.ascontiguousarray(frame, dtype=np.uint8)
+            if flow is not None:
+                flow = np.ascontiguousarray(flow, dtype=np.float32)
+        if pitch is None:
+            pitch = self.width * self.channels
+        fp = 0 if flow is None else _ptr(flow)
+        check(self._lib.sim_push_frame(self.h, _ptr(frame), pitch, fp or None, int(t_us),
+                                       SIM_DEVICE if dev else SIM_HOST), "sim_push_frame")
+
+    def pop(self, cap: int | None = None) -> np.ndarray:
+        """All pending events (or up to cap) as a structured numpy array."""
+        chunks = []
+        while True:
+            st = self.stats()
+            want = st.events_pending if cap is None else min(cap, st.events_pending)
+            out = np.empty(max(int(want), 1), dtype=EVENT_DTYPE)
+            n = ctypes.c_int64(0)
+            rc = self._lib.sim_pop_events(self.h, out.ctypes.data, int(want), ctypes.byref(n), SIM_HOST)
+            check(rc, "sim_pop_events")
+            chunks.append(out[: n.value])
+            if rc != SIM_MORE or cap is not None:
+                break
+        return np.concatenate(chunks) if len(chunks) > 1 else chunks[0]
+
+    def pop_into(self, out, cap: int) -> tuple[int, int]:
+        """Pop into a caller buffer (numpy: host; torch CUDA tensor: device).
+        Returns (count, return code)."""
+        n = ctypes.c_int64(0)
+        rc = self._lib.sim_pop_events(self.h, _ptr(out), int(cap), ctypes.byref(n),
+                                      SIM_DEVICE if _is_device(out) else SIM_HOST)
+        check(rc, "sim_pop_events")
+        return int(n.value), rc
+
+    def sync(self) -> int:
+        return check(self._lib.sim_sync(self.h), "sim_sync")
+
+    def stats(self) -> sim_stats:
+        st = sim_stats()
+        check(self._lib.sim_get_stats(self.h, ctypes.byref(st)), "sim_get_stats")
+        return st
+
+    def reference(self) -> np.ndarray:
+        R = np.empty((self.height, self.width), dtype=np.int32)
+        check(self._lib.sim_get_reference(self.h, R.ctypes.data), "sim_get_reference")
+        return R
+
+    def set_profiling(self, on: bool) -> None:
+        check(self._lib.sim_set_profiling(self.h, 1 if on else 0), "sim_set_profiling")
+
+    def kernel_time(self, kind: int, reset: bool = False) -> tuple[float, int]:
+        ms = ctypes.c_double(0)
+        n = ctypes.c_int64(0)
+        check(self._lib.sim_kernel_time(self.h, kind, ctypes.byref(ms), ctypes.byref(n),
+                                        1 if reset else 0), "sim_kernel_time")
+        return float(ms.value), int(n.value)
+
+    def reset(self) -> None:
+        check(self._lib.sim_reset(self.h), "sim_reset")
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self._lib.sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def simulator_for(seq, mode: int = SIM_DENSE, **kw) -> Simulator:
+    """A Simulator configured for a synth.Sequence."""
+    args = dict(pixel_format=SIM_RGB8 if seq.channels == 3 else SIM_LUMA8, mode=mode,
+                substeps=seq.substeps, max_substeps=seq.max_substeps,
+                c_pos_q16=q16(seq.c_pos), c_neg_q16=q16(seq.c_neg),
+                c_pos_map=seq.cpos_map, c_neg_map=seq.cneg_map)
+    args.update(kw)
+    return Simulator(seq.width, seq.height, **args)

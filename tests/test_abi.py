@@ -1,0 +1,107 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/evsim.h declares.  Runs without a GPU: only argument validation and
+error paths are exercised (no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2209_04634_gb300 import build, evsim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(sim\w*)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return evsim.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["sim_create", "sim_push_frame", "sim_pop_events", "sim_destroy",
+                     "sim_strerror"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_covers_every_declared_function():
+    bound = {n for n, _, _ in evsim.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_library_is_built_for_sm_103a(lib):
+    # the build recipe targets sm_103a only
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert os.path.exists(build.LIB)
+
+
+def test_strerror_and_version(lib):
+    assert lib.sim_strerror(0) == b"ok"
+    assert b"overflow" in lib.sim_strerror(evsim.SIM_ERR_EVENT_OVERFLOW)
+    assert lib.sim_strerror(12345) == b"unknown error"
+    assert lib.sim_version().count(b".") == 2
+
+
+def _cfg(lib, w=64, h=48):
+    c = evsim.sim_config()
+    assert lib.sim_config_default(ctypes.byref(c), w, h) == 0
+    return c
+
+
+@pytest.mark.parametrize("field,value", [
+    ("width", 0), ("height", -3), ("width", 9000), ("pixel_format", 2), ("mode", 7),
+    ("intensity", 5), ("ref_mode", 3), ("substeps", 65), ("substeps", -1),
+    ("c_pos_q16", 0), ("c_neg_q16", 11), ("c_pos_q16", 1 << 30), ("event_capacity", -5),
+])
+def test_create_rejects_bad_config_before_touching_the_device(lib, field, value):
+    c = _cfg(lib)
+    setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(c), ctypes.byref(h)) == evsim.SIM_ERR_ARG
+    assert not h.value
+
+
+def test_linear_accumulate_threshold_floor(lib):
+    c = _cfg(lib)
+    c.intensity = evsim.SIM_LINEAR
+    c.c_pos_q16 = c.c_neg_q16 = 510  # below (255 * 65536) / 32766
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(c), ctypes.byref(h)) == evsim.SIM_ERR_ARG
+
+
+def test_null_arguments(lib):
+    assert lib.sim_create(None, None) == evsim.SIM_ERR_ARG
+    assert lib.sim_push_frame(None, None, 0, None, 0, 0) == evsim.SIM_ERR_ARG
+    n = ctypes.c_int64(0)
+    assert lib.sim_pop_events(None, None, 0, ctypes.byref(n), 0) == evsim.SIM_ERR_ARG
+    assert lib.sim_destroy(None) == evsim.SIM_ERR_ARG
+    assert lib.sim_sync(None) == evsim.SIM_ERR_ARG
+
+
+def test_create_without_a_device_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    c = _cfg(lib)
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(c), ctypes.byref(h)) == evsim.SIM_ERR_NO_DEVICE
