@@ -44,12 +44,13 @@ int32_t orc_luma(int32_t r, int32_t g, int32_t b) {
   return (77 * r + 150 * g + 29 * b + 128) >> 8;
 }
 
-/* Flow to Q16: NaN -> 0; clamp to +-1024 px; nearest, ties to even. */
+/* Flow to Q16: NaN -> 0; clamp to +-1024 px; nearest, ties to even.
+ * *clamped is incremented once per clamped component. */
 int32_t orc_flow_q16(float f, int32_t* clamped) {
   double d = (double)f;
   if (d != d) return 0;
-  if (d > 1024.0) { d = 1024.0; if (clamped) *clamped = 1; }
-  if (d < -1024.0) { d = -1024.0; if (clamped) *clamped = 1; }
+  if (d > 1024.0) { d = 1024.0; if (clamped) *clamped += 1; }
+  if (d < -1024.0) { d = -1024.0; if (clamped) *clamped += 1; }
   return (int32_t)nearbyint(d * 65536.0);
 }
 

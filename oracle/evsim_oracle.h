@@ -58,7 +58,7 @@ typedef struct {
 void orc_lut(int32_t intensity, int32_t lut[256]);
 /* BT.601 integer luma of one RGB triple. */
 int32_t orc_luma(int32_t r, int32_t g, int32_t b);
-/* float flow component -> Q16 (NaN -> 0, clamped to +-1024 px); *clamped set on clamp. */
+/* float flow component -> Q16 (NaN -> 0, clamped to +-1024 px); *clamped += 1 on a clamp. */
 int32_t orc_flow_q16(float f, int32_t* clamped);
 /* Clamp-to-edge bilinear sample of a Q16 image at a Q16 position. */
 int32_t orc_bilinear(const int32_t* L, int32_t W, int32_t H, int64_t px, int64_t py);
