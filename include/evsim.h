@@ -70,6 +70,10 @@ enum { SIM_HOST = 0, SIM_DEVICE = 1 };         /* where a buffer lives */
 
 #define SIM_MAX_DIM 8192
 #define SIM_MAX_SUBSTEPS 64
+#define SIM_MAX_BATCH 1024          /* frames per CUDA-graph replay of sim_push_frames */
+
+/* sim_config.flags */
+#define SIM_FLAG_NO_GRAPHS 1        /* sim_push_frames launches kernels one by one */
 
 typedef struct sim_s sim_t;   /* opaque, owned by the library */
 
@@ -92,7 +96,7 @@ typedef struct {
   int32_t c_pos_q16;         /* uniform C_pos, Q16 (0.2 log units = 13107) */
   int32_t c_neg_q16;         /* uniform |C_neg|, Q16 */
   int32_t c_act_q16;         /* sparse activity threshold, Q16; < 0: min(Cp(x), Cn(x)) */
-  int32_t reserved0;
+  int32_t flags;             /* SIM_FLAG_* bits; 0: defaults */
   const uint16_t* c_pos_map; /* optional host W*H Q16 per-pixel C_pos (copied at create) */
   const uint16_t* c_neg_map; /* optional host W*H Q16 per-pixel |C_neg| */
   int64_t event_capacity;    /* device event buffer (events); 0: default max(2^20, 8 W H) */
@@ -131,8 +135,9 @@ int sim_create(const sim_config* cfg, sim_t** out);
  *   flow  : height * width * 2 floats (dx, dy) in px per frame interval,
  *           row-major, 8-byte aligned; ignored (may be NULL) on the first push.
  *   t_us  : timestamp; strictly increasing; < 2^32 us after the first frame.
- *   mem   : SIM_HOST (copied before return) or SIM_DEVICE (must stay valid
- *           until the handle's stream has passed this push: sim_sync or the
+ *   mem   : SIM_HOST or SIM_DEVICE.  Either way the buffers are read by work
+ *           enqueued on the handle's stream: they must stay valid and
+ *           unchanged until the stream has passed this push (sim_sync or the
  *           next sim_pop_events).
  * Asynchronous: returns once the work is enqueued.  The first push sets the
  * reference from frame 0 and emits no events.  A device-side failure (event
@@ -140,6 +145,16 @@ int sim_create(const sim_config* cfg, sim_t** out);
  * frame and any frame pushed after it are then not committed. */
 int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float* flow,
                    int64_t t_us, int32_t mem);
+
+/* Push count frames in one call; equivalent to count sim_push_frame calls
+ * with frames[i], flows[i], t_us[i] (host arrays of pointers; the pointers
+ * themselves point to host or device memory per mem).  Device-memory batches
+ * are replayed as a CUDA graph (one graph per batch length, captured on first
+ * use and cached; batches longer than SIM_MAX_BATCH are split); host-memory
+ * batches are first copied into a device staging area that grows to fit.
+ * Timestamps are validated for the whole batch before anything is enqueued. */
+int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t pitch_bytes,
+                    const float* const* flows, const int64_t* t_us, int32_t mem);
 
 /* Copy up to cap committed events, in output order, into out (host or device
  * memory per mem) and set *n_out.  Returns SIM_MORE if events remain (the next

@@ -19,12 +19,12 @@ constexpr int HMAX = 16;
 constexpr int SW = TW + 2 * HMAX;  // shared tile stride (int32 elements)
 constexpr int SH = TH + 2 * HMAX;
 constexpr int MAXN = 64;           // largest substep count
-// Sparse: active pixels per chunk (one per thread).
-constexpr int SCHUNK = NT;
-// Order kernel: segments per chunk.
-constexpr int OCHUNK = 4 * NT;
-// Activity mask: pixels per chunk (8 per thread).
-constexpr int MCHUNK = 8 * NT;
+// Sparse: raster pixels per chunk (4 per thread); the active pixels of a
+// chunk are compacted and simulated by the block that owns the chunk.
+constexpr int SCHUNK = 4 * NT;
+constexpr int SROUNDS = SCHUNK / NT;
+// Order kernel: segments per chunk (one per thread).
+constexpr int OCHUNK = NT;
 
 // Look-back status word: [epoch:32][flag:2][value:30].
 constexpr unsigned long long LB_AGG = 1ull << 30;
@@ -48,12 +48,29 @@ struct Ctl {
   long long committed;           // committed: frames
   long long frame_events;        // committed: events of the last committed frame
   long long active;              // sparse: active pixels of the frame in flight
+  long long last_active;         // sparse: active pixels of the last finished frame
   unsigned long long clamped;    // flow components clamped so far
   unsigned long long stage_top;  // staging bump allocator (events)
   unsigned int order_ticket;     // order kernel: chunk tickets
   unsigned int order_done;       // order kernel: chunks finished
   unsigned int order_exit;       // order kernel: blocks that left the ticket loop
-  unsigned int mask_ticket;      // mask kernel: chunk tickets
+  unsigned int pad0;
+};
+
+// Per-frame arguments.  Kernels take a pointer into a device-resident table
+// (CUDA-graph replays of frame batches) or, when it is null, the value.
+struct FrameDesc {
+  const unsigned char* frame;   // current input frame (device)
+  long long pitch;              // bytes per input row
+  const float2* flow;           // H*W (dx, dy)
+  long long t_rel;              // t_i - t_0 of this frame (us)
+  unsigned int serial;          // push serial: epoch of the look-back words
+  int pad;
+};
+
+struct FrameArg {
+  const FrameDesc* ptr;
+  FrameDesc val;
 };
 
 struct Ev {  // same layout as sim_event
@@ -72,14 +89,12 @@ struct SimParams {
   const unsigned short* cpmap;
   const unsigned short* cnmap;
   const int* lut;               // 256 Q16 entries (device)
-  const unsigned char* frame;   // current input frame (device)
-  long long pitch;              // bytes per input row
-  const float2* flow;           // H*W (dx, dy)
   unsigned char* ring0;         // luma frame ring, W bytes per row
   unsigned char* ring1;
   int* R0;                      // reference (dense: ping-pong pair; sparse: R0 only)
   int* R1;
-  int* Rsave;                   // sparse: previous reference of active pixels
+  int* Rsave;                   // sparse: previous reference of active pixels (per chunk slot)
+  int* chunk_active;            // sparse: active pixels per chunk
   Ctl* ctl;
   Ev* staging;
   unsigned int stage_cap;
@@ -88,11 +103,7 @@ struct SimParams {
   unsigned long long* order_status;
   Ev* events;
   long long event_cap;
-  int* idx;                     // sparse: active pixel indices, raster order
-  unsigned long long* mask_status;
-  long long t_rel;              // t_i - t_0 of this frame (us)
-  unsigned int serial;          // push serial: epoch of the look-back words
-  int pad2;
+  int* idx;                     // sparse: active pixel indices per chunk slot
 };
 
 // Shared-memory bytes of the dense kernel for a substep cap.
@@ -100,12 +111,12 @@ size_t dense_smem_bytes(int n_max);
 size_t sparse_smem_bytes(int n_max);
 
 // Launchers (kernels.cu).  Each returns the cudaError_t of the launch.
-cudaError_t launch_init(const SimParams& p, cudaStream_t st);
-cudaError_t launch_flowmax(const SimParams& p, cudaStream_t st);
-cudaError_t launch_dense(const SimParams& p, cudaStream_t st);
-cudaError_t launch_mask(const SimParams& p, cudaStream_t st, int grid);
-cudaError_t launch_sparse(const SimParams& p, cudaStream_t st, int grid);
-cudaError_t launch_order(const SimParams& p, cudaStream_t st, int grid);
+cudaError_t launch_init(const SimParams& p, const FrameArg& f, cudaStream_t st);
+cudaError_t launch_flowmax(const SimParams& p, const FrameArg& f, cudaStream_t st);
+cudaError_t launch_dense(const SimParams& p, const FrameArg& f, cudaStream_t st);
+cudaError_t launch_sparse_pre(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid);
+cudaError_t launch_sparse(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid);
+cudaError_t launch_order(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
 int device_sm_count();
 

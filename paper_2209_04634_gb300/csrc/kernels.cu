@@ -2,19 +2,23 @@
 //
 // One pushed frame runs, on the handle's stream:
 //   dense : [flowmax, adaptive N only] -> dense -> order
-//   sparse: mask -> sparse -> order
+//   sparse: [sparse_pre, adaptive N only] -> sparse -> order
 // The method (Ziegler et al., arXiv 2209.04634, Sec. III-A / III-B) and its
 // integer arithmetic are described in include/evsim.h.  Every kernel checks
 // the stream's sticky error word first and does nothing once it is set.
+// Per-frame arguments (input pointers, timestamp, push serial) come in a
+// FrameArg, so that a batch of frames can be captured once as a CUDA graph
+// whose kernels read their arguments from a device-resident table.
 //
 // Event order.  Within a frame, events are ordered by (substep, row, column,
 // repeat).  The simulating kernels work pixel-major, so they record each
 // pixel's per-substep count in shared memory, write their events to a
 // staging area in their own local order and publish one (count, staging
-// offset) entry per "segment" (dense: one tile row; sparse: one chunk of
-// active pixels).  The order kernel scans the segment counts in output order
-// (a single-pass scan with decoupled look-back) and gathers the events into
-// the stream's event buffer; its last block commits the frame.
+// offset) entry per "segment" (dense: one row of a 64 x 16 tile; sparse: the
+// active pixels of one chunk of 1024 raster pixels).  The order kernel scans
+// the segment counts in output order (a single-pass scan with decoupled
+// look-back) and gathers the events into the stream's event buffer; the
+// block that finishes the last chunk commits the frame.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -222,15 +226,18 @@ __device__ __forceinline__ Ev make_event(unsigned t, int x, int y, bool pos) {
   return e;
 }
 
+__device__ __forceinline__ FrameDesc frame_of(const FrameArg& f) { return f.ptr ? *f.ptr : f.val; }
+
 // ---------------------------------------------------------------------------
 // frame 0: fill the frame ring and the reference
 
-__global__ void k_init(SimParams p) {
+__global__ void k_init(SimParams p, FrameArg fa) {
+  const FrameDesc f = frame_of(fa);
   const long long P = (long long)p.W * p.H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
        i += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
-    const int v = load_luma(p.frame, p.pitch, p.ch, y, x);
+    const int v = load_luma(f.frame, f.pitch, p.ch, y, x);
     p.ring0[i] = (unsigned char)v;
     if (p.ref_mode == SIM_REF_ACCUM) p.R0[i] = p.lut[v];
   }
@@ -239,15 +246,16 @@ __global__ void k_init(SimParams p) {
 // ---------------------------------------------------------------------------
 // adaptive N (dense): max over all pixels of the squared Q16 flow
 
-__global__ void __launch_bounds__(NT) k_flowmax(SimParams p) {
+__global__ void __launch_bounds__(NT) k_flowmax(SimParams p, FrameArg fa) {
   if (block_error(&p.ctl->err)) return;
+  const FrameDesc f = frame_of(fa);
   __shared__ unsigned long long s_m[NWARP];
   const long long P = (long long)p.W * p.H;
   unsigned long long m = 0;
   int dummy = 0;
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-    const float2 f = p.flow[i];
-    const long long fx = flow_q16(f.x, dummy), fy = flow_q16(f.y, dummy);
+    const float2 fl = f.flow[i];
+    const long long fx = flow_q16(fl.x, dummy), fy = flow_q16(fl.y, dummy);
     const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
     m = f2 > m ? f2 : m;
   }
@@ -290,11 +298,11 @@ __device__ __forceinline__ DenseLayout dense_layout(unsigned char* raw, int nmax
 
 // The four pixels of a thread: columns lane, lane + 32 of rows 2 warp, 2 warp + 1.
 template <bool RESET, bool WIDE, bool FAST>
-__device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLayout& L, int N,
-                                               int tx0, int ty0, const int (&Fx)[4],
-                                               const int (&Fy)[4], int (&R)[4],
-                                               const int (&Cp)[4], const int (&Cn)[4],
-                                               const bool (&inb)[4],
+__device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDesc& f,
+                                               const DenseLayout& L, int N, int tx0, int ty0,
+                                               const int (&Fx)[4], const int (&Fy)[4],
+                                               int (&R)[4], const int (&Cp)[4],
+                                               const int (&Cn)[4], const bool (&inb)[4],
                                                const unsigned char* ringp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int px[4], py[4], ax[4], ay[4], qx[4], rx[4], qy[4], ry[4];
@@ -333,7 +341,7 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLa
         s1 = tap_shared<WIDE>(L.sL1, px[j] + Fx[j], py[j] + Fy[j]);
       } else {
         s0 = tap_global<WIDE>(ringp, p.W, 1, p.W, p.H, L.slut, px[j], py[j]);
-        s1 = tap_global<WIDE>(p.frame, p.pitch, p.ch, p.W, p.H, L.slut, px[j] + Fx[j],
+        s1 = tap_global<WIDE>(f.frame, f.pitch, p.ch, p.W, p.H, L.slut, px[j] + Fx[j],
                               py[j] + Fy[j]);
       }
       const int I = lerp12<WIDE>(s0, s1, w);
@@ -357,13 +365,54 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLa
   }
 }
 
+// Tile-local offsets of `E` segment counts (substep-major), staging allocation
+// and the segment table entries.  Returns the staging base, or -1 when the
+// staging area is exhausted (the frame then fails and emits nothing).
+__device__ __forceinline__ int stage_segments(const SimParams& p, const int* cnt, int* off, int E,
+                                              int* s_warp, int* s_base, int* total_out) {
+  const int tid = threadIdx.x;
+  constexpr int PER = 8;  // entries per thread (E <= PER * NT)
+  int v[PER], sum = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = PER * tid + q;
+    v[q] = e < E ? cnt[e] : 0;
+    sum += v[q];
+  }
+  int total;
+  int ex = block_excl_scan(sum, s_warp, &total);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = PER * tid + q;
+    if (e < E) off[e] = ex;
+    ex += v[q];
+  }
+  if (tid == 0) {
+    int base = 0;
+    if (total > 0) {
+      const unsigned long long b = atomicAdd(&p.ctl->stage_top, (unsigned long long)total);
+      if (b + (unsigned long long)total > (unsigned long long)p.stage_cap) {
+        base = -1;
+        atomicExch(&p.ctl->frame_fail, 1);
+      } else {
+        base = (int)b;
+      }
+    }
+    *s_base = base;
+  }
+  __syncthreads();
+  *total_out = total;
+  return *s_base;
+}
+
 template <bool RESET, bool MAPS, bool WIDE>
-__global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
+__global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NWARP + 1];
-  __shared__ int s_fx, s_fy, s_clamp, s_base, s_fail;
+  __shared__ int s_fx, s_fy, s_clamp, s_base;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
+  const FrameDesc f = frame_of(fa);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
@@ -395,9 +444,9 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
     Fx[j] = 0; Fy[j] = 0; R[j] = 0; Cp[j] = p.cp; Cn[j] = p.cn;
     if (inb[j]) {
       const long long i = (long long)y * W + x;
-      const float2 f = p.flow[i];
-      Fx[j] = flow_q16(f.x, clamps);
-      Fy[j] = flow_q16(f.y, clamps);
+      const float2 fl = f.flow[i];
+      Fx[j] = flow_q16(fl.x, clamps);
+      Fy[j] = flow_q16(fl.y, clamps);
       if (!RESET) R[j] = Rin[i];
       if (MAPS) { Cp[j] = p.cpmap[i]; Cn[j] = p.cnmap[i]; }
       mfx = max(mfx, (unsigned)abs(Fx[j]));
@@ -410,7 +459,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
   if (tid < N) {
     const int k = tid + 1;
     L.swk[tid] = (k * 8192 + N) / (2 * N);
-    const long long dt = p.t_rel - tprev;
+    const long long dt = f.t_rel - tprev;
     L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
   }
   for (int e = tid; e < N * TH; e += NT) L.srow[e] = 0;
@@ -438,7 +487,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
         const int rxx = tx0 - HMAX + sc;
         const int gx = min(max(rxx, 0), W - 1);
         const int vp = ringp[(long long)gy * W + gx];
-        const int vc = load_luma(p.frame, p.pitch, p.ch, gy, gx);
+        const int vc = load_luma(f.frame, f.pitch, p.ch, gy, gx);
         L.sL0[sr * SW + sc] = L.slut[vp];
         L.sL1[sr * SW + sc] = L.slut[vc];
         if (ry == gy && rxx == gx && sr >= HMAX && sr < HMAX + TH && sc >= HMAX &&
@@ -451,7 +500,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
     for (int j = 0; j < 4; ++j) {
       if (!inb[j]) continue;
       const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
-      ringn[(long long)y * W + x] = (unsigned char)load_luma(p.frame, p.pitch, p.ch, y, x);
+      ringn[(long long)y * W + x] = (unsigned char)load_luma(f.frame, f.pitch, p.ch, y, x);
     }
   }
   __syncthreads();
@@ -466,9 +515,9 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
   }
 
   if (fast)
-    dense_substeps<RESET, WIDE, true>(p, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
+    dense_substeps<RESET, WIDE, true>(p, f, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
   else
-    dense_substeps<RESET, WIDE, false>(p, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
+    dense_substeps<RESET, WIDE, false>(p, f, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
 
   if (!RESET) {
 #pragma unroll
@@ -482,42 +531,14 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
 
   // Tile-local offsets of the (substep, row) segments, substep-major.
   const int E = N * TH;
-  int v[4], sum = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int e = 4 * tid + q;
-    v[q] = e < E ? L.srow[e] : 0;
-    sum += v[q];
-  }
   int total;
-  int ex = block_excl_scan(sum, s_warp, &total);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int e = 4 * tid + q;
-    if (e < E) L.soff[e] = ex;
-    ex += v[q];
-  }
-  if (tid == 0) {
-    unsigned long long base = 0;
-    int fail = 0;
-    if (total > 0) {
-      base = atomicAdd(&ctl->stage_top, (unsigned long long)total);
-      if (base + (unsigned long long)total > (unsigned long long)p.stage_cap) {
-        fail = 1;
-        atomicExch(&ctl->frame_fail, 1);
-      }
-    }
-    s_base = fail ? 0 : (int)base;
-    s_fail = fail;
-  }
-  __syncthreads();
-  const int base = s_base;
-  const bool fail = s_fail != 0;
+  const int base = stage_segments(p, L.srow, L.soff, E, s_warp, &s_base, &total);
+  const bool fail = base < 0;
   for (int e = tid; e < E; e += NT) {
     const int k = e / TH, ty = e % TH, y = ty0 + ty;
     if (y < H)
       p.seg[((long long)k * H + y) * p.tiles_x + tcx] =
-          make_int2(fail ? 0 : L.srow[e], base + L.soff[e]);
+          make_int2(fail ? 0 : L.srow[e], (fail ? 0 : base) + L.soff[e]);
   }
   if (fail || total == 0) return;
 
@@ -553,209 +574,201 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// sparse: activity mask and order-preserving compaction of active pixels
+// sparse (Sec. III-B): per chunk of SCHUNK raster pixels, find the active
+// pixels (|L_i - L_{i-1}| >= C_act), compact them in raster order and
+// simulate only those.  Segments are (substep, chunk).
 
-__global__ void __launch_bounds__(NT) k_mask(SimParams p) {
+// Activity test of one pixel; also returns the two luma values.
+__device__ __forceinline__ bool pixel_active(const SimParams& p, const FrameDesc& f,
+                                             const int* slut, const unsigned char* ringp,
+                                             long long i, int& vc) {
+  const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
+  const int vp = ringp[i];
+  vc = load_luma(f.frame, f.pitch, p.ch, y, x);
+  const int d = abs(slut[vc] - slut[vp]);
+  int ca = p.cact;
+  if (ca < 0) {
+    const int a = p.cpmap ? p.cpmap[i] : p.cp;
+    const int b = p.cnmap ? p.cnmap[i] : p.cn;
+    ca = min(a, b);
+  }
+  return d >= ca;
+}
+
+// Adaptive N for the sparse method: max squared flow over active pixels.
+__global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, FrameArg fa) {
   __shared__ int slut[256];
-  __shared__ int s_warp[NWARP + 1];
-  __shared__ int s_c;
-  __shared__ long long s_prefix;
   __shared__ unsigned long long s_m[NWARP];
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
+  const FrameDesc f = frame_of(fa);
   const int tid = threadIdx.x;
   slut[tid] = p.lut[tid];
-  const int sel = ctl->sel;
-  const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
-  unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
-  const long long P = (long long)p.W * p.H;
-  const int nchunks = (int)((P + MCHUNK - 1) / MCHUNK);
-  const bool adaptive = p.n_fixed == 0;
-  unsigned long long mloc = 0;
-  int dummy = 0;
   __syncthreads();
-  for (;;) {
-    if (tid == 0) s_c = (int)atomicAdd(&ctl->mask_ticket, 1u);
-    __syncthreads();
-    const int c = s_c;
-    if (c >= nchunks) break;
-    const long long i0 = (long long)c * MCHUNK + 8 * tid;
-    unsigned flags = 0;
-    int cnt = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const long long i = i0 + q;
-      if (i >= P) break;
-      const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
-      const int vp = ringp[i];
-      const int vc = load_luma(p.frame, p.pitch, p.ch, y, x);
-      ringn[i] = (unsigned char)vc;
-      const int d = abs(slut[vc] - slut[vp]);
-      int ca = p.cact;
-      if (ca < 0) {
-        const int a = p.cpmap ? p.cpmap[i] : p.cp;
-        const int b = p.cnmap ? p.cnmap[i] : p.cn;
-        ca = min(a, b);
-      }
-      if (d >= ca) {
-        flags |= 1u << q;
-        ++cnt;
-        if (adaptive) {
-          const float2 f = p.flow[i];
-          const long long fx = flow_q16(f.x, dummy), fy = flow_q16(f.y, dummy);
-          const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
-          mloc = f2 > mloc ? f2 : mloc;
-        }
-      }
+  const unsigned char* ringp = (ctl->sel & 2) ? p.ring1 : p.ring0;
+  const long long P = (long long)p.W * p.H;
+  unsigned long long m = 0;
+  int dummy = 0;
+  for (long long i = blockIdx.x * (long long)NT + tid; i < P; i += (long long)gridDim.x * NT) {
+    int vc;
+    if (pixel_active(p, f, slut, ringp, i, vc)) {
+      const float2 fl = f.flow[i];
+      const long long fx = flow_q16(fl.x, dummy), fy = flow_q16(fl.y, dummy);
+      const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
+      m = f2 > m ? f2 : m;
     }
-    int total;
-    int ex = block_excl_scan(cnt, s_warp, &total);
-    if (tid == 0) s_prefix = lookback(p.mask_status, c, p.serial, total, &ctl->err);
-    __syncthreads();
-    long long o = s_prefix + ex;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (flags & (1u << q)) p.idx[o++] = (int)(i0 + q);
-    if (c == nchunks - 1 && tid == 0) ctl->active = s_prefix + total;
-    __syncthreads();
   }
-  if (adaptive) {
-    mloc = warp_max_u64(mloc);
-    if ((tid & 31) == 0) s_m[tid >> 5] = mloc;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long b = 0;
-      for (int w = 0; w < NWARP; ++w) b = s_m[w] > b ? s_m[w] : b;
-      if (b) atomicMax(&ctl->maxf2, b);
-    }
+  m = warp_max_u64(m);
+  if ((tid & 31) == 0) s_m[tid >> 5] = m;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < NWARP; ++w) b = s_m[w] > b ? s_m[w] : b;
+    if (b) atomicMax(&ctl->maxf2, b);
   }
 }
 
-// ---------------------------------------------------------------------------
-// sparse simulation: one active pixel per thread, chunks of NT active pixels
-
 template <bool RESET, bool MAPS, bool WIDE>
-__global__ void __launch_bounds__(NT) k_sparse(SimParams p) {
+__global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NWARP + 1];
-  __shared__ int s_base, s_fail, s_clamp;
+  __shared__ int s_base, s_clamp, s_active;
+  __shared__ int sidx[SCHUNK];
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
+  const FrameDesc f = frame_of(fa);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
   int* slut = (int*)smem_raw;
   int* swk = slut + 256;
   unsigned* stk = (unsigned*)(swk + nmax);
-  int* swpre = (int*)(stk + nmax);     // [N][NWARP] per-warp counts -> prefixes
-  int* skoff = swpre + nmax * NWARP;   // [N] chunk-local offset of each substep
-  short* snk = (short*)(skoff + nmax); // [N][NT]
+  int* scnt = (int*)(stk + nmax);            // [N][SROUNDS][NWARP] counts
+  int* soff = scnt + nmax * SROUNDS * NWARP; // [N][SROUNDS][NWARP] chunk-local offsets
+  int* skt = soff + nmax * SROUNDS * NWARP;  // [N] events per substep in the chunk
+  short* snk = (short*)(skt + nmax);         // [N][SCHUNK]
 
   slut[tid] = p.lut[tid];
-  if (tid == 0) s_clamp = 0;
-  const long long A = ctl->active;
-  const int S = (int)((A + SCHUNK - 1) / SCHUNK);
+  if (tid == 0) { s_clamp = 0; s_active = 0; }
+  const long long P = (long long)p.W * p.H;
+  const int S = (int)((P + SCHUNK - 1) / SCHUNK);
   const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(ctl->maxf2, nmax);
   if (blockIdx.x == 0 && tid == 0) ctl->n_frame = N;
   const int sel = ctl->sel;
   const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
-  const unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
+  unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
   const long long tprev = ctl->t_prev;
   if (tid < N) {
     const int k = tid + 1;
     swk[tid] = (k * 8192 + N) / (2 * N);
-    const long long dt = p.t_rel - tprev;
+    const long long dt = f.t_rel - tprev;
     stk[tid] = (unsigned)(tprev + (k * dt) / N);
   }
   const int W = p.W, H = p.H;
   const unsigned lt = lanemask_lt();
-  int clamps = 0;
+  const int ESEG = N * SROUNDS * NWARP;
+  int clamps = 0, active_total = 0;
+  __syncthreads();
 
   for (int c = blockIdx.x; c < S; c += gridDim.x) {
-    for (int e = tid; e < N * NWARP; e += NT) swpre[e] = 0;
+    // 1. activity of the chunk's pixels, compacted in raster order
+    const long long i0 = (long long)c * SCHUNK + SROUNDS * tid;
+    unsigned flags = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < SROUNDS; ++q) {
+      const long long i = i0 + q;
+      if (i < P) {
+        int vc;
+        if (pixel_active(p, f, slut, ringp, i, vc)) { flags |= 1u << q; ++cnt; }
+        ringn[i] = (unsigned char)vc;
+      }
+    }
+    for (int e = tid; e < ESEG; e += NT) scnt[e] = 0;
+    int A;
+    int o = block_excl_scan(cnt, s_warp, &A);
+#pragma unroll
+    for (int q = 0; q < SROUNDS; ++q)
+      if (flags & (1u << q)) sidx[o++] = (int)(i0 + q);
+    if (tid == 0) p.chunk_active[c] = A;
+    active_total += A;
     __syncthreads();
-    const long long j = (long long)c * SCHUNK + tid;
-    const bool act = j < A;
-    const int i = act ? p.idx[j] : 0;
-    const int y = i / W, x = i - y * W;
-    int Fx = 0, Fy = 0, R = 0, cp = p.cp, cn = p.cn;
-    if (act) {
-      const float2 f = p.flow[i];
-      Fx = flow_q16(f.x, clamps);
-      Fy = flow_q16(f.y, clamps);
-      if (MAPS) { cp = p.cpmap[i]; cn = p.cnmap[i]; }
-      if (RESET) {
-        R = slut[ringp[i]];
-      } else {
-        R = p.R0[i];
-        p.Rsave[j] = R;
-      }
-    }
-    int qx = Fx / N, rx = Fx - qx * N;
-    if (rx < 0) { rx += N; qx -= 1; }
-    int qy = Fy / N, ry = Fy - qy * N;
-    if (ry < 0) { ry += N; qy -= 1; }
-    int px = x << 16, py = y << 16, ax = 0, ay = 0;
-    for (int k = 0; k < N; ++k) {
-      px -= qx;
-      ax += rx;
-      if (ax >= N) { ax -= N; px -= 1; }
-      py -= qy;
-      ay += ry;
-      if (ay >= N) { ay -= N; py -= 1; }
-      const int s0 = tap_global<WIDE>(ringp, W, 1, W, H, slut, px, py);
-      const int s1 = tap_global<WIDE>(ringn, W, 1, W, H, slut, px + Fx, py + Fy);
-      const int I = lerp12<WIDE>(s0, s1, swk[k]);
-      int n = threshold_step<RESET>(I, R, cp, cn);
-      if (!act) n = 0;
-      snk[k * NT + tid] = (short)n;
-      if (__any_sync(FULL, n != 0)) {
-        const int cw = __reduce_add_sync(FULL, abs(n));
-        if (lane == 0) swpre[k * NWARP + warp] = cw;
-      }
-    }
-    if (!RESET && act) p.R0[i] = R;
-    __syncthreads();
-    int tot = 0;
-    if (tid < N) {
-      for (int w = 0; w < NWARP; ++w) {
-        const int v = swpre[tid * NWARP + w];
-        swpre[tid * NWARP + w] = tot;
-        tot += v;
-      }
-    }
-    int T;
-    const int ex = block_excl_scan(tot, s_warp, &T);
-    if (tid < N) skoff[tid] = ex;
-    if (tid == 0) {
-      unsigned long long base = 0;
-      int fail = 0;
-      if (T > 0) {
-        base = atomicAdd(&ctl->stage_top, (unsigned long long)T);
-        if (base + (unsigned long long)T > (unsigned long long)p.stage_cap) {
-          fail = 1;
-          atomicExch(&ctl->frame_fail, 1);
+
+    // 2. simulate the active pixels, NT at a time (round r: pixels r NT + tid)
+    const int rounds = (A + NT - 1) / NT;
+    for (int r = 0; r < rounds; ++r) {
+      const int j = r * NT + tid;
+      const bool act = j < A;
+      const int i = act ? sidx[j] : 0;
+      const int y = i / W, x = i - y * W;
+      int Fx = 0, Fy = 0, R = 0, cp = p.cp, cn = p.cn;
+      if (act) {
+        const float2 fl = f.flow[i];
+        Fx = flow_q16(fl.x, clamps);
+        Fy = flow_q16(fl.y, clamps);
+        if (MAPS) { cp = p.cpmap[i]; cn = p.cnmap[i]; }
+        if (RESET) {
+          R = slut[ringp[i]];
+        } else {
+          R = p.R0[i];
+          p.Rsave[(long long)c * SCHUNK + j] = R;
+          p.idx[(long long)c * SCHUNK + j] = i;
         }
       }
-      s_base = fail ? 0 : (int)base;
-      s_fail = fail;
+      int qx = Fx / N, rx = Fx - qx * N;
+      if (rx < 0) { rx += N; qx -= 1; }
+      int qy = Fy / N, ry = Fy - qy * N;
+      if (ry < 0) { ry += N; qy -= 1; }
+      int px = x << 16, py = y << 16, ax = 0, ay = 0;
+      for (int k = 0; k < N; ++k) {
+        px -= qx;
+        ax += rx;
+        if (ax >= N) { ax -= N; px -= 1; }
+        py -= qy;
+        ay += ry;
+        if (ay >= N) { ay -= N; py -= 1; }
+        const int s0 = tap_global<WIDE>(ringp, W, 1, W, H, slut, px, py);
+        const int s1 = tap_global<WIDE>(f.frame, f.pitch, p.ch, W, H, slut, px + Fx, py + Fy);
+        const int I = lerp12<WIDE>(s0, s1, swk[k]);
+        int n = threshold_step<RESET>(I, R, cp, cn);
+        if (!act) n = 0;
+        snk[k * SCHUNK + j] = (short)n;
+        if (__any_sync(FULL, n != 0)) {
+          const int cw = __reduce_add_sync(FULL, abs(n));
+          if (lane == 0) scnt[(k * SROUNDS + r) * NWARP + warp] = cw;
+        }
+      }
+      if (!RESET && act) p.R0[i] = R;
     }
     __syncthreads();
-    const int base = s_base;
-    const bool fail = s_fail != 0;
-    if (tid < N) p.seg[(long long)tid * S + c] = make_int2(fail ? 0 : tot, base + skoff[tid]);
-    if (!fail && T > 0) {
+
+    // 3. chunk-local offsets in (substep, round, warp) order, staging, segments
+    int total;
+    const int base = stage_segments(p, scnt, soff, ESEG, s_warp, &s_base, &total);
+    const bool fail = base < 0;
+    if (tid < N) {
+      const int e0 = tid * SROUNDS * NWARP;
+      const int kt = soff[e0 + SROUNDS * NWARP - 1] + scnt[e0 + SROUNDS * NWARP - 1] - soff[e0];
+      p.seg[(long long)tid * S + c] = make_int2(fail ? 0 : kt, (fail ? 0 : base) + soff[e0]);
+    }
+    if (!fail && total > 0) {
       for (int k = 0; k < N; ++k) {
-        const int n = snk[k * NT + tid];
-        const int a = abs(n);
-        if (!__any_sync(FULL, a != 0)) continue;
-        const unsigned o = (unsigned)base + (unsigned)skoff[k] + (unsigned)swpre[k * NWARP + warp];
-        const Ev ev = make_event(stk[k], x, y, n > 0);
-        if (__all_sync(FULL, a <= 1)) {
-          const unsigned b = __ballot_sync(FULL, a != 0);
-          if (a) p.staging[o + __popc(b & lt)] = ev;
-        } else {
-          const int ia = warp_incl_scan(a);
-          for (int m = 0; m < a; ++m) p.staging[o + ia - a + m] = ev;
+        for (int r = 0; r < rounds; ++r) {
+          const int e = (k * SROUNDS + r) * NWARP + warp;
+          if (scnt[e] == 0) continue;
+          const int j = r * NT + tid;
+          const int n = j < A ? snk[k * SCHUNK + j] : 0;
+          const int a = abs(n);
+          const int i = j < A ? sidx[j] : 0;
+          const int y = i / W, x = i - y * W;
+          const unsigned oo = (unsigned)base + (unsigned)soff[e];
+          const Ev ev = make_event(stk[k], x, y, n > 0);
+          if (__all_sync(FULL, a <= 1)) {
+            const unsigned b = __ballot_sync(FULL, a != 0);
+            if (a) p.staging[oo + __popc(b & lt)] = ev;
+          } else {
+            const int ia = warp_incl_scan(a);
+            for (int m = 0; m < a; ++m) p.staging[oo + ia - a + m] = ev;
+          }
         }
       }
     }
@@ -763,26 +776,31 @@ __global__ void __launch_bounds__(NT) k_sparse(SimParams p) {
   }
   clamps = __reduce_add_sync(FULL, clamps);
   if (lane == 0 && clamps) atomicAdd(&s_clamp, clamps);
+  if (tid == 0 && active_total) atomicAdd(&s_active, active_total);
   __syncthreads();
-  if (tid == 0 && s_clamp) atomicAdd(&ctl->clamped, (unsigned long long)s_clamp);
+  if (tid == 0) {
+    if (s_clamp) atomicAdd(&ctl->clamped, (unsigned long long)s_clamp);
+    if (s_active) atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)s_active);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // order: scan segment counts in output order, gather events, commit the frame
 
-__global__ void __launch_bounds__(NT) k_order(SimParams p) {
+__global__ void __launch_bounds__(NT) k_order(SimParams p, FrameArg fa) {
   __shared__ int s_ex[OCHUNK];
   __shared__ int s_src[OCHUNK];
   __shared__ int s_warp[NWARP + 1];
-  __shared__ int s_c, s_last;
+  __shared__ int s_c, s_last, s_ok;
   __shared__ long long s_prefix;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
+  const FrameDesc f = frame_of(fa);
   const int tid = threadIdx.x;
   const int N = ctl->n_frame;
   const bool sparse = p.mode == SIM_SPARSE;
-  const long long A = sparse ? ctl->active : 0;
-  const long long S = sparse ? (A + SCHUNK - 1) / SCHUNK : (long long)p.H * p.tiles_x;
+  const long long P = (long long)p.W * p.H;
+  const long long S = sparse ? (P + SCHUNK - 1) / SCHUNK : (long long)p.H * p.tiles_x;
   const long long nseg = (long long)N * S;
   const int nchunks = (int)max(1LL, (nseg + OCHUNK - 1) / OCHUNK);
   const long long cursor = ctl->cursor;
@@ -792,29 +810,18 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p) {
     __syncthreads();
     const int c = s_c;
     if (c >= nchunks) break;
-    const long long s0 = (long long)c * OCHUNK;
-    int cnt[4], src[4], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long si = s0 + 4 * tid + q;
-      cnt[q] = 0;
-      src[q] = 0;
-      if (si < nseg) {
-        const int2 e = p.seg[si];
-        cnt[q] = e.x;
-        src[q] = e.y;
-      }
-      sum += cnt[q];
+    const long long si = (long long)c * OCHUNK + tid;
+    int cnt = 0, src = 0;
+    if (si < nseg) {
+      const int2 e = p.seg[si];
+      cnt = e.x;
+      src = e.y;
     }
     int total;
-    int ex = block_excl_scan(sum, s_warp, &total);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      s_ex[4 * tid + q] = ex;
-      s_src[4 * tid + q] = src[q];
-      ex += cnt[q];
-    }
-    if (tid == 0) s_prefix = lookback(p.order_status, c, p.serial, total, &ctl->err);
+    const int ex = block_excl_scan(cnt, s_warp, &total);
+    s_ex[tid] = ex;
+    s_src[tid] = src;
+    if (tid == 0) s_prefix = lookback(p.order_status, c, f.serial, total, &ctl->err);
     __syncthreads();
     const long long base = cursor + s_prefix;
     for (int jj = tid; jj < total; jj += NT) {
@@ -835,7 +842,6 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p) {
     __syncthreads();
     if (s_last) {
       // This block finished the frame's last chunk: commit or fail the frame.
-      __shared__ int s_ok;
       if (tid == 0) {
         __threadfence();
         const unsigned long long w = ld_volatile(&p.order_status[nchunks - 1]);
@@ -851,15 +857,16 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p) {
             if (!sparse && p.ref_mode == SIM_REF_ACCUM) flip |= 1;
             ctl->cursor = cursor + tot;
             ctl->sel ^= flip;
-            ctl->t_prev = p.t_rel;
+            ctl->t_prev = f.t_rel;
             ctl->committed += 1;
             ctl->frame_events = tot;
             ok = 1;
           }
         }
+        ctl->last_active = ctl->active;
+        ctl->active = 0;
         ctl->stage_top = 0;
         ctl->order_done = 0;
-        ctl->mask_ticket = 0;
         ctl->maxf2 = 0;
         ctl->frame_fail = 0;
         s_ok = ok;
@@ -867,7 +874,13 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p) {
       __syncthreads();
       if (!s_ok && sparse && p.ref_mode == SIM_REF_ACCUM) {
         // Roll back the in-place reference of the active pixels.
-        for (long long jj = tid; jj < A; jj += NT) p.R0[p.idx[jj]] = p.Rsave[jj];
+        for (int c2 = 0; c2 < (int)S; ++c2) {
+          const int A = p.chunk_active[c2];
+          for (int j = tid; j < A; j += NT) {
+            const long long slot = (long long)c2 * SCHUNK + j;
+            p.R0[p.idx[slot]] = p.Rsave[slot];
+          }
+        }
       }
     }
     __syncthreads();
@@ -901,7 +914,8 @@ size_t dense_smem_bytes(int n_max) {
 }
 
 size_t sparse_smem_bytes(int n_max) {
-  return (size_t)(256 + 2 * n_max + n_max * NWARP + n_max) * 4 + (size_t)n_max * NT * 2;
+  return (size_t)(256 + 2 * n_max + 2 * n_max * SROUNDS * NWARP + n_max) * 4 +
+         (size_t)n_max * SCHUNK * 2;
 }
 
 int device_sm_count() {
@@ -932,28 +946,28 @@ cudaError_t configure_kernels(int n_max) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_init(const SimParams& p, cudaStream_t st) {
+cudaError_t launch_init(const SimParams& p, const FrameArg& f, cudaStream_t st) {
   const long long P = (long long)p.W * p.H;
   const int grid = (int)std::min<long long>((P + NT - 1) / NT, 4096);
-  k_init<<<grid, NT, 0, st>>>(p);
+  k_init<<<grid, NT, 0, st>>>(p, f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_flowmax(const SimParams& p, cudaStream_t st) {
+cudaError_t launch_flowmax(const SimParams& p, const FrameArg& f, cudaStream_t st) {
   const long long P = (long long)p.W * p.H;
   const int sms = device_sm_count();
   const int grid = (int)std::max(1LL, std::min<long long>((P + NT - 1) / NT, (long long)sms * 4));
-  k_flowmax<<<grid, NT, 0, st>>>(p);
+  k_flowmax<<<grid, NT, 0, st>>>(p, f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense(const SimParams& p, cudaStream_t st) {
+cudaError_t launch_dense(const SimParams& p, const FrameArg& f, cudaStream_t st) {
   const int grid = p.tiles_x * p.tiles_y;
   const size_t sm = dense_smem_bytes(p.n_max);
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NT, sm, st>>>(p)
+#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NT, sm, st>>>(p, f)
   if (!reset && !maps && !wide) EVSIM_DENSE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_DENSE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_DENSE(false, false, true);
@@ -966,17 +980,17 @@ cudaError_t launch_dense(const SimParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mask(const SimParams& p, cudaStream_t st, int grid) {
-  k_mask<<<grid, NT, 0, st>>>(p);
+cudaError_t launch_sparse_pre(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid) {
+  k_sparse_pre<<<grid, NT, 0, st>>>(p, f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sparse(const SimParams& p, cudaStream_t st, int grid) {
+cudaError_t launch_sparse(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid) {
   const size_t sm = sparse_smem_bytes(p.n_max);
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_SPARSE(R, M, Wd) k_sparse<R, M, Wd><<<grid, NT, sm, st>>>(p)
+#define EVSIM_SPARSE(R, M, Wd) k_sparse<R, M, Wd><<<grid, NT, sm, st>>>(p, f)
   if (!reset && !maps && !wide) EVSIM_SPARSE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_SPARSE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_SPARSE(false, false, true);
@@ -989,8 +1003,8 @@ cudaError_t launch_sparse(const SimParams& p, cudaStream_t st, int grid) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_order(const SimParams& p, cudaStream_t st, int grid) {
-  k_order<<<grid, NT, 0, st>>>(p);
+cudaError_t launch_order(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid) {
+  k_order<<<grid, NT, 0, st>>>(p, f);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -44,14 +45,20 @@ struct sim_s {
   Ev* d_events = nullptr;
   int2* d_seg = nullptr;
   unsigned long long* d_order_status = nullptr;
-  unsigned long long* d_mask_status = nullptr;
   int* d_idx = nullptr;
+  int* d_chunk_active = nullptr;
   unsigned char* d_frame_stage = nullptr;
   float2* d_flow_stage = nullptr;
+  evsim::FrameDesc* d_desc = nullptr;       // SIM_MAX_BATCH descriptors (graph replays)
+  unsigned char* d_batch_frames = nullptr;  // host batches: staged frames
+  float2* d_batch_flows = nullptr;
+  long long batch_stage_frames = 0;         // frames the batch staging holds
   long long event_cap = 0;
   unsigned stage_cap = 0;
   long long seg_cap = 0;
-  int order_grid = 1, mask_grid = 1, sparse_grid = 1;
+  int order_grid = 1, pre_grid = 1, sparse_grid = 1;
+  bool use_graphs = true;
+  std::map<int, cudaGraphExec_t> graphs;    // batch length -> replayable graph
 
   // host shadow of the stream
   bool have_first = false;
@@ -103,10 +110,14 @@ void free_all(sim_t* s) {
   cudaFree(s->d_events);
   cudaFree(s->d_seg);
   cudaFree(s->d_order_status);
-  cudaFree(s->d_mask_status);
   cudaFree(s->d_idx);
+  cudaFree(s->d_chunk_active);
   cudaFree(s->d_frame_stage);
   cudaFree(s->d_flow_stage);
+  cudaFree(s->d_desc);
+  cudaFree(s->d_batch_frames);
+  cudaFree(s->d_batch_flows);
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.second);
   for (auto& r : s->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -146,7 +157,7 @@ evsim::SimParams make_params(const sim_t* s) {
   p.events = s->d_events;
   p.event_cap = s->event_cap;
   p.idx = s->d_idx;
-  p.mask_status = s->d_mask_status;
+  p.chunk_active = s->d_chunk_active;
   return p;
 }
 
@@ -214,10 +225,86 @@ int recover(sim_t* s, Ctl* c) {
   c->order_ticket = 0;
   c->order_done = 0;
   c->order_exit = 0;
-  c->mask_ticket = 0;
+  c->active = 0;
   s->t_last = s->t0 + c->t_prev;
   cudaError_t e = cudaMemcpy(s->d_ctl, c, sizeof(Ctl), cudaMemcpyHostToDevice);
   return cuda_rc(e);
+}
+
+// Enqueue the kernels of one (non-first) frame.
+cudaError_t enqueue_frame(sim_t* s, const evsim::FrameArg& fa) {
+  const evsim::SimParams p = make_params(s);
+  cudaError_t e;
+  const bool adaptive = s->cfg.substeps == 0;
+  if (s->cfg.mode == SIM_DENSE) {
+    if (adaptive) {
+      e = timed(s, SIM_K_FLOWMAX, [&] { return evsim::launch_flowmax(p, fa, s->stream); });
+      if (e != cudaSuccess) return e;
+    }
+    e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, fa, s->stream); });
+  } else {
+    if (adaptive) {
+      e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, fa, s->stream, s->pre_grid); });
+      if (e != cudaSuccess) return e;
+    }
+    e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, fa, s->stream, s->sparse_grid); });
+  }
+  if (e != cudaSuccess) return e;
+  return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, fa, s->stream, s->order_grid); });
+}
+
+// The replayable graph of a batch of n frames whose descriptors sit in d_desc.
+cudaError_t batch_graph(sim_t* s, int n, cudaGraphExec_t* out) {
+  auto it = s->graphs.find(n);
+  if (it != s->graphs.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const bool prof = s->prof;
+  s->prof = false;
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < n && le == cudaSuccess; ++i) {
+    evsim::FrameArg fa{};
+    fa.ptr = s->d_desc + i;
+    le = enqueue_frame(s, fa);
+  }
+  s->prof = prof;
+  e = cudaStreamEndCapture(s->stream, &g);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le != cudaSuccess ? le : e;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return e;
+  s->graphs[n] = ex;
+  *out = ex;
+  return cudaSuccess;
+}
+
+int push_first(sim_t* s, const unsigned char* dframe, long long pitch, int64_t t_us) {
+  const evsim::SimParams p = make_params(s);
+  evsim::FrameArg fa{};
+  fa.val.frame = dframe;
+  fa.val.pitch = pitch;
+  cudaError_t e = timed(s, SIM_K_INIT, [&] { return evsim::launch_init(p, fa, s->stream); });
+  if (e != cudaSuccess) return cuda_rc(e);
+  Ctl c{};
+  c.committed = 1;
+  e = cudaMemcpyAsync(s->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return cuda_rc(e);
+  // the source is a stack object: make sure the copy has left it
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_rc(e);
+  s->have_first = true;
+  s->t0 = t_us;
+  s->t_last = t_us;
+  s->pushed += 1;
+  return SIM_OK;
 }
 
 }  // namespace
@@ -316,7 +403,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
                                       : (long long)c.height * s->tiles_x;
   s->seg_cap = segs_per_k * s->n_max;
   const long long ochunks = std::max(1LL, (s->seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
-  const long long mchunks = std::max(1LL, (P + evsim::MCHUNK - 1) / evsim::MCHUNK);
+  const long long schunks = (P + evsim::SCHUNK - 1) / evsim::SCHUNK;
+  s->use_graphs = (c.flags & SIM_FLAG_NO_GRAPHS) == 0;
 
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
@@ -332,17 +420,18 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   if (c.ref_mode == SIM_REF_ACCUM) {
     chk(dalloc(&s->d_R[0], P));
     if (!sparse) chk(dalloc(&s->d_R[1], P));
-    if (sparse) chk(dalloc(&s->d_Rsave, P));
+    if (sparse) {
+      chk(dalloc(&s->d_Rsave, schunks * evsim::SCHUNK));
+      chk(dalloc(&s->d_idx, schunks * evsim::SCHUNK));
+    }
   }
+  if (sparse) chk(dalloc(&s->d_chunk_active, schunks));
+  chk(dalloc(&s->d_desc, SIM_MAX_BATCH));
   chk(dalloc(&s->d_ctl, 1));
   chk(dalloc(&s->d_staging, cap));
   chk(dalloc(&s->d_events, cap));
   chk(dalloc(&s->d_seg, s->seg_cap));
   chk(dalloc(&s->d_order_status, ochunks));
-  if (sparse) {
-    chk(dalloc(&s->d_mask_status, mchunks));
-    chk(dalloc(&s->d_idx, P));
-  }
   chk(dalloc(&s->d_frame_stage, P * s->ch));
   chk(dalloc(&s->d_flow_stage, P));
   if (c.c_pos_map) {
@@ -357,7 +446,6 @@ int sim_create(const sim_config* cfg, sim_t** out) {
     chk(cudaMemcpy(s->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice));
     chk(cudaMemset(s->d_ctl, 0, sizeof(Ctl)));
     chk(cudaMemset(s->d_order_status, 0, ochunks * sizeof(unsigned long long)));
-    if (sparse) chk(cudaMemset(s->d_mask_status, 0, mchunks * sizeof(unsigned long long)));
   }
   if (e == cudaSuccess) {
     std::lock_guard<std::mutex> g(g_attr_mu);
@@ -373,9 +461,9 @@ int sim_create(const sim_config* cfg, sim_t** out) {
     return rc;
   }
   s->order_grid = (int)std::min<long long>(ochunks, (long long)s->sms * 4);
-  s->mask_grid = (int)std::min<long long>(mchunks, (long long)s->sms * 4);
-  s->sparse_grid = (int)std::min<long long>((P + evsim::SCHUNK - 1) / evsim::SCHUNK,
-                                            (long long)s->sms * 4);
+  s->pre_grid = (int)std::max(1LL, std::min<long long>((P + evsim::NT - 1) / evsim::NT,
+                                                       (long long)s->sms * 4));
+  s->sparse_grid = (int)std::max(1LL, std::min<long long>(schunks, (long long)s->sms * 4));
   *out = s;
   return SIM_OK;
 }
@@ -408,45 +496,104 @@ int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float
       dflow = s->d_flow_stage;
     }
   }
-  evsim::SimParams p = make_params(s);
-  p.frame = dframe;
-  p.pitch = pitch;
-  p.flow = dflow;
-  if (!s->have_first) {
-    p.t_rel = 0;
-    e = timed(s, SIM_K_INIT, [&] { return evsim::launch_init(p, s->stream); });
-    if (e != cudaSuccess) return cuda_rc(e);
-    Ctl c{};
-    c.committed = 1;
-    e = cudaMemcpyAsync(s->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) return cuda_rc(e);
-    // the source is a stack object: make sure the copy has left it
-    e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_rc(e);
-    s->have_first = true;
-    s->t0 = t_us;
-    s->t_last = t_us;
-    s->pushed += 1;
-    return SIM_OK;
-  }
-  p.t_rel = t_us - s->t0;
-  p.serial = ++s->serial;
-  if (s->cfg.mode == SIM_DENSE) {
-    if (s->cfg.substeps == 0) {
-      e = timed(s, SIM_K_FLOWMAX, [&] { return evsim::launch_flowmax(p, s->stream); });
-      if (e != cudaSuccess) return cuda_rc(e);
-    }
-    e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, s->stream); });
-  } else {
-    e = timed(s, SIM_K_MASK, [&] { return evsim::launch_mask(p, s->stream, s->mask_grid); });
-    if (e != cudaSuccess) return cuda_rc(e);
-    e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, s->stream, s->sparse_grid); });
-  }
-  if (e != cudaSuccess) return cuda_rc(e);
-  e = timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, s->stream, s->order_grid); });
+  if (!s->have_first) return push_first(s, dframe, pitch, t_us);
+  evsim::FrameArg fa{};
+  fa.val.frame = dframe;
+  fa.val.pitch = pitch;
+  fa.val.flow = dflow;
+  fa.val.t_rel = t_us - s->t0;
+  fa.val.serial = ++s->serial;
+  e = enqueue_frame(s, fa);
   if (e != cudaSuccess) return cuda_rc(e);
   s->t_last = t_us;
   s->pushed += 1;
+  return SIM_OK;
+}
+
+int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t pitch_bytes,
+                    const float* const* flows, const int64_t* t_us, int32_t mem) {
+  if (!s || count < 0 || (count > 0 && (!frames || !t_us))) return SIM_ERR_ARG;
+  if (mem != SIM_HOST && mem != SIM_DEVICE) return SIM_ERR_ARG;
+  const long long row = (long long)s->W * s->ch;
+  if (pitch_bytes < row) return SIM_ERR_ARG;
+  // validate the whole batch first
+  long long tl = s->t_last, t0 = s->have_first ? s->t0 : t_us[0];
+  for (int i = 0; i < count; ++i) {
+    const bool first = !s->have_first && i == 0;
+    if (!frames[i]) return SIM_ERR_ARG;
+    if (first) { tl = t_us[0]; continue; }
+    if (!flows || !flows[i]) return SIM_ERR_ARG;
+    if (t_us[i] <= tl) return SIM_ERR_TIME;
+    if (t_us[i] - t0 > 4294967295LL) return SIM_ERR_TIME_RANGE;
+    tl = t_us[i];
+  }
+  int i0 = 0;
+  if (!s->have_first && count > 0) {
+    const int rc = sim_push_frame(s, frames[0], pitch_bytes, nullptr, t_us[0], mem);
+    if (rc) return rc;
+    i0 = 1;
+  }
+  cudaError_t e = cudaSuccess;
+  std::vector<evsim::FrameDesc> desc;
+  while (i0 < count) {
+    const int n = std::min(count - i0, SIM_MAX_BATCH);
+    desc.assign(n, evsim::FrameDesc{});
+    if (mem == SIM_HOST) {
+      if (s->batch_stage_frames < n) {
+        e = cudaStreamSynchronize(s->stream);  // earlier batches may still read the old area
+        if (e != cudaSuccess) return cuda_rc(e);
+        cudaFree(s->d_batch_frames);
+        cudaFree(s->d_batch_flows);
+        s->d_batch_frames = nullptr;
+        s->d_batch_flows = nullptr;
+        s->batch_stage_frames = 0;
+        e = dalloc(&s->d_batch_frames, (size_t)n * s->P * s->ch);
+        if (e == cudaSuccess) e = dalloc(&s->d_batch_flows, (size_t)n * s->P);
+        if (e != cudaSuccess) return cuda_rc(e);
+        s->batch_stage_frames = n;
+      }
+    }
+    for (int j = 0; j < n; ++j) {
+      const int i = i0 + j;
+      evsim::FrameDesc& d = desc[j];
+      if (mem == SIM_HOST) {
+        unsigned char* fd = s->d_batch_frames + (size_t)j * s->P * s->ch;
+        float2* fl = s->d_batch_flows + (size_t)j * s->P;
+        e = cudaMemcpy2DAsync(fd, row, frames[i], pitch_bytes, row, s->H, cudaMemcpyHostToDevice,
+                              s->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(fl, flows[i], s->P * sizeof(float2), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_rc(e);
+        d.frame = fd;
+        d.pitch = row;
+        d.flow = fl;
+      } else {
+        d.frame = (const unsigned char*)frames[i];
+        d.pitch = pitch_bytes;
+        d.flow = (const float2*)flows[i];
+      }
+      d.t_rel = t_us[i] - s->t0;
+      d.serial = ++s->serial;
+    }
+    if (s->use_graphs && !s->prof && n >= 2) {
+      e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
+                          cudaMemcpyHostToDevice, s->stream);
+      cudaGraphExec_t ex = nullptr;
+      if (e == cudaSuccess) e = batch_graph(s, n, &ex);
+      if (e == cudaSuccess) e = cudaGraphLaunch(ex, s->stream);
+      if (e != cudaSuccess) return cuda_rc(e);
+    } else {
+      for (int j = 0; j < n; ++j) {
+        evsim::FrameArg fa{};
+        fa.val = desc[j];
+        e = enqueue_frame(s, fa);
+        if (e != cudaSuccess) return cuda_rc(e);
+      }
+    }
+    s->t_last = t_us[i0 + n - 1];
+    s->pushed += n;
+    i0 += n;
+  }
   return SIM_OK;
 }
 
@@ -506,7 +653,7 @@ int sim_get_stats(sim_t* s, sim_stats* st) {
   st->frames_committed = c.committed;
   st->events_pending = c.cursor - s->popped;
   st->events_popped = s->popped_total;
-  st->last_active = s->cfg.mode == SIM_SPARSE ? c.active : s->P;
+  st->last_active = s->cfg.mode == SIM_SPARSE ? c.last_active : s->P;
   st->last_frame_events = c.frame_events;
   st->flow_clamped = (int64_t)c.clamped;
   st->last_substeps = c.n_frame;

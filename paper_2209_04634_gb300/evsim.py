@@ -27,6 +27,8 @@ SIM_DENSE, SIM_SPARSE = 0, 1
 SIM_LOG, SIM_LINEAR = 0, 1
 SIM_REF_ACCUM, SIM_REF_RESET = 0, 1
 SIM_HOST, SIM_DEVICE = 0, 1
+SIM_FLAG_NO_GRAPHS = 1
+SIM_MAX_BATCH = 1024
 SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
 KERNEL_NAMES = ["init", "flowmax", "dense", "mask", "sparse", "order", "copy"]
 
@@ -40,7 +42,7 @@ class sim_config(ctypes.Structure):
         ("substeps", ctypes.c_int32), ("max_substeps", ctypes.c_int32),
         ("intensity", ctypes.c_int32), ("ref_mode", ctypes.c_int32),
         ("c_pos_q16", ctypes.c_int32), ("c_neg_q16", ctypes.c_int32),
-        ("c_act_q16", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("c_act_q16", ctypes.c_int32), ("flags", ctypes.c_int32),
         ("c_pos_map", ctypes.c_void_p), ("c_neg_map", ctypes.c_void_p),
         ("event_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
     ]
@@ -62,6 +64,8 @@ SIGNATURES = [
     ("sim_config_default", ctypes.c_int, [ctypes.POINTER(sim_config), _I32, _I32]),
     ("sim_create", ctypes.c_int, [ctypes.POINTER(sim_config), ctypes.POINTER(_VP)]),
     ("sim_push_frame", ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I32]),
+    ("sim_push_frames", ctypes.c_int, [_VP, _I32, ctypes.POINTER(_VP), _I64,
+                                       ctypes.POINTER(_VP), ctypes.POINTER(_I64), _I32]),
     ("sim_pop_events", ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(_I64), _I32]),
     ("sim_sync", ctypes.c_int, [_VP]),
     ("sim_get_stats", ctypes.c_int, [_VP, ctypes.POINTER(sim_stats)]),
@@ -144,7 +148,8 @@ class Simulator:
                  mode: int = SIM_DENSE, substeps: int = 8, max_substeps: int = 16,
                  intensity: int = SIM_LOG, ref_mode: int = SIM_REF_ACCUM,
                  c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
-                 c_pos_map=None, c_neg_map=None, event_capacity: int = 0, stream=None):
+                 c_pos_map=None, c_neg_map=None, event_capacity: int = 0, stream=None,
+                 flags: int = 0):
         lib = load()
         cfg = sim_config()
         check(lib.sim_config_default(ctypes.byref(cfg), width, height), "sim_config_default")
@@ -165,6 +170,7 @@ class Simulator:
             cfg.c_pos_map = cp.ctypes.data
             cfg.c_neg_map = cn.ctypes.data
         cfg.event_capacity = event_capacity
+        cfg.flags = flags
         if stream is not None:
             cfg.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         h = ctypes.c_void_p()
@@ -185,6 +191,27 @@ class Simulator:
         fp = 0 if flow is None else _ptr(flow)
         check(self._lib.sim_push_frame(self.h, _ptr(frame), pitch, fp or None, int(t_us),
                                        SIM_DEVICE if dev else SIM_HOST), "sim_push_frame")
+
+    def push_many(self, frames, flows, t_us, pitch: int | None = None) -> None:
+        """Push frames[0..F) with flows[i] (i -> frame i-1 to i) in one call.
+        frames/flows: torch CUDA tensors (device batch, replayed as a CUDA graph)
+        or numpy arrays (host batch); flows[0] is ignored for a first frame."""
+        F = len(t_us)
+        dev = _is_device(frames)
+        if not dev:
+            frames = np.ascontiguousarray(frames, dtype=np.uint8)
+            flows = np.ascontiguousarray(flows, dtype=np.float32)
+            fb, lb = frames.strides[0], flows.strides[0]
+        else:
+            fb, lb = frames.stride(0) * frames.element_size(), flows.stride(0) * flows.element_size()
+        f0, l0 = _ptr(frames), _ptr(flows)
+        fp = (ctypes.c_void_p * F)(*[f0 + i * fb for i in range(F)])
+        lp = (ctypes.c_void_p * F)(*[l0 + i * lb for i in range(F)])
+        ts = (ctypes.c_int64 * F)(*[int(t) for t in t_us])
+        if pitch is None:
+            pitch = self.width * self.channels
+        check(self._lib.sim_push_frames(self.h, F, fp, pitch, lp, ts,
+                                        SIM_DEVICE if dev else SIM_HOST), "sim_push_frames")
 
     def pop(self, cap: int | None = None) -> np.ndarray:
         """All pending events (or up to cap) as a structured numpy array."""

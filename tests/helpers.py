@@ -26,7 +26,8 @@ def oracle_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, intensity=ev
 def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: bool = True,
             pop_every: int = 1, intensity=evsim.SIM_LOG, ref_mode=evsim.SIM_REF_ACCUM,
             c_act_q16: int = -1, substeps=None, c_pos_q16=None, c_neg_q16=None,
-            use_maps=True, event_capacity: int = 0, stream=None) -> dict:
+            use_maps=True, event_capacity: int = 0, stream=None, batch: int = 0,
+            flags: int = 0) -> dict:
     """Push every frame of seq through the CUDA library; return the events,
     the committed reference and per-frame statistics."""
     import torch
@@ -43,7 +44,10 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
         kw["c_neg_map"] = None
     if stream is not None:
         kw["stream"] = stream
+    kw["flags"] = flags
     sim = evsim.simulator_for(seq, mode, **kw)
+    if batch:
+        return _gpu_run_batched(sim, seq, batch, device_inputs, ref_mode)
     out, n_per_frame, ev_per_frame, active = [], [0], [0], [0]
     F = seq.frames.shape[0]
     if device_inputs:
@@ -84,3 +88,24 @@ def assert_same_events(got: np.ndarray, want: np.ndarray, what: str = "") -> Non
         f"{what}: event streams differ (gpu {len(got)}, oracle {len(want)} events); first "
         f"difference at {first}: gpu {list(zip(gt, gx, gy, gp))} vs oracle "
         f"{list(zip(wt, wx, wy, wp))}")
+
+
+def _gpu_run_batched(sim, seq, batch, device_inputs, ref_mode):
+    """Push the sequence in batches of `batch` frames (sim_push_frames)."""
+    import torch
+    F = seq.frames.shape[0]
+    if device_inputs:
+        frames = torch.from_numpy(np.ascontiguousarray(seq.frames)).cuda()
+        flows = torch.from_numpy(np.ascontiguousarray(seq.flows)).cuda()
+    else:
+        frames, flows = seq.frames, seq.flows
+    out = []
+    for i in range(0, F, batch):
+        j = min(F, i + batch)
+        sim.push_many(frames[i:j], flows[i:j], seq.t_us[i:j])
+        out.append(sim.pop())
+    st = sim.stats()
+    R = sim.reference() if ref_mode == evsim.SIM_REF_ACCUM else None
+    sim.close()
+    ev = np.concatenate(out) if out else np.zeros(0, dtype=evsim.EVENT_DTYPE)
+    return {"events": ev, "R": R, "stats": st}

@@ -296,3 +296,35 @@ def test_two_handles_on_two_streams_are_independent():
     assert_same_events(np.concatenate(eb), oracle_run(b_seq, evsim.SIM_DENSE)["events"], "stream b")
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
+@pytest.mark.parametrize("batch,device", [(7, True), (1, True), (5, False), (40, True)])
+def test_batched_pushes_graph_replay(mode, batch, device):
+    """sim_push_frames (CUDA-graph replay of device batches, staged host
+    batches) gives the same stream as the oracle."""
+    seq = synth.warped_texture(frames=23, width=160, height=120, seed=21)
+    g = gpu_run(seq, mode, batch=batch, device_inputs=device)
+    o = oracle_run(seq, mode)
+    assert_same_events(g["events"], o["events"], f"batch {batch}")
+    assert np.array_equal(g["R"], o["R"])
+
+
+def test_batched_pushes_without_graphs():
+    seq = synth.moving_rectangles(frames=9, width=256, height=144, side=(20, 60), seed=8)
+    g = gpu_run(seq, evsim.SIM_DENSE, batch=4, flags=evsim.SIM_FLAG_NO_GRAPHS)
+    assert_same_events(g["events"], oracle_run(seq)["events"], "no graphs")
+
+
+def test_batch_rejects_bad_timestamps_before_enqueueing():
+    seq = synth.blob_translation(frames=5)
+    sim = evsim.simulator_for(seq)
+    t = seq.t_us.copy()
+    t[3] = t[2]
+    with pytest.raises(evsim.SimError) as e:
+        sim.push_many(seq.frames, seq.flows, t)
+    assert e.value.code == evsim.SIM_ERR_TIME
+    assert sim.stats().frames_pushed == 0
+    sim.push_many(seq.frames, seq.flows, seq.t_us)
+    assert_same_events(sim.pop(), oracle_run(seq)["events"], "after rejected batch")
+    sim.close()
