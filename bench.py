@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 event simulator.
+
+Workload (one "step"): the 640x480 warped-texture sequence (100 frames of
+8-bit luma, a smooth flow field of up to 8 px/frame whose magnitude
+oscillates, adaptive substeps N <= 8, C = 0.2 log units with per-pixel
+Gaussian threshold noise sigma 0.03) run through the dense simulator
+(Sec. III-A of arXiv 2209.04634) and through the sparse simulator
+(Sec. III-B), each from frame 0, with the events popped into device memory.
+Inputs are resident in HBM when the timed region starts; they total
+~277 MB, more than the 129 MB L2, so no flush is needed between steps.
+
+Metric: Gpix-substeps/s = sum over frames and both passes of W H N, divided
+by the device time of the timed steps (CUDA events on the simulators'
+stream, max over ranks).  events/s is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain restatement of the method
+used as the parity reference) on this host's cores on a bounded sample of
+the same workload.  Under torchrun each rank runs its own independently
+seeded stream (weak scaling, no collective on the data path); rank 0 prints
+one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = ("warped_texture 640x480 luma, 100 frames, smooth flow <= 8 px/frame, adaptive "
+            "substeps <= 8, C = 0.2 with per-pixel noise sigma 0.03; dense + sparse passes")
+METRIC = "Gpix-substeps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=100)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait(timeout=10)
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                         if r[3].replace(".", "").isdigit())}
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2209_04634_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".h", ".cuh")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str):
+    """dram bytes per launch from the committed ncu capture, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None, None
+    e = d.get(kernel)
+    if not e or e.get("source_digest") != kernel_source_digest():
+        return None, None
+    return e.get("dram_bytes_per_launch"), e
+
+
+def cpu_baseline(seq, frames_sample: int):
+    """The oracle as it stands, single-threaded, on a bounded head of the workload."""
+    import oracle
+    from paper_2209_04634_gb300 import evsim
+    s = seq.head(frames_sample)
+    work = 0
+    nev = 0
+    t0 = time.perf_counter()
+    for mode in (oracle.DENSE, oracle.SPARSE):
+        r = oracle.run(s.frames, s.flows, s.t_us, mode=mode, substeps=s.substeps,
+                       max_substeps=s.max_substeps, c_pos_q16=evsim.q16(s.c_pos),
+                       c_neg_q16=evsim.q16(s.c_neg), cpos_map=s.cpos_map, cneg_map=s.cneg_map)
+        work += int((r["n_per_frame"][1:].astype("int64") * s.width * s.height).sum())
+        nev += len(r["events"])
+    dt = time.perf_counter() - t0
+    return work / dt / 1e9, nev / dt, dt, work
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_2209_04634_gb300 import synth
+    n = 6  # frames per sampled step: about 2 s of single-core oracle work
+    seq = synth.warped_texture(frames=n)  # the workload's first n frames
+    for _ in range(args.warmup):
+        cpu_baseline(seq, n)
+    vals, works, dts, evs = [], 0, 0.0, 0.0
+    for _ in range(args.steps):
+        v, e, dt, w = cpu_baseline(seq, n)
+        works += w
+        dts += dt
+        evs += e * dt
+    value = works / dts / 1e9
+    sample = f"first {n} frames of the workload, dense + sparse, per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dts / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "events_per_s": evs / dts,
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2209_04634_gb300 import build, evsim, synth
+    build.build()
+    evsim.load()
+
+    seq = synth.warped_texture(frames=args.frames, seed=4209 + 1000 * rank)
+    F, H, W = seq.frames.shape
+    P = W * H
+    stream = torch.cuda.Stream()
+    frames = torch.from_numpy(seq.frames).cuda()
+    flows = torch.from_numpy(seq.flows).cuda()
+    cap = 24_000_000
+    out = torch.empty(cap * 8, dtype=torch.uint8, device="cuda")
+    sims = {m: evsim.simulator_for(seq, m, event_capacity=cap, stream=stream)
+            for m in (evsim.SIM_DENSE, evsim.SIM_SPARSE)}
+    t_us = seq.t_us
+
+    def step():
+        n_ev = 0
+        for sim in sims.values():
+            sim.reset()
+            sim.push_many(frames, flows, t_us)
+            n, rc = sim.pop_into(out, cap)
+            assert rc == evsim.SIM_OK, rc
+            n_ev += n
+        return n_ev
+
+    # units of one step (read once from the library's own counters)
+    step()
+    work = {m: sims[m].stats().pixel_substeps for m in sims}
+    active_work = sims[evsim.SIM_SPARSE].stats().active_substeps
+    work_step = sum(work.values())
+
+    for _ in range(args.warmup):
+        step()
+    dense = sims[evsim.SIM_DENSE]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    n_ev = 0
+    for _ in range(args.steps):
+        n_ev += step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ws, ms)
+
+    # Kernel durations: the same steps again with an event-record node before
+    # and after every kernel of the replayed graphs (no host gaps inside).
+    for sim in sims.values():
+        sim.set_profiling(True)
+    for _ in range(2):
+        step()  # captures the profiled graphs
+    for sim in sims.values():
+        for k in range(7):
+            sim.kernel_time(k, reset=True)
+    prof_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(prof_steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms_step = p0.elapsed_time(p1) / prof_steps
+    ktimes = {}
+    launches_prof = 0
+    for m, sim in sims.items():
+        for k, name in enumerate(evsim.KERNEL_NAMES):
+            t, c = sim.kernel_time(k)
+            if c:
+                ktimes[("dense" if m == evsim.SIM_DENSE else "sparse") + "." + name] = (t, c)
+                launches_prof += c
+        sim.set_profiling(False)
+    # kernels launched in the timed region: the same sequence per step
+    launches = launches_prof // prof_steps * args.steps
+    total_work = sum_over_ranks(ws, work_step * args.steps)
+    total_ev = sum_over_ranks(ws, n_ev)
+    value = total_work / (ms_max / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the dense simulation kernel)
+    dk_ms, dk_n = ktimes.get("dense.dense", (0.0, 0))
+    # events of the dense pass in one step
+    dense.reset()
+    dense.push_many(frames, flows, t_us)
+    dense_ev_step = dense.stats().events_pending
+    dense.pop_into(out, cap)
+    maps = 4 * P if seq.cpos_map is not None else 0
+    bytes_per_launch = (2 * P + 8 * P + 8 * P + maps) + 8 * dense_ev_step / (F - 1)
+    avg_s = dk_ms / dk_n / 1e3 if dk_n else float("nan")
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_per_launch / avg_s / 1e9
+    traffic, tinfo = committed_traffic("dense")
+    roofline = {"bound": "hbm", "kernel": "k_dense (dense simulation)", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": avg_s * 1e6, "launches": dk_n,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 (Q16 fixed point)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": F, "width": W, "height": H,
+                   "pixel_substeps_per_step": work_step,
+                   "active_pixel_substeps_per_step_sparse": active_work,
+                   "l2": "inputs larger than L2 (277 MB resident), no flush",
+                   "parallelism": f"{ws} independent stream(s), one per GPU"},
+        "events_per_s": total_ev / (ms_max / 1e3),
+        "wall_ms_per_step": wall / args.steps * 1e3,
+        "kernel_us_per_launch": {k: v[0] / v[1] * 1e3 for k, v in ktimes.items()},
+        "profiled_ms_per_step": prof_ms_step,
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = run_e2e(args, seq, sims, stream, work_step)
+    if rank == 0 and not args.no_cpu:
+        n = 24
+        v, evs, dt, w = cpu_baseline(seq, n)
+        line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                "sample": f"first {n} frames, dense + sparse ({w} pixel-substeps, "
+                                          f"{dt:.1f} s)", "events_per_s": evs}
+    for sim in sims.values():
+        sim.close()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def run_e2e(args, seq, sims, stream, work_step):
+    """Same metric through the C ABI with host buffers: frames and flows from
+    pinned host memory copied in by the library, events read back to pinned
+    host memory, every step."""
+    import torch
+
+    from paper_2209_04634_gb300 import evsim
+    frames_h = torch.from_numpy(seq.frames).pin_memory()
+    flows_h = torch.from_numpy(seq.flows).pin_memory()
+    cap = 24_000_000
+    out_h = torch.empty(cap * 8, dtype=torch.uint8).pin_memory()
+    fr_np, fl_np, out_np = frames_h.numpy(), flows_h.numpy(), out_h.numpy().view(evsim.EVENT_DTYPE)
+    F = seq.frames.shape[0]
+
+    def step():
+        d2h = 0
+        for sim in sims.values():
+            sim.reset()
+            sim.push_many(fr_np, fl_np, seq.t_us)
+            n, rc = sim.pop_into(out_np, cap)
+            d2h += n * 8
+        return d2h
+
+    for _ in range(2):
+        step()
+    steps = max(3, args.steps // 3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d2h = 0
+    for _ in range(steps):
+        d2h += step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h2d = 2 * (seq.frames.nbytes + seq.flows[1:].nbytes)
+    return {"value": work_step * steps / (ms / 1e3) / 1e9, "unit": METRIC,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // steps),
+            "steps": steps, "ms_per_step": ms / steps}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args) if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -100,7 +100,8 @@ typedef struct {
   const uint16_t* c_pos_map; /* optional host W*H Q16 per-pixel C_pos (copied at create) */
   const uint16_t* c_neg_map; /* optional host W*H Q16 per-pixel |C_neg| */
   int64_t event_capacity;    /* device event buffer (events); 0: default max(2^20, 8 W H) */
-  void* cuda_stream;         /* cudaStream_t to order work on; NULL: library-owned stream */
+  void* cuda_stream;         /* cudaStream_t to order work on; NULL: library-owned stream;
+                                cudaStreamLegacy for the legacy default stream (no graphs) */
 } sim_config;
 
 typedef struct {
@@ -113,6 +114,8 @@ typedef struct {
   int64_t flow_clamped;      /* flow components clamped to +-1024 px so far */
   int32_t last_substeps;     /* N of the last committed frame */
   int32_t reserved0;
+  int64_t pixel_substeps;    /* sum over committed frames of width * height * N */
+  int64_t active_substeps;   /* sum over committed frames of (pixels simulated) * N */
 } sim_stats;
 
 /* Kernel kinds for sim_kernel_time. */

@@ -49,6 +49,8 @@ struct Ctl {
   long long frame_events;        // committed: events of the last committed frame
   long long active;              // sparse: active pixels of the frame in flight
   long long last_active;         // sparse: active pixels of the last finished frame
+  long long work_px;             // committed: sum over frames of W H N
+  long long work_active;         // committed: sum over frames of (processed pixels) N
   unsigned long long clamped;    // flow components clamped so far
   unsigned long long stage_top;  // staging bump allocator (events)
   unsigned int order_ticket;     // order kernel: chunk tickets

@@ -860,6 +860,8 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, FrameArg fa) {
             ctl->t_prev = f.t_rel;
             ctl->committed += 1;
             ctl->frame_events = tot;
+            ctl->work_px += P * N;
+            ctl->work_active += (sparse ? ctl->active : P) * N;
             ok = 1;
           }
         }

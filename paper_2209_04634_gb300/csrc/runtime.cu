@@ -21,6 +21,12 @@ using evsim::Ev;
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
+  bool graph_owned;  // event pair recorded by a node of a cached graph
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ProfRec> recs;  // profiled graphs: the event pairs of their kernels
 };
 
 struct sim_s {
@@ -58,7 +64,7 @@ struct sim_s {
   long long seg_cap = 0;
   int order_grid = 1, pre_grid = 1, sparse_grid = 1;
   bool use_graphs = true;
-  std::map<int, cudaGraphExec_t> graphs;    // batch length -> replayable graph
+  std::map<std::pair<int, bool>, GraphEntry> graphs;  // (batch length, profiled) -> graph
 
   // host shadow of the stream
   bool have_first = false;
@@ -117,8 +123,15 @@ void free_all(sim_t* s) {
   cudaFree(s->d_desc);
   cudaFree(s->d_batch_frames);
   cudaFree(s->d_batch_flows);
-  for (auto& g : s->graphs) cudaGraphExecDestroy(g.second);
+  for (auto& g : s->graphs) {
+    cudaGraphExecDestroy(g.second.exec);
+    for (auto& r : g.second.recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
   for (auto& r : s->pending) {
+    if (r.graph_owned) continue;
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
@@ -184,7 +197,7 @@ cudaEvent_t pool_get(sim_t* s) {
 template <class F>
 cudaError_t timed(sim_t* s, int kind, F&& launch) {
   if (!s->prof) return launch();
-  ProfRec r{kind, pool_get(s), pool_get(s)};
+  ProfRec r{kind, pool_get(s), pool_get(s), false};
   cudaEventRecord(r.a, s->stream);
   cudaError_t e = launch();
   cudaEventRecord(r.b, s->stream);
@@ -201,8 +214,10 @@ void prof_collect(sim_t* s) {
       s->prof_ms[r.kind] += ms;
       s->prof_n[r.kind] += 1;
     }
-    s->pool.push_back(r.a);
-    s->pool.push_back(r.b);
+    if (!r.graph_owned) {
+      s->pool.push_back(r.a);
+      s->pool.push_back(r.b);
+    }
   }
   s->pending.clear();
 }
@@ -254,35 +269,48 @@ cudaError_t enqueue_frame(sim_t* s, const evsim::FrameArg& fa) {
 }
 
 // The replayable graph of a batch of n frames whose descriptors sit in d_desc.
-cudaError_t batch_graph(sim_t* s, int n, cudaGraphExec_t* out) {
-  auto it = s->graphs.find(n);
+// A profiled graph also holds an event-record node before and after each
+// kernel, so kernel durations can be read without host launch gaps.
+cudaError_t batch_graph(sim_t* s, int n, GraphEntry** out) {
+  const auto key = std::make_pair(n, s->prof);
+  auto it = s->graphs.find(key);
   if (it != s->graphs.end()) {
-    *out = it->second;
+    *out = &it->second;
     return cudaSuccess;
   }
+  prof_collect(s);  // pending must hold only this capture's event pairs
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  const bool prof = s->prof;
-  s->prof = false;
   cudaError_t le = cudaSuccess;
   for (int i = 0; i < n && le == cudaSuccess; ++i) {
     evsim::FrameArg fa{};
     fa.ptr = s->d_desc + i;
     le = enqueue_frame(s, fa);
   }
-  s->prof = prof;
   e = cudaStreamEndCapture(s->stream, &g);
+  GraphEntry entry;
+  entry.recs.swap(s->pending);
+  for (auto& r : entry.recs) r.graph_owned = true;
+  auto drop = [&]() {
+    for (auto& r : entry.recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  };
   if (le != cudaSuccess || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
+    drop();
     return le != cudaSuccess ? le : e;
   }
-  cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, g, 0);
+  e = cudaGraphInstantiate(&entry.exec, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return e;
-  s->graphs[n] = ex;
-  *out = ex;
+  if (e != cudaSuccess) {
+    drop();
+    return e;
+  }
+  auto res = s->graphs.emplace(key, std::move(entry));
+  *out = &res.first->second;
   return cudaSuccess;
 }
 
@@ -405,6 +433,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   const long long ochunks = std::max(1LL, (s->seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
   const long long schunks = (P + evsim::SCHUNK - 1) / evsim::SCHUNK;
   s->use_graphs = (c.flags & SIM_FLAG_NO_GRAPHS) == 0;
+  // the legacy default stream cannot be captured
+  if (c.cuda_stream == (void*)cudaStreamLegacy) s->use_graphs = false;
 
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
@@ -575,13 +605,17 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
       d.t_rel = t_us[i] - s->t0;
       d.serial = ++s->serial;
     }
-    if (s->use_graphs && !s->prof && n >= 2) {
-      e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
-                          cudaMemcpyHostToDevice, s->stream);
-      cudaGraphExec_t ex = nullptr;
-      if (e == cudaSuccess) e = batch_graph(s, n, &ex);
-      if (e == cudaSuccess) e = cudaGraphLaunch(ex, s->stream);
+    if (s->use_graphs && n >= 2) {
+      GraphEntry* ge = nullptr;
+      e = batch_graph(s, n, &ge);
+      // a profiled graph reuses its events: read the previous replay first
+      if (e == cudaSuccess && s->prof) prof_collect(s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
+                            cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(ge->exec, s->stream);
       if (e != cudaSuccess) return cuda_rc(e);
+      if (s->prof) s->pending.insert(s->pending.end(), ge->recs.begin(), ge->recs.end());
     } else {
       for (int j = 0; j < n; ++j) {
         evsim::FrameArg fa{};
@@ -657,6 +691,8 @@ int sim_get_stats(sim_t* s, sim_stats* st) {
   st->last_frame_events = c.frame_events;
   st->flow_clamped = (int64_t)c.clamped;
   st->last_substeps = c.n_frame;
+  st->pixel_substeps = c.work_px;
+  st->active_substeps = c.work_active;
   return SIM_OK;
 }
 

@@ -28,6 +28,7 @@ SIM_LOG, SIM_LINEAR = 0, 1
 SIM_REF_ACCUM, SIM_REF_RESET = 0, 1
 SIM_HOST, SIM_DEVICE = 0, 1
 SIM_FLAG_NO_GRAPHS = 1
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 SIM_MAX_BATCH = 1024
 SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
 KERNEL_NAMES = ["init", "flowmax", "dense", "mask", "sparse", "order", "copy"]
@@ -54,7 +55,8 @@ class sim_stats(ctypes.Structure):
         ("events_pending", ctypes.c_int64), ("events_popped", ctypes.c_int64),
         ("last_active", ctypes.c_int64), ("last_frame_events", ctypes.c_int64),
         ("flow_clamped", ctypes.c_int64), ("last_substeps", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32), ("pixel_substeps", ctypes.c_int64),
+        ("active_substeps", ctypes.c_int64),
     ]
 
 
@@ -172,7 +174,10 @@ class Simulator:
         cfg.event_capacity = event_capacity
         cfg.flags = flags
         if stream is not None:
-            cfg.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+            handle = int(getattr(stream, "cuda_stream", stream))
+            # handle 0 is the legacy default stream (torch's default stream):
+            # name it explicitly, since a null handle asks for a library stream
+            cfg.cuda_stream = handle if handle else CUDA_STREAM_LEGACY
         h = ctypes.c_void_p()
         check(lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)), "sim_create")
         self._maps = None

@@ -179,7 +179,7 @@ def test_adaptive_substeps_track_the_flow():
     for i, m in enumerate([0, 0.3, 2.0, 5.5, 11.2, 30.0]):
         seq.flows[i, 7, 9] = (m, -m / 2)
     g, o = check_parity(seq, evsim.SIM_DENSE, "adaptive N", use_maps=False)
-    assert list(g["n_per_frame"][1:]) == [1, 2, 7, 12, 12]
+    assert list(g["n_per_frame"][1:]) == [1, 3, 7, 12, 12]
 
 
 def test_threshold_maps():
