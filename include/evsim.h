@@ -162,9 +162,10 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
 /* Copy up to cap committed events, in output order, into out (host or device
  * memory per mem) and set *n_out.  Returns SIM_MORE if events remain (the next
  * call continues where this one stopped).  Waits for the handle's stream.
- * If a pushed frame failed on the device, returns that error code after
- * delivering the events of the frames committed before it; the handle then
- * continues from the last committed frame (see sim_stats.frames_committed). */
+ * If a pushed frame failed on the device, returns that error code and
+ * delivers nothing (*n_out = 0); the events of the frames committed before
+ * the failure stay for the next call, and the handle continues from the last
+ * committed frame (see sim_stats.frames_committed). */
 int sim_pop_events(sim_t* s, sim_event* out, int64_t cap, int64_t* n_out, int32_t mem);
 
 /* Wait for all work of the handle; returns (and clears) a pending device error. */

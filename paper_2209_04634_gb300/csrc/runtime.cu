@@ -198,9 +198,10 @@ template <class F>
 cudaError_t timed(sim_t* s, int kind, F&& launch) {
   if (!s->prof) return launch();
   ProfRec r{kind, pool_get(s), pool_get(s), false};
-  cudaEventRecord(r.a, s->stream);
+  // External records: under stream capture they become event-record nodes.
+  cudaEventRecordWithFlags(r.a, s->stream, cudaEventRecordExternal);
   cudaError_t e = launch();
-  cudaEventRecord(r.b, s->stream);
+  cudaEventRecordWithFlags(r.b, s->stream, cudaEventRecordExternal);
   s->pending.push_back(r);
   return e;
 }
@@ -651,12 +652,13 @@ int sim_pop_events(sim_t* s, sim_event* out, int64_t cap, int64_t* n_out, int32_
   Ctl c;
   int rc = read_ctl(s, &c);
   if (rc) return rc;
-  int status = SIM_OK;
   if (c.err) {
-    status = c.err;
+    // report the failure first; the committed events stay for the next pop
+    const int err = c.err;
     rc = recover(s, &c);
-    if (rc) return rc;
+    return rc ? rc : err;
   }
+  int status = SIM_OK;
   const long long avail = c.cursor - s->popped;
   const long long m = std::min<long long>(avail, cap);
   if (m > 0) {

@@ -247,9 +247,8 @@ def test_event_overflow_is_transactional():
     sim = evsim.simulator_for(seq, event_capacity=cap)
     for i in range(5):
         sim.push(seq.frames[i], seq.flows[i] if i else None, int(seq.t_us[i]))
-    out = np.empty(cap, dtype=evsim.EVENT_DTYPE)
     with pytest.raises(evsim.SimError) as ei:
-        sim.pop_into(out, cap)
+        sim.sync()
     assert ei.value.code == evsim.SIM_ERR_EVENT_OVERFLOW
     st = sim.stats()
     assert st.frames_committed == 3  # frames 0, 1, 2
@@ -327,4 +326,22 @@ def test_batch_rejects_bad_timestamps_before_enqueueing():
     assert sim.stats().frames_pushed == 0
     sim.push_many(seq.frames, seq.flows, seq.t_us)
     assert_same_events(sim.pop(), oracle_run(seq)["events"], "after rejected batch")
+    sim.close()
+
+
+def test_overflow_reported_by_pop_keeps_committed_events():
+    seq = synth.blob_translation(frames=5)
+    o = oracle_run(seq)
+    per = o["ev_per_frame"]
+    cap = int(per[1] + per[2] // 2)
+    sim = evsim.simulator_for(seq, event_capacity=cap)
+    for i in range(4):
+        sim.push(seq.frames[i], seq.flows[i] if i else None, int(seq.t_us[i]))
+    out = np.empty(cap, dtype=evsim.EVENT_DTYPE)
+    n = evsim.ctypes.c_int64(-1)
+    rc = sim._lib.sim_pop_events(sim.h, out.ctypes.data, cap, evsim.ctypes.byref(n), evsim.SIM_HOST)
+    assert rc == evsim.SIM_ERR_EVENT_OVERFLOW and n.value == 0
+    first = sim.pop()
+    assert len(first) == per[1]
+    assert_same_events(first, o["events"][:per[1]], "committed before the overflow")
     sim.close()
