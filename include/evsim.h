@@ -196,6 +196,10 @@ int sim_destroy(sim_t* s);
 /* Static English description of a return code. */
 const char* sim_strerror(int code);
 
+/* Description of the last CUDA runtime error that made a call of this host
+ * thread return SIM_ERR_CUDA / SIM_ERR_OOM / SIM_ERR_NO_DEVICE. */
+const char* sim_last_cuda_error(void);
+
 /* Library version, "major.minor.patch". */
 const char* sim_version(void);
 

@@ -174,8 +174,11 @@ evsim::SimParams make_params(const sim_t* s) {
   return p;
 }
 
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
 int cuda_rc(cudaError_t e) {
   if (e == cudaSuccess) return SIM_OK;
+  g_last_cuda = e;
   if (e == cudaErrorMemoryAllocation) return SIM_ERR_OOM;
   if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver || e == cudaErrorNoKernelImageForDevice)
     return SIM_ERR_NO_DEVICE;
@@ -280,6 +283,15 @@ cudaError_t batch_graph(sim_t* s, int n, GraphEntry** out) {
     return cudaSuccess;
   }
   prof_collect(s);  // pending must hold only this capture's event pairs
+  if (s->prof) {
+    // create the capture's events up front (4 kernels per frame at most)
+    while ((long long)s->pool.size() < 8LL * n) {
+      cudaEvent_t ev = nullptr;
+      cudaError_t ce = cudaEventCreate(&ev);
+      if (ce != cudaSuccess) return ce;
+      s->pool.push_back(ev);
+    }
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
@@ -341,6 +353,8 @@ int push_first(sim_t* s, const unsigned char* dframe, long long pitch, int64_t t
 extern "C" {
 
 const char* sim_version(void) { return "0.1.0"; }
+
+const char* sim_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
 
 const char* sim_strerror(int code) {
   switch (code) {

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("sim_destroy", ctypes.c_int, [_VP]),
     ("sim_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("sim_version", ctypes.c_char_p, []),
+    ("sim_last_cuda_error", ctypes.c_char_p, []),
 ]
 
 _lock = threading.Lock()
@@ -110,7 +111,10 @@ def load(path: str | None = None):
 class SimError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {strerror(code)} ({code})")
+        detail = ""
+        if code in (SIM_ERR_CUDA, SIM_ERR_OOM, SIM_ERR_NO_DEVICE):
+            detail = " [" + load().sim_last_cuda_error().decode() + "]"
+        super().__init__(f"{what}: {strerror(code)} ({code}){detail}")
 
 
 def strerror(code: int) -> str:
