@@ -180,42 +180,68 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
-// Single-pass scan across chunks with decoupled look-back.  Publishes chunk
-// c's aggregate, walks back over its predecessors (bounded spin) and
-// publishes its inclusive prefix.  Returns the exclusive prefix of chunk c.
+// Single-pass scan across chunks with decoupled look-back, run by one full
+// warp.  Publishes chunk c's aggregate, then inspects 32 predecessors per
+// step (nearest first): their values are summed up to the nearest inclusive
+// prefix, or the window slides back by 32 when all of them hold aggregates.
+// The spin on predecessors that have not published is bounded.  Publishes
+// chunk c's inclusive prefix and returns its exclusive prefix (all lanes).
 // Values saturate at LB_VALUE, which callers treat as an overflow.
-__device__ long long lookback(unsigned long long* status, int c, unsigned epoch,
-                              long long agg, int* err) {
+__device__ long long lookback_warp(unsigned long long* status, int c, unsigned epoch,
+                                   long long agg, int* err) {
+  const int lane = threadIdx.x & 31;
   const unsigned long long hi = (unsigned long long)epoch << 32;
   if (agg > (long long)LB_VALUE) agg = LB_VALUE;
-  if (c == 0) {
+  if (lane == 0) {
     __threadfence();
-    st_volatile(&status[0], hi | LB_INC | (unsigned long long)agg);
-    return 0;
+    st_volatile(&status[c], hi | (c == 0 ? LB_INC : LB_AGG) | (unsigned long long)agg);
   }
-  __threadfence();
-  st_volatile(&status[c], hi | LB_AGG | (unsigned long long)agg);
+  if (c == 0) return 0;
   long long excl = 0;
   int j = c - 1;
   int spins = 0;
-  while (j >= 0) {
-    const unsigned long long w = ld_volatile(&status[j]);
-    if ((unsigned)(w >> 32) == epoch && (w & (LB_AGG | LB_INC))) {
-      excl += (long long)(w & LB_VALUE);
-      if (w & LB_INC) break;
-      --j;
-    } else {
-      if (++spins > SPIN_LIMIT) {
-        atomicCAS(err, 0, SIM_ERR_DEVICE_TIMEOUT);
-        break;
-      }
-      __nanosleep(32);
+  for (;;) {
+    const int idx = j - lane;
+    bool valid = true, inc = true;
+    long long v = 0;
+    if (idx >= 0) {
+      const unsigned long long w = ld_volatile(&status[idx]);
+      valid = (unsigned)(w >> 32) == epoch && (w & (LB_AGG | LB_INC));
+      inc = valid && (w & LB_INC);
+      v = valid ? (long long)(w & LB_VALUE) : 0;
     }
+    const unsigned vm = __ballot_sync(FULL, valid), im = __ballot_sync(FULL, inc);
+    bool done = false, slide = false;
+    unsigned take = 0;
+    if (im) {
+      const int f = __ffs(im) - 1;  // nearest inclusive prefix
+      const unsigned need = f == 31 ? FULL : ((1u << (f + 1)) - 1);
+      if ((vm & need) == need) { done = true; take = need; }
+    } else if (vm == FULL) {
+      slide = true;
+      take = FULL;
+    }
+    if (done || slide) {
+      long long t = (take >> lane) & 1 ? v : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+      excl += t;
+      if (done) break;
+      j -= 32;
+      continue;
+    }
+    if (++spins > SPIN_LIMIT) {
+      if (lane == 0) atomicCAS(err, 0, SIM_ERR_DEVICE_TIMEOUT);
+      break;
+    }
+    __nanosleep(32);
   }
-  long long inc = excl + agg;
-  if (inc > (long long)LB_VALUE) inc = LB_VALUE;
-  __threadfence();
-  st_volatile(&status[c], hi | LB_INC | (unsigned long long)inc);
+  long long inc_v = excl + agg;
+  if (inc_v > (long long)LB_VALUE) inc_v = LB_VALUE;
+  if (lane == 0) {
+    __threadfence();
+    st_volatile(&status[c], hi | LB_INC | (unsigned long long)inc_v);
+  }
   return excl;
 }
 
@@ -250,14 +276,24 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, FrameArg fa) {
   if (block_error(&p.ctl->err)) return;
   const FrameDesc f = frame_of(fa);
   __shared__ unsigned long long s_m[NWARP];
+  constexpr int U = 8;  // independent loads in flight per thread
   const long long P = (long long)p.W * p.H;
   unsigned long long m = 0;
   int dummy = 0;
-  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-    const float2 fl = f.flow[i];
-    const long long fx = flow_q16(fl.x, dummy), fy = flow_q16(fl.y, dummy);
-    const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
-    m = f2 > m ? f2 : m;
+  for (long long i0 = blockIdx.x * (long long)NT * U + threadIdx.x; i0 < P;
+       i0 += (long long)gridDim.x * NT * U) {
+    float2 fl[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const long long i = i0 + (long long)q * NT;
+      fl[q] = i < P ? f.flow[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const long long fx = flow_q16(fl[q].x, dummy), fy = flow_q16(fl[q].y, dummy);
+      const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
+      m = f2 > m ? f2 : m;
+    }
   }
   m = warp_max_u64(m);
   if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
@@ -477,22 +513,39 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
 
   if (fast) {
     // Replicate-padded halo tiles of both log frames; the tile interior of the
-    // new frame also goes to the frame ring for the next push.
-    const int c0 = HMAX - hx, c1 = HMAX + TW + hx;
-    const int r0 = HMAX - hy, r1 = HMAX + TH + hy;
-    for (int sr = r0 + warp; sr < r1; sr += NWARP) {
-      const int ry = ty0 - HMAX + sr;
-      const int gy = min(max(ry, 0), H - 1);
-      for (int sc = c0 + lane; sc < c1; sc += 32) {
-        const int rxx = tx0 - HMAX + sc;
-        const int gx = min(max(rxx, 0), W - 1);
-        const int vp = ringp[(long long)gy * W + gx];
-        const int vc = load_luma(f.frame, f.pitch, p.ch, gy, gx);
-        L.sL0[sr * SW + sc] = L.slut[vp];
-        L.sL1[sr * SW + sc] = L.slut[vc];
-        if (ry == gy && rxx == gx && sr >= HMAX && sr < HMAX + TH && sc >= HMAX &&
-            sc < HMAX + TW)
-          ringn[(long long)gy * W + gx] = (unsigned char)vc;
+    // new frame also goes to the frame ring for the next push.  The region is
+    // walked as a flat index (row = e / ncols by a multiply-high with
+    // ceil(2^32 / ncols), exact for e < 2^16), FILL loads in flight per thread.
+    constexpr int FILL = 4;
+    const int c0 = HMAX - hx, ncols = TW + 2 * hx;
+    const int r0 = HMAX - hy, nrows = TH + 2 * hy;
+    const int total_fill = ncols * nrows;
+    const unsigned mcols = 0xFFFFFFFFu / (unsigned)ncols + 1u;
+    for (int e0 = 0; e0 < total_fill; e0 += NT * FILL) {
+      int vp[FILL], vc[FILL], at[FILL], ring_at[FILL];
+#pragma unroll
+      for (int q = 0; q < FILL; ++q) {
+        const int e = e0 + q * NT + tid;
+        at[q] = -1;
+        ring_at[q] = -1;
+        if (e < total_fill) {
+          const int sr = (int)__umulhi((unsigned)e, mcols);
+          const int sc = e - sr * ncols;
+          const int ry = ty0 - hy + sr, rxx = tx0 - hx + sc;
+          const int gy = min(max(ry, 0), H - 1), gx = min(max(rxx, 0), W - 1);
+          vp[q] = ringp[(long long)gy * W + gx];
+          vc[q] = load_luma(f.frame, f.pitch, p.ch, gy, gx);
+          at[q] = (r0 + sr) * SW + (c0 + sc);
+          if (ry == gy && rxx == gx && sr >= hy && sr < hy + TH && sc >= hx && sc < hx + TW)
+            ring_at[q] = gy * W + gx;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < FILL; ++q) {
+        if (at[q] < 0) continue;
+        L.sL0[at[q]] = L.slut[vp[q]];
+        L.sL1[at[q]] = L.slut[vc[q]];
+        if (ring_at[q] >= 0) ringn[ring_at[q]] = (unsigned char)vc[q];
       }
     }
   } else {
@@ -821,7 +874,10 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, FrameArg fa) {
     const int ex = block_excl_scan(cnt, s_warp, &total);
     s_ex[tid] = ex;
     s_src[tid] = src;
-    if (tid == 0) s_prefix = lookback(p.order_status, c, f.serial, total, &ctl->err);
+    if (tid < 32) {
+      const long long ex0 = lookback_warp(p.order_status, c, f.serial, total, &ctl->err);
+      if (tid == 0) s_prefix = ex0;
+    }
     __syncthreads();
     const long long base = cursor + s_prefix;
     for (int jj = tid; jj < total; jj += NT) {
@@ -958,7 +1014,7 @@ cudaError_t launch_init(const SimParams& p, const FrameArg& f, cudaStream_t st) 
 cudaError_t launch_flowmax(const SimParams& p, const FrameArg& f, cudaStream_t st) {
   const long long P = (long long)p.W * p.H;
   const int sms = device_sm_count();
-  const int grid = (int)std::max(1LL, std::min<long long>((P + NT - 1) / NT, (long long)sms * 4));
+  const int grid = (int)std::max(1LL, std::min<long long>((P + NT * 8 - 1) / (NT * 8), (long long)sms * 4));
   k_flowmax<<<grid, NT, 0, st>>>(p, f);
   return cudaGetLastError();
 }

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -176,6 +177,22 @@ evsim::SimParams make_params(const sim_t* s) {
 
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 
+// EVSIM_TRACE=1 in the environment prints every failing runtime call.
+bool trace_on() {
+  static const bool on = [] {
+    const char* v = std::getenv("EVSIM_TRACE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+cudaError_t traced(cudaError_t e, const char* what, int line) {
+  if (e != cudaSuccess && trace_on())
+    std::fprintf(stderr, "evsim: %s (line %d) -> %s\n", what, line, cudaGetErrorString(e));
+  return e;
+}
+#define TR(x) traced((x), #x, __LINE__)
+
 int cuda_rc(cudaError_t e) {
   if (e == cudaSuccess) return SIM_OK;
   g_last_cuda = e;
@@ -201,20 +218,24 @@ template <class F>
 cudaError_t timed(sim_t* s, int kind, F&& launch) {
   if (!s->prof) return launch();
   ProfRec r{kind, pool_get(s), pool_get(s), false};
-  // External records: under stream capture they become event-record nodes.
-  cudaEventRecordWithFlags(r.a, s->stream, cudaEventRecordExternal);
-  cudaError_t e = launch();
-  cudaEventRecordWithFlags(r.b, s->stream, cudaEventRecordExternal);
+  // Under stream capture the records must be external, so that they become
+  // event-record nodes of the graph; outside capture they are plain records.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s->stream, &cs);
+  const unsigned fl = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0;
+  TR(cudaEventRecordWithFlags(r.a, s->stream, fl));
+  cudaError_t e = TR(launch());
+  TR(cudaEventRecordWithFlags(r.b, s->stream, fl));
   s->pending.push_back(r);
   return e;
 }
 
 void prof_collect(sim_t* s) {
   if (s->pending.empty()) return;
-  cudaStreamSynchronize(s->stream);
+  TR(cudaStreamSynchronize(s->stream));
   for (auto& r : s->pending) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+    if (TR(cudaEventElapsedTime(&ms, r.a, r.b)) == cudaSuccess) {
       s->prof_ms[r.kind] += ms;
       s->prof_n[r.kind] += 1;
     }
@@ -293,7 +314,7 @@ cudaError_t batch_graph(sim_t* s, int n, GraphEntry** out) {
     }
   }
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e = TR(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   if (e != cudaSuccess) return e;
   cudaError_t le = cudaSuccess;
   for (int i = 0; i < n && le == cudaSuccess; ++i) {
@@ -301,7 +322,7 @@ cudaError_t batch_graph(sim_t* s, int n, GraphEntry** out) {
     fa.ptr = s->d_desc + i;
     le = enqueue_frame(s, fa);
   }
-  e = cudaStreamEndCapture(s->stream, &g);
+  e = TR(cudaStreamEndCapture(s->stream, &g));
   GraphEntry entry;
   entry.recs.swap(s->pending);
   for (auto& r : entry.recs) r.graph_owned = true;
@@ -316,7 +337,7 @@ cudaError_t batch_graph(sim_t* s, int n, GraphEntry** out) {
     drop();
     return le != cudaSuccess ? le : e;
   }
-  e = cudaGraphInstantiate(&entry.exec, g, 0);
+  e = TR(cudaGraphInstantiate(&entry.exec, g, 0));
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     drop();
@@ -628,7 +649,7 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
                             cudaMemcpyHostToDevice, s->stream);
-      if (e == cudaSuccess) e = cudaGraphLaunch(ge->exec, s->stream);
+      if (e == cudaSuccess) e = TR(cudaGraphLaunch(ge->exec, s->stream));
       if (e != cudaSuccess) return cuda_rc(e);
       if (s->prof) s->pending.insert(s->pending.end(), ge->recs.begin(), ge->recs.end());
     } else {
