@@ -72,12 +72,14 @@ __device__ __forceinline__ int adaptive_n(unsigned long long m, int nmax) {
   return n;
 }
 
-// a + floor(((b - a) f + 2048) / 4096): Q12-weighted blend, round half up.
-// LOG values span 19 bits so 32-bit products suffice; LINEAR needs 64 bits.
+// a + floor(((b - a) f + 2048) / 4096): Q12-weighted blend, round half up,
+// evaluated as (a (4096 - f) + b f + 2048) >> 12 (the same integer).  LOG
+// values span 19 bits, so the 32-bit products cannot overflow; LINEAR values
+// span 24 bits and take 64-bit products.
 template <bool WIDE>
 __device__ __forceinline__ int lerp12(int a, int b, int f) {
   if (WIDE) return a + (int)(((long long)(b - a) * f + 2048) >> 12);
-  return a + (((b - a) * f + 2048) >> 12);
+  return (a * (4096 - f) + b * f + 2048) >> 12;
 }
 
 __device__ __forceinline__ int load_luma(const unsigned char* f, long long pitch, int ch,
@@ -88,14 +90,24 @@ __device__ __forceinline__ int load_luma(const unsigned char* f, long long pitch
 }
 
 // Bilinear tap from a replicate-padded shared tile at a tile-relative Q16
-// position (always inside the filled region).
+// position (always inside the filled region).  `base` is the tile's 32-bit
+// shared-window address; the four taps are read with immediate offsets.
+static_assert(SW * 4 == 384, "tap offsets below assume a 96-int shared stride");
 template <bool WIDE>
-__device__ __forceinline__ int tap_shared(const int* s, int px, int py) {
+__device__ __forceinline__ int tap_shared(unsigned base, int px, int py) {
   const int ix = px >> 16, iy = py >> 16;
   const int fx = (px >> 4) & 0xFFF, fy = (py >> 4) & 0xFFF;
-  const int* q = s + iy * SW + ix;
-  const int top = lerp12<WIDE>(q[0], q[1], fx);
-  const int bot = lerp12<WIDE>(q[SW], q[SW + 1], fx);
+  const unsigned a = base + (unsigned)(iy * SW + ix) * 4u;
+  int l00, l01, l10, l11;
+  asm volatile(
+      "ld.shared.s32 %0, [%4];\n\t"
+      "ld.shared.s32 %1, [%4+4];\n\t"
+      "ld.shared.s32 %2, [%4+384];\n\t"
+      "ld.shared.s32 %3, [%4+388];"
+      : "=r"(l00), "=r"(l01), "=r"(l10), "=r"(l11)
+      : "r"(a));
+  const int top = lerp12<WIDE>(l00, l01, fx);
+  const int bot = lerp12<WIDE>(l10, l11, fx);
   return lerp12<WIDE>(top, bot, fy);
 }
 
@@ -121,23 +133,22 @@ __device__ __forceinline__ int tap_global(const unsigned char* img, long long pi
 // Threshold test of one interpolated value against the reference.
 // ACCUM: every whole threshold crossed is one event and moves R by it.
 // RESET: the paper's consecutive difference, strict comparisons.
+// Must be called by all 32 lanes: a pixel that crosses two or more
+// thresholds in one substep is rare, and the division it needs runs on a
+// warp-uniform branch.
 template <bool RESET>
 __device__ __forceinline__ int threshold_step(int I, int& R, int cp, int cn) {
   const int D = I - R;
-  int n = 0;
   if (RESET) {
-    n = D > cp ? 1 : (D < -cn ? -1 : 0);
     R = I;
-  } else {
-    if (D >= cp) {
-      n = D < 2 * cp ? 1 : D / cp;
-      R += n * cp;
-    } else if (D <= -cn) {
-      const int m = -D < 2 * cn ? 1 : (-D) / cn;
-      R -= m * cn;
-      n = -m;
-    }
+    return D > cp ? 1 : (D < -cn ? -1 : 0);
   }
+  int n = D >= cp ? 1 : (D <= -cn ? -1 : 0);
+  if (__any_sync(FULL, D >= 2 * cp || D <= -2 * cn)) {
+    if (D >= cp) n = D / cp;
+    else if (D <= -cn) n = -((-D) / cn);
+  }
+  R += n * (n > 0 ? cp : cn);
   return n;
 }
 
@@ -360,6 +371,8 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDe
     ay[j] = 0;
   }
   short* nkrow = L.snk + (2 * warp) * TW + lane;
+  const unsigned b0 = (unsigned)__cvta_generic_to_shared(L.sL0);
+  const unsigned b1 = (unsigned)__cvta_generic_to_shared(L.sL1);
   for (int k = 0; k < N; ++k) {
     const int w = L.swk[k];
     int n[4];
@@ -373,8 +386,8 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDe
       if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
       int s0, s1;
       if (FAST) {
-        s0 = tap_shared<WIDE>(L.sL0, px[j], py[j]);
-        s1 = tap_shared<WIDE>(L.sL1, px[j] + Fx[j], py[j] + Fy[j]);
+        s0 = tap_shared<WIDE>(b0, px[j], py[j]);
+        s1 = tap_shared<WIDE>(b1, px[j] + Fx[j], py[j] + Fy[j]);
       } else {
         s0 = tap_global<WIDE>(ringp, p.W, 1, p.W, p.H, L.slut, px[j], py[j]);
         s1 = tap_global<WIDE>(f.frame, f.pitch, p.ch, p.W, p.H, L.slut, px[j] + Fx[j],
