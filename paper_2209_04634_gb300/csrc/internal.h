@@ -7,12 +7,13 @@
 
 namespace evsim {
 
-// Dense tile: TW x TH pixels, NT threads, 4 pixels per thread (two rows of a
-// warp, columns lane and lane + 32).
+// Dense tile: TW x TH pixels (NTD threads: warp w owns tile row w, lane l
+// owns columns l and l + 32).
 constexpr int TW = 64;
 constexpr int TH = 16;
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
+constexpr int NTD = 512;  // dense kernel: one warp per tile row, 2 pixels per thread
 // Largest per-tile flow reach (pixels) served from the shared-memory halo;
 // tiles whose flow reaches further sample global memory instead.
 constexpr int HMAX = 16;

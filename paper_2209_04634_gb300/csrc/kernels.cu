@@ -162,21 +162,24 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
   return v;
 }
 
-// Exclusive scan of one int per thread over the block; *total gets the sum.
-// s_warp needs NWARP + 1 ints.  Contains barriers: call from all threads.
+// Exclusive scan of one int per thread over a block of NTH threads; *total
+// gets the sum.  s_warp needs NTH / 32 + 1 ints.  Contains barriers: call
+// from all threads.
+template <int NTH = NT>
 __device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int* total) {
+  constexpr int NW = NTH / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int incl = warp_incl_scan(v);
   if (lane == 31) s_warp[w] = incl;
   __syncthreads();
   if (w == 0) {
-    const int s = lane < NWARP ? s_warp[lane] : 0;
+    const int s = lane < NW ? s_warp[lane] : 0;
     const int si = warp_incl_scan(s);
-    if (lane < NWARP) s_warp[lane] = si - s;
-    if (lane == NWARP - 1) s_warp[NWARP] = si;
+    if (lane < NW) s_warp[lane] = si - s;
+    if (lane == NW - 1) s_warp[NW] = si;
   }
   __syncthreads();
-  *total = s_warp[NWARP];
+  *total = s_warp[NW];
   const int r = incl - v + s_warp[w];
   __syncthreads();
   return r;
@@ -317,7 +320,8 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, FrameArg fa) {
 }
 
 // ---------------------------------------------------------------------------
-// dense simulation of one 64 x 16 tile
+// dense simulation of one 64 x 16 tile: NTD threads, warp w owns tile row w,
+// lane l owns columns l and l + 32 of it.
 
 struct DenseLayout {
   int* sL0;
@@ -343,19 +347,18 @@ __device__ __forceinline__ DenseLayout dense_layout(unsigned char* raw, int nmax
   return L;
 }
 
-// The four pixels of a thread: columns lane, lane + 32 of rows 2 warp, 2 warp + 1.
 template <bool RESET, bool WIDE, bool FAST>
 __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDesc& f,
                                                const DenseLayout& L, int N, int tx0, int ty0,
-                                               const int (&Fx)[4], const int (&Fy)[4],
-                                               int (&R)[4], const int (&Cp)[4],
-                                               const int (&Cn)[4], const bool (&inb)[4],
+                                               const int (&Fx)[2], const int (&Fy)[2],
+                                               int (&R)[2], const int (&Cp)[2],
+                                               const int (&Cn)[2], const bool (&inb)[2],
                                                const unsigned char* ringp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int px[4], py[4], ax[4], ay[4], qx[4], rx[4], qy[4], ry[4];
+  int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
+  for (int j = 0; j < 2; ++j) {
+    const int lx = lane + 32 * j, ly = warp;
     // FAST: positions relative to the shared tile origin (tx0 - HMAX, ty0 - HMAX);
     // otherwise absolute image positions.
     px[j] = FAST ? (lx + HMAX) << 16 : (tx0 + lx) << 16;
@@ -370,14 +373,14 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDe
     ax[j] = 0;
     ay[j] = 0;
   }
-  short* nkrow = L.snk + (2 * warp) * TW + lane;
+  short* nkrow = L.snk + warp * TW + lane;
   const unsigned b0 = (unsigned)__cvta_generic_to_shared(L.sL0);
   const unsigned b1 = (unsigned)__cvta_generic_to_shared(L.sL1);
   for (int k = 0; k < N; ++k) {
     const int w = L.swk[k];
-    int n[4];
+    int n[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       px[j] -= qx[j];
       ax[j] += rx[j];
       if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
@@ -400,16 +403,10 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDe
     short* q = nkrow + k * (TH * TW);
     q[0] = (short)n[0];
     q[32] = (short)n[1];
-    q[TW] = (short)n[2];
-    q[TW + 32] = (short)n[3];
-    int c0 = abs(n[0]) + abs(n[1]), c1 = abs(n[2]) + abs(n[3]);
-    if (__any_sync(FULL, (c0 | c1) != 0)) {
+    int c0 = abs(n[0]) + abs(n[1]);
+    if (__any_sync(FULL, c0 != 0)) {
       c0 = __reduce_add_sync(FULL, c0);
-      c1 = __reduce_add_sync(FULL, c1);
-      if (lane == 0) {
-        L.srow[k * TH + 2 * warp] = c0;
-        L.srow[k * TH + 2 * warp + 1] = c1;
-      }
+      if (lane == 0) L.srow[k * TH + warp] = c0;
     }
   }
 }
@@ -417,10 +414,11 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDe
 // Tile-local offsets of `E` segment counts (substep-major), staging allocation
 // and the segment table entries.  Returns the staging base, or -1 when the
 // staging area is exhausted (the frame then fails and emits nothing).
+template <int NTH = NT>
 __device__ __forceinline__ int stage_segments(const SimParams& p, const int* cnt, int* off, int E,
                                               int* s_warp, int* s_base, int* total_out) {
   const int tid = threadIdx.x;
-  constexpr int PER = 8;  // entries per thread (E <= PER * NT)
+  constexpr int PER = 2048 / NTH;  // entries per thread (E <= 2048)
   int v[PER], sum = 0;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -429,7 +427,7 @@ __device__ __forceinline__ int stage_segments(const SimParams& p, const int* cnt
     sum += v[q];
   }
   int total;
-  int ex = block_excl_scan(sum, s_warp, &total);
+  int ex = block_excl_scan<NTH>(sum, s_warp, &total);
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int e = PER * tid + q;
@@ -455,9 +453,9 @@ __device__ __forceinline__ int stage_segments(const SimParams& p, const int* cnt
 }
 
 template <bool RESET, bool MAPS, bool WIDE>
-__global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
+__global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, FrameArg fa) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_warp[NWARP + 1];
+  __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy, s_clamp, s_base;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
@@ -471,7 +469,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
   const int tx0 = tcx * TW, ty0 = tcy * TH;
   const int W = p.W, H = p.H;
 
-  L.slut[tid] = p.lut[tid];
+  if (tid < 256) L.slut[tid] = p.lut[tid];
   if (tid == 0) { s_fx = 0; s_fy = 0; s_clamp = 0; }
   const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(ctl->maxf2, nmax);
   const int sel = ctl->sel;
@@ -482,13 +480,14 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
   if (tile == 0 && tid == 0) ctl->n_frame = N;
   const long long tprev = ctl->t_prev;
 
-  int Fx[4], Fy[4], R[4], Cp[4], Cn[4];
-  bool inb[4];
+  const int y = ty0 + warp;
+  int Fx[2], Fy[2], R[2], Cp[2], Cn[2];
+  bool inb[2];
   int clamps = 0;
   unsigned mfx = 0, mfy = 0;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+  for (int j = 0; j < 2; ++j) {
+    const int x = tx0 + lane + 32 * j;
     inb[j] = x < W && y < H;
     Fx[j] = 0; Fy[j] = 0; R[j] = 0; Cp[j] = p.cp; Cn[j] = p.cn;
     if (inb[j]) {
@@ -511,7 +510,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
     const long long dt = f.t_rel - tprev;
     L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
   }
-  for (int e = tid; e < N * TH; e += NT) L.srow[e] = 0;
+  for (int e = tid; e < N * TH; e += NTD) L.srow[e] = 0;
   __syncthreads();
   if (lane == 0) {
     atomicMax(&s_fx, (int)mfx);
@@ -529,16 +528,16 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
     // new frame also goes to the frame ring for the next push.  The region is
     // walked as a flat index (row = e / ncols by a multiply-high with
     // ceil(2^32 / ncols), exact for e < 2^16), FILL loads in flight per thread.
-    constexpr int FILL = 4;
+    constexpr int FILL = 2;
     const int c0 = HMAX - hx, ncols = TW + 2 * hx;
     const int r0 = HMAX - hy, nrows = TH + 2 * hy;
     const int total_fill = ncols * nrows;
     const unsigned mcols = 0xFFFFFFFFu / (unsigned)ncols + 1u;
-    for (int e0 = 0; e0 < total_fill; e0 += NT * FILL) {
+    for (int e0 = 0; e0 < total_fill; e0 += NTD * FILL) {
       int vp[FILL], vc[FILL], at[FILL], ring_at[FILL];
 #pragma unroll
       for (int q = 0; q < FILL; ++q) {
-        const int e = e0 + q * NT + tid;
+        const int e = e0 + q * NTD + tid;
         at[q] = -1;
         ring_at[q] = -1;
         if (e < total_fill) {
@@ -563,9 +562,9 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       if (!inb[j]) continue;
-      const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+      const int x = tx0 + lane + 32 * j;
       ringn[(long long)y * W + x] = (unsigned char)load_luma(f.frame, f.pitch, p.ch, y, x);
     }
   }
@@ -573,9 +572,9 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
   if (RESET) {
     // Consecutive differences start from frame i-1 itself.
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       if (!inb[j]) continue;
-      const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+      const int x = tx0 + lane + 32 * j;
       R[j] = L.slut[ringp[(long long)y * W + x]];
     }
   }
@@ -587,9 +586,9 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
 
   if (!RESET) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       if (!inb[j]) continue;
-      const int x = tx0 + lane + 32 * (j & 1), y = ty0 + 2 * warp + (j >> 1);
+      const int x = tx0 + lane + 32 * j;
       Rout[(long long)y * W + x] = R[j];
     }
   }
@@ -598,43 +597,38 @@ __global__ void __launch_bounds__(NT, 2) k_dense(SimParams p, FrameArg fa) {
   // Tile-local offsets of the (substep, row) segments, substep-major.
   const int E = N * TH;
   int total;
-  const int base = stage_segments(p, L.srow, L.soff, E, s_warp, &s_base, &total);
+  const int base = stage_segments<NTD>(p, L.srow, L.soff, E, s_warp, &s_base, &total);
   const bool fail = base < 0;
-  for (int e = tid; e < E; e += NT) {
-    const int k = e / TH, ty = e % TH, y = ty0 + ty;
-    if (y < H)
-      p.seg[((long long)k * H + y) * p.tiles_x + tcx] =
+  for (int e = tid; e < E; e += NTD) {
+    const int k = e / TH, ty = e % TH, yy = ty0 + ty;
+    if (yy < H)
+      p.seg[((long long)k * H + yy) * p.tiles_x + tcx] =
           make_int2(fail ? 0 : L.srow[e], (fail ? 0 : base) + L.soff[e]);
   }
   if (fail || total == 0) return;
 
-  // Emission: each warp writes the events of its two rows, substep by substep.
+  // Emission: each warp writes the events of its row, substep by substep.
   const unsigned lt = lanemask_lt();
   for (int k = 0; k < N; ++k) {
+    const int e = k * TH + warp;
+    if (L.srow[e] == 0) continue;
     const unsigned tk = L.stk[k];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int ty = 2 * warp + r;
-      const int e = k * TH + ty;
-      if (L.srow[e] == 0) continue;
-      const int y = ty0 + ty;
-      const unsigned o = (unsigned)base + (unsigned)L.soff[e];
-      const int na = L.snk[e * TW + lane], nb = L.snk[e * TW + lane + 32];
-      const int aa = abs(na), ab = abs(nb);
-      const int xa = tx0 + lane, xb = tx0 + lane + 32;
-      if (__all_sync(FULL, (aa | ab) <= 1)) {
-        const unsigned ba = __ballot_sync(FULL, aa != 0), bb = __ballot_sync(FULL, ab != 0);
-        if (aa) p.staging[o + __popc(ba & lt)] = make_event(tk, xa, y, na > 0);
-        if (ab) p.staging[o + __popc(ba) + __popc(bb & lt)] = make_event(tk, xb, y, nb > 0);
-      } else {
-        const int ia = warp_incl_scan(aa);
-        const int ta = __shfl_sync(FULL, ia, 31);
-        const int ib = warp_incl_scan(ab);
-        const Ev ea = make_event(tk, xa, y, na > 0), eb = make_event(tk, xb, y, nb > 0);
-        const unsigned oa = o + ia - aa, ob = o + ta + ib - ab;
-        for (int m = 0; m < aa; ++m) p.staging[oa + m] = ea;
-        for (int m = 0; m < ab; ++m) p.staging[ob + m] = eb;
-      }
+    const unsigned o = (unsigned)base + (unsigned)L.soff[e];
+    const int na = L.snk[e * TW + lane], nb = L.snk[e * TW + lane + 32];
+    const int aa = abs(na), ab = abs(nb);
+    const int xa = tx0 + lane, xb = tx0 + lane + 32;
+    if (__all_sync(FULL, (aa | ab) <= 1)) {
+      const unsigned ba = __ballot_sync(FULL, aa != 0), bb = __ballot_sync(FULL, ab != 0);
+      if (aa) p.staging[o + __popc(ba & lt)] = make_event(tk, xa, y, na > 0);
+      if (ab) p.staging[o + __popc(ba) + __popc(bb & lt)] = make_event(tk, xb, y, nb > 0);
+    } else {
+      const int ia = warp_incl_scan(aa);
+      const int ta = __shfl_sync(FULL, ia, 31);
+      const int ib = warp_incl_scan(ab);
+      const Ev ea = make_event(tk, xa, y, na > 0), eb = make_event(tk, xb, y, nb > 0);
+      const unsigned oa = o + ia - aa, ob = o + ta + ib - ab;
+      for (int m = 0; m < aa; ++m) p.staging[oa + m] = ea;
+      for (int m = 0; m < ab; ++m) p.staging[ob + m] = eb;
     }
   }
 }
@@ -1038,7 +1032,7 @@ cudaError_t launch_dense(const SimParams& p, const FrameArg& f, cudaStream_t st)
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NT, sm, st>>>(p, f)
+#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NTD, sm, st>>>(p, f)
   if (!reset && !maps && !wide) EVSIM_DENSE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_DENSE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_DENSE(false, false, true);
