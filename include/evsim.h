@@ -70,10 +70,7 @@ enum { SIM_HOST = 0, SIM_DEVICE = 1 };         /* where a buffer lives */
 
 #define SIM_MAX_DIM 8192
 #define SIM_MAX_SUBSTEPS 64
-#define SIM_MAX_BATCH 1024          /* frames per CUDA-graph replay of sim_push_frames */
-
-/* sim_config.flags */
-#define SIM_FLAG_NO_GRAPHS 1        /* sim_push_frames launches kernels one by one */
+#define SIM_MAX_BATCH 1024          /* frames per device batch of sim_push_frames */
 
 typedef struct sim_s sim_t;   /* opaque, owned by the library */
 
@@ -96,12 +93,13 @@ typedef struct {
   int32_t c_pos_q16;         /* uniform C_pos, Q16 (0.2 log units = 13107) */
   int32_t c_neg_q16;         /* uniform |C_neg|, Q16 */
   int32_t c_act_q16;         /* sparse activity threshold, Q16; < 0: min(Cp(x), Cn(x)) */
-  int32_t flags;             /* SIM_FLAG_* bits; 0: defaults */
+  int32_t max_batch;         /* frames per device batch (<= SIM_MAX_BATCH); 0: what a
+                                256 MB segment table holds */
   const uint16_t* c_pos_map; /* optional host W*H Q16 per-pixel C_pos (copied at create) */
   const uint16_t* c_neg_map; /* optional host W*H Q16 per-pixel |C_neg| */
   int64_t event_capacity;    /* device event buffer (events); 0: default max(2^20, 8 W H) */
   void* cuda_stream;         /* cudaStream_t to order work on; NULL: library-owned stream;
-                                cudaStreamLegacy for the legacy default stream (no graphs) */
+                                cudaStreamLegacy for the legacy default stream */
 } sim_config;
 
 typedef struct {
@@ -109,11 +107,13 @@ typedef struct {
   int64_t frames_committed;  /* frames whose events and state are committed */
   int64_t events_pending;    /* committed events not yet popped */
   int64_t events_popped;     /* events returned by sim_pop_events so far */
-  int64_t last_active;       /* sparse: active pixels of the last committed frame */
-  int64_t last_frame_events; /* events of the last committed frame */
+  int64_t last_active;       /* pixels simulated in the last committed batch (sparse:
+                                active pixels summed over its frames) */
+  int64_t last_batch_events; /* events of the last committed batch (a single push is a
+                                batch of one frame) */
   int64_t flow_clamped;      /* flow components clamped to +-1024 px so far */
   int32_t last_substeps;     /* N of the last committed frame */
-  int32_t reserved0;
+  int32_t max_batch;         /* frames per device batch */
   int64_t pixel_substeps;    /* sum over committed frames of width * height * N */
   int64_t active_substeps;   /* sum over committed frames of (pixels simulated) * N */
 } sim_stats;
@@ -145,17 +145,21 @@ int sim_create(const sim_config* cfg, sim_t** out);
  * Asynchronous: returns once the work is enqueued.  The first push sets the
  * reference from frame 0 and emits no events.  A device-side failure (event
  * overflow) is reported by the next sim_sync / sim_pop_events; the failing
- * frame and any frame pushed after it are then not committed. */
+ * frame and any frame pushed after it are then not committed.  Same as
+ * sim_push_frames with count = 1. */
 int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float* flow,
                    int64_t t_us, int32_t mem);
 
-/* Push count frames in one call; equivalent to count sim_push_frame calls
- * with frames[i], flows[i], t_us[i] (host arrays of pointers; the pointers
- * themselves point to host or device memory per mem).  Device-memory batches
- * are replayed as a CUDA graph (one graph per batch length, captured on first
- * use and cached; batches longer than SIM_MAX_BATCH are split); host-memory
- * batches are first copied into a device staging area that grows to fit.
- * Timestamps are validated for the whole batch before anything is enqueued. */
+/* Push count frames in one call: frames[i], flows[i], t_us[i] (host arrays of
+ * pointers; the pointers point to host or device memory per mem).  The
+ * frames are simulated as device batches of up to sim_stats.max_batch frames,
+ * three kernel launches per batch: each tile (or raster chunk) is carried
+ * through every frame of the batch by one block.  A batch commits as a whole:
+ * if its events do not fit, none of its frames commit (SIM_ERR_EVENT_OVERFLOW
+ * at the next sim_sync / sim_pop_events).  Host-memory batches are first
+ * copied into a device staging area that grows to fit.  Timestamps are
+ * validated for the whole call before anything is enqueued.  The event
+ * stream equals that of count sim_push_frame calls. */
 int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t pitch_bytes,
                     const float* const* flows, const int64_t* t_us, int32_t mem);
 

@@ -24,34 +24,35 @@ constexpr int MAXN = 64;           // largest substep count
 // chunk are compacted and simulated by the block that owns the chunk.
 constexpr int SCHUNK = 4 * NT;
 constexpr int SROUNDS = SCHUNK / NT;
-// Order kernel: segments per chunk (one per thread).
-constexpr int OCHUNK = NT;
+// Order kernel: segments per chunk (four per thread).
+constexpr int OPER = 4;
+constexpr int OCHUNK = OPER * NT;
 
 // Look-back status word: [epoch:32][flag:2][value:30].
 constexpr unsigned long long LB_AGG = 1ull << 30;
 constexpr unsigned long long LB_INC = 2ull << 30;
 constexpr unsigned long long LB_VALUE = (1ull << 30) - 1;
-constexpr int MAX_EVENTS_PER_FRAME = (1 << 30) - 1;
+constexpr int MAX_EVENTS = (1 << 30) - 2;  // per batch (and event buffer capacity)
 // Bounded spin: polls before a look-back gives up and flags a timeout.
 constexpr int SPIN_LIMIT = 1 << 22;
 
 // Device-resident control block of one stream.  Fields marked "committed"
-// change only when a frame commits; the others are per-frame scratch that the
-// order kernel resets when it finishes a frame.
+// change only when a batch of frames commits; the others are per-batch
+// scratch that the order kernel resets when it finishes a batch.
 struct Ctl {
   int err;                       // sticky error (0 or a SIM_ERR_* code)
   int sel;                       // committed: bit0 reference ping-pong, bit1 frame ring
-  int n_frame;                   // substeps of the frame in flight / last frame
-  int frame_fail;                // staging overflow seen while simulating this frame
-  unsigned long long maxf2;      // adaptive: max squared Q16 flow of processed pixels
-  long long t_prev;              // committed: t_{i-1} - t_0 (us)
+  int last_n;                    // committed: substeps of the last frame
+  int batch_fail;                // staging overflow seen while simulating this batch
+  long long t_prev;              // committed: t of the last frame - t_0 (us)
   long long cursor;              // committed: events held in the event buffer
   long long committed;           // committed: frames
-  long long frame_events;        // committed: events of the last committed frame
-  long long active;              // sparse: active pixels of the frame in flight
-  long long last_active;         // sparse: active pixels of the last finished frame
+  long long batch_events;        // committed: events of the last committed batch
+  long long active;              // sparse: active pixels of the batch in flight
+  long long last_active;         // sparse: active pixels of the last committed batch
   long long work_px;             // committed: sum over frames of W H N
-  long long work_active;         // committed: sum over frames of (processed pixels) N
+  long long work_active;         // committed: sum over frames of (pixels simulated) N
+  long long active_n;            // sparse: sum over the batch in flight of active pixels x N
   unsigned long long clamped;    // flow components clamped so far
   unsigned long long stage_top;  // staging bump allocator (events)
   unsigned int order_ticket;     // order kernel: chunk tickets
@@ -60,20 +61,18 @@ struct Ctl {
   unsigned int pad0;
 };
 
-// Per-frame arguments.  Kernels take a pointer into a device-resident table
-// (CUDA-graph replays of frame batches) or, when it is null, the value.
+// Per-frame arguments of a batch (device-resident table).
 struct FrameDesc {
-  const unsigned char* frame;   // current input frame (device)
+  const unsigned char* frame;   // input frame (device)
   long long pitch;              // bytes per input row
-  const float2* flow;           // H*W (dx, dy)
-  long long t_rel;              // t_i - t_0 of this frame (us)
-  unsigned int serial;          // push serial: epoch of the look-back words
-  int pad;
+  const float2* flow;           // H*W (dx, dy); unused for a stream's first frame
+  long long t_rel;              // t_i - t_0 (us)
 };
 
-struct FrameArg {
-  const FrameDesc* ptr;
-  FrameDesc val;
+struct BatchArg {
+  const FrameDesc* frames;      // count descriptors (device)
+  int count;
+  unsigned int serial;          // batch serial: epoch of the look-back words
 };
 
 struct Ev {  // same layout as sim_event
@@ -81,45 +80,43 @@ struct Ev {  // same layout as sim_event
   unsigned int xyp;  // x | (yp << 16)
 };
 
-// Everything a kernel needs for one stream and one pushed frame.
+// Everything the kernels need about one stream (fixed for its lifetime).
 struct SimParams {
   int W, H, ch;
   int tiles_x, tiles_y;
   int mode, ref_mode, intensity;
   int n_fixed, n_max;
   int cp, cn, cact;
-  int pad0;
+  int bmax;                     // frames per batch the segment table holds
   const unsigned short* cpmap;
   const unsigned short* cnmap;
   const int* lut;               // 256 Q16 entries (device)
-  unsigned char* ring0;         // luma frame ring, W bytes per row
+  unsigned char* ring0;         // luma frame ring (last frame of the previous batch)
   unsigned char* ring1;
-  int* R0;                      // reference (dense: ping-pong pair; sparse: R0 only)
+  int* R0;                      // reference ping-pong pair
   int* R1;
-  int* Rsave;                   // sparse: previous reference of active pixels (per chunk slot)
-  int* chunk_active;            // sparse: active pixels per chunk
   Ctl* ctl;
+  unsigned long long* maxf2;    // [bmax] adaptive: max squared Q16 flow per frame
   Ev* staging;
-  unsigned int stage_cap;
-  int pad1;
-  int2* seg;                    // (count, staging offset) per (substep, segment)
+  long long stage_cap;
+  int2* seg;                    // (count, staging offset) per (frame, substep, segment)
+  long long segs_per_k;         // segments per substep of one frame
   unsigned long long* order_status;
   Ev* events;
   long long event_cap;
-  int* idx;                     // sparse: active pixel indices per chunk slot
 };
 
-// Shared-memory bytes of the dense kernel for a substep cap.
+// Shared-memory bytes of the dense and sparse kernels for a substep cap.
 size_t dense_smem_bytes(int n_max);
 size_t sparse_smem_bytes(int n_max);
 
 // Launchers (kernels.cu).  Each returns the cudaError_t of the launch.
-cudaError_t launch_init(const SimParams& p, const FrameArg& f, cudaStream_t st);
-cudaError_t launch_flowmax(const SimParams& p, const FrameArg& f, cudaStream_t st);
-cudaError_t launch_dense(const SimParams& p, const FrameArg& f, cudaStream_t st);
-cudaError_t launch_sparse_pre(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid);
-cudaError_t launch_sparse(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid);
-cudaError_t launch_order(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid);
+cudaError_t launch_init(const SimParams& p, const FrameDesc& f, cudaStream_t st);
+cudaError_t launch_flowmax(const SimParams& p, const BatchArg& b, cudaStream_t st);
+cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st);
+cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st);
+cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st);
+cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
 int device_sm_count();
 

@@ -1,24 +1,28 @@
 // CUDA kernels of the evsim library (sm_103a).
 //
-// One pushed frame runs, on the handle's stream:
+// Frames are simulated in batches (a single push is a batch of one).  One
+// batch runs, on the handle's stream:
 //   dense : [flowmax, adaptive N only] -> dense -> order
 //   sparse: [sparse_pre, adaptive N only] -> sparse -> order
 // The method (Ziegler et al., arXiv 2209.04634, Sec. III-A / III-B) and its
 // integer arithmetic are described in include/evsim.h.  Every kernel checks
 // the stream's sticky error word first and does nothing once it is set.
-// Per-frame arguments (input pointers, timestamp, push serial) come in a
-// FrameArg, so that a batch of frames can be captured once as a CUDA graph
-// whose kernels read their arguments from a device-resident table.
+//
+// The simulating kernels are persistent over the batch: each block owns one
+// tile (dense) or one raster chunk (sparse) and carries it through every frame
+// of the batch, keeping the reference in registers / shared memory.  Blocks
+// never wait for each other, so the grid may exceed the resident capacity.
 //
 // Event order.  Within a frame, events are ordered by (substep, row, column,
-// repeat).  The simulating kernels work pixel-major, so they record each
-// pixel's per-substep count in shared memory, write their events to a
-// staging area in their own local order and publish one (count, staging
-// offset) entry per "segment" (dense: one row of a 64 x 16 tile; sparse: the
-// active pixels of one chunk of 1024 raster pixels).  The order kernel scans
-// the segment counts in output order (a single-pass scan with decoupled
-// look-back) and gathers the events into the stream's event buffer; the
-// block that finishes the last chunk commits the frame.
+// repeat); frames follow each other.  The simulating kernels work
+// pixel-major, so they record each pixel's per-substep count in shared
+// memory, write their events to a staging area in their own local order and
+// publish one (count, staging offset) entry per "segment" (dense: one row of
+// a 64 x 16 tile; sparse: the active pixels of one chunk of 1024 raster
+// pixels) per substep and frame.  The order kernel scans the batch's segment
+// counts in output order (a single-pass scan with decoupled look-back),
+// gathers the events into the stream's event buffer, and the block that
+// finishes the last chunk commits the whole batch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -266,13 +270,76 @@ __device__ __forceinline__ Ev make_event(unsigned t, int x, int y, bool pos) {
   return e;
 }
 
-__device__ __forceinline__ FrameDesc frame_of(const FrameArg& f) { return f.ptr ? *f.ptr : f.val; }
+// The previous frame of batch frame i: the frame ring for i = 0 (the last
+// frame of the previous batch, luma), else the batch's own frame i - 1.
+struct FrameRef {
+  const unsigned char* ptr;
+  long long pitch;
+  int ch;
+};
+
+__device__ __forceinline__ FrameRef prev_frame(const SimParams& p, const BatchArg& b, int i,
+                                               const unsigned char* ringp) {
+  FrameRef r;
+  if (i == 0) {
+    r.ptr = ringp;
+    r.pitch = p.W;
+    r.ch = 1;
+  } else {
+    const FrameDesc d = b.frames[i - 1];
+    r.ptr = d.frame;
+    r.pitch = d.pitch;
+    r.ch = p.ch;
+  }
+  return r;
+}
+
+// Tile-local offsets of `E` segment counts (substep-major), staging allocation.
+// Returns the staging base, or -1 when the staging area is exhausted (the
+// batch then fails and emits nothing more).
+template <int NTH = NT>
+__device__ __forceinline__ long long stage_segments(const SimParams& p, const int* cnt, int* off,
+                                                    int E, int* s_warp, long long* s_base,
+                                                    int* total_out) {
+  const int tid = threadIdx.x;
+  constexpr int PER = 2048 / NTH;  // entries per thread (E <= 2048)
+  int v[PER], sum = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = PER * tid + q;
+    v[q] = e < E ? cnt[e] : 0;
+    sum += v[q];
+  }
+  int total;
+  int ex = block_excl_scan<NTH>(sum, s_warp, &total);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = PER * tid + q;
+    if (e < E) off[e] = ex;
+    ex += v[q];
+  }
+  if (tid == 0) {
+    long long base = 0;
+    if (total > 0) {
+      const unsigned long long bb = atomicAdd(&p.ctl->stage_top, (unsigned long long)total);
+      if (bb + (unsigned long long)total > (unsigned long long)p.stage_cap) {
+        base = -1;
+        atomicExch(&p.ctl->batch_fail, 1);
+      } else {
+        base = (long long)bb;
+      }
+    }
+    *s_base = base;
+  }
+  __syncthreads();
+  *total_out = total;
+  return *s_base;
+}
 
 // ---------------------------------------------------------------------------
-// frame 0: fill the frame ring and the reference
+// frame 0 of a stream: fill the frame ring and the reference
 
-__global__ void k_init(SimParams p, FrameArg fa) {
-  const FrameDesc f = frame_of(fa);
+__global__ void k_init(SimParams p, FrameDesc f) {
   const long long P = (long long)p.W * p.H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
        i += (long long)gridDim.x * blockDim.x) {
@@ -284,11 +351,13 @@ __global__ void k_init(SimParams p, FrameArg fa) {
 }
 
 // ---------------------------------------------------------------------------
-// adaptive N (dense): max over all pixels of the squared Q16 flow
+// adaptive N (dense): max over all pixels of the squared Q16 flow, per frame
+// of the batch (blockIdx.y = frame)
 
-__global__ void __launch_bounds__(NT) k_flowmax(SimParams p, FrameArg fa) {
+__global__ void __launch_bounds__(NT) k_flowmax(SimParams p, BatchArg b) {
   if (block_error(&p.ctl->err)) return;
-  const FrameDesc f = frame_of(fa);
+  const int i = blockIdx.y;
+  const FrameDesc f = b.frames[i];
   __shared__ unsigned long long s_m[NWARP];
   constexpr int U = 8;  // independent loads in flight per thread
   const long long P = (long long)p.W * p.H;
@@ -299,8 +368,8 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, FrameArg fa) {
     float2 fl[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const long long i = i0 + (long long)q * NT;
-      fl[q] = i < P ? f.flow[i] : make_float2(0.f, 0.f);
+      const long long j = i0 + (long long)q * NT;
+      fl[q] = j < P ? f.flow[j] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
@@ -313,15 +382,17 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, FrameArg fa) {
   if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long b = 0;
-    for (int w = 0; w < NWARP; ++w) b = s_m[w] > b ? s_m[w] : b;
-    if (b) atomicMax(&p.ctl->maxf2, b);
+    unsigned long long bm = 0;
+    for (int w = 0; w < NWARP; ++w) bm = s_m[w] > bm ? s_m[w] : bm;
+    if (bm) atomicMax(&p.maxf2[i], bm);
   }
 }
 
 // ---------------------------------------------------------------------------
-// dense simulation of one 64 x 16 tile: NTD threads, warp w owns tile row w,
-// lane l owns columns l and l + 32 of it.
+// dense simulation (Sec. III-A).  One block per 64 x 16 tile runs the tile
+// through every frame of the batch, keeping the tile's reference R (and
+// thresholds) in registers from the first frame to the last.  Warp w owns
+// tile row w, lane l owns columns l and l + 32.
 
 struct DenseLayout {
   int* sL0;
@@ -348,12 +419,12 @@ __device__ __forceinline__ DenseLayout dense_layout(unsigned char* raw, int nmax
 }
 
 template <bool RESET, bool WIDE, bool FAST>
-__device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDesc& f,
-                                               const DenseLayout& L, int N, int tx0, int ty0,
-                                               const int (&Fx)[2], const int (&Fy)[2],
-                                               int (&R)[2], const int (&Cp)[2],
-                                               const int (&Cn)[2], const bool (&inb)[2],
-                                               const unsigned char* ringp) {
+__device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLayout& L, int N,
+                                               int tx0, int ty0, const FrameRef& prv,
+                                               const FrameDesc& cur, const int (&Fx)[2],
+                                               const int (&Fy)[2], int (&R)[2],
+                                               const int (&Cp)[2], const int (&Cn)[2],
+                                               const bool (&inb)[2]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
@@ -392,8 +463,8 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDe
         s0 = tap_shared<WIDE>(b0, px[j], py[j]);
         s1 = tap_shared<WIDE>(b1, px[j] + Fx[j], py[j] + Fy[j]);
       } else {
-        s0 = tap_global<WIDE>(ringp, p.W, 1, p.W, p.H, L.slut, px[j], py[j]);
-        s1 = tap_global<WIDE>(f.frame, f.pitch, p.ch, p.W, p.H, L.slut, px[j] + Fx[j],
+        s0 = tap_global<WIDE>(prv.ptr, prv.pitch, prv.ch, p.W, p.H, L.slut, px[j], py[j]);
+        s1 = tap_global<WIDE>(cur.frame, cur.pitch, p.ch, p.W, p.H, L.slut, px[j] + Fx[j],
                               py[j] + Fy[j]);
       }
       const int I = lerp12<WIDE>(s0, s1, w);
@@ -411,55 +482,14 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const FrameDe
   }
 }
 
-// Tile-local offsets of `E` segment counts (substep-major), staging allocation
-// and the segment table entries.  Returns the staging base, or -1 when the
-// staging area is exhausted (the frame then fails and emits nothing).
-template <int NTH = NT>
-__device__ __forceinline__ int stage_segments(const SimParams& p, const int* cnt, int* off, int E,
-                                              int* s_warp, int* s_base, int* total_out) {
-  const int tid = threadIdx.x;
-  constexpr int PER = 2048 / NTH;  // entries per thread (E <= 2048)
-  int v[PER], sum = 0;
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int e = PER * tid + q;
-    v[q] = e < E ? cnt[e] : 0;
-    sum += v[q];
-  }
-  int total;
-  int ex = block_excl_scan<NTH>(sum, s_warp, &total);
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int e = PER * tid + q;
-    if (e < E) off[e] = ex;
-    ex += v[q];
-  }
-  if (tid == 0) {
-    int base = 0;
-    if (total > 0) {
-      const unsigned long long b = atomicAdd(&p.ctl->stage_top, (unsigned long long)total);
-      if (b + (unsigned long long)total > (unsigned long long)p.stage_cap) {
-        base = -1;
-        atomicExch(&p.ctl->frame_fail, 1);
-      } else {
-        base = (int)b;
-      }
-    }
-    *s_base = base;
-  }
-  __syncthreads();
-  *total_out = total;
-  return *s_base;
-}
-
 template <bool RESET, bool MAPS, bool WIDE>
-__global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, FrameArg fa) {
+__global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NTD / 32 + 1];
-  __shared__ int s_fx, s_fy, s_clamp, s_base;
+  __shared__ int s_fx, s_fy;
+  __shared__ long long s_base;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
-  const FrameDesc f = frame_of(fa);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
@@ -470,121 +500,170 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, FrameArg fa) {
   const int W = p.W, H = p.H;
 
   if (tid < 256) L.slut[tid] = p.lut[tid];
-  if (tid == 0) { s_fx = 0; s_fy = 0; s_clamp = 0; }
-  const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(ctl->maxf2, nmax);
   const int sel = ctl->sel;
   const int* Rin = (sel & 1) ? p.R1 : p.R0;
   int* Rout = (sel & 1) ? p.R0 : p.R1;
   const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
   unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
-  if (tile == 0 && tid == 0) ctl->n_frame = N;
-  const long long tprev = ctl->t_prev;
+  long long tprev = ctl->t_prev;
 
   const int y = ty0 + warp;
-  int Fx[2], Fy[2], R[2], Cp[2], Cn[2];
+  int R[2], Cp[2], Cn[2];
   bool inb[2];
-  int clamps = 0;
-  unsigned mfx = 0, mfy = 0;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int x = tx0 + lane + 32 * j;
     inb[j] = x < W && y < H;
-    Fx[j] = 0; Fy[j] = 0; R[j] = 0; Cp[j] = p.cp; Cn[j] = p.cn;
+    R[j] = 0; Cp[j] = p.cp; Cn[j] = p.cn;
     if (inb[j]) {
       const long long i = (long long)y * W + x;
-      const float2 fl = f.flow[i];
-      Fx[j] = flow_q16(fl.x, clamps);
-      Fy[j] = flow_q16(fl.y, clamps);
       if (!RESET) R[j] = Rin[i];
       if (MAPS) { Cp[j] = p.cpmap[i]; Cn[j] = p.cnmap[i]; }
-      mfx = max(mfx, (unsigned)abs(Fx[j]));
-      mfy = max(mfy, (unsigned)abs(Fy[j]));
     }
   }
-  mfx = __reduce_max_sync(FULL, mfx);
-  mfy = __reduce_max_sync(FULL, mfy);
-  clamps = __reduce_add_sync(FULL, clamps);
-  if (tid < N) {
-    const int k = tid + 1;
-    L.swk[tid] = (k * 8192 + N) / (2 * N);
-    const long long dt = f.t_rel - tprev;
-    L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
-  }
-  for (int e = tid; e < N * TH; e += NTD) L.srow[e] = 0;
-  __syncthreads();
-  if (lane == 0) {
-    atomicMax(&s_fx, (int)mfx);
-    atomicMax(&s_fy, (int)mfy);
-    if (clamps) atomicAdd(&s_clamp, clamps);
-  }
-  __syncthreads();
-  if (tid == 0 && s_clamp) atomicAdd(&ctl->clamped, (unsigned long long)s_clamp);
-  // Reach of every tap of the tile: floor(max |F|) + 1 pixels on each side.
-  const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
-  const bool fast = hx <= HMAX && hy <= HMAX;
+  int clamps = 0;
+  bool failed = false;
 
-  if (fast) {
-    // Replicate-padded halo tiles of both log frames; the tile interior of the
-    // new frame also goes to the frame ring for the next push.  The region is
-    // walked as a flat index (row = e / ncols by a multiply-high with
-    // ceil(2^32 / ncols), exact for e < 2^16), FILL loads in flight per thread.
-    constexpr int FILL = 2;
-    const int c0 = HMAX - hx, ncols = TW + 2 * hx;
-    const int r0 = HMAX - hy, nrows = TH + 2 * hy;
-    const int total_fill = ncols * nrows;
-    const unsigned mcols = 0xFFFFFFFFu / (unsigned)ncols + 1u;
-    for (int e0 = 0; e0 < total_fill; e0 += NTD * FILL) {
-      int vp[FILL], vc[FILL], at[FILL], ring_at[FILL];
+  for (int fi = 0; fi < b.count && !failed; ++fi) {
+    const FrameDesc cur = b.frames[fi];
+    const FrameRef prv = prev_frame(p, b, fi, ringp);
+    const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
+    int Fx[2], Fy[2];
+    unsigned mfx = 0, mfy = 0;
 #pragma unroll
-      for (int q = 0; q < FILL; ++q) {
-        const int e = e0 + q * NTD + tid;
-        at[q] = -1;
-        ring_at[q] = -1;
-        if (e < total_fill) {
-          const int sr = (int)__umulhi((unsigned)e, mcols);
-          const int sc = e - sr * ncols;
-          const int ry = ty0 - hy + sr, rxx = tx0 - hx + sc;
-          const int gy = min(max(ry, 0), H - 1), gx = min(max(rxx, 0), W - 1);
-          vp[q] = ringp[(long long)gy * W + gx];
-          vc[q] = load_luma(f.frame, f.pitch, p.ch, gy, gx);
-          at[q] = (r0 + sr) * SW + (c0 + sc);
-          if (ry == gy && rxx == gx && sr >= hy && sr < hy + TH && sc >= hx && sc < hx + TW)
-            ring_at[q] = gy * W + gx;
+    for (int j = 0; j < 2; ++j) {
+      Fx[j] = 0;
+      Fy[j] = 0;
+      if (inb[j]) {
+        const float2 fl = cur.flow[(long long)y * W + tx0 + lane + 32 * j];
+        Fx[j] = flow_q16(fl.x, clamps);
+        Fy[j] = flow_q16(fl.y, clamps);
+        mfx = max(mfx, (unsigned)abs(Fx[j]));
+        mfy = max(mfy, (unsigned)abs(Fy[j]));
+      }
+    }
+    mfx = __reduce_max_sync(FULL, mfx);
+    mfy = __reduce_max_sync(FULL, mfy);
+    if (tid == 0) { s_fx = 0; s_fy = 0; }
+    if (tid < N) {
+      const int k = tid + 1;
+      L.swk[tid] = (k * 8192 + N) / (2 * N);
+      const long long dt = cur.t_rel - tprev;
+      L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
+    }
+    for (int e = tid; e < N * TH; e += NTD) L.srow[e] = 0;
+    __syncthreads();
+    if (lane == 0) {
+      atomicMax(&s_fx, (int)mfx);
+      atomicMax(&s_fy, (int)mfy);
+    }
+    __syncthreads();
+    // Reach of every tap of the tile: floor(max |F|) + 1 pixels on each side.
+    const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
+    const bool fast = hx <= HMAX && hy <= HMAX;
+    if (fast) {
+      // Replicate-padded halo tiles of both log frames.  The region is walked
+      // as a flat index (row = e / ncols by a multiply-high with
+      // ceil(2^32 / ncols), exact for e < 2^16), FILL loads in flight.
+      constexpr int FILL = 2;
+      const int c0 = HMAX - hx, ncols = TW + 2 * hx;
+      const int r0 = HMAX - hy, nrows = TH + 2 * hy;
+      const int total_fill = ncols * nrows;
+      const unsigned mcols = 0xFFFFFFFFu / (unsigned)ncols + 1u;
+      for (int e0 = 0; e0 < total_fill; e0 += NTD * FILL) {
+        int vp[FILL], vc[FILL], at[FILL];
+#pragma unroll
+        for (int q = 0; q < FILL; ++q) {
+          const int e = e0 + q * NTD + tid;
+          at[q] = -1;
+          if (e < total_fill) {
+            const int sr = (int)__umulhi((unsigned)e, mcols);
+            const int sc = e - sr * ncols;
+            const int gy = min(max(ty0 - hy + sr, 0), H - 1);
+            const int gx = min(max(tx0 - hx + sc, 0), W - 1);
+            vp[q] = load_luma(prv.ptr, prv.pitch, prv.ch, gy, gx);
+            vc[q] = load_luma(cur.frame, cur.pitch, p.ch, gy, gx);
+            at[q] = (r0 + sr) * SW + (c0 + sc);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < FILL; ++q) {
+          if (at[q] < 0) continue;
+          L.sL0[at[q]] = L.slut[vp[q]];
+          L.sL1[at[q]] = L.slut[vc[q]];
         }
       }
+    }
+    if (fi == b.count - 1) {
+      // the batch's last frame becomes the previous frame of the next batch
 #pragma unroll
-      for (int q = 0; q < FILL; ++q) {
-        if (at[q] < 0) continue;
-        L.sL0[at[q]] = L.slut[vp[q]];
-        L.sL1[at[q]] = L.slut[vc[q]];
-        if (ring_at[q] >= 0) ringn[ring_at[q]] = (unsigned char)vc[q];
+      for (int j = 0; j < 2; ++j) {
+        if (!inb[j]) continue;
+        const int x = tx0 + lane + 32 * j;
+        ringn[(long long)y * W + x] = (unsigned char)load_luma(cur.frame, cur.pitch, p.ch, y, x);
       }
     }
-  } else {
+    if (RESET) {
+      // Consecutive differences start from frame i-1 itself.
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (!inb[j]) continue;
-      const int x = tx0 + lane + 32 * j;
-      ringn[(long long)y * W + x] = (unsigned char)load_luma(f.frame, f.pitch, p.ch, y, x);
+      for (int j = 0; j < 2; ++j) {
+        if (!inb[j]) continue;
+        const int x = tx0 + lane + 32 * j;
+        R[j] = L.slut[load_luma(prv.ptr, prv.pitch, prv.ch, y, x)];
+      }
     }
-  }
-  __syncthreads();
-  if (RESET) {
-    // Consecutive differences start from frame i-1 itself.
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (!inb[j]) continue;
-      const int x = tx0 + lane + 32 * j;
-      R[j] = L.slut[ringp[(long long)y * W + x]];
+    __syncthreads();
+
+    if (fast)
+      dense_substeps<RESET, WIDE, true>(p, L, N, tx0, ty0, prv, cur, Fx, Fy, R, Cp, Cn, inb);
+    else
+      dense_substeps<RESET, WIDE, false>(p, L, N, tx0, ty0, prv, cur, Fx, Fy, R, Cp, Cn, inb);
+    __syncthreads();
+
+    // Tile-local offsets of the (substep, row) segments, substep-major.
+    const int E = N * TH;
+    int total;
+    const long long base = stage_segments<NTD>(p, L.srow, L.soff, E, s_warp, &s_base, &total);
+    const bool fail = base < 0;
+    int2* segf = p.seg + (long long)fi * nmax * p.segs_per_k;
+    for (int e = tid; e < E; e += NTD) {
+      const int k = e / TH, ty = e % TH, yy = ty0 + ty;
+      if (yy < H)
+        segf[(long long)k * p.segs_per_k + (long long)yy * p.tiles_x + tcx] =
+            make_int2(fail ? 0 : L.srow[e], (int)(fail ? 0 : base) + L.soff[e]);
     }
+    if (!fail && total > 0) {
+      // Emission: each warp writes the events of its row, substep by substep.
+      const unsigned lt = lanemask_lt();
+      for (int k = 0; k < N; ++k) {
+        const int e = k * TH + warp;
+        if (L.srow[e] == 0) continue;
+        const unsigned tk = L.stk[k];
+        const long long o = base + L.soff[e];
+        const int na = L.snk[e * TW + lane], nb = L.snk[e * TW + lane + 32];
+        const int aa = abs(na), ab = abs(nb);
+        const int xa = tx0 + lane, xb = tx0 + lane + 32;
+        if (__all_sync(FULL, (aa | ab) <= 1)) {
+          const unsigned ba = __ballot_sync(FULL, aa != 0), bb = __ballot_sync(FULL, ab != 0);
+          if (aa) p.staging[o + __popc(ba & lt)] = make_event(tk, xa, y, na > 0);
+          if (ab) p.staging[o + __popc(ba) + __popc(bb & lt)] = make_event(tk, xb, y, nb > 0);
+        } else {
+          const int ia = warp_incl_scan(aa);
+          const int ta = __shfl_sync(FULL, ia, 31);
+          const int ib = warp_incl_scan(ab);
+          const Ev ea = make_event(tk, xa, y, na > 0), eb = make_event(tk, xb, y, nb > 0);
+          const long long oa = o + ia - aa, ob = o + ta + ib - ab;
+          for (int m = 0; m < aa; ++m) p.staging[oa + m] = ea;
+          for (int m = 0; m < ab; ++m) p.staging[ob + m] = eb;
+        }
+      }
+    }
+    failed = fail;
+    tprev = cur.t_rel;
+    __syncthreads();
   }
 
-  if (fast)
-    dense_substeps<RESET, WIDE, true>(p, f, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
-  else
-    dense_substeps<RESET, WIDE, false>(p, f, L, N, tx0, ty0, Fx, Fy, R, Cp, Cn, inb, ringp);
-
-  if (!RESET) {
+  if (!RESET && !failed) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       if (!inb[j]) continue;
@@ -592,87 +671,46 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, FrameArg fa) {
       Rout[(long long)y * W + x] = R[j];
     }
   }
-  __syncthreads();
-
-  // Tile-local offsets of the (substep, row) segments, substep-major.
-  const int E = N * TH;
-  int total;
-  const int base = stage_segments<NTD>(p, L.srow, L.soff, E, s_warp, &s_base, &total);
-  const bool fail = base < 0;
-  for (int e = tid; e < E; e += NTD) {
-    const int k = e / TH, ty = e % TH, yy = ty0 + ty;
-    if (yy < H)
-      p.seg[((long long)k * H + yy) * p.tiles_x + tcx] =
-          make_int2(fail ? 0 : L.srow[e], (fail ? 0 : base) + L.soff[e]);
-  }
-  if (fail || total == 0) return;
-
-  // Emission: each warp writes the events of its row, substep by substep.
-  const unsigned lt = lanemask_lt();
-  for (int k = 0; k < N; ++k) {
-    const int e = k * TH + warp;
-    if (L.srow[e] == 0) continue;
-    const unsigned tk = L.stk[k];
-    const unsigned o = (unsigned)base + (unsigned)L.soff[e];
-    const int na = L.snk[e * TW + lane], nb = L.snk[e * TW + lane + 32];
-    const int aa = abs(na), ab = abs(nb);
-    const int xa = tx0 + lane, xb = tx0 + lane + 32;
-    if (__all_sync(FULL, (aa | ab) <= 1)) {
-      const unsigned ba = __ballot_sync(FULL, aa != 0), bb = __ballot_sync(FULL, ab != 0);
-      if (aa) p.staging[o + __popc(ba & lt)] = make_event(tk, xa, y, na > 0);
-      if (ab) p.staging[o + __popc(ba) + __popc(bb & lt)] = make_event(tk, xb, y, nb > 0);
-    } else {
-      const int ia = warp_incl_scan(aa);
-      const int ta = __shfl_sync(FULL, ia, 31);
-      const int ib = warp_incl_scan(ab);
-      const Ev ea = make_event(tk, xa, y, na > 0), eb = make_event(tk, xb, y, nb > 0);
-      const unsigned oa = o + ia - aa, ob = o + ta + ib - ab;
-      for (int m = 0; m < aa; ++m) p.staging[oa + m] = ea;
-      for (int m = 0; m < ab; ++m) p.staging[ob + m] = eb;
-    }
-  }
+  clamps = __reduce_add_sync(FULL, clamps);
+  if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
 }
 
 // ---------------------------------------------------------------------------
-// sparse (Sec. III-B): per chunk of SCHUNK raster pixels, find the active
-// pixels (|L_i - L_{i-1}| >= C_act), compact them in raster order and
-// simulate only those.  Segments are (substep, chunk).
+// sparse (Sec. III-B): one block per chunk of SCHUNK raster pixels runs the
+// chunk through every frame of the batch.  Per frame it finds the active
+// pixels (|L_i - L_{i-1}| >= C_act), compacts them in raster order and
+// simulates only those; the chunk's reference stays in shared memory across
+// the batch.  Segments are (frame, substep, chunk).
 
-// Activity test of one pixel; also returns the two luma values.
-__device__ __forceinline__ bool pixel_active(const SimParams& p, const FrameDesc& f,
-                                             const int* slut, const unsigned char* ringp,
-                                             long long i, int& vc) {
-  const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
-  const int vp = ringp[i];
-  vc = load_luma(f.frame, f.pitch, p.ch, y, x);
-  const int d = abs(slut[vc] - slut[vp]);
-  int ca = p.cact;
-  if (ca < 0) {
-    const int a = p.cpmap ? p.cpmap[i] : p.cp;
-    const int b = p.cnmap ? p.cnmap[i] : p.cn;
-    ca = min(a, b);
-  }
-  return d >= ca;
+__device__ __forceinline__ int activity_threshold(const SimParams& p, int cp, int cn) {
+  return p.cact >= 0 ? p.cact : min(cp, cn);
 }
 
-// Adaptive N for the sparse method: max squared flow over active pixels.
-__global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, FrameArg fa) {
+// Adaptive N for the sparse method: max squared flow over the active pixels
+// of each frame (blockIdx.y = frame).
+__global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, BatchArg b) {
   __shared__ int slut[256];
   __shared__ unsigned long long s_m[NWARP];
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
-  const FrameDesc f = frame_of(fa);
   const int tid = threadIdx.x;
+  const int fi = blockIdx.y;
   slut[tid] = p.lut[tid];
   __syncthreads();
   const unsigned char* ringp = (ctl->sel & 2) ? p.ring1 : p.ring0;
+  const FrameDesc cur = b.frames[fi];
+  const FrameRef prv = prev_frame(p, b, fi, ringp);
   const long long P = (long long)p.W * p.H;
   unsigned long long m = 0;
   int dummy = 0;
   for (long long i = blockIdx.x * (long long)NT + tid; i < P; i += (long long)gridDim.x * NT) {
-    int vc;
-    if (pixel_active(p, f, slut, ringp, i, vc)) {
-      const float2 fl = f.flow[i];
+    const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
+    const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
+    const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
+    const int cp = p.cpmap ? p.cpmap[i] : p.cp;
+    const int cn = p.cnmap ? p.cnmap[i] : p.cn;
+    if (abs(slut[vc] - slut[vp]) >= activity_threshold(p, cp, cn)) {
+      const float2 fl = cur.flow[i];
       const long long fx = flow_q16(fl.x, dummy), fy = flow_q16(fl.y, dummy);
       const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
       m = f2 > m ? f2 : m;
@@ -682,21 +720,21 @@ __global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, FrameArg fa) {
   if ((tid & 31) == 0) s_m[tid >> 5] = m;
   __syncthreads();
   if (tid == 0) {
-    unsigned long long b = 0;
-    for (int w = 0; w < NWARP; ++w) b = s_m[w] > b ? s_m[w] : b;
-    if (b) atomicMax(&ctl->maxf2, b);
+    unsigned long long bm = 0;
+    for (int w = 0; w < NWARP; ++w) bm = s_m[w] > bm ? s_m[w] : bm;
+    if (bm) atomicMax(&p.maxf2[fi], bm);
   }
 }
 
 template <bool RESET, bool MAPS, bool WIDE>
-__global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
+__global__ void __launch_bounds__(NT) k_sparse(SimParams p, BatchArg b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NWARP + 1];
-  __shared__ int s_base, s_clamp, s_active;
-  __shared__ int sidx[SCHUNK];
+  __shared__ long long s_base;
+  __shared__ int sidx[SCHUNK];   // active pixels of the chunk (chunk-local index)
+  __shared__ int sR[SCHUNK];     // the chunk's reference
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
-  const FrameDesc f = frame_of(fa);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
   int* slut = (int*)smem_raw;
@@ -704,53 +742,74 @@ __global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
   unsigned* stk = (unsigned*)(swk + nmax);
   int* scnt = (int*)(stk + nmax);            // [N][SROUNDS][NWARP] counts
   int* soff = scnt + nmax * SROUNDS * NWARP; // [N][SROUNDS][NWARP] chunk-local offsets
-  int* skt = soff + nmax * SROUNDS * NWARP;  // [N] events per substep in the chunk
-  short* snk = (short*)(skt + nmax);         // [N][SCHUNK]
+  short* snk = (short*)(soff + nmax * SROUNDS * NWARP);  // [N][SCHUNK]
+  unsigned short* sCp = (unsigned short*)(snk + nmax * SCHUNK);  // [SCHUNK] (maps)
+  unsigned short* sCn = sCp + SCHUNK;
 
   slut[tid] = p.lut[tid];
-  if (tid == 0) { s_clamp = 0; s_active = 0; }
   const long long P = (long long)p.W * p.H;
-  const int S = (int)((P + SCHUNK - 1) / SCHUNK);
-  const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(ctl->maxf2, nmax);
-  if (blockIdx.x == 0 && tid == 0) ctl->n_frame = N;
+  const int S = (int)p.segs_per_k;
+  const int c = blockIdx.x;
+  const long long cbase = (long long)c * SCHUNK;
+  const int W = p.W, H = p.H;
   const int sel = ctl->sel;
+  const int* Rin = (sel & 1) ? p.R1 : p.R0;
+  int* Rout = (sel & 1) ? p.R0 : p.R1;
   const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
   unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
-  const long long tprev = ctl->t_prev;
-  if (tid < N) {
-    const int k = tid + 1;
-    swk[tid] = (k * 8192 + N) / (2 * N);
-    const long long dt = f.t_rel - tprev;
-    stk[tid] = (unsigned)(tprev + (k * dt) / N);
+  long long tprev = ctl->t_prev;
+  for (int q = tid; q < SCHUNK; q += NT) {
+    const long long i = cbase + q;
+    if (i < P) {
+      if (!RESET) sR[q] = Rin[i];
+      if (MAPS) { sCp[q] = p.cpmap[i]; sCn[q] = p.cnmap[i]; }
+    }
   }
-  const int W = p.W, H = p.H;
   const unsigned lt = lanemask_lt();
-  const int ESEG = N * SROUNDS * NWARP;
-  int clamps = 0, active_total = 0;
-  __syncthreads();
+  int clamps = 0;
+  long long act_sum = 0, act_n = 0;
+  bool failed = false;
 
-  for (int c = blockIdx.x; c < S; c += gridDim.x) {
+  for (int fi = 0; fi < b.count && !failed; ++fi) {
+    const FrameDesc cur = b.frames[fi];
+    const FrameRef prv = prev_frame(p, b, fi, ringp);
+    const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
+    const int ESEG = N * SROUNDS * NWARP;
+    if (tid < N) {
+      const int k = tid + 1;
+      swk[tid] = (k * 8192 + N) / (2 * N);
+      const long long dt = cur.t_rel - tprev;
+      stk[tid] = (unsigned)(tprev + (k * dt) / N);
+    }
+    for (int e = tid; e < ESEG; e += NT) scnt[e] = 0;
+    __syncthreads();
+
     // 1. activity of the chunk's pixels, compacted in raster order
-    const long long i0 = (long long)c * SCHUNK + SROUNDS * tid;
     unsigned flags = 0;
     int cnt = 0;
 #pragma unroll
     for (int q = 0; q < SROUNDS; ++q) {
-      const long long i = i0 + q;
+      const int li = SROUNDS * tid + q;
+      const long long i = cbase + li;
       if (i < P) {
-        int vc;
-        if (pixel_active(p, f, slut, ringp, i, vc)) { flags |= 1u << q; ++cnt; }
-        ringn[i] = (unsigned char)vc;
+        const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+        const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
+        const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
+        const int cp = MAPS ? (int)sCp[li] : p.cp, cn = MAPS ? (int)sCn[li] : p.cn;
+        if (abs(slut[vc] - slut[vp]) >= activity_threshold(p, cp, cn)) {
+          flags |= 1u << q;
+          ++cnt;
+        }
+        if (fi == b.count - 1) ringn[i] = (unsigned char)vc;
       }
     }
-    for (int e = tid; e < ESEG; e += NT) scnt[e] = 0;
     int A;
     int o = block_excl_scan(cnt, s_warp, &A);
 #pragma unroll
     for (int q = 0; q < SROUNDS; ++q)
-      if (flags & (1u << q)) sidx[o++] = (int)(i0 + q);
-    if (tid == 0) p.chunk_active[c] = A;
-    active_total += A;
+      if (flags & (1u << q)) sidx[o++] = SROUNDS * tid + q;
+    act_sum += A;
+    act_n += (long long)A * N;
     __syncthreads();
 
     // 2. simulate the active pixels, NT at a time (round r: pixels r NT + tid)
@@ -758,21 +817,16 @@ __global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
     for (int r = 0; r < rounds; ++r) {
       const int j = r * NT + tid;
       const bool act = j < A;
-      const int i = act ? sidx[j] : 0;
-      const int y = i / W, x = i - y * W;
+      const int li = act ? sidx[j] : 0;
+      const long long i = cbase + li;
+      const int y = (int)(i / W), x = (int)(i - (long long)y * W);
       int Fx = 0, Fy = 0, R = 0, cp = p.cp, cn = p.cn;
       if (act) {
-        const float2 fl = f.flow[i];
+        const float2 fl = cur.flow[i];
         Fx = flow_q16(fl.x, clamps);
         Fy = flow_q16(fl.y, clamps);
-        if (MAPS) { cp = p.cpmap[i]; cn = p.cnmap[i]; }
-        if (RESET) {
-          R = slut[ringp[i]];
-        } else {
-          R = p.R0[i];
-          p.Rsave[(long long)c * SCHUNK + j] = R;
-          p.idx[(long long)c * SCHUNK + j] = i;
-        }
+        if (MAPS) { cp = sCp[li]; cn = sCn[li]; }
+        R = RESET ? slut[load_luma(prv.ptr, prv.pitch, prv.ch, y, x)] : sR[li];
       }
       int qx = Fx / N, rx = Fx - qx * N;
       if (rx < 0) { rx += N; qx -= 1; }
@@ -786,8 +840,8 @@ __global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
         py -= qy;
         ay += ry;
         if (ay >= N) { ay -= N; py -= 1; }
-        const int s0 = tap_global<WIDE>(ringp, W, 1, W, H, slut, px, py);
-        const int s1 = tap_global<WIDE>(f.frame, f.pitch, p.ch, W, H, slut, px + Fx, py + Fy);
+        const int s0 = tap_global<WIDE>(prv.ptr, prv.pitch, prv.ch, W, H, slut, px, py);
+        const int s1 = tap_global<WIDE>(cur.frame, cur.pitch, p.ch, W, H, slut, px + Fx, py + Fy);
         const int I = lerp12<WIDE>(s0, s1, swk[k]);
         int n = threshold_step<RESET>(I, R, cp, cn);
         if (!act) n = 0;
@@ -797,18 +851,19 @@ __global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
           if (lane == 0) scnt[(k * SROUNDS + r) * NWARP + warp] = cw;
         }
       }
-      if (!RESET && act) p.R0[i] = R;
+      if (!RESET && act) sR[li] = R;
     }
     __syncthreads();
 
     // 3. chunk-local offsets in (substep, round, warp) order, staging, segments
     int total;
-    const int base = stage_segments(p, scnt, soff, ESEG, s_warp, &s_base, &total);
+    const long long base = stage_segments(p, scnt, soff, ESEG, s_warp, &s_base, &total);
     const bool fail = base < 0;
+    int2* segf = p.seg + (long long)fi * nmax * S;
     if (tid < N) {
       const int e0 = tid * SROUNDS * NWARP;
       const int kt = soff[e0 + SROUNDS * NWARP - 1] + scnt[e0 + SROUNDS * NWARP - 1] - soff[e0];
-      p.seg[(long long)tid * S + c] = make_int2(fail ? 0 : kt, (fail ? 0 : base) + soff[e0]);
+      segf[(long long)tid * S + c] = make_int2(fail ? 0 : kt, (int)(fail ? 0 : base) + soff[e0]);
     }
     if (!fail && total > 0) {
       for (int k = 0; k < N; ++k) {
@@ -818,13 +873,13 @@ __global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
           const int j = r * NT + tid;
           const int n = j < A ? snk[k * SCHUNK + j] : 0;
           const int a = abs(n);
-          const int i = j < A ? sidx[j] : 0;
-          const int y = i / W, x = i - y * W;
-          const unsigned oo = (unsigned)base + (unsigned)soff[e];
+          const long long i = cbase + (j < A ? sidx[j] : 0);
+          const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+          const long long oo = base + soff[e];
           const Ev ev = make_event(stk[k], x, y, n > 0);
           if (__all_sync(FULL, a <= 1)) {
-            const unsigned b = __ballot_sync(FULL, a != 0);
-            if (a) p.staging[oo + __popc(b & lt)] = ev;
+            const unsigned bb = __ballot_sync(FULL, a != 0);
+            if (a) p.staging[oo + __popc(bb & lt)] = ev;
           } else {
             const int ia = warp_incl_scan(a);
             for (int m = 0; m < a; ++m) p.staging[oo + ia - a + m] = ev;
@@ -832,57 +887,83 @@ __global__ void __launch_bounds__(NT) k_sparse(SimParams p, FrameArg fa) {
         }
       }
     }
+    failed = fail;
+    tprev = cur.t_rel;
     __syncthreads();
   }
+
+  if (!RESET && !failed) {
+    for (int q = tid; q < SCHUNK; q += NT) {
+      const long long i = cbase + q;
+      if (i < P) Rout[i] = sR[q];
+    }
+  }
   clamps = __reduce_add_sync(FULL, clamps);
-  if (lane == 0 && clamps) atomicAdd(&s_clamp, clamps);
-  if (tid == 0 && active_total) atomicAdd(&s_active, active_total);
-  __syncthreads();
-  if (tid == 0) {
-    if (s_clamp) atomicAdd(&ctl->clamped, (unsigned long long)s_clamp);
-    if (s_active) atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)s_active);
+  if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
+  if (tid == 0 && act_sum) {
+    atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)act_sum);
+    atomicAdd((unsigned long long*)&ctl->active_n, (unsigned long long)act_n);
   }
 }
 
 // ---------------------------------------------------------------------------
-// order: scan segment counts in output order, gather events, commit the frame
+// order: scan the segment counts of the whole batch in output order (frame,
+// substep, segment), gather the events from staging into the event buffer,
+// and commit the batch (all of its frames, or none).
 
-__global__ void __launch_bounds__(NT) k_order(SimParams p, FrameArg fa) {
+__global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
   __shared__ int s_ex[OCHUNK];
   __shared__ int s_src[OCHUNK];
+  __shared__ int s_N[1024];
   __shared__ int s_warp[NWARP + 1];
   __shared__ int s_c, s_last, s_ok;
   __shared__ long long s_prefix;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
-  const FrameDesc f = frame_of(fa);
   const int tid = threadIdx.x;
-  const int N = ctl->n_frame;
-  const bool sparse = p.mode == SIM_SPARSE;
-  const long long P = (long long)p.W * p.H;
-  const long long S = sparse ? (P + SCHUNK - 1) / SCHUNK : (long long)p.H * p.tiles_x;
-  const long long nseg = (long long)N * S;
+  const int nmax = p.n_max;
+  for (int i = tid; i < b.count; i += NT)
+    s_N[i] = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[i], nmax);
+  const long long S = p.segs_per_k;
+  const long long per_frame = (long long)nmax * S;
+  const long long nseg = (long long)b.count * per_frame;
   const int nchunks = (int)max(1LL, (nseg + OCHUNK - 1) / OCHUNK);
   const long long cursor = ctl->cursor;
+  __syncthreads();
 
   for (;;) {
     if (tid == 0) s_c = (int)atomicAdd(&ctl->order_ticket, 1u);
     __syncthreads();
     const int c = s_c;
     if (c >= nchunks) break;
-    const long long si = (long long)c * OCHUNK + tid;
-    int cnt = 0, src = 0;
-    if (si < nseg) {
-      const int2 e = p.seg[si];
-      cnt = e.x;
-      src = e.y;
+    // four consecutive segments per thread; segments of substeps k >= N of
+    // their frame were never written and count zero
+    const long long s0 = (long long)c * OCHUNK + OPER * tid;
+    long long fi = s0 / per_frame;
+    long long rem = s0 - fi * per_frame;
+    int cnt[OPER], src[OPER], sum = 0;
+#pragma unroll
+    for (int q = 0; q < OPER; ++q) {
+      cnt[q] = 0;
+      src[q] = 0;
+      if (s0 + q < nseg && rem / S < s_N[fi]) {
+        const int2 e = p.seg[s0 + q];
+        cnt[q] = e.x;
+        src[q] = e.y;
+      }
+      sum += cnt[q];
+      if (++rem == per_frame) { rem = 0; ++fi; }
     }
     int total;
-    const int ex = block_excl_scan(cnt, s_warp, &total);
-    s_ex[tid] = ex;
-    s_src[tid] = src;
+    int ex = block_excl_scan(sum, s_warp, &total);
+#pragma unroll
+    for (int q = 0; q < OPER; ++q) {
+      s_ex[OPER * tid + q] = ex;
+      s_src[OPER * tid + q] = src[q];
+      ex += cnt[q];
+    }
     if (tid < 32) {
-      const long long ex0 = lookback_warp(p.order_status, c, f.serial, total, &ctl->err);
+      const long long ex0 = lookback_warp(p.order_status, c, b.serial, total, &ctl->err);
       if (tid == 0) s_prefix = ex0;
     }
     __syncthreads();
@@ -894,7 +975,7 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, FrameArg fa) {
         if (s_ex[mid] <= jj) lo = mid; else hi = mid;
       }
       const long long dst = base + jj;
-      if (dst < p.event_cap) p.events[dst] = p.staging[s_src[lo] + (jj - s_ex[lo])];
+      if (dst < p.event_cap) p.events[dst] = p.staging[(long long)s_src[lo] + (jj - s_ex[lo])];
     }
     __syncthreads();
     if (tid == 0) {
@@ -904,49 +985,41 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, FrameArg fa) {
     }
     __syncthreads();
     if (s_last) {
-      // This block finished the frame's last chunk: commit or fail the frame.
+      // This block finished the batch's last chunk: commit or fail the batch.
       if (tid == 0) {
         __threadfence();
         const unsigned long long w = ld_volatile(&p.order_status[nchunks - 1]);
         const long long tot = (long long)(w & LB_VALUE);
-        const bool over = ctl->frame_fail != 0 || tot >= (long long)LB_VALUE ||
+        const bool over = ctl->batch_fail != 0 || tot >= (long long)LB_VALUE ||
                           cursor + tot > p.event_cap;
         int ok = 0;
         if (ld_volatile(&ctl->err) == 0) {
           if (over) {
             atomicCAS(&ctl->err, 0, SIM_ERR_EVENT_OVERFLOW);
           } else {
-            int flip = 2;
-            if (!sparse && p.ref_mode == SIM_REF_ACCUM) flip |= 1;
+            const long long P = (long long)p.W * p.H;
+            long long nsum = 0;
+            for (int i = 0; i < b.count; ++i) nsum += s_N[i];
             ctl->cursor = cursor + tot;
-            ctl->sel ^= flip;
-            ctl->t_prev = f.t_rel;
-            ctl->committed += 1;
-            ctl->frame_events = tot;
-            ctl->work_px += P * N;
-            ctl->work_active += (sparse ? ctl->active : P) * N;
+            ctl->sel ^= p.ref_mode == SIM_REF_ACCUM ? 3 : 2;
+            ctl->t_prev = b.frames[b.count - 1].t_rel;
+            ctl->committed += b.count;
+            ctl->batch_events = tot;
+            ctl->last_n = s_N[b.count - 1];
+            ctl->work_px += P * nsum;
+            ctl->work_active += p.mode == SIM_SPARSE ? ctl->active_n : P * nsum;
+            ctl->last_active = p.mode == SIM_SPARSE ? ctl->active : P * b.count;
             ok = 1;
           }
         }
-        ctl->last_active = ctl->active;
         ctl->active = 0;
+        ctl->active_n = 0;
         ctl->stage_top = 0;
         ctl->order_done = 0;
-        ctl->maxf2 = 0;
-        ctl->frame_fail = 0;
+        ctl->batch_fail = 0;
         s_ok = ok;
       }
-      __syncthreads();
-      if (!s_ok && sparse && p.ref_mode == SIM_REF_ACCUM) {
-        // Roll back the in-place reference of the active pixels.
-        for (int c2 = 0; c2 < (int)S; ++c2) {
-          const int A = p.chunk_active[c2];
-          for (int j = tid; j < A; j += NT) {
-            const long long slot = (long long)c2 * SCHUNK + j;
-            p.R0[p.idx[slot]] = p.Rsave[slot];
-          }
-        }
-      }
+      for (int i = tid; i < b.count; i += NT) p.maxf2[i] = 0;
     }
     __syncthreads();
   }
@@ -979,8 +1052,8 @@ size_t dense_smem_bytes(int n_max) {
 }
 
 size_t sparse_smem_bytes(int n_max) {
-  return (size_t)(256 + 2 * n_max + 2 * n_max * SROUNDS * NWARP + n_max) * 4 +
-         (size_t)n_max * SCHUNK * 2;
+  return (size_t)(256 + 2 * n_max + 2 * n_max * SROUNDS * NWARP) * 4 +
+         (size_t)n_max * SCHUNK * 2 + (size_t)2 * SCHUNK * 2;
 }
 
 int device_sm_count() {
@@ -1011,28 +1084,29 @@ cudaError_t configure_kernels(int n_max) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_init(const SimParams& p, const FrameArg& f, cudaStream_t st) {
+cudaError_t launch_init(const SimParams& p, const FrameDesc& f, cudaStream_t st) {
   const long long P = (long long)p.W * p.H;
   const int grid = (int)std::min<long long>((P + NT - 1) / NT, 4096);
   k_init<<<grid, NT, 0, st>>>(p, f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_flowmax(const SimParams& p, const FrameArg& f, cudaStream_t st) {
+cudaError_t launch_flowmax(const SimParams& p, const BatchArg& b, cudaStream_t st) {
   const long long P = (long long)p.W * p.H;
   const int sms = device_sm_count();
-  const int grid = (int)std::max(1LL, std::min<long long>((P + NT * 8 - 1) / (NT * 8), (long long)sms * 4));
-  k_flowmax<<<grid, NT, 0, st>>>(p, f);
+  const long long per_frame = std::max(1LL, (long long)sms * 4 / std::max(1, b.count));
+  const int gx = (int)std::max(1LL, std::min<long long>((P + NT * 8 - 1) / (NT * 8), per_frame));
+  k_flowmax<<<dim3(gx, b.count), NT, 0, st>>>(p, b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense(const SimParams& p, const FrameArg& f, cudaStream_t st) {
+cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st) {
   const int grid = p.tiles_x * p.tiles_y;
   const size_t sm = dense_smem_bytes(p.n_max);
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NTD, sm, st>>>(p, f)
+#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NTD, sm, st>>>(p, b)
   if (!reset && !maps && !wide) EVSIM_DENSE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_DENSE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_DENSE(false, false, true);
@@ -1045,17 +1119,22 @@ cudaError_t launch_dense(const SimParams& p, const FrameArg& f, cudaStream_t st)
   return cudaGetLastError();
 }
 
-cudaError_t launch_sparse_pre(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid) {
-  k_sparse_pre<<<grid, NT, 0, st>>>(p, f);
+cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  const long long P = (long long)p.W * p.H;
+  const int sms = device_sm_count();
+  const long long per_frame = std::max(1LL, (long long)sms * 4 / std::max(1, b.count));
+  const int gx = (int)std::max(1LL, std::min<long long>((P + NT - 1) / NT, per_frame));
+  k_sparse_pre<<<dim3(gx, b.count), NT, 0, st>>>(p, b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sparse(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid) {
+cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  const int grid = (int)p.segs_per_k;  // one block per raster chunk
   const size_t sm = sparse_smem_bytes(p.n_max);
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_SPARSE(R, M, Wd) k_sparse<R, M, Wd><<<grid, NT, sm, st>>>(p, f)
+#define EVSIM_SPARSE(R, M, Wd) k_sparse<R, M, Wd><<<grid, NT, sm, st>>>(p, b)
   if (!reset && !maps && !wide) EVSIM_SPARSE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_SPARSE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_SPARSE(false, false, true);
@@ -1068,8 +1147,8 @@ cudaError_t launch_sparse(const SimParams& p, const FrameArg& f, cudaStream_t st
   return cudaGetLastError();
 }
 
-cudaError_t launch_order(const SimParams& p, const FrameArg& f, cudaStream_t st, int grid) {
-  k_order<<<grid, NT, 0, st>>>(p, f);
+cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid) {
+  k_order<<<grid, NT, 0, st>>>(p, b);
   return cudaGetLastError();
 }
 

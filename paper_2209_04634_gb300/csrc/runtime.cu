@@ -1,14 +1,13 @@
 // Host runtime and C ABI of the evsim library: handle state, device
-// allocation, per-push launch sequence, event pop, error recovery, profiling.
+// allocation, the per-batch launch sequence, event pop, error recovery and
+// per-kernel profiling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -22,12 +21,6 @@ using evsim::Ev;
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
-  bool graph_owned;  // event pair recorded by a node of a cached graph
-};
-
-struct GraphEntry {
-  cudaGraphExec_t exec = nullptr;
-  std::vector<ProfRec> recs;  // profiled graphs: the event pairs of their kernels
 };
 
 struct sim_s {
@@ -46,26 +39,20 @@ struct sim_s {
   unsigned short* d_cnmap = nullptr;
   unsigned char* d_ring[2] = {nullptr, nullptr};
   int* d_R[2] = {nullptr, nullptr};
-  int* d_Rsave = nullptr;
   Ctl* d_ctl = nullptr;
+  unsigned long long* d_maxf2 = nullptr;
   Ev* d_staging = nullptr;
   Ev* d_events = nullptr;
   int2* d_seg = nullptr;
   unsigned long long* d_order_status = nullptr;
-  int* d_idx = nullptr;
-  int* d_chunk_active = nullptr;
-  unsigned char* d_frame_stage = nullptr;
-  float2* d_flow_stage = nullptr;
-  evsim::FrameDesc* d_desc = nullptr;       // SIM_MAX_BATCH descriptors (graph replays)
-  unsigned char* d_batch_frames = nullptr;  // host batches: staged frames
-  float2* d_batch_flows = nullptr;
-  long long batch_stage_frames = 0;         // frames the batch staging holds
+  evsim::FrameDesc* d_desc = nullptr;       // bmax descriptors of the batch in flight
+  unsigned char* d_stage_frames = nullptr;  // host batches: staged frames and flows
+  float2* d_stage_flows = nullptr;
+  long long stage_frames = 0;               // frames the host staging holds
   long long event_cap = 0;
-  unsigned stage_cap = 0;
-  long long seg_cap = 0;
-  int order_grid = 1, pre_grid = 1, sparse_grid = 1;
-  bool use_graphs = true;
-  std::map<std::pair<int, bool>, GraphEntry> graphs;  // (batch length, profiled) -> graph
+  long long segs_per_k = 0;
+  int bmax = 1;
+  int order_grid = 1;
 
   // host shadow of the stream
   bool have_first = false;
@@ -86,6 +73,7 @@ namespace {
 
 std::mutex g_attr_mu;
 int g_attr_nmax = 0;
+thread_local cudaError_t g_last_cuda = cudaSuccess;
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -111,28 +99,16 @@ void free_all(sim_t* s) {
   cudaFree(s->d_ring[1]);
   cudaFree(s->d_R[0]);
   cudaFree(s->d_R[1]);
-  cudaFree(s->d_Rsave);
   cudaFree(s->d_ctl);
+  cudaFree(s->d_maxf2);
   cudaFree(s->d_staging);
   cudaFree(s->d_events);
   cudaFree(s->d_seg);
   cudaFree(s->d_order_status);
-  cudaFree(s->d_idx);
-  cudaFree(s->d_chunk_active);
-  cudaFree(s->d_frame_stage);
-  cudaFree(s->d_flow_stage);
   cudaFree(s->d_desc);
-  cudaFree(s->d_batch_frames);
-  cudaFree(s->d_batch_flows);
-  for (auto& g : s->graphs) {
-    cudaGraphExecDestroy(g.second.exec);
-    for (auto& r : g.second.recs) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
-    }
-  }
+  cudaFree(s->d_stage_frames);
+  cudaFree(s->d_stage_flows);
   for (auto& r : s->pending) {
-    if (r.graph_owned) continue;
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
@@ -155,6 +131,7 @@ evsim::SimParams make_params(const sim_t* s) {
   p.cp = s->cfg.c_pos_q16;
   p.cn = s->cfg.c_neg_q16;
   p.cact = s->cfg.c_act_q16;
+  p.bmax = s->bmax;
   p.cpmap = s->d_cpmap;
   p.cnmap = s->d_cnmap;
   p.lut = s->d_lut;
@@ -162,36 +139,17 @@ evsim::SimParams make_params(const sim_t* s) {
   p.ring1 = s->d_ring[1];
   p.R0 = s->d_R[0];
   p.R1 = s->d_R[1];
-  p.Rsave = s->d_Rsave;
   p.ctl = s->d_ctl;
+  p.maxf2 = s->d_maxf2;
   p.staging = s->d_staging;
-  p.stage_cap = s->stage_cap;
+  p.stage_cap = s->event_cap;
   p.seg = s->d_seg;
+  p.segs_per_k = s->segs_per_k;
   p.order_status = s->d_order_status;
   p.events = s->d_events;
   p.event_cap = s->event_cap;
-  p.idx = s->d_idx;
-  p.chunk_active = s->d_chunk_active;
   return p;
 }
-
-thread_local cudaError_t g_last_cuda = cudaSuccess;
-
-// EVSIM_TRACE=1 in the environment prints every failing runtime call.
-bool trace_on() {
-  static const bool on = [] {
-    const char* v = std::getenv("EVSIM_TRACE");
-    return v && v[0] == '1';
-  }();
-  return on;
-}
-
-cudaError_t traced(cudaError_t e, const char* what, int line) {
-  if (e != cudaSuccess && trace_on())
-    std::fprintf(stderr, "evsim: %s (line %d) -> %s\n", what, line, cudaGetErrorString(e));
-  return e;
-}
-#define TR(x) traced((x), #x, __LINE__)
 
 int cuda_rc(cudaError_t e) {
   if (e == cudaSuccess) return SIM_OK;
@@ -217,32 +175,25 @@ cudaEvent_t pool_get(sim_t* s) {
 template <class F>
 cudaError_t timed(sim_t* s, int kind, F&& launch) {
   if (!s->prof) return launch();
-  ProfRec r{kind, pool_get(s), pool_get(s), false};
-  // Under stream capture the records must be external, so that they become
-  // event-record nodes of the graph; outside capture they are plain records.
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s->stream, &cs);
-  const unsigned fl = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0;
-  TR(cudaEventRecordWithFlags(r.a, s->stream, fl));
-  cudaError_t e = TR(launch());
-  TR(cudaEventRecordWithFlags(r.b, s->stream, fl));
+  ProfRec r{kind, pool_get(s), pool_get(s)};
+  cudaEventRecord(r.a, s->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(r.b, s->stream);
   s->pending.push_back(r);
   return e;
 }
 
 void prof_collect(sim_t* s) {
   if (s->pending.empty()) return;
-  TR(cudaStreamSynchronize(s->stream));
+  cudaStreamSynchronize(s->stream);
   for (auto& r : s->pending) {
     float ms = 0.f;
-    if (TR(cudaEventElapsedTime(&ms, r.a, r.b)) == cudaSuccess) {
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       s->prof_ms[r.kind] += ms;
       s->prof_n[r.kind] += 1;
     }
-    if (!r.graph_owned) {
-      s->pool.push_back(r.a);
-      s->pool.push_back(r.b);
-    }
+    s->pool.push_back(r.a);
+    s->pool.push_back(r.b);
   }
   s->pending.clear();
 }
@@ -255,105 +206,38 @@ int read_ctl(sim_t* s, Ctl* c) {
   return cuda_rc(e);
 }
 
-// After a device-side failure: clear the error and the per-frame scratch, and
+// After a device-side failure: clear the error and the per-batch scratch, and
 // roll the host shadow back to the last committed frame.
 int recover(sim_t* s, Ctl* c) {
   c->err = 0;
-  c->frame_fail = 0;
-  c->maxf2 = 0;
+  c->batch_fail = 0;
+  c->active = 0;
+  c->active_n = 0;
   c->stage_top = 0;
   c->order_ticket = 0;
   c->order_done = 0;
   c->order_exit = 0;
-  c->active = 0;
   s->t_last = s->t0 + c->t_prev;
   cudaError_t e = cudaMemcpy(s->d_ctl, c, sizeof(Ctl), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->d_maxf2, 0, s->bmax * sizeof(unsigned long long));
   return cuda_rc(e);
 }
 
-// Enqueue the kernels of one (non-first) frame.
-cudaError_t enqueue_frame(sim_t* s, const evsim::FrameArg& fa) {
+int push_first(sim_t* s, const void* frame, long long pitch, int64_t t_us, int32_t mem) {
+  const long long row = (long long)s->W * s->ch;
+  evsim::FrameDesc f{};
+  f.frame = (const unsigned char*)frame;
+  f.pitch = pitch;
+  cudaError_t e = cudaSuccess;
+  if (mem == SIM_HOST) {
+    e = cudaMemcpy2DAsync(s->d_stage_frames, row, frame, pitch, row, s->H, cudaMemcpyHostToDevice,
+                          s->stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    f.frame = s->d_stage_frames;
+    f.pitch = row;
+  }
   const evsim::SimParams p = make_params(s);
-  cudaError_t e;
-  const bool adaptive = s->cfg.substeps == 0;
-  if (s->cfg.mode == SIM_DENSE) {
-    if (adaptive) {
-      e = timed(s, SIM_K_FLOWMAX, [&] { return evsim::launch_flowmax(p, fa, s->stream); });
-      if (e != cudaSuccess) return e;
-    }
-    e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, fa, s->stream); });
-  } else {
-    if (adaptive) {
-      e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, fa, s->stream, s->pre_grid); });
-      if (e != cudaSuccess) return e;
-    }
-    e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, fa, s->stream, s->sparse_grid); });
-  }
-  if (e != cudaSuccess) return e;
-  return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, fa, s->stream, s->order_grid); });
-}
-
-// The replayable graph of a batch of n frames whose descriptors sit in d_desc.
-// A profiled graph also holds an event-record node before and after each
-// kernel, so kernel durations can be read without host launch gaps.
-cudaError_t batch_graph(sim_t* s, int n, GraphEntry** out) {
-  const auto key = std::make_pair(n, s->prof);
-  auto it = s->graphs.find(key);
-  if (it != s->graphs.end()) {
-    *out = &it->second;
-    return cudaSuccess;
-  }
-  prof_collect(s);  // pending must hold only this capture's event pairs
-  if (s->prof) {
-    // create the capture's events up front (4 kernels per frame at most)
-    while ((long long)s->pool.size() < 8LL * n) {
-      cudaEvent_t ev = nullptr;
-      cudaError_t ce = cudaEventCreate(&ev);
-      if (ce != cudaSuccess) return ce;
-      s->pool.push_back(ev);
-    }
-  }
-  cudaGraph_t g = nullptr;
-  cudaError_t e = TR(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-  if (e != cudaSuccess) return e;
-  cudaError_t le = cudaSuccess;
-  for (int i = 0; i < n && le == cudaSuccess; ++i) {
-    evsim::FrameArg fa{};
-    fa.ptr = s->d_desc + i;
-    le = enqueue_frame(s, fa);
-  }
-  e = TR(cudaStreamEndCapture(s->stream, &g));
-  GraphEntry entry;
-  entry.recs.swap(s->pending);
-  for (auto& r : entry.recs) r.graph_owned = true;
-  auto drop = [&]() {
-    for (auto& r : entry.recs) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
-    }
-  };
-  if (le != cudaSuccess || e != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    drop();
-    return le != cudaSuccess ? le : e;
-  }
-  e = TR(cudaGraphInstantiate(&entry.exec, g, 0));
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    drop();
-    return e;
-  }
-  auto res = s->graphs.emplace(key, std::move(entry));
-  *out = &res.first->second;
-  return cudaSuccess;
-}
-
-int push_first(sim_t* s, const unsigned char* dframe, long long pitch, int64_t t_us) {
-  const evsim::SimParams p = make_params(s);
-  evsim::FrameArg fa{};
-  fa.val.frame = dframe;
-  fa.val.pitch = pitch;
-  cudaError_t e = timed(s, SIM_K_INIT, [&] { return evsim::launch_init(p, fa, s->stream); });
+  e = timed(s, SIM_K_INIT, [&] { return evsim::launch_init(p, f, s->stream); });
   if (e != cudaSuccess) return cuda_rc(e);
   Ctl c{};
   c.committed = 1;
@@ -369,11 +253,37 @@ int push_first(sim_t* s, const unsigned char* dframe, long long pitch, int64_t t
   return SIM_OK;
 }
 
+// Enqueue one batch whose descriptors are already in d_desc.
+cudaError_t enqueue_batch(sim_t* s, int n) {
+  const evsim::SimParams p = make_params(s);
+  evsim::BatchArg b{};
+  b.frames = s->d_desc;
+  b.count = n;
+  b.serial = ++s->serial;
+  cudaError_t e;
+  const bool adaptive = s->cfg.substeps == 0;
+  if (s->cfg.mode == SIM_DENSE) {
+    if (adaptive) {
+      e = timed(s, SIM_K_FLOWMAX, [&] { return evsim::launch_flowmax(p, b, s->stream); });
+      if (e != cudaSuccess) return e;
+    }
+    e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, b, s->stream); });
+  } else {
+    if (adaptive) {
+      e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, b, s->stream); });
+      if (e != cudaSuccess) return e;
+    }
+    e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, b, s->stream); });
+  }
+  if (e != cudaSuccess) return e;
+  return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, b, s->stream, s->order_grid); });
+}
+
 }  // namespace
 
 extern "C" {
 
-const char* sim_version(void) { return "0.1.0"; }
+const char* sim_version(void) { return "0.2.0"; }
 
 const char* sim_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
 
@@ -386,7 +296,7 @@ const char* sim_strerror(int code) {
     case SIM_ERR_OOM: return "out of memory";
     case SIM_ERR_TIME: return "timestamp not strictly increasing";
     case SIM_ERR_TIME_RANGE: return "timestamp more than 2^32-1 us after the first frame";
-    case SIM_ERR_EVENT_OVERFLOW: return "event buffer overflow; frame not committed";
+    case SIM_ERR_EVENT_OVERFLOW: return "event buffer overflow; batch not committed";
     case SIM_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
     case SIM_ERR_STATE: return "call not valid in this state";
     case SIM_ERR_ADMIT: return "admission refused";
@@ -422,7 +332,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   if (c.ref_mode != SIM_REF_ACCUM && c.ref_mode != SIM_REF_RESET) return SIM_ERR_ARG;
   if (c.substeps < 0 || c.substeps > SIM_MAX_SUBSTEPS) return SIM_ERR_ARG;
   if (c.substeps == 0 && (c.max_substeps < 1 || c.max_substeps > SIM_MAX_SUBSTEPS)) return SIM_ERR_ARG;
-  if (c.event_capacity < 0 || c.event_capacity > evsim::MAX_EVENTS_PER_FRAME - 1) return SIM_ERR_ARG;
+  if (c.event_capacity < 0 || c.event_capacity > evsim::MAX_EVENTS) return SIM_ERR_ARG;
+  if (c.max_batch < 0 || c.max_batch > SIM_MAX_BATCH) return SIM_ERR_ARG;
 
   int lut[256];
   build_lut(c.intensity, lut);
@@ -459,18 +370,18 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   s->sms = std::max(1, evsim::device_sm_count());
 
   long long cap = c.event_capacity > 0 ? c.event_capacity : std::max<long long>(1LL << 20, 8 * P);
-  cap = std::min<long long>(cap, evsim::MAX_EVENTS_PER_FRAME - 1);
+  cap = std::min<long long>(cap, evsim::MAX_EVENTS);
   s->event_cap = cap;
-  s->stage_cap = (unsigned)cap;
   const bool sparse = c.mode == SIM_SPARSE;
-  const long long segs_per_k = sparse ? (P + evsim::SCHUNK - 1) / evsim::SCHUNK
-                                      : (long long)c.height * s->tiles_x;
-  s->seg_cap = segs_per_k * s->n_max;
-  const long long ochunks = std::max(1LL, (s->seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
-  const long long schunks = (P + evsim::SCHUNK - 1) / evsim::SCHUNK;
-  s->use_graphs = (c.flags & SIM_FLAG_NO_GRAPHS) == 0;
-  // the legacy default stream cannot be captured
-  if (c.cuda_stream == (void*)cudaStreamLegacy) s->use_graphs = false;
+  s->segs_per_k = sparse ? (P + evsim::SCHUNK - 1) / evsim::SCHUNK
+                         : (long long)c.height * s->tiles_x;
+  // frames per batch: the requested cap, else what a 256 MB segment table holds
+  const long long seg_bytes_per_frame = s->segs_per_k * s->n_max * (long long)sizeof(int2);
+  long long bm = c.max_batch > 0 ? c.max_batch
+                                 : std::max(1LL, (256LL << 20) / std::max(1LL, seg_bytes_per_frame));
+  s->bmax = (int)std::min<long long>(bm, SIM_MAX_BATCH);
+  const long long seg_cap = (long long)s->bmax * s->n_max * s->segs_per_k;
+  const long long ochunks = std::max(1LL, (seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
 
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
@@ -485,21 +396,16 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   chk(dalloc(&s->d_ring[1], P));
   if (c.ref_mode == SIM_REF_ACCUM) {
     chk(dalloc(&s->d_R[0], P));
-    if (!sparse) chk(dalloc(&s->d_R[1], P));
-    if (sparse) {
-      chk(dalloc(&s->d_Rsave, schunks * evsim::SCHUNK));
-      chk(dalloc(&s->d_idx, schunks * evsim::SCHUNK));
-    }
+    chk(dalloc(&s->d_R[1], P));
   }
-  if (sparse) chk(dalloc(&s->d_chunk_active, schunks));
-  chk(dalloc(&s->d_desc, SIM_MAX_BATCH));
   chk(dalloc(&s->d_ctl, 1));
+  chk(dalloc(&s->d_maxf2, s->bmax));
   chk(dalloc(&s->d_staging, cap));
   chk(dalloc(&s->d_events, cap));
-  chk(dalloc(&s->d_seg, s->seg_cap));
+  chk(dalloc(&s->d_seg, seg_cap));
   chk(dalloc(&s->d_order_status, ochunks));
-  chk(dalloc(&s->d_frame_stage, P * s->ch));
-  chk(dalloc(&s->d_flow_stage, P));
+  chk(dalloc(&s->d_desc, s->bmax));
+  chk(dalloc(&s->d_stage_frames, P * s->ch));
   if (c.c_pos_map) {
     chk(dalloc(&s->d_cpmap, P));
     chk(dalloc(&s->d_cnmap, P));
@@ -511,6 +417,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   if (e == cudaSuccess) {
     chk(cudaMemcpy(s->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice));
     chk(cudaMemset(s->d_ctl, 0, sizeof(Ctl)));
+    chk(cudaMemset(s->d_maxf2, 0, s->bmax * sizeof(unsigned long long)));
     chk(cudaMemset(s->d_order_status, 0, ochunks * sizeof(unsigned long long)));
   }
   if (e == cudaSuccess) {
@@ -526,53 +433,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
     delete s;
     return rc;
   }
-  s->order_grid = (int)std::min<long long>(ochunks, (long long)s->sms * 4);
-  s->pre_grid = (int)std::max(1LL, std::min<long long>((P + evsim::NT - 1) / evsim::NT,
-                                                       (long long)s->sms * 4));
-  s->sparse_grid = (int)std::max(1LL, std::min<long long>(schunks, (long long)s->sms * 4));
+  s->order_grid = (int)std::min<long long>(ochunks, (long long)s->sms * 8);
   *out = s;
-  return SIM_OK;
-}
-
-int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float* flow,
-                   int64_t t_us, int32_t mem) {
-  if (!s || !frame) return SIM_ERR_ARG;
-  if (mem != SIM_HOST && mem != SIM_DEVICE) return SIM_ERR_ARG;
-  const long long row = (long long)s->W * s->ch;
-  if (pitch_bytes < row) return SIM_ERR_ARG;
-  if (s->have_first) {
-    if (!flow) return SIM_ERR_ARG;
-    if (t_us <= s->t_last) return SIM_ERR_TIME;
-    if (t_us - s->t0 > 4294967295LL) return SIM_ERR_TIME_RANGE;
-  }
-  cudaError_t e = cudaSuccess;
-  const unsigned char* dframe = (const unsigned char*)frame;
-  const float2* dflow = (const float2*)flow;
-  long long pitch = pitch_bytes;
-  if (mem == SIM_HOST) {
-    e = cudaMemcpy2DAsync(s->d_frame_stage, row, frame, pitch_bytes, row, s->H,
-                          cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) return cuda_rc(e);
-    dframe = s->d_frame_stage;
-    pitch = row;
-    if (s->have_first) {
-      e = cudaMemcpyAsync(s->d_flow_stage, flow, s->P * sizeof(float2), cudaMemcpyHostToDevice,
-                          s->stream);
-      if (e != cudaSuccess) return cuda_rc(e);
-      dflow = s->d_flow_stage;
-    }
-  }
-  if (!s->have_first) return push_first(s, dframe, pitch, t_us);
-  evsim::FrameArg fa{};
-  fa.val.frame = dframe;
-  fa.val.pitch = pitch;
-  fa.val.flow = dflow;
-  fa.val.t_rel = t_us - s->t0;
-  fa.val.serial = ++s->serial;
-  e = enqueue_frame(s, fa);
-  if (e != cudaSuccess) return cuda_rc(e);
-  s->t_last = t_us;
-  s->pushed += 1;
   return SIM_OK;
 }
 
@@ -583,11 +445,13 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
   const long long row = (long long)s->W * s->ch;
   if (pitch_bytes < row) return SIM_ERR_ARG;
   // validate the whole batch first
-  long long tl = s->t_last, t0 = s->have_first ? s->t0 : t_us[0];
+  long long tl = s->t_last, t0 = s->have_first ? s->t0 : (count > 0 ? t_us[0] : 0);
   for (int i = 0; i < count; ++i) {
-    const bool first = !s->have_first && i == 0;
     if (!frames[i]) return SIM_ERR_ARG;
-    if (first) { tl = t_us[0]; continue; }
+    if (!s->have_first && i == 0) {
+      tl = t_us[0];
+      continue;
+    }
     if (!flows || !flows[i]) return SIM_ERR_ARG;
     if (t_us[i] <= tl) return SIM_ERR_TIME;
     if (t_us[i] - t0 > 4294967295LL) return SIM_ERR_TIME_RANGE;
@@ -595,36 +459,34 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
   }
   int i0 = 0;
   if (!s->have_first && count > 0) {
-    const int rc = sim_push_frame(s, frames[0], pitch_bytes, nullptr, t_us[0], mem);
+    const int rc = push_first(s, frames[0], pitch_bytes, t_us[0], mem);
     if (rc) return rc;
     i0 = 1;
   }
   cudaError_t e = cudaSuccess;
   std::vector<evsim::FrameDesc> desc;
   while (i0 < count) {
-    const int n = std::min(count - i0, SIM_MAX_BATCH);
+    const int n = std::min(count - i0, s->bmax);
     desc.assign(n, evsim::FrameDesc{});
-    if (mem == SIM_HOST) {
-      if (s->batch_stage_frames < n) {
-        e = cudaStreamSynchronize(s->stream);  // earlier batches may still read the old area
-        if (e != cudaSuccess) return cuda_rc(e);
-        cudaFree(s->d_batch_frames);
-        cudaFree(s->d_batch_flows);
-        s->d_batch_frames = nullptr;
-        s->d_batch_flows = nullptr;
-        s->batch_stage_frames = 0;
-        e = dalloc(&s->d_batch_frames, (size_t)n * s->P * s->ch);
-        if (e == cudaSuccess) e = dalloc(&s->d_batch_flows, (size_t)n * s->P);
-        if (e != cudaSuccess) return cuda_rc(e);
-        s->batch_stage_frames = n;
-      }
+    if (mem == SIM_HOST && s->stage_frames < n) {
+      e = cudaStreamSynchronize(s->stream);  // earlier batches may still read the old area
+      if (e != cudaSuccess) return cuda_rc(e);
+      cudaFree(s->d_stage_frames);
+      cudaFree(s->d_stage_flows);
+      s->d_stage_frames = nullptr;
+      s->d_stage_flows = nullptr;
+      s->stage_frames = 0;
+      e = dalloc(&s->d_stage_frames, (size_t)n * s->P * s->ch);
+      if (e == cudaSuccess) e = dalloc(&s->d_stage_flows, (size_t)n * s->P);
+      if (e != cudaSuccess) return cuda_rc(e);
+      s->stage_frames = n;
     }
     for (int j = 0; j < n; ++j) {
       const int i = i0 + j;
       evsim::FrameDesc& d = desc[j];
       if (mem == SIM_HOST) {
-        unsigned char* fd = s->d_batch_frames + (size_t)j * s->P * s->ch;
-        float2* fl = s->d_batch_flows + (size_t)j * s->P;
+        unsigned char* fd = s->d_stage_frames + (size_t)j * s->P * s->ch;
+        float2* fl = s->d_stage_flows + (size_t)j * s->P;
         e = cudaMemcpy2DAsync(fd, row, frames[i], pitch_bytes, row, s->H, cudaMemcpyHostToDevice,
                               s->stream);
         if (e == cudaSuccess)
@@ -639,32 +501,21 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
         d.flow = (const float2*)flows[i];
       }
       d.t_rel = t_us[i] - s->t0;
-      d.serial = ++s->serial;
     }
-    if (s->use_graphs && n >= 2) {
-      GraphEntry* ge = nullptr;
-      e = batch_graph(s, n, &ge);
-      // a profiled graph reuses its events: read the previous replay first
-      if (e == cudaSuccess && s->prof) prof_collect(s);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
-                            cudaMemcpyHostToDevice, s->stream);
-      if (e == cudaSuccess) e = TR(cudaGraphLaunch(ge->exec, s->stream));
-      if (e != cudaSuccess) return cuda_rc(e);
-      if (s->prof) s->pending.insert(s->pending.end(), ge->recs.begin(), ge->recs.end());
-    } else {
-      for (int j = 0; j < n; ++j) {
-        evsim::FrameArg fa{};
-        fa.val = desc[j];
-        e = enqueue_frame(s, fa);
-        if (e != cudaSuccess) return cuda_rc(e);
-      }
-    }
+    e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
+                        cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = enqueue_batch(s, n);
+    if (e != cudaSuccess) return cuda_rc(e);
     s->t_last = t_us[i0 + n - 1];
     s->pushed += n;
     i0 += n;
   }
   return SIM_OK;
+}
+
+int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float* flow,
+                   int64_t t_us, int32_t mem) {
+  return sim_push_frames(s, 1, &frame, pitch_bytes, &flow, &t_us, mem);
 }
 
 int sim_sync(sim_t* s) {
@@ -710,7 +561,7 @@ int sim_pop_events(sim_t* s, sim_event* out, int64_t cap, int64_t* n_out, int32_
     if (e != cudaSuccess) return cuda_rc(e);
     s->popped = 0;
   }
-  if (status == SIM_OK && avail > m) status = SIM_MORE;
+  if (avail > m) status = SIM_MORE;
   return status;
 }
 
@@ -724,10 +575,11 @@ int sim_get_stats(sim_t* s, sim_stats* st) {
   st->frames_committed = c.committed;
   st->events_pending = c.cursor - s->popped;
   st->events_popped = s->popped_total;
-  st->last_active = s->cfg.mode == SIM_SPARSE ? c.last_active : s->P;
-  st->last_frame_events = c.frame_events;
+  st->last_active = c.last_active;
+  st->last_batch_events = c.batch_events;
   st->flow_clamped = (int64_t)c.clamped;
-  st->last_substeps = c.n_frame;
+  st->last_substeps = c.last_n;
+  st->max_batch = s->bmax;
   st->pixel_substeps = c.work_px;
   st->active_substeps = c.work_active;
   return SIM_OK;
@@ -739,7 +591,7 @@ int sim_get_reference(sim_t* s, int32_t* out_host) {
   Ctl c;
   int rc = read_ctl(s, &c);
   if (rc) return rc;
-  const int* src = (s->cfg.mode == SIM_DENSE && (c.sel & 1)) ? s->d_R[1] : s->d_R[0];
+  const int* src = (c.sel & 1) ? s->d_R[1] : s->d_R[0];
   cudaError_t e = cudaMemcpy(out_host, src, s->P * sizeof(int), cudaMemcpyDeviceToHost);
   return cuda_rc(e);
 }
@@ -767,6 +619,7 @@ int sim_reset(sim_t* s) {
   if (!s) return SIM_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e == cudaSuccess) e = cudaMemset(s->d_ctl, 0, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMemset(s->d_maxf2, 0, s->bmax * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_rc(e);
   s->have_first = false;
   s->t0 = s->t_last = 0;

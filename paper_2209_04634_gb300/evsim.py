@@ -27,7 +27,6 @@ SIM_DENSE, SIM_SPARSE = 0, 1
 SIM_LOG, SIM_LINEAR = 0, 1
 SIM_REF_ACCUM, SIM_REF_RESET = 0, 1
 SIM_HOST, SIM_DEVICE = 0, 1
-SIM_FLAG_NO_GRAPHS = 1
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 SIM_MAX_BATCH = 1024
 SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
@@ -43,7 +42,7 @@ class sim_config(ctypes.Structure):
         ("substeps", ctypes.c_int32), ("max_substeps", ctypes.c_int32),
         ("intensity", ctypes.c_int32), ("ref_mode", ctypes.c_int32),
         ("c_pos_q16", ctypes.c_int32), ("c_neg_q16", ctypes.c_int32),
-        ("c_act_q16", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("c_act_q16", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("c_pos_map", ctypes.c_void_p), ("c_neg_map", ctypes.c_void_p),
         ("event_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
     ]
@@ -53,9 +52,9 @@ class sim_stats(ctypes.Structure):
     _fields_ = [
         ("frames_pushed", ctypes.c_int64), ("frames_committed", ctypes.c_int64),
         ("events_pending", ctypes.c_int64), ("events_popped", ctypes.c_int64),
-        ("last_active", ctypes.c_int64), ("last_frame_events", ctypes.c_int64),
+        ("last_active", ctypes.c_int64), ("last_batch_events", ctypes.c_int64),
         ("flow_clamped", ctypes.c_int64), ("last_substeps", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32), ("pixel_substeps", ctypes.c_int64),
+        ("max_batch", ctypes.c_int32), ("pixel_substeps", ctypes.c_int64),
         ("active_substeps", ctypes.c_int64),
     ]
 
@@ -155,7 +154,7 @@ class Simulator:
                  intensity: int = SIM_LOG, ref_mode: int = SIM_REF_ACCUM,
                  c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
                  c_pos_map=None, c_neg_map=None, event_capacity: int = 0, stream=None,
-                 flags: int = 0):
+                 max_batch: int = 0):
         lib = load()
         cfg = sim_config()
         check(lib.sim_config_default(ctypes.byref(cfg), width, height), "sim_config_default")
@@ -176,7 +175,7 @@ class Simulator:
             cfg.c_pos_map = cp.ctypes.data
             cfg.c_neg_map = cn.ctypes.data
         cfg.event_capacity = event_capacity
-        cfg.flags = flags
+        cfg.max_batch = max_batch
         if stream is not None:
             handle = int(getattr(stream, "cuda_stream", stream))
             # handle 0 is the legacy default stream (torch's default stream):
@@ -203,8 +202,8 @@ class Simulator:
 
     def push_many(self, frames, flows, t_us, pitch: int | None = None) -> None:
         """Push frames[0..F) with flows[i] (i -> frame i-1 to i) in one call.
-        frames/flows: torch CUDA tensors (device batch, replayed as a CUDA graph)
-        or numpy arrays (host batch); flows[0] is ignored for a first frame."""
+        frames/flows: torch CUDA tensors (device batch) or numpy arrays (host
+        batch); flows[0] is ignored for a stream's first frame."""
         F = len(t_us)
         dev = _is_device(frames)
         if not dev:

@@ -27,7 +27,7 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
             pop_every: int = 1, intensity=evsim.SIM_LOG, ref_mode=evsim.SIM_REF_ACCUM,
             c_act_q16: int = -1, substeps=None, c_pos_q16=None, c_neg_q16=None,
             use_maps=True, event_capacity: int = 0, stream=None, batch: int = 0,
-            flags: int = 0) -> dict:
+            max_batch: int = 0) -> dict:
     """Push every frame of seq through the CUDA library; return the events,
     the committed reference and per-frame statistics."""
     import torch
@@ -44,7 +44,7 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
         kw["c_neg_map"] = None
     if stream is not None:
         kw["stream"] = stream
-    kw["flags"] = flags
+    kw["max_batch"] = max_batch
     sim = evsim.simulator_for(seq, mode, **kw)
     if batch:
         return _gpu_run_batched(sim, seq, batch, device_inputs, ref_mode)
@@ -62,7 +62,7 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
             st = sim.stats()
             if pop_every == 1:
                 n_per_frame.append(st.last_substeps)
-                ev_per_frame.append(st.last_frame_events)
+                ev_per_frame.append(st.last_batch_events)
                 active.append(st.last_active)
             out.append(sim.pop())
     st = sim.stats()

@@ -299,9 +299,9 @@ def test_two_handles_on_two_streams_are_independent():
 
 @pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
 @pytest.mark.parametrize("batch,device", [(7, True), (1, True), (5, False), (40, True)])
-def test_batched_pushes_graph_replay(mode, batch, device):
-    """sim_push_frames (CUDA-graph replay of device batches, staged host
-    batches) gives the same stream as the oracle."""
+def test_batched_pushes(mode, batch, device):
+    """sim_push_frames (device batches carried through by persistent blocks,
+    staged host batches) gives the same stream as the oracle."""
     seq = synth.warped_texture(frames=23, width=160, height=120, seed=21)
     g = gpu_run(seq, mode, batch=batch, device_inputs=device)
     o = oracle_run(seq, mode)
@@ -309,10 +309,35 @@ def test_batched_pushes_graph_replay(mode, batch, device):
     assert np.array_equal(g["R"], o["R"])
 
 
-def test_batched_pushes_without_graphs():
-    seq = synth.moving_rectangles(frames=9, width=256, height=144, side=(20, 60), seed=8)
-    g = gpu_run(seq, evsim.SIM_DENSE, batch=4, flags=evsim.SIM_FLAG_NO_GRAPHS)
-    assert_same_events(g["events"], oracle_run(seq)["events"], "no graphs")
+@pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
+def test_batches_split_at_the_device_batch_cap(mode):
+    """A push of 9 frames on a handle whose device batch holds 4 frames runs
+    as batches of 4, 4, 1 (+ the first frame) and still equals the oracle."""
+    seq = synth.moving_rectangles(frames=10, width=256, height=144, side=(20, 60), seed=8)
+    g = gpu_run(seq, mode, batch=10, max_batch=4)
+    assert g["stats"].max_batch == 4
+    assert_same_events(g["events"], oracle_run(seq, mode)["events"], "split batches")
+
+
+@pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
+def test_batch_overflow_commits_nothing_of_the_batch(mode):
+    seq = synth.blob_translation(frames=7)
+    o = oracle_run(seq, mode)
+    per = o["ev_per_frame"]
+    cap = int(per[1:4].sum() + per[4:6].sum() // 2)  # frames 1-3 fit, 1-6 do not
+    sim = evsim.simulator_for(seq, mode, event_capacity=cap)
+    sim.push_many(seq.frames[:4], seq.flows[:4], seq.t_us[:4])
+    sim.push_many(seq.frames[4:7], seq.flows[4:7], seq.t_us[4:7])
+    with pytest.raises(evsim.SimError) as ei:
+        sim.sync()
+    assert ei.value.code == evsim.SIM_ERR_EVENT_OVERFLOW
+    assert sim.stats().frames_committed == 4
+    got = [sim.pop()]
+    sim.push_many(seq.frames[4:7], seq.flows[4:7], seq.t_us[4:7])
+    got.append(sim.pop())
+    assert_same_events(np.concatenate(got), o["events"], "after a failed batch")
+    assert np.array_equal(sim.reference(), o["R"])
+    sim.close()
 
 
 def test_batch_rejects_bad_timestamps_before_enqueueing():
