@@ -7,23 +7,20 @@
 
 namespace evsim {
 
-// Dense tile: TW x TH pixels (NTD threads: warp w owns tile row w, lane l
-// owns columns l and l + 32).
+// Tile of the simulation kernel (dense and sparse): TW x TH pixels, NTD
+// threads, up to two simulated pixels per thread.
 constexpr int TW = 64;
 constexpr int TH = 16;
+constexpr int NTD = 512;
+// Block size of the other kernels.
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
-constexpr int NTD = 512;  // dense kernel: one warp per tile row, 2 pixels per thread
 // Largest per-tile flow reach (pixels) served from the shared-memory halo;
 // tiles whose flow reaches further sample global memory instead.
 constexpr int HMAX = 16;
 constexpr int SW = TW + 2 * HMAX;  // shared tile stride (int32 elements)
 constexpr int SH = TH + 2 * HMAX;
 constexpr int MAXN = 64;           // largest substep count
-// Sparse: raster pixels per chunk (4 per thread); the active pixels of a
-// chunk are compacted and simulated by the block that owns the chunk.
-constexpr int SCHUNK = 4 * NT;
-constexpr int SROUNDS = SCHUNK / NT;
 // Order kernel: segments per chunk (four per thread).
 constexpr int OPER = 4;
 constexpr int OCHUNK = OPER * NT;
@@ -106,9 +103,8 @@ struct SimParams {
   long long event_cap;
 };
 
-// Shared-memory bytes of the dense and sparse kernels for a substep cap.
-size_t dense_smem_bytes(int n_max);
-size_t sparse_smem_bytes(int n_max);
+// Shared-memory bytes of the tile kernel (dense and sparse) for a substep cap.
+size_t tile_smem_bytes(int n_max);
 
 // Launchers (kernels.cu).  Each returns the cudaError_t of the launch.
 cudaError_t launch_init(const SimParams& p, const FrameDesc& f, cudaStream_t st);

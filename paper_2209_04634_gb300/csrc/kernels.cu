@@ -389,47 +389,72 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, BatchArg b) {
 }
 
 // ---------------------------------------------------------------------------
-// dense simulation (Sec. III-A).  One block per 64 x 16 tile runs the tile
-// through every frame of the batch, keeping the tile's reference R (and
-// thresholds) in registers from the first frame to the last.  Warp w owns
-// tile row w, lane l owns columns l and l + 32.
+// Tile simulation, dense (Sec. III-A) and sparse (Sec. III-B).  One block
+// (NTD threads) per 64 x 16 tile carries the tile through every frame of the
+// batch; the tile's reference R and thresholds stay in shared memory from the
+// first frame to the last.  Per frame:
+//   1. the pixels to simulate are selected: every pixel of the image (dense),
+//      or the pixels whose log intensity changed by at least C_act from frame
+//      i-1 to frame i (sparse), and compacted in raster order ("slots");
+//   2. their flow is read, the tile's flow reach sizes a replicate-padded halo
+//      of both log frames in shared memory;
+//   3. each thread runs up to two compacted pixels through the N substeps,
+//      recording every pixel-substep's signed event count;
+//   4. events per (substep, tile row) are counted, the tile's events are
+//      written to staging in (substep, row, column) order and one segment
+//      entry per (substep, row) is published for the order kernel.
 
-struct DenseLayout {
+__device__ __forceinline__ int activity_threshold(const SimParams& p, int cp, int cn) {
+  return p.cact >= 0 ? p.cact : min(cp, cn);
+}
+
+constexpr int TP = TW * TH;  // pixels per tile (1024)
+
+struct TileLayout {
   int* sL0;
   int* sL1;
   int* slut;
-  int* srow;   // [N][TH] events per (substep, tile row)
-  int* soff;   // [N][TH] tile-local exclusive offsets
+  int* sR;               // [TP] the tile's reference
+  int* srow;             // [N][TH] events per (substep, tile row)
+  int* soff;             // [N][TH] tile-local exclusive offsets
   unsigned* stk;
   int* swk;
-  short* snk;  // [N][TH][TW] signed event count per pixel-substep
+  short* snk;            // [N][TP] signed event count per (substep, slot)
+  short* sslot;          // [TP] tile pixel index (ty * TW + tx) of each slot
+  unsigned short* sCp;   // [TP] per-pixel thresholds (maps)
+  unsigned short* sCn;
 };
 
-__device__ __forceinline__ DenseLayout dense_layout(unsigned char* raw, int nmax) {
-  DenseLayout L;
+__device__ __forceinline__ TileLayout tile_layout(unsigned char* raw, int nmax) {
+  TileLayout L;
   L.sL0 = (int*)raw;
   L.sL1 = L.sL0 + SH * SW;
   L.slut = L.sL1 + SH * SW;
-  L.srow = L.slut + 256;
+  L.sR = L.slut + 256;
+  L.srow = L.sR + TP;
   L.soff = L.srow + nmax * TH;
   L.stk = (unsigned*)(L.soff + nmax * TH);
   L.swk = (int*)(L.stk + nmax);
   L.snk = (short*)(L.swk + nmax);
+  L.sslot = L.snk + nmax * TP;
+  L.sCp = (unsigned short*)(L.sslot + TP);
+  L.sCn = L.sCp + TP;
   return L;
 }
 
+// The substeps of the (up to) two compacted pixels of this thread.
 template <bool RESET, bool WIDE, bool FAST>
-__device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLayout& L, int N,
-                                               int tx0, int ty0, const FrameRef& prv,
-                                               const FrameDesc& cur, const int (&Fx)[2],
-                                               const int (&Fy)[2], int (&R)[2],
-                                               const int (&Cp)[2], const int (&Cn)[2],
-                                               const bool (&inb)[2]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
+                                              int tx0, int ty0, const FrameRef& prv,
+                                              const FrameDesc& cur, const int (&slot)[2],
+                                              const bool (&act)[2], const int (&Fx)[2],
+                                              const int (&Fy)[2], int (&R)[2],
+                                              const int (&Cp)[2], const int (&Cn)[2]) {
+  const int tid = threadIdx.x;
   int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const int lx = lane + 32 * j, ly = warp;
+    const int lx = slot[j] & (TW - 1), ly = slot[j] / TW;
     // FAST: positions relative to the shared tile origin (tx0 - HMAX, ty0 - HMAX);
     // otherwise absolute image positions.
     px[j] = FAST ? (lx + HMAX) << 16 : (tx0 + lx) << 16;
@@ -444,12 +469,10 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLa
     ax[j] = 0;
     ay[j] = 0;
   }
-  short* nkrow = L.snk + warp * TW + lane;
   const unsigned b0 = (unsigned)__cvta_generic_to_shared(L.sL0);
   const unsigned b1 = (unsigned)__cvta_generic_to_shared(L.sL1);
   for (int k = 0; k < N; ++k) {
     const int w = L.swk[k];
-    int n[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       px[j] -= qx[j];
@@ -468,32 +491,26 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const DenseLa
                               py[j] + Fy[j]);
       }
       const int I = lerp12<WIDE>(s0, s1, w);
-      n[j] = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
-      if (!inb[j]) n[j] = 0;
-    }
-    short* q = nkrow + k * (TH * TW);
-    q[0] = (short)n[0];
-    q[32] = (short)n[1];
-    int c0 = abs(n[0]) + abs(n[1]);
-    if (__any_sync(FULL, c0 != 0)) {
-      c0 = __reduce_add_sync(FULL, c0);
-      if (lane == 0) L.srow[k * TH + warp] = c0;
+      int n = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
+      if (!act[j]) n = 0;
+      L.snk[k * TP + tid + j * NTD] = (short)n;
     }
   }
 }
 
-template <bool RESET, bool MAPS, bool WIDE>
-__global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+__global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy;
+  __shared__ int s_rs[TH + 1];  // first slot of each tile row
   __shared__ long long s_base;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
-  const DenseLayout L = dense_layout(smem_raw, nmax);
+  const TileLayout L = tile_layout(smem_raw, nmax);
   const int tile = blockIdx.x;
   const int tcx = tile % p.tiles_x, tcy = tile / p.tiles_x;
   const int tx0 = tcx * TW, ty0 = tcy * TH;
@@ -507,43 +524,27 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
   unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
   long long tprev = ctl->t_prev;
 
-  const int y = ty0 + warp;
-  int R[2], Cp[2], Cn[2];
-  bool inb[2];
+  // Thread t owns tile pixels (slots in raster order) t and t + NTD.
+  bool inimg[2];
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int x = tx0 + lane + 32 * j;
-    inb[j] = x < W && y < H;
-    R[j] = 0; Cp[j] = p.cp; Cn[j] = p.cn;
-    if (inb[j]) {
+  for (int q = 0; q < 2; ++q) {
+    const int s = tid + q * NTD;
+    const int x = tx0 + (s & (TW - 1)), y = ty0 + s / TW;
+    inimg[q] = x < W && y < H;
+    if (inimg[q]) {
       const long long i = (long long)y * W + x;
-      if (!RESET) R[j] = Rin[i];
-      if (MAPS) { Cp[j] = p.cpmap[i]; Cn[j] = p.cnmap[i]; }
+      if (!RESET) L.sR[s] = Rin[i];
+      if (MAPS) { L.sCp[s] = p.cpmap[i]; L.sCn[s] = p.cnmap[i]; }
     }
   }
   int clamps = 0;
+  long long act_sum = 0, act_n = 0;
   bool failed = false;
 
   for (int fi = 0; fi < b.count && !failed; ++fi) {
     const FrameDesc cur = b.frames[fi];
     const FrameRef prv = prev_frame(p, b, fi, ringp);
     const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
-    int Fx[2], Fy[2];
-    unsigned mfx = 0, mfy = 0;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      Fx[j] = 0;
-      Fy[j] = 0;
-      if (inb[j]) {
-        const float2 fl = cur.flow[(long long)y * W + tx0 + lane + 32 * j];
-        Fx[j] = flow_q16(fl.x, clamps);
-        Fy[j] = flow_q16(fl.y, clamps);
-        mfx = max(mfx, (unsigned)abs(Fx[j]));
-        mfy = max(mfy, (unsigned)abs(Fy[j]));
-      }
-    }
-    mfx = __reduce_max_sync(FULL, mfx);
-    mfy = __reduce_max_sync(FULL, mfy);
     if (tid == 0) { s_fx = 0; s_fy = 0; }
     if (tid < N) {
       const int k = tid + 1;
@@ -551,8 +552,67 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
       const long long dt = cur.t_rel - tprev;
       L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
     }
+
+    // 1. select and compact (raster order: slots 0..NTD-1 by q = 0 first)
+    int sel_flag[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int s = tid + q * NTD;
+      const int x = tx0 + (s & (TW - 1)), y = ty0 + s / TW;
+      bool a = inimg[q];
+      if (inimg[q]) {
+        const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
+        if (fi == b.count - 1) ringn[(long long)y * W + x] = (unsigned char)vc;
+        if (SPARSE) {
+          const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
+          const int cp = MAPS ? (int)L.sCp[s] : p.cp, cn = MAPS ? (int)L.sCn[s] : p.cn;
+          a = abs(L.slut[vc] - L.slut[vp]) >= activity_threshold(p, cp, cn);
+        }
+      }
+      sel_flag[q] = a ? 1 : 0;
+    }
+    int A;
+    const int packed = block_excl_scan<NTD>(sel_flag[0] | (sel_flag[1] << 16), s_warp, &A);
+    const int A0 = A & 0xFFFF;
+    A = A0 + (A >> 16);
+    const int o0 = packed & 0xFFFF, o1 = A0 + (packed >> 16);
+    if (sel_flag[0]) L.sslot[o0] = (short)tid;
+    if (sel_flag[1]) L.sslot[o1] = (short)(tid + NTD);
+    // first slot of each row: rows 0..7 start at slots handled by q = 0, rows 8..15 by q = 1
+    if ((tid & (TW - 1)) == 0) {
+      const int r = tid / TW;
+      s_rs[r] = o0;
+      s_rs[r + NTD / TW] = o1;
+    }
+    if (tid == 0) s_rs[TH] = A;
     for (int e = tid; e < N * TH; e += NTD) L.srow[e] = 0;
+    act_sum += A;
+    act_n += (long long)A * N;
     __syncthreads();
+
+    // 2. the thread's compacted pixels: j = tid, tid + NTD
+    int slot[2], Fx[2], Fy[2], R[2], Cp[2], Cn[2];
+    bool act[2];
+    unsigned mfx = 0, mfy = 0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int j = tid + q * NTD;
+      act[q] = j < A;
+      slot[q] = act[q] ? L.sslot[j] : 0;
+      Fx[q] = 0; Fy[q] = 0; R[q] = 0; Cp[q] = p.cp; Cn[q] = p.cn;
+      if (act[q]) {
+        const int x = tx0 + (slot[q] & (TW - 1)), y = ty0 + slot[q] / TW;
+        const float2 fl = cur.flow[(long long)y * W + x];
+        Fx[q] = flow_q16(fl.x, clamps);
+        Fy[q] = flow_q16(fl.y, clamps);
+        if (MAPS) { Cp[q] = L.sCp[slot[q]]; Cn[q] = L.sCn[slot[q]]; }
+        R[q] = RESET ? L.slut[load_luma(prv.ptr, prv.pitch, prv.ch, y, x)] : L.sR[slot[q]];
+        mfx = max(mfx, (unsigned)abs(Fx[q]));
+        mfy = max(mfy, (unsigned)abs(Fy[q]));
+      }
+    }
+    mfx = __reduce_max_sync(FULL, mfx);
+    mfy = __reduce_max_sync(FULL, mfy);
     if (lane == 0) {
       atomicMax(&s_fx, (int)mfx);
       atomicMax(&s_fy, (int)mfy);
@@ -561,7 +621,7 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
     // Reach of every tap of the tile: floor(max |F|) + 1 pixels on each side.
     const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
     const bool fast = hx <= HMAX && hy <= HMAX;
-    if (fast) {
+    if (fast && A > 0) {
       // Replicate-padded halo tiles of both log frames.  The region is walked
       // as a flat index (row = e / ncols by a multiply-high with
       // ceil(2^32 / ncols), exact for e < 2^16), FILL loads in flight.
@@ -594,33 +654,35 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
         }
       }
     }
-    if (fi == b.count - 1) {
-      // the batch's last frame becomes the previous frame of the next batch
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (!inb[j]) continue;
-        const int x = tx0 + lane + 32 * j;
-        ringn[(long long)y * W + x] = (unsigned char)load_luma(cur.frame, cur.pitch, p.ch, y, x);
-      }
+    __syncthreads();
+
+    // 3. substeps (warps without a compacted pixel skip them)
+    if (warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
+      if (fast)
+        tile_substeps<RESET, WIDE, true>(p, L, N, tx0, ty0, prv, cur, slot, act, Fx, Fy, R, Cp, Cn);
+      else
+        tile_substeps<RESET, WIDE, false>(p, L, N, tx0, ty0, prv, cur, slot, act, Fx, Fy, R, Cp, Cn);
     }
-    if (RESET) {
-      // Consecutive differences start from frame i-1 itself.
+    if (!RESET) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (!inb[j]) continue;
-        const int x = tx0 + lane + 32 * j;
-        R[j] = L.slut[load_luma(prv.ptr, prv.pitch, prv.ch, y, x)];
-      }
+      for (int q = 0; q < 2; ++q)
+        if (act[q]) L.sR[slot[q]] = R[q];
     }
     __syncthreads();
 
-    if (fast)
-      dense_substeps<RESET, WIDE, true>(p, L, N, tx0, ty0, prv, cur, Fx, Fy, R, Cp, Cn, inb);
-    else
-      dense_substeps<RESET, WIDE, false>(p, L, N, tx0, ty0, prv, cur, Fx, Fy, R, Cp, Cn, inb);
+    // 4. events per (substep, row): warp r sums its row's slots
+    if (warp < TH) {
+      const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
+      for (int k = 0; k < N; ++k) {
+        int c = 0;
+        for (int j = s0 + lane; j < s1; j += 32) c += abs((int)L.snk[k * TP + j]);
+        if (__any_sync(FULL, c != 0)) {
+          c = __reduce_add_sync(FULL, c);
+          if (lane == 0) L.srow[k * TH + r] = c;
+        }
+      }
+    }
     __syncthreads();
-
-    // Tile-local offsets of the (substep, row) segments, substep-major.
     const int E = N * TH;
     int total;
     const long long base = stage_segments<NTD>(p, L.srow, L.soff, E, s_warp, &s_base, &total);
@@ -632,29 +694,34 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
         segf[(long long)k * p.segs_per_k + (long long)yy * p.tiles_x + tcx] =
             make_int2(fail ? 0 : L.srow[e], (int)(fail ? 0 : base) + L.soff[e]);
     }
-    if (!fail && total > 0) {
-      // Emission: each warp writes the events of its row, substep by substep.
+    if (!fail && total > 0 && warp < TH) {
+      // Emission: warp r writes its row's events, substep by substep, in
+      // column order (the row's slots are contiguous and in raster order).
       const unsigned lt = lanemask_lt();
+      const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
+      const int y = ty0 + r;
       for (int k = 0; k < N; ++k) {
-        const int e = k * TH + warp;
+        const int e = k * TH + r;
         if (L.srow[e] == 0) continue;
         const unsigned tk = L.stk[k];
-        const long long o = base + L.soff[e];
-        const int na = L.snk[e * TW + lane], nb = L.snk[e * TW + lane + 32];
-        const int aa = abs(na), ab = abs(nb);
-        const int xa = tx0 + lane, xb = tx0 + lane + 32;
-        if (__all_sync(FULL, (aa | ab) <= 1)) {
-          const unsigned ba = __ballot_sync(FULL, aa != 0), bb = __ballot_sync(FULL, ab != 0);
-          if (aa) p.staging[o + __popc(ba & lt)] = make_event(tk, xa, y, na > 0);
-          if (ab) p.staging[o + __popc(ba) + __popc(bb & lt)] = make_event(tk, xb, y, nb > 0);
-        } else {
-          const int ia = warp_incl_scan(aa);
-          const int ta = __shfl_sync(FULL, ia, 31);
-          const int ib = warp_incl_scan(ab);
-          const Ev ea = make_event(tk, xa, y, na > 0), eb = make_event(tk, xb, y, nb > 0);
-          const long long oa = o + ia - aa, ob = o + ta + ib - ab;
-          for (int m = 0; m < aa; ++m) p.staging[oa + m] = ea;
-          for (int m = 0; m < ab; ++m) p.staging[ob + m] = eb;
+        long long o = base + L.soff[e];
+        for (int j0 = s0; j0 < s1; j0 += 32) {
+          const int j = j0 + lane;
+          const int n = j < s1 ? L.snk[k * TP + j] : 0;
+          const int a = abs(n);
+          const int x = tx0 + (j < s1 ? (L.sslot[j] & (TW - 1)) : 0);
+          const Ev ev = make_event(tk, x, y, n > 0);
+          int seg_total;
+          if (__all_sync(FULL, a <= 1)) {
+            const unsigned bb = __ballot_sync(FULL, a != 0);
+            if (a) p.staging[o + __popc(bb & lt)] = ev;
+            seg_total = __popc(bb);
+          } else {
+            const int ia = warp_incl_scan(a);
+            for (int m = 0; m < a; ++m) p.staging[o + ia - a + m] = ev;
+            seg_total = __shfl_sync(FULL, ia, 31);
+          }
+          o += seg_total;
         }
       }
     }
@@ -665,25 +732,18 @@ __global__ void __launch_bounds__(NTD, 2) k_dense(SimParams p, BatchArg b) {
 
   if (!RESET && !failed) {
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (!inb[j]) continue;
-      const int x = tx0 + lane + 32 * j;
-      Rout[(long long)y * W + x] = R[j];
+    for (int q = 0; q < 2; ++q) {
+      if (!inimg[q]) continue;
+      const int s = tid + q * NTD;
+      Rout[(long long)(ty0 + s / TW) * W + tx0 + (s & (TW - 1))] = L.sR[s];
     }
   }
   clamps = __reduce_add_sync(FULL, clamps);
   if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
-}
-
-// ---------------------------------------------------------------------------
-// sparse (Sec. III-B): one block per chunk of SCHUNK raster pixels runs the
-// chunk through every frame of the batch.  Per frame it finds the active
-// pixels (|L_i - L_{i-1}| >= C_act), compacts them in raster order and
-// simulates only those; the chunk's reference stays in shared memory across
-// the batch.  Segments are (frame, substep, chunk).
-
-__device__ __forceinline__ int activity_threshold(const SimParams& p, int cp, int cn) {
-  return p.cact >= 0 ? p.cact : min(cp, cn);
+  if (SPARSE && tid == 0 && act_sum) {
+    atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)act_sum);
+    atomicAdd((unsigned long long*)&ctl->active_n, (unsigned long long)act_n);
+  }
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
@@ -723,186 +783,6 @@ __global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, BatchArg b) {
     unsigned long long bm = 0;
     for (int w = 0; w < NWARP; ++w) bm = s_m[w] > bm ? s_m[w] : bm;
     if (bm) atomicMax(&p.maxf2[fi], bm);
-  }
-}
-
-template <bool RESET, bool MAPS, bool WIDE>
-__global__ void __launch_bounds__(NT) k_sparse(SimParams p, BatchArg b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_warp[NWARP + 1];
-  __shared__ long long s_base;
-  __shared__ int sidx[SCHUNK];   // active pixels of the chunk (chunk-local index)
-  __shared__ int sR[SCHUNK];     // the chunk's reference
-  Ctl* ctl = p.ctl;
-  if (block_error(&ctl->err)) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nmax = p.n_max;
-  int* slut = (int*)smem_raw;
-  int* swk = slut + 256;
-  unsigned* stk = (unsigned*)(swk + nmax);
-  int* scnt = (int*)(stk + nmax);            // [N][SROUNDS][NWARP] counts
-  int* soff = scnt + nmax * SROUNDS * NWARP; // [N][SROUNDS][NWARP] chunk-local offsets
-  short* snk = (short*)(soff + nmax * SROUNDS * NWARP);  // [N][SCHUNK]
-  unsigned short* sCp = (unsigned short*)(snk + nmax * SCHUNK);  // [SCHUNK] (maps)
-  unsigned short* sCn = sCp + SCHUNK;
-
-  slut[tid] = p.lut[tid];
-  const long long P = (long long)p.W * p.H;
-  const int S = (int)p.segs_per_k;
-  const int c = blockIdx.x;
-  const long long cbase = (long long)c * SCHUNK;
-  const int W = p.W, H = p.H;
-  const int sel = ctl->sel;
-  const int* Rin = (sel & 1) ? p.R1 : p.R0;
-  int* Rout = (sel & 1) ? p.R0 : p.R1;
-  const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
-  unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
-  long long tprev = ctl->t_prev;
-  for (int q = tid; q < SCHUNK; q += NT) {
-    const long long i = cbase + q;
-    if (i < P) {
-      if (!RESET) sR[q] = Rin[i];
-      if (MAPS) { sCp[q] = p.cpmap[i]; sCn[q] = p.cnmap[i]; }
-    }
-  }
-  const unsigned lt = lanemask_lt();
-  int clamps = 0;
-  long long act_sum = 0, act_n = 0;
-  bool failed = false;
-
-  for (int fi = 0; fi < b.count && !failed; ++fi) {
-    const FrameDesc cur = b.frames[fi];
-    const FrameRef prv = prev_frame(p, b, fi, ringp);
-    const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
-    const int ESEG = N * SROUNDS * NWARP;
-    if (tid < N) {
-      const int k = tid + 1;
-      swk[tid] = (k * 8192 + N) / (2 * N);
-      const long long dt = cur.t_rel - tprev;
-      stk[tid] = (unsigned)(tprev + (k * dt) / N);
-    }
-    for (int e = tid; e < ESEG; e += NT) scnt[e] = 0;
-    __syncthreads();
-
-    // 1. activity of the chunk's pixels, compacted in raster order
-    unsigned flags = 0;
-    int cnt = 0;
-#pragma unroll
-    for (int q = 0; q < SROUNDS; ++q) {
-      const int li = SROUNDS * tid + q;
-      const long long i = cbase + li;
-      if (i < P) {
-        const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-        const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
-        const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
-        const int cp = MAPS ? (int)sCp[li] : p.cp, cn = MAPS ? (int)sCn[li] : p.cn;
-        if (abs(slut[vc] - slut[vp]) >= activity_threshold(p, cp, cn)) {
-          flags |= 1u << q;
-          ++cnt;
-        }
-        if (fi == b.count - 1) ringn[i] = (unsigned char)vc;
-      }
-    }
-    int A;
-    int o = block_excl_scan(cnt, s_warp, &A);
-#pragma unroll
-    for (int q = 0; q < SROUNDS; ++q)
-      if (flags & (1u << q)) sidx[o++] = SROUNDS * tid + q;
-    act_sum += A;
-    act_n += (long long)A * N;
-    __syncthreads();
-
-    // 2. simulate the active pixels, NT at a time (round r: pixels r NT + tid)
-    const int rounds = (A + NT - 1) / NT;
-    for (int r = 0; r < rounds; ++r) {
-      const int j = r * NT + tid;
-      const bool act = j < A;
-      const int li = act ? sidx[j] : 0;
-      const long long i = cbase + li;
-      const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-      int Fx = 0, Fy = 0, R = 0, cp = p.cp, cn = p.cn;
-      if (act) {
-        const float2 fl = cur.flow[i];
-        Fx = flow_q16(fl.x, clamps);
-        Fy = flow_q16(fl.y, clamps);
-        if (MAPS) { cp = sCp[li]; cn = sCn[li]; }
-        R = RESET ? slut[load_luma(prv.ptr, prv.pitch, prv.ch, y, x)] : sR[li];
-      }
-      int qx = Fx / N, rx = Fx - qx * N;
-      if (rx < 0) { rx += N; qx -= 1; }
-      int qy = Fy / N, ry = Fy - qy * N;
-      if (ry < 0) { ry += N; qy -= 1; }
-      int px = x << 16, py = y << 16, ax = 0, ay = 0;
-      for (int k = 0; k < N; ++k) {
-        px -= qx;
-        ax += rx;
-        if (ax >= N) { ax -= N; px -= 1; }
-        py -= qy;
-        ay += ry;
-        if (ay >= N) { ay -= N; py -= 1; }
-        const int s0 = tap_global<WIDE>(prv.ptr, prv.pitch, prv.ch, W, H, slut, px, py);
-        const int s1 = tap_global<WIDE>(cur.frame, cur.pitch, p.ch, W, H, slut, px + Fx, py + Fy);
-        const int I = lerp12<WIDE>(s0, s1, swk[k]);
-        int n = threshold_step<RESET>(I, R, cp, cn);
-        if (!act) n = 0;
-        snk[k * SCHUNK + j] = (short)n;
-        if (__any_sync(FULL, n != 0)) {
-          const int cw = __reduce_add_sync(FULL, abs(n));
-          if (lane == 0) scnt[(k * SROUNDS + r) * NWARP + warp] = cw;
-        }
-      }
-      if (!RESET && act) sR[li] = R;
-    }
-    __syncthreads();
-
-    // 3. chunk-local offsets in (substep, round, warp) order, staging, segments
-    int total;
-    const long long base = stage_segments(p, scnt, soff, ESEG, s_warp, &s_base, &total);
-    const bool fail = base < 0;
-    int2* segf = p.seg + (long long)fi * nmax * S;
-    if (tid < N) {
-      const int e0 = tid * SROUNDS * NWARP;
-      const int kt = soff[e0 + SROUNDS * NWARP - 1] + scnt[e0 + SROUNDS * NWARP - 1] - soff[e0];
-      segf[(long long)tid * S + c] = make_int2(fail ? 0 : kt, (int)(fail ? 0 : base) + soff[e0]);
-    }
-    if (!fail && total > 0) {
-      for (int k = 0; k < N; ++k) {
-        for (int r = 0; r < rounds; ++r) {
-          const int e = (k * SROUNDS + r) * NWARP + warp;
-          if (scnt[e] == 0) continue;
-          const int j = r * NT + tid;
-          const int n = j < A ? snk[k * SCHUNK + j] : 0;
-          const int a = abs(n);
-          const long long i = cbase + (j < A ? sidx[j] : 0);
-          const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-          const long long oo = base + soff[e];
-          const Ev ev = make_event(stk[k], x, y, n > 0);
-          if (__all_sync(FULL, a <= 1)) {
-            const unsigned bb = __ballot_sync(FULL, a != 0);
-            if (a) p.staging[oo + __popc(bb & lt)] = ev;
-          } else {
-            const int ia = warp_incl_scan(a);
-            for (int m = 0; m < a; ++m) p.staging[oo + ia - a + m] = ev;
-          }
-        }
-      }
-    }
-    failed = fail;
-    tprev = cur.t_rel;
-    __syncthreads();
-  }
-
-  if (!RESET && !failed) {
-    for (int q = tid; q < SCHUNK; q += NT) {
-      const long long i = cbase + q;
-      if (i < P) Rout[i] = sR[q];
-    }
-  }
-  clamps = __reduce_add_sync(FULL, clamps);
-  if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
-  if (tid == 0 && act_sum) {
-    atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)act_sum);
-    atomicAdd((unsigned long long*)&ctl->active_n, (unsigned long long)act_n);
   }
 }
 
@@ -1032,28 +912,37 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
   }
 }
 
-template <bool RESET, bool MAPS, bool WIDE>
-void set_dense_attr(size_t bytes) {
-  cudaFuncSetAttribute(k_dense<RESET, MAPS, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)bytes);
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+void set_tile_attr(size_t bytes) {
+  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <bool RESET, bool MAPS, bool WIDE>
-void set_sparse_attr(size_t bytes) {
-  cudaFuncSetAttribute(k_sparse<RESET, MAPS, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)bytes);
+template <bool SPARSE>
+cudaError_t launch_tile_mode(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  const int grid = p.tiles_x * p.tiles_y;
+  const size_t sm = tile_smem_bytes(p.n_max);
+  const bool reset = p.ref_mode == SIM_REF_RESET;
+  const bool maps = p.cpmap != nullptr;
+  const bool wide = p.intensity == SIM_LINEAR;
+#define EVSIM_TILE(R, M, Wd) k_tile<R, M, Wd, SPARSE><<<grid, NTD, sm, st>>>(p, b)
+  if (!reset && !maps && !wide) EVSIM_TILE(false, false, false);
+  else if (!reset && maps && !wide) EVSIM_TILE(false, true, false);
+  else if (!reset && !maps && wide) EVSIM_TILE(false, false, true);
+  else if (!reset && maps && wide) EVSIM_TILE(false, true, true);
+  else if (reset && !maps && !wide) EVSIM_TILE(true, false, false);
+  else if (reset && maps && !wide) EVSIM_TILE(true, true, false);
+  else if (reset && !maps && wide) EVSIM_TILE(true, false, true);
+  else EVSIM_TILE(true, true, true);
+#undef EVSIM_TILE
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t dense_smem_bytes(int n_max) {
-  return (size_t)(2 * SH * SW + 256 + 2 * n_max * TH + 2 * n_max) * 4 +
-         (size_t)n_max * TH * TW * 2;
-}
-
-size_t sparse_smem_bytes(int n_max) {
-  return (size_t)(256 + 2 * n_max + 2 * n_max * SROUNDS * NWARP) * 4 +
-         (size_t)n_max * SCHUNK * 2 + (size_t)2 * SCHUNK * 2;
+size_t tile_smem_bytes(int n_max) {
+  return (size_t)(2 * SH * SW + 256 + TP + 2 * n_max * TH + 2 * n_max) * 4 +
+         (size_t)(n_max * TP + 3 * TP) * 2;
 }
 
 int device_sm_count() {
@@ -1064,23 +953,23 @@ int device_sm_count() {
 }
 
 cudaError_t configure_kernels(int n_max) {
-  const size_t d = dense_smem_bytes(n_max), s = sparse_smem_bytes(n_max);
-  set_dense_attr<false, false, false>(d);
-  set_dense_attr<false, true, false>(d);
-  set_dense_attr<false, false, true>(d);
-  set_dense_attr<false, true, true>(d);
-  set_dense_attr<true, false, false>(d);
-  set_dense_attr<true, true, false>(d);
-  set_dense_attr<true, false, true>(d);
-  set_dense_attr<true, true, true>(d);
-  set_sparse_attr<false, false, false>(s);
-  set_sparse_attr<false, true, false>(s);
-  set_sparse_attr<false, false, true>(s);
-  set_sparse_attr<false, true, true>(s);
-  set_sparse_attr<true, false, false>(s);
-  set_sparse_attr<true, true, false>(s);
-  set_sparse_attr<true, false, true>(s);
-  set_sparse_attr<true, true, true>(s);
+  const size_t t = tile_smem_bytes(n_max);
+  set_tile_attr<false, false, false, false>(t);
+  set_tile_attr<false, true, false, false>(t);
+  set_tile_attr<false, false, true, false>(t);
+  set_tile_attr<false, true, true, false>(t);
+  set_tile_attr<true, false, false, false>(t);
+  set_tile_attr<true, true, false, false>(t);
+  set_tile_attr<true, false, true, false>(t);
+  set_tile_attr<true, true, true, false>(t);
+  set_tile_attr<false, false, false, true>(t);
+  set_tile_attr<false, true, false, true>(t);
+  set_tile_attr<false, false, true, true>(t);
+  set_tile_attr<false, true, true, true>(t);
+  set_tile_attr<true, false, false, true>(t);
+  set_tile_attr<true, true, false, true>(t);
+  set_tile_attr<true, false, true, true>(t);
+  set_tile_attr<true, true, true, true>(t);
   return cudaGetLastError();
 }
 
@@ -1101,22 +990,11 @@ cudaError_t launch_flowmax(const SimParams& p, const BatchArg& b, cudaStream_t s
 }
 
 cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st) {
-  const int grid = p.tiles_x * p.tiles_y;
-  const size_t sm = dense_smem_bytes(p.n_max);
-  const bool reset = p.ref_mode == SIM_REF_RESET;
-  const bool maps = p.cpmap != nullptr;
-  const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_DENSE(R, M, Wd) k_dense<R, M, Wd><<<grid, NTD, sm, st>>>(p, b)
-  if (!reset && !maps && !wide) EVSIM_DENSE(false, false, false);
-  else if (!reset && maps && !wide) EVSIM_DENSE(false, true, false);
-  else if (!reset && !maps && wide) EVSIM_DENSE(false, false, true);
-  else if (!reset && maps && wide) EVSIM_DENSE(false, true, true);
-  else if (reset && !maps && !wide) EVSIM_DENSE(true, false, false);
-  else if (reset && maps && !wide) EVSIM_DENSE(true, true, false);
-  else if (reset && !maps && wide) EVSIM_DENSE(true, false, true);
-  else EVSIM_DENSE(true, true, true);
-#undef EVSIM_DENSE
-  return cudaGetLastError();
+  return launch_tile_mode<false>(p, b, st);
+}
+
+cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  return launch_tile_mode<true>(p, b, st);
 }
 
 cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st) {
@@ -1125,25 +1003,6 @@ cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_
   const long long per_frame = std::max(1LL, (long long)sms * 4 / std::max(1, b.count));
   const int gx = (int)std::max(1LL, std::min<long long>((P + NT - 1) / NT, per_frame));
   k_sparse_pre<<<dim3(gx, b.count), NT, 0, st>>>(p, b);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st) {
-  const int grid = (int)p.segs_per_k;  // one block per raster chunk
-  const size_t sm = sparse_smem_bytes(p.n_max);
-  const bool reset = p.ref_mode == SIM_REF_RESET;
-  const bool maps = p.cpmap != nullptr;
-  const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_SPARSE(R, M, Wd) k_sparse<R, M, Wd><<<grid, NT, sm, st>>>(p, b)
-  if (!reset && !maps && !wide) EVSIM_SPARSE(false, false, false);
-  else if (!reset && maps && !wide) EVSIM_SPARSE(false, true, false);
-  else if (!reset && !maps && wide) EVSIM_SPARSE(false, false, true);
-  else if (!reset && maps && wide) EVSIM_SPARSE(false, true, true);
-  else if (reset && !maps && !wide) EVSIM_SPARSE(true, false, false);
-  else if (reset && maps && !wide) EVSIM_SPARSE(true, true, false);
-  else if (reset && !maps && wide) EVSIM_SPARSE(true, false, true);
-  else EVSIM_SPARSE(true, true, true);
-#undef EVSIM_SPARSE
   return cudaGetLastError();
 }
 

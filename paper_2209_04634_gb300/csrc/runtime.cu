@@ -373,8 +373,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   cap = std::min<long long>(cap, evsim::MAX_EVENTS);
   s->event_cap = cap;
   const bool sparse = c.mode == SIM_SPARSE;
-  s->segs_per_k = sparse ? (P + evsim::SCHUNK - 1) / evsim::SCHUNK
-                         : (long long)c.height * s->tiles_x;
+  (void)sparse;
+  s->segs_per_k = (long long)c.height * s->tiles_x;  // one segment per tile row
   // frames per batch: the requested cap, else what a 256 MB segment table holds
   const long long seg_bytes_per_frame = s->segs_per_k * s->n_max * (long long)sizeof(int2);
   long long bm = c.max_batch > 0 ? c.max_batch
