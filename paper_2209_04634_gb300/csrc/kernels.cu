@@ -540,6 +540,7 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
   int clamps = 0;
   long long act_sum = 0, act_n = 0;
   bool failed = false;
+  __syncthreads();  // the table, reference and thresholds above are read by all threads
 
   for (int fi = 0; fi < b.count && !failed; ++fi) {
     const FrameDesc cur = b.frames[fi];
