@@ -391,18 +391,22 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, BatchArg b) {
 // ---------------------------------------------------------------------------
 // Tile simulation, dense (Sec. III-A) and sparse (Sec. III-B).  One block
 // (NTD threads) per 64 x 16 tile carries the tile through every frame of the
-// batch; the tile's reference R and thresholds stay in shared memory from the
-// first frame to the last.  Per frame:
-//   1. the pixels to simulate are selected: every pixel of the image (dense),
-//      or the pixels whose log intensity changed by at least C_act from frame
-//      i-1 to frame i (sparse), and compacted in raster order ("slots");
-//   2. their flow is read, the tile's flow reach sizes a replicate-padded halo
-//      of both log frames in shared memory;
-//   3. each thread runs up to two compacted pixels through the N substeps,
-//      recording every pixel-substep's signed event count;
-//   4. events per (substep, tile row) are counted, the tile's events are
-//      written to staging in (substep, row, column) order and one segment
-//      entry per (substep, row) is published for the order kernel.
+// batch.  Per frame:
+//   1. the pixels to simulate: dense - every pixel of the tile in the image,
+//      warp w owning tile row w and lane l its columns l and l + 32, with the
+//      reference and thresholds in the owner's registers for the whole batch;
+//      sparse - the pixels whose log intensity changed by at least C_act from
+//      frame i-1 to frame i, compacted in raster order ("slots") and spread
+//      over the block, with the reference and thresholds in shared memory;
+//   2. their flow is read and the tile's flow reach sizes a replicate-padded
+//      halo of both log frames in shared memory.  Frame i's halo is kept as
+//      the next frame's previous-frame halo whenever its extent suffices, so
+//      usually one frame is loaded per frame;
+//   3. every simulated pixel runs through the N substeps, recording each
+//      pixel-substep's signed event count;
+//   4. the tile's events are written to staging in (substep, row, column)
+//      order and one segment entry per (substep, row) is published for the
+//      order kernel.
 
 __device__ __forceinline__ int activity_threshold(const SimParams& p, int cp, int cn) {
   return p.cact >= 0 ? p.cact : min(cp, cn);
@@ -411,25 +415,25 @@ __device__ __forceinline__ int activity_threshold(const SimParams& p, int cp, in
 constexpr int TP = TW * TH;  // pixels per tile (1024)
 
 struct TileLayout {
-  int* sL0;
-  int* sL1;
+  int* sLa;              // two halo buffers (SH x SW); roles swap between frames
+  int* sLb;
   int* slut;
-  int* sR;               // [TP] the tile's reference
+  int* sR;               // [TP] sparse: the tile's reference
   int* srow;             // [N][TH] events per (substep, tile row)
   int* soff;             // [N][TH] tile-local exclusive offsets
   unsigned* stk;
   int* swk;
   short* snk;            // [N][TP] signed event count per (substep, slot)
-  short* sslot;          // [TP] tile pixel index (ty * TW + tx) of each slot
-  unsigned short* sCp;   // [TP] per-pixel thresholds (maps)
+  short* sslot;          // [TP] sparse: tile pixel index (ty * TW + tx) of each slot
+  unsigned short* sCp;   // [TP] sparse: per-pixel thresholds (maps)
   unsigned short* sCn;
 };
 
 __device__ __forceinline__ TileLayout tile_layout(unsigned char* raw, int nmax) {
   TileLayout L;
-  L.sL0 = (int*)raw;
-  L.sL1 = L.sL0 + SH * SW;
-  L.slut = L.sL1 + SH * SW;
+  L.sLa = (int*)raw;
+  L.sLb = L.sLa + SH * SW;
+  L.slut = L.sLb + SH * SW;
   L.sR = L.slut + 256;
   L.srow = L.sR + TP;
   L.soff = L.srow + nmax * TH;
@@ -442,23 +446,59 @@ __device__ __forceinline__ TileLayout tile_layout(unsigned char* raw, int nmax) 
   return L;
 }
 
-// The substeps of the (up to) two compacted pixels of this thread.
-template <bool RESET, bool WIDE, bool FAST>
-__device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
-                                              int tx0, int ty0, const FrameRef& prv,
-                                              const FrameDesc& cur, const int (&slot)[2],
-                                              const bool (&act)[2], const int (&Fx)[2],
-                                              const int (&Fy)[2], int (&R)[2],
-                                              const int (&Cp)[2], const int (&Cn)[2]) {
+// Fill a replicate-padded halo buffer (LUT'd) of one frame with reach (hx, hy)
+// around the tile.  The region is walked as a flat index (row = e / ncols by
+// a multiply-high with ceil(2^32 / ncols), exact for e < 2^16).
+__device__ __forceinline__ void fill_halo(int* dst, const int* slut, const FrameRef& f, int W,
+                                          int H, int tx0, int ty0, int hx, int hy) {
+  constexpr int FILL = 4;
   const int tid = threadIdx.x;
+  const int c0 = HMAX - hx, ncols = TW + 2 * hx;
+  const int r0 = HMAX - hy, nrows = TH + 2 * hy;
+  const int total_fill = ncols * nrows;
+  const unsigned mcols = 0xFFFFFFFFu / (unsigned)ncols + 1u;
+  for (int e0 = 0; e0 < total_fill; e0 += NTD * FILL) {
+    int v[FILL], at[FILL];
+#pragma unroll
+    for (int q = 0; q < FILL; ++q) {
+      const int e = e0 + q * NTD + tid;
+      at[q] = -1;
+      if (e < total_fill) {
+        const int sr = (int)__umulhi((unsigned)e, mcols);
+        const int sc = e - sr * ncols;
+        const int gy = min(max(ty0 - hy + sr, 0), H - 1);
+        const int gx = min(max(tx0 - hx + sc, 0), W - 1);
+        v[q] = load_luma(f.ptr, f.pitch, f.ch, gy, gx);
+        at[q] = (r0 + sr) * SW + (c0 + sc);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < FILL; ++q)
+      if (at[q] >= 0) dst[at[q]] = slut[v[q]];
+  }
+}
+
+// The substeps of the (up to) two pixels of this thread.  `lx, ly` are the
+// pixels' tile coordinates, `nk_at` their columns in the per-substep record.
+// DENSE: the two pixels are columns lane, lane + 32 of tile row `warp`, and the
+// row's event count is reduced over the warp in the loop.
+template <bool RESET, bool WIDE, bool FAST, bool DENSE>
+__device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
+                                              int tx0, int ty0, unsigned b0, unsigned b1,
+                                              const FrameRef& prv, const FrameDesc& cur,
+                                              const int (&lx)[2], const int (&ly)[2],
+                                              const int (&nk_at)[2], const bool (&act)[2],
+                                              const int (&Fx)[2], const int (&Fy)[2],
+                                              int (&R)[2], const int (&Cp)[2],
+                                              const int (&Cn)[2]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const int lx = slot[j] & (TW - 1), ly = slot[j] / TW;
     // FAST: positions relative to the shared tile origin (tx0 - HMAX, ty0 - HMAX);
     // otherwise absolute image positions.
-    px[j] = FAST ? (lx + HMAX) << 16 : (tx0 + lx) << 16;
-    py[j] = FAST ? (ly + HMAX) << 16 : (ty0 + ly) << 16;
+    px[j] = FAST ? (lx[j] + HMAX) << 16 : (tx0 + lx[j]) << 16;
+    py[j] = FAST ? (ly[j] + HMAX) << 16 : (ty0 + ly[j]) << 16;
     // F = q N + r with 0 <= r < N: offset_k = q k + floor(r k / N)
     qx[j] = Fx[j] / N;
     rx[j] = Fx[j] - qx[j] * N;
@@ -469,10 +509,9 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
     ax[j] = 0;
     ay[j] = 0;
   }
-  const unsigned b0 = (unsigned)__cvta_generic_to_shared(L.sL0);
-  const unsigned b1 = (unsigned)__cvta_generic_to_shared(L.sL1);
   for (int k = 0; k < N; ++k) {
     const int w = L.swk[k];
+    int n[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       px[j] -= qx[j];
@@ -491,9 +530,16 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
                               py[j] + Fy[j]);
       }
       const int I = lerp12<WIDE>(s0, s1, w);
-      int n = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
-      if (!act[j]) n = 0;
-      L.snk[k * TP + tid + j * NTD] = (short)n;
+      n[j] = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
+      if (!act[j]) n[j] = 0;
+      L.snk[k * TP + nk_at[j]] = (short)n[j];
+    }
+    if (DENSE) {
+      int c = abs(n[0]) + abs(n[1]);
+      if (__any_sync(FULL, c != 0)) {
+        c = __reduce_add_sync(FULL, c);
+        if (lane == 0) L.srow[k * TH + warp] = c;
+      }
     }
   }
 }
@@ -524,27 +570,50 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
   unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
   long long tprev = ctl->t_prev;
 
-  // Thread t owns tile pixels (slots in raster order) t and t + NTD.
+  // Dense: thread (warp w, lane l) owns tile pixels (l, w) and (l + 32, w);
+  // sparse: thread t owns tile pixels t and t + NTD for selection and the
+  // reference store.
+  int own[2];
   bool inimg[2];
+  int Rd[2], Cpd[2], Cnd[2];  // dense: the owned pixels' reference and thresholds
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const int s = tid + q * NTD;
-    const int x = tx0 + (s & (TW - 1)), y = ty0 + s / TW;
+    own[q] = SPARSE ? tid + q * NTD : warp * TW + lane + 32 * q;
+    const int x = tx0 + (own[q] & (TW - 1)), y = ty0 + own[q] / TW;
     inimg[q] = x < W && y < H;
+    Rd[q] = 0; Cpd[q] = p.cp; Cnd[q] = p.cn;
     if (inimg[q]) {
       const long long i = (long long)y * W + x;
-      if (!RESET) L.sR[s] = Rin[i];
-      if (MAPS) { L.sCp[s] = p.cpmap[i]; L.sCn[s] = p.cnmap[i]; }
+      if (SPARSE) {
+        if (!RESET) L.sR[own[q]] = Rin[i];
+        if (MAPS) { L.sCp[own[q]] = p.cpmap[i]; L.sCn[own[q]] = p.cnmap[i]; }
+      } else {
+        if (!RESET) Rd[q] = Rin[i];
+        if (MAPS) { Cpd[q] = p.cpmap[i]; Cnd[q] = p.cnmap[i]; }
+      }
     }
+  }
+  if (!SPARSE && tid == 0) {
+    for (int r = 0; r <= TH; ++r) s_rs[r] = r * TW;
   }
   int clamps = 0;
   long long act_sum = 0, act_n = 0;
   bool failed = false;
+  // halo buffers: `cb` will receive frame i; `pb` holds frame i-1 over the
+  // extent (phx, phy), or nothing yet (-1)
+  int* cb = L.sLb;
+  int* pb = L.sLa;
+  int phx = -1, phy = -1;
+  int hfx = 1, hfy = 1;  // fill extents only grow within a batch
   __syncthreads();  // the table, reference and thresholds above are read by all threads
 
   for (int fi = 0; fi < b.count && !failed; ++fi) {
     const FrameDesc cur = b.frames[fi];
     const FrameRef prv = prev_frame(p, b, fi, ringp);
+    FrameRef curf;
+    curf.ptr = cur.frame;
+    curf.pitch = cur.pitch;
+    curf.ch = p.ch;
     const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
     if (tid == 0) { s_fx = 0; s_fy = 0; }
     if (tid < N) {
@@ -553,61 +622,80 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
       const long long dt = cur.t_rel - tprev;
       L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
     }
+    for (int e = tid; e < N * TH; e += NTD) L.srow[e] = 0;
 
-    // 1. select and compact (raster order: slots 0..NTD-1 by q = 0 first)
+    // 1. the pixels to simulate
+    int A = 0;
     int sel_flag[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const int s = tid + q * NTD;
-      const int x = tx0 + (s & (TW - 1)), y = ty0 + s / TW;
+      const int x = tx0 + (own[q] & (TW - 1)), y = ty0 + own[q] / TW;
       bool a = inimg[q];
-      if (inimg[q]) {
+      if (inimg[q] && (SPARSE || fi == b.count - 1)) {
         const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
         if (fi == b.count - 1) ringn[(long long)y * W + x] = (unsigned char)vc;
         if (SPARSE) {
           const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
-          const int cp = MAPS ? (int)L.sCp[s] : p.cp, cn = MAPS ? (int)L.sCn[s] : p.cn;
+          const int cp = MAPS ? (int)L.sCp[own[q]] : p.cp, cn = MAPS ? (int)L.sCn[own[q]] : p.cn;
           a = abs(L.slut[vc] - L.slut[vp]) >= activity_threshold(p, cp, cn);
         }
       }
       sel_flag[q] = a ? 1 : 0;
     }
-    int A;
-    const int packed = block_excl_scan<NTD>(sel_flag[0] | (sel_flag[1] << 16), s_warp, &A);
-    const int A0 = A & 0xFFFF;
-    A = A0 + (A >> 16);
-    const int o0 = packed & 0xFFFF, o1 = A0 + (packed >> 16);
-    if (sel_flag[0]) L.sslot[o0] = (short)tid;
-    if (sel_flag[1]) L.sslot[o1] = (short)(tid + NTD);
-    // first slot of each row: rows 0..7 start at slots handled by q = 0, rows 8..15 by q = 1
-    if ((tid & (TW - 1)) == 0) {
-      const int r = tid / TW;
-      s_rs[r] = o0;
-      s_rs[r + NTD / TW] = o1;
+    if (SPARSE) {
+      // compaction in raster order: slots 0..NTD-1 (q = 0) come first
+      const int packed = block_excl_scan<NTD>(sel_flag[0] | (sel_flag[1] << 16), s_warp, &A);
+      const int A0 = A & 0xFFFF;
+      A = A0 + (A >> 16);
+      const int o0 = packed & 0xFFFF, o1 = A0 + (packed >> 16);
+      if (sel_flag[0]) L.sslot[o0] = (short)tid;
+      if (sel_flag[1]) L.sslot[o1] = (short)(tid + NTD);
+      if ((tid & (TW - 1)) == 0) {
+        const int r = tid / TW;
+        s_rs[r] = o0;
+        s_rs[r + NTD / TW] = o1;
+      }
+      if (tid == 0) s_rs[TH] = A;
+      __syncthreads();
+    } else {
+      A = TP;
     }
-    if (tid == 0) s_rs[TH] = A;
-    for (int e = tid; e < N * TH; e += NTD) L.srow[e] = 0;
     act_sum += A;
     act_n += (long long)A * N;
-    __syncthreads();
 
-    // 2. the thread's compacted pixels: j = tid, tid + NTD
-    int slot[2], Fx[2], Fy[2], R[2], Cp[2], Cn[2];
+    // 2. the simulated pixels of this thread, their flow; the tile's reach
+    int lx[2], ly[2], nk_at[2], Fx[2], Fy[2], R[2], Cp[2], Cn[2];
     bool act[2];
     unsigned mfx = 0, mfy = 0;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const int j = tid + q * NTD;
-      act[q] = j < A;
-      slot[q] = act[q] ? L.sslot[j] : 0;
-      Fx[q] = 0; Fy[q] = 0; R[q] = 0; Cp[q] = p.cp; Cn[q] = p.cn;
+      int slot;
+      if (SPARSE) {
+        const int j = tid + q * NTD;
+        act[q] = j < A;
+        slot = act[q] ? L.sslot[j] : 0;
+        nk_at[q] = j;
+      } else {
+        act[q] = inimg[q];
+        slot = own[q];
+        nk_at[q] = own[q];
+      }
+      lx[q] = slot & (TW - 1);
+      ly[q] = slot / TW;
+      Fx[q] = 0; Fy[q] = 0;
+      R[q] = SPARSE ? 0 : Rd[q];
+      Cp[q] = SPARSE ? p.cp : Cpd[q];
+      Cn[q] = SPARSE ? p.cn : Cnd[q];
       if (act[q]) {
-        const int x = tx0 + (slot[q] & (TW - 1)), y = ty0 + slot[q] / TW;
+        const int x = tx0 + lx[q], y = ty0 + ly[q];
         const float2 fl = cur.flow[(long long)y * W + x];
         Fx[q] = flow_q16(fl.x, clamps);
         Fy[q] = flow_q16(fl.y, clamps);
-        if (MAPS) { Cp[q] = L.sCp[slot[q]]; Cn[q] = L.sCn[slot[q]]; }
-        R[q] = RESET ? L.slut[load_luma(prv.ptr, prv.pitch, prv.ch, y, x)] : L.sR[slot[q]];
+        if (SPARSE) {
+          if (MAPS) { Cp[q] = L.sCp[slot]; Cn[q] = L.sCn[slot]; }
+          if (!RESET) R[q] = L.sR[slot];
+        }
+        if (RESET) R[q] = L.slut[load_luma(prv.ptr, prv.pitch, prv.ch, y, x)];
         mfx = max(mfx, (unsigned)abs(Fx[q]));
         mfy = max(mfy, (unsigned)abs(Fy[q]));
       }
@@ -623,67 +711,56 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
     const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
     const bool fast = hx <= HMAX && hy <= HMAX;
     if (fast && A > 0) {
-      // Replicate-padded halo tiles of both log frames.  The region is walked
-      // as a flat index (row = e / ncols by a multiply-high with
-      // ceil(2^32 / ncols), exact for e < 2^16), FILL loads in flight.
-      constexpr int FILL = 2;
-      const int c0 = HMAX - hx, ncols = TW + 2 * hx;
-      const int r0 = HMAX - hy, nrows = TH + 2 * hy;
-      const int total_fill = ncols * nrows;
-      const unsigned mcols = 0xFFFFFFFFu / (unsigned)ncols + 1u;
-      for (int e0 = 0; e0 < total_fill; e0 += NTD * FILL) {
-        int vp[FILL], vc[FILL], at[FILL];
-#pragma unroll
-        for (int q = 0; q < FILL; ++q) {
-          const int e = e0 + q * NTD + tid;
-          at[q] = -1;
-          if (e < total_fill) {
-            const int sr = (int)__umulhi((unsigned)e, mcols);
-            const int sc = e - sr * ncols;
-            const int gy = min(max(ty0 - hy + sr, 0), H - 1);
-            const int gx = min(max(tx0 - hx + sc, 0), W - 1);
-            vp[q] = load_luma(prv.ptr, prv.pitch, prv.ch, gy, gx);
-            vc[q] = load_luma(cur.frame, cur.pitch, p.ch, gy, gx);
-            at[q] = (r0 + sr) * SW + (c0 + sc);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < FILL; ++q) {
-          if (at[q] < 0) continue;
-          L.sL0[at[q]] = L.slut[vp[q]];
-          L.sL1[at[q]] = L.slut[vc[q]];
-        }
+      hfx = max(hfx, hx);
+      hfy = max(hfy, hy);
+      if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
+        fill_halo(pb, L.slut, prv, W, H, tx0, ty0, hfx, hfy);
+        phx = hfx;
+        phy = hfy;
       }
+      fill_halo(cb, L.slut, curf, W, H, tx0, ty0, hfx, hfy);
     }
     __syncthreads();
 
-    // 3. substeps (warps without a compacted pixel skip them)
-    if (warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
+    // 3. substeps (sparse: warps without a compacted pixel skip them)
+    const unsigned b0 = (unsigned)__cvta_generic_to_shared(pb);
+    const unsigned b1 = (unsigned)__cvta_generic_to_shared(cb);
+    if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
       if (fast)
-        tile_substeps<RESET, WIDE, true>(p, L, N, tx0, ty0, prv, cur, slot, act, Fx, Fy, R, Cp, Cn);
+        tile_substeps<RESET, WIDE, true, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, lx, ly,
+                                                  nk_at, act, Fx, Fy, R, Cp, Cn);
       else
-        tile_substeps<RESET, WIDE, false>(p, L, N, tx0, ty0, prv, cur, slot, act, Fx, Fy, R, Cp, Cn);
+        tile_substeps<RESET, WIDE, false, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, lx, ly,
+                                                   nk_at, act, Fx, Fy, R, Cp, Cn);
     }
     if (!RESET) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
-        if (act[q]) L.sR[slot[q]] = R[q];
-    }
-    __syncthreads();
-
-    // 4. events per (substep, row): warp r sums its row's slots
-    if (warp < TH) {
-      const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
-      for (int k = 0; k < N; ++k) {
-        int c = 0;
-        for (int j = s0 + lane; j < s1; j += 32) c += abs((int)L.snk[k * TP + j]);
-        if (__any_sync(FULL, c != 0)) {
-          c = __reduce_add_sync(FULL, c);
-          if (lane == 0) L.srow[k * TH + r] = c;
+      for (int q = 0; q < 2; ++q) {
+        if (SPARSE) {
+          if (act[q]) L.sR[lx[q] + ly[q] * TW] = R[q];
+        } else {
+          Rd[q] = R[q];
         }
       }
     }
     __syncthreads();
+
+    // 4. sparse: events per (substep, row) from the records of the row's slots
+    static_assert(NTD / 32 == TH, "one warp per tile row");
+    if (SPARSE) {
+      const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
+      if (s1 > s0) {
+        for (int k = 0; k < N; ++k) {
+          int c = 0;
+          for (int j = s0 + lane; j < s1; j += 32) c += abs((int)L.snk[k * TP + j]);
+          if (__any_sync(FULL, c != 0)) {
+            c = __reduce_add_sync(FULL, c);
+            if (lane == 0) L.srow[k * TH + r] = c;
+          }
+        }
+      }
+      __syncthreads();
+    }
     const int E = N * TH;
     int total;
     const long long base = stage_segments<NTD>(p, L.srow, L.soff, E, s_warp, &s_base, &total);
@@ -695,7 +772,7 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
         segf[(long long)k * p.segs_per_k + (long long)yy * p.tiles_x + tcx] =
             make_int2(fail ? 0 : L.srow[e], (int)(fail ? 0 : base) + L.soff[e]);
     }
-    if (!fail && total > 0 && warp < TH) {
+    if (!fail && total > 0) {
       // Emission: warp r writes its row's events, substep by substep, in
       // column order (the row's slots are contiguous and in raster order).
       const unsigned lt = lanemask_lt();
@@ -710,7 +787,7 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
           const int j = j0 + lane;
           const int n = j < s1 ? L.snk[k * TP + j] : 0;
           const int a = abs(n);
-          const int x = tx0 + (j < s1 ? (L.sslot[j] & (TW - 1)) : 0);
+          const int x = tx0 + (SPARSE ? (j < s1 ? (L.sslot[j] & (TW - 1)) : 0) : (j & (TW - 1)));
           const Ev ev = make_event(tk, x, y, n > 0);
           int seg_total;
           if (__all_sync(FULL, a <= 1)) {
@@ -728,6 +805,17 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
     }
     failed = fail;
     tprev = cur.t_rel;
+    // frame i's halo becomes the previous-frame halo of frame i + 1
+    if (fast && A > 0) {
+      int* t = pb;
+      pb = cb;
+      cb = t;
+      phx = hfx;
+      phy = hfy;
+    } else {
+      phx = -1;
+      phy = -1;
+    }
     __syncthreads();
   }
 
@@ -735,8 +823,8 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!inimg[q]) continue;
-      const int s = tid + q * NTD;
-      Rout[(long long)(ty0 + s / TW) * W + tx0 + (s & (TW - 1))] = L.sR[s];
+      Rout[(long long)(ty0 + own[q] / TW) * W + tx0 + (own[q] & (TW - 1))] =
+          SPARSE ? L.sR[own[q]] : Rd[q];
     }
   }
   clamps = __reduce_add_sync(FULL, clamps);
