@@ -94,7 +94,7 @@ typedef struct {
   int32_t c_neg_q16;         /* uniform |C_neg|, Q16 */
   int32_t c_act_q16;         /* sparse activity threshold, Q16; < 0: min(Cp(x), Cn(x)) */
   int32_t max_batch;         /* frames per device batch (<= SIM_MAX_BATCH); 0: what a
-                                256 MB segment table holds */
+                                512 MB segment table holds */
   const uint16_t* c_pos_map; /* optional host W*H Q16 per-pixel C_pos (copied at create) */
   const uint16_t* c_neg_map; /* optional host W*H Q16 per-pixel |C_neg| */
   int64_t event_capacity;    /* device event buffer (events); 0: default max(2^20, 8 W H) */

@@ -21,9 +21,8 @@ constexpr int HMAX = 16;
 constexpr int SW = TW + 2 * HMAX;  // shared tile stride (int32 elements)
 constexpr int SH = TH + 2 * HMAX;
 constexpr int MAXN = 64;           // largest substep count
-// Order kernel: segments per chunk (four per thread).
-constexpr int OPER = 4;
-constexpr int OCHUNK = OPER * NT;
+// Order kernel: segments per chunk (one per thread).
+constexpr int OCHUNK = NT;
 
 // Look-back status word: [epoch:32][flag:2][value:30].
 constexpr unsigned long long LB_AGG = 1ull << 30;
@@ -77,6 +76,18 @@ struct Ev {  // same layout as sim_event
   unsigned int xyp;  // x | (yp << 16)
 };
 
+// The events of one segment: one (frame, substep, tile row).  When no pixel
+// of the row crossed more than one threshold in the substep (src < 0), the
+// events are bit b of `mask` (pixel tx0 + b has an event) with polarity bit b
+// of `pol`; the order kernel materialises them.  Otherwise the tile kernel
+// wrote the row's `cnt` events to staging at `src`.
+struct Seg {
+  unsigned long long mask;
+  unsigned long long pol;
+  int cnt;
+  int src;
+};
+
 // Everything the kernels need about one stream (fixed for its lifetime).
 struct SimParams {
   int W, H, ch;
@@ -96,7 +107,7 @@ struct SimParams {
   unsigned long long* maxf2;    // [bmax] adaptive: max squared Q16 flow per frame
   Ev* staging;
   long long stage_cap;
-  int2* seg;                    // (count, staging offset) per (frame, substep, segment)
+  Seg* seg;                     // per (frame, substep, tile row)
   long long segs_per_k;         // segments per substep of one frame
   unsigned long long* order_status;
   Ev* events;

@@ -14,15 +14,15 @@
 // never wait for each other, so the grid may exceed the resident capacity.
 //
 // Event order.  Within a frame, events are ordered by (substep, row, column,
-// repeat); frames follow each other.  The simulating kernels work
-// pixel-major, so they record each pixel's per-substep count in shared
-// memory, write their events to a staging area in their own local order and
-// publish one (count, staging offset) entry per "segment" (dense: one row of
-// a 64 x 16 tile; sparse: the active pixels of one chunk of 1024 raster
-// pixels) per substep and frame.  The order kernel scans the batch's segment
-// counts in output order (a single-pass scan with decoupled look-back),
-// gathers the events into the stream's event buffer, and the block that
-// finishes the last chunk commits the whole batch.
+// repeat); frames follow each other.  The simulating kernel works
+// pixel-major and publishes one "segment" per (frame, substep, row of a
+// 64 x 16 tile): the row's event and polarity bit masks, or - when a pixel
+// of the row crossed more than one threshold in the substep - the row's
+// events written to a staging area.  The order kernel scans the batch's
+// segment counts in output order (a single-pass scan with decoupled
+// look-back), writes the events into the stream's event buffer (expanding
+// the masks, copying the staged rows), and the block that finishes the last
+// chunk commits the whole batch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -294,48 +294,6 @@ __device__ __forceinline__ FrameRef prev_frame(const SimParams& p, const BatchAr
   return r;
 }
 
-// Tile-local offsets of `E` segment counts (substep-major), staging allocation.
-// Returns the staging base, or -1 when the staging area is exhausted (the
-// batch then fails and emits nothing more).
-template <int NTH = NT>
-__device__ __forceinline__ long long stage_segments(const SimParams& p, const int* cnt, int* off,
-                                                    int E, int* s_warp, long long* s_base,
-                                                    int* total_out) {
-  const int tid = threadIdx.x;
-  constexpr int PER = 2048 / NTH;  // entries per thread (E <= 2048)
-  int v[PER], sum = 0;
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int e = PER * tid + q;
-    v[q] = e < E ? cnt[e] : 0;
-    sum += v[q];
-  }
-  int total;
-  int ex = block_excl_scan<NTH>(sum, s_warp, &total);
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int e = PER * tid + q;
-    if (e < E) off[e] = ex;
-    ex += v[q];
-  }
-  if (tid == 0) {
-    long long base = 0;
-    if (total > 0) {
-      const unsigned long long bb = atomicAdd(&p.ctl->stage_top, (unsigned long long)total);
-      if (bb + (unsigned long long)total > (unsigned long long)p.stage_cap) {
-        base = -1;
-        atomicExch(&p.ctl->batch_fail, 1);
-      } else {
-        base = (long long)bb;
-      }
-    }
-    *s_base = base;
-  }
-  __syncthreads();
-  *total_out = total;
-  return *s_base;
-}
-
 // ---------------------------------------------------------------------------
 // frame 0 of a stream: fill the frame ring and the reference
 
@@ -402,11 +360,10 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, BatchArg b) {
 //      halo of both log frames in shared memory.  Frame i's halo is kept as
 //      the next frame's previous-frame halo whenever its extent suffices, so
 //      usually one frame is loaded per frame;
-//   3. every simulated pixel runs through the N substeps, recording each
-//      pixel-substep's signed event count;
-//   4. the tile's events are written to staging in (substep, row, column)
-//      order and one segment entry per (substep, row) is published for the
-//      order kernel.
+//   3. every simulated pixel runs through the N substeps;
+//   4. for each (substep, tile row) one segment is published: the row's event
+//      and polarity bit masks, or, when a pixel of the row crossed more than
+//      one threshold, the row's events written to staging in column order.
 
 __device__ __forceinline__ int activity_threshold(const SimParams& p, int cp, int cn) {
   return p.cact >= 0 ? p.cact : min(cp, cn);
@@ -419,11 +376,9 @@ struct TileLayout {
   int* sLb;
   int* slut;
   int* sR;               // [TP] sparse: the tile's reference
-  int* srow;             // [N][TH] events per (substep, tile row)
-  int* soff;             // [N][TH] tile-local exclusive offsets
   unsigned* stk;
   int* swk;
-  short* snk;            // [N][TP] signed event count per (substep, slot)
+  short* snk;            // [N][TP] sparse: signed event count per (substep, slot)
   short* sslot;          // [TP] sparse: tile pixel index (ty * TW + tx) of each slot
   unsigned short* sCp;   // [TP] sparse: per-pixel thresholds (maps)
   unsigned short* sCn;
@@ -435,9 +390,7 @@ __device__ __forceinline__ TileLayout tile_layout(unsigned char* raw, int nmax) 
   L.sLb = L.sLa + SH * SW;
   L.slut = L.sLb + SH * SW;
   L.sR = L.slut + 256;
-  L.srow = L.sR + TP;
-  L.soff = L.srow + nmax * TH;
-  L.stk = (unsigned*)(L.soff + nmax * TH);
+  L.stk = (unsigned*)(L.sR + TP);
   L.swk = (int*)(L.stk + nmax);
   L.snk = (short*)(L.swk + nmax);
   L.sslot = L.snk + nmax * TP;
@@ -478,20 +431,77 @@ __device__ __forceinline__ void fill_halo(int* dst, const int* slut, const Frame
   }
 }
 
+// Publish the segment of one (substep, tile row) from a warp that holds the
+// row's pixels in two 32-lane halves: lanes' event counts n_lo (columns
+// col_lo) and n_hi (columns col_hi); columns are the bit positions in the
+// segment masks and must increase with the lane within each half, the lo
+// half preceding the hi half.  A row with a multi-crossing pixel stages its
+// events (column order, repeats adjacent).  All 32 lanes must call this.
+__device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_lo, int col_lo,
+                                            bool v_lo, int n_hi, int col_hi, bool v_hi,
+                                            unsigned tk, int tx0, int y) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b_lo = v_lo && n_lo ? 1u << (col_lo & 31) : 0u;
+  const unsigned b_hi = v_hi && n_hi ? 1u << (col_hi & 31) : 0u;
+  const bool lo_in_low = col_lo < 32, hi_in_low = col_hi < 32;
+  const unsigned m_any = __ballot_sync(FULL, (v_lo && n_lo) || (v_hi && n_hi));
+  if (m_any == 0) {
+    if (lane == 0) *sg = Seg{0ull, 0ull, 0, -1};
+    return;
+  }
+  const unsigned low = __reduce_or_sync(FULL, (lo_in_low ? b_lo : 0u) | (hi_in_low ? b_hi : 0u));
+  const unsigned high = __reduce_or_sync(FULL, (lo_in_low ? 0u : b_lo) | (hi_in_low ? 0u : b_hi));
+  const unsigned plow = __reduce_or_sync(FULL, (lo_in_low && n_lo > 0 ? b_lo : 0u) |
+                                                   (hi_in_low && n_hi > 0 ? b_hi : 0u));
+  const unsigned phigh = __reduce_or_sync(FULL, (!lo_in_low && n_lo > 0 ? b_lo : 0u) |
+                                                    (!hi_in_low && n_hi > 0 ? b_hi : 0u));
+  const int a_lo = v_lo ? abs(n_lo) : 0, a_hi = v_hi ? abs(n_hi) : 0;
+  if (!__any_sync(FULL, a_lo > 1 || a_hi > 1)) {
+    if (lane == 0)
+      *sg = Seg{(unsigned long long)low | ((unsigned long long)high << 32),
+                (unsigned long long)plow | ((unsigned long long)phigh << 32),
+                __popc(low) + __popc(high), -1};
+    return;
+  }
+  // rare: stage the row's events explicitly
+  const int i_lo = warp_incl_scan(a_lo);
+  const int t_lo = __shfl_sync(FULL, i_lo, 31);
+  const int i_hi = warp_incl_scan(a_hi);
+  const int total = t_lo + __shfl_sync(FULL, i_hi, 31);
+  long long base = 0;
+  if (lane == 0) {
+    const unsigned long long b = atomicAdd(&p.ctl->stage_top, (unsigned long long)total);
+    if (b + (unsigned long long)total > (unsigned long long)p.stage_cap) {
+      base = -1;
+      atomicExch(&p.ctl->batch_fail, 1);
+    } else {
+      base = (long long)b;
+    }
+  }
+  base = __shfl_sync(FULL, base, 0);
+  if (base >= 0) {
+    const Ev e_lo = make_event(tk, tx0 + col_lo, y, n_lo > 0);
+    const Ev e_hi = make_event(tk, tx0 + col_hi, y, n_hi > 0);
+    for (int m = 0; m < a_lo; ++m) p.staging[base + i_lo - a_lo + m] = e_lo;
+    for (int m = 0; m < a_hi; ++m) p.staging[base + t_lo + i_hi - a_hi + m] = e_hi;
+  }
+  if (lane == 0) *sg = Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1};
+}
+
 // The substeps of the (up to) two pixels of this thread.  `lx, ly` are the
 // pixels' tile coordinates, `nk_at` their columns in the per-substep record.
 // DENSE: the two pixels are columns lane, lane + 32 of tile row `warp`, and the
-// row's event count is reduced over the warp in the loop.
+// row's segment is published from the loop.
 template <bool RESET, bool WIDE, bool FAST, bool DENSE>
 __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
                                               int tx0, int ty0, unsigned b0, unsigned b1,
                                               const FrameRef& prv, const FrameDesc& cur,
-                                              const int (&lx)[2], const int (&ly)[2],
+                                              Seg* segf, const int (&lx)[2], const int (&ly)[2],
                                               const int (&nk_at)[2], const bool (&act)[2],
                                               const int (&Fx)[2], const int (&Fy)[2],
                                               int (&R)[2], const int (&Cp)[2],
                                               const int (&Cn)[2]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -509,6 +519,8 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
     ax[j] = 0;
     ay[j] = 0;
   }
+  const int y = ty0 + warp;
+  const bool row_in = !DENSE || y < p.H;
   for (int k = 0; k < N; ++k) {
     const int w = L.swk[k];
     int n[2];
@@ -532,15 +544,11 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
       const int I = lerp12<WIDE>(s0, s1, w);
       n[j] = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
       if (!act[j]) n[j] = 0;
-      L.snk[k * TP + nk_at[j]] = (short)n[j];
+      if (!DENSE) L.snk[k * TP + nk_at[j]] = (short)n[j];
     }
-    if (DENSE) {
-      int c = abs(n[0]) + abs(n[1]);
-      if (__any_sync(FULL, c != 0)) {
-        c = __reduce_add_sync(FULL, c);
-        if (lane == 0) L.srow[k * TH + warp] = c;
-      }
-    }
+    if (DENSE && row_in)  // warp-uniform
+      publish_row(p, segf + (long long)k * p.segs_per_k + warp * p.tiles_x, n[0], lx[0], true,
+                  n[1], lx[1], true, L.stk[k], tx0, y);
   }
 }
 
@@ -550,7 +558,6 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
   __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy;
   __shared__ int s_rs[TH + 1];  // first slot of each tile row
-  __shared__ long long s_base;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
 
@@ -593,12 +600,8 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
       }
     }
   }
-  if (!SPARSE && tid == 0) {
-    for (int r = 0; r <= TH; ++r) s_rs[r] = r * TW;
-  }
   int clamps = 0;
   long long act_sum = 0, act_n = 0;
-  bool failed = false;
   // halo buffers: `cb` will receive frame i; `pb` holds frame i-1 over the
   // extent (phx, phy), or nothing yet (-1)
   int* cb = L.sLb;
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
   int hfx = 1, hfy = 1;  // fill extents only grow within a batch
   __syncthreads();  // the table, reference and thresholds above are read by all threads
 
-  for (int fi = 0; fi < b.count && !failed; ++fi) {
+  for (int fi = 0; fi < b.count; ++fi) {
     const FrameDesc cur = b.frames[fi];
     const FrameRef prv = prev_frame(p, b, fi, ringp);
     FrameRef curf;
@@ -615,6 +618,7 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
     curf.pitch = cur.pitch;
     curf.ch = p.ch;
     const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
+    Seg* segf = p.seg + (long long)fi * nmax * p.segs_per_k + (long long)ty0 * p.tiles_x + tcx;
     if (tid == 0) { s_fx = 0; s_fy = 0; }
     if (tid < N) {
       const int k = tid + 1;
@@ -622,7 +626,6 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
       const long long dt = cur.t_rel - tprev;
       L.stk[tid] = (unsigned)(tprev + (k * dt) / N);
     }
-    for (int e = tid; e < N * TH; e += NTD) L.srow[e] = 0;
 
     // 1. the pixels to simulate
     int A = 0;
@@ -722,16 +725,17 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
     }
     __syncthreads();
 
-    // 3. substeps (sparse: warps without a compacted pixel skip them)
+    // 3. substeps (sparse: warps without a compacted pixel skip them); dense
+    // rows publish their segments from the loop
     const unsigned b0 = (unsigned)__cvta_generic_to_shared(pb);
     const unsigned b1 = (unsigned)__cvta_generic_to_shared(cb);
     if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
       if (fast)
-        tile_substeps<RESET, WIDE, true, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, lx, ly,
-                                                  nk_at, act, Fx, Fy, R, Cp, Cn);
+        tile_substeps<RESET, WIDE, true, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, segf,
+                                                  lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn);
       else
-        tile_substeps<RESET, WIDE, false, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, lx, ly,
-                                                   nk_at, act, Fx, Fy, R, Cp, Cn);
+        tile_substeps<RESET, WIDE, false, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, segf,
+                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn);
     }
     if (!RESET) {
 #pragma unroll
@@ -743,67 +747,32 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
         }
       }
     }
-    __syncthreads();
 
-    // 4. sparse: events per (substep, row) from the records of the row's slots
+    // 4. sparse: warp r publishes the segments of tile row r from the
+    // records of the row's slots (contiguous, in column order)
     static_assert(NTD / 32 == TH, "one warp per tile row");
     if (SPARSE) {
-      const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
-      if (s1 > s0) {
-        for (int k = 0; k < N; ++k) {
-          int c = 0;
-          for (int j = s0 + lane; j < s1; j += 32) c += abs((int)L.snk[k * TP + j]);
-          if (__any_sync(FULL, c != 0)) {
-            c = __reduce_add_sync(FULL, c);
-            if (lane == 0) L.srow[k * TH + r] = c;
-          }
-        }
-      }
       __syncthreads();
-    }
-    const int E = N * TH;
-    int total;
-    const long long base = stage_segments<NTD>(p, L.srow, L.soff, E, s_warp, &s_base, &total);
-    const bool fail = base < 0;
-    int2* segf = p.seg + (long long)fi * nmax * p.segs_per_k;
-    for (int e = tid; e < E; e += NTD) {
-      const int k = e / TH, ty = e % TH, yy = ty0 + ty;
-      if (yy < H)
-        segf[(long long)k * p.segs_per_k + (long long)yy * p.tiles_x + tcx] =
-            make_int2(fail ? 0 : L.srow[e], (int)(fail ? 0 : base) + L.soff[e]);
-    }
-    if (!fail && total > 0) {
-      // Emission: warp r writes its row's events, substep by substep, in
-      // column order (the row's slots are contiguous and in raster order).
-      const unsigned lt = lanemask_lt();
       const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
       const int y = ty0 + r;
-      for (int k = 0; k < N; ++k) {
-        const int e = k * TH + r;
-        if (L.srow[e] == 0) continue;
-        const unsigned tk = L.stk[k];
-        long long o = base + L.soff[e];
-        for (int j0 = s0; j0 < s1; j0 += 32) {
-          const int j = j0 + lane;
-          const int n = j < s1 ? L.snk[k * TP + j] : 0;
-          const int a = abs(n);
-          const int x = tx0 + (SPARSE ? (j < s1 ? (L.sslot[j] & (TW - 1)) : 0) : (j & (TW - 1)));
-          const Ev ev = make_event(tk, x, y, n > 0);
-          int seg_total;
-          if (__all_sync(FULL, a <= 1)) {
-            const unsigned bb = __ballot_sync(FULL, a != 0);
-            if (a) p.staging[o + __popc(bb & lt)] = ev;
-            seg_total = __popc(bb);
-          } else {
-            const int ia = warp_incl_scan(a);
-            for (int m = 0; m < a; ++m) p.staging[o + ia - a + m] = ev;
-            seg_total = __shfl_sync(FULL, ia, 31);
+      if (y < H) {
+        if (s1 == s0) {
+          for (int k = lane; k < N; k += 32) segf[(long long)k * p.segs_per_k + r * p.tiles_x] =
+              Seg{0ull, 0ull, 0, -1};
+        } else {
+          const int j_lo = s0 + lane, j_hi = s0 + 32 + lane;
+          const bool v_lo = j_lo < s1, v_hi = j_hi < s1;
+          const int col_lo = v_lo ? (L.sslot[j_lo] & (TW - 1)) : 0;
+          const int col_hi = v_hi ? (L.sslot[j_hi] & (TW - 1)) : 0;
+          for (int k = 0; k < N; ++k) {
+            const int n_lo = v_lo ? L.snk[k * TP + j_lo] : 0;
+            const int n_hi = v_hi ? L.snk[k * TP + j_hi] : 0;
+            publish_row(p, segf + (long long)k * p.segs_per_k + r * p.tiles_x, n_lo, col_lo, v_lo,
+                        n_hi, col_hi, v_hi, L.stk[k], tx0, y);
           }
-          o += seg_total;
         }
       }
     }
-    failed = fail;
     tprev = cur.t_rel;
     // frame i's halo becomes the previous-frame halo of frame i + 1
     if (fast && A > 0) {
@@ -819,7 +788,7 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
     __syncthreads();
   }
 
-  if (!RESET && !failed) {
+  if (!RESET) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!inimg[q]) continue;
@@ -877,12 +846,26 @@ __global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, BatchArg b) {
 
 // ---------------------------------------------------------------------------
 // order: scan the segment counts of the whole batch in output order (frame,
-// substep, segment), gather the events from staging into the event buffer,
-// and commit the batch (all of its frames, or none).
+// substep, row, tile column), write the events into the event buffer (from
+// the segments' bit masks, or copied from staging), and commit the batch
+// (all of its frames, or none).
+
+// Position of the m-th (0-based) set bit of a 64-bit mask that has more than
+// m set bits.
+__device__ __forceinline__ int nth_set_bit(unsigned long long mask, int m) {
+  const unsigned lo = (unsigned)mask, hi = (unsigned)(mask >> 32);
+  const int c = __popc(lo);
+  if (m < c) return (int)__fns(lo, 0, m + 1);
+  return 32 + (int)__fns(hi, 0, m - c + 1);
+}
 
 __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
   __shared__ int s_ex[OCHUNK];
   __shared__ int s_src[OCHUNK];
+  __shared__ unsigned long long s_mask[OCHUNK];
+  __shared__ unsigned long long s_pol[OCHUNK];
+  __shared__ unsigned s_t[OCHUNK];
+  __shared__ unsigned s_xy[OCHUNK];  // x0 | (y << 16)
   __shared__ int s_N[1024];
   __shared__ int s_warp[NWARP + 1];
   __shared__ int s_c, s_last, s_ok;
@@ -898,6 +881,7 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
   const long long nseg = (long long)b.count * per_frame;
   const int nchunks = (int)max(1LL, (nseg + OCHUNK - 1) / OCHUNK);
   const long long cursor = ctl->cursor;
+  const long long t_first = ctl->t_prev;  // t of the frame before the batch
   __syncthreads();
 
   for (;;) {
@@ -905,32 +889,39 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
     __syncthreads();
     const int c = s_c;
     if (c >= nchunks) break;
-    // four consecutive segments per thread; segments of substeps k >= N of
-    // their frame were never written and count zero
-    const long long s0 = (long long)c * OCHUNK + OPER * tid;
-    long long fi = s0 / per_frame;
-    long long rem = s0 - fi * per_frame;
-    int cnt[OPER], src[OPER], sum = 0;
-#pragma unroll
-    for (int q = 0; q < OPER; ++q) {
-      cnt[q] = 0;
-      src[q] = 0;
-      if (s0 + q < nseg && rem / S < s_N[fi]) {
-        const int2 e = p.seg[s0 + q];
-        cnt[q] = e.x;
-        src[q] = e.y;
+    // one segment per thread; segments of substeps k >= N of their frame were
+    // never written and count zero
+    const long long si = (long long)c * OCHUNK + tid;
+    int cnt = 0, src = -1;
+    unsigned long long mask = 0, pol = 0;
+    unsigned tk = 0, xy = 0;
+    if (si < nseg) {
+      const int fi = (int)(si / per_frame);
+      const long long rem = si - (long long)fi * per_frame;
+      const int k = (int)(rem / S);
+      const int N = s_N[fi];
+      if (k < N) {
+        const Seg sg = p.seg[si];
+        cnt = sg.cnt;
+        src = sg.src;
+        mask = sg.mask;
+        pol = sg.pol;
+        const int rs = (int)(rem - (long long)k * S);
+        const int y = rs / p.tiles_x, tc = rs - y * p.tiles_x;
+        xy = (unsigned)(tc * TW) | ((unsigned)y << 16);
+        const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
+        const long long dt = b.frames[fi].t_rel - tp;
+        tk = (unsigned)(tp + ((long long)(k + 1) * dt) / N);
       }
-      sum += cnt[q];
-      if (++rem == per_frame) { rem = 0; ++fi; }
     }
     int total;
-    int ex = block_excl_scan(sum, s_warp, &total);
-#pragma unroll
-    for (int q = 0; q < OPER; ++q) {
-      s_ex[OPER * tid + q] = ex;
-      s_src[OPER * tid + q] = src[q];
-      ex += cnt[q];
-    }
+    const int ex = block_excl_scan(cnt, s_warp, &total);
+    s_ex[tid] = ex;
+    s_src[tid] = src;
+    s_mask[tid] = mask;
+    s_pol[tid] = pol;
+    s_t[tid] = tk;
+    s_xy[tid] = xy;
     if (tid < 32) {
       const long long ex0 = lookback_warp(p.order_status, c, b.serial, total, &ctl->err);
       if (tid == 0) s_prefix = ex0;
@@ -944,7 +935,18 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
         if (s_ex[mid] <= jj) lo = mid; else hi = mid;
       }
       const long long dst = base + jj;
-      if (dst < p.event_cap) p.events[dst] = p.staging[(long long)s_src[lo] + (jj - s_ex[lo])];
+      if (dst >= p.event_cap) continue;
+      const int m = jj - s_ex[lo];
+      Ev ev;
+      if (s_src[lo] >= 0) {
+        ev = p.staging[(long long)s_src[lo] + m];
+      } else {
+        const int bit = nth_set_bit(s_mask[lo], m);
+        const unsigned xy0 = s_xy[lo];
+        ev = make_event(s_t[lo], (int)(xy0 & 0xFFFF) + bit, (int)(xy0 >> 16),
+                        (s_pol[lo] >> bit) & 1ull);
+      }
+      p.events[dst] = ev;
     }
     __syncthreads();
     if (tid == 0) {
@@ -1030,8 +1032,7 @@ cudaError_t launch_tile_mode(const SimParams& p, const BatchArg& b, cudaStream_t
 }  // namespace
 
 size_t tile_smem_bytes(int n_max) {
-  return (size_t)(2 * SH * SW + 256 + TP + 2 * n_max * TH + 2 * n_max) * 4 +
-         (size_t)(n_max * TP + 3 * TP) * 2;
+  return (size_t)(2 * SH * SW + 256 + TP + 2 * n_max) * 4 + (size_t)(n_max * TP + 3 * TP) * 2;
 }
 
 int device_sm_count() {

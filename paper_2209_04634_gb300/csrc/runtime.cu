@@ -43,7 +43,7 @@ struct sim_s {
   unsigned long long* d_maxf2 = nullptr;
   Ev* d_staging = nullptr;
   Ev* d_events = nullptr;
-  int2* d_seg = nullptr;
+  evsim::Seg* d_seg = nullptr;
   unsigned long long* d_order_status = nullptr;
   evsim::FrameDesc* d_desc = nullptr;       // bmax descriptors of the batch in flight
   unsigned char* d_stage_frames = nullptr;  // host batches: staged frames and flows
@@ -375,10 +375,10 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   const bool sparse = c.mode == SIM_SPARSE;
   (void)sparse;
   s->segs_per_k = (long long)c.height * s->tiles_x;  // one segment per tile row
-  // frames per batch: the requested cap, else what a 256 MB segment table holds
-  const long long seg_bytes_per_frame = s->segs_per_k * s->n_max * (long long)sizeof(int2);
+  // frames per batch: the requested cap, else what a 512 MB segment table holds
+  const long long seg_bytes_per_frame = s->segs_per_k * s->n_max * (long long)sizeof(evsim::Seg);
   long long bm = c.max_batch > 0 ? c.max_batch
-                                 : std::max(1LL, (256LL << 20) / std::max(1LL, seg_bytes_per_frame));
+                                 : std::max(1LL, (512LL << 20) / std::max(1LL, seg_bytes_per_frame));
   s->bmax = (int)std::min<long long>(bm, SIM_MAX_BATCH);
   const long long seg_cap = (long long)s->bmax * s->n_max * s->segs_per_k;
   const long long ochunks = std::max(1LL, (seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
