@@ -312,17 +312,16 @@ __global__ void k_init(SimParams p, FrameDesc f) {
 // adaptive N (dense): max over all pixels of the squared Q16 flow, per frame
 // of the batch (blockIdx.y = frame)
 
-__global__ void __launch_bounds__(NT) k_flowmax(SimParams p, BatchArg b) {
+__device__ __forceinline__ void flowmax_run(const SimParams& p, const BatchArg& b, int i, int bx,
+                                            int nbx) {
   if (block_error(&p.ctl->err)) return;
-  const int i = blockIdx.y;
   const FrameDesc f = b.frames[i];
   __shared__ unsigned long long s_m[NWARP];
   constexpr int U = 8;  // independent loads in flight per thread
   const long long P = (long long)p.W * p.H;
   unsigned long long m = 0;
   int dummy = 0;
-  for (long long i0 = blockIdx.x * (long long)NT * U + threadIdx.x; i0 < P;
-       i0 += (long long)gridDim.x * NT * U) {
+  for (long long i0 = bx * (long long)NT * U + threadIdx.x; i0 < P; i0 += (long long)nbx * NT * U) {
     float2 fl[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
@@ -344,6 +343,10 @@ __global__ void __launch_bounds__(NT) k_flowmax(SimParams p, BatchArg b) {
     for (int w = 0; w < NWARP; ++w) bm = s_m[w] > bm ? s_m[w] : bm;
     if (bm) atomicMax(&p.maxf2[i], bm);
   }
+}
+
+__global__ void __launch_bounds__(NT) k_flowmax(SimParams p, BatchArg b) {
+  flowmax_run(p, b, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -553,7 +556,7 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
 }
 
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
-__global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
+__device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, int tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy;
@@ -564,7 +567,6 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
   const TileLayout L = tile_layout(smem_raw, nmax);
-  const int tile = blockIdx.x;
   const int tcx = tile % p.tiles_x, tcy = tile / p.tiles_x;
   const int tx0 = tcx * TW, ty0 = tcy * TH;
   const int W = p.W, H = p.H;
@@ -804,15 +806,20 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
   }
 }
 
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+__global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
+  tile_run<RESET, MAPS, WIDE, SPARSE>(p, b, blockIdx.x);
+}
+
 // Adaptive N for the sparse method: max squared flow over the active pixels
-// of each frame (blockIdx.y = frame).
-__global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, BatchArg b) {
+// of each frame.
+__device__ __forceinline__ void sparse_pre_run(const SimParams& p, const BatchArg& b, int fi,
+                                               int bx, int nbx) {
   __shared__ int slut[256];
   __shared__ unsigned long long s_m[NWARP];
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
   const int tid = threadIdx.x;
-  const int fi = blockIdx.y;
   slut[tid] = p.lut[tid];
   __syncthreads();
   const unsigned char* ringp = (ctl->sel & 2) ? p.ring1 : p.ring0;
@@ -821,7 +828,7 @@ __global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, BatchArg b) {
   const long long P = (long long)p.W * p.H;
   unsigned long long m = 0;
   int dummy = 0;
-  for (long long i = blockIdx.x * (long long)NT + tid; i < P; i += (long long)gridDim.x * NT) {
+  for (long long i = bx * (long long)NT + tid; i < P; i += (long long)nbx * NT) {
     const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
     const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
     const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
@@ -842,6 +849,10 @@ __global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, BatchArg b) {
     for (int w = 0; w < NWARP; ++w) bm = s_m[w] > bm ? s_m[w] : bm;
     if (bm) atomicMax(&p.maxf2[fi], bm);
   }
+}
+
+__global__ void __launch_bounds__(NT) k_sparse_pre(SimParams p, BatchArg b) {
+  sparse_pre_run(p, b, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
