@@ -60,6 +60,7 @@ extern "C" {
 #define SIM_ERR_STATE (-8)         /* call not valid in the handle's state */
 #define SIM_ERR_ADMIT (-9)         /* batch: admission refused (memory budget / slots) */
 #define SIM_ERR_NO_DEVICE (-10)    /* no usable CUDA device / kernel image */
+#define SIM_ERR_TOO_LARGE (-11)    /* sim_step_pair_static: problem exceeds its scratch */
 
 /* ---- enumerations ------------------------------------------------------- */
 enum { SIM_LUMA8 = 1, SIM_RGB8 = 3 };          /* bytes per input pixel */
@@ -206,6 +207,68 @@ const char* sim_last_cuda_error(void);
 
 /* Library version, "major.minor.patch". */
 const char* sim_version(void);
+
+/* ---- allocation-free frame pair ------------------------------------------
+ * The paper has no counterpart: this is a library service for callers that
+ * must not allocate device memory while they run, such as code whose device
+ * memory belongs to another framework's caching allocator (a raw cudaMalloc
+ * bypasses and fragments that pool, and cudaFree synchronises the whole
+ * device), frame-rate pipelines with a no-allocation rule after start-up
+ * (cudaMalloc / cudaFree have unbounded latency), or plug-ins that are handed
+ * device buffers by their host application and may not allocate their own.
+ *
+ * One step of the simulation from camera frame i-1 to frame i, with the same
+ * arithmetic and event order as a sim_t handle that was given frame i-1 and
+ * then frame i.  All inputs and outputs are the caller's device memory; every
+ * scratch buffer the kernels use (control block, log table, luma frames,
+ * segment table, staging, look-back words) is carved out of one file-scope
+ * device array of SIM_STATIC_SCRATCH_BYTES per device.  The call makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *
+ *   cfg        : width, height, pixel_format, mode, substeps, max_substeps,
+ *                intensity, ref_mode, c_pos_q16, c_neg_q16, c_act_q16 as for
+ *                sim_create (same limits); c_pos_map / c_neg_map must be NULL;
+ *                max_batch and event_capacity are ignored; cuda_stream orders
+ *                the work (NULL: the legacy default stream).
+ *   prev_frame, prev_pitch : frame i-1 (device, rows of prev_pitch bytes).
+ *   frame, pitch           : frame i (device).
+ *   flow       : device, H * W * 2 floats (dx, dy), flow from frame i-1 to
+ *                frame i, 8-byte aligned.
+ *   t_prev_us, t_us : times of frames i-1 and i; 0 <= t_prev_us < t_us <
+ *                2^32; event times are t_prev_us + floor(k (t_us - t_prev_us) / N).
+ *   ref_in, ref_out : accumulate mode: the per-pixel reference R (Q16, W*H
+ *                int32, device, 4-byte aligned) before and after the step.
+ *                ref_in = NULL starts a stream: R = LUT[luma of frame i-1].
+ *                ref_in may equal ref_out (updated in place).  Reset mode:
+ *                both ignored (may be NULL).
+ *   events, event_capacity : device output, 8-byte aligned; the step's
+ *                events in output order.
+ *   n_events   : host; events written (0 on any error).
+ * Returns SIM_OK, or: SIM_ERR_ARG (invalid argument), SIM_ERR_TIME /
+ * SIM_ERR_TIME_RANGE, SIM_ERR_TOO_LARGE when the problem does not fit the
+ * scratch array (checked before any device work), SIM_ERR_EVENT_OVERFLOW
+ * when the events exceed event_capacity or the 8-byte staging that remains
+ * after the other parts (then ref_out has already been updated and the
+ * events buffer holds no usable result), SIM_ERR_DEVICE_TIMEOUT,
+ * SIM_ERR_CUDA / SIM_ERR_NO_DEVICE.
+ *
+ * Scratch: the array needs about 2 W H + 24.3 N_max H ceil(W / 64) bytes
+ * (N_max = substeps, or max_substeps when adaptive), plus 2 KB, plus at
+ * least 1 MiB of staging; larger problems get SIM_ERR_TOO_LARGE.  The 32 MiB
+ * array admits 1280 x 720 at any N_max, 1920 x 1080 up to N_max = 36 and
+ * 3840 x 2160 up to N_max = 5.
+ * The first call on a device, with that device current, looks the array's
+ * address up (cudaGetSymbolAddress): make that first call before any stream
+ * capture begins on the device.  Each call clears the parts that must start
+ * at zero.  Every call on a device shares the one array: calls whose device
+ * work overlaps (two streams, or two host threads) race and corrupt each
+ * other's results; order them on one stream or serialise them.  The call
+ * waits for its stream before returning (it reads the event count back). */
+#define SIM_STATIC_SCRATCH_BYTES (32LL << 20)
+int sim_step_pair_static(const sim_config* cfg, const void* prev_frame, int64_t prev_pitch,
+                         const void* frame, int64_t pitch, const float* flow, int64_t t_prev_us,
+                         int64_t t_us, const int32_t* ref_in, int32_t* ref_out,
+                         sim_event* events, int64_t event_capacity, int64_t* n_events);
 
 #ifdef __cplusplus
 }

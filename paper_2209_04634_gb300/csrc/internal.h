@@ -125,6 +125,8 @@ cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
+// Record a CUDA error for sim_last_cuda_error (runtime.cu).
+void note_cuda_error(cudaError_t e);
 int device_sm_count();
 
 }  // namespace evsim

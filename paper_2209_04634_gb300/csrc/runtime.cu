@@ -281,6 +281,8 @@ cudaError_t enqueue_batch(sim_t* s, int n) {
 
 }  // namespace
 
+void evsim::note_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
 extern "C" {
 
 const char* sim_version(void) { return "0.2.0"; }
@@ -301,6 +303,7 @@ const char* sim_strerror(int code) {
     case SIM_ERR_STATE: return "call not valid in this state";
     case SIM_ERR_ADMIT: return "admission refused";
     case SIM_ERR_NO_DEVICE: return "no usable CUDA device";
+    case SIM_ERR_TOO_LARGE: return "problem too large for the fixed scratch array";
     default: return "unknown error";
   }
 }

@@ -1,0 +1,245 @@
+// sim_step_pair_static: one frame pair through the simulation kernels with
+// every scratch buffer carved out of a fixed, file-scope device array, so the
+// call itself allocates no memory.
+//
+// Who needs it: callers that may not allocate device memory once they are
+// running.  A process whose device memory is owned by another framework's
+// caching allocator (cudaMalloc outside that pool can fail or fragment it,
+// and cudaFree synchronises the whole device, stalling every other stream); a
+// frame-rate pipeline with a no-allocation rule after start-up, because
+// cudaMalloc / cudaFree have unbounded latency; a plug-in that receives device
+// buffers from its host application and is not allowed to allocate its own.
+// Such callers own their frames, flow, reference and event buffers and pass
+// them in; everything else lives in g_scratch.
+//
+// The array is shared by every call on a device: it is re-initialised at the
+// start of each call (control block, look-back words and flow maxima are
+// cleared there), and two calls whose GPU work overlaps race on it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/evsim.h"
+#include "internal.h"
+
+namespace {
+
+using evsim::Ctl;
+using evsim::Ev;
+using evsim::FrameDesc;
+using evsim::Seg;
+
+static __device__ __align__(256) unsigned char g_scratch[SIM_STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 256;
+std::mutex g_setup_mu;
+unsigned char* g_base[MAX_DEVICES] = {};  // address of g_scratch on each device (set-up done)
+
+// Start of the array: uploaded by every call in one copy.
+struct alignas(256) Header {
+  Ctl ctl;
+  unsigned char pad0[256 - sizeof(Ctl) % 256];
+  int lut[256];
+  FrameDesc desc;
+};
+static_assert(sizeof(Ctl) < 256, "control block fits the first 256 bytes");
+static_assert(offsetof(Header, lut) % 16 == 0, "table alignment");
+
+constexpr long long align256(long long v) { return (v + 255) & ~255LL; }
+constexpr long long STAGE_MIN = 1LL << 20;  // bytes of staging a call must have at least
+
+// Byte offsets of the parts of g_scratch for one problem size.
+struct Layout {
+  long long zero;      // maxf2 (one frame) then the look-back words: cleared per call
+  long long zero_len;
+  long long status;
+  long long ring0, ring1;
+  long long seg;
+  long long staging;
+  long long stage_events;
+  long long need;      // bytes up to and including the minimum staging
+};
+
+Layout layout(long long P, long long nseg) {
+  Layout l{};
+  const long long nchunks = (nseg + evsim::OCHUNK - 1) / evsim::OCHUNK;
+  l.zero = align256(sizeof(Header));
+  l.status = l.zero + 256;
+  l.zero_len = 256 + nchunks * 8;
+  l.ring0 = align256(l.zero + l.zero_len);
+  l.ring1 = align256(l.ring0 + P);
+  l.seg = align256(l.ring1 + P);
+  l.staging = align256(l.seg + nseg * (long long)sizeof(Seg));
+  l.need = l.staging + STAGE_MIN;
+  l.stage_events = (SIM_STATIC_SCRATCH_BYTES - l.staging) / (long long)sizeof(Ev);
+  return l;
+}
+
+int fail(cudaError_t e) {
+  evsim::note_cuda_error(e);
+  return e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
+                 e == cudaErrorNoKernelImageForDevice
+             ? SIM_ERR_NO_DEVICE
+             : SIM_ERR_CUDA;
+}
+
+// Once per device, with that device current: look up the array's address.
+int scratch_base(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> g(g_setup_mu);
+  if (!g_base[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+    if (e != cudaSuccess) return fail(e);
+    g_base[dev] = (unsigned char*)ptr;
+  }
+  *out = g_base[dev];
+  return SIM_OK;
+}
+
+bool misaligned(const void* p, unsigned a) { return ((size_t)p & (a - 1)) != 0; }
+
+}  // namespace
+
+extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_frame,
+                                    int64_t prev_pitch, const void* frame, int64_t pitch,
+                                    const float* flow, int64_t t_prev_us, int64_t t_us,
+                                    const int32_t* ref_in, int32_t* ref_out, sim_event* events,
+                                    int64_t event_capacity, int64_t* n_events) {
+  if (!cfg || !n_events) return SIM_ERR_ARG;
+  *n_events = 0;
+  const sim_config& c = *cfg;
+  if (c.width < 1 || c.height < 1 || c.width > SIM_MAX_DIM || c.height > SIM_MAX_DIM) return SIM_ERR_ARG;
+  if (c.pixel_format != SIM_LUMA8 && c.pixel_format != SIM_RGB8) return SIM_ERR_ARG;
+  if (c.mode != SIM_DENSE && c.mode != SIM_SPARSE) return SIM_ERR_ARG;
+  if (c.intensity != SIM_LOG && c.intensity != SIM_LINEAR) return SIM_ERR_ARG;
+  if (c.ref_mode != SIM_REF_ACCUM && c.ref_mode != SIM_REF_RESET) return SIM_ERR_ARG;
+  if (c.substeps < 0 || c.substeps > SIM_MAX_SUBSTEPS) return SIM_ERR_ARG;
+  if (c.substeps == 0 && (c.max_substeps < 1 || c.max_substeps > SIM_MAX_SUBSTEPS)) return SIM_ERR_ARG;
+  if (c.c_pos_map || c.c_neg_map) return SIM_ERR_ARG;  // threshold maps: sim_create only
+  if (event_capacity < 0 || event_capacity > evsim::MAX_EVENTS) return SIM_ERR_ARG;
+  if (!prev_frame || !frame || !flow || (event_capacity > 0 && !events)) return SIM_ERR_ARG;
+  if (misaligned(flow, 8) || misaligned(events, 8)) return SIM_ERR_ARG;
+  const bool accum = c.ref_mode == SIM_REF_ACCUM;
+  if (accum && (!ref_out || misaligned(ref_out, 4) || misaligned(ref_in, 4))) return SIM_ERR_ARG;
+  const long long row = (long long)c.width * c.pixel_format;
+  if (prev_pitch < row || pitch < row) return SIM_ERR_ARG;
+  if (t_prev_us < 0) return SIM_ERR_TIME_RANGE;
+  if (t_us <= t_prev_us) return SIM_ERR_TIME;
+  if (t_us > 4294967295LL) return SIM_ERR_TIME_RANGE;
+
+  Header h;
+  std::memset(&h, 0, sizeof(h));
+  for (int v = 0; v < 256; ++v)
+    h.lut[v] = c.intensity == SIM_LINEAR ? v * 65536 : (int)std::nearbyint(65536.0 * std::log(v + 1.0));
+  const long long range = (long long)h.lut[255] - h.lut[0];
+  const long long cmin = accum ? (range + 32765) / 32766 : 1;
+  if (c.c_pos_q16 < cmin || c.c_pos_q16 >= (1 << 30)) return SIM_ERR_ARG;
+  if (c.c_neg_q16 < cmin || c.c_neg_q16 >= (1 << 30)) return SIM_ERR_ARG;
+
+  const int tiles_x = (c.width + evsim::TW - 1) / evsim::TW;
+  const int tiles_y = (c.height + evsim::TH - 1) / evsim::TH;
+  const int n_max = c.substeps > 0 ? c.substeps : c.max_substeps;
+  const long long P = (long long)c.width * c.height;
+  const long long segs_per_k = (long long)c.height * tiles_x;
+  const long long nseg = (long long)n_max * segs_per_k;
+  const Layout L = layout(P, nseg);
+  if (L.need > SIM_STATIC_SCRATCH_BYTES) return SIM_ERR_TOO_LARGE;
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(e);
+  if (dev < 0 || dev >= MAX_DEVICES) return SIM_ERR_NO_DEVICE;
+  unsigned char* base = nullptr;
+  const int rc = scratch_base(dev, &base);
+  if (rc) return rc;
+  // shared-memory permission of the tile kernels, at the largest substep cap
+  // (never below what any handle needs)
+  e = evsim::configure_kernels(SIM_MAX_SUBSTEPS);
+  if (e != cudaSuccess) return fail(e);
+  const int sms = evsim::device_sm_count();
+  cudaStream_t st = c.cuda_stream ? (cudaStream_t)c.cuda_stream : cudaStreamLegacy;
+
+  evsim::SimParams p{};
+  p.W = c.width;
+  p.H = c.height;
+  p.ch = c.pixel_format;
+  p.tiles_x = tiles_x;
+  p.tiles_y = tiles_y;
+  p.mode = c.mode;
+  p.ref_mode = c.ref_mode;
+  p.intensity = c.intensity;
+  p.n_fixed = c.substeps;
+  p.n_max = n_max;
+  p.cp = c.c_pos_q16;
+  p.cn = c.c_neg_q16;
+  p.cact = c.c_act_q16;
+  p.bmax = 1;
+  p.lut = (const int*)(base + offsetof(Header, lut));
+  p.ring0 = base + L.ring0;
+  p.ring1 = base + L.ring1;
+  p.ctl = (Ctl*)(base + offsetof(Header, ctl));
+  p.maxf2 = (unsigned long long*)(base + L.zero);
+  p.staging = (Ev*)(base + L.staging);
+  p.stage_cap = L.stage_events;
+  p.seg = (Seg*)(base + L.seg);
+  p.segs_per_k = segs_per_k;
+  p.order_status = (unsigned long long*)(base + L.status);
+  p.events = (Ev*)events;
+  p.event_cap = event_capacity;
+
+  // control block (zero, t of frame i-1), table and the frame descriptor
+  h.ctl.t_prev = t_prev_us;
+  h.desc.frame = (const unsigned char*)frame;
+  h.desc.pitch = pitch;
+  h.desc.flow = (const float2*)flow;
+  h.desc.t_rel = t_us;
+  e = cudaMemcpyAsync(base, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + L.zero, 0, L.zero_len, st);
+  if (e != cudaSuccess) return fail(e);
+
+  // frame i-1: its luma into the ring; with no reference given (accumulate
+  // mode), also the reference R = LUT[luma], written to ref_out
+  evsim::SimParams pi = p;
+  FrameDesc f0{};
+  f0.frame = (const unsigned char*)prev_frame;
+  f0.pitch = prev_pitch;
+  if (accum && !ref_in) {
+    pi.R0 = ref_out;
+  } else {
+    pi.ref_mode = SIM_REF_RESET;  // ring only
+  }
+  e = evsim::launch_init(pi, f0, st);
+  if (e != cudaSuccess) return fail(e);
+  if (accum) {
+    p.R0 = ref_in ? const_cast<int32_t*>(ref_in) : ref_out;  // read (sel = 0)
+    p.R1 = ref_out;                                          // written
+  }
+
+  evsim::BatchArg b{};
+  b.frames = (const FrameDesc*)(base + offsetof(Header, desc));
+  b.count = 1;
+  b.serial = 1;  // the look-back words were cleared above
+  const bool adaptive = c.substeps == 0;
+  if (c.mode == SIM_DENSE) {
+    if (adaptive) e = evsim::launch_flowmax(p, b, st);
+    if (e == cudaSuccess) e = evsim::launch_dense(p, b, st);
+  } else {
+    if (adaptive) e = evsim::launch_sparse_pre(p, b, st);
+    if (e == cudaSuccess) e = evsim::launch_sparse(p, b, st);
+  }
+  const long long ochunks = (nseg + evsim::OCHUNK - 1) / evsim::OCHUNK;
+  const int grid = (int)(ochunks < (long long)sms * 8 ? ochunks : (long long)sms * 8);
+  if (e == cudaSuccess) e = evsim::launch_order(p, b, st, grid > 0 ? grid : 1);
+  if (e != cudaSuccess) return fail(e);
+
+  Ctl out;
+  e = cudaMemcpyAsync(&out, p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(e);
+  if (out.err) return out.err;
+  *n_events = out.cursor;
+  return SIM_OK;
+}

@@ -22,6 +22,8 @@ SIM_OK, SIM_MORE = 0, 1
 SIM_ERR_ARG, SIM_ERR_CUDA, SIM_ERR_OOM, SIM_ERR_TIME = -1, -2, -3, -4
 SIM_ERR_TIME_RANGE, SIM_ERR_EVENT_OVERFLOW, SIM_ERR_DEVICE_TIMEOUT = -5, -6, -7
 SIM_ERR_STATE, SIM_ERR_ADMIT, SIM_ERR_NO_DEVICE = -8, -9, -10
+SIM_ERR_TOO_LARGE = -11
+SIM_STATIC_SCRATCH_BYTES = 32 << 20
 SIM_LUMA8, SIM_RGB8 = 1, 3
 SIM_DENSE, SIM_SPARSE = 0, 1
 SIM_LOG, SIM_LINEAR = 0, 1
@@ -79,6 +81,9 @@ SIGNATURES = [
     ("sim_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("sim_version", ctypes.c_char_p, []),
     ("sim_last_cuda_error", ctypes.c_char_p, []),
+    ("sim_step_pair_static", ctypes.c_int, [ctypes.POINTER(sim_config), _VP, _I64, _VP, _I64, _VP,
+                                            _I64, _I64, _VP, _VP, _VP, _I64,
+                                            ctypes.POINTER(_I64)]),
 ]
 
 _lock = threading.Lock()
@@ -297,3 +302,39 @@ def simulator_for(seq, mode: int = SIM_DENSE, **kw) -> Simulator:
                 c_pos_map=seq.cpos_map, c_neg_map=seq.cneg_map)
     args.update(kw)
     return Simulator(seq.width, seq.height, **args)
+
+
+def step_pair_static(prev_frame, frame, flow, t_prev_us: int, t_us: int, ref_in, ref_out,
+                     events, *, pixel_format: int = SIM_LUMA8, mode: int = SIM_DENSE,
+                     substeps: int = 8, max_substeps: int = 16, intensity: int = SIM_LOG,
+                     ref_mode: int = SIM_REF_ACCUM, c_pos_q16: int = 13107,
+                     c_neg_q16: int = 13107, c_act_q16: int = -1, stream=None) -> int:
+    """``sim_step_pair_static`` on torch CUDA tensors (the caller allocates
+    every buffer; the library call allocates nothing).  prev_frame / frame:
+    (H, W) or (H, W, 3) uint8, contiguous; flow: (H, W, 2) float32; ref_in /
+    ref_out: (H, W) int32 or None; events: uint8 tensor of 8 * capacity bytes.
+    Returns the number of events written."""
+    lib = load()
+    H, W = int(frame.shape[0]), int(frame.shape[1])
+    cfg = sim_config()
+    check(lib.sim_config_default(ctypes.byref(cfg), W, H), "sim_config_default")
+    cfg.pixel_format = pixel_format
+    cfg.mode = mode
+    cfg.substeps = substeps
+    cfg.max_substeps = max_substeps
+    cfg.intensity = intensity
+    cfg.ref_mode = ref_mode
+    cfg.c_pos_q16 = c_pos_q16
+    cfg.c_neg_q16 = c_neg_q16
+    cfg.c_act_q16 = c_act_q16
+    if stream is not None:
+        handle = int(getattr(stream, "cuda_stream", stream))
+        cfg.cuda_stream = handle if handle else CUDA_STREAM_LEGACY
+    n = ctypes.c_int64(0)
+    pitch = W * pixel_format
+    check(lib.sim_step_pair_static(
+        ctypes.byref(cfg), _ptr(prev_frame), pitch, _ptr(frame), pitch, _ptr(flow),
+        int(t_prev_us), int(t_us), None if ref_in is None else _ptr(ref_in),
+        None if ref_out is None else _ptr(ref_out), _ptr(events), events.numel() // 8,
+        ctypes.byref(n)), "sim_step_pair_static")
+    return int(n.value)
