@@ -208,6 +208,103 @@ const char* sim_last_cuda_error(void);
 /* Library version, "major.minor.patch". */
 const char* sim_version(void);
 
+/* ---- multi-stream group ---------------------------------------------------
+ * Many independent camera streams of mixed sizes and settings advanced
+ * together (the batched pattern the spec names; the paper itself runs
+ * one stream).  Each member is a full stream with the semantics, arithmetic
+ * and event stream of a sim_t handle fed the same frames: the group only
+ * changes how the work is launched.  simb_step advances every member that has
+ * queued frames with one launch per kernel for all of them: an adaptive-N
+ * pre-pass over (member, frame, block) work items, one tile launch per tile
+ * class present (dense/sparse x accumulate/reset x log/linear x maps), and one
+ * order launch whose tickets run over the chunks of all members (each member
+ * keeps its own look-back chain and commits its own frames).  With graphs on,
+ * that launch sequence is captured once per member set and replayed; the
+ * per-step data (frame counts, batch serials, frame descriptors) are read
+ * from a device table that the step uploads in one copy.
+ *
+ * All work of the group is ordered on one CUDA stream.  Not thread-safe: one
+ * host thread drives a group. */
+#define SIM_MAX_GROUP 1024
+
+typedef struct simb_s simb_t;  /* opaque, owned by the library */
+
+typedef struct {
+  int32_t max_streams;       /* members at most, 1..SIM_MAX_GROUP */
+  int32_t frames_per_step;   /* frames a member may queue between steps, 1..64 */
+  int64_t hbm_budget_bytes;  /* admission bound on the members' device state; 0: 8 GiB */
+  int32_t use_graphs;        /* 1: replay one CUDA graph per member set; 0: plain launches */
+  int32_t reserved;
+  void* cuda_stream;         /* cudaStream_t; NULL: group-owned stream */
+} simb_config;
+
+typedef struct {
+  int32_t members;           /* admitted streams */
+  int32_t tile_classes;      /* tile launches per step for the current members */
+  int64_t bytes_used;        /* device state of the members (admission accounting) */
+  int64_t budget;            /* hbm_budget_bytes */
+  int64_t steps;             /* simb_step calls that launched work */
+  int64_t frames_stepped;    /* member frames advanced by those steps */
+  int64_t graph_captures;    /* graphs captured (one per member set) */
+  int64_t graph_launches;    /* steps run as a graph replay */
+  int64_t kernel_launches;   /* kernels launched by steps (a replay counts its kernels) */
+  int64_t admit_refused;     /* simb_admit calls refused with SIM_ERR_ADMIT */
+} simb_stats;
+
+/* Defaults: 64 streams, 4 frames per step, 8 GiB budget, graphs on. */
+int simb_config_default(simb_config* cfg);
+
+/* Create an empty group (allocates its tables: about 1 KB per possible member
+ * plus 32 bytes per member frame slot). */
+int simb_create(const simb_config* cfg, simb_t** out);
+
+/* Device bytes a stream of this configuration holds as a member (what
+ * admission charges against the budget). */
+int simb_state_bytes(const simb_t* g, const sim_config* cfg, int64_t* bytes);
+
+/* Admit a stream: allocates its device state (as sim_create, with max_batch
+ * = frames_per_step and the group's stream; cfg->cuda_stream and
+ * cfg->max_batch are ignored).  *id is a small integer naming the member
+ * until it is evicted (ids of evicted members are reused).  Returns
+ * SIM_ERR_ADMIT, allocating nothing, when the group is full or the state
+ * would exceed the budget.  Waits for the group's stream. */
+int simb_admit(simb_t* g, const sim_config* cfg, int32_t* id);
+
+/* Queue frame i of member id, as sim_push_frame (same buffer rules: device
+ * buffers must stay valid until the step that consumes them has finished,
+ * e.g. until the next simb_pop / simb_sync).  A member's first frame sets its
+ * reference at once (one small launch) and is never queued.  Host frames are
+ * copied into the member's staging slots.  SIM_ERR_STATE when the member
+ * already has frames_per_step frames queued (call simb_step). */
+int simb_push(simb_t* g, int32_t id, const void* frame, int64_t pitch_bytes, const float* flow,
+              int64_t t_us, int32_t mem);
+
+/* Advance every member with queued frames by all of its queued frames
+ * (asynchronous; *frames, if not NULL, receives the number of member frames
+ * launched, 0 when nothing was queued).  Device-side failures of a member
+ * (event overflow) are reported by that member's next simb_pop and roll only
+ * that member back, as for a sim_t. */
+int simb_step(simb_t* g, int64_t* frames);
+
+/* Committed events of member id, as sim_pop_events (waits for the group's
+ * stream). */
+int simb_pop(simb_t* g, int32_t id, sim_event* out, int64_t cap, int64_t* n_out, int32_t mem);
+
+/* Statistics of member id, as sim_get_stats. */
+int simb_stream_stats(simb_t* g, int32_t id, sim_stats* st);
+
+/* Remove member id and free its state (waits for the group's stream);
+ * its undelivered events are dropped. */
+int simb_evict(simb_t* g, int32_t id);
+
+/* Wait for the group's stream. */
+int simb_sync(simb_t* g);
+
+int simb_get_stats(simb_t* g, simb_stats* st);
+
+/* Evict every member and free the group. */
+int simb_destroy(simb_t* g);
+
 /* ---- allocation-free frame pair ------------------------------------------
  * The paper has no counterpart: this is a library service for callers that
  * must not allocate device memory while they run, such as code whose device

@@ -1,0 +1,85 @@
+// Private header of the evsim host runtime: the handle structure and the
+// helpers that the single-stream API (runtime.cu) and the multi-stream group
+// API (group.cu) share.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/evsim.h"
+#include "internal.h"
+
+using evsim::Ctl;
+using evsim::Ev;
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct sim_s {
+  sim_config cfg{};
+  int W = 0, H = 0, ch = 1;
+  long long P = 0;
+  int n_max = 0;
+  int tiles_x = 0, tiles_y = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int sms = 1;
+
+  int* d_lut = nullptr;
+  unsigned short* d_cpmap = nullptr;
+  unsigned short* d_cnmap = nullptr;
+  unsigned char* d_ring[2] = {nullptr, nullptr};
+  int* d_R[2] = {nullptr, nullptr};
+  Ctl* d_ctl = nullptr;
+  unsigned long long* d_maxf2 = nullptr;
+  Ev* d_staging = nullptr;
+  Ev* d_events = nullptr;
+  evsim::Seg* d_seg = nullptr;
+  unsigned long long* d_order_status = nullptr;
+  evsim::FrameDesc* d_desc = nullptr;       // bmax descriptors of the batch in flight
+  unsigned char* d_stage_frames = nullptr;  // host batches: staged frames and flows
+  float2* d_stage_flows = nullptr;
+  long long stage_frames = 0;               // frames the host staging holds
+  long long event_cap = 0;
+  long long segs_per_k = 0;
+  int bmax = 1;
+  int order_grid = 1;
+
+  // host shadow of the stream
+  bool have_first = false;
+  long long t0 = 0, t_last = 0;
+  long long pushed = 0;
+  unsigned serial = 0;
+  long long popped = 0;
+  long long popped_total = 0;
+
+  bool prof = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[SIM_K_COUNT] = {};
+  long long prof_n[SIM_K_COUNT] = {};
+};
+
+namespace evsim_rt {
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// Kernel parameters of a handle.
+evsim::SimParams make_params(const sim_t* s);
+// cudaError_t -> SIM_* code (records the error for sim_last_cuda_error).
+int cuda_rc(cudaError_t e);
+// Frame 0 of a stream: frame ring and reference (enqueued on s->stream).
+int push_first(sim_t* s, const void* frame, long long pitch, int64_t t_us, int32_t mem);
+// Device bytes sim_create allocates for a configuration (before host staging grows).
+long long state_bytes(const sim_config& c);
+
+}  // namespace evsim_rt

@@ -114,6 +114,43 @@ struct SimParams {
   long long event_cap;
 };
 
+// ---- multi-stream step (one launch per kernel for every member of a group)
+constexpr int MAX_GROUP = 1024;  // members of one group
+// Tile kernel classes (template flags); members of one class share a launch.
+enum { TILE_RESET = 1, TILE_MAPS = 2, TILE_WIDE = 4, TILE_SPARSE = 8, TILE_CLASSES = 16 };
+
+struct GroupStream {            // per member; changes only when members change
+  SimParams p;
+  const FrameDesc* frames;      // the member's descriptor slots (device)
+  int tile_begin;               // first block of the member in its class's tile grid
+  int pre_blocks;               // pre-pass blocks per frame (adaptive members)
+};
+
+struct StreamStep {             // per member and step
+  int count;                    // frames in this step (0: idle)
+  unsigned int serial;          // batch serial (look-back epoch)
+  int chunk_begin;              // first order ticket of the member
+  int pre_begin;                // first pre-pass work item of the member
+};
+
+struct GroupTotals {            // per step
+  int chunks;                   // order tickets over all members
+  int pre_items;                // pre-pass work items over all members
+};
+
+struct GroupCtl {
+  unsigned int order_ticket;
+  unsigned int order_exit;
+};
+
+struct GroupArg {
+  const GroupStream* gs;        // n members (device)
+  const StreamStep* steps;      // n members (device)
+  const GroupTotals* tot;       // device
+  GroupCtl* gctl;               // device
+  int n;
+};
+
 // Shared-memory bytes of the tile kernel (dense and sparse) for a substep cap.
 size_t tile_smem_bytes(int n_max);
 
@@ -125,6 +162,14 @@ cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
+int tile_class(const SimParams& p);
+cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st);
+cudaError_t launch_tile_multi(const GroupArg& g, int cls, const int* block_map, int grid,
+                              size_t smem, cudaStream_t st);
+cudaError_t launch_order_multi(const GroupArg& g, int grid, cudaStream_t st);
+// Shared-memory permission of the multi-stream tile kernels.
+cudaError_t configure_group_kernels(size_t smem);
+
 // Record a CUDA error for sim_last_cuda_error (runtime.cu).
 void note_cuda_error(cudaError_t e);
 int device_sm_count();

@@ -252,6 +252,8 @@ __device__ long long lookback_warp(unsigned long long* status, int c, unsigned e
       if (lane == 0) atomicCAS(err, 0, SIM_ERR_DEVICE_TIMEOUT);
       break;
     }
+    // a failed stream publishes nothing more: stop waiting for it
+    if ((spins & 1023) == 0 && __shfl_sync(FULL, ld_volatile(err), 0) != 0) break;
     __nanosleep(32);
   }
   long long inc_v = excl + agg;
@@ -870,140 +872,163 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long mask, int m) {
   return 32 + (int)__fns(hi, 0, m - c + 1);
 }
 
+// Shared memory of an order block.
+struct OrderSmem {
+  int ex[OCHUNK];
+  int src[OCHUNK];
+  unsigned long long mask[OCHUNK];
+  unsigned long long pol[OCHUNK];
+  unsigned t[OCHUNK];
+  unsigned xy[OCHUNK];  // x0 | (y << 16)
+  int N[SIM_MAX_BATCH];  // substeps of each frame of the batch
+  int warp[NWARP + 1];
+  int last;
+  long long prefix;
+};
+
+// Substep counts of the batch's frames into o.N (all threads; the caller
+// synchronises before they are read).
+__device__ __forceinline__ void order_fill_n(const SimParams& p, const BatchArg& b, OrderSmem& o) {
+  for (int i = threadIdx.x; i < b.count; i += NT)
+    o.N[i] = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[i], p.n_max);
+}
+
+// Chunk c (of nchunks) of one stream's batch: OCHUNK segments in output
+// order; the block that finishes the batch's last chunk commits the batch.
+// cursor and t_first are the stream's committed event count and time.
+__device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& b, int c,
+                                            int nchunks, long long cursor, long long t_first,
+                                            OrderSmem& o) {
+  Ctl* ctl = p.ctl;
+  const int tid = threadIdx.x;
+  const long long S = p.segs_per_k;
+  const long long per_frame = (long long)p.n_max * S;
+  const long long nseg = (long long)b.count * per_frame;
+  // one segment per thread; segments of substeps k >= N of their frame were
+  // never written and count zero
+  const long long si = (long long)c * OCHUNK + tid;
+  int cnt = 0, src = -1;
+  unsigned long long mask = 0, pol = 0;
+  unsigned tk = 0, xy = 0;
+  if (si < nseg) {
+    const int fi = (int)(si / per_frame);
+    const long long rem = si - (long long)fi * per_frame;
+    const int k = (int)(rem / S);
+    const int N = o.N[fi];
+    if (k < N) {
+      const Seg sg = p.seg[si];
+      cnt = sg.cnt;
+      src = sg.src;
+      mask = sg.mask;
+      pol = sg.pol;
+      const int rs = (int)(rem - (long long)k * S);
+      const int y = rs / p.tiles_x, tc = rs - y * p.tiles_x;
+      xy = (unsigned)(tc * TW) | ((unsigned)y << 16);
+      const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
+      const long long dt = b.frames[fi].t_rel - tp;
+      tk = (unsigned)(tp + ((long long)(k + 1) * dt) / N);
+    }
+  }
+  int total;
+  const int ex = block_excl_scan(cnt, o.warp, &total);
+  o.ex[tid] = ex;
+  o.src[tid] = src;
+  o.mask[tid] = mask;
+  o.pol[tid] = pol;
+  o.t[tid] = tk;
+  o.xy[tid] = xy;
+  if (tid < 32) {
+    const long long ex0 = lookback_warp(p.order_status, c, b.serial, total, &ctl->err);
+    if (tid == 0) o.prefix = ex0;
+  }
+  __syncthreads();
+  const long long base = cursor + o.prefix;
+  for (int jj = tid; jj < total; jj += NT) {
+    int lo = 0, hi = OCHUNK;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (o.ex[mid] <= jj) lo = mid; else hi = mid;
+    }
+    const long long dst = base + jj;
+    if (dst >= p.event_cap) continue;
+    const int m = jj - o.ex[lo];
+    Ev ev;
+    if (o.src[lo] >= 0) {
+      ev = p.staging[(long long)o.src[lo] + m];
+    } else {
+      const int bit = nth_set_bit(o.mask[lo], m);
+      const unsigned xy0 = o.xy[lo];
+      ev = make_event(o.t[lo], (int)(xy0 & 0xFFFF) + bit, (int)(xy0 >> 16),
+                      (o.pol[lo] >> bit) & 1ull);
+    }
+    p.events[dst] = ev;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned d = atomicAdd(&ctl->order_done, 1u);
+    o.last = d == (unsigned)(nchunks - 1);
+  }
+  __syncthreads();
+  if (o.last) {
+    // This block finished the batch's last chunk: commit or fail the batch.
+    if (tid == 0) {
+      __threadfence();
+      const unsigned long long w = ld_volatile(&p.order_status[nchunks - 1]);
+      const long long tot = (long long)(w & LB_VALUE);
+      const bool over = ctl->batch_fail != 0 || tot >= (long long)LB_VALUE ||
+                        cursor + tot > p.event_cap;
+      if (ld_volatile(&ctl->err) == 0) {
+        if (over) {
+          atomicCAS(&ctl->err, 0, SIM_ERR_EVENT_OVERFLOW);
+        } else {
+          const long long P = (long long)p.W * p.H;
+          long long nsum = 0;
+          for (int i = 0; i < b.count; ++i) nsum += o.N[i];
+          ctl->cursor = cursor + tot;
+          ctl->sel ^= p.ref_mode == SIM_REF_ACCUM ? 3 : 2;
+          ctl->t_prev = b.frames[b.count - 1].t_rel;
+          ctl->committed += b.count;
+          ctl->batch_events = tot;
+          ctl->last_n = o.N[b.count - 1];
+          ctl->work_px += P * nsum;
+          ctl->work_active += p.mode == SIM_SPARSE ? ctl->active_n : P * nsum;
+          ctl->last_active = p.mode == SIM_SPARSE ? ctl->active : P * b.count;
+        }
+      }
+      ctl->active = 0;
+      ctl->active_n = 0;
+      ctl->stage_top = 0;
+      ctl->order_done = 0;
+      ctl->batch_fail = 0;
+    }
+    for (int i = tid; i < b.count; i += NT) p.maxf2[i] = 0;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int order_nchunks(const SimParams& p, int count) {
+  const long long nseg = (long long)count * p.n_max * p.segs_per_k;
+  return (int)max(1LL, (nseg + OCHUNK - 1) / OCHUNK);
+}
+
 __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
-  __shared__ int s_ex[OCHUNK];
-  __shared__ int s_src[OCHUNK];
-  __shared__ unsigned long long s_mask[OCHUNK];
-  __shared__ unsigned long long s_pol[OCHUNK];
-  __shared__ unsigned s_t[OCHUNK];
-  __shared__ unsigned s_xy[OCHUNK];  // x0 | (y << 16)
-  __shared__ int s_N[1024];
-  __shared__ int s_warp[NWARP + 1];
-  __shared__ int s_c, s_last, s_ok;
-  __shared__ long long s_prefix;
+  __shared__ OrderSmem o;
+  __shared__ int s_c;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
   const int tid = threadIdx.x;
-  const int nmax = p.n_max;
-  for (int i = tid; i < b.count; i += NT)
-    s_N[i] = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[i], nmax);
-  const long long S = p.segs_per_k;
-  const long long per_frame = (long long)nmax * S;
-  const long long nseg = (long long)b.count * per_frame;
-  const int nchunks = (int)max(1LL, (nseg + OCHUNK - 1) / OCHUNK);
+  order_fill_n(p, b, o);
+  const int nchunks = order_nchunks(p, b.count);
   const long long cursor = ctl->cursor;
   const long long t_first = ctl->t_prev;  // t of the frame before the batch
   __syncthreads();
-
   for (;;) {
     if (tid == 0) s_c = (int)atomicAdd(&ctl->order_ticket, 1u);
     __syncthreads();
     const int c = s_c;
     if (c >= nchunks) break;
-    // one segment per thread; segments of substeps k >= N of their frame were
-    // never written and count zero
-    const long long si = (long long)c * OCHUNK + tid;
-    int cnt = 0, src = -1;
-    unsigned long long mask = 0, pol = 0;
-    unsigned tk = 0, xy = 0;
-    if (si < nseg) {
-      const int fi = (int)(si / per_frame);
-      const long long rem = si - (long long)fi * per_frame;
-      const int k = (int)(rem / S);
-      const int N = s_N[fi];
-      if (k < N) {
-        const Seg sg = p.seg[si];
-        cnt = sg.cnt;
-        src = sg.src;
-        mask = sg.mask;
-        pol = sg.pol;
-        const int rs = (int)(rem - (long long)k * S);
-        const int y = rs / p.tiles_x, tc = rs - y * p.tiles_x;
-        xy = (unsigned)(tc * TW) | ((unsigned)y << 16);
-        const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
-        const long long dt = b.frames[fi].t_rel - tp;
-        tk = (unsigned)(tp + ((long long)(k + 1) * dt) / N);
-      }
-    }
-    int total;
-    const int ex = block_excl_scan(cnt, s_warp, &total);
-    s_ex[tid] = ex;
-    s_src[tid] = src;
-    s_mask[tid] = mask;
-    s_pol[tid] = pol;
-    s_t[tid] = tk;
-    s_xy[tid] = xy;
-    if (tid < 32) {
-      const long long ex0 = lookback_warp(p.order_status, c, b.serial, total, &ctl->err);
-      if (tid == 0) s_prefix = ex0;
-    }
-    __syncthreads();
-    const long long base = cursor + s_prefix;
-    for (int jj = tid; jj < total; jj += NT) {
-      int lo = 0, hi = OCHUNK;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_ex[mid] <= jj) lo = mid; else hi = mid;
-      }
-      const long long dst = base + jj;
-      if (dst >= p.event_cap) continue;
-      const int m = jj - s_ex[lo];
-      Ev ev;
-      if (s_src[lo] >= 0) {
-        ev = p.staging[(long long)s_src[lo] + m];
-      } else {
-        const int bit = nth_set_bit(s_mask[lo], m);
-        const unsigned xy0 = s_xy[lo];
-        ev = make_event(s_t[lo], (int)(xy0 & 0xFFFF) + bit, (int)(xy0 >> 16),
-                        (s_pol[lo] >> bit) & 1ull);
-      }
-      p.events[dst] = ev;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      const unsigned d = atomicAdd(&ctl->order_done, 1u);
-      s_last = d == (unsigned)(nchunks - 1);
-    }
-    __syncthreads();
-    if (s_last) {
-      // This block finished the batch's last chunk: commit or fail the batch.
-      if (tid == 0) {
-        __threadfence();
-        const unsigned long long w = ld_volatile(&p.order_status[nchunks - 1]);
-        const long long tot = (long long)(w & LB_VALUE);
-        const bool over = ctl->batch_fail != 0 || tot >= (long long)LB_VALUE ||
-                          cursor + tot > p.event_cap;
-        int ok = 0;
-        if (ld_volatile(&ctl->err) == 0) {
-          if (over) {
-            atomicCAS(&ctl->err, 0, SIM_ERR_EVENT_OVERFLOW);
-          } else {
-            const long long P = (long long)p.W * p.H;
-            long long nsum = 0;
-            for (int i = 0; i < b.count; ++i) nsum += s_N[i];
-            ctl->cursor = cursor + tot;
-            ctl->sel ^= p.ref_mode == SIM_REF_ACCUM ? 3 : 2;
-            ctl->t_prev = b.frames[b.count - 1].t_rel;
-            ctl->committed += b.count;
-            ctl->batch_events = tot;
-            ctl->last_n = s_N[b.count - 1];
-            ctl->work_px += P * nsum;
-            ctl->work_active += p.mode == SIM_SPARSE ? ctl->active_n : P * nsum;
-            ctl->last_active = p.mode == SIM_SPARSE ? ctl->active : P * b.count;
-            ok = 1;
-          }
-        }
-        ctl->active = 0;
-        ctl->active_n = 0;
-        ctl->stage_top = 0;
-        ctl->order_done = 0;
-        ctl->batch_fail = 0;
-        s_ok = ok;
-      }
-      for (int i = tid; i < b.count; i += NT) p.maxf2[i] = 0;
-    }
-    __syncthreads();
+    order_chunk(p, b, c, nchunks, cursor, t_first, o);
   }
   if (tid == 0) {
     const unsigned e = atomicAdd(&ctl->order_exit, 1u);
@@ -1014,10 +1039,149 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Multi-stream step: the same work for every member stream of a group in one
+// launch per kernel.  Per-stream parameters are copied into shared memory by
+// each block; streams without frames in this step (count 0) are skipped.
+
+__device__ __forceinline__ void load_stream(const GroupArg& g, int s, SimParams& sp,
+                                            BatchArg& sb) {
+  constexpr int WORDS = sizeof(SimParams) / 4;
+  static_assert(sizeof(SimParams) % 4 == 0 && WORDS <= NT, "parameter copy");
+  if (threadIdx.x < WORDS) ((int*)&sp)[threadIdx.x] = ((const int*)&g.gs[s].p)[threadIdx.x];
+  if (threadIdx.x == 0) {
+    sb.frames = g.gs[s].frames;
+    sb.count = g.steps[s].count;
+    sb.serial = g.steps[s].serial;
+  }
+}
+
+// Largest s with begin[s] <= v over n ascending entries (shared memory).
+__device__ __forceinline__ int find_stream(const int* begin, int n, int v) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (begin[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Adaptive N pre-pass of every adaptive member (dense: flow maximum; sparse:
+// flow maximum over active pixels): work items (stream, frame, block) taken
+// in a grid-stride loop.
+__global__ void __launch_bounds__(NT) k_pre_multi(GroupArg g) {
+  __shared__ SimParams sp;
+  __shared__ BatchArg sb;
+  __shared__ int s_begin[MAX_GROUP];
+  const int n = g.n;
+  for (int i = threadIdx.x; i < n; i += NT) s_begin[i] = g.steps[i].pre_begin;
+  const int items = g.tot->pre_items;
+  int cur = -1;
+  __syncthreads();
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int s = find_stream(s_begin, n, it);
+    if (s != cur) {
+      __syncthreads();  // previous users of sp / sb are done
+      load_stream(g, s, sp, sb);
+      cur = s;
+    }
+    __syncthreads();
+    const int nb = g.gs[s].pre_blocks;
+    const int r = it - s_begin[s];
+    const int fi = r / nb, bx = r - fi * nb;
+    if (sp.mode == SIM_SPARSE)
+      sparse_pre_run(sp, sb, fi, bx, nb);
+    else
+      flowmax_run(sp, sb, fi, bx, nb);
+  }
+}
+
+// Tiles of every member of one kernel class; block_map[block] = member.
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+__global__ void __launch_bounds__(NTD, 2) k_tile_multi(GroupArg g, const int* block_map) {
+  __shared__ SimParams sp;
+  __shared__ BatchArg sb;
+  const int s = block_map[blockIdx.x];
+  if (g.steps[s].count == 0) return;  // block-uniform
+  load_stream(g, s, sp, sb);
+  __syncthreads();
+  tile_run<RESET, MAPS, WIDE, SPARSE>(sp, sb, blockIdx.x - g.gs[s].tile_begin);
+}
+
+// Order pass of every member: one ticket counter over the concatenated
+// chunks of all members (in member order); each member keeps its own
+// look-back chain and commits its own batch.
+__global__ void __launch_bounds__(NT) k_order_multi(GroupArg g) {
+  __shared__ OrderSmem o;
+  __shared__ SimParams sp;
+  __shared__ BatchArg sb;
+  __shared__ int s_begin[MAX_GROUP];
+  __shared__ int s_c, s_err;
+  __shared__ long long s_cursor, s_tfirst;
+  const int tid = threadIdx.x;
+  const int n = g.n;
+  for (int i = tid; i < n; i += NT) s_begin[i] = g.steps[i].chunk_begin;
+  const int chunks = g.tot->chunks;
+  int cur = -1, nchunks = 0;
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) s_c = (int)atomicAdd(&g.gctl->order_ticket, 1u);
+    __syncthreads();
+    const int t = s_c;
+    if (t >= chunks) break;
+    const int s = find_stream(s_begin, n, t);
+    if (s != cur) {
+      load_stream(g, s, sp, sb);
+      __syncthreads();
+      order_fill_n(sp, sb, o);
+      if (tid == 0) {
+        s_cursor = sp.ctl->cursor;
+        s_tfirst = sp.ctl->t_prev;
+      }
+      cur = s;
+      nchunks = order_nchunks(sp, sb.count);
+    }
+    if (tid == 0) s_err = ld_volatile(&sp.ctl->err);
+    __syncthreads();
+    if (s_err == 0) order_chunk(sp, sb, t - s_begin[s], nchunks, s_cursor, s_tfirst, o);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const unsigned e = atomicAdd(&g.gctl->order_exit, 1u);
+    if (e == gridDim.x - 1) {  // every block has left the ticket loop
+      g.gctl->order_ticket = 0;
+      g.gctl->order_exit = 0;
+    }
+  }
+}
+
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
 void set_tile_attr(size_t bytes) {
   cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+void set_tile_multi_attr(size_t bytes) {
+  cudaFuncSetAttribute(k_tile_multi<RESET, MAPS, WIDE, SPARSE>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <bool SPARSE>
+cudaError_t launch_tile_multi_mode(const GroupArg& g, int cls, const int* block_map, int grid,
+                                   size_t sm, cudaStream_t st) {
+  const bool reset = cls & TILE_RESET, maps = cls & TILE_MAPS, wide = cls & TILE_WIDE;
+#define EVSIM_TILE(R, M, Wd) k_tile_multi<R, M, Wd, SPARSE><<<grid, NTD, sm, st>>>(g, block_map)
+  if (!reset && !maps && !wide) EVSIM_TILE(false, false, false);
+  else if (!reset && maps && !wide) EVSIM_TILE(false, true, false);
+  else if (!reset && !maps && wide) EVSIM_TILE(false, false, true);
+  else if (!reset && maps && wide) EVSIM_TILE(false, true, true);
+  else if (reset && !maps && !wide) EVSIM_TILE(true, false, false);
+  else if (reset && maps && !wide) EVSIM_TILE(true, true, false);
+  else if (reset && !maps && wide) EVSIM_TILE(true, false, true);
+  else EVSIM_TILE(true, true, true);
+#undef EVSIM_TILE
+  return cudaGetLastError();
 }
 
 template <bool SPARSE>
@@ -1109,6 +1273,47 @@ cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_
 
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid) {
   k_order<<<grid, NT, 0, st>>>(p, b);
+  return cudaGetLastError();
+}
+
+int tile_class(const SimParams& p) {
+  return (p.ref_mode == SIM_REF_RESET ? TILE_RESET : 0) | (p.cpmap ? TILE_MAPS : 0) |
+         (p.intensity == SIM_LINEAR ? TILE_WIDE : 0) | (p.mode == SIM_SPARSE ? TILE_SPARSE : 0);
+}
+
+cudaError_t configure_group_kernels(size_t t) {
+  set_tile_multi_attr<false, false, false, false>(t);
+  set_tile_multi_attr<false, true, false, false>(t);
+  set_tile_multi_attr<false, false, true, false>(t);
+  set_tile_multi_attr<false, true, true, false>(t);
+  set_tile_multi_attr<true, false, false, false>(t);
+  set_tile_multi_attr<true, true, false, false>(t);
+  set_tile_multi_attr<true, false, true, false>(t);
+  set_tile_multi_attr<true, true, true, false>(t);
+  set_tile_multi_attr<false, false, false, true>(t);
+  set_tile_multi_attr<false, true, false, true>(t);
+  set_tile_multi_attr<false, false, true, true>(t);
+  set_tile_multi_attr<false, true, true, true>(t);
+  set_tile_multi_attr<true, false, false, true>(t);
+  set_tile_multi_attr<true, true, false, true>(t);
+  set_tile_multi_attr<true, false, true, true>(t);
+  set_tile_multi_attr<true, true, true, true>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st) {
+  k_pre_multi<<<grid, NT, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_multi(const GroupArg& g, int cls, const int* block_map, int grid,
+                              size_t smem, cudaStream_t st) {
+  if (cls & TILE_SPARSE) return launch_tile_multi_mode<true>(g, cls, block_map, grid, smem, st);
+  return launch_tile_multi_mode<false>(g, cls, block_map, grid, smem, st);
+}
+
+cudaError_t launch_order_multi(const GroupArg& g, int grid, cudaStream_t st) {
+  k_order_multi<<<grid, NT, 0, st>>>(g);
   return cudaGetLastError();
 }
 

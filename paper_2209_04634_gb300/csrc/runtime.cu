@@ -12,74 +12,50 @@
 #include <new>
 #include <vector>
 
-#include "../../include/evsim.h"
-#include "internal.h"
+#include "handle.h"
 
-using evsim::Ctl;
-using evsim::Ev;
-
-struct ProfRec {
-  int kind;
-  cudaEvent_t a, b;
-};
-
-struct sim_s {
-  sim_config cfg{};
-  int W = 0, H = 0, ch = 1;
-  long long P = 0;
-  int n_max = 0;
-  int tiles_x = 0, tiles_y = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int device = 0;
-  int sms = 1;
-
-  int* d_lut = nullptr;
-  unsigned short* d_cpmap = nullptr;
-  unsigned short* d_cnmap = nullptr;
-  unsigned char* d_ring[2] = {nullptr, nullptr};
-  int* d_R[2] = {nullptr, nullptr};
-  Ctl* d_ctl = nullptr;
-  unsigned long long* d_maxf2 = nullptr;
-  Ev* d_staging = nullptr;
-  Ev* d_events = nullptr;
-  evsim::Seg* d_seg = nullptr;
-  unsigned long long* d_order_status = nullptr;
-  evsim::FrameDesc* d_desc = nullptr;       // bmax descriptors of the batch in flight
-  unsigned char* d_stage_frames = nullptr;  // host batches: staged frames and flows
-  float2* d_stage_flows = nullptr;
-  long long stage_frames = 0;               // frames the host staging holds
-  long long event_cap = 0;
-  long long segs_per_k = 0;
-  int bmax = 1;
-  int order_grid = 1;
-
-  // host shadow of the stream
-  bool have_first = false;
-  long long t0 = 0, t_last = 0;
-  long long pushed = 0;
-  unsigned serial = 0;
-  long long popped = 0;
-  long long popped_total = 0;
-
-  bool prof = false;
-  std::vector<ProfRec> pending;
-  std::vector<cudaEvent_t> pool;
-  double prof_ms[SIM_K_COUNT] = {};
-  long long prof_n[SIM_K_COUNT] = {};
-};
-
-namespace {
+namespace evsim_rt {
 
 std::mutex g_attr_mu;
 int g_attr_nmax = 0;
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 
-template <class T>
-cudaError_t dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) return cudaSuccess;
-  return cudaMalloc((void**)p, count * sizeof(T));
+// Sizes of a handle's device buffers.
+struct Sizing {
+  int n_max, tiles_x;
+  long long P, cap, segs_per_k, seg_cap, ochunks;
+  int bmax;
+};
+
+Sizing sizing(const sim_config& c) {
+  Sizing z{};
+  z.P = (long long)c.width * c.height;
+  z.n_max = c.substeps > 0 ? c.substeps : c.max_substeps;
+  z.tiles_x = (c.width + evsim::TW - 1) / evsim::TW;
+  long long cap = c.event_capacity > 0 ? c.event_capacity : std::max<long long>(1LL << 20, 8 * z.P);
+  z.cap = std::min<long long>(cap, evsim::MAX_EVENTS);
+  z.segs_per_k = (long long)c.height * z.tiles_x;  // one segment per tile row
+  // frames per batch: the requested cap, else what a 512 MB segment table holds
+  const long long seg_bytes_per_frame = z.segs_per_k * z.n_max * (long long)sizeof(evsim::Seg);
+  const long long bm = c.max_batch > 0
+                           ? c.max_batch
+                           : std::max(1LL, (512LL << 20) / std::max(1LL, seg_bytes_per_frame));
+  z.bmax = (int)std::min<long long>(bm, SIM_MAX_BATCH);
+  z.seg_cap = (long long)z.bmax * z.n_max * z.segs_per_k;
+  z.ochunks = std::max(1LL, (z.seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
+  return z;
+}
+
+long long state_bytes(const sim_config& c) {
+  const Sizing z = sizing(c);
+  long long b = 256 * 4 + 2 * z.P + (long long)sizeof(Ctl) + 8LL * z.bmax;
+  if (c.ref_mode == SIM_REF_ACCUM) b += 8 * z.P;
+  b += 2 * z.cap * (long long)sizeof(Ev);                // staging + events
+  b += z.seg_cap * (long long)sizeof(evsim::Seg) + 8 * z.ochunks;
+  b += (long long)z.bmax * sizeof(evsim::FrameDesc);
+  b += z.P * c.pixel_format;                             // host-frame staging (one frame)
+  if (c.c_pos_map) b += 4 * z.P;
+  return b;
 }
 
 void build_lut(int intensity, int lut[256]) {
@@ -279,7 +255,9 @@ cudaError_t enqueue_batch(sim_t* s, int n) {
   return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, b, s->stream, s->order_grid); });
 }
 
-}  // namespace
+}  // namespace evsim_rt
+
+using namespace evsim_rt;
 
 void evsim::note_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
@@ -372,19 +350,13 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   cudaGetDevice(&s->device);
   s->sms = std::max(1, evsim::device_sm_count());
 
-  long long cap = c.event_capacity > 0 ? c.event_capacity : std::max<long long>(1LL << 20, 8 * P);
-  cap = std::min<long long>(cap, evsim::MAX_EVENTS);
+  const Sizing z = sizing(c);
+  const long long cap = z.cap;
   s->event_cap = cap;
-  const bool sparse = c.mode == SIM_SPARSE;
-  (void)sparse;
-  s->segs_per_k = (long long)c.height * s->tiles_x;  // one segment per tile row
-  // frames per batch: the requested cap, else what a 512 MB segment table holds
-  const long long seg_bytes_per_frame = s->segs_per_k * s->n_max * (long long)sizeof(evsim::Seg);
-  long long bm = c.max_batch > 0 ? c.max_batch
-                                 : std::max(1LL, (512LL << 20) / std::max(1LL, seg_bytes_per_frame));
-  s->bmax = (int)std::min<long long>(bm, SIM_MAX_BATCH);
-  const long long seg_cap = (long long)s->bmax * s->n_max * s->segs_per_k;
-  const long long ochunks = std::max(1LL, (seg_cap + evsim::OCHUNK - 1) / evsim::OCHUNK);
+  s->segs_per_k = z.segs_per_k;
+  s->bmax = z.bmax;
+  const long long seg_cap = z.seg_cap;
+  const long long ochunks = z.ochunks;
 
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };

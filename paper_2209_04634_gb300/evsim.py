@@ -23,6 +23,7 @@ SIM_ERR_ARG, SIM_ERR_CUDA, SIM_ERR_OOM, SIM_ERR_TIME = -1, -2, -3, -4
 SIM_ERR_TIME_RANGE, SIM_ERR_EVENT_OVERFLOW, SIM_ERR_DEVICE_TIMEOUT = -5, -6, -7
 SIM_ERR_STATE, SIM_ERR_ADMIT, SIM_ERR_NO_DEVICE = -8, -9, -10
 SIM_ERR_TOO_LARGE = -11
+SIM_MAX_GROUP = 1024
 SIM_STATIC_SCRATCH_BYTES = 32 << 20
 SIM_LUMA8, SIM_RGB8 = 1, 3
 SIM_DENSE, SIM_SPARSE = 0, 1
@@ -61,6 +62,24 @@ class sim_stats(ctypes.Structure):
     ]
 
 
+class simb_config(ctypes.Structure):
+    _fields_ = [
+        ("max_streams", ctypes.c_int32), ("frames_per_step", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_int64), ("use_graphs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class simb_stats(ctypes.Structure):
+    _fields_ = [
+        ("members", ctypes.c_int32), ("tile_classes", ctypes.c_int32),
+        ("bytes_used", ctypes.c_int64), ("budget", ctypes.c_int64),
+        ("steps", ctypes.c_int64), ("frames_stepped", ctypes.c_int64),
+        ("graph_captures", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64), ("admit_refused", ctypes.c_int64),
+    ]
+
+
 # (name, restype, argtypes) of every function that include/evsim.h declares
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 SIGNATURES = [
@@ -81,6 +100,18 @@ SIGNATURES = [
     ("sim_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("sim_version", ctypes.c_char_p, []),
     ("sim_last_cuda_error", ctypes.c_char_p, []),
+    ("simb_config_default", ctypes.c_int, [ctypes.POINTER(simb_config)]),
+    ("simb_create", ctypes.c_int, [ctypes.POINTER(simb_config), ctypes.POINTER(_VP)]),
+    ("simb_state_bytes", ctypes.c_int, [_VP, ctypes.POINTER(sim_config), ctypes.POINTER(_I64)]),
+    ("simb_admit", ctypes.c_int, [_VP, ctypes.POINTER(sim_config), ctypes.POINTER(_I32)]),
+    ("simb_push", ctypes.c_int, [_VP, _I32, _VP, _I64, _VP, _I64, _I32]),
+    ("simb_step", ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+    ("simb_pop", ctypes.c_int, [_VP, _I32, _VP, _I64, ctypes.POINTER(_I64), _I32]),
+    ("simb_stream_stats", ctypes.c_int, [_VP, _I32, ctypes.POINTER(sim_stats)]),
+    ("simb_evict", ctypes.c_int, [_VP, _I32]),
+    ("simb_sync", ctypes.c_int, [_VP]),
+    ("simb_get_stats", ctypes.c_int, [_VP, ctypes.POINTER(simb_stats)]),
+    ("simb_destroy", ctypes.c_int, [_VP]),
     ("sim_step_pair_static", ctypes.c_int, [ctypes.POINTER(sim_config), _VP, _I64, _VP, _I64, _VP,
                                             _I64, _I64, _VP, _VP, _VP, _I64,
                                             ctypes.POINTER(_I64)]),
@@ -292,6 +323,156 @@ class Simulator:
 
     def __exit__(self, *a):
         self.close()
+
+
+def make_config(width: int, height: int, *, pixel_format: int = SIM_LUMA8,
+                mode: int = SIM_DENSE, substeps: int = 8, max_substeps: int = 16,
+                intensity: int = SIM_LOG, ref_mode: int = SIM_REF_ACCUM,
+                c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
+                c_pos_map=None, c_neg_map=None, event_capacity: int = 0):
+    """A sim_config (plus the threshold-map arrays it points to, which must
+    outlive the call that reads it)."""
+    cfg = sim_config()
+    check(load().sim_config_default(ctypes.byref(cfg), width, height), "sim_config_default")
+    cfg.pixel_format = pixel_format
+    cfg.mode = mode
+    cfg.substeps = substeps
+    cfg.max_substeps = max_substeps
+    cfg.intensity = intensity
+    cfg.ref_mode = ref_mode
+    cfg.c_pos_q16 = c_pos_q16
+    cfg.c_neg_q16 = c_neg_q16
+    cfg.c_act_q16 = c_act_q16
+    keep = None
+    if c_pos_map is not None:
+        cp = np.ascontiguousarray(c_pos_map, dtype=np.uint16)
+        cn = np.ascontiguousarray(c_neg_map, dtype=np.uint16)
+        keep = (cp, cn)
+        cfg.c_pos_map = cp.ctypes.data
+        cfg.c_neg_map = cn.ctypes.data
+    cfg.event_capacity = event_capacity
+    return cfg, keep
+
+
+class Group:
+    """A multi-stream group (simb_*): admit streams, push frames to members,
+    advance all of them with step(), pop each member's events."""
+
+    def __init__(self, max_streams: int = 64, frames_per_step: int = 4,
+                 hbm_budget_bytes: int = 0, use_graphs: bool = True, stream=None):
+        lib = load()
+        cfg = simb_config()
+        check(lib.simb_config_default(ctypes.byref(cfg)), "simb_config_default")
+        cfg.max_streams = max_streams
+        cfg.frames_per_step = frames_per_step
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.use_graphs = 1 if use_graphs else 0
+        if stream is not None:
+            handle = int(getattr(stream, "cuda_stream", stream))
+            cfg.cuda_stream = handle if handle else CUDA_STREAM_LEGACY
+        h = ctypes.c_void_p()
+        check(lib.simb_create(ctypes.byref(cfg), ctypes.byref(h)), "simb_create")
+        self.h = h
+        self._lib = lib
+        self.shapes = {}
+
+    def state_bytes(self, width: int, height: int, **kw) -> int:
+        cfg, _keep = make_config(width, height, **kw)
+        out = ctypes.c_int64(0)
+        check(self._lib.simb_state_bytes(self.h, ctypes.byref(cfg), ctypes.byref(out)),
+              "simb_state_bytes")
+        return int(out.value)
+
+    def admit(self, width: int, height: int, **kw) -> int | None:
+        """Member id, or None when admission is refused."""
+        cfg, _keep = make_config(width, height, **kw)
+        out = ctypes.c_int32(-1)
+        rc = self._lib.simb_admit(self.h, ctypes.byref(cfg), ctypes.byref(out))
+        if rc == SIM_ERR_ADMIT:
+            return None
+        check(rc, "simb_admit")
+        self.shapes[int(out.value)] = (width, height, kw.get("pixel_format", SIM_LUMA8))
+        return int(out.value)
+
+    def push(self, sid: int, frame, flow, t_us: int, pitch: int | None = None) -> None:
+        dev = _is_device(frame)
+        if not dev:
+            frame = np.ascontiguousarray(frame, dtype=np.uint8)
+            if flow is not None:
+                flow = np.ascontiguousarray(flow, dtype=np.float32)
+        w, _, ch = self.shapes[sid]
+        if pitch is None:
+            pitch = w * ch
+        fp = 0 if flow is None else _ptr(flow)
+        check(self._lib.simb_push(self.h, sid, _ptr(frame), pitch, fp or None, int(t_us),
+                                  SIM_DEVICE if dev else SIM_HOST), "simb_push")
+
+    def step(self) -> int:
+        n = ctypes.c_int64(0)
+        check(self._lib.simb_step(self.h, ctypes.byref(n)), "simb_step")
+        return int(n.value)
+
+    def pop(self, sid: int, cap: int | None = None) -> np.ndarray:
+        st = self.stream_stats(sid)
+        cap = max(int(st.events_pending), 1) if cap is None else cap
+        out = np.empty(cap, dtype=EVENT_DTYPE)
+        n = ctypes.c_int64(0)
+        check(self._lib.simb_pop(self.h, sid, out.ctypes.data, cap, ctypes.byref(n), SIM_HOST),
+              "simb_pop")
+        return out[: n.value]
+
+    def pop_into(self, sid: int, out, cap: int) -> tuple[int, int]:
+        """Pop into a caller buffer (numpy: host; torch CUDA tensor: device);
+        returns (return code, events)."""
+        n = ctypes.c_int64(0)
+        rc = self._lib.simb_pop(self.h, sid, _ptr(out), cap, ctypes.byref(n),
+                                SIM_DEVICE if _is_device(out) else SIM_HOST)
+        check(rc, "simb_pop")
+        return rc, int(n.value)
+
+    def stream_stats(self, sid: int) -> sim_stats:
+        st = sim_stats()
+        check(self._lib.simb_stream_stats(self.h, sid, ctypes.byref(st)), "simb_stream_stats")
+        return st
+
+    def evict(self, sid: int) -> None:
+        check(self._lib.simb_evict(self.h, sid), "simb_evict")
+        self.shapes.pop(sid, None)
+
+    def sync(self) -> None:
+        check(self._lib.simb_sync(self.h), "simb_sync")
+
+    def stats(self) -> simb_stats:
+        st = simb_stats()
+        check(self._lib.simb_get_stats(self.h, ctypes.byref(st)), "simb_get_stats")
+        return st
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self._lib.simb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def seq_options(seq, **kw) -> dict:
+    """Simulator / Group.admit options for a synth.Sequence."""
+    args = dict(pixel_format=SIM_RGB8 if seq.channels == 3 else SIM_LUMA8,
+                substeps=seq.substeps, max_substeps=seq.max_substeps,
+                c_pos_q16=q16(seq.c_pos), c_neg_q16=q16(seq.c_neg),
+                c_pos_map=seq.cpos_map, c_neg_map=seq.cneg_map)
+    args.update(kw)
+    return args
 
 
 def simulator_for(seq, mode: int = SIM_DENSE, **kw) -> Simulator:

@@ -268,3 +268,45 @@ def mixed_streams(seed: int = 6209, frames: int = 50,
             out[-1].name = f"stream{sid}_{w}x{h}"
             sid += 1
     return out
+
+
+def shifted_streams(seed: int = 6209, unique_frames: int = 6,
+                    sizes=((240, 180, 32), (640, 480, 24), (1280, 720, 8)),
+                    max_substeps: int = 8) -> list[Sequence]:
+    """Many independent streams of mixed resolutions, cheap to generate: one
+    warped-texture sequence of `unique_frames` frames per resolution, and
+    each stream a distinct cyclic shift of it (frames, flow and threshold
+    maps shifted together, so every stream is a valid warped texture of its
+    own).  Play them to any length with `pingpong`."""
+    out = []
+    sid = 0
+    for k, (w, h, count) in enumerate(sizes):
+        base = warped_texture(seed=seed + 1000 * k, frames=unique_frames, width=w, height=h,
+                              max_substeps=max_substeps)
+        off = Rng(seed + 7 * k + 1).uniform(2 * count, 0.0, 1.0)
+        for j in range(count):
+            dy, dx = int(off[2 * j] * h), int(off[2 * j + 1] * w)
+            s = Sequence(f"stream{sid}_{w}x{h}", np.roll(base.frames, (dy, dx), axis=(1, 2)),
+                         np.roll(base.flows, (dy, dx), axis=(1, 2)), base.t_us.copy(),
+                         base.substeps, base.max_substeps, base.c_pos, base.c_neg,
+                         np.roll(base.cpos_map, (dy, dx), axis=(0, 1)),
+                         np.roll(base.cneg_map, (dy, dx), axis=(0, 1)),
+                         info={"seed": seed + 1000 * k, "shift": (dy, dx)})
+            out.append(s)
+            sid += 1
+    return out
+
+
+def pingpong(step: int, n: int) -> tuple[int, int, int]:
+    """Frame played at `step` (>= 1) when n frames are replayed forward and
+    backward, the frame before it, and the sign of the stored flow to use:
+    (b, a, +1) uses flows[b] (a = b - 1); (b, a, -1) uses -flows[a]
+    (a = b + 1), the exact reverse of a warped-texture step."""
+    period = 2 * (n - 1)
+
+    def at(t):
+        p = t % period
+        return p if p < n else period - p
+
+    a, b = at(step - 1), at(step)
+    return (b, a, 1) if b == a + 1 else (b, a, -1)
