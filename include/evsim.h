@@ -236,6 +236,7 @@ typedef struct {
   int32_t use_graphs;        /* 1: replay one CUDA graph per member set; 0: plain launches */
   int32_t reserved;
   void* cuda_stream;         /* cudaStream_t; NULL: group-owned stream */
+  int64_t delivery_events;   /* simb_step_deliver: events per delivery area; 0: 2^23 */
 } simb_config;
 
 typedef struct {
@@ -286,6 +287,43 @@ int simb_push(simb_t* g, int32_t id, const void* frame, int64_t pitch_bytes, con
  * that member back, as for a sim_t. */
 int simb_step(simb_t* g, int64_t* frames);
 
+/* One member's share of a delivered step. */
+typedef struct {
+  int32_t id;                /* member id */
+  int32_t status;            /* SIM_OK, or the member's device error (its frames of this
+                                step and later queued frames are dropped, as for a sim_t;
+                                see sim_pop_events) */
+  int64_t first;             /* index of its first event in the delivered array */
+  int64_t count;             /* events delivered (in the member's output order) */
+  int64_t frames_committed;  /* the member's committed frames after this step */
+  int64_t pixel_substeps;    /* the member's sum over committed frames of W H N */
+} simb_delivery;
+
+/* Serving form of a step: simb_step, then one more kernel that copies every
+ * member's committed, undelivered events into a library-owned pinned host
+ * area (delivery_events events; members in table order, each member's events
+ * contiguous) and fills one simb_delivery per member.  Asynchronous: two
+ * deliveries may be in flight (the areas alternate), so the next step can be
+ * launched before the host reads this one.  Events that do not fit the area
+ * stay on the device for the next delivery.  May be called with no frames
+ * queued (delivers only).  A group that delivers must not use simb_pop
+ * (SIM_ERR_STATE); SIM_ERR_STATE as well when two deliveries are already
+ * uncollected. */
+int simb_step_deliver(simb_t* g, int64_t* frames);
+
+/* Wait for the oldest uncollected delivery and return its table (*n entries,
+ * one per member at the time of the step) and its events (*n_events).  The
+ * pointers stay valid until the second simb_step_deliver after this call.
+ * Members that reported a device error are rolled back here (this waits for
+ * the group's stream).  SIM_ERR_STATE when no delivery is in flight. */
+int simb_collect(simb_t* g, const simb_delivery** table, int32_t* n, const sim_event** events,
+                 int64_t* n_events);
+
+/* 1 if the oldest uncollected delivery has finished on the device (so that
+ * simb_collect will not wait), 0 if not; SIM_ERR_STATE when none is in
+ * flight. */
+int simb_delivery_ready(simb_t* g);
+
 /* Committed events of member id, as sim_pop_events (waits for the group's
  * stream). */
 int simb_pop(simb_t* g, int32_t id, sim_event* out, int64_t cap, int64_t* n_out, int32_t mem);
@@ -294,7 +332,8 @@ int simb_pop(simb_t* g, int32_t id, sim_event* out, int64_t cap, int64_t* n_out,
 int simb_stream_stats(simb_t* g, int32_t id, sim_stats* st);
 
 /* Remove member id and free its state (waits for the group's stream);
- * its undelivered events are dropped. */
+ * its undelivered events are dropped.  SIM_ERR_STATE while deliveries are
+ * uncollected. */
 int simb_evict(simb_t* g, int32_t id);
 
 /* Wait for the group's stream. */
@@ -304,6 +343,93 @@ int simb_get_stats(simb_t* g, simb_stats* st);
 
 /* Evict every member and free the group. */
 int simb_destroy(simb_t* g);
+
+/* ---- serving loop -----------------------------------------------------------
+ * A request loop over the library (host code, one thread): camera streams
+ * arrive as a Poisson process, are admitted while their device state fits a
+ * memory budget (first come, first served; a stream that does not fit waits),
+ * release frames on a wall-clock timeline at their own frame rate, and leave
+ * when their duration ends.  Two policies serve the same arrival trace:
+ *   SIM_SERVE_GROUP      continuous batching: every iteration queues the
+ *                        frames that have arrived and launches one group step
+ *                        for all streams (simb_step_deliver); the host
+ *                        collects a step's events while the next one runs.
+ *   SIM_SERVE_PER_STREAM one sim_t and one CUDA stream per camera: each frame
+ *                        is pushed as it arrives, and each stream with frames
+ *                        in flight is popped every iteration.
+ * Latency of a frame = time its events are in host memory - its release time.
+ * Frames are device-resident content pools (a camera feeding device memory,
+ * e.g. a hardware decoder); frame j of a stream is pool frame
+ * pingpong(j + phase). */
+enum { SIM_SERVE_GROUP = 0, SIM_SERVE_PER_STREAM = 1 };
+
+typedef struct {
+  int32_t width, height;             /* luma frames, pitch = width */
+  int32_t frames;                    /* U >= 2 pool frames, replayed forward and backward */
+  int32_t substeps, max_substeps;    /* as sim_config */
+  int32_t c_pos_q16, c_neg_q16;
+  int32_t reserved;
+  const void* const* frame;          /* U device pointers */
+  const float* const* flow;          /* U device pointers: flow from pool frame u-1 to u */
+  const float* const* flow_back;     /* U device pointers: flow from pool frame u to u-1 */
+  const uint16_t* c_pos_map;         /* optional host W*H maps, as sim_config */
+  const uint16_t* c_neg_map;
+} sim_serve_pool;
+
+typedef struct {
+  int32_t sid;                       /* index in the arrival trace */
+  int32_t width, height, fps;
+  int32_t pool, phase;
+  int32_t frames;                    /* frames whose events were delivered (frame 0 included) */
+  int32_t status;                    /* SIM_OK or the stream's first device error */
+  int64_t events;
+  uint64_t digest;                   /* sum of e_i M^(n-1-i) mod 2^64 over the delivered
+                                        events e_0..e_{n-1} as 64-bit little-endian words,
+                                        M = 0x9E3779B97F4A7C15 */
+} sim_serve_stream;
+
+typedef struct {
+  int32_t policy;                    /* SIM_SERVE_GROUP | SIM_SERVE_PER_STREAM */
+  int32_t mode;                      /* SIM_DENSE | SIM_SPARSE */
+  double horizon_s;                  /* frames are released for this long */
+  double warmup_s;                   /* frames released earlier are not in the latency stats */
+  double rate_per_s;                 /* stream arrivals per second */
+  double dur_min_s, dur_max_s;       /* stream duration, uniform */
+  int32_t warm_start;                /* 1: streams that arrived in the dur_max_s before t = 0
+                                        and are still running are present at t = 0 */
+  int32_t n_pools;                   /* stream size: one of the pools, uniform */
+  const sim_serve_pool* pools;
+  int32_t n_fps;                     /* stream frame rate: uniform over fps[] */
+  int32_t reserved;
+  const int32_t* fps;
+  uint64_t seed;                     /* arrival trace */
+  int32_t max_streams;               /* streams at once */
+  int32_t frames_per_step;           /* frames a stream may have in flight */
+  int64_t hbm_budget_bytes;          /* admission bound on the streams' device state */
+  int64_t events_per_pixel;          /* event buffer of a stream: this x W x H events */
+  double* latency_ms;                /* optional: latencies of the counted frames */
+  int64_t latency_cap;
+  sim_serve_stream* streams;         /* optional: one record per admitted stream */
+  int32_t streams_cap;
+  int32_t reserved2;
+} sim_serve_config;
+
+typedef struct {
+  int64_t arrived, admitted, never_admitted, peak_streams;
+  int64_t frames_released, frames_completed, frames_failed;
+  int64_t events, pixel_substeps, steps, kernel_launches;
+  double wall_s;                     /* from t = 0 until the last event was delivered */
+  double gpix_substeps_per_s, events_per_s;
+  double lat_p50_ms, lat_p90_ms, lat_p99_ms, lat_max_ms, lat_mean_ms;
+  double admit_wait_p50_ms, admit_wait_p99_ms;
+  int64_t latencies;                 /* frames in the latency statistics */
+  int32_t streams_written;
+  int32_t reserved;
+} sim_serve_result;
+
+/* Run the loop to the horizon and until every released frame is delivered.
+ * Uses the current device; allocates and frees all state itself. */
+int sim_serve_run(const sim_serve_config* cfg, sim_serve_result* res);
 
 /* ---- allocation-free frame pair ------------------------------------------
  * The paper has no counterpart: this is a library service for callers that

@@ -51,21 +51,21 @@ struct simb_s {
   std::vector<int> id_slot;      // id -> index in members (-1: free)
   long long bytes_used = 0;
 
-  // device tables: [GroupTotals][StreamStep x max][FrameDesc x max x fmax]
+  // per-step device table: [GroupTotals][StreamStep x max][ActiveTile x max]
+  // [FrameDesc x max x fmax], uploaded in one copy from a pinned mirror
   unsigned char* d_step = nullptr;
-  unsigned char* h_step = nullptr;  // pinned mirror
+  unsigned char* h_step = nullptr;
   size_t step_bytes = 0;
   GroupStream* d_gs = nullptr;
   GroupCtl* d_gctl = nullptr;
-  int* d_block_map = nullptr;
-  size_t block_map_cap = 0;
   cudaEvent_t copy_done = nullptr;
   bool copy_pending = false;
 
   // launch plan of the current member set
   bool dirty = true;
-  int cls_off[evsim::TILE_CLASSES] = {};
-  int cls_tiles[evsim::TILE_CLASSES] = {};
+  int cls_moff[evsim::TILE_CLASSES] = {};   // first work-list slot of each class
+  int cls_tiles[evsim::TILE_CLASSES] = {};  // tiles of all members of the class
+  int cls_grid[evsim::TILE_CLASSES] = {};
   size_t cls_smem[evsim::TILE_CLASSES] = {};
   int n_classes = 0;
   bool any_adaptive = false;
@@ -74,20 +74,46 @@ struct simb_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 
+  // delivery areas (serving form of a step), alternating
+  struct Area {
+    unsigned char* host = nullptr;   // pinned, mapped: events, table, total
+    evsim::Ev* h_events = nullptr;
+    evsim::Delivery* h_table = nullptr;
+    long long* h_total = nullptr;
+    evsim::Ev* d_events = nullptr;   // device views of the same memory
+    evsim::Delivery* d_table = nullptr;
+    long long* d_total = nullptr;
+    cudaEvent_t done = nullptr;
+    int n = 0;
+  };
+  Area area[2];
+  bool delivering = false;
+  int next_area = 0;
+  int oldest = 0;
+  int inflight = 0;
+  long long deliv_cap = 0;
+  int* d_ids = nullptr;              // member ids in table order
+
   simb_stats st{};
 };
 
 namespace {
 
+static_assert(sizeof(GroupTotals) <= 256, "totals fit their slot");
 size_t off_steps() { return 256; }
-size_t off_desc(const simb_t* g) {
+size_t off_act(const simb_t* g) {
   return (off_steps() + sizeof(StreamStep) * g->cfg.max_streams + 255) & ~(size_t)255;
+}
+size_t off_desc(const simb_t* g) {
+  return (off_act(g) + sizeof(evsim::ActiveTile) * g->cfg.max_streams + 255) & ~(size_t)255;
 }
 GroupTotals* d_tot(const simb_t* g) { return (GroupTotals*)g->d_step; }
 StreamStep* d_steps(const simb_t* g) { return (StreamStep*)(g->d_step + off_steps()); }
+evsim::ActiveTile* d_act(const simb_t* g) { return (evsim::ActiveTile*)(g->d_step + off_act(g)); }
 FrameDesc* d_desc(const simb_t* g) { return (FrameDesc*)(g->d_step + off_desc(g)); }
 GroupTotals* h_tot(const simb_t* g) { return (GroupTotals*)g->h_step; }
 StreamStep* h_steps(const simb_t* g) { return (StreamStep*)(g->h_step + off_steps()); }
+evsim::ActiveTile* h_act(const simb_t* g) { return (evsim::ActiveTile*)(g->h_step + off_act(g)); }
 FrameDesc* h_desc(const simb_t* g) { return (FrameDesc*)(g->h_step + off_desc(g)); }
 
 int order_chunks(const sim_t* s, int count) {
@@ -102,12 +128,13 @@ void drop_graph(simb_t* g) {
   g->graph = nullptr;
 }
 
-// Rebuild the member table, the tile block maps and the launch plan after a
-// change of members (the group's stream is idle).
+// Rebuild the member table and the launch plan after a change of members
+// (the group's stream is idle).
 int rebuild(simb_t* g) {
   drop_graph(g);
   const int n = (int)g->members.size();
   std::vector<GroupStream> gs(n);
+  int cls_members[evsim::TILE_CLASSES] = {};
   std::fill(std::begin(g->cls_tiles), std::end(g->cls_tiles), 0);
   std::fill(std::begin(g->cls_smem), std::end(g->cls_smem), 0);
   g->any_adaptive = false;
@@ -115,39 +142,26 @@ int rebuild(simb_t* g) {
   for (int i = 0; i < n; ++i) {
     const Member* m = g->members[i];
     g->cls_tiles[m->cls] += m->tiles;
+    cls_members[m->cls] += 1;
     g->cls_smem[m->cls] = std::max(g->cls_smem[m->cls], evsim::tile_smem_bytes(m->s->n_max));
     g->any_adaptive |= m->adaptive;
     max_chunks += order_chunks(m->s, g->fmax);
-  }
-  int total = 0;
-  g->n_classes = 0;
-  for (int c = 0; c < evsim::TILE_CLASSES; ++c) {
-    g->cls_off[c] = total;
-    total += g->cls_tiles[c];
-    if (g->cls_tiles[c]) ++g->n_classes;
-  }
-  std::vector<int> map(std::max(total, 1));
-  int fill[evsim::TILE_CLASSES];
-  std::memcpy(fill, g->cls_off, sizeof(fill));
-  for (int i = 0; i < n; ++i) {
-    const Member* m = g->members[i];
     gs[i].p = evsim_rt::make_params(m->s);
     gs[i].frames = d_desc(g) + (size_t)i * g->fmax;
-    gs[i].tile_begin = fill[m->cls] - g->cls_off[m->cls];
     gs[i].pre_blocks = m->pre_blocks;
-    for (int t = 0; t < m->tiles; ++t) map[fill[m->cls] + t] = i;
-    fill[m->cls] += m->tiles;
   }
-  cudaError_t e = cudaSuccess;
-  if ((size_t)map.size() > g->block_map_cap) {
-    cudaFree(g->d_block_map);
-    g->d_block_map = nullptr;
-    g->block_map_cap = 0;
-    e = evsim_rt::dalloc(&g->d_block_map, map.size() * 2);
-    if (e != cudaSuccess) return cuda_rc(e);
-    g->block_map_cap = map.size() * 2;
+  g->n_classes = 0;
+  int moff = 0;
+  for (int c = 0; c < evsim::TILE_CLASSES; ++c) {
+    g->cls_moff[c] = moff;
+    moff += cls_members[c];
+    // persistent tile grid: two blocks per SM (the kernel's residency)
+    g->cls_grid[c] = std::min(g->cls_tiles[c], 2 * g->sms);
+    if (g->cls_tiles[c]) ++g->n_classes;
   }
-  e = cudaMemcpy(g->d_block_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice);
+  std::vector<int> ids(std::max(n, 1));
+  for (int i = 0; i < n; ++i) ids[i] = g->members[i]->id;
+  cudaError_t e = cudaMemcpy(g->d_ids, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && n > 0)
     e = cudaMemcpy(g->d_gs, gs.data(), n * sizeof(GroupStream), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
@@ -163,14 +177,40 @@ int rebuild(simb_t* g) {
   return SIM_OK;
 }
 
-// The step's launches (also what a graph captures).
-cudaError_t launch_step(simb_t* g, int* launches) {
+GroupArg group_arg(const simb_t* g) {
   GroupArg a{};
   a.gs = g->d_gs;
   a.steps = d_steps(g);
   a.tot = d_tot(g);
   a.gctl = g->d_gctl;
   a.n = (int)g->members.size();
+  return a;
+}
+
+// Pinned, mapped delivery areas (allocated at the first delivery).
+int alloc_areas(simb_t* g) {
+  const size_t ev = (size_t)g->deliv_cap * sizeof(evsim::Ev);
+  const size_t tab = (size_t)g->cfg.max_streams * sizeof(evsim::Delivery);
+  for (auto& a : g->area) {
+    if (a.host) continue;
+    cudaError_t e = cudaHostAlloc((void**)&a.host, ev + tab + 64, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming);
+    unsigned char* d = nullptr;
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&d, a.host, 0);
+    if (e != cudaSuccess) return cuda_rc(e);
+    a.h_events = (evsim::Ev*)a.host;
+    a.h_table = (evsim::Delivery*)(a.host + ev);
+    a.h_total = (long long*)(a.host + ev + tab);
+    a.d_events = (evsim::Ev*)d;
+    a.d_table = (evsim::Delivery*)(d + ev);
+    a.d_total = (long long*)(d + ev + tab);
+  }
+  return SIM_OK;
+}
+
+// The step's launches (also what a graph captures).
+cudaError_t launch_step(simb_t* g, int* launches) {
+  const GroupArg a = group_arg(g);
   int k = 0;
   cudaError_t e = cudaSuccess;
   if (g->any_adaptive) {
@@ -179,7 +219,7 @@ cudaError_t launch_step(simb_t* g, int* launches) {
   }
   for (int c = 0; c < evsim::TILE_CLASSES && e == cudaSuccess; ++c) {
     if (!g->cls_tiles[c]) continue;
-    e = evsim::launch_tile_multi(a, c, g->d_block_map + g->cls_off[c], g->cls_tiles[c],
+    e = evsim::launch_tile_multi(a, c, d_act(g) + g->cls_moff[c], g->cls_grid[c],
                                  g->cls_smem[c], g->stream);
     ++k;
   }
@@ -207,7 +247,11 @@ void free_group(simb_t* g) {
   cudaFreeHost(g->h_step);
   cudaFree(g->d_gs);
   cudaFree(g->d_gctl);
-  cudaFree(g->d_block_map);
+  cudaFree(g->d_ids);
+  for (auto& a : g->area) {
+    if (a.host) cudaFreeHost(a.host);
+    if (a.done) cudaEventDestroy(a.done);
+  }
   if (g->copy_done) cudaEventDestroy(g->copy_done);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
 }
@@ -238,6 +282,7 @@ int simb_create(const simb_config* cfg, simb_t** out) {
   if (cfg->max_streams < 1 || cfg->max_streams > SIM_MAX_GROUP) return SIM_ERR_ARG;
   if (cfg->frames_per_step < 1 || cfg->frames_per_step > SIM_MAX_SUBSTEPS) return SIM_ERR_ARG;
   if (cfg->hbm_budget_bytes < 0) return SIM_ERR_ARG;
+  if (cfg->delivery_events < 0 || cfg->delivery_events > evsim::MAX_EVENTS) return SIM_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SIM_ERR_NO_DEVICE;
   simb_t* g = new (std::nothrow) simb_t();
@@ -263,6 +308,8 @@ int simb_create(const simb_config* cfg, simb_t** out) {
   chk(cudaMallocHost((void**)&g->h_step, g->step_bytes));
   chk(evsim_rt::dalloc(&g->d_gs, (size_t)cfg->max_streams));
   chk(evsim_rt::dalloc(&g->d_gctl, 1));
+  chk(evsim_rt::dalloc(&g->d_ids, (size_t)cfg->max_streams));
+  g->deliv_cap = cfg->delivery_events > 0 ? cfg->delivery_events : (1LL << 23);
   chk(cudaEventCreateWithFlags(&g->copy_done, cudaEventDisableTiming));
   if (e == cudaSuccess) {
     std::memset(g->h_step, 0, g->step_bytes);
@@ -423,6 +470,9 @@ int simb_step(simb_t* g, int64_t* frames) {
   const int n = (int)g->members.size();
   StreamStep* hs = h_steps(g);
   FrameDesc* hd = h_desc(g);
+  evsim::ActiveTile* ha = h_act(g);
+  GroupTotals* ht = h_tot(g);
+  std::memset(ht, 0, sizeof(GroupTotals));
   int chunks = 0, pre = 0;
   long long nf = 0;
   for (int i = 0; i < n; ++i) {
@@ -434,14 +484,18 @@ int simb_step(simb_t* g, int64_t* frames) {
     st.chunk_begin = chunks;
     st.pre_begin = pre;
     if (!cnt) continue;
+    evsim::ActiveTile& a = ha[g->cls_moff[m->cls] + ht->active[m->cls]++];
+    a.member = i;
+    a.tile_begin = ht->tiles[m->cls];
+    ht->tiles[m->cls] += m->tiles;
     chunks += order_chunks(m->s, cnt);
     if (m->adaptive) pre += cnt * m->pre_blocks;
     for (int j = 0; j < cnt; ++j) hd[(size_t)i * g->fmax + j] = m->q[j].d;
     nf += cnt;
   }
   if (nf == 0) return SIM_OK;
-  h_tot(g)->chunks = chunks;
-  h_tot(g)->pre_items = pre;
+  ht->chunks = chunks;
+  ht->pre_items = pre;
   const size_t bytes = off_desc(g) + sizeof(FrameDesc) * (size_t)n * g->fmax;
   e = cudaMemcpyAsync(g->d_step, g->h_step, bytes, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaEventRecord(g->copy_done, g->stream);
@@ -487,9 +541,81 @@ int simb_step(simb_t* g, int64_t* frames) {
   return SIM_OK;
 }
 
+int simb_step_deliver(simb_t* g, int64_t* frames) {
+  if (!g) return SIM_ERR_ARG;
+  if (frames) *frames = 0;
+  if (g->inflight == 2) return SIM_ERR_STATE;
+  int rc = alloc_areas(g);
+  if (rc) return rc;
+  g->delivering = true;
+  rc = simb_step(g, frames);
+  if (rc) return rc;
+  auto& A = g->area[g->next_area];
+  evsim::DrainArg d{};
+  d.events = A.d_events;
+  d.cap = g->deliv_cap;
+  d.table = A.d_table;
+  d.total = A.d_total;
+  d.ids = g->d_ids;
+  d.done = &g->d_gctl->drain_done;
+  cudaError_t e = evsim::launch_drain(group_arg(g), d, g->sms * 2, g->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(A.done, g->stream);
+  if (e != cudaSuccess) return cuda_rc(e);
+  g->st.kernel_launches += 1;
+  A.n = (int)g->members.size();
+  g->next_area ^= 1;
+  g->inflight += 1;
+  return SIM_OK;
+}
+
+int simb_collect(simb_t* g, const simb_delivery** table, int32_t* n, const sim_event** events,
+                 int64_t* n_events) {
+  if (!g || !table || !n || !events || !n_events) return SIM_ERR_ARG;
+  if (!g->inflight) return SIM_ERR_STATE;
+  auto& A = g->area[g->oldest];
+  cudaError_t e = cudaEventSynchronize(A.done);
+  if (e != cudaSuccess) return cuda_rc(e);
+  bool synced = false;
+  for (int i = 0; i < A.n; ++i) {
+    if (!A.h_table[i].status) continue;
+    Member* m = member(g, A.h_table[i].id);
+    if (!m) continue;
+    if (!synced) {
+      e = cudaStreamSynchronize(g->stream);
+      if (e != cudaSuccess) return cuda_rc(e);
+      synced = true;
+    }
+    Ctl c;
+    int rc = evsim_rt::read_ctl(m->s, &c);
+    if (rc) return rc;
+    if (!c.err) continue;  // already rolled back by an earlier collect
+    rc = evsim_rt::recover(m->s, &c);
+    if (rc) return rc;
+    m->q.clear();
+  }
+  static_assert(sizeof(simb_delivery) == sizeof(evsim::Delivery), "delivery layout");
+  *table = (const simb_delivery*)A.h_table;
+  *n = A.n;
+  *events = (const sim_event*)A.h_events;
+  *n_events = *A.h_total;
+  g->oldest ^= 1;
+  g->inflight -= 1;
+  return SIM_OK;
+}
+
+int simb_delivery_ready(simb_t* g) {
+  if (!g) return SIM_ERR_ARG;
+  if (!g->inflight) return SIM_ERR_STATE;
+  const cudaError_t e = cudaEventQuery(g->area[g->oldest].done);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return cuda_rc(e);
+}
+
 int simb_pop(simb_t* g, int32_t id, sim_event* out, int64_t cap, int64_t* n_out, int32_t mem) {
   Member* m = member(g, id);
   if (!m) return SIM_ERR_ARG;
+  if (g->delivering) return SIM_ERR_STATE;
   const int rc = sim_pop_events(m->s, out, cap, n_out, mem);
   // a device failure rolled the member back to its last committed frame:
   // frames queued after the failure are dropped as well
@@ -506,6 +632,7 @@ int simb_stream_stats(simb_t* g, int32_t id, sim_stats* st) {
 int simb_evict(simb_t* g, int32_t id) {
   Member* m = member(g, id);
   if (!m) return SIM_ERR_ARG;
+  if (g->inflight) return SIM_ERR_STATE;  // collect the deliveries first
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_rc(e);
   const int idx = g->id_slot[id];

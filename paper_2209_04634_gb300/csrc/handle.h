@@ -79,6 +79,11 @@ evsim::SimParams make_params(const sim_t* s);
 int cuda_rc(cudaError_t e);
 // Frame 0 of a stream: frame ring and reference (enqueued on s->stream).
 int push_first(sim_t* s, const void* frame, long long pitch, int64_t t_us, int32_t mem);
+// Wait for the handle's stream and read its control block.
+int read_ctl(sim_t* s, Ctl* c);
+// After a device-side failure: clear the error and the per-batch scratch and
+// roll the host shadow back to the last committed frame.
+int recover(sim_t* s, Ctl* c);
 // Device bytes sim_create allocates for a configuration (before host staging grows).
 long long state_bytes(const sim_config& c);
 

@@ -55,6 +55,7 @@ struct Ctl {
   unsigned int order_done;       // order kernel: chunks finished
   unsigned int order_exit;       // order kernel: blocks that left the ticket loop
   unsigned int pad0;
+  long long drained;             // group delivery: events of the buffer already delivered
 };
 
 // Per-frame arguments of a batch (device-resident table).
@@ -122,8 +123,8 @@ enum { TILE_RESET = 1, TILE_MAPS = 2, TILE_WIDE = 4, TILE_SPARSE = 8, TILE_CLASS
 struct GroupStream {            // per member; changes only when members change
   SimParams p;
   const FrameDesc* frames;      // the member's descriptor slots (device)
-  int tile_begin;               // first block of the member in its class's tile grid
   int pre_blocks;               // pre-pass blocks per frame (adaptive members)
+  int pad;
 };
 
 struct StreamStep {             // per member and step
@@ -136,11 +137,45 @@ struct StreamStep {             // per member and step
 struct GroupTotals {            // per step
   int chunks;                   // order tickets over all members
   int pre_items;                // pre-pass work items over all members
+  int tiles[TILE_CLASSES];      // tiles of the members with frames, per class
+  int active[TILE_CLASSES];     // members with frames, per class
+};
+
+// A member with frames in this step, in its class's work list: tiles
+// [tile_begin, tile_begin + its tile count) of the class's step are its.
+struct ActiveTile {
+  int member;
+  int tile_begin;
 };
 
 struct GroupCtl {
   unsigned int order_ticket;
   unsigned int order_exit;
+  unsigned int drain_done;
+  unsigned int tile_ticket;     // tile launches: next tile of the class's work list
+  unsigned int tile_exit;       // tile launches: blocks done
+  unsigned int pad[3];
+};
+
+// One member's share of a delivered step (same layout as simb_delivery).
+struct Delivery {
+  int id;
+  int status;
+  long long first;
+  long long count;
+  long long committed;
+  long long work_px;
+};
+
+// Destination of a delivery: host memory the device writes through its
+// mapping.
+struct DrainArg {
+  Ev* events;                   // cap events
+  long long cap;
+  Delivery* table;              // one entry per member
+  long long* total;             // events delivered
+  const int* ids;               // member ids in table order (device)
+  unsigned int* done;           // blocks finished (device, reset by the last block)
 };
 
 struct GroupArg {
@@ -164,9 +199,10 @@ cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st,
 cudaError_t configure_kernels(int n_max);
 int tile_class(const SimParams& p);
 cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st);
-cudaError_t launch_tile_multi(const GroupArg& g, int cls, const int* block_map, int grid,
+cudaError_t launch_tile_multi(const GroupArg& g, int cls, const ActiveTile* act, int grid,
                               size_t smem, cudaStream_t st);
 cudaError_t launch_order_multi(const GroupArg& g, int grid, cudaStream_t st);
+cudaError_t launch_drain(const GroupArg& g, const DrainArg& d, int grid, cudaStream_t st);
 // Shared-memory permission of the multi-stream tile kernels.
 cudaError_t configure_group_kernels(size_t smem);
 

@@ -612,6 +612,10 @@ __device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, 
   int* pb = L.sLa;
   int phx = -1, phy = -1;
   int hfx = 1, hfy = 1;  // fill extents only grow within a batch
+  // the tile's flow reach of the first frame; each frame resets it for the
+  // next one once every thread has read it (a barrier always separates the
+  // reset from the next frame's atomicMax)
+  if (tid == 0) { s_fx = 0; s_fy = 0; }
   __syncthreads();  // the table, reference and thresholds above are read by all threads
 
   for (int fi = 0; fi < b.count; ++fi) {
@@ -623,7 +627,6 @@ __device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, 
     curf.ch = p.ch;
     const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
     Seg* segf = p.seg + (long long)fi * nmax * p.segs_per_k + (long long)ty0 * p.tiles_x + tcx;
-    if (tid == 0) { s_fx = 0; s_fy = 0; }
     if (tid < N) {
       const int k = tid + 1;
       L.swk[tid] = (k * 8192 + N) / (2 * N);
@@ -728,6 +731,7 @@ __device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, 
       fill_halo(cb, L.slut, curf, W, H, tx0, ty0, hfx, hfy);
     }
     __syncthreads();
+    if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
 
     // 3. substeps (sparse: warps without a compacted pixel skip them); dense
     // rows publish their segments from the loop
@@ -1031,6 +1035,7 @@ __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
     order_chunk(p, b, c, nchunks, cursor, t_first, o);
   }
   if (tid == 0) {
+    __threadfence();  // this block's ticket increments precede its exit count
     const unsigned e = atomicAdd(&ctl->order_exit, 1u);
     if (e == gridDim.x - 1) {  // every block has left the ticket loop
       ctl->order_ticket = 0;
@@ -1096,16 +1101,48 @@ __global__ void __launch_bounds__(NT) k_pre_multi(GroupArg g) {
   }
 }
 
-// Tiles of every member of one kernel class; block_map[block] = member.
+// Tiles of the members of one kernel class that have frames in this step:
+// a persistent grid takes tiles of the class's work list (act, members in
+// table order with their first tile) by ticket, so members without frames
+// cost nothing and tiles of unequal cost balance across the SMs.
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
-__global__ void __launch_bounds__(NTD, 2) k_tile_multi(GroupArg g, const int* block_map) {
+__global__ void __launch_bounds__(NTD, 2) k_tile_multi(GroupArg g, const ActiveTile* act,
+                                                       int cls) {
   __shared__ SimParams sp;
   __shared__ BatchArg sb;
-  const int s = block_map[blockIdx.x];
-  if (g.steps[s].count == 0) return;  // block-uniform
-  load_stream(g, s, sp, sb);
-  __syncthreads();
-  tile_run<RESET, MAPS, WIDE, SPARSE>(sp, sb, blockIdx.x - g.gs[s].tile_begin);
+  __shared__ int s_begin[MAX_GROUP];
+  __shared__ int s_member[MAX_GROUP];
+  __shared__ int s_t;
+  const int na = g.tot->active[cls], nt = g.tot->tiles[cls];
+  for (int i = threadIdx.x; i < na; i += NTD) {
+    const ActiveTile a = act[i];
+    s_begin[i] = a.tile_begin;
+    s_member[i] = a.member;
+  }
+  int cur = -1;
+  for (;;) {
+    __syncthreads();  // the work list is loaded; the previous tile is done with shared memory
+    if (threadIdx.x == 0) s_t = (int)atomicAdd(&g.gctl->tile_ticket, 1u);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= nt) break;
+    const int k = find_stream(s_begin, na, t);
+    const int s = s_member[k];
+    if (s != cur) {
+      load_stream(g, s, sp, sb);
+      cur = s;
+      __syncthreads();
+    }
+    tile_run<RESET, MAPS, WIDE, SPARSE>(sp, sb, t - s_begin[k]);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's ticket increments precede its exit count
+    const unsigned e = atomicAdd(&g.gctl->tile_exit, 1u);
+    if (e == gridDim.x - 1) {  // every block has left the ticket loop
+      g.gctl->tile_ticket = 0;
+      g.gctl->tile_exit = 0;
+    }
+  }
 }
 
 // Order pass of every member: one ticket counter over the concatenated
@@ -1147,11 +1184,103 @@ __global__ void __launch_bounds__(NT) k_order_multi(GroupArg g) {
     __syncthreads();
   }
   if (tid == 0) {
+    __threadfence();  // this block's ticket increments precede its exit count
     const unsigned e = atomicAdd(&g.gctl->order_exit, 1u);
     if (e == gridDim.x - 1) {  // every block has left the ticket loop
       g.gctl->order_ticket = 0;
       g.gctl->order_exit = 0;
     }
+  }
+}
+
+// Delivery of every member's committed, undelivered events to host memory
+// (one array, members in table order, each member's events in output order),
+// with a table of what each member received.  Every block computes the same
+// member offsets; the blocks copy in a grid-stride loop; the last block to
+// finish writes the table and advances the members' delivered positions.
+// Members whose events do not fit get a prefix (the rest waits for the next
+// delivery).
+__global__ void __launch_bounds__(NT) k_drain(GroupArg g, DrainArg d) {
+  __shared__ long long s_off[MAX_GROUP + 1];
+  __shared__ long long s_warp64[NWARP];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = g.n;
+  // available events of member i: [drained, cursor); a failed member delivers nothing
+  constexpr int PER = (MAX_GROUP + NT - 1) / NT;
+  long long av[PER];
+  long long run = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = tid * PER + q;
+    av[q] = 0;
+    if (i < n) {
+      const Ctl* c = g.gs[i].p.ctl;
+      av[q] = ld_volatile(&c->err) ? 0 : c->cursor - c->drained;
+    }
+    run += av[q];
+  }
+  // exclusive scan of the per-thread sums
+  long long inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long v = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) s_warp64[warp] = inc;
+  __syncthreads();
+  long long base = 0;
+  for (int w = 0; w < warp; ++w) base += s_warp64[w];
+  long long off = base + inc - run;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = tid * PER + q;
+    if (i < n) s_off[i] = off;
+    off += av[q];
+  }
+  if (tid == NT - 1) s_off[n] = off;
+  __syncthreads();
+  const long long total = s_off[n] < d.cap ? s_off[n] : d.cap;
+  for (long long j = (long long)blockIdx.x * NT + tid; j < total; j += (long long)gridDim.x * NT) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_off[mid] <= j) lo = mid; else hi = mid;
+    }
+    const SimParams& p = g.gs[lo].p;
+    d.events[j] = p.events[p.ctl->drained + (j - s_off[lo])];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(d.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = tid; i < n; i += NT) {
+    Ctl* c = g.gs[i].p.ctl;
+    const long long first = s_off[i] < d.cap ? s_off[i] : d.cap;
+    const long long end = s_off[i + 1] < d.cap ? s_off[i + 1] : d.cap;
+    Delivery e;
+    e.id = d.ids[i];
+    e.status = ld_volatile(&c->err);
+    e.first = first;
+    e.count = end - first;
+    e.committed = c->committed;
+    e.work_px = c->work_px;
+    d.table[i] = e;
+    if (e.status == 0) {
+      c->drained += e.count;
+      if (c->drained == c->cursor) {
+        c->drained = 0;
+        c->cursor = 0;
+      }
+    }
+  }
+  if (tid == 0) {
+    *d.total = total;
+    *d.done = 0;
   }
 }
 
@@ -1168,10 +1297,10 @@ void set_tile_multi_attr(size_t bytes) {
 }
 
 template <bool SPARSE>
-cudaError_t launch_tile_multi_mode(const GroupArg& g, int cls, const int* block_map, int grid,
+cudaError_t launch_tile_multi_mode(const GroupArg& g, int cls, const ActiveTile* act, int grid,
                                    size_t sm, cudaStream_t st) {
   const bool reset = cls & TILE_RESET, maps = cls & TILE_MAPS, wide = cls & TILE_WIDE;
-#define EVSIM_TILE(R, M, Wd) k_tile_multi<R, M, Wd, SPARSE><<<grid, NTD, sm, st>>>(g, block_map)
+#define EVSIM_TILE(R, M, Wd) k_tile_multi<R, M, Wd, SPARSE><<<grid, NTD, sm, st>>>(g, act, cls)
   if (!reset && !maps && !wide) EVSIM_TILE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_TILE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_TILE(false, false, true);
@@ -1306,14 +1435,19 @@ cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_multi(const GroupArg& g, int cls, const int* block_map, int grid,
+cudaError_t launch_tile_multi(const GroupArg& g, int cls, const ActiveTile* act, int grid,
                               size_t smem, cudaStream_t st) {
-  if (cls & TILE_SPARSE) return launch_tile_multi_mode<true>(g, cls, block_map, grid, smem, st);
-  return launch_tile_multi_mode<false>(g, cls, block_map, grid, smem, st);
+  if (cls & TILE_SPARSE) return launch_tile_multi_mode<true>(g, cls, act, grid, smem, st);
+  return launch_tile_multi_mode<false>(g, cls, act, grid, smem, st);
 }
 
 cudaError_t launch_order_multi(const GroupArg& g, int grid, cudaStream_t st) {
   k_order_multi<<<grid, NT, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drain(const GroupArg& g, const DrainArg& d, int grid, cudaStream_t st) {
+  k_drain<<<grid, NT, 0, st>>>(g, d);
   return cudaGetLastError();
 }
 

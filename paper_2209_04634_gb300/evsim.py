@@ -67,7 +67,21 @@ class simb_config(ctypes.Structure):
         ("max_streams", ctypes.c_int32), ("frames_per_step", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_int64), ("use_graphs", ctypes.c_int32),
         ("reserved", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+        ("delivery_events", ctypes.c_int64),
     ]
+
+
+class simb_delivery(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int32), ("status", ctypes.c_int32), ("first", ctypes.c_int64),
+        ("count", ctypes.c_int64), ("frames_committed", ctypes.c_int64),
+        ("pixel_substeps", ctypes.c_int64),
+    ]
+
+
+DELIVERY_DTYPE = np.dtype([("id", "<i4"), ("status", "<i4"), ("first", "<i8"),
+                           ("count", "<i8"), ("frames_committed", "<i8"),
+                           ("pixel_substeps", "<i8")])
 
 
 class simb_stats(ctypes.Structure):
@@ -106,12 +120,18 @@ SIGNATURES = [
     ("simb_admit", ctypes.c_int, [_VP, ctypes.POINTER(sim_config), ctypes.POINTER(_I32)]),
     ("simb_push", ctypes.c_int, [_VP, _I32, _VP, _I64, _VP, _I64, _I32]),
     ("simb_step", ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+    ("simb_step_deliver", ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+    ("simb_collect", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.POINTER(simb_delivery)),
+                                    ctypes.POINTER(_I32), ctypes.POINTER(_VP),
+                                    ctypes.POINTER(_I64)]),
+    ("simb_delivery_ready", ctypes.c_int, [_VP]),
     ("simb_pop", ctypes.c_int, [_VP, _I32, _VP, _I64, ctypes.POINTER(_I64), _I32]),
     ("simb_stream_stats", ctypes.c_int, [_VP, _I32, ctypes.POINTER(sim_stats)]),
     ("simb_evict", ctypes.c_int, [_VP, _I32]),
     ("simb_sync", ctypes.c_int, [_VP]),
     ("simb_get_stats", ctypes.c_int, [_VP, ctypes.POINTER(simb_stats)]),
     ("simb_destroy", ctypes.c_int, [_VP]),
+    ("sim_serve_run", ctypes.c_int, [_VP, _VP]),
     ("sim_step_pair_static", ctypes.c_int, [ctypes.POINTER(sim_config), _VP, _I64, _VP, _I64, _VP,
                                             _I64, _I64, _VP, _VP, _VP, _I64,
                                             ctypes.POINTER(_I64)]),
@@ -359,7 +379,8 @@ class Group:
     advance all of them with step(), pop each member's events."""
 
     def __init__(self, max_streams: int = 64, frames_per_step: int = 4,
-                 hbm_budget_bytes: int = 0, use_graphs: bool = True, stream=None):
+                 hbm_budget_bytes: int = 0, use_graphs: bool = True, stream=None,
+                 delivery_events: int = 0):
         lib = load()
         cfg = simb_config()
         check(lib.simb_config_default(ctypes.byref(cfg)), "simb_config_default")
@@ -367,6 +388,7 @@ class Group:
         cfg.frames_per_step = frames_per_step
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.use_graphs = 1 if use_graphs else 0
+        cfg.delivery_events = delivery_events
         if stream is not None:
             handle = int(getattr(stream, "cuda_stream", stream))
             cfg.cuda_stream = handle if handle else CUDA_STREAM_LEGACY
@@ -411,6 +433,40 @@ class Group:
         n = ctypes.c_int64(0)
         check(self._lib.simb_step(self.h, ctypes.byref(n)), "simb_step")
         return int(n.value)
+
+    def step_deliver(self) -> int:
+        """Step and deliver every member's committed events to host memory
+        (asynchronous; collect() returns them)."""
+        n = ctypes.c_int64(0)
+        check(self._lib.simb_step_deliver(self.h, ctypes.byref(n)), "simb_step_deliver")
+        return int(n.value)
+
+    def collect(self, copy: bool = True):
+        """Wait for the oldest delivery: (table, events).  table: structured
+        array (id, status, first, count, frames_committed) per member; events:
+        EVENT_DTYPE array.  With copy=False both are views of library memory,
+        valid until the next step_deliver()."""
+        tab = ctypes.POINTER(simb_delivery)()
+        n = ctypes.c_int32(0)
+        ev = ctypes.c_void_p()
+        ne = ctypes.c_int64(0)
+        check(self._lib.simb_collect(self.h, ctypes.byref(tab), ctypes.byref(n), ctypes.byref(ev),
+                                     ctypes.byref(ne)), "simb_collect")
+        nt, nev = int(n.value), int(ne.value)
+        if nt:
+            buf = (ctypes.c_char * (nt * DELIVERY_DTYPE.itemsize)).from_address(
+                ctypes.addressof(tab.contents))
+            table = np.frombuffer(buf, dtype=DELIVERY_DTYPE)
+        else:
+            table = np.zeros(0, dtype=DELIVERY_DTYPE)
+        if nev:
+            ebuf = (ctypes.c_char * (nev * 8)).from_address(ev.value)
+            events = np.frombuffer(ebuf, dtype=EVENT_DTYPE)
+        else:
+            events = np.zeros(0, dtype=EVENT_DTYPE)
+        if copy:
+            table, events = table.copy(), events.copy()
+        return table, events
 
     def pop(self, sid: int, cap: int | None = None) -> np.ndarray:
         st = self.stream_stats(sid)

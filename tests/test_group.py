@@ -207,3 +207,72 @@ def test_group_create_validates_and_needs_a_device():
         has_gpu = False
     if not has_gpu:
         assert lib.simb_create(ctypes.byref(cfg), ctypes.byref(h)) == evsim.SIM_ERR_NO_DEVICE
+
+
+def _run_group_delivered(mix, *, fmax, schedule, delivery_events=0, depth=2):
+    """As _run_group, with simb_step_deliver / simb_collect (up to `depth`
+    deliveries in flight); returns each member's events."""
+    import torch
+    g = evsim.Group(max_streams=16, frames_per_step=fmax, delivery_events=delivery_events)
+    ids, inputs, nxt = [], [], []
+    for name, seq, opts in mix:
+        sid = g.admit(seq.width, seq.height, **evsim.seq_options(seq, **opts))
+        ids.append(sid)
+        inputs.append((torch.from_numpy(np.ascontiguousarray(seq.frames)).cuda(),
+                       torch.from_numpy(np.ascontiguousarray(seq.flows)).cuda()))
+        g.push(sid, inputs[-1][0][0], None, int(seq.t_us[0]))
+        nxt.append(1)
+    got = {sid: [] for sid in ids}
+    inflight = 0
+    committed = {}
+
+    def collect():
+        tab, ev = g.collect()
+        for r in tab:
+            assert r["status"] == 0
+            got[int(r["id"])].append(ev[r["first"]: r["first"] + r["count"]])
+            committed[int(r["id"])] = int(r["frames_committed"])
+
+    step = 0
+    while any(nxt[i] < mix[i][1].frames.shape[0] for i in range(len(mix))):
+        for i, (name, seq, _o) in enumerate(mix):
+            k = min(schedule(i, step), seq.frames.shape[0] - nxt[i], fmax)
+            for _ in range(k):
+                j = nxt[i]
+                g.push(ids[i], inputs[i][0][j], inputs[i][1][j], int(seq.t_us[j]))
+                nxt[i] += 1
+        if inflight == depth:
+            collect()
+            inflight -= 1
+        g.step_deliver()
+        inflight += 1
+        step += 1
+    while inflight:
+        collect()
+        inflight -= 1
+    # deliveries without frames until nothing is left on the device
+    for _ in range(10000):
+        g.step_deliver()
+        before = sum(len(x) for v in got.values() for x in v)
+        collect()
+        if sum(len(x) for v in got.values() for x in v) == before:
+            break
+    for i in range(len(mix)):
+        assert committed[ids[i]] == mix[i][1].frames.shape[0]
+    with pytest.raises(evsim.SimError) as e:
+        g.pop(ids[0])
+    assert e.value.code == evsim.SIM_ERR_STATE
+    g.close()
+    return [np.concatenate(got[sid]) if got[sid] else np.zeros(0, evsim.EVENT_DTYPE)
+            for sid in ids]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("delivery_events,depth", [(0, 1), (0, 2), (3000, 2)])
+def test_group_delivery_matches_single_stream_handles(delivery_events, depth):
+    mix = _mix()
+    want = [_alone(seq, opts) for _n, seq, opts in mix]
+    got = _run_group_delivered(mix, fmax=2, schedule=lambda i, s: 1 + (i + s) % 2,
+                               delivery_events=delivery_events, depth=depth)
+    for (name, _s, _o), gv, wv in zip(mix, got, want):
+        assert_same_events(gv, wv, name)
