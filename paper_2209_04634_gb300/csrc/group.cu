@@ -156,7 +156,7 @@ int rebuild(simb_t* g) {
     g->cls_moff[c] = moff;
     moff += cls_members[c];
     // persistent tile grid: two blocks per SM (the kernel's residency)
-    g->cls_grid[c] = std::min(g->cls_tiles[c], 2 * g->sms);
+    g->cls_grid[c] = std::min(g->cls_tiles[c] * g->fmax, 2 * g->sms);
     if (g->cls_tiles[c]) ++g->n_classes;
   }
   std::vector<int> ids(std::max(n, 1));
@@ -487,7 +487,7 @@ int simb_step(simb_t* g, int64_t* frames) {
     evsim::ActiveTile& a = ha[g->cls_moff[m->cls] + ht->active[m->cls]++];
     a.member = i;
     a.tile_begin = ht->tiles[m->cls];
-    ht->tiles[m->cls] += m->tiles;
+    ht->tiles[m->cls] += cnt * m->tiles;  // (frame, tile) items
     chunks += order_chunks(m->s, cnt);
     if (m->adaptive) pre += cnt * m->pre_blocks;
     for (int j = 0; j < cnt; ++j) hd[(size_t)i * g->fmax + j] = m->q[j].d;

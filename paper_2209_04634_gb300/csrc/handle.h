@@ -39,6 +39,7 @@ struct sim_s {
   Ev* d_staging = nullptr;
   Ev* d_events = nullptr;
   evsim::Seg* d_seg = nullptr;
+  unsigned long long* d_tdone = nullptr;    // per tile progress words
   unsigned long long* d_order_status = nullptr;
   evsim::FrameDesc* d_desc = nullptr;       // bmax descriptors of the batch in flight
   unsigned char* d_stage_frames = nullptr;  // host batches: staged frames and flows

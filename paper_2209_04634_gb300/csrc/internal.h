@@ -108,6 +108,7 @@ struct SimParams {
   unsigned long long* maxf2;    // [bmax] adaptive: max squared Q16 flow per frame
   Ev* staging;
   long long stage_cap;
+  unsigned long long* tdone;    // per tile: [batch serial:32][frames of the batch done:32]
   Seg* seg;                     // per (frame, substep, tile row)
   long long segs_per_k;         // segments per substep of one frame
   unsigned long long* order_status;
@@ -152,7 +153,7 @@ struct GroupCtl {
   unsigned int order_ticket;
   unsigned int order_exit;
   unsigned int drain_done;
-  unsigned int tile_ticket;     // tile launches: next tile of the class's work list
+  unsigned int tile_ticket;     // tile launches: next item of the class's work list
   unsigned int tile_exit;       // tile launches: blocks done
   unsigned int pad[3];
 };

@@ -557,8 +557,31 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
   }
 }
 
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
-__device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, int tile) {
+// Wait (thread 0, bounded) until the tile's progress word reaches `want`
+// ([batch serial:32][frames done:32]); gives up when the stream has failed
+// or after SPIN_LIMIT polls (then flags a timeout).
+__device__ __forceinline__ void wait_tile(const SimParams& p, int tile, unsigned long long want) {
+  int spins = 0;
+  while (ld_volatile(&p.tdone[tile]) < want) {
+    if (++spins > SPIN_LIMIT) {
+      atomicCAS(&p.ctl->err, 0, SIM_ERR_DEVICE_TIMEOUT);
+      break;
+    }
+    if ((spins & 1023) == 0 && ld_volatile(&p.ctl->err) != 0) break;
+    __nanosleep(64);
+  }
+  __threadfence();
+}
+
+// Frames [f0, f1) of one tile, carried by one block: the tile's reference and
+// thresholds stay in registers (dense) or shared memory (sparse) across the
+// frames, and frame i's halo is kept as frame i+1's previous-frame halo.
+// f0 > 0: the tile's earlier frames were simulated by another block; wait for
+// them.  Publishes the tile's progress word at the end.  ONE: a single frame
+// (f1 = f0 + 1), which needs no state carried from frame to frame.
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, bool ONE = false>
+__device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& b, int tile, int f0,
+                                            int f1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy;
@@ -573,13 +596,22 @@ __device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, 
   const int tx0 = tcx * TW, ty0 = tcy * TH;
   const int W = p.W, H = p.H;
 
+  // frames before f0 were simulated by other blocks: wait for the last one
+  if (f0 > 0) {
+    if (tid == 0) wait_tile(p, tile, ((unsigned long long)b.serial << 32) | (unsigned)f0);
+    if (block_error(&ctl->err)) return;
+  }
   if (tid < 256) L.slut[tid] = p.lut[tid];
   const int sel = ctl->sel;
   const int* Rin = (sel & 1) ? p.R1 : p.R0;
   int* Rout = (sel & 1) ? p.R0 : p.R1;
+  // frame 0 of the batch starts from the committed reference, a later first
+  // frame from what the previous frame wrote (read through L2: another block
+  // wrote it)
+  const int* Rsrc = f0 == 0 ? Rin : Rout;
   const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
   unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
-  long long tprev = ctl->t_prev;
+  long long tprev = f0 == 0 ? ctl->t_prev : b.frames[f0 - 1].t_rel;
 
   // Dense: thread (warp w, lane l) owns tile pixels (l, w) and (l + 32, w);
   // sparse: thread t owns tile pixels t and t + NTD for selection and the
@@ -596,10 +628,10 @@ __device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, 
     if (inimg[q]) {
       const long long i = (long long)y * W + x;
       if (SPARSE) {
-        if (!RESET) L.sR[own[q]] = Rin[i];
+        if (!RESET) L.sR[own[q]] = __ldcg(Rsrc + i);
         if (MAPS) { L.sCp[own[q]] = p.cpmap[i]; L.sCn[own[q]] = p.cnmap[i]; }
       } else {
-        if (!RESET) Rd[q] = Rin[i];
+        if (!RESET) Rd[q] = __ldcg(Rsrc + i);
         if (MAPS) { Cpd[q] = p.cpmap[i]; Cnd[q] = p.cnmap[i]; }
       }
     }
@@ -618,7 +650,7 @@ __device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, 
   if (tid == 0) { s_fx = 0; s_fy = 0; }
   __syncthreads();  // the table, reference and thresholds above are read by all threads
 
-  for (int fi = 0; fi < b.count; ++fi) {
+  for (int fi = f0; fi < (ONE ? f0 + 1 : f1); ++fi) {
     const FrameDesc cur = b.frames[fi];
     const FrameRef prv = prev_frame(p, b, fi, ringp);
     FrameRef curf;
@@ -810,11 +842,20 @@ __device__ __forceinline__ void tile_run(const SimParams& p, const BatchArg& b, 
     atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)act_sum);
     atomicAdd((unsigned long long*)&ctl->active_n, (unsigned long long)act_n);
   }
+  // frames [f0, f1) of the tile are done: their reference may be read
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_volatile(&p.tdone[tile], ((unsigned long long)b.serial << 32) | (unsigned)f1);
+  }
 }
 
+
+// One stream's batch: one block per tile carries the tile through every
+// frame of the batch (blocks never wait for one another).
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
 __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
-  tile_run<RESET, MAPS, WIDE, SPARSE>(p, b, blockIdx.x);
+  tile_frames<RESET, MAPS, WIDE, SPARSE>(p, b, blockIdx.x, 0, b.count);
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
@@ -1101,10 +1142,11 @@ __global__ void __launch_bounds__(NT) k_pre_multi(GroupArg g) {
   }
 }
 
-// Tiles of the members of one kernel class that have frames in this step:
-// a persistent grid takes tiles of the class's work list (act, members in
-// table order with their first tile) by ticket, so members without frames
-// cost nothing and tiles of unequal cost balance across the SMs.
+// Work items (member, frame, tile) of the members of one kernel class that
+// have frames in this step: a persistent grid takes the items of the class's
+// work list (act: members in table order with their first item; frames in
+// order within a member) by ticket, so members without frames cost nothing
+// and items of unequal cost balance across the SMs.
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
 __global__ void __launch_bounds__(NTD, 2) k_tile_multi(GroupArg g, const ActiveTile* act,
                                                        int cls) {
@@ -1133,7 +1175,8 @@ __global__ void __launch_bounds__(NTD, 2) k_tile_multi(GroupArg g, const ActiveT
       cur = s;
       __syncthreads();
     }
-    tile_run<RESET, MAPS, WIDE, SPARSE>(sp, sb, t - s_begin[k]);
+    const int T = sp.tiles_x * sp.tiles_y, r = t - s_begin[k], fi = r / T;
+    tile_frames<RESET, MAPS, WIDE, SPARSE, true>(sp, sb, r - fi * T, fi, fi + 1);
   }
   if (threadIdx.x == 0) {
     __threadfence();  // this block's ticket increments precede its exit count

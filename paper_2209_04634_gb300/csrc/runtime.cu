@@ -52,6 +52,7 @@ long long state_bytes(const sim_config& c) {
   if (c.ref_mode == SIM_REF_ACCUM) b += 8 * z.P;
   b += 2 * z.cap * (long long)sizeof(Ev);                // staging + events
   b += z.seg_cap * (long long)sizeof(evsim::Seg) + 8 * z.ochunks;
+  b += 8LL * z.tiles_x * ((c.height + evsim::TH - 1) / evsim::TH);  // tile progress words
   b += (long long)z.bmax * sizeof(evsim::FrameDesc);
   b += z.P * c.pixel_format;                             // host-frame staging (one frame)
   if (c.c_pos_map) b += 4 * z.P;
@@ -80,6 +81,7 @@ void free_all(sim_t* s) {
   cudaFree(s->d_staging);
   cudaFree(s->d_events);
   cudaFree(s->d_seg);
+  cudaFree(s->d_tdone);
   cudaFree(s->d_order_status);
   cudaFree(s->d_desc);
   cudaFree(s->d_stage_frames);
@@ -120,6 +122,7 @@ evsim::SimParams make_params(const sim_t* s) {
   p.staging = s->d_staging;
   p.stage_cap = s->event_cap;
   p.seg = s->d_seg;
+  p.tdone = s->d_tdone;
   p.segs_per_k = s->segs_per_k;
   p.order_status = s->d_order_status;
   p.events = s->d_events;
@@ -378,6 +381,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   chk(dalloc(&s->d_staging, cap));
   chk(dalloc(&s->d_events, cap));
   chk(dalloc(&s->d_seg, seg_cap));
+  chk(dalloc(&s->d_tdone, (size_t)s->tiles_x * s->tiles_y));
   chk(dalloc(&s->d_order_status, ochunks));
   chk(dalloc(&s->d_desc, s->bmax));
   chk(dalloc(&s->d_stage_frames, P * s->ch));
@@ -394,6 +398,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
     chk(cudaMemset(s->d_ctl, 0, sizeof(Ctl)));
     chk(cudaMemset(s->d_maxf2, 0, s->bmax * sizeof(unsigned long long)));
     chk(cudaMemset(s->d_order_status, 0, ochunks * sizeof(unsigned long long)));
+    chk(cudaMemset(s->d_tdone, 0, (size_t)s->tiles_x * s->tiles_y * sizeof(unsigned long long)));
   }
   if (e == cudaSuccess) {
     std::lock_guard<std::mutex> g(g_attr_mu);

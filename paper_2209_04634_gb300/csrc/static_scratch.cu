@@ -13,8 +13,9 @@
 // them in; everything else lives in g_scratch.
 //
 // The array is shared by every call on a device: it is re-initialised at the
-// start of each call (control block, look-back words and flow maxima are
-// cleared there), and two calls whose GPU work overlaps race on it.
+// start of each call (control block, tile progress words, look-back words
+// and flow maxima are cleared there), and two calls whose GPU work overlaps
+// race on it.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -53,8 +54,9 @@ constexpr long long STAGE_MIN = 1LL << 20;  // bytes of staging a call must have
 
 // Byte offsets of the parts of g_scratch for one problem size.
 struct Layout {
-  long long zero;      // maxf2 (one frame) then the look-back words: cleared per call
+  long long zero;      // maxf2 (one frame), tile progress words, look-back words: cleared per call
   long long zero_len;
+  long long tdone;
   long long status;
   long long ring0, ring1;
   long long seg;
@@ -63,12 +65,13 @@ struct Layout {
   long long need;      // bytes up to and including the minimum staging
 };
 
-Layout layout(long long P, long long nseg) {
+Layout layout(long long P, long long nseg, long long tiles) {
   Layout l{};
   const long long nchunks = (nseg + evsim::OCHUNK - 1) / evsim::OCHUNK;
   l.zero = align256(sizeof(Header));
-  l.status = l.zero + 256;
-  l.zero_len = 256 + nchunks * 8;
+  l.tdone = l.zero + 256;
+  l.status = align256(l.tdone + tiles * 8);
+  l.zero_len = l.status - l.zero + nchunks * 8;
   l.ring0 = align256(l.zero + l.zero_len);
   l.ring1 = align256(l.ring0 + P);
   l.seg = align256(l.ring1 + P);
@@ -145,7 +148,7 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   const long long P = (long long)c.width * c.height;
   const long long segs_per_k = (long long)c.height * tiles_x;
   const long long nseg = (long long)n_max * segs_per_k;
-  const Layout L = layout(P, nseg);
+  const Layout L = layout(P, nseg, (long long)tiles_x * tiles_y);
   if (L.need > SIM_STATIC_SCRATCH_BYTES) return SIM_ERR_TOO_LARGE;
 
   int dev = 0;
@@ -187,6 +190,7 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   p.seg = (Seg*)(base + L.seg);
   p.segs_per_k = segs_per_k;
   p.order_status = (unsigned long long*)(base + L.status);
+  p.tdone = (unsigned long long*)(base + L.tdone);
   p.events = (Ev*)events;
   p.event_cap = event_capacity;
 
