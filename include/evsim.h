@@ -210,8 +210,8 @@ const char* sim_version(void);
 
 /* ---- multi-stream group ---------------------------------------------------
  * Many independent camera streams of mixed sizes and settings advanced
- * together (the batched pattern the spec names; the paper itself runs
- * one stream).  Each member is a full stream with the semantics, arithmetic
+ * together (a serving-side batching pattern; the paper itself runs one
+ * stream).  Each member is a full stream with the semantics, arithmetic
  * and event stream of a sim_t handle fed the same frames: the group only
  * changes how the work is launched.  simb_step advances every member that has
  * queued frames with one launch per kernel for all of them: an adaptive-N

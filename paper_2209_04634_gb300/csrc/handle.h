@@ -46,6 +46,7 @@ struct sim_s {
   float2* d_stage_flows = nullptr;
   long long stage_frames = 0;               // frames the host staging holds
   long long event_cap = 0;
+  long long stage_cap = 0;     // staging events (event capacity plus chunk slack)
   long long segs_per_k = 0;
   int bmax = 1;
   int order_grid = 1;

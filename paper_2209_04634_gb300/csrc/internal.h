@@ -23,6 +23,10 @@ constexpr int SH = TH + 2 * HMAX;
 constexpr int MAXN = 64;           // largest substep count
 // Order kernel: segments per chunk (one per thread).
 constexpr int OCHUNK = NT;
+// Staging chunk of one warp of the batch tile kernel (events).  A stream's
+// staging area holds 4/3 of its event capacity plus one chunk per warp of its
+// tiles, so chunking never turns a batch that fits into an overflow.
+constexpr int STAGE_CHUNK = 64;
 
 // Look-back status word: [epoch:32][flag:2][value:30].
 constexpr unsigned long long LB_AGG = 1ull << 30;
@@ -78,10 +82,14 @@ struct Ev {  // same layout as sim_event
 };
 
 // The events of one segment: one (frame, substep, tile row).  When no pixel
-// of the row crossed more than one threshold in the substep (src < 0), the
+// of the row crossed more than one threshold in the substep (src == -1), the
 // events are bit b of `mask` (pixel tx0 + b has an event) with polarity bit b
-// of `pol`; the order kernel materialises them.  Otherwise the tile kernel
-// wrote the row's `cnt` events to staging at `src`.
+// of `pol`; the order kernel materialises them.  Otherwise either the tile
+// kernel wrote the row's `cnt` events to staging at `src` (src >= 0), or -
+// dense tiles - the row's per-pixel event counts are in staging at
+// -2 - src (src <= -2): 32 words, word l holding the counts of columns l (low
+// 16 bits) and l + 32 (high 16 bits), with `mask` and `pol` marking the
+// pixels with events and their polarity as for a one-crossing row.
 struct Seg {
   unsigned long long mask;
   unsigned long long pol;
@@ -97,6 +105,7 @@ struct SimParams {
   int n_fixed, n_max;
   int cp, cn, cact;
   int bmax;                     // frames per batch the segment table holds
+  int stage_chunk;              // staging chunk per warp of the batch kernel (0: exact)
   const unsigned short* cpmap;
   const unsigned short* cnmap;
   const int* lut;               // 256 Q16 entries (device)

@@ -76,6 +76,23 @@ __device__ __forceinline__ int adaptive_n(unsigned long long m, int nmax) {
   return n;
 }
 
+// floor(F / N) and F - N floor(F / N) for |F| <= 2^26 (Q16 flows are
+// clamped to 1024 px) and 1 <= N <= 64, with mN = floor(2^32 / N) + 1: the
+// multiply-high of |F| by mN is floor(|F| / N) exactly, because
+// |F| (mN - 2^32 / N) / 2^32 <= 2^-6 and the fraction (|F| mod N) / N is at most
+// 1 - 1/N (and below 1 - 2^-6 whenever N = 64 and |F| = 2^26 is a multiple of N).
+__device__ __forceinline__ void divmod_n(int F, int N, unsigned mN, int& q, int& r) {
+  const unsigned a = (unsigned)abs(F);
+  unsigned qa = N == 1 ? a : __umulhi(a, mN);
+  int ra = (int)(a - qa * (unsigned)N);
+  if (F < 0 && ra != 0) {
+    qa += 1;
+    ra = N - ra;
+  }
+  q = F < 0 ? -(int)qa : (int)qa;
+  r = ra;
+}
+
 // a + floor(((b - a) f + 2048) / 4096): Q12-weighted blend, round half up,
 // evaluated as (a (4096 - f) + b f + 2048) >> 12 (the same integer).  LOG
 // values span 19 bits, so the 32-bit products cannot overflow; LINEAR values
@@ -436,6 +453,103 @@ __device__ __forceinline__ void fill_halo(int* dst, const int* slut, const Frame
   }
 }
 
+// Staging space of one warp: multi-crossing rows take their events' space
+// from the warp's chunk of the stream's staging area, so that one global
+// atomic serves many rows.  A row that does not fit the chunk either starts a
+// new chunk (rows of at most STAGE_CHUNK / 4 events, wasting the old chunk's
+// remainder: less than a third of what the chunk served) or takes exactly its
+// own space.  Chunks are off (chunk == 0) where a block serves several
+// streams.  Only lane 0 touches it.
+struct WarpStage {
+  long long base;
+  int left;
+  int chunk;
+};
+
+__device__ __forceinline__ long long stage_take(const SimParams& p, WarpStage& w, int total) {
+  if (total <= w.left) {
+    const long long b = w.base;
+    w.base += total;
+    w.left -= total;
+    return b;
+  }
+  const bool refill = w.chunk > 0 && total <= w.chunk / 4;
+  const long long size = refill ? w.chunk : total;
+  const unsigned long long b = atomicAdd(&p.ctl->stage_top, (unsigned long long)size);
+  if (b + (unsigned long long)size > (unsigned long long)p.stage_cap) {
+    atomicExch(&p.ctl->batch_fail, 1);
+    return -1;
+  }
+  if (refill) {
+    w.base = (long long)b + total;
+    w.left = (int)size - total;
+  }
+  return (long long)b;
+}
+
+// Stage the events of a row whose lanes hold a_lo events of e_lo (the lo
+// half's column) and a_hi of e_hi, in column order with repeats adjacent, and
+// publish the row's segment.  All 32 lanes must call this.
+__device__ __forceinline__ void stage_row(const SimParams& p, WarpStage* ws, Seg* sg, int a_lo,
+                                          int a_hi, Ev e_lo, Ev e_hi) {
+  const int lane = threadIdx.x & 31;
+  const int i_lo = warp_incl_scan(a_lo);
+  const int t_lo = __shfl_sync(FULL, i_lo, 31);
+  const int i_hi = warp_incl_scan(a_hi);
+  const int total = t_lo + __shfl_sync(FULL, i_hi, 31);
+  long long base = 0;
+  if (lane == 0) base = stage_take(p, *ws, total);
+  base = __shfl_sync(FULL, base, 0);
+  if (base >= 0) {
+    for (int m = 0; m < a_lo; ++m) p.staging[base + i_lo - a_lo + m] = e_lo;
+    for (int m = 0; m < a_hi; ++m) p.staging[base + t_lo + i_hi - a_hi + m] = e_hi;
+  }
+  if (lane == 0) *sg = Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1};
+}
+
+// Publish the segment of one (substep, tile row) of a dense tile: lane l
+// holds the event counts of columns l (n0) and l + 32 (n1).  All 32 lanes
+// must call this.
+__device__ __forceinline__ void publish_row_dense(const SimParams& p, Seg* sg, int n0, int n1,
+                                                  unsigned tk, int tx0, int y, WarpStage* ws) {
+  const int lane = threadIdx.x & 31;
+  const unsigned e0 = __ballot_sync(FULL, n0 != 0), e1 = __ballot_sync(FULL, n1 != 0);
+  if ((e0 | e1) == 0) {
+    if (lane == 0) *sg = Seg{0ull, 0ull, 0, -1};
+    return;
+  }
+  const unsigned multi = __ballot_sync(FULL, (unsigned)(n0 + 1) > 2u || (unsigned)(n1 + 1) > 2u);
+  if (multi == 0) {
+    const unsigned p0 = __ballot_sync(FULL, n0 > 0), p1 = __ballot_sync(FULL, n1 > 0);
+    if (lane == 0)
+      *sg = Seg{(unsigned long long)e0 | ((unsigned long long)e1 << 32),
+                (unsigned long long)p0 | ((unsigned long long)p1 << 32), __popc(e0) + __popc(e1),
+                -1};
+    return;
+  }
+  // a pixel crossed two or more thresholds: rows of at least 16 events
+  // publish their per-pixel counts (16 bits each, 128 bytes = 16 staging
+  // slots, so staging never holds more slots than events), which the order
+  // kernel expands; smaller rows stage their events
+  const int a0 = abs(n0), a1 = abs(n1);
+  const int total = __reduce_add_sync(FULL, a0 + a1);
+  if (total < 16) {
+    stage_row(p, ws, sg, a0, a1, make_event(tk, tx0 + lane, y, n0 > 0),
+              make_event(tk, tx0 + lane + 32, y, n1 > 0));
+    return;
+  }
+  const unsigned p0 = __ballot_sync(FULL, n0 > 0), p1 = __ballot_sync(FULL, n1 > 0);
+  long long base = 0;
+  if (lane == 0) base = stage_take(p, *ws, 16);
+  base = __shfl_sync(FULL, base, 0);
+  if (base >= 0) ((unsigned*)(p.staging + base))[lane] = (unsigned)a0 | ((unsigned)a1 << 16);
+  if (lane == 0)
+    *sg = base >= 0 ? Seg{(unsigned long long)e0 | ((unsigned long long)e1 << 32),
+                          (unsigned long long)p0 | ((unsigned long long)p1 << 32), total,
+                          -2 - (int)base}
+                    : Seg{0ull, 0ull, 0, -1};
+}
+
 // Publish the segment of one (substep, tile row) from a warp that holds the
 // row's pixels in two 32-lane halves: lanes' event counts n_lo (columns
 // col_lo) and n_hi (columns col_hi); columns are the bit positions in the
@@ -444,7 +558,7 @@ __device__ __forceinline__ void fill_halo(int* dst, const int* slut, const Frame
 // events (column order, repeats adjacent).  All 32 lanes must call this.
 __device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_lo, int col_lo,
                                             bool v_lo, int n_hi, int col_hi, bool v_hi,
-                                            unsigned tk, int tx0, int y) {
+                                            unsigned tk, int tx0, int y, WarpStage* ws) {
   const int lane = threadIdx.x & 31;
   const unsigned b_lo = v_lo && n_lo ? 1u << (col_lo & 31) : 0u;
   const unsigned b_hi = v_hi && n_hi ? 1u << (col_hi & 31) : 0u;
@@ -468,29 +582,8 @@ __device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_l
                 __popc(low) + __popc(high), -1};
     return;
   }
-  // rare: stage the row's events explicitly
-  const int i_lo = warp_incl_scan(a_lo);
-  const int t_lo = __shfl_sync(FULL, i_lo, 31);
-  const int i_hi = warp_incl_scan(a_hi);
-  const int total = t_lo + __shfl_sync(FULL, i_hi, 31);
-  long long base = 0;
-  if (lane == 0) {
-    const unsigned long long b = atomicAdd(&p.ctl->stage_top, (unsigned long long)total);
-    if (b + (unsigned long long)total > (unsigned long long)p.stage_cap) {
-      base = -1;
-      atomicExch(&p.ctl->batch_fail, 1);
-    } else {
-      base = (long long)b;
-    }
-  }
-  base = __shfl_sync(FULL, base, 0);
-  if (base >= 0) {
-    const Ev e_lo = make_event(tk, tx0 + col_lo, y, n_lo > 0);
-    const Ev e_hi = make_event(tk, tx0 + col_hi, y, n_hi > 0);
-    for (int m = 0; m < a_lo; ++m) p.staging[base + i_lo - a_lo + m] = e_lo;
-    for (int m = 0; m < a_hi; ++m) p.staging[base + t_lo + i_hi - a_hi + m] = e_hi;
-  }
-  if (lane == 0) *sg = Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1};
+  stage_row(p, ws, sg, a_lo, a_hi, make_event(tk, tx0 + col_lo, y, n_lo > 0),
+            make_event(tk, tx0 + col_hi, y, n_hi > 0));
 }
 
 // The substeps of the (up to) two pixels of this thread.  `lx, ly` are the
@@ -499,13 +592,13 @@ __device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_l
 // row's segment is published from the loop.
 template <bool RESET, bool WIDE, bool FAST, bool DENSE>
 __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
-                                              int tx0, int ty0, unsigned b0, unsigned b1,
+                                              unsigned mN, int tx0, int ty0, unsigned b0, unsigned b1,
                                               const FrameRef& prv, const FrameDesc& cur,
                                               Seg* segf, const int (&lx)[2], const int (&ly)[2],
                                               const int (&nk_at)[2], const bool (&act)[2],
                                               const int (&Fx)[2], const int (&Fy)[2],
                                               int (&R)[2], const int (&Cp)[2],
-                                              const int (&Cn)[2]) {
+                                              const int (&Cn)[2], WarpStage* ws) {
   const int warp = threadIdx.x >> 5;
   int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
@@ -515,12 +608,8 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
     px[j] = FAST ? (lx[j] + HMAX) << 16 : (tx0 + lx[j]) << 16;
     py[j] = FAST ? (ly[j] + HMAX) << 16 : (ty0 + ly[j]) << 16;
     // F = q N + r with 0 <= r < N: offset_k = q k + floor(r k / N)
-    qx[j] = Fx[j] / N;
-    rx[j] = Fx[j] - qx[j] * N;
-    if (rx[j] < 0) { rx[j] += N; qx[j] -= 1; }
-    qy[j] = Fy[j] / N;
-    ry[j] = Fy[j] - qy[j] * N;
-    if (ry[j] < 0) { ry[j] += N; qy[j] -= 1; }
+    divmod_n(Fx[j], N, mN, qx[j], rx[j]);
+    divmod_n(Fy[j], N, mN, qy[j], ry[j]);
     ax[j] = 0;
     ay[j] = 0;
   }
@@ -553,7 +642,91 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
     }
     if (DENSE && row_in)  // warp-uniform
       publish_row(p, segf + (long long)k * p.segs_per_k + warp * p.tiles_x, n[0], lx[0], true,
-                  n[1], lx[1], true, L.stk[k], tx0, y);
+                  n[1], lx[1], true, L.stk[k], tx0, y, ws);
+  }
+}
+
+// floor(d / c) for d >= c > 0.  Narrow (log) values: d < 2^21, so the fast
+// single-precision quotient is within one of the exact one, which an integer
+// check corrects; wide (linear) values use integer division.
+template <bool WIDE>
+__device__ __forceinline__ int floordiv_pos(int d, int c) {
+  if (WIDE) return d / c;
+  int q = (int)__fdividef((float)d, (float)c);
+  if (q * c > d) --q;
+  else if ((q + 1) * c <= d) ++q;
+  return q;
+}
+
+// Dense fast path: the substeps of this thread's two pixels (columns lane and
+// lane + 32 of tile row `warp`, both in the image unless `act` says
+// otherwise), sampling the shared halos; every substep's row segment is
+// published from the loop.  The common case crosses at most one threshold
+// per pixel and substep; a warp in which some pixel crossed two or more
+// computes those pixels' counts exactly afterwards.
+template <bool RESET, bool WIDE>
+__device__ __forceinline__ void dense_substeps(const SimParams& p, const int* swk,
+                                               const unsigned* stk, int N, unsigned mN,
+                                               int tx0, int y,
+                                               unsigned b0, unsigned b1, Seg* segr,
+                                               WarpStage* ws, const bool (&act)[2],
+                                               const int (&Fx)[2], const int (&Fy)[2],
+                                               int (&R)[2], const int (&Cp)[2],
+                                               const int (&Cn)[2]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    px[j] = (lane + 32 * j + HMAX) << 16;
+    py[j] = (warp + HMAX) << 16;
+    // F = q N + r with 0 <= r < N: offset_k = q k + floor(r k / N)
+    divmod_n(Fx[j], N, mN, qx[j], rx[j]);
+    divmod_n(Fy[j], N, mN, qy[j], ry[j]);
+    ax[j] = 0;
+    ay[j] = 0;
+  }
+  for (int k = 0; k < N; ++k) {
+    const int w = swk[k];
+    int n[2], D[2];
+    bool multi = false;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      px[j] -= qx[j];
+      ax[j] += rx[j];
+      if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
+      py[j] -= qy[j];
+      ay[j] += ry[j];
+      if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
+      const int s0 = tap_shared<WIDE>(b0, px[j], py[j]);
+      const int s1 = tap_shared<WIDE>(b1, px[j] + Fx[j], py[j] + Fy[j]);
+      const int I = lerp12<WIDE>(s0, s1, w);
+      const int d = I - R[j];
+      if (RESET) {
+        R[j] = I;
+        n[j] = d > Cp[j] ? 1 : (d < -Cn[j] ? -1 : 0);
+      } else {
+        n[j] = d >= Cp[j] ? 1 : (d <= -Cn[j] ? -1 : 0);
+        R[j] += n[j] > 0 ? Cp[j] : (n[j] < 0 ? -Cn[j] : 0);
+        multi |= act[j] && (d >= 2 * Cp[j] || d <= -2 * Cn[j]);
+        D[j] = d;
+      }
+      if (!act[j]) n[j] = 0;
+    }
+    if (!RESET && __any_sync(FULL, multi)) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (act[j] && D[j] >= 2 * Cp[j]) {
+          const int m = floordiv_pos<WIDE>(D[j], Cp[j]);
+          R[j] += (m - 1) * Cp[j];
+          n[j] = m;
+        } else if (act[j] && D[j] <= -2 * Cn[j]) {
+          const int m = floordiv_pos<WIDE>(-D[j], Cn[j]);
+          R[j] -= (m - 1) * Cn[j];
+          n[j] = -m;
+        }
+      }
+    }
+    publish_row_dense(p, segr + (long long)k * p.segs_per_k, n[0], n[1], stk[k], tx0, y, ws);
   }
 }
 
@@ -586,8 +759,11 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
   __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy;
   __shared__ int s_rs[TH + 1];  // first slot of each tile row
+  __shared__ WarpStage s_stage[NTD / 32];
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
+  // exact staging allocations: this block may serve several streams
+  if ((threadIdx.x & 31) == 0) s_stage[threadIdx.x >> 5] = WarpStage{0, 0, 0};
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
@@ -658,6 +834,7 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
     curf.pitch = cur.pitch;
     curf.ch = p.ch;
     const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
+    const unsigned mN = N > 1 ? (unsigned)(0x100000000ull / (unsigned)N) + 1u : 0u;
     Seg* segf = p.seg + (long long)fi * nmax * p.segs_per_k + (long long)ty0 * p.tiles_x + tcx;
     if (tid < N) {
       const int k = tid + 1;
@@ -771,11 +948,11 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
     const unsigned b1 = (unsigned)__cvta_generic_to_shared(cb);
     if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
       if (fast)
-        tile_substeps<RESET, WIDE, true, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, segf,
-                                                  lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn);
+        tile_substeps<RESET, WIDE, true, !SPARSE>(p, L, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
+                                                  lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn, &s_stage[warp]);
       else
-        tile_substeps<RESET, WIDE, false, !SPARSE>(p, L, N, tx0, ty0, b0, b1, prv, cur, segf,
-                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn);
+        tile_substeps<RESET, WIDE, false, !SPARSE>(p, L, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
+                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn, &s_stage[warp]);
     }
     if (!RESET) {
 #pragma unroll
@@ -808,7 +985,7 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
             const int n_lo = v_lo ? L.snk[k * TP + j_lo] : 0;
             const int n_hi = v_hi ? L.snk[k * TP + j_hi] : 0;
             publish_row(p, segf + (long long)k * p.segs_per_k + r * p.tiles_x, n_lo, col_lo, v_lo,
-                        n_hi, col_hi, v_hi, L.stk[k], tx0, y);
+                        n_hi, col_hi, v_hi, L.stk[k], tx0, y, &s_stage[warp]);
           }
         }
       }
@@ -851,11 +1028,490 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
 }
 
 
+// ---------------------------------------------------------------------------
+// One stream's batch, software-pipelined over the frames.  One block per tile
+// carries the tile through every frame of the batch (blocks never wait for
+// one another), as tile_frames does, but the inputs of frame i+1 - its raw
+// bytes over the tile's largest window, its flow at the tile's pixels, the
+// descriptor of frame i+2 - are copied into shared memory asynchronously
+// (cp.async) while frame i is simulated.  Per frame, the block then reads HBM
+// only through copies already in flight; the halo of log values is built from
+// the staged bytes.  Frames whose base or pitch is not a multiple of 4 bytes
+// (flows: 8 bytes) are staged with plain loads instead.
+
+__device__ __forceinline__ void cp_async4(unsigned dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(unsigned dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Shared memory of the batch kernel.  `raw` holds two frames' bytes over the
+// tile window (SH rows of SW pixels, stride SW * ch bytes): the previous and
+// the current frame, the next frame being copied over the previous one
+// during the substeps.  sflow holds the flows of two frames.  Dense tiles do
+// not use the sparse arrays (sR, snk, sslot, sCp, sCn).
+struct BatchLayout {
+  float2* sflow;        // [2][TP]
+  int* sLa;             // two halo buffers (SH x SW)
+  int* sLb;
+  int* slut;
+  int* sR;              // [TP] sparse
+  unsigned* stk;        // [2][nmax] substep times (frame parity)
+  int* swk;             // [2][nmax] substep weights
+  unsigned char* raw;   // [2][SH][SW * ch]
+  short* snk;           // [nmax][TP] sparse
+  short* sslot;         // [TP] sparse
+  unsigned short* sCp;  // [TP] sparse maps
+  unsigned short* sCn;
+};
+
+__host__ __device__ inline size_t batch_smem_bytes(int n_max, int ch, bool sparse) {
+  size_t b = (size_t)2 * TP * sizeof(float2);
+  b += (size_t)(2 * SH * SW + 256 + (sparse ? TP : 0) + 4 * n_max) * 4;
+  b += (size_t)2 * SH * SW * ch;
+  if (sparse) b += (size_t)(n_max * TP + 3 * TP) * 2;
+  return b;
+}
+
+template <bool SPARSE>
+__device__ __forceinline__ BatchLayout batch_layout(unsigned char* base, int nmax, int ch) {
+  BatchLayout L;
+  L.sflow = (float2*)base;
+  L.sLa = (int*)(L.sflow + 2 * TP);
+  L.sLb = L.sLa + SH * SW;
+  L.slut = L.sLb + SH * SW;
+  L.sR = L.slut + 256;
+  L.stk = (unsigned*)(L.sR + (SPARSE ? TP : 0));
+  L.swk = (int*)(L.stk + 2 * nmax);
+  L.raw = (unsigned char*)(L.swk + 2 * nmax);
+  L.snk = (short*)(L.raw + 2 * SH * SW * ch);
+  L.sslot = L.snk + nmax * TP;
+  L.sCp = (unsigned short*)(L.sslot + TP);
+  L.sCn = L.sCp + TP;
+  return L;
+}
+
+// Stage the bytes of frame f over the tile window (image rows ty0 - HMAX ..
+// ty0 + TH + HMAX - 1 and columns tx0 - HMAX .. tx0 + TW + HMAX - 1, clipped
+// to the image) into raw, row r of the window at raw + r * SW * ch.  Window
+// rows and columns outside the image are never read.
+__device__ __forceinline__ void stage_raw(unsigned char* raw, const FrameRef& f, int W, int H,
+                                          int tx0, int ty0) {
+  const int ch = f.ch, RW = SW * ch;
+  const int r0 = max(0, HMAX - ty0), r1 = min(SH, H - ty0 + HMAX);
+  const int cx0 = max(0, tx0 - HMAX), cx1 = min(W, tx0 + TW + HMAX);
+  const int b0 = (cx0 - (tx0 - HMAX)) * ch;  // byte offset of column cx0 in a window row
+  const int nb = (cx1 - cx0) * ch;            // bytes per row
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((((unsigned long long)f.ptr | (unsigned long long)f.pitch) & 3) == 0) {
+    // cx0 * ch is a multiple of 16, so every word starts 4-byte aligned; the
+    // last word of a row copies only the row's remaining bytes (zero fill
+    // within the window row)
+    const int nw = (nb + 3) >> 2;
+    const unsigned dst0 = smem_addr(raw) + (unsigned)b0;
+    for (int r = r0 + warp; r < r1; r += NTD / 32) {
+      const unsigned char* src = f.ptr + (long long)(ty0 - HMAX + r) * f.pitch + (long long)cx0 * ch;
+      for (int w = lane; w < nw; w += 32)
+        cp_async4(dst0 + (unsigned)(r * RW + 4 * w), src + 4 * w, min(4, nb - 4 * w));
+    }
+  } else {
+    for (int r = r0 + warp; r < r1; r += NTD / 32) {
+      const unsigned char* src = f.ptr + (long long)(ty0 - HMAX + r) * f.pitch + (long long)cx0 * ch;
+      for (int c = lane; c < nb; c += 32) raw[r * RW + b0 + c] = src[c];
+    }
+  }
+}
+
+// Stage the flow of the tile's pixels (tile pixel index ly * TW + lx) into sf;
+// pixels outside the image are not written.
+__device__ __forceinline__ void stage_flow(float2* sf, const float2* flow, int W, int H, int tx0,
+                                           int ty0) {
+  const bool al = ((unsigned long long)flow & 7) == 0;
+  const unsigned d0 = smem_addr(sf);
+#pragma unroll
+  for (int q = 0; q < TP / NTD; ++q) {
+    const int t = threadIdx.x + q * NTD;
+    const int lx = t & (TW - 1), ly = t / TW;
+    const int x = tx0 + lx, y = ty0 + ly;
+    if (x < W && y < H) {
+      const float2* src = flow + (long long)y * W + x;
+      if (al) cp_async8(d0 + (unsigned)t * 8u, src);
+      else sf[t] = *src;
+    }
+  }
+}
+
+// 8-bit luma of window pixel (row rr, column rc) of a staged frame.
+__device__ __forceinline__ int raw_luma(const unsigned char* raw, int ch, int rr, int rc) {
+  const unsigned char* q = raw + rr * (SW * ch) + rc * ch;
+  if (ch == 1) return q[0];
+  return (77 * q[0] + 150 * q[1] + 29 * q[2] + 128) >> 8;
+}
+
+// Replicate-padded halo of log values with reach (hx, hy) from a staged
+// frame (same region and layout as fill_halo): one warp per halo row.
+__device__ __forceinline__ void fill_halo_raw(int* dst, const int* slut, const unsigned char* raw,
+                                              int ch, int W, int H, int tx0, int ty0, int hx,
+                                              int hy) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncols = TW + 2 * hx, nrows = TH + 2 * hy;
+  const int RW = SW * ch;
+  for (int sr = warp; sr < nrows; sr += NTD / 32) {
+    const int gy = min(max(ty0 - hy + sr, 0), H - 1);
+    const unsigned char* src = raw + (gy - (ty0 - HMAX)) * RW;
+    int* d = dst + (HMAX - hy + sr) * SW + (HMAX - hx);
+    for (int sc = lane; sc < ncols; sc += 32) {
+      const int gx = min(max(tx0 - hx + sc, 0), W - 1);
+      const unsigned char* q = src + (gx - (tx0 - HMAX)) * ch;
+      const int v = ch == 1 ? q[0] : (77 * q[0] + 150 * q[1] + 29 * q[2] + 128) >> 8;
+      d[sc] = slut[v];
+    }
+  }
+}
+
+// Substep weights and times of one frame (threads k < N) into the parity's
+// tables; thread 0 publishes N and its division multiplier (divmod_n).
+// Called by threads 0..63 only.
+__device__ __forceinline__ void substep_tables(const SimParams& p, unsigned long long maxf2,
+                                               long long t_prev, long long t_cur, int* swk,
+                                               unsigned* stk, int* sN, unsigned* smN) {
+  const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(maxf2, p.n_max);
+  if ((int)threadIdx.x < N) {
+    const int k = threadIdx.x + 1;
+    swk[threadIdx.x] = (k * 8192 + N) / (2 * N);
+    stk[threadIdx.x] = (unsigned)(t_prev + (k * (t_cur - t_prev)) / N);
+  }
+  if (threadIdx.x == 0) {
+    *sN = N;
+    *smN = N > 1 ? (unsigned)(0x100000000ull / (unsigned)N) + 1u : 0u;
+  }
+}
+
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+__device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b, int tile) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_warp[NTD / 32 + 1];
+  __shared__ int s_fx, s_fy;
+  __shared__ int s_rs[TH + 1];
+  __shared__ int s_N[2];
+  __shared__ unsigned s_mN[2];
+  __shared__ __align__(16) FrameDesc s_desc[4];     // frame fi at fi & 3
+  __shared__ __align__(8) unsigned long long s_mf[4];  // its squared flow maximum
+  __shared__ WarpStage s_stage[NTD / 32];
+  Ctl* ctl = p.ctl;
+  if (block_error(&ctl->err)) return;
+  if ((threadIdx.x & 31) == 0) s_stage[threadIdx.x >> 5] = WarpStage{0, 0, p.stage_chunk};
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nmax = p.n_max, ch = p.ch, RW = SW * ch;
+  const BatchLayout L = batch_layout<SPARSE>(smem_raw, nmax, ch);
+  const int tcx = tile % p.tiles_x, tcy = tile / p.tiles_x;
+  const int tx0 = tcx * TW, ty0 = tcy * TH;
+  const int W = p.W, H = p.H, count = b.count;
+  const bool adaptive = p.n_fixed <= 0;
+
+  if (tid < 256) L.slut[tid] = p.lut[tid];
+  const int sel = ctl->sel;
+  const int* Rin = (sel & 1) ? p.R1 : p.R0;
+  int* Rout = (sel & 1) ? p.R0 : p.R1;
+  const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
+  unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
+  const long long t_first = ctl->t_prev;
+
+  // Dense: thread (warp w, lane l) owns tile pixels (l, w) and (l + 32, w);
+  // sparse: thread t owns tile pixels t and t + NTD.
+  int own[2];
+  bool inimg[2];
+  int Rd[2], Cpd[2], Cnd[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    own[q] = SPARSE ? tid + q * NTD : warp * TW + lane + 32 * q;
+    const int x = tx0 + (own[q] & (TW - 1)), y = ty0 + own[q] / TW;
+    inimg[q] = x < W && y < H;
+    Rd[q] = 0; Cpd[q] = p.cp; Cnd[q] = p.cn;
+    if (inimg[q]) {
+      const long long i = (long long)y * W + x;
+      if (SPARSE) {
+        if (!RESET) L.sR[own[q]] = Rin[i];
+        if (MAPS) { L.sCp[own[q]] = p.cpmap[i]; L.sCn[own[q]] = p.cnmap[i]; }
+      } else {
+        if (!RESET) Rd[q] = Rin[i];
+        if (MAPS) { Cpd[q] = p.cpmap[i]; Cnd[q] = p.cnmap[i]; }
+      }
+    }
+  }
+
+  // prologue: descriptors of frames 0 and 1, the previous frame (ring) and
+  // frame 0 staged, frame 0's flow and substep tables
+  if (tid < 2 && tid < count) {
+    s_desc[tid] = b.frames[tid];
+    s_mf[tid] = adaptive ? p.maxf2[tid] : 0ull;
+  }
+  if (tid == 0) { s_fx = 0; s_fy = 0; }
+  __syncthreads();
+  {
+    const FrameRef ring{ringp, (long long)W, 1};
+    const FrameDesc d0 = s_desc[0];
+    stage_raw(L.raw, ring, W, H, tx0, ty0);
+    stage_raw(L.raw + SH * RW, FrameRef{d0.frame, d0.pitch, ch}, W, H, tx0, ty0);
+    stage_flow(L.sflow, d0.flow, W, H, tx0, ty0);
+    cp_async_commit();
+    if (tid < 64) substep_tables(p, s_mf[0], t_first, d0.t_rel, L.swk, L.stk, &s_N[0], &s_mN[0]);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+
+  int clamps = 0;
+  long long act_sum = 0, act_n = 0;
+  int rb = 1;  // raw buffer of the current frame; 1 - rb holds the previous frame
+  int* cb = L.sLb;
+  int* pb = L.sLa;
+  int phx = -1, phy = -1;
+  int hfx = 1, hfy = 1;  // halo extents only grow within a batch
+
+  for (int fi = 0; fi < count; ++fi) {
+    const int par = fi & 1;
+    const FrameDesc cur = s_desc[fi & 3];
+    FrameRef prv;
+    if (fi == 0) {
+      prv = FrameRef{ringp, (long long)W, 1};
+    } else {
+      const FrameDesc d = s_desc[(fi - 1) & 3];
+      prv = FrameRef{d.frame, d.pitch, ch};
+    }
+    const FrameRef curf{cur.frame, cur.pitch, ch};
+    const unsigned char* rawc = L.raw + rb * SH * RW;
+    const unsigned char* rawp = L.raw + (1 - rb) * SH * RW;
+    const int chp = fi == 0 ? 1 : ch;  // the ring holds luma
+    const int N = s_N[par];
+    const unsigned mN = s_mN[par];
+    Seg* segf = p.seg + (long long)fi * nmax * p.segs_per_k + (long long)ty0 * p.tiles_x + tcx;
+
+    // 1. the pixels to simulate (the previous and current bytes are staged)
+    int A = 0;
+    int sel_flag[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int lx = own[q] & (TW - 1), ly = own[q] / TW;
+      bool a = inimg[q];
+      if (inimg[q] && (SPARSE || fi == count - 1)) {
+        const int vc = raw_luma(rawc, ch, ly + HMAX, lx + HMAX);
+        if (fi == count - 1) ringn[(long long)(ty0 + ly) * W + tx0 + lx] = (unsigned char)vc;
+        if (SPARSE) {
+          const int vp = raw_luma(rawp, chp, ly + HMAX, lx + HMAX);
+          const int cp = MAPS ? (int)L.sCp[own[q]] : p.cp, cn = MAPS ? (int)L.sCn[own[q]] : p.cn;
+          a = abs(L.slut[vc] - L.slut[vp]) >= activity_threshold(p, cp, cn);
+        }
+      }
+      sel_flag[q] = a ? 1 : 0;
+    }
+    if (SPARSE) {
+      const int packed = block_excl_scan<NTD>(sel_flag[0] | (sel_flag[1] << 16), s_warp, &A);
+      const int A0 = A & 0xFFFF;
+      A = A0 + (A >> 16);
+      const int o0 = packed & 0xFFFF, o1 = A0 + (packed >> 16);
+      if (sel_flag[0]) L.sslot[o0] = (short)tid;
+      if (sel_flag[1]) L.sslot[o1] = (short)(tid + NTD);
+      if ((tid & (TW - 1)) == 0) {
+        const int r = tid / TW;
+        s_rs[r] = o0;
+        s_rs[r + NTD / TW] = o1;
+      }
+      if (tid == 0) s_rs[TH] = A;
+      __syncthreads();
+    } else {
+      A = TP;
+    }
+    act_sum += A;
+    act_n += (long long)A * N;
+
+    // 2. the simulated pixels of this thread and their (staged) flow; the
+    // tile's reach
+    int lx[2], ly[2], nk_at[2], Fx[2], Fy[2], R[2], Cp[2], Cn[2];
+    bool act[2];
+    unsigned mfx = 0, mfy = 0;
+    const float2* sfl = L.sflow + par * TP;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int slot;
+      if (SPARSE) {
+        const int j = tid + q * NTD;
+        act[q] = j < A;
+        slot = act[q] ? L.sslot[j] : 0;
+        nk_at[q] = j;
+      } else {
+        act[q] = inimg[q];
+        slot = own[q];
+        nk_at[q] = own[q];
+      }
+      lx[q] = slot & (TW - 1);
+      ly[q] = slot / TW;
+      Fx[q] = 0; Fy[q] = 0;
+      R[q] = SPARSE ? 0 : Rd[q];
+      Cp[q] = SPARSE ? p.cp : Cpd[q];
+      Cn[q] = SPARSE ? p.cn : Cnd[q];
+      if (act[q]) {
+        const float2 fl = sfl[slot];
+        Fx[q] = flow_q16(fl.x, clamps);
+        Fy[q] = flow_q16(fl.y, clamps);
+        if (SPARSE) {
+          if (MAPS) { Cp[q] = L.sCp[slot]; Cn[q] = L.sCn[slot]; }
+          if (!RESET) R[q] = L.sR[slot];
+        }
+        if (RESET) R[q] = L.slut[raw_luma(rawp, chp, ly[q] + HMAX, lx[q] + HMAX)];
+        mfx = max(mfx, (unsigned)abs(Fx[q]));
+        mfy = max(mfy, (unsigned)abs(Fy[q]));
+      }
+    }
+    mfx = __reduce_max_sync(FULL, mfx);
+    mfy = __reduce_max_sync(FULL, mfy);
+    if (lane == 0) {
+      atomicMax(&s_fx, (int)mfx);
+      atomicMax(&s_fy, (int)mfy);
+    }
+    __syncthreads();
+    const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
+    const bool fast = hx <= HMAX && hy <= HMAX;
+    if (fast && A > 0) {
+      hfx = max(hfx, hx);
+      hfy = max(hfy, hy);
+      if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
+        fill_halo_raw(pb, L.slut, rawp, chp, W, H, tx0, ty0, hfx, hfy);
+        phx = hfx;
+        phy = hfy;
+      }
+      fill_halo_raw(cb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy);
+    }
+    __syncthreads();
+    if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
+
+    // 3. the next frame's inputs: its bytes over the previous frame's raw
+    // buffer (read by now), its flow, the descriptor two frames ahead; its
+    // substep tables
+    if (fi + 1 < count) {
+      const FrameDesc nd = s_desc[(fi + 1) & 3];
+      stage_raw(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
+      stage_flow(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
+      if (fi + 2 < count && tid < 2) {
+        // descriptors are 32-byte, 16-byte aligned records
+        cp_async16(smem_addr(&s_desc[(fi + 2) & 3]) + 16u * tid,
+                   (const unsigned char*)&b.frames[fi + 2] + 16 * tid);
+        if (tid == 0 && adaptive) cp_async8(smem_addr(&s_mf[(fi + 2) & 3]), &p.maxf2[fi + 2]);
+      }
+      cp_async_commit();
+      if (tid < 64)
+        substep_tables(p, s_mf[(fi + 1) & 3], cur.t_rel, nd.t_rel, L.swk + (par ^ 1) * nmax,
+                       L.stk + (par ^ 1) * nmax, &s_N[par ^ 1], &s_mN[par ^ 1]);
+    }
+
+    // 4. substeps (sparse: warps without a compacted pixel skip them); dense
+    // rows publish their segments from the loop
+    TileLayout V;
+    V.slut = L.slut;
+    V.stk = L.stk + par * nmax;
+    V.swk = L.swk + par * nmax;
+    V.snk = L.snk;
+    const unsigned b0 = smem_addr(pb);
+    const unsigned b1 = smem_addr(cb);
+    if (!SPARSE && fast) {
+      if (ty0 + warp < H)  // warp-uniform: rows below the image publish nothing
+        dense_substeps<RESET, WIDE>(p, V.swk, V.stk, N, mN, tx0, ty0 + warp, b0, b1,
+                                    segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy, R, Cp,
+                                    Cn);
+    } else if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
+      if (fast)
+        tile_substeps<RESET, WIDE, true, !SPARSE>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
+                                                  lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
+                                                  &s_stage[warp]);
+      else
+        tile_substeps<RESET, WIDE, false, !SPARSE>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
+                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
+                                                   &s_stage[warp]);
+    }
+    if (!RESET) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (SPARSE) {
+          if (act[q]) L.sR[lx[q] + ly[q] * TW] = R[q];
+        } else {
+          Rd[q] = R[q];
+        }
+      }
+    }
+
+    // 5. sparse: warp r publishes the segments of tile row r from the
+    // records of the row's slots (contiguous, in column order)
+    if (SPARSE) {
+      __syncthreads();
+      const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
+      const int y = ty0 + r;
+      if (y < H) {
+        if (s1 == s0) {
+          for (int k = lane; k < N; k += 32) segf[(long long)k * p.segs_per_k + r * p.tiles_x] =
+              Seg{0ull, 0ull, 0, -1};
+        } else {
+          const int j_lo = s0 + lane, j_hi = s0 + 32 + lane;
+          const bool v_lo = j_lo < s1, v_hi = j_hi < s1;
+          const int col_lo = v_lo ? (L.sslot[j_lo] & (TW - 1)) : 0;
+          const int col_hi = v_hi ? (L.sslot[j_hi] & (TW - 1)) : 0;
+          for (int k = 0; k < N; ++k) {
+            const int n_lo = v_lo ? L.snk[k * TP + j_lo] : 0;
+            const int n_hi = v_hi ? L.snk[k * TP + j_hi] : 0;
+            publish_row(p, segf + (long long)k * p.segs_per_k + r * p.tiles_x, n_lo, col_lo, v_lo,
+                        n_hi, col_hi, v_hi, V.stk[k], tx0, y, &s_stage[warp]);
+          }
+        }
+      }
+    }
+    // frame i's halo becomes the previous-frame halo of frame i + 1
+    if (fast && A > 0) {
+      int* t = pb;
+      pb = cb;
+      cb = t;
+      phx = hfx;
+      phy = hfy;
+    } else {
+      phx = -1;
+      phy = -1;
+    }
+    rb = 1 - rb;
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
+  if (!RESET) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!inimg[q]) continue;
+      Rout[(long long)(ty0 + own[q] / TW) * W + tx0 + (own[q] & (TW - 1))] =
+          SPARSE ? L.sR[own[q]] : Rd[q];
+    }
+  }
+  clamps = __reduce_add_sync(FULL, clamps);
+  if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
+  if (SPARSE && tid == 0 && act_sum) {
+    atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)act_sum);
+    atomicAdd((unsigned long long*)&ctl->active_n, (unsigned long long)act_n);
+  }
+}
+
 // One stream's batch: one block per tile carries the tile through every
-// frame of the batch (blocks never wait for one another).
+// frame of the batch, its inputs staged a frame ahead (blocks never wait for
+// one another).
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
 __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
-  tile_frames<RESET, MAPS, WIDE, SPARSE>(p, b, blockIdx.x, 0, b.count);
+  tile_batch<RESET, MAPS, WIDE, SPARSE>(p, b, blockIdx.x);
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
@@ -927,6 +1583,8 @@ struct OrderSmem {
   unsigned xy[OCHUNK];  // x0 | (y << 16)
   int N[SIM_MAX_BATCH];  // substeps of each frame of the batch
   int warp[NWARP + 1];
+  int cblk[OCHUNK];      // segments of the chunk with per-pixel counts
+  int ncblk;
   int last;
   long long prefix;
 };
@@ -974,8 +1632,10 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
       tk = (unsigned)(tp + ((long long)(k + 1) * dt) / N);
     }
   }
+  if (tid == 0) o.ncblk = 0;
   int total;
   const int ex = block_excl_scan(cnt, o.warp, &total);
+  if (src <= -2 && cnt > 0) o.cblk[atomicAdd(&o.ncblk, 1)] = tid;
   o.ex[tid] = ex;
   o.src[tid] = src;
   o.mask[tid] = mask;
@@ -996,6 +1656,7 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
     }
     const long long dst = base + jj;
     if (dst >= p.event_cap) continue;
+    if (o.src[lo] <= -2) continue;  // per-pixel counts: expanded below
     const int m = jj - o.ex[lo];
     Ev ev;
     if (o.src[lo] >= 0) {
@@ -1007,6 +1668,33 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
                       (o.pol[lo] >> bit) & 1ull);
     }
     p.events[dst] = ev;
+  }
+  // rows published as per-pixel counts: one warp per row, columns l and
+  // l + 32 on lane l, in column order with repeats adjacent
+  {
+    const int lane = tid & 31;
+    for (int q = tid >> 5; q < o.ncblk; q += NWARP) {
+      const int sidx = o.cblk[q];
+      const unsigned wd = ((const unsigned*)(p.staging + (-2LL - o.src[sidx])))[lane];
+      const int a_lo = (int)(wd & 0xFFFFu), a_hi = (int)(wd >> 16);
+      const int i_lo = warp_incl_scan(a_lo);
+      const int t_lo = __shfl_sync(FULL, i_lo, 31);
+      const int i_hi = warp_incl_scan(a_hi);
+      const long long d0 = base + o.ex[sidx];
+      const unsigned xy0 = o.xy[sidx], tk = o.t[sidx];
+      const unsigned long long pl = o.pol[sidx];
+      const int x0 = (int)(xy0 & 0xFFFF), y = (int)(xy0 >> 16);
+      const Ev e_lo = make_event(tk, x0 + lane, y, (pl >> lane) & 1ull);
+      const Ev e_hi = make_event(tk, x0 + lane + 32, y, (pl >> (lane + 32)) & 1ull);
+      for (int m = 0; m < a_lo; ++m) {
+        const long long dst = d0 + i_lo - a_lo + m;
+        if (dst < p.event_cap) p.events[dst] = e_lo;
+      }
+      for (int m = 0; m < a_hi; ++m) {
+        const long long dst = d0 + t_lo + i_hi - a_hi + m;
+        if (dst < p.event_cap) p.events[dst] = e_hi;
+      }
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -1328,9 +2016,10 @@ __global__ void __launch_bounds__(NT) k_drain(GroupArg g, DrainArg d) {
 }
 
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
-void set_tile_attr(size_t bytes) {
+void set_tile_attr(int n_max) {
   cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batch_smem_bytes(n_max, 3, SPARSE));
 }
 
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
@@ -1359,7 +2048,7 @@ cudaError_t launch_tile_multi_mode(const GroupArg& g, int cls, const ActiveTile*
 template <bool SPARSE>
 cudaError_t launch_tile_mode(const SimParams& p, const BatchArg& b, cudaStream_t st) {
   const int grid = p.tiles_x * p.tiles_y;
-  const size_t sm = tile_smem_bytes(p.n_max);
+  const size_t sm = batch_smem_bytes(p.n_max, p.ch, SPARSE);
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
@@ -1390,7 +2079,7 @@ int device_sm_count() {
 }
 
 cudaError_t configure_kernels(int n_max) {
-  const size_t t = tile_smem_bytes(n_max);
+  const int t = n_max;
   set_tile_attr<false, false, false, false>(t);
   set_tile_attr<false, true, false, false>(t);
   set_tile_attr<false, false, true, false>(t);

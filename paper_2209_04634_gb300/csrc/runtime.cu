@@ -23,7 +23,7 @@ thread_local cudaError_t g_last_cuda = cudaSuccess;
 // Sizes of a handle's device buffers.
 struct Sizing {
   int n_max, tiles_x;
-  long long P, cap, segs_per_k, seg_cap, ochunks;
+  long long P, cap, stage, segs_per_k, seg_cap, ochunks;
   int bmax;
 };
 
@@ -34,6 +34,11 @@ Sizing sizing(const sim_config& c) {
   z.tiles_x = (c.width + evsim::TW - 1) / evsim::TW;
   long long cap = c.event_capacity > 0 ? c.event_capacity : std::max<long long>(1LL << 20, 8 * z.P);
   z.cap = std::min<long long>(cap, evsim::MAX_EVENTS);
+  // staging: the events of multi-crossing rows, taken in per-warp chunks
+  // (at most a third wasted, plus one chunk per warp)
+  const long long warps = (long long)z.tiles_x * ((c.height + evsim::TH - 1) / evsim::TH) *
+                          (evsim::NTD / 32);
+  z.stage = z.cap + z.cap / 3 + (warps + 1) * evsim::STAGE_CHUNK;
   z.segs_per_k = (long long)c.height * z.tiles_x;  // one segment per tile row
   // frames per batch: the requested cap, else what a 512 MB segment table holds
   const long long seg_bytes_per_frame = z.segs_per_k * z.n_max * (long long)sizeof(evsim::Seg);
@@ -50,7 +55,7 @@ long long state_bytes(const sim_config& c) {
   const Sizing z = sizing(c);
   long long b = 256 * 4 + 2 * z.P + (long long)sizeof(Ctl) + 8LL * z.bmax;
   if (c.ref_mode == SIM_REF_ACCUM) b += 8 * z.P;
-  b += 2 * z.cap * (long long)sizeof(Ev);                // staging + events
+  b += (z.stage + z.cap) * (long long)sizeof(Ev);       // staging + events
   b += z.seg_cap * (long long)sizeof(evsim::Seg) + 8 * z.ochunks;
   b += 8LL * z.tiles_x * ((c.height + evsim::TH - 1) / evsim::TH);  // tile progress words
   b += (long long)z.bmax * sizeof(evsim::FrameDesc);
@@ -120,7 +125,8 @@ evsim::SimParams make_params(const sim_t* s) {
   p.ctl = s->d_ctl;
   p.maxf2 = s->d_maxf2;
   p.staging = s->d_staging;
-  p.stage_cap = s->event_cap;
+  p.stage_cap = s->stage_cap;
+  p.stage_chunk = evsim::STAGE_CHUNK;
   p.seg = s->d_seg;
   p.tdone = s->d_tdone;
   p.segs_per_k = s->segs_per_k;
@@ -356,6 +362,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   const Sizing z = sizing(c);
   const long long cap = z.cap;
   s->event_cap = cap;
+  s->stage_cap = z.stage;
   s->segs_per_k = z.segs_per_k;
   s->bmax = z.bmax;
   const long long seg_cap = z.seg_cap;
@@ -378,7 +385,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   }
   chk(dalloc(&s->d_ctl, 1));
   chk(dalloc(&s->d_maxf2, s->bmax));
-  chk(dalloc(&s->d_staging, cap));
+  chk(dalloc(&s->d_staging, z.stage));
   chk(dalloc(&s->d_events, cap));
   chk(dalloc(&s->d_seg, seg_cap));
   chk(dalloc(&s->d_tdone, (size_t)s->tiles_x * s->tiles_y));

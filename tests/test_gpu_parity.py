@@ -163,6 +163,33 @@ def test_mixed_tiles_small_and_large_flow():
 
 
 @pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
+@pytest.mark.parametrize("batch", [0, 3])
+def test_rows_of_multi_crossings(mode, batch):
+    """Pixels that cross several thresholds in one substep: whole rows of
+    them (rows of 16 or more events, which dense tiles publish as per-pixel
+    counts) and a single such pixel in a row (its events are staged), both in
+    the oracle's order (substep, row, column, repeats adjacent)."""
+    H, W, F = 40, 150, 4
+    fr = np.full((F, H, W), 20, np.uint8)
+    fr[1] = 240                          # ~12 thresholds per pixel in one substep
+    fr[2] = 240
+    fr[2, 5, 7] = 100                    # one pixel: 4 thresholds down
+    fr[3] = 240
+    fr[3, 30:33, 64:70] = 15             # a small block: rows of 36 events
+    flows = np.zeros((F, H, W, 2), np.float32)
+    t = np.arange(F, dtype=np.int64) * 10000
+    seq = synth.Sequence("multi", fr, flows, t, 1, 8, 0.2, 0.2)
+    if batch:
+        g = gpu_run(seq, mode, use_maps=False, substeps=1, batch=batch)
+        o = oracle_run(seq, mode, use_maps=False, substeps=1)
+        assert_same_events(g["events"], o["events"], "multi-crossing rows (batched)")
+        assert np.array_equal(g["R"], o["R"])
+    else:
+        g, o = check_parity(seq, mode, "multi-crossing rows", use_maps=False, substeps=1)
+    assert o["ev_per_frame"][1] >= 12 * H * W
+
+
+@pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
 def test_nan_and_clamped_flow(mode):
     seq = random_seq(40, 70, F=3, seed=5)
     seq.flows[1, 3, 4] = (np.nan, 2.0)
