@@ -730,6 +730,69 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const int* sw
   }
 }
 
+// Sparse fast path: the substeps of this thread's compacted pixels (slots
+// tid and, NPX = 2, tid + NTD; `act` says which exist), sampling the shared
+// halos.  Each pixel's count per substep goes to snk (slot order) and, when
+// non-zero, into the tile's row masks: rowm[(k TH + row) 4 + {0,1}] event
+// bits of columns 0-31 / 32-63, {2,3} polarity bits; rows in which a pixel
+// crossed two or more thresholds are flagged in smulti[k] (bit = row).
+template <bool RESET, bool WIDE, int NPX>
+__device__ __forceinline__ void sparse_substeps(const int* swk, int N, unsigned mN, unsigned b0,
+                                                unsigned b1, short* snk, unsigned* rowm,
+                                                unsigned* smulti, const int (&lx)[2],
+                                                const int (&ly)[2], const bool (&act)[2],
+                                                const int (&Fx)[2], const int (&Fy)[2],
+                                                int (&R)[2], const int (&Cp)[2],
+                                                const int (&Cn)[2]) {
+  int px[NPX], py[NPX], ax[NPX], ay[NPX], qx[NPX], rx[NPX], qy[NPX], ry[NPX];
+#pragma unroll
+  for (int j = 0; j < NPX; ++j) {
+    px[j] = (lx[j] + HMAX) << 16;
+    py[j] = (ly[j] + HMAX) << 16;
+    divmod_n(Fx[j], N, mN, qx[j], rx[j]);
+    divmod_n(Fy[j], N, mN, qy[j], ry[j]);
+    ax[j] = 0;
+    ay[j] = 0;
+  }
+  for (int k = 0; k < N; ++k) {
+    const int w = swk[k];
+#pragma unroll
+    for (int j = 0; j < NPX; ++j) {
+      px[j] -= qx[j];
+      ax[j] += rx[j];
+      if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
+      py[j] -= qy[j];
+      ay[j] += ry[j];
+      if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
+      const int s0 = tap_shared<WIDE>(b0, px[j], py[j]);
+      const int s1 = tap_shared<WIDE>(b1, px[j] + Fx[j], py[j] + Fy[j]);
+      const int I = lerp12<WIDE>(s0, s1, w);
+      const int d = I - R[j];
+      int n;
+      if (RESET) {
+        R[j] = I;
+        n = d > Cp[j] ? 1 : (d < -Cn[j] ? -1 : 0);
+      } else {
+        n = d >= Cp[j] ? 1 : (d <= -Cn[j] ? -1 : 0);
+        if (d >= 2 * Cp[j]) n = floordiv_pos<WIDE>(d, Cp[j]);
+        else if (d <= -2 * Cn[j]) n = -floordiv_pos<WIDE>(-d, Cn[j]);
+        R[j] += n * (n > 0 ? Cp[j] : Cn[j]);
+      }
+      if (act[j]) {
+        snk[k * TP + threadIdx.x + j * NTD] = (short)n;
+        if (n != 0) {
+          unsigned* m = rowm + (k * TH + ly[j]) * 4;
+          const unsigned bit = 1u << (lx[j] & 31);
+          const int h = lx[j] >> 5;
+          atomicOr(m + h, bit);
+          if (n > 0) atomicOr(m + 2 + h, bit);
+          if (n > 1 || n < -1) atomicOr(smulti + k, 1u << ly[j]);
+        }
+      }
+    }
+  }
+}
+
 // Wait (thread 0, bounded) until the tile's progress word reaches `want`
 // ([batch serial:32][frames done:32]); gives up when the stream has failed
 // or after SPIN_LIMIT polls (then flags a timeout).
@@ -1206,6 +1269,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   __shared__ int s_rs[TH + 1];
   __shared__ int s_N[2];
   __shared__ unsigned s_mN[2];
+  __shared__ unsigned s_multi[32];  // sparse: rows with multi-crossings, per substep
   __shared__ __align__(16) FrameDesc s_desc[4];     // frame fi at fi & 3
   __shared__ __align__(8) unsigned long long s_mf[4];  // its squared flow maximum
   __shared__ WarpStage s_stage[NTD / 32];
@@ -1383,6 +1447,14 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     __syncthreads();
     const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
     const bool fast = hx <= HMAX && hy <= HMAX;
+    // sparse fast path: row masks in the current flow buffer (its flows are
+    // in registers by now), cleared here
+    const bool maskpub = SPARSE && fast && N <= 32;
+    unsigned* rowm = (unsigned*)(L.sflow + par * TP);
+    if (maskpub) {
+      for (int i = tid; i < N * TH * 4; i += NTD) rowm[i] = 0u;
+      if (tid < N) s_multi[tid] = 0u;
+    }
     if (fast && A > 0) {
       hfx = max(hfx, hx);
       hfy = max(hfy, hy);
@@ -1429,6 +1501,15 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         dense_substeps<RESET, WIDE>(p, V.swk, V.stk, N, mN, tx0, ty0 + warp, b0, b1,
                                     segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy, R, Cp,
                                     Cn);
+    } else if (maskpub) {  // warp-uniform: one pixel per thread when A <= NTD
+      if (A <= NTD) {
+        if (warp * 32 < A)
+          sparse_substeps<RESET, WIDE, 1>(V.swk, N, mN, b0, b1, L.snk, rowm, s_multi, lx, ly, act,
+                                          Fx, Fy, R, Cp, Cn);
+      } else {
+        sparse_substeps<RESET, WIDE, 2>(V.swk, N, mN, b0, b1, L.snk, rowm, s_multi, lx, ly, act,
+                                        Fx, Fy, R, Cp, Cn);
+      }
     } else if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
       if (fast)
         tile_substeps<RESET, WIDE, true, !SPARSE>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
@@ -1450,9 +1531,37 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       }
     }
 
-    // 5. sparse: warp r publishes the segments of tile row r from the
-    // records of the row's slots (contiguous, in column order)
-    if (SPARSE) {
+    // 5. sparse, fast path: one thread per (substep, row) publishes the row's
+    // masks; warp r stages the rows with multi-crossings from the records of
+    // the row's slots (contiguous, in column order)
+    if (maskpub) {
+      __syncthreads();
+      for (int t = tid; t < N * TH; t += NTD) {
+        const int k = t / TH, r = t - k * TH;
+        if (ty0 + r >= H || ((s_multi[k] >> r) & 1u)) continue;
+        const unsigned* m = rowm + t * 4;
+        const int cnt = __popc(m[0]) + __popc(m[1]);
+        segf[(long long)k * p.segs_per_k + r * p.tiles_x] =
+            cnt ? Seg{(unsigned long long)m[0] | ((unsigned long long)m[1] << 32),
+                      (unsigned long long)m[2] | ((unsigned long long)m[3] << 32), cnt, -1}
+                : Seg{0ull, 0ull, 0, -1};
+      }
+      const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
+      const int y = ty0 + r;
+      if (y < H) {
+        const int j_lo = s0 + lane, j_hi = s0 + 32 + lane;
+        const bool v_lo = j_lo < s1, v_hi = j_hi < s1;
+        const int col_lo = v_lo ? (L.sslot[j_lo] & (TW - 1)) : 0;
+        const int col_hi = v_hi ? (L.sslot[j_hi] & (TW - 1)) : 0;
+        for (int k = 0; k < N; ++k) {
+          if (!((s_multi[k] >> r) & 1u)) continue;  // warp-uniform
+          const int n_lo = v_lo ? L.snk[k * TP + j_lo] : 0;
+          const int n_hi = v_hi ? L.snk[k * TP + j_hi] : 0;
+          publish_row(p, segf + (long long)k * p.segs_per_k + r * p.tiles_x, n_lo, col_lo, v_lo,
+                      n_hi, col_hi, v_hi, V.stk[k], tx0, y, &s_stage[warp]);
+        }
+      }
+    } else if (SPARSE) {
       __syncthreads();
       const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
       const int y = ty0 + r;
@@ -1515,7 +1624,8 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
-// of each frame.
+// of each frame.  Block bx of nbx walks rows bx, bx + nbx, ...; each thread
+// takes four columns of a row at a time, their loads issued together.
 __device__ __forceinline__ void sparse_pre_run(const SimParams& p, const BatchArg& b, int fi,
                                                int bx, int nbx) {
   __shared__ int slut[256];
@@ -1528,20 +1638,39 @@ __device__ __forceinline__ void sparse_pre_run(const SimParams& p, const BatchAr
   const unsigned char* ringp = (ctl->sel & 2) ? p.ring1 : p.ring0;
   const FrameDesc cur = b.frames[fi];
   const FrameRef prv = prev_frame(p, b, fi, ringp);
-  const long long P = (long long)p.W * p.H;
+  const int W = p.W;
+  constexpr int U = 4;
   unsigned long long m = 0;
   int dummy = 0;
-  for (long long i = bx * (long long)NT + tid; i < P; i += (long long)nbx * NT) {
-    const int y = (int)(i / p.W), x = (int)(i - (long long)y * p.W);
-    const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
-    const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
-    const int cp = p.cpmap ? p.cpmap[i] : p.cp;
-    const int cn = p.cnmap ? p.cnmap[i] : p.cn;
-    if (abs(slut[vc] - slut[vp]) >= activity_threshold(p, cp, cn)) {
-      const float2 fl = cur.flow[i];
-      const long long fx = flow_q16(fl.x, dummy), fy = flow_q16(fl.y, dummy);
-      const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
-      m = f2 > m ? f2 : m;
+  for (int y = bx; y < p.H; y += nbx) {
+    const unsigned char* rp = prv.ptr + (long long)y * prv.pitch;
+    const unsigned char* rc = cur.frame + (long long)y * cur.pitch;
+    const long long row = (long long)y * W;
+    for (int x0 = tid; x0 < W; x0 += NT * U) {
+      int d[U], c[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int x = x0 + q * NT;
+        d[q] = -1;
+        c[q] = 0;
+        if (x < W) {
+          const int vp = prv.ch == 1 ? rp[x] : load_luma(rp, 0, prv.ch, 0, x);
+          const int vc = p.ch == 1 ? rc[x] : load_luma(rc, 0, p.ch, 0, x);
+          const int cp = p.cpmap ? p.cpmap[row + x] : p.cp;
+          const int cn = p.cnmap ? p.cnmap[row + x] : p.cn;
+          d[q] = abs(slut[vc] - slut[vp]);
+          c[q] = activity_threshold(p, cp, cn);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (d[q] >= c[q]) {
+          const float2 fl = cur.flow[row + x0 + q * NT];
+          const long long fx = flow_q16(fl.x, dummy), fy = flow_q16(fl.y, dummy);
+          const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
+          m = f2 > m ? f2 : m;
+        }
+      }
     }
   }
   m = warp_max_u64(m);
@@ -1582,6 +1711,7 @@ struct OrderSmem {
   unsigned t[OCHUNK];
   unsigned xy[OCHUNK];  // x0 | (y << 16)
   int N[SIM_MAX_BATCH];  // substeps of each frame of the batch
+  int FN[SIM_MAX_BATCH + 1];  // substeps of the frames before each frame
   int warp[NWARP + 1];
   int cblk[OCHUNK];      // segments of the chunk with per-pixel counts
   int ncblk;
@@ -1589,11 +1719,26 @@ struct OrderSmem {
   long long prefix;
 };
 
-// Substep counts of the batch's frames into o.N (all threads; the caller
-// synchronises before they are read).
-__device__ __forceinline__ void order_fill_n(const SimParams& p, const BatchArg& b, OrderSmem& o) {
+// Substep counts of the batch's frames into o.N and their exclusive prefix
+// into o.FN (FN[count] = all substeps of the batch); returns the number of
+// chunks of the batch's live segments (those of substeps k < N of their
+// frame).  All threads; contains barriers.
+__device__ __forceinline__ int order_fill_n(const SimParams& p, const BatchArg& b, OrderSmem& o) {
   for (int i = threadIdx.x; i < b.count; i += NT)
     o.N[i] = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[i], p.n_max);
+  __syncthreads();
+  int carry = 0;
+  for (int base = 0; base < b.count; base += NT) {
+    const int i = base + threadIdx.x;
+    int tot;
+    const int ex = block_excl_scan(i < b.count ? o.N[i] : 0, o.warp, &tot);
+    if (i < b.count) o.FN[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) o.FN[b.count] = carry;
+  __syncthreads();
+  const long long live = (long long)carry * p.segs_per_k;
+  return (int)max(1LL, (live + OCHUNK - 1) / OCHUNK);
 }
 
 // Chunk c (of nchunks) of one stream's batch: OCHUNK segments in output
@@ -1605,26 +1750,31 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
   Ctl* ctl = p.ctl;
   const int tid = threadIdx.x;
   const long long S = p.segs_per_k;
-  const long long per_frame = (long long)p.n_max * S;
-  const long long nseg = (long long)b.count * per_frame;
-  // one segment per thread; segments of substeps k >= N of their frame were
-  // never written and count zero
+  // live segments only: (frame, substep k < N of the frame, row); a chunk
+  // index beyond them (a ticket range sized for n_max substeps) is empty
+  const long long nlive = (long long)o.FN[b.count] * S;
+  if ((long long)c * OCHUNK >= nlive) return;
+  // one segment per thread
   const long long si = (long long)c * OCHUNK + tid;
   int cnt = 0, src = -1;
   unsigned long long mask = 0, pol = 0;
   unsigned tk = 0, xy = 0;
-  if (si < nseg) {
-    const int fi = (int)(si / per_frame);
-    const long long rem = si - (long long)fi * per_frame;
-    const int k = (int)(rem / S);
+  if (si < nlive) {
+    const long long q = si / S;  // frame-substep of the batch
+    const int rs = (int)(si - q * S);
+    int fi = 0, hi = b.count;
+    while (hi - fi > 1) {
+      const int mid = (fi + hi) >> 1;
+      if (o.FN[mid] <= q) fi = mid; else hi = mid;
+    }
+    const int k = (int)(q - o.FN[fi]);
     const int N = o.N[fi];
-    if (k < N) {
-      const Seg sg = p.seg[si];
+    {
+      const Seg sg = p.seg[((long long)fi * p.n_max + k) * S + rs];
       cnt = sg.cnt;
       src = sg.src;
       mask = sg.mask;
       pol = sg.pol;
-      const int rs = (int)(rem - (long long)k * S);
       const int y = rs / p.tiles_x, tc = rs - y * p.tiles_x;
       xy = (unsigned)(tc * TW) | ((unsigned)y << 16);
       const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
@@ -1740,19 +1890,13 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
   __syncthreads();
 }
 
-__device__ __forceinline__ int order_nchunks(const SimParams& p, int count) {
-  const long long nseg = (long long)count * p.n_max * p.segs_per_k;
-  return (int)max(1LL, (nseg + OCHUNK - 1) / OCHUNK);
-}
-
 __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
   __shared__ OrderSmem o;
   __shared__ int s_c;
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
   const int tid = threadIdx.x;
-  order_fill_n(p, b, o);
-  const int nchunks = order_nchunks(p, b.count);
+  const int nchunks = order_fill_n(p, b, o);
   const long long cursor = ctl->cursor;
   const long long t_first = ctl->t_prev;  // t of the frame before the batch
   __syncthreads();
@@ -1901,13 +2045,12 @@ __global__ void __launch_bounds__(NT) k_order_multi(GroupArg g) {
     if (s != cur) {
       load_stream(g, s, sp, sb);
       __syncthreads();
-      order_fill_n(sp, sb, o);
+      nchunks = order_fill_n(sp, sb, o);
       if (tid == 0) {
         s_cursor = sp.ctl->cursor;
         s_tfirst = sp.ctl->t_prev;
       }
       cur = s;
-      nchunks = order_nchunks(sp, sb.count);
     }
     if (tid == 0) s_err = ld_volatile(&sp.ctl->err);
     __syncthreads();
@@ -2124,10 +2267,9 @@ cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st
 }
 
 cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st) {
-  const long long P = (long long)p.W * p.H;
   const int sms = device_sm_count();
-  const long long per_frame = std::max(1LL, (long long)sms * 4 / std::max(1, b.count));
-  const int gx = (int)std::max(1LL, std::min<long long>((P + NT - 1) / NT, per_frame));
+  const long long per_frame = std::max(1LL, (long long)sms * 8 / std::max(1, b.count));
+  const int gx = (int)std::max(1LL, std::min<long long>(p.H, per_frame));
   k_sparse_pre<<<dim3(gx, b.count), NT, 0, st>>>(p, b);
   return cudaGetLastError();
 }
