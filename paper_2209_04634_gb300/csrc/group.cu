@@ -377,7 +377,11 @@ int simb_admit(simb_t* g, const sim_config* cfg, int32_t* id) {
   m->cls = evsim::tile_class(p);
   m->tiles = s->tiles_x * s->tiles_y;
   m->adaptive = s->cfg.substeps == 0;
-  m->pre_blocks = (int)std::max(1LL, (P + evsim::NT * 8 - 1) / (evsim::NT * 8));
+  // pre-pass blocks per frame: dense flow maximum over NT * 8 pixels per
+  // block, sparse activity + flow maximum one warp per row
+  m->pre_blocks = s->cfg.mode == SIM_SPARSE
+                      ? (s->H + evsim::NWARP - 1) / evsim::NWARP
+                      : (int)std::max(1LL, (P + evsim::NT * 8 - 1) / (evsim::NT * 8));
   m->q.reserve(g->fmax);
   g->id_slot[slot] = (int)g->members.size();
   g->members.push_back(m);

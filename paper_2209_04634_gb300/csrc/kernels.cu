@@ -1624,15 +1624,16 @@ __global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
-// of each frame.  Block bx of nbx walks rows bx, bx + nbx, ...; each thread
-// takes four columns of a row at a time, their loads issued together.
+// of each frame.  Warp w of block bx (of nbx) takes rows bx * NWARP + w,
+// + nbx * NWARP, ...; each lane four columns of the row at a time, their
+// loads issued together.
 __device__ __forceinline__ void sparse_pre_run(const SimParams& p, const BatchArg& b, int fi,
                                                int bx, int nbx) {
   __shared__ int slut[256];
   __shared__ unsigned long long s_m[NWARP];
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   slut[tid] = p.lut[tid];
   __syncthreads();
   const unsigned char* ringp = (ctl->sel & 2) ? p.ring1 : p.ring0;
@@ -1642,15 +1643,15 @@ __device__ __forceinline__ void sparse_pre_run(const SimParams& p, const BatchAr
   constexpr int U = 4;
   unsigned long long m = 0;
   int dummy = 0;
-  for (int y = bx; y < p.H; y += nbx) {
+  for (int y = bx * NWARP + warp; y < p.H; y += nbx * NWARP) {
     const unsigned char* rp = prv.ptr + (long long)y * prv.pitch;
     const unsigned char* rc = cur.frame + (long long)y * cur.pitch;
     const long long row = (long long)y * W;
-    for (int x0 = tid; x0 < W; x0 += NT * U) {
+    for (int x0 = lane; x0 < W; x0 += 32 * U) {
       int d[U], c[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        const int x = x0 + q * NT;
+        const int x = x0 + q * 32;
         d[q] = -1;
         c[q] = 0;
         if (x < W) {
@@ -1665,7 +1666,7 @@ __device__ __forceinline__ void sparse_pre_run(const SimParams& p, const BatchAr
 #pragma unroll
       for (int q = 0; q < U; ++q) {
         if (d[q] >= c[q]) {
-          const float2 fl = cur.flow[row + x0 + q * NT];
+          const float2 fl = cur.flow[row + x0 + q * 32];
           const long long fx = flow_q16(fl.x, dummy), fy = flow_q16(fl.y, dummy);
           const unsigned long long f2 = (unsigned long long)(fx * fx + fy * fy);
           m = f2 > m ? f2 : m;
@@ -1674,7 +1675,7 @@ __device__ __forceinline__ void sparse_pre_run(const SimParams& p, const BatchAr
     }
   }
   m = warp_max_u64(m);
-  if ((tid & 31) == 0) s_m[tid >> 5] = m;
+  if (lane == 0) s_m[warp] = m;
   __syncthreads();
   if (tid == 0) {
     unsigned long long bm = 0;
@@ -2267,9 +2268,8 @@ cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st
 }
 
 cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st) {
-  const int sms = device_sm_count();
-  const long long per_frame = std::max(1LL, (long long)sms * 8 / std::max(1, b.count));
-  const int gx = (int)std::max(1LL, std::min<long long>(p.H, per_frame));
+  // one warp per row
+  const int gx = (p.H + NWARP - 1) / NWARP;
   k_sparse_pre<<<dim3(gx, b.count), NT, 0, st>>>(p, b);
   return cudaGetLastError();
 }
