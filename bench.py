@@ -231,8 +231,17 @@ def run_ours(args, ws, rank, local):
     flows = torch.from_numpy(seq.flows).cuda()
     cap = 24_000_000
     out = torch.empty(cap * 8, dtype=torch.uint8, device="cuda")
+    # tile shape of each pass from the library's autotuner (synthetic probe of
+    # the same configuration, before the timed region); the simulators take it
+    tune = {}
+    for m, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
+        th, us16, us8 = evsim.autotune(W, H, frames=8, **evsim.seq_options(seq, mode=m))
+        tune[name] = {"tile_height": th, "probe_us_per_frame_64x16": us16,
+                      "probe_us_per_frame_64x8": us8}
     sims = {m: evsim.simulator_for(seq, m, event_capacity=cap, stream=stream)
             for m in (evsim.SIM_DENSE, evsim.SIM_SPARSE)}
+    for m, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
+        assert sims[m].stats().tile_height == tune[name]["tile_height"]
     t_us = seq.t_us
 
     def step():
@@ -291,7 +300,8 @@ def run_ours(args, ws, rank, local):
     total_work = sum_over_ranks(ws, work_step * args.steps)
     total_ev = sum_over_ranks(ws, n_ev)
     value = total_work / (ms_max / 1e3) / 1e9
-    line_roofline = roofline_dense(seq, ktimes, work[evsim.SIM_DENSE])
+    line_roofline = roofline_dense(seq, ktimes, work[evsim.SIM_DENSE],
+                                   tune["dense"]["tile_height"])
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
@@ -309,6 +319,7 @@ def run_ours(args, ws, rank, local):
         "roofline": line_roofline,
         "gpu_launches": launches,
         "clocks": clk,
+        "autotune": tune,
     }
 
     if rank == 0 and not args.no_e2e:
@@ -338,7 +349,7 @@ def run_ours(args, ws, rank, local):
 OPS_PER_PIXEL_SUBSTEP = 4 + 4 + 2 * (6 + 2 + 15) + 5 + 3
 
 
-def roofline_dense(seq, ktimes, dense_units):
+def roofline_dense(seq, ktimes, dense_units, tile_h):
     """Roofline of the dense tile kernel (the dominant kernel): integer issue
     bound; its HBM figures are reported beside it."""
     import torch
@@ -364,7 +375,8 @@ def roofline_dense(seq, ktimes, dense_units):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm = hbm_bytes / avg_s / 1e9
     traffic, _ = committed_traffic("dense")
-    return {"bound": "alu", "kernel": "k_tile<dense> (one launch per 99-frame batch)",
+    return {"bound": "alu",
+            "kernel": f"k_tile<dense>, 64x{tile_h} tiles (one launch per 99-frame batch)",
             "achieved": alu, "peak": alu_peak, "unit": "Tops/s (32-bit integer lane ops)",
             "frac": alu / alu_peak, "traffic": traffic,
             "ops_per_pixel_substep": OPS_PER_PIXEL_SUBSTEP, "pixel_substeps_per_launch": dense_units,

@@ -101,7 +101,17 @@ typedef struct {
   int64_t event_capacity;    /* device event buffer (events); 0: default max(2^20, 8 W H) */
   void* cuda_stream;         /* cudaStream_t to order work on; NULL: library-owned stream;
                                 cudaStreamLegacy for the legacy default stream */
+  int32_t tile_height;       /* batch kernel tile shape: SIM_TILE_AUTO, SIM_TILE_TUNE, 8 or
+                                16 (64 x 8 tiles of 256 threads / 64 x 16 of 512); see
+                                sim_autotune.  Group members always use 16. */
+  int32_t reserved0;
 } sim_config;
+
+/* Tile shape choices of sim_config.tile_height. */
+enum {
+  SIM_TILE_AUTO = 0,    /* the shape the autotuner table holds for this configuration, else 16 */
+  SIM_TILE_TUNE = -1    /* as SIM_TILE_AUTO, but run sim_autotune first on a table miss */
+};
 
 typedef struct {
   int64_t frames_pushed;     /* frames accepted by sim_push_frame */
@@ -117,6 +127,8 @@ typedef struct {
   int32_t max_batch;         /* frames per device batch */
   int64_t pixel_substeps;    /* sum over committed frames of width * height * N */
   int64_t active_substeps;   /* sum over committed frames of (pixels simulated) * N */
+  int32_t tile_height;       /* tile height of the batch kernel (8 or 16) */
+  int32_t reserved0;
 } sim_stats;
 
 /* Kernel kinds for sim_kernel_time. */
@@ -207,6 +219,38 @@ const char* sim_last_cuda_error(void);
 
 /* Library version, "major.minor.patch". */
 const char* sim_version(void);
+
+/* ---- autotuner -------------------------------------------------------------
+ * The paper has no counterpart (it runs one configuration on one machine).
+ * The batch kernel comes in two tile shapes: 64 x 16 pixels per 512-thread
+ * block (two blocks per SM) and 64 x 8 per 256-thread block (four per SM).
+ * The smaller shape has twice the blocks for a frame of a given size - more
+ * parallelism for small frames, finer balance across SMs - at the price of
+ * a larger halo per pixel.  Which one is faster depends on the frame size,
+ * the mode and the substep count, so it is measured.
+ *
+ * sim_autotune runs the simulation kernel of a stream configured as *cfg in
+ * both shapes on `frames` (2..64) synthetic frames generated on the device
+ * (a moving sinusoidal texture with a constant flow of (3.0, -2.0) px per
+ * frame; frame and flow content do not depend on the shape), times each
+ * kernel launch with CUDA events, and records the faster shape in a
+ * process-wide table keyed by (width, height, pixel_format, mode, substeps,
+ * max_substeps, intensity, ref_mode, threshold maps present).  sim_create
+ * consults the table when cfg->tile_height is SIM_TILE_AUTO or SIM_TILE_TUNE.
+ * *tile_height_out (if not NULL) receives 8 or 16; us_out (if not NULL, 2
+ * doubles) the kernel time per frame in microseconds of shapes 16 and 8.
+ * Allocates two temporary simulators and the probe's frames on the current
+ * device and frees them before returning; blocks until done.  Errors:
+ * SIM_ERR_ARG (bad configuration or frames), SIM_ERR_OOM, SIM_ERR_CUDA. */
+int sim_autotune(const sim_config* cfg, int32_t frames, int32_t* tile_height_out,
+                 double* us_out);
+
+/* Write the autotuner table to a text file (one line per configuration:
+ * the key's nine fields, the chosen tile height, the two per-frame times),
+ * or merge such a file into the table (later lines win).  Return SIM_OK or
+ * SIM_ERR_ARG (NULL path, unreadable or malformed file: nothing merged). */
+int sim_autotune_save(const char* path);
+int sim_autotune_load(const char* path);
 
 /* ---- multi-stream group ---------------------------------------------------
  * Many independent camera streams of mixed sizes and settings advanced

@@ -1,0 +1,195 @@
+// Autotuner of the batch kernel's tile shape (sim_autotune): both shapes run
+// the same synthetic frames, the faster one is recorded per configuration in
+// a process-wide table that sim_create consults.  The paper has no
+// counterpart; the choice changes only how the work is launched, never the
+// events (both shapes compute the same integer arithmetic).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/evsim.h"
+#include "handle.h"
+#include "internal.h"
+
+namespace {
+
+using Key = std::tuple<int, int, int, int, int, int, int, int, int>;
+
+struct Entry {
+  int th;
+  double us16, us8;
+};
+
+std::mutex g_tune_mu;
+std::map<Key, Entry> g_table;
+
+Key key_of(const sim_config& c) {
+  // max_substeps matters only for adaptive N
+  return Key{c.width, c.height, c.pixel_format, c.mode, c.substeps,
+             c.substeps == 0 ? c.max_substeps : 0, c.intensity, c.ref_mode,
+             c.c_pos_map != nullptr ? 1 : 0};
+}
+
+// Probe frame j of a moving sinusoidal texture (the same content for both
+// shapes), and a constant flow of (3.0, -2.0) px per frame.
+__global__ void k_probe(unsigned char* frames, float2* flows, int W, int H, int ch, int F) {
+  const long long P = (long long)W * H;
+  const long long total = P * F;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / P);
+    const long long r = i - (long long)j * P;
+    const int y = (int)(r / W), x = (int)(r - (long long)y * W);
+    const float u = x - 3.0f * j, v = y + 2.0f * j;
+    const float a = 128.f + 70.f * __sinf(0.09f * u + 0.6f * __sinf(0.031f * v)) +
+                    40.f * __sinf(0.13f * v - 0.05f * u);
+    const int g = min(255, max(0, (int)a));
+    for (int c = 0; c < ch; ++c) frames[i * ch + c] = (unsigned char)min(255, g + 9 * c);
+    flows[i] = make_float2(3.0f, -2.0f);
+  }
+}
+
+int rc_of(cudaError_t e) { return evsim_rt::cuda_rc(e); }
+
+// Per-frame time (us) of the simulation kernel of a stream with tile height th.
+int time_shape(const sim_config& c, int th, int F, const unsigned char* frames,
+               const float2* flows, double* us) {
+  sim_config tc = c;
+  tc.tile_height = th;
+  tc.cuda_stream = nullptr;
+  tc.max_batch = F;
+  tc.event_capacity = std::min<long long>((long long)c.width * c.height * 2 * F, 1LL << 27);
+  sim_t* s = nullptr;
+  int rc = sim_create(&tc, &s);
+  if (rc) return rc;
+  const long long P = (long long)c.width * c.height;
+  const long long row = (long long)c.width * c.pixel_format;
+  std::vector<const void*> fr(F);
+  std::vector<const float*> fl(F);
+  std::vector<int64_t> t(F);
+  for (int j = 0; j < F; ++j) {
+    fr[j] = frames + (size_t)j * P * c.pixel_format;
+    fl[j] = (const float*)(flows + (size_t)j * P);
+    t[j] = 16667LL * j;
+  }
+  const int kind = c.mode == SIM_SPARSE ? SIM_K_SPARSE : SIM_K_DENSE;
+  // a warm-up batch, then the timed one (the same frames, continued in time).
+  // An event overflow only means the batch did not commit: its kernels ran
+  // in full and were timed.
+  auto ok = [](int r) { return r == SIM_OK || r == SIM_ERR_EVENT_OVERFLOW ? SIM_OK : r; };
+  rc = sim_push_frames(s, F, fr.data(), row, fl.data(), t.data(), SIM_DEVICE);
+  if (!rc) rc = ok(sim_sync(s));
+  if (!rc) rc = sim_set_profiling(s, 1);
+  for (int j = 0; j < F && !rc; ++j) t[j] += 16667LL * F;
+  if (!rc) rc = sim_push_frames(s, F - 1, fr.data() + 1, row, fl.data() + 1, t.data() + 1,
+                                SIM_DEVICE);
+  if (!rc) rc = ok(sim_sync(s));
+  double ms = 0;
+  int64_t n = 0;
+  if (!rc) rc = sim_kernel_time(s, kind, &ms, &n, 1);
+  const int rd = sim_destroy(s);
+  if (!rc) rc = rd;
+  if (!rc && n < 1) rc = SIM_ERR_STATE;
+  if (!rc) *us = ms * 1e3 / (F - 1);
+  return rc;
+}
+
+}  // namespace
+
+bool evsim_rt::tuned_tile_height(const sim_config& c, int* th) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_table.find(key_of(c));
+  if (it == g_table.end()) return false;
+  *th = it->second.th;
+  return true;
+}
+
+extern "C" {
+
+int sim_autotune(const sim_config* cfg, int32_t frames, int32_t* tile_height_out,
+                 double* us_out) {
+  if (!cfg || frames < 2 || frames > 64) return SIM_ERR_ARG;
+  sim_config c = *cfg;
+  if (c.width < 1 || c.height < 1 || c.width > SIM_MAX_DIM || c.height > SIM_MAX_DIM)
+    return SIM_ERR_ARG;
+  if (c.pixel_format != SIM_LUMA8 && c.pixel_format != SIM_RGB8) return SIM_ERR_ARG;
+  const long long P = (long long)c.width * c.height;
+  unsigned char* d_frames = nullptr;
+  float2* d_flows = nullptr;
+  cudaError_t e = cudaMalloc(&d_frames, (size_t)P * c.pixel_format * frames);
+  if (e == cudaSuccess) e = cudaMalloc(&d_flows, (size_t)P * sizeof(float2) * frames);
+  if (e == cudaSuccess) {
+    const long long total = P * frames;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 8192);
+    k_probe<<<grid, 256>>>(d_frames, d_flows, c.width, c.height, c.pixel_format, frames);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  int rc = e == cudaSuccess ? SIM_OK : (e == cudaErrorMemoryAllocation ? SIM_ERR_OOM : rc_of(e));
+  double us16 = 0, us8 = 0;
+  if (!rc) rc = time_shape(c, 16, frames, d_frames, d_flows, &us16);
+  if (!rc) rc = time_shape(c, 8, frames, d_frames, d_flows, &us8);
+  cudaFree(d_frames);
+  cudaFree(d_flows);
+  if (rc) return rc;
+  const int th = us8 < us16 ? 8 : 16;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_table[key_of(c)] = Entry{th, us16, us8};
+  }
+  if (tile_height_out) *tile_height_out = th;
+  if (us_out) {
+    us_out[0] = us16;
+    us_out[1] = us8;
+  }
+  return SIM_OK;
+}
+
+int sim_autotune_save(const char* path) {
+  if (!path) return SIM_ERR_ARG;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return SIM_ERR_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (const auto& kv : g_table) {
+    const Key& k = kv.first;
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %.3f %.3f\n", std::get<0>(k), std::get<1>(k),
+                 std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k),
+                 std::get<7>(k), std::get<8>(k), kv.second.th, kv.second.us16, kv.second.us8);
+  }
+  const bool ok = std::fclose(f) == 0;
+  return ok ? SIM_OK : SIM_ERR_ARG;
+}
+
+int sim_autotune_load(const char* path) {
+  if (!path) return SIM_ERR_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return SIM_ERR_ARG;
+  std::map<Key, Entry> add;
+  char line[512];
+  bool bad = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    int v[10];
+    double a = 0, b = 0;
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %lf %lf", &v[0], &v[1], &v[2], &v[3],
+                    &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &a, &b) != 12 ||
+        (v[9] != 8 && v[9] != 16)) {
+      bad = true;
+      break;
+    }
+    add[Key{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]}] = Entry{v[9], a, b};
+  }
+  std::fclose(f);
+  if (bad) return SIM_ERR_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (const auto& kv : add) g_table[kv.first] = kv.second;
+  return SIM_OK;
+}
+
+}  // extern "C"

@@ -260,6 +260,7 @@ sim_config member_config(const simb_t* g, const sim_config& c) {
   sim_config mc = c;
   mc.cuda_stream = g->stream;
   mc.max_batch = g->fmax;
+  mc.tile_height = 16;  // the group's tile kernel has the 64 x 16 shape only
   return mc;
 }
 

@@ -24,6 +24,7 @@ struct sim_s {
   long long P = 0;
   int n_max = 0;
   int tiles_x = 0, tiles_y = 0;
+  int tile_h = 16;             // batch kernel tile height (8 or 16)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
@@ -88,5 +89,7 @@ int read_ctl(sim_t* s, Ctl* c);
 int recover(sim_t* s, Ctl* c);
 // Device bytes sim_create allocates for a configuration (before host staging grows).
 long long state_bytes(const sim_config& c);
+// The autotuner's tile height for a configuration, if its table has one.
+bool tuned_tile_height(const sim_config& c, int* th);
 
 }  // namespace evsim_rt

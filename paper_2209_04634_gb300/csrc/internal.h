@@ -8,7 +8,9 @@
 namespace evsim {
 
 // Tile of the simulation kernel (dense and sparse): TW x TH pixels, NTD
-// threads, up to two simulated pixels per thread.
+// threads, up to two simulated pixels per thread.  The batch kernel also
+// comes in a TW x 8 shape (256 threads), chosen per stream by the
+// autotuner; multi-stream group launches use TW x TH.
 constexpr int TW = 64;
 constexpr int TH = 16;
 constexpr int NTD = 512;
@@ -100,12 +102,14 @@ struct Seg {
 // Everything the kernels need about one stream (fixed for its lifetime).
 struct SimParams {
   int W, H, ch;
-  int tiles_x, tiles_y;
+  int tiles_x, tiles_y;          // tiles of TW x tile_h pixels
   int mode, ref_mode, intensity;
   int n_fixed, n_max;
   int cp, cn, cact;
   int bmax;                     // frames per batch the segment table holds
   int stage_chunk;              // staging chunk per warp of the batch kernel (0: exact)
+  int tile_h;                   // batch kernel tile height: 16 (512 threads) or 8 (256)
+  int pad_tile;
   const unsigned short* cpmap;
   const unsigned short* cnmap;
   const int* lut;               // 256 Q16 entries (device)

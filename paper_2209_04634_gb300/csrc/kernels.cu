@@ -590,7 +590,7 @@ __device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_l
 // pixels' tile coordinates, `nk_at` their columns in the per-substep record.
 // DENSE: the two pixels are columns lane, lane + 32 of tile row `warp`, and the
 // row's segment is published from the loop.
-template <bool RESET, bool WIDE, bool FAST, bool DENSE>
+template <bool RESET, bool WIDE, bool FAST, bool DENSE, int TH_ = 16>
 __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
                                               unsigned mN, int tx0, int ty0, unsigned b0, unsigned b1,
                                               const FrameRef& prv, const FrameDesc& cur,
@@ -599,6 +599,8 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
                                               const int (&Fx)[2], const int (&Fy)[2],
                                               int (&R)[2], const int (&Cp)[2],
                                               const int (&Cn)[2], WarpStage* ws) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)TH; (void)NTD; (void)TP; (void)SH;
   const int warp = threadIdx.x >> 5;
   int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
@@ -736,7 +738,7 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const int* sw
 // non-zero, into the tile's row masks: rowm[(k TH + row) 4 + {0,1}] event
 // bits of columns 0-31 / 32-63, {2,3} polarity bits; rows in which a pixel
 // crossed two or more thresholds are flagged in smulti[k] (bit = row).
-template <bool RESET, bool WIDE, int NPX>
+template <bool RESET, bool WIDE, int NPX, int TH_>
 __device__ __forceinline__ void sparse_substeps(const int* swk, int N, unsigned mN, unsigned b0,
                                                 unsigned b1, short* snk, unsigned* rowm,
                                                 unsigned* smulti, const int (&lx)[2],
@@ -744,6 +746,8 @@ __device__ __forceinline__ void sparse_substeps(const int* swk, int N, unsigned 
                                                 const int (&Fx)[2], const int (&Fy)[2],
                                                 int (&R)[2], const int (&Cp)[2],
                                                 const int (&Cn)[2]) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)TH; (void)NTD; (void)TP; (void)SH;
   int px[NPX], py[NPX], ax[NPX], ay[NPX], qx[NPX], rx[NPX], qy[NPX], ry[NPX];
 #pragma unroll
   for (int j = 0; j < NPX; ++j) {
@@ -1139,7 +1143,8 @@ struct BatchLayout {
   unsigned short* sCn;
 };
 
-__host__ __device__ inline size_t batch_smem_bytes(int n_max, int ch, bool sparse) {
+__host__ __device__ inline size_t batch_smem_bytes(int n_max, int ch, bool sparse, int th) {
+  const int TP = TW * th, SH = th + 2 * HMAX;
   size_t b = (size_t)2 * TP * sizeof(float2);
   b += (size_t)(2 * SH * SW + 256 + (sparse ? TP : 0) + 4 * n_max) * 4;
   b += (size_t)2 * SH * SW * ch;
@@ -1147,8 +1152,10 @@ __host__ __device__ inline size_t batch_smem_bytes(int n_max, int ch, bool spars
   return b;
 }
 
-template <bool SPARSE>
+template <bool SPARSE, int TH_>
 __device__ __forceinline__ BatchLayout batch_layout(unsigned char* base, int nmax, int ch) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)TH; (void)NTD; (void)TP; (void)SH;
   BatchLayout L;
   L.sflow = (float2*)base;
   L.sLa = (int*)(L.sflow + 2 * TP);
@@ -1169,8 +1176,11 @@ __device__ __forceinline__ BatchLayout batch_layout(unsigned char* base, int nma
 // ty0 + TH + HMAX - 1 and columns tx0 - HMAX .. tx0 + TW + HMAX - 1, clipped
 // to the image) into raw, row r of the window at raw + r * SW * ch.  Window
 // rows and columns outside the image are never read.
+template <int TH_>
 __device__ __forceinline__ void stage_raw(unsigned char* raw, const FrameRef& f, int W, int H,
                                           int tx0, int ty0) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)TH; (void)NTD; (void)TP; (void)SH;
   const int ch = f.ch, RW = SW * ch;
   const int r0 = max(0, HMAX - ty0), r1 = min(SH, H - ty0 + HMAX);
   const int cx0 = max(0, tx0 - HMAX), cx1 = min(W, tx0 + TW + HMAX);
@@ -1198,8 +1208,11 @@ __device__ __forceinline__ void stage_raw(unsigned char* raw, const FrameRef& f,
 
 // Stage the flow of the tile's pixels (tile pixel index ly * TW + lx) into sf;
 // pixels outside the image are not written.
+template <int TH_>
 __device__ __forceinline__ void stage_flow(float2* sf, const float2* flow, int W, int H, int tx0,
                                            int ty0) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)TH; (void)NTD; (void)TP; (void)SH;
   const bool al = ((unsigned long long)flow & 7) == 0;
   const unsigned d0 = smem_addr(sf);
 #pragma unroll
@@ -1224,9 +1237,12 @@ __device__ __forceinline__ int raw_luma(const unsigned char* raw, int ch, int rr
 
 // Replicate-padded halo of log values with reach (hx, hy) from a staged
 // frame (same region and layout as fill_halo): one warp per halo row.
+template <int TH_>
 __device__ __forceinline__ void fill_halo_raw(int* dst, const int* slut, const unsigned char* raw,
                                               int ch, int W, int H, int tx0, int ty0, int hx,
                                               int hy) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)TH; (void)NTD; (void)TP; (void)SH;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncols = TW + 2 * hx, nrows = TH + 2 * hy;
   const int RW = SW * ch;
@@ -1261,8 +1277,10 @@ __device__ __forceinline__ void substep_tables(const SimParams& p, unsigned long
   }
 }
 
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_>
 __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b, int tile) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)TH; (void)NTD; (void)TP; (void)SH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy;
@@ -1279,7 +1297,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max, ch = p.ch, RW = SW * ch;
-  const BatchLayout L = batch_layout<SPARSE>(smem_raw, nmax, ch);
+  const BatchLayout L = batch_layout<SPARSE, TH_>(smem_raw, nmax, ch);
   const int tcx = tile % p.tiles_x, tcy = tile / p.tiles_x;
   const int tx0 = tcx * TW, ty0 = tcy * TH;
   const int W = p.W, H = p.H, count = b.count;
@@ -1327,9 +1345,9 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   {
     const FrameRef ring{ringp, (long long)W, 1};
     const FrameDesc d0 = s_desc[0];
-    stage_raw(L.raw, ring, W, H, tx0, ty0);
-    stage_raw(L.raw + SH * RW, FrameRef{d0.frame, d0.pitch, ch}, W, H, tx0, ty0);
-    stage_flow(L.sflow, d0.flow, W, H, tx0, ty0);
+    stage_raw<TH_>(L.raw, ring, W, H, tx0, ty0);
+    stage_raw<TH_>(L.raw + SH * RW, FrameRef{d0.frame, d0.pitch, ch}, W, H, tx0, ty0);
+    stage_flow<TH_>(L.sflow, d0.flow, W, H, tx0, ty0);
     cp_async_commit();
     if (tid < 64) substep_tables(p, s_mf[0], t_first, d0.t_rel, L.swk, L.stk, &s_N[0], &s_mN[0]);
     cp_async_wait_all();
@@ -1459,11 +1477,11 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       hfx = max(hfx, hx);
       hfy = max(hfy, hy);
       if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
-        fill_halo_raw(pb, L.slut, rawp, chp, W, H, tx0, ty0, hfx, hfy);
+        fill_halo_raw<TH_>(pb, L.slut, rawp, chp, W, H, tx0, ty0, hfx, hfy);
         phx = hfx;
         phy = hfy;
       }
-      fill_halo_raw(cb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy);
+      fill_halo_raw<TH_>(cb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy);
     }
     __syncthreads();
     if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
@@ -1473,8 +1491,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     // substep tables
     if (fi + 1 < count) {
       const FrameDesc nd = s_desc[(fi + 1) & 3];
-      stage_raw(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
-      stage_flow(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
+      stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
+      stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
       if (fi + 2 < count && tid < 2) {
         // descriptors are 32-byte, 16-byte aligned records
         cp_async16(smem_addr(&s_desc[(fi + 2) & 3]) + 16u * tid,
@@ -1504,19 +1522,19 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     } else if (maskpub) {  // warp-uniform: one pixel per thread when A <= NTD
       if (A <= NTD) {
         if (warp * 32 < A)
-          sparse_substeps<RESET, WIDE, 1>(V.swk, N, mN, b0, b1, L.snk, rowm, s_multi, lx, ly, act,
+          sparse_substeps<RESET, WIDE, 1, TH_>(V.swk, N, mN, b0, b1, L.snk, rowm, s_multi, lx, ly, act,
                                           Fx, Fy, R, Cp, Cn);
       } else {
-        sparse_substeps<RESET, WIDE, 2>(V.swk, N, mN, b0, b1, L.snk, rowm, s_multi, lx, ly, act,
+        sparse_substeps<RESET, WIDE, 2, TH_>(V.swk, N, mN, b0, b1, L.snk, rowm, s_multi, lx, ly, act,
                                         Fx, Fy, R, Cp, Cn);
       }
     } else if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
       if (fast)
-        tile_substeps<RESET, WIDE, true, !SPARSE>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
+        tile_substeps<RESET, WIDE, true, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
                                                   &s_stage[warp]);
       else
-        tile_substeps<RESET, WIDE, false, !SPARSE>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
+        tile_substeps<RESET, WIDE, false, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
                                                    lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
                                                    &s_stage[warp]);
     }
@@ -1618,9 +1636,9 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 // One stream's batch: one block per tile carries the tile through every
 // frame of the batch, its inputs staged a frame ahead (blocks never wait for
 // one another).
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
-__global__ void __launch_bounds__(NTD, 2) k_tile(SimParams p, BatchArg b) {
-  tile_batch<RESET, MAPS, WIDE, SPARSE>(p, b, blockIdx.x);
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_>
+__global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile(SimParams p, BatchArg b) {
+  tile_batch<RESET, MAPS, WIDE, SPARSE, TH_>(p, b, blockIdx.x);
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
@@ -2161,9 +2179,12 @@ __global__ void __launch_bounds__(NT) k_drain(GroupArg g, DrainArg d) {
 
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
 void set_tile_attr(int n_max) {
-  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE>,
+  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 16>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)batch_smem_bytes(n_max, 3, SPARSE));
+                       (int)batch_smem_bytes(n_max, 3, SPARSE, 16));
+  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 8>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batch_smem_bytes(n_max, 3, SPARSE, 8));
 }
 
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
@@ -2189,14 +2210,14 @@ cudaError_t launch_tile_multi_mode(const GroupArg& g, int cls, const ActiveTile*
   return cudaGetLastError();
 }
 
-template <bool SPARSE>
-cudaError_t launch_tile_mode(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+template <bool SPARSE, int TH_>
+cudaError_t launch_tile_shape(const SimParams& p, const BatchArg& b, cudaStream_t st) {
   const int grid = p.tiles_x * p.tiles_y;
-  const size_t sm = batch_smem_bytes(p.n_max, p.ch, SPARSE);
+  const size_t sm = batch_smem_bytes(p.n_max, p.ch, SPARSE, TH_);
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_TILE(R, M, Wd) k_tile<R, M, Wd, SPARSE><<<grid, NTD, sm, st>>>(p, b)
+#define EVSIM_TILE(R, M, Wd) k_tile<R, M, Wd, SPARSE, TH_><<<grid, 32 * TH_, sm, st>>>(p, b)
   if (!reset && !maps && !wide) EVSIM_TILE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_TILE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_TILE(false, false, true);
@@ -2207,6 +2228,12 @@ cudaError_t launch_tile_mode(const SimParams& p, const BatchArg& b, cudaStream_t
   else EVSIM_TILE(true, true, true);
 #undef EVSIM_TILE
   return cudaGetLastError();
+}
+
+template <bool SPARSE>
+cudaError_t launch_tile_mode(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  if (p.tile_h == 8) return launch_tile_shape<SPARSE, 8>(p, b, st);
+  return launch_tile_shape<SPARSE, 16>(p, b, st);
 }
 
 }  // namespace

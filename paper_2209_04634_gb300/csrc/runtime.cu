@@ -57,7 +57,7 @@ long long state_bytes(const sim_config& c) {
   if (c.ref_mode == SIM_REF_ACCUM) b += 8 * z.P;
   b += (z.stage + z.cap) * (long long)sizeof(Ev);       // staging + events
   b += z.seg_cap * (long long)sizeof(evsim::Seg) + 8 * z.ochunks;
-  b += 8LL * z.tiles_x * ((c.height + evsim::TH - 1) / evsim::TH);  // tile progress words
+  b += 8LL * z.tiles_x * ((c.height + 7) / 8);                     // tile progress words
   b += (long long)z.bmax * sizeof(evsim::FrameDesc);
   b += z.P * c.pixel_format;                             // host-frame staging (one frame)
   if (c.c_pos_map) b += 4 * z.P;
@@ -106,6 +106,7 @@ evsim::SimParams make_params(const sim_t* s) {
   p.ch = s->ch;
   p.tiles_x = s->tiles_x;
   p.tiles_y = s->tiles_y;
+  p.tile_h = s->tile_h;
   p.mode = s->cfg.mode;
   p.ref_mode = s->cfg.ref_mode;
   p.intensity = s->cfg.intensity;
@@ -324,6 +325,9 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   if (c.substeps == 0 && (c.max_substeps < 1 || c.max_substeps > SIM_MAX_SUBSTEPS)) return SIM_ERR_ARG;
   if (c.event_capacity < 0 || c.event_capacity > evsim::MAX_EVENTS) return SIM_ERR_ARG;
   if (c.max_batch < 0 || c.max_batch > SIM_MAX_BATCH) return SIM_ERR_ARG;
+  if (c.tile_height != SIM_TILE_AUTO && c.tile_height != SIM_TILE_TUNE && c.tile_height != 8 &&
+      c.tile_height != 16)
+    return SIM_ERR_ARG;
 
   int lut[256];
   build_lut(c.intensity, lut);
@@ -344,6 +348,20 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SIM_ERR_NO_DEVICE;
 
+  // tile shape: fixed, or the autotuner's choice for this configuration
+  int th = c.tile_height;
+  if (th != 8 && th != 16) {
+    if (!tuned_tile_height(c, &th)) {
+      th = 16;
+      if (c.tile_height == SIM_TILE_TUNE) {
+        int32_t t = 16;
+        const int rc = sim_autotune(&c, 8, &t, nullptr);
+        if (rc) return rc;
+        th = t;
+      }
+    }
+  }
+
   sim_t* s = new (std::nothrow) sim_t();
   if (!s) return SIM_ERR_OOM;
   s->cfg = c;
@@ -355,7 +373,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   s->P = P;
   s->n_max = c.substeps > 0 ? c.substeps : c.max_substeps;
   s->tiles_x = (c.width + evsim::TW - 1) / evsim::TW;
-  s->tiles_y = (c.height + evsim::TH - 1) / evsim::TH;
+  s->tile_h = th;
+  s->tiles_y = (c.height + th - 1) / th;
   cudaGetDevice(&s->device);
   s->sms = std::max(1, evsim::device_sm_count());
 
@@ -569,6 +588,7 @@ int sim_get_stats(sim_t* s, sim_stats* st) {
   st->max_batch = s->bmax;
   st->pixel_substeps = c.work_px;
   st->active_substeps = c.work_active;
+  st->tile_height = s->tile_h;
   return SIM_OK;
 }
 

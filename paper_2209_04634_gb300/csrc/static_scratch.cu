@@ -171,6 +171,7 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   p.ch = c.pixel_format;
   p.tiles_x = tiles_x;
   p.tiles_y = tiles_y;
+  p.tile_h = evsim::TH;
   p.mode = c.mode;
   p.ref_mode = c.ref_mode;
   p.intensity = c.intensity;

@@ -32,6 +32,7 @@ SIM_REF_ACCUM, SIM_REF_RESET = 0, 1
 SIM_HOST, SIM_DEVICE = 0, 1
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 SIM_MAX_BATCH = 1024
+SIM_TILE_AUTO, SIM_TILE_TUNE = 0, -1
 SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
 KERNEL_NAMES = ["init", "flowmax", "dense", "mask", "sparse", "order", "copy"]
 
@@ -48,6 +49,7 @@ class sim_config(ctypes.Structure):
         ("c_act_q16", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("c_pos_map", ctypes.c_void_p), ("c_neg_map", ctypes.c_void_p),
         ("event_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+        ("tile_height", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -59,6 +61,7 @@ class sim_stats(ctypes.Structure):
         ("flow_clamped", ctypes.c_int64), ("last_substeps", ctypes.c_int32),
         ("max_batch", ctypes.c_int32), ("pixel_substeps", ctypes.c_int64),
         ("active_substeps", ctypes.c_int64),
+        ("tile_height", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -114,6 +117,10 @@ SIGNATURES = [
     ("sim_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("sim_version", ctypes.c_char_p, []),
     ("sim_last_cuda_error", ctypes.c_char_p, []),
+    ("sim_autotune", ctypes.c_int, [ctypes.POINTER(sim_config), _I32, ctypes.POINTER(_I32),
+                                    ctypes.POINTER(ctypes.c_double)]),
+    ("sim_autotune_save", ctypes.c_int, [ctypes.c_char_p]),
+    ("sim_autotune_load", ctypes.c_int, [ctypes.c_char_p]),
     ("simb_config_default", ctypes.c_int, [ctypes.POINTER(simb_config)]),
     ("simb_create", ctypes.c_int, [ctypes.POINTER(simb_config), ctypes.POINTER(_VP)]),
     ("simb_state_bytes", ctypes.c_int, [_VP, ctypes.POINTER(sim_config), ctypes.POINTER(_I64)]),
@@ -210,7 +217,7 @@ class Simulator:
                  intensity: int = SIM_LOG, ref_mode: int = SIM_REF_ACCUM,
                  c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
                  c_pos_map=None, c_neg_map=None, event_capacity: int = 0, stream=None,
-                 max_batch: int = 0):
+                 max_batch: int = 0, tile_height: int = SIM_TILE_AUTO):
         lib = load()
         cfg = sim_config()
         check(lib.sim_config_default(ctypes.byref(cfg), width, height), "sim_config_default")
@@ -232,6 +239,7 @@ class Simulator:
             cfg.c_neg_map = cn.ctypes.data
         cfg.event_capacity = event_capacity
         cfg.max_batch = max_batch
+        cfg.tile_height = tile_height
         if stream is not None:
             handle = int(getattr(stream, "cuda_stream", stream))
             # handle 0 is the legacy default stream (torch's default stream):
@@ -349,7 +357,8 @@ def make_config(width: int, height: int, *, pixel_format: int = SIM_LUMA8,
                 mode: int = SIM_DENSE, substeps: int = 8, max_substeps: int = 16,
                 intensity: int = SIM_LOG, ref_mode: int = SIM_REF_ACCUM,
                 c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
-                c_pos_map=None, c_neg_map=None, event_capacity: int = 0):
+                c_pos_map=None, c_neg_map=None, event_capacity: int = 0,
+                tile_height: int = SIM_TILE_AUTO):
     """A sim_config (plus the threshold-map arrays it points to, which must
     outlive the call that reads it)."""
     cfg = sim_config()
@@ -371,7 +380,27 @@ def make_config(width: int, height: int, *, pixel_format: int = SIM_LUMA8,
         cfg.c_pos_map = cp.ctypes.data
         cfg.c_neg_map = cn.ctypes.data
     cfg.event_capacity = event_capacity
+    cfg.tile_height = tile_height
     return cfg, keep
+
+
+def autotune(width: int, height: int, frames: int = 8, **kw) -> tuple[int, float, float]:
+    """sim_autotune for a configuration (make_config keywords): returns the
+    chosen tile height and the per-frame kernel times (us) of heights 16 and 8."""
+    cfg, keep = make_config(width, height, **kw)
+    th = ctypes.c_int32(0)
+    us = (ctypes.c_double * 2)()
+    check(load().sim_autotune(ctypes.byref(cfg), frames, ctypes.byref(th), us), "sim_autotune")
+    del keep
+    return int(th.value), float(us[0]), float(us[1])
+
+
+def autotune_save(path: str) -> None:
+    check(load().sim_autotune_save(path.encode()), "sim_autotune_save")
+
+
+def autotune_load(path: str) -> None:
+    check(load().sim_autotune_load(path.encode()), "sim_autotune_load")
 
 
 class Group:

@@ -27,7 +27,7 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
             pop_every: int = 1, intensity=evsim.SIM_LOG, ref_mode=evsim.SIM_REF_ACCUM,
             c_act_q16: int = -1, substeps=None, c_pos_q16=None, c_neg_q16=None,
             use_maps=True, event_capacity: int = 0, stream=None, batch: int = 0,
-            max_batch: int = 0) -> dict:
+            max_batch: int = 0, tile_height: int = 0) -> dict:
     """Push every frame of seq through the CUDA library; return the events,
     the committed reference and per-frame statistics."""
     import torch
@@ -45,6 +45,7 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
     if stream is not None:
         kw["stream"] = stream
     kw["max_batch"] = max_batch
+    kw["tile_height"] = tile_height
     sim = evsim.simulator_for(seq, mode, **kw)
     if batch:
         return _gpu_run_batched(sim, seq, batch, device_inputs, ref_mode)

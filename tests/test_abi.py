@@ -105,3 +105,29 @@ def test_create_without_a_device_fails_cleanly(lib):
     c = _cfg(lib)
     h = ctypes.c_void_p()
     assert lib.sim_create(ctypes.byref(c), ctypes.byref(h)) == evsim.SIM_ERR_NO_DEVICE
+
+
+def test_autotune_arguments_and_table_file(lib, tmp_path):
+    """Argument errors of the autotuner and its table file round trip (no
+    kernel runs)."""
+    cfg, _ = evsim.make_config(64, 32)
+    assert lib.sim_autotune(ctypes.byref(cfg), 1, None, None) == evsim.SIM_ERR_ARG
+    assert lib.sim_autotune(ctypes.byref(cfg), 65, None, None) == evsim.SIM_ERR_ARG
+    assert lib.sim_autotune(None, 8, None, None) == evsim.SIM_ERR_ARG
+    cfg.tile_height = 5
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)) == evsim.SIM_ERR_ARG
+    src = tmp_path / "tune.txt"
+    src.write_text("64 32 1 0 8 0 0 0 0 8 10.000 9.000\n"
+                   "640 480 1 1 0 8 0 0 1 16 900.000 950.000\n")
+    assert lib.sim_autotune_load(str(src).encode()) == evsim.SIM_OK
+    out = tmp_path / "out.txt"
+    assert lib.sim_autotune_save(str(out).encode()) == evsim.SIM_OK
+    text = out.read_text()
+    assert "64 32 1 0 8 0 0 0 0 8 10.000 9.000" in text
+    assert "640 480 1 1 0 8 0 0 1 16 900.000 950.000" in text
+    bad = tmp_path / "bad.txt"
+    bad.write_text("64 32 1 0 8 0 0 0 0 12 1 1\n")  # tile height must be 8 or 16
+    assert lib.sim_autotune_load(str(bad).encode()) == evsim.SIM_ERR_ARG
+    assert lib.sim_autotune_load(str(tmp_path / "missing.txt").encode()) == evsim.SIM_ERR_ARG
+    assert lib.sim_autotune_load(None) == evsim.SIM_ERR_ARG

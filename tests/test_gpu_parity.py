@@ -141,19 +141,21 @@ def test_mode_matrix(intensity, ref, mode):
 
 
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 37), (37, 1), (17, 65), (15, 63), (16, 64),
-                                 (33, 130), (3, 200), (70, 9)])
+                                 (33, 130), (3, 200), (70, 9), (9, 70), (8, 64)])
 @pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
-def test_ragged_shapes(H, W, mode):
+@pytest.mark.parametrize("th", [16, 8])
+def test_ragged_shapes(H, W, mode, th):
     seq = random_seq(H, W, F=4, seed=H * 1000 + W)
-    check_parity(seq, mode, f"{W}x{H}", use_maps=False)
+    check_parity(seq, mode, f"{W}x{H} tiles 64x{th}", use_maps=False, tile_height=th)
 
 
 @pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
 @pytest.mark.parametrize("amp", [15.5, 40.0])
-def test_large_flow_beyond_the_shared_halo(mode, amp):
+@pytest.mark.parametrize("th", [16, 8])
+def test_large_flow_beyond_the_shared_halo(mode, amp, th):
     """Flows beyond the shared-memory halo take the global-memory taps."""
     seq = random_seq(60, 150, F=3, flow_amp=amp, seed=int(amp))
-    check_parity(seq, mode, f"flow amplitude {amp}", use_maps=False)
+    check_parity(seq, mode, f"flow amplitude {amp}", use_maps=False, tile_height=th)
 
 
 def test_mixed_tiles_small_and_large_flow():
@@ -164,7 +166,8 @@ def test_mixed_tiles_small_and_large_flow():
 
 @pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
 @pytest.mark.parametrize("batch", [0, 3])
-def test_rows_of_multi_crossings(mode, batch):
+@pytest.mark.parametrize("th", [16, 8])
+def test_rows_of_multi_crossings(mode, batch, th):
     """Pixels that cross several thresholds in one substep: whole rows of
     them (rows of 16 or more events, which dense tiles publish as per-pixel
     counts) and a single such pixel in a row (its events are staged), both in
@@ -180,12 +183,13 @@ def test_rows_of_multi_crossings(mode, batch):
     t = np.arange(F, dtype=np.int64) * 10000
     seq = synth.Sequence("multi", fr, flows, t, 1, 8, 0.2, 0.2)
     if batch:
-        g = gpu_run(seq, mode, use_maps=False, substeps=1, batch=batch)
+        g = gpu_run(seq, mode, use_maps=False, substeps=1, batch=batch, tile_height=th)
         o = oracle_run(seq, mode, use_maps=False, substeps=1)
         assert_same_events(g["events"], o["events"], "multi-crossing rows (batched)")
         assert np.array_equal(g["R"], o["R"])
     else:
-        g, o = check_parity(seq, mode, "multi-crossing rows", use_maps=False, substeps=1)
+        g, o = check_parity(seq, mode, "multi-crossing rows", use_maps=False, substeps=1,
+                            tile_height=th)
     assert o["ev_per_frame"][1] >= 12 * H * W
 
 
@@ -396,4 +400,33 @@ def test_overflow_reported_by_pop_keeps_committed_events():
     first = sim.pop()
     assert len(first) == per[1]
     assert_same_events(first, o["events"][:per[1]], "committed before the overflow")
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
+def test_tile_shapes_agree_on_the_workloads(mode):
+    """Both tile shapes of the batch kernel give the oracle's events on heads of
+    the 640x480 and 1280x720 workloads, pushed as one batch."""
+    for seq in (synth.warped_texture(frames=6), synth.moving_rectangles(frames=4)):
+        o = oracle_run(seq, mode)
+        for th in (16, 8):
+            g = gpu_run(seq, mode, batch=seq.frames.shape[0], tile_height=th)
+            assert g["stats"].tile_height == th
+            assert_same_events(g["events"], o["events"], f"{seq.name} tiles 64x{th}")
+            assert np.array_equal(g["R"], o["R"])
+
+
+def test_autotune_chooses_a_shape_that_sim_create_uses():
+    th, us16, us8 = evsim.autotune(240, 180, frames=6, substeps=0, max_substeps=8)
+    assert th in (8, 16) and us16 > 0 and us8 > 0
+    assert th == (8 if us8 < us16 else 16)
+    sim = evsim.Simulator(240, 180, substeps=0, max_substeps=8)  # SIM_TILE_AUTO
+    assert sim.stats().tile_height == th
+    sim.close()
+    sim = evsim.Simulator(240, 180, substeps=0, max_substeps=8, tile_height=16)
+    assert sim.stats().tile_height == 16
+    sim.close()
+    # a configuration the table does not hold: tuned at create (SIM_TILE_TUNE)
+    sim = evsim.Simulator(200, 100, substeps=3, tile_height=evsim.SIM_TILE_TUNE)
+    assert sim.stats().tile_height in (8, 16)
     sim.close()
