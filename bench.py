@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=50)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=12.0)
+    ap.add_argument("--tile-height", type=int, default=0, choices=[0, 8, 16],
+                    help="batch kernel tile height; 0: the library's autotuner chooses")
     return ap.parse_args()
 
 
@@ -143,12 +145,12 @@ class ClockSampler:
 
 
 def kernel_source_digest() -> str:
+    """Digest of the kernel sources (kernels.cu and the structures they share)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2209_04634_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".h", ".cuh")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(f.read())
+    for name in ("internal.h", "kernels.cu"):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -235,10 +237,17 @@ def run_ours(args, ws, rank, local):
     # the same configuration, before the timed region); the simulators take it
     tune = {}
     for m, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
-        th, us16, us8 = evsim.autotune(W, H, frames=8, **evsim.seq_options(seq, mode=m))
-        tune[name] = {"tile_height": th, "probe_us_per_frame_64x16": us16,
-                      "probe_us_per_frame_64x8": us8}
-    sims = {m: evsim.simulator_for(seq, m, event_capacity=cap, stream=stream)
+        if args.tile_height:
+            tune[name] = {"tile_height": args.tile_height, "fixed": True}
+            continue
+        # tuned on a sample of this stream: its first 16 frames
+        th, us16, us8 = evsim.autotune_sample(W, H, frames[:16], flows[:16], seq.t_us[:16],
+                                              **evsim.seq_options(seq, mode=m))
+        tune[name] = {"tile_height": th, "sample": "first 16 frames",
+                      "us_per_frame_64x16": us16, "us_per_frame_64x8": us8}
+    sims = {m: evsim.simulator_for(seq, m, event_capacity=cap, stream=stream,
+                                   tile_height=tune["dense" if m == evsim.SIM_DENSE
+                                                    else "sparse"]["tile_height"])
             for m in (evsim.SIM_DENSE, evsim.SIM_SPARSE)}
     for m, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
         assert sims[m].stats().tile_height == tune[name]["tile_height"]
@@ -374,7 +383,7 @@ def roofline_dense(seq, ktimes, dense_units, tile_h):
     hbm_bytes = (F - 1) * 9 * P + 8 * P + (4 * P if seq.cpos_map is not None else 0)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm = hbm_bytes / avg_s / 1e9
-    traffic, _ = committed_traffic("dense")
+    traffic, _ = committed_traffic(f"dense_64x{tile_h}")
     return {"bound": "alu",
             "kernel": f"k_tile<dense>, 64x{tile_h} tiles (one launch per 99-frame batch)",
             "achieved": alu, "peak": alu_peak, "unit": "Tops/s (32-bit integer lane ops)",

@@ -230,7 +230,8 @@ const char* sim_version(void);
  * the mode and the substep count, so it is measured.
  *
  * sim_autotune runs the simulation kernel of a stream configured as *cfg in
- * both shapes on `frames` (2..64) synthetic frames generated on the device
+ * both shapes on `frames` (2..64) synthetic frames (after a first frame)
+ * generated on the device
  * (a moving sinusoidal texture with a constant flow of (3.0, -2.0) px per
  * frame; frame and flow content do not depend on the shape), times each
  * kernel launch with CUDA events, and records the faster shape in a
@@ -244,6 +245,19 @@ const char* sim_version(void);
  * SIM_ERR_ARG (bad configuration or frames), SIM_ERR_OOM, SIM_ERR_CUDA. */
 int sim_autotune(const sim_config* cfg, int32_t frames, int32_t* tile_height_out,
                  double* us_out);
+
+/* As sim_autotune, but on the caller's frames: frames[0..count) (count 3..
+ * SIM_MAX_BATCH) with flows and timestamps as for sim_push_frames (frame 0
+ * starts the stream, flows[0] is not read; mem = SIM_HOST | SIM_DEVICE for
+ * all of them, pitch_bytes per row), pushed as one batch through a
+ * temporary simulator of each shape - twice, the second pass timed.  A
+ * sample of the stream that will run gives the choice for its content (flow
+ * reach, event density, active fraction), which a synthetic probe does not
+ * know.  The caller's buffers are only read.  Errors as sim_autotune, plus
+ * those of sim_push_frames for the sample (SIM_ERR_TIME ...). */
+int sim_autotune_sample(const sim_config* cfg, int32_t count, const void* const* frames,
+                        int64_t pitch_bytes, const float* const* flows, const int64_t* t_us,
+                        int32_t mem, int32_t* tile_height_out, double* us_out);
 
 /* Write the autotuner table to a text file (one line per configuration:
  * the key's nine fields, the chosen tile height, the two per-frame times),

@@ -58,47 +58,68 @@ __global__ void k_probe(unsigned char* frames, float2* flows, int W, int H, int 
 
 int rc_of(cudaError_t e) { return evsim_rt::cuda_rc(e); }
 
-// Per-frame time (us) of the simulation kernel of a stream with tile height th.
-int time_shape(const sim_config& c, int th, int F, const unsigned char* frames,
-               const float2* flows, double* us) {
+// Per-frame time (us) of the simulation kernel of a stream with tile height th
+// on frames[0..count): frame 0 starts the stream, frames 1.. form one batch;
+// run twice (the first pass warms up), the second pass's tile launch timed.
+int time_shape(const sim_config& c, int th, int count, const void* const* frames,
+               int64_t pitch, const float* const* flows, const int64_t* t_us, int32_t mem,
+               double* us) {
   sim_config tc = c;
   tc.tile_height = th;
   tc.cuda_stream = nullptr;
-  tc.max_batch = F;
-  tc.event_capacity = std::min<long long>((long long)c.width * c.height * 2 * F, 1LL << 27);
+  tc.max_batch = count - 1;
+  tc.event_capacity = std::min<long long>((long long)c.width * c.height * 2 * count, 1LL << 27);
   sim_t* s = nullptr;
   int rc = sim_create(&tc, &s);
   if (rc) return rc;
-  const long long P = (long long)c.width * c.height;
-  const long long row = (long long)c.width * c.pixel_format;
-  std::vector<const void*> fr(F);
-  std::vector<const float*> fl(F);
-  std::vector<int64_t> t(F);
-  for (int j = 0; j < F; ++j) {
-    fr[j] = frames + (size_t)j * P * c.pixel_format;
-    fl[j] = (const float*)(flows + (size_t)j * P);
-    t[j] = 16667LL * j;
-  }
   const int kind = c.mode == SIM_SPARSE ? SIM_K_SPARSE : SIM_K_DENSE;
-  // a warm-up batch, then the timed one (the same frames, continued in time).
   // An event overflow only means the batch did not commit: its kernels ran
   // in full and were timed.
   auto ok = [](int r) { return r == SIM_OK || r == SIM_ERR_EVENT_OVERFLOW ? SIM_OK : r; };
-  rc = sim_push_frames(s, F, fr.data(), row, fl.data(), t.data(), SIM_DEVICE);
-  if (!rc) rc = ok(sim_sync(s));
-  if (!rc) rc = sim_set_profiling(s, 1);
-  for (int j = 0; j < F && !rc; ++j) t[j] += 16667LL * F;
-  if (!rc) rc = sim_push_frames(s, F - 1, fr.data() + 1, row, fl.data() + 1, t.data() + 1,
-                                SIM_DEVICE);
-  if (!rc) rc = ok(sim_sync(s));
+  for (int pass = 0; pass < 2 && !rc; ++pass) {
+    if (pass == 1) {
+      rc = sim_reset(s);
+      if (!rc) rc = sim_set_profiling(s, 1);
+    }
+    if (!rc) rc = sim_push_frames(s, count, frames, pitch, flows, t_us, mem);
+    if (!rc) rc = ok(sim_sync(s));
+  }
   double ms = 0;
   int64_t n = 0;
   if (!rc) rc = sim_kernel_time(s, kind, &ms, &n, 1);
   const int rd = sim_destroy(s);
   if (!rc) rc = rd;
   if (!rc && n < 1) rc = SIM_ERR_STATE;
-  if (!rc) *us = ms * 1e3 / (F - 1);
+  if (!rc) *us = ms * 1e3 / (count - 1);
   return rc;
+}
+
+int valid_cfg(const sim_config& c) {
+  if (c.width < 1 || c.height < 1 || c.width > SIM_MAX_DIM || c.height > SIM_MAX_DIM)
+    return SIM_ERR_ARG;
+  if (c.pixel_format != SIM_LUMA8 && c.pixel_format != SIM_RGB8) return SIM_ERR_ARG;
+  return SIM_OK;
+}
+
+// Time both shapes on the frames and record the faster one.
+int tune(const sim_config& c, int count, const void* const* frames, int64_t pitch,
+         const float* const* flows, const int64_t* t_us, int32_t mem, int32_t* th_out,
+         double* us_out) {
+  double us16 = 0, us8 = 0;
+  int rc = time_shape(c, 16, count, frames, pitch, flows, t_us, mem, &us16);
+  if (!rc) rc = time_shape(c, 8, count, frames, pitch, flows, t_us, mem, &us8);
+  if (rc) return rc;
+  const int th = us8 < us16 ? 8 : 16;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_table[key_of(c)] = Entry{th, us16, us8};
+  }
+  if (th_out) *th_out = th;
+  if (us_out) {
+    us_out[0] = us16;
+    us_out[1] = us8;
+  }
+  return SIM_OK;
 }
 
 }  // namespace
@@ -116,40 +137,46 @@ extern "C" {
 int sim_autotune(const sim_config* cfg, int32_t frames, int32_t* tile_height_out,
                  double* us_out) {
   if (!cfg || frames < 2 || frames > 64) return SIM_ERR_ARG;
-  sim_config c = *cfg;
-  if (c.width < 1 || c.height < 1 || c.width > SIM_MAX_DIM || c.height > SIM_MAX_DIM)
-    return SIM_ERR_ARG;
-  if (c.pixel_format != SIM_LUMA8 && c.pixel_format != SIM_RGB8) return SIM_ERR_ARG;
+  const sim_config c = *cfg;
+  if (valid_cfg(c)) return SIM_ERR_ARG;
+  const int F = frames + 1;  // frame 0 starts the stream
   const long long P = (long long)c.width * c.height;
   unsigned char* d_frames = nullptr;
   float2* d_flows = nullptr;
-  cudaError_t e = cudaMalloc(&d_frames, (size_t)P * c.pixel_format * frames);
-  if (e == cudaSuccess) e = cudaMalloc(&d_flows, (size_t)P * sizeof(float2) * frames);
+  cudaError_t e = cudaMalloc(&d_frames, (size_t)P * c.pixel_format * F);
+  if (e == cudaSuccess) e = cudaMalloc(&d_flows, (size_t)P * sizeof(float2) * F);
   if (e == cudaSuccess) {
-    const long long total = P * frames;
+    const long long total = P * F;
     const int grid = (int)std::min<long long>((total + 255) / 256, 8192);
-    k_probe<<<grid, 256>>>(d_frames, d_flows, c.width, c.height, c.pixel_format, frames);
+    k_probe<<<grid, 256>>>(d_frames, d_flows, c.width, c.height, c.pixel_format, F);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   int rc = e == cudaSuccess ? SIM_OK : (e == cudaErrorMemoryAllocation ? SIM_ERR_OOM : rc_of(e));
-  double us16 = 0, us8 = 0;
-  if (!rc) rc = time_shape(c, 16, frames, d_frames, d_flows, &us16);
-  if (!rc) rc = time_shape(c, 8, frames, d_frames, d_flows, &us8);
+  if (!rc) {
+    std::vector<const void*> fr(F);
+    std::vector<const float*> fl(F);
+    std::vector<int64_t> t(F);
+    for (int j = 0; j < F; ++j) {
+      fr[j] = d_frames + (size_t)j * P * c.pixel_format;
+      fl[j] = (const float*)(d_flows + (size_t)j * P);
+      t[j] = 16667LL * j;
+    }
+    rc = tune(c, F, fr.data(), (int64_t)c.width * c.pixel_format, fl.data(), t.data(),
+              SIM_DEVICE, tile_height_out, us_out);
+  }
   cudaFree(d_frames);
   cudaFree(d_flows);
-  if (rc) return rc;
-  const int th = us8 < us16 ? 8 : 16;
-  {
-    std::lock_guard<std::mutex> g(g_tune_mu);
-    g_table[key_of(c)] = Entry{th, us16, us8};
-  }
-  if (tile_height_out) *tile_height_out = th;
-  if (us_out) {
-    us_out[0] = us16;
-    us_out[1] = us8;
-  }
-  return SIM_OK;
+  return rc;
+}
+
+int sim_autotune_sample(const sim_config* cfg, int32_t count, const void* const* frames,
+                        int64_t pitch_bytes, const float* const* flows, const int64_t* t_us,
+                        int32_t mem, int32_t* tile_height_out, double* us_out) {
+  if (!cfg || count < 3 || count > SIM_MAX_BATCH || !frames || !flows || !t_us) return SIM_ERR_ARG;
+  if (mem != SIM_HOST && mem != SIM_DEVICE) return SIM_ERR_ARG;
+  if (valid_cfg(*cfg)) return SIM_ERR_ARG;
+  return tune(*cfg, count, frames, pitch_bytes, flows, t_us, mem, tile_height_out, us_out);
 }
 
 int sim_autotune_save(const char* path) {

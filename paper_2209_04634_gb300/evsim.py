@@ -119,6 +119,9 @@ SIGNATURES = [
     ("sim_last_cuda_error", ctypes.c_char_p, []),
     ("sim_autotune", ctypes.c_int, [ctypes.POINTER(sim_config), _I32, ctypes.POINTER(_I32),
                                     ctypes.POINTER(ctypes.c_double)]),
+    ("sim_autotune_sample", ctypes.c_int, [ctypes.POINTER(sim_config), _I32, ctypes.POINTER(_VP),
+                                           _I64, ctypes.POINTER(_VP), ctypes.POINTER(_I64), _I32,
+                                           ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     ("sim_autotune_save", ctypes.c_int, [ctypes.c_char_p]),
     ("sim_autotune_load", ctypes.c_int, [ctypes.c_char_p]),
     ("simb_config_default", ctypes.c_int, [ctypes.POINTER(simb_config)]),
@@ -391,6 +394,29 @@ def autotune(width: int, height: int, frames: int = 8, **kw) -> tuple[int, float
     th = ctypes.c_int32(0)
     us = (ctypes.c_double * 2)()
     check(load().sim_autotune(ctypes.byref(cfg), frames, ctypes.byref(th), us), "sim_autotune")
+    del keep
+    return int(th.value), float(us[0]), float(us[1])
+
+
+def autotune_sample(width: int, height: int, frames, flows, t_us, **kw) -> tuple[int, float, float]:
+    """sim_autotune_sample on a sample of a stream: frames (F, H, W[, 3]) uint8
+    and flows (F, H, W, 2) float32, numpy (host) or torch CUDA tensors
+    (device), t_us (F,) int64; make_config keywords for the rest."""
+    cfg, keep = make_config(width, height, **kw)
+    F = len(frames)
+    dev = _is_device(frames)
+    if not dev:
+        frames = np.ascontiguousarray(frames, dtype=np.uint8)
+        flows = np.ascontiguousarray(flows, dtype=np.float32)
+    fr = (ctypes.c_void_p * F)(*[_ptr(frames[i]) for i in range(F)])
+    fl = (ctypes.c_void_p * F)(*[_ptr(flows[i]) for i in range(F)])
+    t = (ctypes.c_int64 * F)(*[int(v) for v in t_us])
+    pitch = width * (3 if getattr(frames, "ndim", len(frames.shape)) == 4 else 1)
+    th = ctypes.c_int32(0)
+    us = (ctypes.c_double * 2)()
+    check(load().sim_autotune_sample(ctypes.byref(cfg), F, fr, pitch, fl, t,
+                                     SIM_DEVICE if dev else SIM_HOST, ctypes.byref(th), us),
+          "sim_autotune_sample")
     del keep
     return int(th.value), float(us[0]), float(us[1])
 

@@ -430,3 +430,20 @@ def test_autotune_chooses_a_shape_that_sim_create_uses():
     sim = evsim.Simulator(200, 100, substeps=3, tile_height=evsim.SIM_TILE_TUNE)
     assert sim.stats().tile_height in (8, 16)
     sim.close()
+
+
+@pytest.mark.parametrize("device", [True, False])
+def test_autotune_on_a_sample_of_the_stream(device):
+    seq = synth.warped_texture(frames=6, width=200, height=96)
+    fr, fl = seq.frames, seq.flows
+    if device:
+        fr, fl = torch.from_numpy(fr).cuda(), torch.from_numpy(fl).cuda()
+    opts = evsim.seq_options(seq, mode=evsim.SIM_SPARSE)
+    th, us16, us8 = evsim.autotune_sample(seq.width, seq.height, fr, fl, seq.t_us, **opts)
+    assert th == (8 if us8 < us16 else 16) and us16 > 0 and us8 > 0
+    sim = evsim.simulator_for(seq, evsim.SIM_SPARSE)  # SIM_TILE_AUTO: the table's entry
+    assert sim.stats().tile_height == th
+    sim.close()
+    # the sample's own events are unaffected: a stream run afterwards matches the oracle
+    g = gpu_run(seq, evsim.SIM_SPARSE)
+    assert_same_events(g["events"], oracle_run(seq, evsim.SIM_SPARSE)["events"], "after tuning")
