@@ -8,7 +8,8 @@ it, and the two share no code: this package holds its own C source
 
 ``run()`` is a ctypes wrapper of ``orc_run`` (the whole per-stream method of
 Sec. III-A / III-B of Ziegler et al., arXiv 2209.04634, as restated in
-``evsim_oracle.c``).  ``exact.py`` is a second, pixel-major restatement in
+``evsim_oracle.c``); ``run_diff()`` wraps ``orc_run_diff`` (the
+difference-frame interpolation of Sec. III-C).  ``exact.py`` is a second, pixel-major restatement in
 pure Python integers for tiny inputs.
 
 Parity status of each function is pinned by ``tests/test_oracle_pins.py``
@@ -100,6 +101,9 @@ def _load():
             lib.orc_run.argtypes = [ctypes.POINTER(OrcConfig), ctypes.c_int32, vp, vp, vp,
                                     vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp]
             lib.orc_run.restype = ctypes.c_int64
+            lib.orc_run_diff.argtypes = [ctypes.POINTER(OrcConfig), ctypes.c_int32, vp, vp, vp,
+                                         vp, vp, vp, ctypes.c_int64, vp, vp, vp]
+            lib.orc_run_diff.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -193,6 +197,49 @@ def run(frames: np.ndarray, flows: np.ndarray | None, t_us, *, mode: int = DENSE
         raise ValueError(f"oracle rejected the input (code {n})")
     return {"events": ev[:n].copy(), "R": R, "n_per_frame": npf, "ev_per_frame": epf,
             "active_per_frame": apf, "clamped": int(clamped.value)}
+
+
+def run_diff(frames: np.ndarray, flows: np.ndarray | None, t_us, *, substeps: int = 8,
+             max_substeps: int = 64, intensity: int = LOG, c_pos_q16: int = 13107,
+             c_neg_q16: int = 13107, cpos_map: np.ndarray | None = None,
+             cneg_map: np.ndarray | None = None, cap: int | None = None) -> dict:
+    """Run the difference-frame interpolation oracle (orc_run_diff, Sec. III-C)
+    over a whole sequence; flows[i] is the flow between difference frames i-1
+    and i.  Returns 'events', 'n_per_frame', 'ev_per_frame', 'clamped'."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    F = frames.shape[0]
+    H, W = frames.shape[1], frames.shape[2]
+    ch = 3 if frames.ndim == 4 else 1
+    t = np.ascontiguousarray(np.asarray(t_us, dtype=np.int64))
+    if flows is not None:
+        flows = np.ascontiguousarray(flows, dtype=np.float32)
+        assert flows.shape == (F, H, W, 2), flows.shape
+    cfg = OrcConfig(W, H, ch, 0, substeps, max_substeps, intensity, RESET,
+                    c_pos_q16, c_neg_q16, -1)
+    maps = [None if m is None else np.ascontiguousarray(m, dtype=np.uint16)
+            for m in (cpos_map, cneg_map)]
+    npf = np.zeros(F, dtype=np.int32)
+    epf = np.zeros(F, dtype=np.int64)
+    clamped = ctypes.c_int64(0)
+    lib = _load()
+
+    def call(capacity):
+        ev = np.zeros(max(capacity, 1), dtype=EVENT_DTYPE)
+        n = lib.orc_run_diff(ctypes.byref(cfg), F, frames.ctypes.data,
+                             None if flows is None else flows.ctypes.data, t.ctypes.data,
+                             None if maps[0] is None else maps[0].ctypes.data,
+                             None if maps[1] is None else maps[1].ctypes.data,
+                             ev.ctypes.data, capacity, npf.ctypes.data, epf.ctypes.data,
+                             ctypes.byref(clamped))
+        return n, ev
+
+    n, ev = call(cap if cap is not None else 1 << 16)
+    if n > len(ev):
+        n, ev = call(int(n))
+    if n < 0:
+        raise ValueError(f"oracle rejected the input (code {n})")
+    return {"events": ev[:n].copy(), "n_per_frame": npf, "ev_per_frame": epf,
+            "clamped": int(clamped.value)}
 
 
 def unpack(events: np.ndarray):

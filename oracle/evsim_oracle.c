@@ -5,7 +5,7 @@
  * repeated crossings.  No blocking, no fusion, no SIMD, no threads.
  *
  * Paper: Ziegler et al., "Real-time event simulation with frame-based
- * cameras" (arXiv 2209.04634), Sec. III, III-A, III-B, Table I.
+ * cameras" (arXiv 2209.04634), Sec. III, III-A, III-B, III-C, Table I.
  */
 #include "evsim_oracle.h"
 
@@ -258,5 +258,105 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
   if (R_final) memcpy(R_final, R, P * sizeof(int32_t));
   if (clamped_total) *clamped_total = clamped;
   free(Lprev); free(Lcur); free(R); free(Fx); free(Fy); free(act);
+  return rc < 0 ? rc : n;
+}
+
+/*
+ * Difference-frame interpolation (Sec. III-C).  From three consecutive
+ * frames i-2, i-1, i the method forms two difference frames,
+ *   D_{i-1} = L_{i-1} - L_{i-2},   D_i = L_i - L_{i-1}
+ * (L the intensity table applied to the frame; Sec. III's linear difference
+ * in ORC_LINEAR), takes the flow between the two difference frames (an
+ * input, stored at index i), interpolates N difference frames between them
+ * with the sampling and blend of the dense method (Sec. III-A), and
+ * thresholds each interpolated difference frame with the two-case equations
+ * of Sec. III-A (strict): the difference frames stand for the events, so
+ * there is no reference state.  Events of substep k carry t_k between
+ * t_{i-1} and t_i.  Frames 0 and 1 emit nothing (three frames are needed).
+ * N: fixed, or adaptive from the largest flow of the frame (every pixel).
+ */
+int64_t orc_run_diff(const orc_config* c, int32_t n_frames, const uint8_t* frames,
+                     const float* flows, const int64_t* t_us,
+                     const uint16_t* cpos_map, const uint16_t* cneg_map,
+                     orc_event* out, int64_t cap, int32_t* n_per_frame,
+                     int64_t* ev_per_frame, int64_t* clamped_total) {
+  if (!c || n_frames < 1 || !frames || !t_us || c->width < 1 || c->height < 1) return -1;
+  if (c->channels != 1 && c->channels != 3) return -1;
+  if (c->substeps < 0 || (c->substeps == 0 && c->max_substeps < 1)) return -1;
+  if (n_frames > 2 && !flows) return -1;
+  const int32_t W = c->width, H = c->height;
+  const int64_t P = (int64_t)W * H;
+  const int64_t fbytes = P * c->channels;
+
+  int32_t lut[256];
+  orc_lut(c->intensity, lut);
+
+  int32_t* L2 = (int32_t*)malloc(P * sizeof(int32_t));   /* frame i-2 */
+  int32_t* L1 = (int32_t*)malloc(P * sizeof(int32_t));   /* frame i-1 */
+  int32_t* L0 = (int32_t*)malloc(P * sizeof(int32_t));   /* frame i */
+  int32_t* Dp = (int32_t*)malloc(P * sizeof(int32_t));   /* D_{i-1} */
+  int32_t* Dc = (int32_t*)malloc(P * sizeof(int32_t));   /* D_i */
+  int32_t* Fx = (int32_t*)malloc(P * sizeof(int32_t));
+  int32_t* Fy = (int32_t*)malloc(P * sizeof(int32_t));
+  if (!L2 || !L1 || !L0 || !Dp || !Dc || !Fx || !Fy) {
+    free(L2); free(L1); free(L0); free(Dp); free(Dc); free(Fx); free(Fy);
+    return -4;
+  }
+  int64_t clamped = 0, n = 0, rc = 0;
+  for (int32_t i = 0; i < n_frames; ++i) {
+    if (i > 0) {
+      if (t_us[i] <= t_us[i - 1]) { rc = -2; break; }
+      if (t_us[i] - t_us[0] > 4294967295LL) { rc = -3; break; }
+    }
+    /* roll the three frames: L2 <- L1 <- L0 <- frame i */
+    int32_t* tmp = L2; L2 = L1; L1 = L0; L0 = tmp;
+    frame_to_log(c, lut, frames + (int64_t)i * fbytes, L0);
+    if (n_per_frame) n_per_frame[i] = 0;
+    if (ev_per_frame) ev_per_frame[i] = 0;
+    if (i < 2) continue;
+    int64_t n_before = n;
+    for (int64_t p = 0; p < P; ++p) {
+      Dp[p] = L1[p] - L2[p];
+      Dc[p] = L0[p] - L1[p];
+    }
+    const float* fl = flows + (int64_t)i * P * 2;
+    int64_t m = 0;
+    for (int64_t p = 0; p < P; ++p) {
+      int32_t cl = 0;
+      Fx[p] = orc_flow_q16(fl[2 * p], &cl);
+      Fy[p] = orc_flow_q16(fl[2 * p + 1], &cl);
+      clamped += cl;
+      int64_t f2 = (int64_t)Fx[p] * Fx[p] + (int64_t)Fy[p] * Fy[p];
+      if (f2 > m) m = f2;
+    }
+    int32_t N = c->substeps > 0 ? c->substeps : orc_adaptive_substeps(m, c->max_substeps);
+    int64_t t_prev = t_us[i - 1] - t_us[0];
+    int64_t dt = t_us[i] - t_us[i - 1];
+    for (int32_t k = 1; k <= N; ++k) {
+      int64_t w = ((int64_t)k * 8192 + N) / (2 * (int64_t)N);
+      uint32_t tk = (uint32_t)(t_prev + floordiv((int64_t)k * dt, N));
+      for (int32_t y = 0; y < H; ++y) {
+        for (int32_t x = 0; x < W; ++x) {
+          int64_t p = (int64_t)y * W + x;
+          /* interpolated difference frame k of N between D_{i-1} and D_i */
+          int64_t offx = floordiv((int64_t)Fx[p] * k, N);
+          int64_t offy = floordiv((int64_t)Fy[p] * k, N);
+          int64_t p0x = (int64_t)x * 65536 - offx, p0y = (int64_t)y * 65536 - offy;
+          int64_t p1x = p0x + Fx[p], p1y = p0y + Fy[p];
+          int64_t s0 = orc_bilinear(Dp, W, H, p0x, p0y);
+          int64_t s1 = orc_bilinear(Dc, W, H, p1x, p1y);
+          int64_t I = lerp_q12(s0, s1, w);
+          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);
+          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);
+          if (I > cp) emit(out, cap, &n, tk, x, y, 1);
+          else if (I < -(int64_t)cn) emit(out, cap, &n, tk, x, y, 0);
+        }
+      }
+    }
+    if (n_per_frame) n_per_frame[i] = N;
+    if (ev_per_frame) ev_per_frame[i] = n - n_before;
+  }
+  if (clamped_total) *clamped_total = clamped;
+  free(L2); free(L1); free(L0); free(Dp); free(Dc); free(Fx); free(Fy);
   return rc < 0 ? rc : n;
 }

@@ -16,6 +16,9 @@
  *     and events <x, y, t, p> are emitted.
  *   - Sec. III-B (sparse frame interpolation): only pixels whose change from
  *     frame i-1 to frame i reaches a threshold are interpolated.
+ *   - Sec. III-C (difference frame interpolation): difference frames of three
+ *     consecutive frames are interpolated along the flow between them and
+ *     each interpolated difference frame is thresholded (orc_run_diff).
  * The fixed-point readings (Q16 log LUT, Q12 weights, clamp-to-edge bilinear
  * sampling, reference-accumulating threshold test) are stated beside each
  * function in evsim_oracle.c.
@@ -88,6 +91,18 @@ int64_t orc_run(const orc_config* cfg, int32_t n_frames, const uint8_t* frames,
                 orc_event* out, int64_t cap, int32_t* R_final,
                 int32_t* n_per_frame, int64_t* ev_per_frame,
                 int64_t* active_per_frame, int64_t* clamped_total);
+
+/*
+ * Difference-frame interpolation (Sec. III-C) over n_frames frames: the same
+ * arguments as orc_run (mode, ref_mode and c_act_q16 are not used; flows[i]
+ * is the flow between difference frames i-1 and i).  Frames 0 and 1 emit
+ * nothing.  Returns the event count or a negative error as orc_run.
+ */
+int64_t orc_run_diff(const orc_config* cfg, int32_t n_frames, const uint8_t* frames,
+                     const float* flows, const int64_t* t_us,
+                     const uint16_t* cpos_map, const uint16_t* cneg_map,
+                     orc_event* out, int64_t cap, int32_t* n_per_frame,
+                     int64_t* ev_per_frame, int64_t* clamped_total);
 
 #ifdef __cplusplus
 }

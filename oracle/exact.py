@@ -7,7 +7,8 @@ that a loop-order or ordering slip in either shows up as a mismatch.  Pure
 Python loops: tiny inputs only (8x8 and similar).
 
 Paper: Ziegler et al., arXiv 2209.04634, Sec. III-A (dense interpolation and
-the two-case threshold equations) and Sec. III-B (sparse activity test).
+the two-case threshold equations), Sec. III-B (sparse activity test) and
+Sec. III-C (difference-frame interpolation, ``simulate_diff``).
 """
 from __future__ import annotations
 
@@ -107,3 +108,48 @@ def simulate(frames, flows_q16, t_us, *, n_sub, cp, cn, linear=False, reset=Fals
             out.extend([(tk, x, y, p)] * m)
         L0 = L1
     return out, R
+
+
+def simulate_diff(frames, flows_q16, t_us, *, n_sub, cp, cn, linear=False, cp_map=None,
+                  cn_map=None, max_sub=64):
+    """Difference-frame interpolation (Sec. III-C), pixel-major: for frame
+    i >= 2 each pixel samples the difference frames D_{i-1} = L_{i-1} - L_{i-2}
+    and D_i = L_i - L_{i-1} along flows_q16[i] for k = 1..N and emits an event
+    where the interpolated difference exceeds C_pos or falls below -C_neg.
+    Returns the events as (t, x, y, p) tuples in output order."""
+    lut = log_table(linear)
+    H, W = len(frames[0]), len(frames[0][0])
+    L = [[[lut[v] for v in row] for row in f] for f in frames]
+    t0 = t_us[0]
+    out = []
+    for i in range(2, len(frames)):
+        Dp = [[L[i - 1][y][x] - L[i - 2][y][x] for x in range(W)] for y in range(H)]
+        Dc = [[L[i][y][x] - L[i - 1][y][x] for x in range(W)] for y in range(H)]
+        N = n_sub
+        if N == 0:
+            m = max(flows_q16[i][y][x][0] ** 2 + flows_q16[i][y][x][1] ** 2
+                    for y in range(H) for x in range(W))
+            N = 1
+            while N < max_sub and N * N * (1 << 32) < m:
+                N += 1
+        dt, tprev = t_us[i] - t_us[i - 1], t_us[i - 1] - t0
+        ev = []
+        for y in range(H):
+            for x in range(W):
+                fx, fy = flows_q16[i][y][x]
+                c_p = cp_map[y][x] if cp_map is not None else cp
+                c_n = cn_map[y][x] if cn_map is not None else cn
+                for k in range(1, N + 1):
+                    w = (k * 8192 + N) // (2 * N)
+                    p0x, p0y = (x << 16) - (fx * k) // N, (y << 16) - (fy * k) // N
+                    s0 = _sample(Dp, W, H, p0x, p0y)
+                    s1 = _sample(Dc, W, H, p0x + fx, p0y + fy)
+                    I = s0 + ((s1 - s0) * w + 2048) // 4096
+                    tk = tprev + (k * dt) // N
+                    if I > c_p:
+                        ev.append((k, y, x, tk, 1))
+                    elif I < -c_n:
+                        ev.append((k, y, x, tk, -1))
+        ev.sort(key=lambda e: (e[0], e[1], e[2]))
+        out.extend((tk, x, y, p) for k, y, x, tk, p in ev)
+    return out

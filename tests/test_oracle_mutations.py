@@ -52,6 +52,19 @@ MUTATIONS = {
     "clamp_y_one_row_short": ("maxy = (int64_t)(H - 1) * 65536", "maxy = (int64_t)(H - 2) * 65536"),
     "time_base_from_current_frame": ("int64_t t_prev = t_us[i - 1] - t_us[0];",
                                      "int64_t t_prev = t_us[i] - t_us[0] - (t_us[1] - t_us[0]);"),
+    # difference-frame interpolation (orc_run_diff)
+    "diff_planes_swapped": [("int64_t s0 = orc_bilinear(Dp, W, H, p0x, p0y);",
+                             "int64_t s0 = orc_bilinear(Dc, W, H, p0x, p0y);"),
+                            ("int64_t s1 = orc_bilinear(Dc, W, H, p1x, p1y);",
+                             "int64_t s1 = orc_bilinear(Dp, W, H, p1x, p1y);")],
+    "diff_current_plane_sign": ("Dc[p] = L0[p] - L1[p];", "Dc[p] = L1[p] - L0[p];"),
+    "diff_previous_plane_skips_a_frame": ("Dp[p] = L1[p] - L2[p];", "Dp[p] = L0[p] - L2[p];"),
+    "diff_non_strict_threshold": ("if (I > cp) emit(out, cap, &n, tk, x, y, 1);",
+                                  "if (I >= cp) emit(out, cap, &n, tk, x, y, 1);"),
+    "diff_offset_sign": ("int64_t s0 = orc_bilinear(Dp, W, H, p0x, p0y);",
+                         "int64_t s0 = orc_bilinear(Dp, W, H, p0x + 2 * offx, p0y);"),
+    "diff_blend_reversed": ("int64_t I = lerp_q12(s0, s1, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)",
+                            "int64_t I = lerp_q12(s1, s0, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)"),
 }
 
 
@@ -88,6 +101,12 @@ def battery():
     yield pins.test_rgb_input_uses_bt601_luma
     yield pins.test_per_pixel_threshold_maps
     yield pins.test_adaptive_substeps_per_frame
+    yield pins.test_diff_one_substep_is_the_kaiser_difference_frame
+    for N in (4, 10):
+        for v in [(40, 120, 30), (200, 90, 210), (128, 130, 250)]:
+            yield lambda N=N, v=v: pins.test_diff_uniform_frames_follow_the_exact_line(N, v)
+    for s_, N in [((1, 0), 3), ((0, -1), 4), ((1, 1), 2), ((-2, 1), 2)]:
+        yield lambda s_=s_, N=N: pins.test_diff_translation_reproduces_shifted_difference_samples(s_, N)
 
 
 def test_battery_passes_on_the_real_oracle():

@@ -595,3 +595,129 @@ def test_second_restatement_on_random_8x8(case):
     assert got == ev
     if not reset:
         assert r["R"].tolist() == R
+
+
+# ---------------------------------------------------------------------------
+# Difference-frame interpolation (Sec. III-C): orc_run_diff
+
+
+def test_diff_one_substep_is_the_kaiser_difference_frame():
+    """With one substep and no flow, the interpolated difference frame is the
+    difference frame D_i = L_i - L_{i-1} itself, thresholded with the Sec. III-A
+    equations (strict): the Kaiser difference frame, from the third frame on
+    (frames 0 and 1 only build the first difference frame)."""
+    rng = np.random.default_rng(41)
+    F, H, W = 6, 12, 17
+    frames = rng.integers(0, 256, size=(F, H, W), dtype=np.uint8)
+    for intensity, C in ((oracle.LINEAR, 2 * Q), (oracle.LOG, 13107)):
+        r = oracle.run_diff(frames, zero_flows(frames), times(F), substeps=1,
+                            intensity=intensity, c_pos_q16=C, c_neg_q16=C)
+        lut = py_lut(intensity == oracle.LINEAR)
+        t, x, y, p = oracle.unpack(r["events"])
+        assert not np.any(t < 2 * 1000)
+        for i in range(2, F):
+            d = lut[frames[i]] - lut[frames[i - 1]]
+            want = set(zip(*np.nonzero(d > C))) | set(zip(*np.nonzero(d < -C)))
+            sel = t == i * 1000
+            assert set(zip(y[sel], x[sel])) == want
+            for yy, xx, pp in zip(y[sel], x[sel], p[sel]):
+                assert pp == np.sign(d[yy, xx])
+        assert list(r["n_per_frame"]) == [0, 0] + [1] * (F - 2)
+
+
+@pytest.mark.parametrize("N", [4, 10])
+@pytest.mark.parametrize("v", [(40, 120, 30), (200, 90, 210), (128, 130, 250)])
+def test_diff_uniform_frames_follow_the_exact_line(N, v):
+    """Uniform frames v0, v1, v2 and no flow: the difference frames are the
+    constants D1 = L(v1) - L(v0) and D2 = L(v2) - L(v1), and interpolated
+    difference frame k lies on the line D1 + (k/N)(D2 - D1) (within the blend's
+    rounding).  Where that line is clear of the thresholds, substep k emits one
+    event of its sign at every pixel."""
+    H, W = 5, 7
+    frames = np.stack([np.full((H, W), a, np.uint8) for a in v])
+    C = 13107
+    r = oracle.run_diff(frames, zero_flows(frames), times(3), substeps=N,
+                        c_pos_q16=C, c_neg_q16=C)
+    lut = py_lut()
+    D1 = int(lut[v[1]] - lut[v[0]])
+    D2 = int(lut[v[2]] - lut[v[1]])
+    t, x, y, p = oracle.unpack(r["events"])
+    checked = 0
+    for k in range(1, N + 1):
+        line = D1 + (D2 - D1) * k / N
+        sel = t == 1000 + k * 1000 // N
+        if abs(line - C) < 2 or abs(line + C) < 2:
+            continue
+        want = 1 if line > C else (-1 if line < -C else 0)
+        if want == 0:
+            assert not np.any(sel)
+        else:
+            assert sel.sum() == H * W and np.all(p[sel] == want)
+        checked += 1
+    assert checked >= N - 1
+
+
+@pytest.mark.parametrize("s,N", [((1, 0), 3), ((0, -1), 4), ((1, 1), 2), ((-2, 1), 2)])
+def test_diff_translation_reproduces_shifted_difference_samples(s, N):
+    """Frames moving by m = N s whole pixels per frame: the difference frames
+    move by m too (D_i(x) = D_{i-1}(x - m)), every tap is exact, and the
+    interpolated difference frame k is D_{i-1} moved by k s.  Interior pixels
+    emit exactly the threshold crossings of D_{i-1}(x - k s)."""
+    rng = np.random.default_rng(53)
+    H, W = 28, 36
+    m = (N * s[0], N * s[1])
+    base = rng.integers(0, 256, size=(H, W), dtype=np.uint8)
+    frames = np.stack([np.roll(base, (j * m[1], j * m[0]), axis=(0, 1)) for j in range(3)])
+    flows = zero_flows(frames)
+    flows[2, ..., 0] = m[0]
+    flows[2, ..., 1] = m[1]
+    cp, cn = 20000, 15000
+    r = oracle.run_diff(frames, flows, times(3), substeps=N, c_pos_q16=cp, c_neg_q16=cn)
+    lut = py_lut()
+    D1 = lut[frames[1]] - lut[frames[0]]
+    got = per_pixel_sequences(r["events"])
+    margin = 2 * N * max(abs(s[0]), abs(s[1])) + 1
+    checked = 0
+    for y in range(margin, H - margin):
+        for x in range(margin, W - margin):
+            exp = []
+            for k in range(1, N + 1):
+                d = int(D1[y - k * s[1], x - k * s[0]])
+                if d > cp:
+                    exp.append((1000 + k * 1000 // N, 1))
+                elif d < -cn:
+                    exp.append((1000 + k * 1000 // N, -1))
+            assert got.get((x, y), []) == exp, (x, y)
+            checked += 1
+    assert checked > 100
+
+
+@pytest.mark.parametrize("case", range(60))
+def test_diff_second_restatement_on_random_8x8(case):
+    """orc_run_diff (substep-major C) and exact.simulate_diff (pixel-major
+    Python) agree event for event on random 8x8 inputs."""
+    rng = np.random.default_rng(5000 + case)
+    F = int(rng.integers(3, 5))
+    H = W = 8
+    frames = rng.integers(0, 256, size=(F, H, W), dtype=np.uint8)
+    if case % 3 == 0:
+        frames = np.clip(np.cumsum(rng.integers(-20, 21, size=(F, H, W)), axis=2) + 128,
+                         0, 255).astype(np.uint8)
+    flows = rng.uniform(-3, 3, size=(F, H, W, 2)).astype(np.float32)
+    N = int(rng.integers(0, 6))
+    linear = bool(case % 4 == 1)
+    if linear:
+        cp, cn = int(rng.integers(Q, 40 * Q)), int(rng.integers(Q, 40 * Q))
+    else:
+        cp, cn = int(rng.integers(2000, 40000)), int(rng.integers(2000, 40000))
+    t_us = np.cumsum(rng.integers(1, 50000, size=F)).astype(np.int64)
+    r = oracle.run_diff(frames, flows, t_us, substeps=N, max_substeps=6,
+                        intensity=oracle.LINEAR if linear else oracle.LOG,
+                        c_pos_q16=cp, c_neg_q16=cn)
+    fq = [[[(int(np.rint(np.float64(flows[i, y, x, 0]) * Q)),
+             int(np.rint(np.float64(flows[i, y, x, 1]) * Q))) for x in range(W)]
+           for y in range(H)] for i in range(F)]
+    ev = exact.simulate_diff([f.tolist() for f in frames], fq, t_us.tolist(), n_sub=N,
+                             cp=cp, cn=cn, linear=linear, max_sub=6)
+    t, x, y, p = oracle.unpack(r["events"])
+    assert list(zip(t.tolist(), x.tolist(), y.tolist(), p.tolist())) == ev
