@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=50)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=12.0)
+    ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--tile-height", type=int, default=0, choices=[0, 8, 16],
                     help="batch kernel tile height; 0: the library's autotuner chooses")
     return ap.parse_args()
@@ -333,6 +334,8 @@ def run_ours(args, ws, rank, local):
 
     if rank == 0 and not args.no_e2e:
         line["e2e"] = run_e2e(args, seq, sims, stream, work_step)
+    if rank == 0 and not args.no_diff:
+        line["difference"] = run_difference(args, seq, frames, flows, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(args)
     if rank == 0 and not args.no_serve:
@@ -348,6 +351,58 @@ def run_ours(args, ws, rank, local):
     if rank == 0:
         print(json.dumps(line))
     return 0
+
+
+def run_difference(args, seq, frames, flows, stream):
+    """The difference-frame interpolation method (Sec. III-C) on the same
+    device-resident sequence, the flows read as flows between difference
+    frames: one 99-frame batch per step, device time with CUDA events."""
+    import torch
+
+    from paper_2209_04634_gb300 import evsim
+    # every interpolated difference frame is thresholded on its own: far more
+    # events than the reference-based methods, hence buffers of its own
+    cap = 120_000_000
+    out = torch.empty(cap * 8, dtype=torch.uint8, device="cuda")
+    sim = evsim.simulator_for(seq, evsim.SIM_DIFF, event_capacity=cap, stream=stream,
+                              c_pos_map=None, c_neg_map=None)
+
+    def step():
+        sim.reset()
+        sim.push_many(frames, flows, seq.t_us)
+        n, rc = sim.pop_into(out, cap)
+        assert rc == evsim.SIM_OK, rc
+        return n
+
+    step()
+    work = sim.stats().pixel_substeps
+    for _ in range(3):
+        step()
+    sim.set_profiling(True)
+    step()
+    for k in range(len(evsim.KERNEL_NAMES)):
+        sim.kernel_time(k, reset=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_ev = 0
+    for _ in range(args.steps):
+        n_ev += step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = {}
+    for k, name in enumerate(evsim.KERNEL_NAMES):
+        t, c = sim.kernel_time(k)
+        if c:
+            kt[name] = t / c * 1e3
+    sim.close()
+    return {"workload": "warped_texture 640x480, 100 frames, flows read as flows between "
+                        "difference frames, adaptive N <= 8, C = 0.2 (uniform)",
+            "value": work * args.steps / (ms / 1e3) / 1e9, "unit": METRIC,
+            "ms_per_step": ms / args.steps, "events_per_s": n_ev / (ms / 1e3),
+            "kernel_us_per_launch": kt}
 
 
 # Integer operations the method defines for one pixel-substep (Sec. III-A as

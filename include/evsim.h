@@ -14,6 +14,17 @@
  *   - Sec. III-B: sparse frame interpolation.  Only pixels whose change from
  *                 frame i-1 to frame i reaches an activity threshold are
  *                 interpolated; the others emit nothing.
+ *   - Sec. III-C: difference-frame interpolation (SIM_DIFF).  From frames
+ *                 i-2, i-1, i the difference frames D_{i-1} = L_{i-1} - L_{i-2}
+ *                 and D_i = L_i - L_{i-1} are formed; the pushed flow of frame
+ *                 i is the flow between the two difference frames; N difference
+ *                 frames are interpolated between them with the sampling and
+ *                 blend below (D in place of L) and each is thresholded with
+ *                 the strict two-case equations (> Cp positive, < -Cn
+ *                 negative, at most one event per substep, no reference:
+ *                 ref_mode is ignored).  Frames 0 and 1 of a stream emit
+ *                 nothing.  SIM_DIFF streams are single handles (not group
+ *                 members, not sim_step_pair_static).
  * The flow itself is an input (the paper computes it with OpenCV; it is not
  * part of this library).
  *
@@ -64,7 +75,7 @@ extern "C" {
 
 /* ---- enumerations ------------------------------------------------------- */
 enum { SIM_LUMA8 = 1, SIM_RGB8 = 3 };          /* bytes per input pixel */
-enum { SIM_DENSE = 0, SIM_SPARSE = 1 };
+enum { SIM_DENSE = 0, SIM_SPARSE = 1, SIM_DIFF = 2 };
 enum { SIM_LOG = 0, SIM_LINEAR = 1 };
 enum { SIM_REF_ACCUM = 0, SIM_REF_RESET = 1 };
 enum { SIM_HOST = 0, SIM_DEVICE = 1 };         /* where a buffer lives */
@@ -86,7 +97,7 @@ typedef struct {
 typedef struct {
   int32_t width, height;     /* 1..SIM_MAX_DIM */
   int32_t pixel_format;      /* SIM_LUMA8 | SIM_RGB8 (BT.601 luma on device) */
-  int32_t mode;              /* SIM_DENSE | SIM_SPARSE */
+  int32_t mode;              /* SIM_DENSE | SIM_SPARSE | SIM_DIFF (see below) */
   int32_t substeps;          /* > 0: fixed N; 0: N = ceil(max |flow|) per frame */
   int32_t max_substeps;      /* cap, 1..SIM_MAX_SUBSTEPS */
   int32_t intensity;         /* SIM_LOG | SIM_LINEAR */

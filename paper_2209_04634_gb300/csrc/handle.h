@@ -34,6 +34,7 @@ struct sim_s {
   unsigned short* d_cpmap = nullptr;
   unsigned short* d_cnmap = nullptr;
   unsigned char* d_ring[2] = {nullptr, nullptr};
+  unsigned char* d_ring2[2] = {nullptr, nullptr};  // difference mode: frame i-2
   int* d_R[2] = {nullptr, nullptr};
   Ctl* d_ctl = nullptr;
   unsigned long long* d_maxf2 = nullptr;

@@ -115,6 +115,8 @@ struct SimParams {
   const int* lut;               // 256 Q16 entries (device)
   unsigned char* ring0;         // luma frame ring (last frame of the previous batch)
   unsigned char* ring1;
+  unsigned char* ring2_0;       // difference mode: the frame before that (ping-pong as ring)
+  unsigned char* ring2_1;
   int* R0;                      // reference ping-pong pair
   int* R1;
   Ctl* ctl;
@@ -209,6 +211,7 @@ cudaError_t launch_flowmax(const SimParams& p, const BatchArg& b, cudaStream_t s
 cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st);
+cudaError_t launch_diff(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
 int tile_class(const SimParams& p);

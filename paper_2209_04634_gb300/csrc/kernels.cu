@@ -1641,6 +1641,202 @@ __global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile(SimParams p, BatchA
   tile_batch<RESET, MAPS, WIDE, SPARSE, TH_>(p, b, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Difference-frame interpolation (Sec. III-C).  The difference frames of
+// three consecutive frames, D_{i-1} = L_{i-1} - L_{i-2} and D_i = L_i - L_{i-1},
+// are sampled and blended along the flow between them exactly as the dense
+// method samples frames; each interpolated difference frame is thresholded
+// with the strict two-case equations (no reference state).  Nothing carries
+// from frame to frame, so every (tile, frame) of a batch is its own block.
+
+// Bilinear tap of a difference plane (frame b minus frame a, LUT'd) in global
+// memory at an absolute Q16 position, clamped to the image.
+template <bool WIDE>
+__device__ __forceinline__ int tap_global_diff(const FrameRef& fa, const FrameRef& fb, int W,
+                                               int H, const int* slut, int px, int py) {
+  px = min(max(px, 0), (W - 1) << 16);
+  py = min(max(py, 0), (H - 1) << 16);
+  const int ix = px >> 16, iy = py >> 16;
+  const int fx = (px >> 4) & 0xFFF, fy = (py >> 4) & 0xFFF;
+  const int x1 = min(ix + 1, W - 1), y1 = min(iy + 1, H - 1);
+  auto d = [&](int y, int x) {
+    return slut[load_luma(fb.ptr, fb.pitch, fb.ch, y, x)] -
+           slut[load_luma(fa.ptr, fa.pitch, fa.ch, y, x)];
+  };
+  const int top = lerp12<WIDE>(d(iy, ix), d(iy, x1), fx);
+  const int bot = lerp12<WIDE>(d(y1, ix), d(y1, x1), fx);
+  return lerp12<WIDE>(top, bot, fy);
+}
+
+// Replicate-padded halo of the difference plane (frame b minus frame a) with
+// reach (hx, hy) around the tile (same layout as fill_halo).
+__device__ __forceinline__ void fill_halo_diff(int* dst, const int* slut, const FrameRef& fa,
+                                               const FrameRef& fb, int W, int H, int tx0,
+                                               int ty0, int hx, int hy) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncols = TW + 2 * hx, nrows = TH + 2 * hy;
+  for (int sr = warp; sr < nrows; sr += NTD / 32) {
+    const int gy = min(max(ty0 - hy + sr, 0), H - 1);
+    int* d = dst + (HMAX - hy + sr) * SW + (HMAX - hx);
+    for (int sc = lane; sc < ncols; sc += 32) {
+      const int gx = min(max(tx0 - hx + sc, 0), W - 1);
+      d[sc] = slut[load_luma(fb.ptr, fb.pitch, fb.ch, gy, gx)] -
+              slut[load_luma(fa.ptr, fa.pitch, fa.ch, gy, gx)];
+    }
+  }
+}
+
+// The substeps of this thread's two pixels (columns lane and lane + 32 of tile
+// row `warp`) on the difference planes: FAST samples the shared halos (b0:
+// D_{i-1}, b1: D_i), otherwise global memory (frames f2, f1, f0 = i-2, i-1, i).
+template <bool WIDE, bool FAST>
+__device__ __forceinline__ void diff_substeps(const SimParams& p, const int* swk,
+                                              const unsigned* stk, int N, unsigned mN, int tx0,
+                                              int ty0, unsigned b0, unsigned b1,
+                                              const FrameRef& f2, const FrameRef& f1,
+                                              const FrameRef& f0, const int* slut, Seg* segr,
+                                              WarpStage* ws, const bool (&act)[2],
+                                              const int (&Fx)[2], const int (&Fy)[2],
+                                              const int (&Cp)[2], const int (&Cn)[2]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    px[j] = FAST ? (lane + 32 * j + HMAX) << 16 : (tx0 + lane + 32 * j) << 16;
+    py[j] = FAST ? (warp + HMAX) << 16 : (ty0 + warp) << 16;
+    divmod_n(Fx[j], N, mN, qx[j], rx[j]);
+    divmod_n(Fy[j], N, mN, qy[j], ry[j]);
+    ax[j] = 0;
+    ay[j] = 0;
+  }
+  for (int k = 0; k < N; ++k) {
+    const int w = swk[k];
+    int n[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      px[j] -= qx[j];
+      ax[j] += rx[j];
+      if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
+      py[j] -= qy[j];
+      ay[j] += ry[j];
+      if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
+      int s0, s1;
+      if (FAST) {
+        s0 = tap_shared<WIDE>(b0, px[j], py[j]);
+        s1 = tap_shared<WIDE>(b1, px[j] + Fx[j], py[j] + Fy[j]);
+      } else {
+        s0 = tap_global_diff<WIDE>(f2, f1, p.W, p.H, slut, px[j], py[j]);
+        s1 = tap_global_diff<WIDE>(f1, f0, p.W, p.H, slut, px[j] + Fx[j], py[j] + Fy[j]);
+      }
+      const int I = lerp12<WIDE>(s0, s1, w);
+      n[j] = act[j] ? (I > Cp[j] ? 1 : (I < -Cn[j] ? -1 : 0)) : 0;
+    }
+    publish_row_dense(p, segr + (long long)k * p.segs_per_k, n[0], n[1], stk[k], tx0,
+                      ty0 + warp, ws);
+  }
+}
+
+template <bool MAPS, bool WIDE>
+__global__ void __launch_bounds__(NTD, 2) k_diff(SimParams p, BatchArg b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_fx, s_fy;
+  __shared__ unsigned s_mN;
+  __shared__ WarpStage s_stage[NTD / 32];
+  Ctl* ctl = p.ctl;
+  if (block_error(&ctl->err)) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tile = blockIdx.x, fi = blockIdx.y;
+  const int tcx = tile % p.tiles_x, tcy = tile / p.tiles_x;
+  const int tx0 = tcx * TW, ty0 = tcy * TH;
+  const int W = p.W, H = p.H, nmax = p.n_max;
+  int* pb = (int*)smem_raw;  // D_{i-1} halo
+  int* cb = pb + SH * SW;    // D_i halo
+  int* slut = cb + SH * SW;
+  int* swk = slut + 256;
+  unsigned* stk = (unsigned*)(swk + nmax);
+  if (tid < 256) slut[tid] = p.lut[tid];
+  if ((tid & 31) == 0) s_stage[tid >> 5] = WarpStage{0, 0, 0};
+  if (tid == 0) { s_fx = 0; s_fy = 0; }
+
+  const int sel = ctl->sel;
+  const unsigned char* r1p = (sel & 2) ? p.ring1 : p.ring0;  // frame before the batch
+  unsigned char* r1n = (sel & 2) ? p.ring0 : p.ring1;
+  const unsigned char* r2p = (sel & 2) ? p.ring2_1 : p.ring2_0;  // the frame before that
+  unsigned char* r2n = (sel & 2) ? p.ring2_0 : p.ring2_1;
+  const long long stream_i = ctl->committed + fi;  // frames of the stream before this one
+  const FrameRef ring1{r1p, (long long)W, 1}, ring2{r2p, (long long)W, 1};
+  const FrameDesc cd = b.frames[fi];
+  const FrameRef f0{cd.frame, cd.pitch, p.ch};
+  FrameRef f1 = ring1, f2 = ring2;
+  if (fi >= 1) f1 = FrameRef{b.frames[fi - 1].frame, b.frames[fi - 1].pitch, p.ch};
+  if (fi >= 2) f2 = FrameRef{b.frames[fi - 2].frame, b.frames[fi - 2].pitch, p.ch};
+  else if (fi == 1) f2 = ring1;
+  const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[fi], nmax);
+  const long long tprev = fi == 0 ? ctl->t_prev : b.frames[fi - 1].t_rel;
+  if (tid < N) {
+    const int k = tid + 1;
+    swk[tid] = (k * 8192 + N) / (2 * N);
+    stk[tid] = (unsigned)(tprev + (k * (cd.t_rel - tprev)) / N);
+  }
+  if (tid == 0) s_mN = N > 1 ? (unsigned)(0x100000000ull / (unsigned)N) + 1u : 0u;
+
+  // this block's pixels, their flow and thresholds; the next batch's frame ring
+  bool act[2];
+  int Fx[2], Fy[2], Cp[2], Cn[2];
+  int clamps = 0;
+  unsigned mfx = 0, mfy = 0;
+  const int y = ty0 + warp;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int x = tx0 + lane + 32 * q;
+    act[q] = x < W && y < H;
+    Fx[q] = 0; Fy[q] = 0; Cp[q] = p.cp; Cn[q] = p.cn;
+    if (act[q]) {
+      const long long i = (long long)y * W + x;
+      const float2 fl = cd.flow[i];
+      Fx[q] = flow_q16(fl.x, clamps);
+      Fy[q] = flow_q16(fl.y, clamps);
+      if (MAPS) { Cp[q] = p.cpmap[i]; Cn[q] = p.cnmap[i]; }
+      mfx = max(mfx, (unsigned)abs(Fx[q]));
+      mfy = max(mfy, (unsigned)abs(Fy[q]));
+      if (fi == b.count - 1) r1n[i] = (unsigned char)load_luma(f0.ptr, f0.pitch, f0.ch, y, x);
+      if (fi == b.count - 2) r2n[i] = (unsigned char)load_luma(f0.ptr, f0.pitch, f0.ch, y, x);
+      if (b.count == 1) r2n[i] = r1p[i];
+    }
+  }
+  // frames 0 and 1 of the stream only build the first difference frame
+  const bool emits = stream_i >= 2;
+  mfx = __reduce_max_sync(FULL, mfx);
+  mfy = __reduce_max_sync(FULL, mfy);
+  if (lane == 0) {
+    atomicMax(&s_fx, (int)mfx);
+    atomicMax(&s_fy, (int)mfy);
+  }
+  __syncthreads();
+  const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
+  const bool fast = hx <= HMAX && hy <= HMAX;
+  if (emits && fast) {
+    fill_halo_diff(pb, slut, f2, f1, W, H, tx0, ty0, hx, hy);
+    fill_halo_diff(cb, slut, f1, f0, W, H, tx0, ty0, hx, hy);
+  }
+  __syncthreads();
+  Seg* segr = p.seg + (long long)fi * nmax * p.segs_per_k + (long long)y * p.tiles_x + tcx;
+  if (y < H) {  // warp-uniform
+    if (!emits) {
+      for (int k = lane; k < N; k += 32) segr[(long long)k * p.segs_per_k] = Seg{0ull, 0ull, 0, -1};
+    } else if (fast) {
+      diff_substeps<WIDE, true>(p, swk, stk, N, s_mN, tx0, ty0, (unsigned)__cvta_generic_to_shared(pb),
+                                (unsigned)__cvta_generic_to_shared(cb), f2, f1, f0, slut, segr,
+                                &s_stage[warp], act, Fx, Fy, Cp, Cn);
+    } else {
+      diff_substeps<WIDE, false>(p, swk, stk, N, s_mN, tx0, ty0, 0u, 0u, f2, f1, f0, slut, segr,
+                                 &s_stage[warp], act, Fx, Fy, Cp, Cn);
+    }
+  }
+  clamps = __reduce_add_sync(FULL, clamps);
+  if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
+}
+
 // Adaptive N for the sparse method: max squared flow over the active pixels
 // of each frame.  Warp w of block bx (of nbx) takes rows bx * NWARP + w,
 // + nbx * NWARP, ...; each lane four columns of the row at a time, their
@@ -2292,6 +2488,19 @@ cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st)
 
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st) {
   return launch_tile_mode<true>(p, b, st);
+}
+
+size_t diff_smem_bytes(int n_max) { return (size_t)(2 * SH * SW + 256 + 2 * n_max) * 4; }
+
+cudaError_t launch_diff(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  const dim3 grid(p.tiles_x * p.tiles_y, b.count);
+  const size_t sm = diff_smem_bytes(p.n_max);
+  const bool maps = p.cpmap != nullptr, wide = p.intensity == SIM_LINEAR;
+  if (!maps && !wide) k_diff<false, false><<<grid, NTD, sm, st>>>(p, b);
+  else if (maps && !wide) k_diff<true, false><<<grid, NTD, sm, st>>>(p, b);
+  else if (!maps && wide) k_diff<false, true><<<grid, NTD, sm, st>>>(p, b);
+  else k_diff<true, true><<<grid, NTD, sm, st>>>(p, b);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st) {

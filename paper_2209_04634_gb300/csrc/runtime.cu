@@ -54,7 +54,8 @@ Sizing sizing(const sim_config& c) {
 long long state_bytes(const sim_config& c) {
   const Sizing z = sizing(c);
   long long b = 256 * 4 + 2 * z.P + (long long)sizeof(Ctl) + 8LL * z.bmax;
-  if (c.ref_mode == SIM_REF_ACCUM) b += 8 * z.P;
+  if (c.ref_mode == SIM_REF_ACCUM && c.mode != SIM_DIFF) b += 8 * z.P;
+  if (c.mode == SIM_DIFF) b += 2 * z.P;  // the second frame ring
   b += (z.stage + z.cap) * (long long)sizeof(Ev);       // staging + events
   b += z.seg_cap * (long long)sizeof(evsim::Seg) + 8 * z.ochunks;
   b += 8LL * z.tiles_x * ((c.height + 7) / 8);                     // tile progress words
@@ -79,6 +80,8 @@ void free_all(sim_t* s) {
   cudaFree(s->d_cnmap);
   cudaFree(s->d_ring[0]);
   cudaFree(s->d_ring[1]);
+  cudaFree(s->d_ring2[0]);
+  cudaFree(s->d_ring2[1]);
   cudaFree(s->d_R[0]);
   cudaFree(s->d_R[1]);
   cudaFree(s->d_ctl);
@@ -121,6 +124,8 @@ evsim::SimParams make_params(const sim_t* s) {
   p.lut = s->d_lut;
   p.ring0 = s->d_ring[0];
   p.ring1 = s->d_ring[1];
+  p.ring2_0 = s->d_ring2[0];
+  p.ring2_1 = s->d_ring2[1];
   p.R0 = s->d_R[0];
   p.R1 = s->d_R[1];
   p.ctl = s->d_ctl;
@@ -248,12 +253,15 @@ cudaError_t enqueue_batch(sim_t* s, int n) {
   b.serial = ++s->serial;
   cudaError_t e;
   const bool adaptive = s->cfg.substeps == 0;
-  if (s->cfg.mode == SIM_DENSE) {
+  if (s->cfg.mode == SIM_DENSE || s->cfg.mode == SIM_DIFF) {
     if (adaptive) {
       e = timed(s, SIM_K_FLOWMAX, [&] { return evsim::launch_flowmax(p, b, s->stream); });
       if (e != cudaSuccess) return e;
     }
-    e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, b, s->stream); });
+    if (s->cfg.mode == SIM_DIFF)
+      e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_diff(p, b, s->stream); });
+    else
+      e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, b, s->stream); });
   } else {
     if (adaptive) {
       e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, b, s->stream); });
@@ -318,7 +326,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   const sim_config& c = *cfg;
   if (c.width < 1 || c.height < 1 || c.width > SIM_MAX_DIM || c.height > SIM_MAX_DIM) return SIM_ERR_ARG;
   if (c.pixel_format != SIM_LUMA8 && c.pixel_format != SIM_RGB8) return SIM_ERR_ARG;
-  if (c.mode != SIM_DENSE && c.mode != SIM_SPARSE) return SIM_ERR_ARG;
+  if (c.mode != SIM_DENSE && c.mode != SIM_SPARSE && c.mode != SIM_DIFF) return SIM_ERR_ARG;
   if (c.intensity != SIM_LOG && c.intensity != SIM_LINEAR) return SIM_ERR_ARG;
   if (c.ref_mode != SIM_REF_ACCUM && c.ref_mode != SIM_REF_RESET) return SIM_ERR_ARG;
   if (c.substeps < 0 || c.substeps > SIM_MAX_SUBSTEPS) return SIM_ERR_ARG;
@@ -334,7 +342,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   // Thresholds: >= 1, < 2^30; accumulate mode also bounds the events of one
   // pixel-substep to 32767 (they are counted in 16 bits).
   const long long range = (long long)lut[255] - lut[0];
-  const long long cmin = c.ref_mode == SIM_REF_ACCUM ? (range + 32765) / 32766 : 1;
+  const bool accum = c.ref_mode == SIM_REF_ACCUM && c.mode != SIM_DIFF;
+  const long long cmin = accum ? (range + 32765) / 32766 : 1;
   auto bad_c = [&](long long v) { return v < cmin || v >= (1LL << 30); };
   const long long P = (long long)c.width * c.height;
   if (!c.c_pos_map && bad_c(c.c_pos_q16)) return SIM_ERR_ARG;
@@ -365,6 +374,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   sim_t* s = new (std::nothrow) sim_t();
   if (!s) return SIM_ERR_OOM;
   s->cfg = c;
+  if (c.mode == SIM_DIFF) s->cfg.ref_mode = SIM_REF_RESET;  // no reference state
   s->cfg.c_pos_map = nullptr;
   s->cfg.c_neg_map = nullptr;
   s->W = c.width;
@@ -398,7 +408,11 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   chk(dalloc(&s->d_lut, 256));
   chk(dalloc(&s->d_ring[0], P));
   chk(dalloc(&s->d_ring[1], P));
-  if (c.ref_mode == SIM_REF_ACCUM) {
+  if (c.mode == SIM_DIFF) {
+    chk(dalloc(&s->d_ring2[0], P));
+    chk(dalloc(&s->d_ring2[1], P));
+  }
+  if (s->cfg.ref_mode == SIM_REF_ACCUM) {
     chk(dalloc(&s->d_R[0], P));
     chk(dalloc(&s->d_R[1], P));
   }

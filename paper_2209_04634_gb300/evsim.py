@@ -26,7 +26,7 @@ SIM_ERR_TOO_LARGE = -11
 SIM_MAX_GROUP = 1024
 SIM_STATIC_SCRATCH_BYTES = 32 << 20
 SIM_LUMA8, SIM_RGB8 = 1, 3
-SIM_DENSE, SIM_SPARSE = 0, 1
+SIM_DENSE, SIM_SPARSE, SIM_DIFF = 0, 1, 2
 SIM_LOG, SIM_LINEAR = 0, 1
 SIM_REF_ACCUM, SIM_REF_RESET = 0, 1
 SIM_HOST, SIM_DEVICE = 0, 1

@@ -12,6 +12,14 @@ from paper_2209_04634_gb300 import synth
 def oracle_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, intensity=evsim.SIM_LOG,
                ref_mode=evsim.SIM_REF_ACCUM, c_act_q16: int = -1, substeps=None,
                c_pos_q16=None, c_neg_q16=None, use_maps=True) -> dict:
+    if mode == evsim.SIM_DIFF:
+        return oracle.run_diff(seq.frames, seq.flows, seq.t_us,
+                               substeps=seq.substeps if substeps is None else substeps,
+                               max_substeps=seq.max_substeps, intensity=intensity,
+                               c_pos_q16=evsim.q16(seq.c_pos) if c_pos_q16 is None else c_pos_q16,
+                               c_neg_q16=evsim.q16(seq.c_neg) if c_neg_q16 is None else c_neg_q16,
+                               cpos_map=seq.cpos_map if use_maps else None,
+                               cneg_map=seq.cneg_map if use_maps else None)
     return oracle.run(seq.frames, seq.flows, seq.t_us,
                       mode=oracle.SPARSE if mode == evsim.SIM_SPARSE else oracle.DENSE,
                       substeps=seq.substeps if substeps is None else substeps,
@@ -47,6 +55,8 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
     kw["max_batch"] = max_batch
     kw["tile_height"] = tile_height
     sim = evsim.simulator_for(seq, mode, **kw)
+    if mode == evsim.SIM_DIFF:
+        ref_mode = evsim.SIM_REF_RESET  # no reference state
     if batch:
         return _gpu_run_batched(sim, seq, batch, device_inputs, ref_mode)
     out, n_per_frame, ev_per_frame, active = [], [0], [0], [0]
