@@ -335,6 +335,8 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_e2e:
         line["e2e"] = run_e2e(args, seq, sims, stream, work_step)
     if rank == 0 and not args.no_diff:
+        line["accumulate"] = run_accumulate(seq, sims[evsim.SIM_DENSE], frames, flows, stream,
+                                            cap, out)
         line["difference"] = run_difference(args, seq, frames, flows, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(args)
@@ -351,6 +353,44 @@ def run_ours(args, ws, rank, local):
     if rank == 0:
         print(json.dumps(line))
     return 0
+
+
+def run_accumulate(seq, sim, frames, flows, stream, cap, out):
+    """Accumulated event frames (the paper's second output form) of the dense
+    pass: one sim_accumulate launch per frame window (99 per step), device
+    time with CUDA events."""
+    import torch
+
+    from paper_2209_04634_gb300 import evsim
+    sim.reset()
+    sim.push_many(frames, flows, seq.t_us)
+    n, rc = sim.pop_into(out, cap)
+    assert rc == evsim.SIM_OK, rc
+    H, W = seq.height, seq.width
+    t = seq.t_us - seq.t_us[0]
+    acc = torch.zeros((len(t), H, W), dtype=torch.int32, device="cuda")
+
+    def step():
+        for i in range(1, len(t)):
+            evsim.accumulate(out, n, W, H, int(t[i - 1]) + 1, int(t[i]) + 1, acc[i], stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    launches = len(t) - 1
+    return {"what": "sim_accumulate of the dense pass's events, one launch per frame window",
+            "events": n, "launches_per_pass": launches, "ms_per_pass": ms,
+            "us_per_launch": ms * 1e3 / launches,
+            "events_scanned_per_s": n * launches / (ms / 1e3)}
 
 
 def run_difference(args, seq, frames, flows, stream):

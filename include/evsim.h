@@ -228,6 +228,45 @@ const char* sim_strerror(int code);
  * thread return SIM_ERR_CUDA / SIM_ERR_OOM / SIM_ERR_NO_DEVICE. */
 const char* sim_last_cuda_error(void);
 
+/* Accumulated event frame, the paper's second output form (Fig. 1 caption:
+ * "a frame with the accumulated events"): frame[y * width + x] += +1 for
+ * every positive and -1 for every negative event of events[0..n) with
+ * t_begin <= t_us < t_end.  events (n sim_event) and frame (width * height
+ * int32, caller-owned, not cleared first, so windows add up) are device
+ * memory; events outside the frame are skipped.  The work is enqueued on
+ * cuda_stream (NULL: the legacy default stream) and not waited for.  The
+ * sum is exact and independent of the event order (integer atomics).
+ * SIM_ERR_ARG for a negative n, a NULL buffer or a bad size; SIM_ERR_CUDA
+ * if the launch fails. */
+int sim_accumulate(const sim_event* events, int64_t n, int32_t width, int32_t height,
+                   int64_t t_begin, int64_t t_end, int32_t* frame, void* cuda_stream);
+
+/* ---- checkpoint / restore ---------------------------------------------
+ * The paper has no counterpart (it runs recorded sequences end to end).  A
+ * stream's simulation state - committed frame count, the first frame's and
+ * the last committed frame's times, the last frame's luma (SIM_DIFF: and the
+ * frame before it), the reference (SIM_REF_ACCUM) and the statistics - can
+ * be saved to host memory and restored into another handle, so a stream can
+ * move between handles, devices or processes and continue bit-exactly.
+ * Events not yet popped are output, not state: they stay with the source
+ * handle.
+ *
+ * sim_state_size: bytes of a checkpoint of s (a function of its
+ * configuration: a header plus W*H, plus W*H in SIM_DIFF, plus 4*W*H in
+ * SIM_REF_ACCUM).
+ * sim_get_state: waits for s's stream and writes the checkpoint into the
+ * caller's host buffer of exactly that size.  SIM_ERR_STATE if a batch failed
+ * and has not been reported yet (call sim_sync first); SIM_ERR_ARG for a NULL
+ * or wrongly sized buffer.
+ * sim_set_state: replaces s's state (and drops its pending events) with a
+ * checkpoint taken from a handle of the same configuration (size, pixel
+ * format, mode, intensity, reference mode, substeps, thresholds, threshold
+ * maps present; the map contents are the caller's to match).  SIM_ERR_ARG
+ * for a mismatching or malformed checkpoint (nothing changed). */
+int sim_state_size(const sim_t* s, int64_t* bytes);
+int sim_get_state(sim_t* s, void* buf, int64_t bytes);
+int sim_set_state(sim_t* s, const void* buf, int64_t bytes);
+
 /* Library version, "major.minor.patch". */
 const char* sim_version(void);
 

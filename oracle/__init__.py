@@ -104,6 +104,9 @@ def _load():
             lib.orc_run_diff.argtypes = [ctypes.POINTER(OrcConfig), ctypes.c_int32, vp, vp, vp,
                                          vp, vp, vp, ctypes.c_int64, vp, vp, vp]
             lib.orc_run_diff.restype = ctypes.c_int64
+            lib.orc_accumulate.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int64, ctypes.c_int64, vp]
+            lib.orc_accumulate.restype = None
             _lib = lib
     return _lib
 
@@ -240,6 +243,18 @@ def run_diff(frames: np.ndarray, flows: np.ndarray | None, t_us, *, substeps: in
         raise ValueError(f"oracle rejected the input (code {n})")
     return {"events": ev[:n].copy(), "n_per_frame": npf, "ev_per_frame": epf,
             "clamped": int(clamped.value)}
+
+
+def accumulate(events: np.ndarray, W: int, H: int, t_begin: int, t_end: int,
+               frame: np.ndarray | None = None) -> np.ndarray:
+    """orc_accumulate: the accumulated event frame of the events with
+    t_begin <= t < t_end, added to `frame` (a new zero frame if None)."""
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    out = np.zeros((H, W), dtype=np.int32) if frame is None else frame
+    assert out.dtype == np.int32 and out.flags.c_contiguous and out.shape == (H, W)
+    _load().orc_accumulate(ev.ctypes.data if ev.size else None, len(ev), W, H, int(t_begin),
+                           int(t_end), out.ctypes.data)
+    return out
 
 
 def unpack(events: np.ndarray):

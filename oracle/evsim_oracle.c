@@ -360,3 +360,19 @@ int64_t orc_run_diff(const orc_config* c, int32_t n_frames, const uint8_t* frame
   free(L2); free(L1); free(L0); free(Dp); free(Dc); free(Fx); free(Fy);
   return rc < 0 ? rc : n;
 }
+
+/*
+ * Accumulated event frame, the second output form of the methods (Fig. 1
+ * caption: "a frame with the accumulated events"): every event with
+ * t_begin <= t < t_end adds its polarity (+1 / -1) to its pixel.
+ */
+void orc_accumulate(const orc_event* ev, int64_t n, int32_t W, int32_t H, int64_t t_begin,
+                    int64_t t_end, int32_t* frame) {
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t t = ev[i].t;
+    if (t < t_begin || t >= t_end) continue;
+    int32_t x = ev[i].x, y = ev[i].yp >> 1;
+    if (x >= W || y >= H) continue;
+    frame[(int64_t)y * W + x] += (ev[i].yp & 1) ? 1 : -1;
+  }
+}

@@ -104,6 +104,12 @@ int64_t orc_run_diff(const orc_config* cfg, int32_t n_frames, const uint8_t* fra
                      orc_event* out, int64_t cap, int32_t* n_per_frame,
                      int64_t* ev_per_frame, int64_t* clamped_total);
 
+/* Accumulated event frame (Fig. 1 caption): frame[y * W + x] += +1 / -1 for
+ * every positive / negative event with t_begin <= t < t_end (frame not
+ * cleared first; events outside the frame skipped). */
+void orc_accumulate(const orc_event* ev, int64_t n, int32_t W, int32_t H, int64_t t_begin,
+                    int64_t t_end, int32_t* frame);
+
 #ifdef __cplusplus
 }
 #endif

@@ -212,6 +212,8 @@ cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st)
 cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_diff(const SimParams& p, const BatchArg& b, cudaStream_t st);
+cudaError_t launch_accumulate(const Ev* ev, long long n, int W, int H, long long t_begin,
+                              long long t_end, int* frame, cudaStream_t st);
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
 int tile_class(const SimParams& p);

@@ -1837,6 +1837,24 @@ __global__ void __launch_bounds__(NTD, 2) k_diff(SimParams p, BatchArg b) {
   if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
 }
 
+// Accumulated event frame (Fig. 1 caption: the output is either the events or
+// a frame with the accumulated events): every event with t_begin <= t < t_end
+// adds its polarity (+1 / -1) to its pixel.  Integer atomics: the result does
+// not depend on the order the events are visited in.
+__global__ void k_accumulate(const Ev* ev, long long n, int W, int H, long long t_begin,
+                             long long t_end, int* frame) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const Ev e = ev[i];
+    const long long t = e.t;
+    if (t < t_begin || t >= t_end) continue;
+    const int x = (int)(e.xyp & 0xFFFFu), yp = (int)(e.xyp >> 16);
+    const int y = yp >> 1;
+    if (x >= W || y >= H) continue;
+    atomicAdd(frame + (long long)y * W + x, (yp & 1) ? 1 : -1);
+  }
+}
+
 // Adaptive N for the sparse method: max squared flow over the active pixels
 // of each frame.  Warp w of block bx (of nbx) takes rows bx * NWARP + w,
 // + nbx * NWARP, ...; each lane four columns of the row at a time, their
@@ -2488,6 +2506,14 @@ cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st)
 
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st) {
   return launch_tile_mode<true>(p, b, st);
+}
+
+cudaError_t launch_accumulate(const Ev* ev, long long n, int W, int H, long long t_begin,
+                              long long t_end, int* frame, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>((n + NT - 1) / NT, (long long)device_sm_count() * 8);
+  k_accumulate<<<std::max(grid, 1), NT, 0, st>>>(ev, n, W, H, t_begin, t_end, frame);
+  return cudaGetLastError();
 }
 
 size_t diff_smem_bytes(int n_max) { return (size_t)(2 * SH * SW + 256 + 2 * n_max) * 4; }

@@ -636,6 +636,16 @@ int sim_kernel_time(sim_t* s, int32_t kind, double* ms, int64_t* launches, int32
   return SIM_OK;
 }
 
+int sim_accumulate(const sim_event* events, int64_t n, int32_t width, int32_t height,
+                   int64_t t_begin, int64_t t_end, int32_t* frame, void* cuda_stream) {
+  if (n < 0 || (n > 0 && !events) || !frame || width < 1 || height < 1 ||
+      width > SIM_MAX_DIM || height > SIM_MAX_DIM)
+    return SIM_ERR_ARG;
+  cudaError_t e = evsim::launch_accumulate((const Ev*)events, n, width, height, t_begin, t_end,
+                                           frame, (cudaStream_t)cuda_stream);
+  return cuda_rc(e);
+}
+
 int sim_reset(sim_t* s) {
   if (!s) return SIM_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(s->stream);

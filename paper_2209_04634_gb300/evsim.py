@@ -123,6 +123,10 @@ SIGNATURES = [
                                            _I64, ctypes.POINTER(_VP), ctypes.POINTER(_I64), _I32,
                                            ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     ("sim_autotune_save", ctypes.c_int, [ctypes.c_char_p]),
+    ("sim_accumulate", ctypes.c_int, [_VP, _I64, _I32, _I32, _I64, _I64, _VP, _VP]),
+    ("sim_state_size", ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+    ("sim_get_state", ctypes.c_int, [_VP, _VP, _I64]),
+    ("sim_set_state", ctypes.c_int, [_VP, _VP, _I64]),
     ("sim_autotune_load", ctypes.c_int, [ctypes.c_char_p]),
     ("simb_config_default", ctypes.c_int, [ctypes.POINTER(simb_config)]),
     ("simb_create", ctypes.c_int, [ctypes.POINTER(simb_config), ctypes.POINTER(_VP)]),
@@ -335,6 +339,19 @@ class Simulator:
                                         1 if reset else 0), "sim_kernel_time")
         return float(ms.value), int(n.value)
 
+    def get_state(self) -> bytes:
+        """Checkpoint of the stream's simulation state (sim_get_state)."""
+        n = ctypes.c_int64(0)
+        check(self._lib.sim_state_size(self.h, ctypes.byref(n)), "sim_state_size")
+        buf = ctypes.create_string_buffer(int(n.value))
+        check(self._lib.sim_get_state(self.h, buf, n.value), "sim_get_state")
+        return buf.raw
+
+    def set_state(self, state: bytes) -> None:
+        """Restore a checkpoint taken from a handle of the same configuration."""
+        buf = ctypes.create_string_buffer(state, len(state))
+        check(self._lib.sim_set_state(self.h, buf, len(state)), "sim_set_state")
+
     def reset(self) -> None:
         check(self._lib.sim_reset(self.h), "sim_reset")
 
@@ -419,6 +436,16 @@ def autotune_sample(width: int, height: int, frames, flows, t_us, **kw) -> tuple
           "sim_autotune_sample")
     del keep
     return int(th.value), float(us[0]), float(us[1])
+
+
+def accumulate(events, n: int, width: int, height: int, t_begin: int, t_end: int, frame,
+               stream=None) -> None:
+    """sim_accumulate: add the polarities of events[0..n) (a device buffer of
+    sim_event records, e.g. filled by Simulator.pop_into) with
+    t_begin <= t < t_end into frame (a device int32 tensor of height x width)."""
+    s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    check(load().sim_accumulate(_ptr(events), int(n), width, height, int(t_begin), int(t_end),
+                                _ptr(frame), s or None), "sim_accumulate")
 
 
 def autotune_save(path: str) -> None:

@@ -131,3 +131,10 @@ def test_autotune_arguments_and_table_file(lib, tmp_path):
     assert lib.sim_autotune_load(str(bad).encode()) == evsim.SIM_ERR_ARG
     assert lib.sim_autotune_load(str(tmp_path / "missing.txt").encode()) == evsim.SIM_ERR_ARG
     assert lib.sim_autotune_load(None) == evsim.SIM_ERR_ARG
+
+
+def test_checkpoint_argument_errors(lib):
+    n = ctypes.c_int64(0)
+    assert lib.sim_state_size(None, ctypes.byref(n)) == evsim.SIM_ERR_ARG
+    assert lib.sim_get_state(None, None, 0) == evsim.SIM_ERR_ARG
+    assert lib.sim_set_state(None, None, 0) == evsim.SIM_ERR_ARG

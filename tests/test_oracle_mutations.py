@@ -63,6 +63,11 @@ MUTATIONS = {
                                   "if (I >= cp) emit(out, cap, &n, tk, x, y, 1);"),
     "diff_offset_sign": ("int64_t s0 = orc_bilinear(Dp, W, H, p0x, p0y);",
                          "int64_t s0 = orc_bilinear(Dp, W, H, p0x + 2 * offx, p0y);"),
+    "accumulate_polarity_inverted": ("frame[(int64_t)y * W + x] += (ev[i].yp & 1) ? 1 : -1;",
+                                     "frame[(int64_t)y * W + x] += (ev[i].yp & 1) ? -1 : 1;"),
+    "accumulate_window_end_inclusive": ("if (t < t_begin || t >= t_end) continue;",
+                                        "if (t < t_begin || t > t_end) continue;"),
+    "accumulate_transposed": ("frame[(int64_t)y * W + x] +=", "frame[(int64_t)x * H + y] +="),
     "diff_blend_reversed": ("int64_t I = lerp_q12(s0, s1, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)",
                             "int64_t I = lerp_q12(s1, s0, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)"),
 }
@@ -107,6 +112,9 @@ def battery():
             yield lambda N=N, v=v: pins.test_diff_uniform_frames_follow_the_exact_line(N, v)
     for s_, N in [((1, 0), 3), ((0, -1), 4), ((1, 1), 2), ((-2, 1), 2)]:
         yield lambda s_=s_, N=N: pins.test_diff_translation_reproduces_shifted_difference_samples(s_, N)
+    for v0, v1 in [(60, 200), (220, 35), (128, 128)]:
+        yield lambda v0=v0, v1=v1: pins.test_accumulated_frame_of_a_uniform_step(v0, v1)
+    yield pins.test_accumulated_frame_positions_polarity_and_window
 
 
 def test_battery_passes_on_the_real_oracle():

@@ -721,3 +721,42 @@ def test_diff_second_restatement_on_random_8x8(case):
                              cp=cp, cn=cn, linear=linear, max_sub=6)
     t, x, y, p = oracle.unpack(r["events"])
     assert list(zip(t.tolist(), x.tolist(), y.tolist(), p.tolist())) == ev
+
+
+# ---------------------------------------------------------------------------
+# Accumulated event frame (Fig. 1 caption): orc_accumulate
+
+
+@pytest.mark.parametrize("v0,v1", [(60, 200), (220, 35), (128, 128)])
+def test_accumulated_frame_of_a_uniform_step(v0, v1):
+    """A uniform step with no flow gives every pixel floor(|D| / C) events of
+    the step's sign (accumulate mode): the accumulated frame over the whole
+    stream is that signed count at every pixel, and frames of disjoint time
+    windows add up to it."""
+    H, W, C = 6, 9, 13107
+    frames = np.stack([np.full((H, W), v0, np.uint8), np.full((H, W), v1, np.uint8)])
+    r = oracle.run(frames, zero_flows(frames), times(2, 1000), substeps=5,
+                   c_pos_q16=C, c_neg_q16=C)
+    lut = py_lut()
+    d = int(lut[v1] - lut[v0])
+    want = int(np.sign(d)) * (abs(d) // C)
+    acc = oracle.accumulate(r["events"], W, H, 0, 1 << 40)
+    assert np.all(acc == want)
+    parts = np.zeros((H, W), np.int32)
+    for t0 in range(0, 1001, 250):
+        oracle.accumulate(r["events"], W, H, t0, t0 + 250, parts)
+    assert np.array_equal(parts, acc)
+    assert not np.any(oracle.accumulate(r["events"], W, H, 1001, 1 << 40))
+
+
+def test_accumulated_frame_positions_polarity_and_window():
+    ev = np.zeros(5, dtype=oracle.EVENT_DTYPE)
+    ev["t"] = [10, 10, 20, 30, 40]
+    ev["x"] = [3, 3, 0, 6, 2]
+    ev["yp"] = [(1 << 1) | 1, (1 << 1) | 1, (4 << 1) | 0, (0 << 1) | 1, (9 << 1) | 1]
+    acc = oracle.accumulate(ev, 7, 5, 10, 40)  # t = 40 excluded; (2, 9) outside
+    want = np.zeros((5, 7), np.int32)
+    want[1, 3] = 2
+    want[4, 0] = -1
+    want[0, 6] = 1
+    assert np.array_equal(acc, want)
