@@ -662,30 +662,43 @@ __device__ __forceinline__ int floordiv_pos(int d, int c) {
 
 // Dense fast path: the substeps of this thread's two pixels (columns lane and
 // lane + 32 of tile row `warp`, both in the image unless `act` says
-// otherwise), sampling the shared halos; every substep's row segment is
-// published from the loop.  The common case crosses at most one threshold
-// per pixel and substep; a warp in which some pixel crossed two or more
-// computes those pixels' counts exactly afterwards.
-template <bool RESET, bool WIDE>
+// otherwise; FULLT: the whole tile row is in the image), sampling the shared
+// halos; every substep's row segment is published from the loop.  The common
+// case crosses at most one threshold per pixel and substep; a warp in which
+// some pixel crossed two or more computes those pixels' counts exactly
+// afterwards.  MASKS (N <= 32): the carries of the split offset floor(r k / N)
+// come from the frame's carry table cmask[r] (bit 31 - (k - 1) set where the
+// offset steps by one more at substep k), shifted out one bit per substep.
+template <bool RESET, bool WIDE, bool FULLT, bool MASKS>
 __device__ __forceinline__ void dense_substeps(const SimParams& p, const int* swk,
-                                               const unsigned* stk, int N, unsigned mN,
-                                               int tx0, int y,
-                                               unsigned b0, unsigned b1, Seg* segr,
-                                               WarpStage* ws, const bool (&act)[2],
-                                               const int (&Fx)[2], const int (&Fy)[2],
-                                               int (&R)[2], const int (&Cp)[2],
-                                               const int (&Cn)[2]) {
+                                               const unsigned* stk, const unsigned* cmask,
+                                               int N, unsigned mN, int tx0, int y, unsigned b0,
+                                               unsigned b1, Seg* segr, WarpStage* ws,
+                                               const bool (&act)[2], const int (&Fx)[2],
+                                               const int (&Fy)[2], int (&R)[2],
+                                               const int (&Cp)[2], const int (&Cn)[2]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
+  int px[2], py[2], qx[2], qy[2];
+  unsigned ax[2], ay[2], rx[2], ry[2];  // MASKS: carry bits; else Bresenham state
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     px[j] = (lane + 32 * j + HMAX) << 16;
     py[j] = (warp + HMAX) << 16;
     // F = q N + r with 0 <= r < N: offset_k = q k + floor(r k / N)
-    divmod_n(Fx[j], N, mN, qx[j], rx[j]);
-    divmod_n(Fy[j], N, mN, qy[j], ry[j]);
-    ax[j] = 0;
-    ay[j] = 0;
+    int r_x, r_y;
+    divmod_n(Fx[j], N, mN, qx[j], r_x);
+    divmod_n(Fy[j], N, mN, qy[j], r_y);
+    if (MASKS) {
+      ax[j] = cmask[r_x];
+      ay[j] = cmask[r_y];
+      qx[j] = -qx[j];
+      qy[j] = -qy[j];
+    } else {
+      rx[j] = (unsigned)r_x;
+      ry[j] = (unsigned)r_y;
+      ax[j] = 0;
+      ay[j] = 0;
+    }
   }
   for (int k = 0; k < N; ++k) {
     const int w = swk[k];
@@ -693,12 +706,19 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const int* sw
     bool multi = false;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      px[j] -= qx[j];
-      ax[j] += rx[j];
-      if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
-      py[j] -= qy[j];
-      ay[j] += ry[j];
-      if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
+      if (MASKS) {
+        px[j] += qx[j] + ((int)ax[j] >> 31);
+        ax[j] <<= 1;
+        py[j] += qy[j] + ((int)ay[j] >> 31);
+        ay[j] <<= 1;
+      } else {
+        px[j] -= qx[j];
+        ax[j] += rx[j];
+        if (ax[j] >= (unsigned)N) { ax[j] -= N; px[j] -= 1; }
+        py[j] -= qy[j];
+        ay[j] += ry[j];
+        if (ay[j] >= (unsigned)N) { ay[j] -= N; py[j] -= 1; }
+      }
       const int s0 = tap_shared<WIDE>(b0, px[j], py[j]);
       const int s1 = tap_shared<WIDE>(b1, px[j] + Fx[j], py[j] + Fy[j]);
       const int I = lerp12<WIDE>(s0, s1, w);
@@ -709,19 +729,21 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const int* sw
       } else {
         n[j] = d >= Cp[j] ? 1 : (d <= -Cn[j] ? -1 : 0);
         R[j] += n[j] > 0 ? Cp[j] : (n[j] < 0 ? -Cn[j] : 0);
-        multi |= act[j] && (d >= 2 * Cp[j] || d <= -2 * Cn[j]);
+        // a second crossing remains exactly when the residual still crosses
+        const int d2 = I - R[j];
+        multi |= (FULLT || act[j]) && (d2 >= Cp[j] || d2 <= -Cn[j]);
         D[j] = d;
       }
-      if (!act[j]) n[j] = 0;
+      if (!FULLT && !act[j]) n[j] = 0;
     }
     if (!RESET && __any_sync(FULL, multi)) {
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        if (act[j] && D[j] >= 2 * Cp[j]) {
+        if ((FULLT || act[j]) && D[j] >= 2 * Cp[j]) {
           const int m = floordiv_pos<WIDE>(D[j], Cp[j]);
           R[j] += (m - 1) * Cp[j];
           n[j] = m;
-        } else if (act[j] && D[j] <= -2 * Cn[j]) {
+        } else if ((FULLT || act[j]) && D[j] <= -2 * Cn[j]) {
           const int m = floordiv_pos<WIDE>(-D[j], Cn[j]);
           R[j] -= (m - 1) * Cn[j];
           n[j] = -m;
@@ -1260,16 +1282,25 @@ __device__ __forceinline__ void fill_halo_raw(int* dst, const int* slut, const u
 }
 
 // Substep weights and times of one frame (threads k < N) into the parity's
-// tables; thread 0 publishes N and its division multiplier (divmod_n).
-// Called by threads 0..63 only.
+// tables, and for N <= 32 its carry table (dense_substeps); thread 0
+// publishes N and its division multiplier (divmod_n).  Called by threads
+// 0..63 only.
 __device__ __forceinline__ void substep_tables(const SimParams& p, unsigned long long maxf2,
                                                long long t_prev, long long t_cur, int* swk,
-                                               unsigned* stk, int* sN, unsigned* smN) {
+                                               unsigned* stk, int* sN, unsigned* smN,
+                                               unsigned* cmask) {
   const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(maxf2, p.n_max);
   if ((int)threadIdx.x < N) {
     const int k = threadIdx.x + 1;
     swk[threadIdx.x] = (k * 8192 + N) / (2 * N);
     stk[threadIdx.x] = (unsigned)(t_prev + (k * (t_cur - t_prev)) / N);
+    if (N <= 32) {  // carry table of remainder r = threadIdx.x
+      const int r = threadIdx.x;
+      unsigned m = 0;
+      for (int j = 1; j <= N; ++j)
+        if ((r * j) / N != (r * (j - 1)) / N) m |= 1u << (32 - j);
+      cmask[r] = m;
+    }
   }
   if (threadIdx.x == 0) {
     *sN = N;
@@ -1287,6 +1318,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   __shared__ int s_rs[TH + 1];
   __shared__ int s_N[2];
   __shared__ unsigned s_mN[2];
+  __shared__ unsigned s_cmask[2][32];  // carry tables of the frame parities
   __shared__ unsigned s_multi[32];  // sparse: rows with multi-crossings, per substep
   __shared__ __align__(16) FrameDesc s_desc[4];     // frame fi at fi & 3
   __shared__ __align__(8) unsigned long long s_mf[4];  // its squared flow maximum
@@ -1349,7 +1381,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     stage_raw<TH_>(L.raw + SH * RW, FrameRef{d0.frame, d0.pitch, ch}, W, H, tx0, ty0);
     stage_flow<TH_>(L.sflow, d0.flow, W, H, tx0, ty0);
     cp_async_commit();
-    if (tid < 64) substep_tables(p, s_mf[0], t_first, d0.t_rel, L.swk, L.stk, &s_N[0], &s_mN[0]);
+    if (tid < 64)
+      substep_tables(p, s_mf[0], t_first, d0.t_rel, L.swk, L.stk, &s_N[0], &s_mN[0], s_cmask[0]);
     cp_async_wait_all();
   }
   __syncthreads();
@@ -1502,7 +1535,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       cp_async_commit();
       if (tid < 64)
         substep_tables(p, s_mf[(fi + 1) & 3], cur.t_rel, nd.t_rel, L.swk + (par ^ 1) * nmax,
-                       L.stk + (par ^ 1) * nmax, &s_N[par ^ 1], &s_mN[par ^ 1]);
+                       L.stk + (par ^ 1) * nmax, &s_N[par ^ 1], &s_mN[par ^ 1], s_cmask[par ^ 1]);
     }
 
     // 4. substeps (sparse: warps without a compacted pixel skip them); dense
@@ -1515,10 +1548,21 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     const unsigned b0 = smem_addr(pb);
     const unsigned b1 = smem_addr(cb);
     if (!SPARSE && fast) {
-      if (ty0 + warp < H)  // warp-uniform: rows below the image publish nothing
-        dense_substeps<RESET, WIDE>(p, V.swk, V.stk, N, mN, tx0, ty0 + warp, b0, b1,
-                                    segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy, R, Cp,
-                                    Cn);
+      if (ty0 + warp < H) {  // warp-uniform: rows below the image publish nothing
+        const bool fullt = tx0 + TW <= W;  // the row's 64 pixels are in the image
+#define EVSIM_DENSE(FT, MK)                                                                    \
+  dense_substeps<RESET, WIDE, FT, MK>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp, b0, \
+                                      b1, segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy,  \
+                                      R, Cp, Cn)
+        if (N <= 32) {
+          if (fullt) EVSIM_DENSE(true, true);
+          else EVSIM_DENSE(false, true);
+        } else {
+          if (fullt) EVSIM_DENSE(true, false);
+          else EVSIM_DENSE(false, false);
+        }
+#undef EVSIM_DENSE
+      }
     } else if (maskpub) {  // warp-uniform: one pixel per thread when A <= NTD
       if (A <= NTD) {
         if (warp * 32 < A)
