@@ -241,10 +241,10 @@ def run_ours(args, ws, rank, local):
         if args.tile_height:
             tune[name] = {"tile_height": args.tile_height, "fixed": True}
             continue
-        # tuned on a sample of this stream: its first 16 frames
-        th, us16, us8 = evsim.autotune_sample(W, H, frames[:16], flows[:16], seq.t_us[:16],
+        # tuned on a sample of this stream: its first 32 frames
+        th, us16, us8 = evsim.autotune_sample(W, H, frames[:32], flows[:32], seq.t_us[:32],
                                               **evsim.seq_options(seq, mode=m))
-        tune[name] = {"tile_height": th, "sample": "first 16 frames",
+        tune[name] = {"tile_height": th, "sample": "first 32 frames",
                       "us_per_frame_64x16": us16, "us_per_frame_64x8": us8}
     sims = {m: evsim.simulator_for(seq, m, event_capacity=cap, stream=stream,
                                    tile_height=tune["dense" if m == evsim.SIM_DENSE
@@ -252,6 +252,7 @@ def run_ours(args, ws, rank, local):
             for m in (evsim.SIM_DENSE, evsim.SIM_SPARSE)}
     for m, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
         assert sims[m].stats().tile_height == tune[name]["tile_height"]
+        tune[name]["block_order"] = ["linear", "serpentine"][sims[m].stats().block_order]
     t_us = seq.t_us
 
     def step():

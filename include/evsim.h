@@ -139,7 +139,7 @@ typedef struct {
   int64_t pixel_substeps;    /* sum over committed frames of width * height * N */
   int64_t active_substeps;   /* sum over committed frames of (pixels simulated) * N */
   int32_t tile_height;       /* tile height of the batch kernel (8 or 16) */
-  int32_t reserved0;
+  int32_t block_order;       /* its tile order: 0 linear, 1 serpentine (see sim_autotune) */
 } sim_stats;
 
 /* Kernel kinds for sim_kernel_time. */
@@ -273,7 +273,10 @@ const char* sim_version(void);
 /* ---- autotuner -------------------------------------------------------------
  * The paper has no counterpart (it runs one configuration on one machine).
  * The batch kernel comes in two tile shapes: 64 x 16 pixels per 512-thread
- * block (two blocks per SM) and 64 x 8 per 256-thread block (four per SM).
+ * block (two blocks per SM) and 64 x 8 per 256-thread block (four per SM),
+ * and takes its tiles in two block orders: linear, or serpentine (odd rounds
+ * of one block per SM reversed, so that the blocks sharing an SM hold tiles
+ * from opposite ends of the image).
  * The smaller shape has twice the blocks for a frame of a given size - more
  * parallelism for small frames, finer balance across SMs - at the price of
  * a larger halo per pixel.  Which one is faster depends on the frame size,
@@ -284,12 +287,16 @@ const char* sim_version(void);
  * generated on the device
  * (a moving sinusoidal texture with a constant flow of (3.0, -2.0) px per
  * frame; frame and flow content do not depend on the shape), times each
- * kernel launch with CUDA events, and records the faster shape in a
- * process-wide table keyed by (width, height, pixel_format, mode, substeps,
+ * kernel launch with CUDA events, and records the fastest shape and order
+ * (another choice than 64 x 16 in linear order only when it is at least 5 %
+ * faster: a sample's timings scatter by a few percent) in a process-wide
+ * table keyed by (width, height, pixel_format, mode, substeps,
  * max_substeps, intensity, ref_mode, threshold maps present).  sim_create
  * consults the table when cfg->tile_height is SIM_TILE_AUTO or SIM_TILE_TUNE.
  * *tile_height_out (if not NULL) receives 8 or 16; us_out (if not NULL, 2
- * doubles) the kernel time per frame in microseconds of shapes 16 and 8.
+ * doubles) the kernel time per frame in microseconds of shapes 16 and 8
+ * (each in its faster order).  sim_get_stats reports a handle's shape and
+ * order.
  * Allocates two temporary simulators and the probe's frames on the current
  * device and frees them before returning; blocks until done.  Errors:
  * SIM_ERR_ARG (bad configuration or frames), SIM_ERR_OOM, SIM_ERR_CUDA. */
@@ -310,7 +317,8 @@ int sim_autotune_sample(const sim_config* cfg, int32_t count, const void* const*
                         int32_t mem, int32_t* tile_height_out, double* us_out);
 
 /* Write the autotuner table to a text file (one line per configuration:
- * the key's nine fields, the chosen tile height, the two per-frame times),
+ * the key's nine fields, the chosen tile height and block order, the two
+ * per-frame times),
  * or merge such a file into the table (later lines win).  Return SIM_OK or
  * SIM_ERR_ARG (NULL path, unreadable or malformed file: nothing merged). */
 int sim_autotune_save(const char* path);

@@ -23,11 +23,12 @@ namespace {
 using Key = std::tuple<int, int, int, int, int, int, int, int, int>;
 
 struct Entry {
-  int th;
-  double us16, us8;
+  int th, order;
+  double us16, us8;  // best per-frame time of each shape over the block orders
 };
 
 std::mutex g_tune_mu;
+constexpr double kMargin = 0.95;  // another choice than 64x16 / linear only when 5 % faster
 std::map<Key, Entry> g_table;
 
 Key key_of(const sim_config& c) {
@@ -61,7 +62,7 @@ int rc_of(cudaError_t e) { return evsim_rt::cuda_rc(e); }
 // Per-frame time (us) of the simulation kernel of a stream with tile height th
 // on frames[0..count): frame 0 starts the stream, frames 1.. form one batch;
 // run twice (the first pass warms up), the second pass's tile launch timed.
-int time_shape(const sim_config& c, int th, int count, const void* const* frames,
+int time_shape(const sim_config& c, int th, int order, int count, const void* const* frames,
                int64_t pitch, const float* const* flows, const int64_t* t_us, int32_t mem,
                double* us) {
   sim_config tc = c;
@@ -72,6 +73,7 @@ int time_shape(const sim_config& c, int th, int count, const void* const* frames
   sim_t* s = nullptr;
   int rc = sim_create(&tc, &s);
   if (rc) return rc;
+  s->block_order = order;
   const int kind = c.mode == SIM_SPARSE ? SIM_K_SPARSE : SIM_K_DENSE;
   // An event overflow only means the batch did not commit: its kernels ran
   // in full and were timed.
@@ -101,20 +103,30 @@ int valid_cfg(const sim_config& c) {
   return SIM_OK;
 }
 
-// Time both shapes on the frames and record the faster one.
+// Time both shapes in both block orders on the frames and record the
+// fastest; the default (64x16, linear order) unless another choice is at
+// least 5 % faster (a sample's timings scatter by a few percent).
 int tune(const sim_config& c, int count, const void* const* frames, int64_t pitch,
          const float* const* flows, const int64_t* t_us, int32_t mem, int32_t* th_out,
          double* us_out) {
-  double us16 = 0, us8 = 0;
-  int rc = time_shape(c, 16, count, frames, pitch, flows, t_us, mem, &us16);
-  if (!rc) rc = time_shape(c, 8, count, frames, pitch, flows, t_us, mem, &us8);
-  if (rc) return rc;
-  const int th = us8 < us16 ? 8 : 16;
+  const int shapes[2] = {16, 8};
+  double us[2][2] = {{0, 0}, {0, 0}};
+  for (int a = 0; a < 2; ++a)
+    for (int o = 0; o < 2; ++o) {
+      const int rc = time_shape(c, shapes[a], o, count, frames, pitch, flows, t_us, mem, &us[a][o]);
+      if (rc) return rc;
+    }
+  int ba = 0, bo = 0;
+  for (int a = 0; a < 2; ++a)
+    for (int o = 0; o < 2; ++o)
+      if (us[a][o] < us[ba][bo]) { ba = a; bo = o; }
+  if (!(us[ba][bo] < kMargin * us[0][0])) { ba = 0; bo = 0; }
+  const double us16 = std::min(us[0][0], us[0][1]), us8 = std::min(us[1][0], us[1][1]);
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_table[key_of(c)] = Entry{th, us16, us8};
+    g_table[key_of(c)] = Entry{shapes[ba], bo, us16, us8};
   }
-  if (th_out) *th_out = th;
+  if (th_out) *th_out = shapes[ba];
   if (us_out) {
     us_out[0] = us16;
     us_out[1] = us8;
@@ -124,11 +136,12 @@ int tune(const sim_config& c, int count, const void* const* frames, int64_t pitc
 
 }  // namespace
 
-bool evsim_rt::tuned_tile_height(const sim_config& c, int* th) {
+bool evsim_rt::tuned_tile_height(const sim_config& c, int* th, int* order) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   auto it = g_table.find(key_of(c));
   if (it == g_table.end()) return false;
   *th = it->second.th;
+  *order = it->second.order;
   return true;
 }
 
@@ -186,9 +199,10 @@ int sim_autotune_save(const char* path) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   for (const auto& kv : g_table) {
     const Key& k = kv.first;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %.3f %.3f\n", std::get<0>(k), std::get<1>(k),
-                 std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k),
-                 std::get<7>(k), std::get<8>(k), kv.second.th, kv.second.us16, kv.second.us8);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.3f %.3f\n", std::get<0>(k),
+                 std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k),
+                 std::get<6>(k), std::get<7>(k), std::get<8>(k), kv.second.th, kv.second.order,
+                 kv.second.us16, kv.second.us8);
   }
   const bool ok = std::fclose(f) == 0;
   return ok ? SIM_OK : SIM_ERR_ARG;
@@ -202,15 +216,15 @@ int sim_autotune_load(const char* path) {
   char line[512];
   bool bad = false;
   while (std::fgets(line, sizeof(line), f)) {
-    int v[10];
+    int v[11];
     double a = 0, b = 0;
-    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %lf %lf", &v[0], &v[1], &v[2], &v[3],
-                    &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &a, &b) != 12 ||
-        (v[9] != 8 && v[9] != 16)) {
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %lf %lf", &v[0], &v[1], &v[2], &v[3],
+                    &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10], &a, &b) != 13 ||
+        (v[9] != 8 && v[9] != 16) || (v[10] != 0 && v[10] != 1)) {
       bad = true;
       break;
     }
-    add[Key{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]}] = Entry{v[9], a, b};
+    add[Key{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]}] = Entry{v[9], v[10], a, b};
   }
   std::fclose(f);
   if (bad) return SIM_ERR_ARG;

@@ -25,6 +25,7 @@ struct sim_s {
   int n_max = 0;
   int tiles_x = 0, tiles_y = 0;
   int tile_h = 16;             // batch kernel tile height (8 or 16)
+  int block_order = 0;         // batch kernel tile order: 0 linear, 1 serpentine
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
@@ -91,6 +92,6 @@ int recover(sim_t* s, Ctl* c);
 // Device bytes sim_create allocates for a configuration (before host staging grows).
 long long state_bytes(const sim_config& c);
 // The autotuner's tile height for a configuration, if its table has one.
-bool tuned_tile_height(const sim_config& c, int* th);
+bool tuned_tile_height(const sim_config& c, int* th, int* order);
 
 }  // namespace evsim_rt

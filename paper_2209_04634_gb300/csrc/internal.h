@@ -109,7 +109,8 @@ struct SimParams {
   int bmax;                     // frames per batch the segment table holds
   int stage_chunk;              // staging chunk per warp of the batch kernel (0: exact)
   int tile_h;                   // batch kernel tile height: 16 (512 threads) or 8 (256)
-  int pad_tile;
+  int sms;                      // SMs of the device (block placement of the batch kernel)
+  int block_order;              // batch kernel: 0 tiles in block order, 1 serpentine
   const unsigned short* cpmap;
   const unsigned short* cnmap;
   const int* lut;               // 256 Q16 entries (device)

@@ -1680,9 +1680,24 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 // One stream's batch: one block per tile carries the tile through every
 // frame of the batch, its inputs staged a frame ahead (blocks never wait for
 // one another).
+// Tile of block b in serpentine order (one of the autotuner's choices):
+// blocks are placed on the SMs in rounds of one block per SM, and the blocks
+// of consecutive rounds share SMs.  Odd rounds take their tiles in reverse
+// order, so the blocks sharing an SM hold tiles from opposite ends of the
+// image: where activity is concentrated in one region, its tiles do not pile
+// up on the same SMs.  Tiles are independent, so the order changes only the
+// schedule.
+__device__ __forceinline__ int serpentine_tile(int b, int T, int S) {
+  if (S < 1) return b;
+  const int r = b / S, j = b - r * S;
+  const int size = min(S, T - r * S);
+  return r * S + ((r & 1) ? size - 1 - j : j);
+}
+
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_>
 __global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile(SimParams p, BatchArg b) {
-  tile_batch<RESET, MAPS, WIDE, SPARSE, TH_>(p, b, blockIdx.x);
+  tile_batch<RESET, MAPS, WIDE, SPARSE, TH_>(
+      p, b, p.block_order ? serpentine_tile(blockIdx.x, gridDim.x, p.sms) : (int)blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -110,6 +110,8 @@ evsim::SimParams make_params(const sim_t* s) {
   p.tiles_x = s->tiles_x;
   p.tiles_y = s->tiles_y;
   p.tile_h = s->tile_h;
+  p.sms = s->sms;
+  p.block_order = s->block_order;
   p.mode = s->cfg.mode;
   p.ref_mode = s->cfg.ref_mode;
   p.intensity = s->cfg.intensity;
@@ -358,17 +360,25 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SIM_ERR_NO_DEVICE;
 
   // tile shape: fixed, or the autotuner's choice for this configuration
-  int th = c.tile_height;
+  int th = c.tile_height, order = 0, tth = 16, torder = 0;
+  const bool tuned = tuned_tile_height(c, &tth, &torder);
   if (th != 8 && th != 16) {
-    if (!tuned_tile_height(c, &th)) {
+    if (tuned) {
+      th = tth;
+      order = torder;
+    } else {
       th = 16;
       if (c.tile_height == SIM_TILE_TUNE) {
         int32_t t = 16;
         const int rc = sim_autotune(&c, 8, &t, nullptr);
         if (rc) return rc;
+        tuned_tile_height(c, &tth, &torder);
         th = t;
+        order = torder;
       }
     }
+  } else if (tuned && tth == th) {
+    order = torder;  // a fixed shape keeps the tuned order for that shape
   }
 
   sim_t* s = new (std::nothrow) sim_t();
@@ -384,6 +394,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   s->n_max = c.substeps > 0 ? c.substeps : c.max_substeps;
   s->tiles_x = (c.width + evsim::TW - 1) / evsim::TW;
   s->tile_h = th;
+  s->block_order = order;
   s->tiles_y = (c.height + th - 1) / th;
   cudaGetDevice(&s->device);
   s->sms = std::max(1, evsim::device_sm_count());
@@ -603,6 +614,7 @@ int sim_get_stats(sim_t* s, sim_stats* st) {
   st->pixel_substeps = c.work_px;
   st->active_substeps = c.work_active;
   st->tile_height = s->tile_h;
+  st->block_order = s->block_order;
   return SIM_OK;
 }
 

@@ -172,6 +172,7 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   p.tiles_x = tiles_x;
   p.tiles_y = tiles_y;
   p.tile_h = evsim::TH;
+  p.sms = evsim::device_sm_count();
   p.mode = c.mode;
   p.ref_mode = c.ref_mode;
   p.intensity = c.intensity;

@@ -61,7 +61,7 @@ class sim_stats(ctypes.Structure):
         ("flow_clamped", ctypes.c_int64), ("last_substeps", ctypes.c_int32),
         ("max_batch", ctypes.c_int32), ("pixel_substeps", ctypes.c_int64),
         ("active_substeps", ctypes.c_int64),
-        ("tile_height", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("tile_height", ctypes.c_int32), ("block_order", ctypes.c_int32),
     ]
 
 
