@@ -252,7 +252,8 @@ def run_ours(args, ws, rank, local):
             for m in (evsim.SIM_DENSE, evsim.SIM_SPARSE)}
     for m, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
         assert sims[m].stats().tile_height == tune[name]["tile_height"]
-        tune[name]["block_order"] = ["linear", "serpentine"][sims[m].stats().block_order]
+        tune[name]["block_order"] = ["linear", "serpentine", "balanced"][
+            sims[m].stats().block_order]
     t_us = seq.t_us
 
     def step():

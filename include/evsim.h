@@ -139,7 +139,8 @@ typedef struct {
   int64_t pixel_substeps;    /* sum over committed frames of width * height * N */
   int64_t active_substeps;   /* sum over committed frames of (pixels simulated) * N */
   int32_t tile_height;       /* tile height of the batch kernel (8 or 16) */
-  int32_t block_order;       /* its tile order: 0 linear, 1 serpentine (see sim_autotune) */
+  int32_t block_order;       /* its tile order: 0 linear, 1 serpentine, 2 balanced
+                                (see sim_autotune) */
 } sim_stats;
 
 /* Kernel kinds for sim_kernel_time. */
@@ -274,9 +275,12 @@ const char* sim_version(void);
  * The paper has no counterpart (it runs one configuration on one machine).
  * The batch kernel comes in two tile shapes: 64 x 16 pixels per 512-thread
  * block (two blocks per SM) and 64 x 8 per 256-thread block (four per SM),
- * and takes its tiles in two block orders: linear, or serpentine (odd rounds
- * of one block per SM reversed, so that the blocks sharing an SM hold tiles
- * from opposite ends of the image).
+ * and takes its tiles in one of three block orders: linear; serpentine (odd
+ * rounds of one block per SM reversed, so that the blocks sharing an SM hold
+ * tiles from opposite ends of the image); or balanced (each batch records
+ * how long each tile's block took, and the next batch places the tiles in
+ * serpentine order over that ranking, so that the heaviest tile shares its
+ * SM with the lightest; frames up to 4096 tiles).
  * The smaller shape has twice the blocks for a frame of a given size - more
  * parallelism for small frames, finer balance across SMs - at the price of
  * a larger halo per pixel.  Which one is faster depends on the frame size,

@@ -103,25 +103,33 @@ int valid_cfg(const sim_config& c) {
   return SIM_OK;
 }
 
-// Time both shapes in both block orders on the frames and record the
-// fastest; the default (64x16, linear order) unless another choice is at
-// least 5 % faster (a sample's timings scatter by a few percent).
+// Time both shapes in each block order (linear, serpentine, balanced) on the
+// frames and record the fastest; the default (64x16, linear order) unless
+// another choice is at least 5 % faster (a sample's timings scatter by a few
+// percent).  The balanced order's timed pass runs on the plan its warm-up
+// pass measured.
 int tune(const sim_config& c, int count, const void* const* frames, int64_t pitch,
          const float* const* flows, const int64_t* t_us, int32_t mem, int32_t* th_out,
          double* us_out) {
   const int shapes[2] = {16, 8};
-  double us[2][2] = {{0, 0}, {0, 0}};
+  const long long T16 = ((c.width + 63) / 64) * (long long)((c.height + 15) / 16);
+  const int norders = T16 * 2 <= evsim::PLAN_MAX_TILES ? 3 : 2;  // balanced needs a plan
+  double us[2][3] = {{0, 0, 0}, {0, 0, 0}};
   for (int a = 0; a < 2; ++a)
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < norders; ++o) {
       const int rc = time_shape(c, shapes[a], o, count, frames, pitch, flows, t_us, mem, &us[a][o]);
       if (rc) return rc;
     }
   int ba = 0, bo = 0;
   for (int a = 0; a < 2; ++a)
-    for (int o = 0; o < 2; ++o)
+    for (int o = 0; o < norders; ++o)
       if (us[a][o] < us[ba][bo]) { ba = a; bo = o; }
   if (!(us[ba][bo] < kMargin * us[0][0])) { ba = 0; bo = 0; }
-  const double us16 = std::min(us[0][0], us[0][1]), us8 = std::min(us[1][0], us[1][1]);
+  double us16 = us[0][0], us8 = us[1][0];
+  for (int o = 1; o < norders; ++o) {
+    us16 = std::min(us16, us[0][o]);
+    us8 = std::min(us8, us[1][o]);
+  }
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_table[key_of(c)] = Entry{shapes[ba], bo, us16, us8};
@@ -220,7 +228,7 @@ int sim_autotune_load(const char* path) {
     double a = 0, b = 0;
     if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %lf %lf", &v[0], &v[1], &v[2], &v[3],
                     &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10], &a, &b) != 13 ||
-        (v[9] != 8 && v[9] != 16) || (v[10] != 0 && v[10] != 1)) {
+        (v[9] != 8 && v[9] != 16) || v[10] < 0 || v[10] > 2) {
       bad = true;
       break;
     }

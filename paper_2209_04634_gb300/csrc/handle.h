@@ -25,7 +25,9 @@ struct sim_s {
   int n_max = 0;
   int tiles_x = 0, tiles_y = 0;
   int tile_h = 16;             // batch kernel tile height (8 or 16)
-  int block_order = 0;         // batch kernel tile order: 0 linear, 1 serpentine
+  int block_order = 0;         // batch kernel tile order: 0 linear, 1 serpentine, 2 balanced
+  unsigned int* d_tile_cost = nullptr;  // balanced order: cycles per tile of the last batch
+  int* d_tile_order = nullptr;          // balanced order: tile of each block
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;

@@ -110,7 +110,10 @@ struct SimParams {
   int stage_chunk;              // staging chunk per warp of the batch kernel (0: exact)
   int tile_h;                   // batch kernel tile height: 16 (512 threads) or 8 (256)
   int sms;                      // SMs of the device (block placement of the batch kernel)
-  int block_order;              // batch kernel: 0 tiles in block order, 1 serpentine
+  int block_order;              // batch kernel: 0 tiles in block order, 1 serpentine,
+                                // 2 balanced by the previous batch's tile costs
+  unsigned int* tile_cost;      // balanced order: [tiles] cycles of each tile's last batch
+  int* tile_order;              // balanced order: [tiles] tile of each block
   const unsigned short* cpmap;
   const unsigned short* cnmap;
   const int* lut;               // 256 Q16 entries (device)
@@ -215,6 +218,10 @@ cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st
 cudaError_t launch_diff(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_accumulate(const Ev* ev, long long n, int W, int H, long long t_begin,
                               long long t_end, int* frame, cudaStream_t st);
+// Balanced block order: rank the tiles by their last batch's cost and lay
+// them out for the next batch (one block).
+cudaError_t launch_plan(const SimParams& p, cudaStream_t st);
+constexpr int PLAN_MAX_TILES = 4096;  // tiles a balanced plan covers
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
 int tile_class(const SimParams& p);

@@ -1320,6 +1320,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   __shared__ unsigned s_mN[2];
   __shared__ unsigned s_cmask[2][32];  // carry tables of the frame parities
   __shared__ unsigned s_multi[32];  // sparse: rows with multi-crossings, per substep
+  __shared__ unsigned char s_act[TP];  // sparse: activity of each tile pixel
   __shared__ __align__(16) FrameDesc s_desc[4];     // frame fi at fi & 3
   __shared__ __align__(8) unsigned long long s_mf[4];  // its squared flow maximum
   __shared__ WarpStage s_stage[NTD / 32];
@@ -1430,6 +1431,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         }
       }
       sel_flag[q] = a ? 1 : 0;
+      if (SPARSE) s_act[own[q]] = (unsigned char)sel_flag[q];
     }
     if (SPARSE) {
       const int packed = block_excl_scan<NTD>(sel_flag[0] | (sel_flag[1] << 16), s_warp, &A);
@@ -1450,6 +1452,10 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     }
     act_sum += A;
     act_n += (long long)A * N;
+    // sparse tiles with at least half their pixels active run the frame
+    // through the dense loop (inactive pixels masked, their reference kept):
+    // cheaper per pixel than compaction, per-slot records and mask atomics
+    const bool dsw = SPARSE && 2 * A >= TP;
 
     // 2. the simulated pixels of this thread and their (staged) flow; the
     // tile's reach
@@ -1460,7 +1466,11 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       int slot;
-      if (SPARSE) {
+      if (dsw) {  // the dense mapping: columns lane, lane + 32 of row warp
+        slot = warp * TW + lane + 32 * q;
+        act[q] = s_act[slot] != 0;
+        nk_at[q] = slot;
+      } else if (SPARSE) {
         const int j = tid + q * NTD;
         act[q] = j < A;
         slot = act[q] ? L.sslot[j] : 0;
@@ -1500,7 +1510,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     const bool fast = hx <= HMAX && hy <= HMAX;
     // sparse fast path: row masks in the current flow buffer (its flows are
     // in registers by now), cleared here
-    const bool maskpub = SPARSE && fast && N <= 32;
+    const bool maskpub = SPARSE && !dsw && fast && N <= 32;
     unsigned* rowm = (unsigned*)(L.sflow + par * TP);
     if (maskpub) {
       for (int i = tid; i < N * TH * 4; i += NTD) rowm[i] = 0u;
@@ -1547,9 +1557,19 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     V.snk = L.snk;
     const unsigned b0 = smem_addr(pb);
     const unsigned b1 = smem_addr(cb);
-    if (!SPARSE && fast) {
+    if (SPARSE && dsw && !(fast && N <= 32)) {
+      if (fast)
+        tile_substeps<RESET, WIDE, true, true, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
+                                                    lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
+                                                    &s_stage[warp]);
+      else
+        tile_substeps<RESET, WIDE, false, true, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur,
+                                                     segf, lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
+                                                     &s_stage[warp]);
+    } else if ((!SPARSE || dsw) && fast) {
       if (ty0 + warp < H) {  // warp-uniform: rows below the image publish nothing
-        const bool fullt = tx0 + TW <= W;  // the row's 64 pixels are in the image
+        // the row's 64 pixels are in the image (and, sparse, all simulated)
+        const bool fullt = !SPARSE && tx0 + TW <= W;
 #define EVSIM_DENSE(FT, MK)                                                                    \
   dense_substeps<RESET, WIDE, FT, MK>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp, b0, \
                                       b1, segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy,  \
@@ -1623,7 +1643,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
                       n_hi, col_hi, v_hi, V.stk[k], tx0, y, &s_stage[warp]);
         }
       }
-    } else if (SPARSE) {
+    } else if (SPARSE && !dsw) {
       __syncthreads();
       const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
       const int y = ty0 + r;
@@ -1696,8 +1716,13 @@ __device__ __forceinline__ int serpentine_tile(int b, int T, int S) {
 
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_>
 __global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile(SimParams p, BatchArg b) {
-  tile_batch<RESET, MAPS, WIDE, SPARSE, TH_>(
-      p, b, p.block_order ? serpentine_tile(blockIdx.x, gridDim.x, p.sms) : (int)blockIdx.x);
+  const int bi = blockIdx.x;
+  const int tile = p.block_order == 2 ? p.tile_order[bi]
+                   : p.block_order == 1 ? serpentine_tile(bi, gridDim.x, p.sms)
+                                        : bi;
+  const long long c0 = clock64();
+  tile_batch<RESET, MAPS, WIDE, SPARSE, TH_>(p, b, tile);
+  if (p.tile_cost && threadIdx.x == 0) p.tile_cost[tile] = (unsigned)((clock64() - c0) >> 8);
 }
 
 // ---------------------------------------------------------------------------
@@ -1912,6 +1937,27 @@ __global__ void k_accumulate(const Ev* ev, long long n, int W, int H, long long 
     if (x >= W || y >= H) continue;
     atomicAdd(frame + (long long)y * W + x, (yp & 1) ? 1 : -1);
   }
+}
+
+// Balanced block order for the next batch (one block): tiles ranked by the
+// cycles their blocks took in the last batch (heaviest first, ties by tile
+// index), laid out in serpentine order over the ranks - round 0 of one block
+// per SM takes the heaviest tiles, round 1 the lightest in reverse - so the
+// heaviest tile shares its SM with the lightest.  An order of the tiles like
+// any other: it changes only the schedule.
+__global__ void k_plan(int T, int S, const unsigned* cost, int* order) {
+  __shared__ unsigned sc[PLAN_MAX_TILES];
+  __shared__ int sorted[PLAN_MAX_TILES];
+  for (int t = threadIdx.x; t < T; t += blockDim.x) sc[t] = cost[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    const unsigned c = sc[t];
+    int rank = 0;
+    for (int u = 0; u < T; ++u) rank += sc[u] > c || (sc[u] == c && u < t);
+    sorted[rank] = t;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < T; b += blockDim.x) order[b] = sorted[serpentine_tile(b, T, S)];
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
@@ -2572,6 +2618,13 @@ cudaError_t launch_accumulate(const Ev* ev, long long n, int W, int H, long long
   if (n <= 0) return cudaSuccess;
   const int grid = (int)std::min<long long>((n + NT - 1) / NT, (long long)device_sm_count() * 8);
   k_accumulate<<<std::max(grid, 1), NT, 0, st>>>(ev, n, W, H, t_begin, t_end, frame);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const SimParams& p, cudaStream_t st) {
+  const int T = p.tiles_x * p.tiles_y;
+  if (T > PLAN_MAX_TILES || !p.tile_cost || !p.tile_order) return cudaSuccess;
+  k_plan<<<1, 1024, 0, st>>>(T, p.sms, p.tile_cost, p.tile_order);
   return cudaGetLastError();
 }
 

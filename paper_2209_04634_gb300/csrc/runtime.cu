@@ -86,6 +86,8 @@ void free_all(sim_t* s) {
   cudaFree(s->d_R[1]);
   cudaFree(s->d_ctl);
   cudaFree(s->d_maxf2);
+  cudaFree(s->d_tile_cost);
+  cudaFree(s->d_tile_order);
   cudaFree(s->d_staging);
   cudaFree(s->d_events);
   cudaFree(s->d_seg);
@@ -112,7 +114,8 @@ evsim::SimParams make_params(const sim_t* s) {
   p.tile_h = s->tile_h;
   p.sms = s->sms;
   p.block_order = s->block_order;
-  p.mode = s->cfg.mode;
+  p.tile_cost = s->block_order == 2 ? s->d_tile_cost : nullptr;
+  p.tile_order = s->d_tile_order;  p.mode = s->cfg.mode;
   p.ref_mode = s->cfg.ref_mode;
   p.intensity = s->cfg.intensity;
   p.n_fixed = s->cfg.substeps;
@@ -264,12 +267,15 @@ cudaError_t enqueue_batch(sim_t* s, int n) {
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_diff(p, b, s->stream); });
     else
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, b, s->stream); });
+    if (e == cudaSuccess && s->block_order == 2 && s->cfg.mode != SIM_DIFF)
+      e = evsim::launch_plan(p, s->stream);
   } else {
     if (adaptive) {
       e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, b, s->stream); });
       if (e != cudaSuccess) return e;
     }
     e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, b, s->stream); });
+    if (e == cudaSuccess && s->block_order == 2) e = evsim::launch_plan(p, s->stream);
   }
   if (e != cudaSuccess) return e;
   return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, b, s->stream, s->order_grid); });
@@ -428,6 +434,23 @@ int sim_create(const sim_config* cfg, sim_t** out) {
     chk(dalloc(&s->d_R[1], P));
   }
   chk(dalloc(&s->d_ctl, 1));
+  {
+    // balanced block order: per-tile costs of the last batch and the plan,
+    // identity until a batch has been measured
+    const int T = s->tiles_x * s->tiles_y;
+    if (T <= evsim::PLAN_MAX_TILES) {
+      chk(dalloc(&s->d_tile_cost, T));
+      chk(dalloc(&s->d_tile_order, T));
+      if (e == cudaSuccess) {
+        std::vector<int> id(T);
+        for (int t = 0; t < T; ++t) id[t] = t;
+        chk(cudaMemcpy(s->d_tile_order, id.data(), T * sizeof(int), cudaMemcpyHostToDevice));
+        chk(cudaMemset(s->d_tile_cost, 0, T * sizeof(unsigned)));
+      }
+    } else if (s->block_order == 2) {
+      s->block_order = 0;
+    }
+  }
   chk(dalloc(&s->d_maxf2, s->bmax));
   chk(dalloc(&s->d_staging, z.stage));
   chk(dalloc(&s->d_events, cap));

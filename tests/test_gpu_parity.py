@@ -447,3 +447,20 @@ def test_autotune_on_a_sample_of_the_stream(device):
     # the sample's own events are unaffected: a stream run afterwards matches the oracle
     g = gpu_run(seq, evsim.SIM_SPARSE)
     assert_same_events(g["events"], oracle_run(seq, evsim.SIM_SPARSE)["events"], "after tuning")
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
+def test_block_orders_give_the_oracle_events(order, mode, tmp_path):
+    """The serpentine and the balanced block orders (set through an autotuner
+    table) only reschedule the tiles: the events stay the oracle's, over
+    several batches (the balanced order's plan comes from the batch before)."""
+    seq = random_seq(90, 200, F=7, seed=31 + order, substeps=3)
+    f = tmp_path / "table.txt"
+    f.write_text(f"200 90 1 {mode} 3 0 0 0 0 16 {order} 1.0 1.0\n")
+    evsim.autotune_load(str(f))
+    g = gpu_run(seq, mode, use_maps=False, batch=2)
+    assert g["stats"].block_order == order and g["stats"].tile_height == 16
+    o = oracle_run(seq, mode, use_maps=False)
+    assert_same_events(g["events"], o["events"], f"block order {order}")
+    assert np.array_equal(g["R"], o["R"])
