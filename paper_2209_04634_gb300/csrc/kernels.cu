@@ -1452,10 +1452,10 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     }
     act_sum += A;
     act_n += (long long)A * N;
-    // sparse tiles with at least half their pixels active run the frame
+    // sparse tiles with at least 3/8 of their pixels active run the frame
     // through the dense loop (inactive pixels masked, their reference kept):
     // cheaper per pixel than compaction, per-slot records and mask atomics
-    const bool dsw = SPARSE && 2 * A >= TP;
+    const bool dsw = SPARSE && 8 * A >= 3 * TP;
 
     // 2. the simulated pixels of this thread and their (staged) flow; the
     // tile's reach
