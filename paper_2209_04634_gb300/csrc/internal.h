@@ -23,8 +23,9 @@ constexpr int HMAX = 16;
 constexpr int SW = TW + 2 * HMAX;  // shared tile stride (int32 elements)
 constexpr int SH = TH + 2 * HMAX;
 constexpr int MAXN = 64;           // largest substep count
-// Order kernel: segments per chunk (one per thread).
-constexpr int OCHUNK = NT;
+// Order kernel: segments per chunk (OSEG per thread).
+constexpr int OSEG = 4;
+constexpr int OCHUNK = NT * OSEG;
 // Staging chunk of one warp of the batch tile kernel (events).  A stream's
 // staging area holds 4/3 of its event capacity plus one chunk per warp of its
 // tiles, so chunking never turns a batch that fits into an overflow.

@@ -2051,7 +2051,7 @@ struct OrderSmem {
   int N[SIM_MAX_BATCH];  // substeps of each frame of the batch
   int FN[SIM_MAX_BATCH + 1];  // substeps of the frames before each frame
   int warp[NWARP + 1];
-  int cblk[OCHUNK];      // segments of the chunk with per-pixel counts
+  short cblk[OCHUNK];    // segments of the chunk with per-pixel counts
   int ncblk;
   int last;
   long long prefix;
@@ -2092,22 +2092,27 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
   // index beyond them (a ticket range sized for n_max substeps) is empty
   const long long nlive = (long long)o.FN[b.count] * S;
   if ((long long)c * OCHUNK >= nlive) return;
-  // one segment per thread
-  const long long si = (long long)c * OCHUNK + tid;
-  int cnt = 0, src = -1;
-  unsigned long long mask = 0, pol = 0;
-  unsigned tk = 0, xy = 0;
-  if (si < nlive) {
-    const long long q = si / S;  // frame-substep of the batch
-    const int rs = (int)(si - q * S);
-    int fi = 0, hi = b.count;
-    while (hi - fi > 1) {
-      const int mid = (fi + hi) >> 1;
-      if (o.FN[mid] <= q) fi = mid; else hi = mid;
-    }
-    const int k = (int)(q - o.FN[fi]);
-    const int N = o.N[fi];
-    {
+  // OSEG segments per thread: loaded interleaved (segment u * NT + tid, so a
+  // warp's loads are contiguous) into the chunk's arrays, then scanned with
+  // each thread owning OSEG consecutive segments
+  if (tid == 0) o.ncblk = 0;
+#pragma unroll
+  for (int u = 0; u < OSEG; ++u) {
+    const int ls = u * NT + tid;  // segment of the chunk
+    const long long si = (long long)c * OCHUNK + ls;
+    int cnt = 0, src = -1;
+    unsigned long long mask = 0, pol = 0;
+    unsigned tk = 0, xy = 0;
+    if (si < nlive) {
+      const long long q = si / S;  // frame-substep of the batch
+      const int rs = (int)(si - q * S);
+      int fi = 0, hi = b.count;
+      while (hi - fi > 1) {
+        const int mid = (fi + hi) >> 1;
+        if (o.FN[mid] <= q) fi = mid; else hi = mid;
+      }
+      const int k = (int)(q - o.FN[fi]);
+      const int N = o.N[fi];
       const Seg sg = p.seg[((long long)fi * p.n_max + k) * S + rs];
       cnt = sg.cnt;
       src = sg.src;
@@ -2119,17 +2124,30 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
       const long long dt = b.frames[fi].t_rel - tp;
       tk = (unsigned)(tp + ((long long)(k + 1) * dt) / N);
     }
+    o.ex[ls] = cnt;
+    o.src[ls] = src;
+    o.mask[ls] = mask;
+    o.pol[ls] = pol;
+    o.t[ls] = tk;
+    o.xy[ls] = xy;
   }
-  if (tid == 0) o.ncblk = 0;
+  __syncthreads();
+  int mine = 0;
+  int cnts[OSEG];
+#pragma unroll
+  for (int u = 0; u < OSEG; ++u) {
+    cnts[u] = o.ex[tid * OSEG + u];
+    mine += cnts[u];
+  }
   int total;
-  const int ex = block_excl_scan(cnt, o.warp, &total);
-  if (src <= -2 && cnt > 0) o.cblk[atomicAdd(&o.ncblk, 1)] = tid;
-  o.ex[tid] = ex;
-  o.src[tid] = src;
-  o.mask[tid] = mask;
-  o.pol[tid] = pol;
-  o.t[tid] = tk;
-  o.xy[tid] = xy;
+  int ex = block_excl_scan(mine, o.warp, &total);
+#pragma unroll
+  for (int u = 0; u < OSEG; ++u) {
+    const int ls = tid * OSEG + u;
+    o.ex[ls] = ex;
+    if (o.src[ls] <= -2 && cnts[u] > 0) o.cblk[atomicAdd(&o.ncblk, 1)] = (short)ls;
+    ex += cnts[u];
+  }
   if (tid < 32) {
     const long long ex0 = lookback_warp(p.order_status, c, b.serial, total, &ctl->err);
     if (tid == 0) o.prefix = ex0;
