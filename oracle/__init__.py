@@ -8,7 +8,8 @@ it, and the two share no code: this package holds its own C source
 
 ``run()`` is a ctypes wrapper of ``orc_run`` (the whole per-stream method of
 Sec. III-A / III-B of Ziegler et al., arXiv 2209.04634, as restated in
-``evsim_oracle.c``); ``run_diff()`` wraps ``orc_run_diff`` (the
+``evsim_oracle.c``; ``event_time=T_CROSSING`` gives each threshold crossing
+its own time inside its interpolation step, ``orc_crossing_time``); ``run_diff()`` wraps ``orc_run_diff`` (the
 difference-frame interpolation of Sec. III-C).  ``exact.py`` is a second, pixel-major restatement in
 pure Python integers for tiny inputs.
 
@@ -37,6 +38,7 @@ EVENT_DTYPE = np.dtype([("t", "<u4"), ("x", "<u2"), ("yp", "<u2")])
 DENSE, SPARSE = 0, 1
 LOG, LINEAR = 0, 1
 ACCUM, RESET = 0, 1
+T_SUBSTEP, T_CROSSING = 0, 1
 
 
 class OrcConfig(ctypes.Structure):
@@ -52,6 +54,7 @@ class OrcConfig(ctypes.Structure):
         ("c_pos_q16", ctypes.c_int32),
         ("c_neg_q16", ctypes.c_int32),
         ("c_act_q16", ctypes.c_int32),
+        ("event_time", ctypes.c_int32),
     ]
 
 
@@ -97,6 +100,8 @@ def _load():
             lib.orc_bilinear.restype = ctypes.c_int32
             lib.orc_adaptive_substeps.argtypes = [ctypes.c_int64, ctypes.c_int32]
             lib.orc_adaptive_substeps.restype = ctypes.c_int32
+            lib.orc_crossing_time.argtypes = [ctypes.c_int64] * 5 + [ctypes.c_int32]
+            lib.orc_crossing_time.restype = ctypes.c_int64
             vp = ctypes.c_void_p
             lib.orc_run.argtypes = [ctypes.POINTER(OrcConfig), ctypes.c_int32, vp, vp, vp,
                                     vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp]
@@ -137,6 +142,14 @@ def adaptive_substeps(max_f2: int, max_substeps: int) -> int:
     return int(_load().orc_adaptive_substeps(max_f2, max_substeps))
 
 
+def crossing_time(t_prev: int, t_cur: int, i_prev: int, i_cur: int, level: int,
+                  rising: bool) -> int:
+    """orc_crossing_time: the time at which a value moving linearly from i_prev
+    (at t_prev) to i_cur (at t_cur) reaches `level` (floor; t_prev for a level
+    at or behind i_prev)."""
+    return int(_load().orc_crossing_time(t_prev, t_cur, i_prev, i_cur, level, int(rising)))
+
+
 def q16(c: float) -> int:
     """Host conversion of a threshold in log (or 8-bit) units to Q16."""
     return int(round(abs(float(c)) * 65536.0))
@@ -146,7 +159,8 @@ def run(frames: np.ndarray, flows: np.ndarray | None, t_us, *, mode: int = DENSE
         substeps: int = 8, max_substeps: int = 64, intensity: int = LOG,
         ref_mode: int = ACCUM, c_pos_q16: int = 13107, c_neg_q16: int = 13107,
         c_act_q16: int = -1, cpos_map: np.ndarray | None = None,
-        cneg_map: np.ndarray | None = None, cap: int | None = None) -> dict:
+        cneg_map: np.ndarray | None = None, cap: int | None = None,
+        event_time: int = T_SUBSTEP) -> dict:
     """Run the oracle over a whole sequence.
 
     frames: (F, H, W) uint8 luma or (F, H, W, 3) uint8 RGB.
@@ -165,7 +179,7 @@ def run(frames: np.ndarray, flows: np.ndarray | None, t_us, *, mode: int = DENSE
         flows = np.ascontiguousarray(flows, dtype=np.float32)
         assert flows.shape == (F, H, W, 2), flows.shape
     cfg = OrcConfig(W, H, ch, mode, substeps, max_substeps, intensity, ref_mode,
-                    c_pos_q16, c_neg_q16, c_act_q16)
+                    c_pos_q16, c_neg_q16, c_act_q16, event_time)
     maps = []
     for m in (cpos_map, cneg_map):
         if m is None:
@@ -218,7 +232,7 @@ def run_diff(frames: np.ndarray, flows: np.ndarray | None, t_us, *, substeps: in
         flows = np.ascontiguousarray(flows, dtype=np.float32)
         assert flows.shape == (F, H, W, 2), flows.shape
     cfg = OrcConfig(W, H, ch, 0, substeps, max_substeps, intensity, RESET,
-                    c_pos_q16, c_neg_q16, -1)
+                    c_pos_q16, c_neg_q16, -1, T_SUBSTEP)
     maps = [None if m is None else np.ascontiguousarray(m, dtype=np.uint16)
             for m in (cpos_map, cneg_map)]
     npf = np.zeros(F, dtype=np.int32)

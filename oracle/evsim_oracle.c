@@ -93,6 +93,26 @@ int32_t orc_adaptive_substeps(int64_t max_f2, int32_t max_substeps) {
   return n;
 }
 
+/*
+ * Per-crossing event time (reading O16; the paper's events carry a time t,
+ * Sec. III, without saying where inside an interpolation step it falls).
+ * Between two consecutive interpolated frames the pixel's value is taken to
+ * change linearly in time, from i_prev at t_prev to i_cur at t_cur; a
+ * threshold level crossed in that step is reached at
+ *   t_prev + floor((t_cur - t_prev) (level - i_prev) / (i_cur - i_prev))
+ * (mirrored for a falling value).  The levels an accumulating reference
+ * crosses lie beyond i_prev and at or before i_cur, so the time falls in
+ * (t_prev, t_cur]; a level at or behind i_prev (a sparse pixel whose
+ * reference was left behind while it was inactive) gets t_prev.
+ */
+int64_t orc_crossing_time(int64_t t_prev, int64_t t_cur, int64_t i_prev, int64_t i_cur,
+                          int64_t level, int32_t rising) {
+  int64_t num = rising ? level - i_prev : i_prev - level;
+  int64_t den = rising ? i_cur - i_prev : i_prev - i_cur;
+  if (num <= 0 || den <= 0) return t_prev;
+  return t_prev + floordiv((t_cur - t_prev) * num, den);
+}
+
 static int32_t pixel_threshold(const uint16_t* map, int32_t uniform, int64_t i) {
   return map ? (int32_t)map[i] : uniform;
 }
@@ -143,10 +163,13 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
   int32_t* Fx = (int32_t*)malloc(P * sizeof(int32_t));
   int32_t* Fy = (int32_t*)malloc(P * sizeof(int32_t));
   uint8_t* act = (uint8_t*)malloc(P);
-  if (!Lprev || !Lcur || !R || !Fx || !Fy || !act) {
-    free(Lprev); free(Lcur); free(R); free(Fx); free(Fy); free(act);
+  /* value of the previous interpolated frame per pixel (ORC_T_CROSSING) */
+  int32_t* Iprev = (int32_t*)malloc(P * sizeof(int32_t));
+  if (!Lprev || !Lcur || !R || !Fx || !Fy || !act || !Iprev) {
+    free(Lprev); free(Lcur); free(R); free(Fx); free(Fy); free(act); free(Iprev);
     return -4;
   }
+  const int crossing = c->event_time == ORC_T_CROSSING;
 
   /* Frame 0 sets the reference and emits nothing. */
   frame_to_log(c, lut, frames, Lprev);
@@ -206,11 +229,14 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
     /* RESET mode differences consecutive interpolated frames: the frame
      * before substep 1 is frame i-1 itself (Sec. III-A). */
     if (c->ref_mode == ORC_RESET) memcpy(R, Lprev, P * sizeof(int32_t));
+    /* interpolated frame 0 of N is frame i-1 itself (zero offset, weight 0) */
+    memcpy(Iprev, Lprev, P * sizeof(int32_t));
 
     for (int32_t k = 1; k <= N; ++k) {
       /* Q12 blend weight round-half-up(4096 k / N); w_N = 4096. */
       int64_t w = ((int64_t)k * 8192 + N) / (2 * (int64_t)N);
       uint32_t tk = (uint32_t)(t_prev + floordiv((int64_t)k * dt, N));
+      int64_t tk1 = t_prev + floordiv((int64_t)(k - 1) * dt, N);  /* t_{k-1} */
       for (int32_t y = 0; y < H; ++y) {
         for (int32_t x = 0; x < W; ++x) {
           int64_t p = (int64_t)y * W + x;
@@ -228,10 +254,18 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
           int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);
           int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);
           int64_t D = I - R[p];
+          /* the reference before this substep; the j-th level crossed is
+           * Rb + j Cp (rising) or Rb - j Cn (falling) */
+          int64_t Rb = R[p], ip = Iprev[p];
+          Iprev[p] = (int32_t)I;
           if (c->ref_mode == ORC_RESET) {
             /* The two-case threshold equations of Sec. III-A, strict. */
-            if (D > cp) emit(out, cap, &n, tk, x, y, 1);
-            else if (D < -(int64_t)cn) emit(out, cap, &n, tk, x, y, 0);
+            if (D > cp)
+              emit(out, cap, &n, crossing ? (uint32_t)orc_crossing_time(tk1, tk, ip, I, Rb + cp, 1)
+                                          : tk, x, y, 1);
+            else if (D < -(int64_t)cn)
+              emit(out, cap, &n, crossing ? (uint32_t)orc_crossing_time(tk1, tk, ip, I, Rb - cn, 0)
+                                          : tk, x, y, 0);
             R[p] = (int32_t)I;
           } else {
             /* Reference-accumulating reading: every whole threshold crossed
@@ -239,11 +273,17 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
             if (D >= cp) {
               int64_t m = D / cp;
               R[p] = (int32_t)(R[p] + m * cp);
-              for (int64_t j = 0; j < m; ++j) emit(out, cap, &n, tk, x, y, 1);
+              for (int64_t j = 1; j <= m; ++j)
+                emit(out, cap, &n,
+                     crossing ? (uint32_t)orc_crossing_time(tk1, tk, ip, I, Rb + j * cp, 1) : tk,
+                     x, y, 1);
             } else if (-D >= cn) {
               int64_t m = (-D) / cn;
               R[p] = (int32_t)(R[p] - m * cn);
-              for (int64_t j = 0; j < m; ++j) emit(out, cap, &n, tk, x, y, 0);
+              for (int64_t j = 1; j <= m; ++j)
+                emit(out, cap, &n,
+                     crossing ? (uint32_t)orc_crossing_time(tk1, tk, ip, I, Rb - j * cn, 0) : tk,
+                     x, y, 0);
             }
           }
         }
@@ -257,7 +297,7 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
 
   if (R_final) memcpy(R_final, R, P * sizeof(int32_t));
   if (clamped_total) *clamped_total = clamped;
-  free(Lprev); free(Lcur); free(R); free(Fx); free(Fy); free(act);
+  free(Lprev); free(Lcur); free(R); free(Fx); free(Fy); free(act); free(Iprev);
   return rc < 0 ? rc : n;
 }
 

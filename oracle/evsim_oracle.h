@@ -37,6 +37,7 @@ extern "C" {
 enum { ORC_DENSE = 0, ORC_SPARSE = 1 };
 enum { ORC_LOG = 0, ORC_LINEAR = 1 };
 enum { ORC_ACCUM = 0, ORC_RESET = 1 };
+enum { ORC_T_SUBSTEP = 0, ORC_T_CROSSING = 1 };
 
 typedef struct {
   int32_t width, height;
@@ -49,6 +50,9 @@ typedef struct {
   int32_t c_pos_q16;     /* uniform C_pos (Q16) when no per-pixel map is given */
   int32_t c_neg_q16;     /* uniform |C_neg| (Q16) */
   int32_t c_act_q16;     /* sparse activity threshold (Q16); < 0: min(Cp(x), Cn(x)) */
+  int32_t event_time;    /* ORC_T_SUBSTEP: every crossing of substep k at t_k;
+                            ORC_T_CROSSING: each crossing at its own time between
+                            t_{k-1} and t_k (see orc_crossing_time) */
 } orc_config;
 
 typedef struct {
@@ -65,6 +69,13 @@ int32_t orc_luma(int32_t r, int32_t g, int32_t b);
 int32_t orc_flow_q16(float f, int32_t* clamped);
 /* Clamp-to-edge bilinear sample of a Q16 image at a Q16 position. */
 int32_t orc_bilinear(const int32_t* L, int32_t W, int32_t H, int64_t px, int64_t py);
+/* Time of one threshold crossing inside substep k (ORC_T_CROSSING): the
+ * pixel's value is taken to move linearly in time from i_prev (substep k-1,
+ * at t_prev) to i_cur (substep k, at t_cur); the crossing happens where it
+ * reaches `level`.  rising: the level is above i_prev (positive event).
+ * Levels at or behind i_prev give t_prev. */
+int64_t orc_crossing_time(int64_t t_prev, int64_t t_cur, int64_t i_prev, int64_t i_cur,
+                          int64_t level, int32_t rising);
 /* Adaptive substep count for a maximum squared Q16 flow magnitude. */
 int32_t orc_adaptive_substeps(int64_t max_f2, int32_t max_substeps);
 

@@ -13,6 +13,7 @@ Sec. III-C (difference-frame interpolation, ``simulate_diff``).
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 
 
 def log_table(linear: bool) -> list[int]:
@@ -37,11 +38,25 @@ def _sample(L, W, H, px, py):
     return mix(top, bot, fy)
 
 
+def _crossing(t_a, t_b, i_a, i_b, level):
+    """Time at which the straight line from (t_a, i_a) to (t_b, i_b) meets
+    `level`, as an exact rational, floored; t_a when the level is not ahead of
+    i_a in the direction of travel."""
+    if i_b == i_a:
+        return t_a
+    s = Fraction(level - i_a, i_b - i_a)
+    if s <= 0:
+        return t_a
+    return math.floor(t_a + (t_b - t_a) * s)
+
+
 def simulate(frames, flows_q16, t_us, *, n_sub, cp, cn, linear=False, reset=False,
-             sparse=False, c_act=None, cp_map=None, cn_map=None, max_sub=64):
+             sparse=False, c_act=None, cp_map=None, cn_map=None, max_sub=64, crossing=False):
     """frames: list of HxW lists of ints (luma); flows_q16: list (per frame) of
     HxW lists of (fx, fy) Q16 ints (entry 0 unused).  n_sub: fixed N or 0 for
-    adaptive.  Returns (events as (t, x, y, p) tuples in output order, R)."""
+    adaptive.  crossing: each threshold crossing gets its own time on the
+    straight line between consecutive substeps.  Returns (events as
+    (t, x, y, p) tuples in output order, R)."""
     lut = log_table(linear)
     H, W = len(frames[0]), len(frames[0][0])
     L0 = [[lut[v] for v in row] for row in frames[0]]
@@ -78,6 +93,7 @@ def simulate(frames, flows_q16, t_us, *, n_sub, cp, cn, linear=False, reset=Fals
                 fx, fy = flows_q16[i][y][x]
                 r = L0[y][x] if reset else R[y][x]
                 c_p, c_n = thr(cp_map, cp, y, x), thr(cn_map, cn, y, x)
+                i_last, t_last = L0[y][x], tprev  # substep 0 is frame i-1 itself
                 for k in range(1, N + 1):
                     w = (k * 8192 + N) // (2 * N)
                     ox, oy = (fx * k) // N, (fy * k) // N
@@ -86,26 +102,35 @@ def simulate(frames, flows_q16, t_us, *, n_sub, cp, cn, linear=False, reset=Fals
                     s1 = _sample(L1, W, H, p0x + fx, p0y + fy)
                     I = s0 + ((s1 - s0) * w + 2048) // 4096
                     tk = tprev + (k * dt) // N
+
+                    def times(levels):
+                        if not crossing:
+                            return [tk] * len(levels)
+                        return [_crossing(t_last, tk, i_last, I, lv) for lv in levels]
+
                     d = I - r
                     if reset:
                         if d > c_p:
-                            frame_events.append((k, y, x, tk, 1, 1))
+                            frame_events.append((k, y, x, times([r + c_p]), 1))
                         elif d < -c_n:
-                            frame_events.append((k, y, x, tk, -1, 1))
+                            frame_events.append((k, y, x, times([r - c_n]), -1))
                         r = I
                     else:
                         if d >= c_p:
                             m = d // c_p
+                            frame_events.append(
+                                (k, y, x, times([r + j * c_p for j in range(1, m + 1)]), 1))
                             r += m * c_p
-                            frame_events.append((k, y, x, tk, 1, m))
                         elif -d >= c_n:
                             m = (-d) // c_n
+                            frame_events.append(
+                                (k, y, x, times([r - j * c_n for j in range(1, m + 1)]), -1))
                             r -= m * c_n
-                            frame_events.append((k, y, x, tk, -1, m))
+                    i_last, t_last = I, tk
                 R[y][x] = r
         frame_events.sort(key=lambda e: (e[0], e[1], e[2]))
-        for k, y, x, tk, p, m in frame_events:
-            out.extend([(tk, x, y, p)] * m)
+        for k, y, x, ts, p in frame_events:
+            out.extend((t, x, y, p) for t in ts)
         L0 = L1
     return out, R
 

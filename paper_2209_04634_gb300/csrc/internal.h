@@ -210,7 +210,8 @@ struct GroupArg {
 // Shared-memory bytes of the tile kernel (dense and sparse) for a substep cap.
 size_t tile_smem_bytes(int n_max);
 
-// Launchers (kernels.cu).  Each returns the cudaError_t of the launch.
+// Launchers (kernels.cu; launch_dense in tile_dense.cu, launch_sparse in
+// tile_sparse.cu).  Each returns the cudaError_t of the launch.
 cudaError_t launch_init(const SimParams& p, const FrameDesc& f, cudaStream_t st);
 cudaError_t launch_flowmax(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st);
@@ -225,6 +226,10 @@ cudaError_t launch_plan(const SimParams& p, cudaStream_t st);
 constexpr int PLAN_MAX_TILES = 4096;  // tiles a balanced plan covers
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
+// Per-mode tile kernels (tile_dense.cu, tile_sparse.cu): dynamic shared-memory
+// limits of their k_tile instances for batches of up to n_max substeps.
+cudaError_t configure_dense_kernels(int n_max);
+cudaError_t configure_sparse_kernels(int n_max);
 int tile_class(const SimParams& p);
 cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st);
 cudaError_t launch_tile_multi(const GroupArg& g, int cls, const ActiveTile* act, int grid,

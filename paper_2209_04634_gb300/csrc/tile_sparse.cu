@@ -1,0 +1,24 @@
+// The batch-persistent tile kernel, sparse (Sec. III-B) instances: every combination
+// of reference mode, threshold maps and intensity table, in 64x16 and 64x8
+// tiles.
+#include "tile.cuh"
+
+namespace evsim {
+
+cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  return launch_tile_mode<true>(p, b, st);
+}
+
+cudaError_t configure_sparse_kernels(int n_max) {
+  set_tile_attr<false, false, false, true>(n_max);
+  set_tile_attr<false, true, false, true>(n_max);
+  set_tile_attr<false, false, true, true>(n_max);
+  set_tile_attr<false, true, true, true>(n_max);
+  set_tile_attr<true, false, false, true>(n_max);
+  set_tile_attr<true, true, false, true>(n_max);
+  set_tile_attr<true, false, true, true>(n_max);
+  set_tile_attr<true, true, true, true>(n_max);
+  return cudaGetLastError();
+}
+
+}  // namespace evsim

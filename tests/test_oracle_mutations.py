@@ -33,8 +33,8 @@ MUTATIONS = {
     "fraction_before_clamp": [("  if (px < 0) px = 0;", "  int64_t fx0 = (px & 0xFFFF) >> 4;\n  if (px < 0) px = 0;"),
                               ("int64_t fx = (px & 0xFFFF) >> 4,", "int64_t fx = fx0,")],
     "offset_truncated": ("floordiv((int64_t)Fx[p] * k, N)", "(((int64_t)Fx[p] * k) / N)"),
-    "reset_non_strict": ("if (D > cp) emit(out, cap, &n, tk, x, y, 1);",
-                         "if (D >= cp) emit(out, cap, &n, tk, x, y, 1);"),
+    "reset_non_strict": ("            if (D > cp)\n              emit(out, cap, &n, crossing",
+                         "            if (D >= cp)\n              emit(out, cap, &n, crossing"),
     "log_base_2": ("65536.0 * log((double)v + 1.0)", "65536.0 * log2((double)v + 1.0)"),
     "luma_weights_swapped": ("77 * r + 150 * g + 29 * b", "29 * r + 150 * g + 77 * b"),
     "reference_moves_one_step": ("R[p] = (int32_t)(R[p] + m * cp);", "R[p] = (int32_t)(R[p] + cp);"),
@@ -68,6 +68,18 @@ MUTATIONS = {
     "accumulate_window_end_inclusive": ("if (t < t_begin || t >= t_end) continue;",
                                         "if (t < t_begin || t > t_end) continue;"),
     "accumulate_transposed": ("frame[(int64_t)y * W + x] +=", "frame[(int64_t)x * H + y] +="),
+    # per-crossing event times (orc_crossing_time and its callers)
+    "crossing_level_counted_from_zero": ("orc_crossing_time(tk1, tk, ip, I, Rb + j * cp, 1)",
+                                         "orc_crossing_time(tk1, tk, ip, I, Rb + (j - 1) * cp, 1)"),
+    "crossing_from_substep_end_time": ("int64_t tk1 = t_prev + floordiv((int64_t)(k - 1) * dt, N);",
+                                       "int64_t tk1 = t_prev + floordiv((int64_t)k * dt, N);"),
+    "crossing_previous_value_kept_at_frame": ("          Iprev[p] = (int32_t)I;\n", "\n"),
+    "crossing_falling_measured_as_rising": ("int64_t num = rising ? level - i_prev : i_prev - level;",
+                                            "int64_t num = level - i_prev;"),
+    "crossing_time_rounded": ("return t_prev + floordiv((t_cur - t_prev) * num, den);",
+                              "return t_prev + ((t_cur - t_prev) * num + den / 2) / den;"),
+    "crossing_negative_level_uses_cp": ("orc_crossing_time(tk1, tk, ip, I, Rb - j * cn, 0)",
+                                        "orc_crossing_time(tk1, tk, ip, I, Rb - j * cp, 0)"),
     "diff_blend_reversed": ("int64_t I = lerp_q12(s0, s1, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)",
                             "int64_t I = lerp_q12(s1, s0, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)"),
 }
@@ -115,6 +127,14 @@ def battery():
     for v0, v1 in [(60, 200), (220, 35), (128, 128)]:
         yield lambda v0=v0, v1=v1: pins.test_accumulated_frame_of_a_uniform_step(v0, v1)
     yield pins.test_accumulated_frame_positions_polarity_and_window
+    for N in (1, 4):
+        for cp, cn in [(40000, 40000), (70001, 123457)]:
+            yield lambda N=N, cp=cp, cn=cn: \
+                pins.test_crossing_times_of_monotone_ramps_follow_the_exact_line(N, cp, cn)
+    yield lambda: pins.test_crossing_times_reset_one_substep(5 * 65536 + 123)
+    yield pins.test_crossing_time_primitive_properties
+    yield lambda: pins.test_crossing_times_keep_events_and_stay_inside_their_substep(
+        oracle.SPARSE, oracle.ACCUM)
 
 
 def test_battery_passes_on_the_real_oracle():

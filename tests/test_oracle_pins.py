@@ -760,3 +760,189 @@ def test_accumulated_frame_positions_polarity_and_window():
     want[4, 0] = -1
     want[0, 6] = 1
     assert np.array_equal(acc, want)
+
+
+# ---------------------------------------------------------------------------
+# Per-crossing event times (event_time = T_CROSSING, reading O16): each
+# crossing of substep k happens where the straight line between the values
+# of substeps k-1 and k (substep 0 = frame i-1) meets the crossed level.
+
+
+def monotone_ramps(rng, F, H, W, max_step=40):
+    """Per-pixel monotone luma sequences (each pixel rises or falls)."""
+    v0 = rng.integers(max_step * F // 2, 256 - max_step * F // 2, size=(H, W))
+    steps = rng.integers(0, max_step // 2 + 1, size=(F - 1, H, W))
+    sign = np.where(rng.random((H, W)) < 0.5, 1, -1)
+    seq = np.concatenate([v0[None], v0[None] + sign * np.cumsum(steps, axis=0)])
+    assert seq.min() >= 0 and seq.max() <= 255
+    return seq.astype(np.uint8)
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 8])
+@pytest.mark.parametrize("cp,cn", [(40000, 40000), (70001, 123457)])
+def test_crossing_times_of_monotone_ramps_follow_the_exact_line(N, cp, cn):
+    """Linear intensity, no flow: a pixel's value changes by D_i = 65536 dv
+    per frame, and with N a power of two dividing dv 65536 and dt, the
+    substep values and times are exact fractions of the frame step, so the
+    interpolated path is the straight line through (t_{i-1}, L_{i-1}) and
+    (t_i, L_i).  Every level L_0 + j Cp (rising) or L_0 - j Cn (falling) the
+    line passes in frame i is crossed at t_{i-1} + floor(dt_i (level -
+    L_{i-1}) / D_i), whichever substep it falls in."""
+    rng = np.random.default_rng(N * 7 + cp)
+    F, H, W = 6, 5, 9
+    frames = monotone_ramps(rng, F, H, W)
+    t_us = np.concatenate([[0], np.cumsum(rng.integers(1, 4000, size=F - 1) * 8)]).astype(np.int64)
+    r = oracle.run(frames, zero_flows(frames), t_us, substeps=N, intensity=oracle.LINEAR,
+                   c_pos_q16=cp, c_neg_q16=cn, event_time=oracle.T_CROSSING)
+    t, x, y, p = oracle.unpack(r["events"])
+    got = {}
+    for ti, xi, yi, pi in zip(t.tolist(), x.tolist(), y.tolist(), p.tolist()):
+        got.setdefault((xi, yi), []).append((ti, pi))
+    L = frames.astype(np.int64) * Q
+    for yy in range(H):
+        for xx in range(W):
+            want = []
+            for i in range(1, F):
+                a, b = L[i - 1, yy, xx], L[i, yy, xx]
+                dt = int(t_us[i] - t_us[i - 1])
+                base = L[0, yy, xx]
+                if b > a:
+                    j = (a - base) // cp + 1
+                    while base + j * cp <= b:
+                        want.append((int(t_us[i - 1]) + dt * (base + j * cp - a) // (b - a), 1))
+                        j += 1
+                elif b < a:
+                    j = (base - a) // cn + 1
+                    while base - j * cn >= b:
+                        want.append((int(t_us[i - 1]) + dt * (a - (base - j * cn)) // (a - b), -1))
+                        j += 1
+            assert got.get((xx, yy), []) == want, (xx, yy)
+
+
+@pytest.mark.parametrize("C", [2 * Q, 5 * Q + 123])
+def test_crossing_times_reset_one_substep(C):
+    """Paper mode (strict two-case test, one substep, no flow): an event
+    where |L_i - L_{i-1}| > C (the Kaiser difference frame), at the time the
+    straight line from L_{i-1} to L_i has moved by C: t_{i-1} +
+    floor(dt C / |D|)."""
+    rng = np.random.default_rng(C)
+    F, H, W = 5, 7, 11
+    frames = rng.integers(0, 256, size=(F, H, W), dtype=np.uint8)
+    t_us = np.concatenate([[0], np.cumsum(rng.integers(1, 30000, size=F - 1))]).astype(np.int64)
+    r = oracle.run(frames, zero_flows(frames), t_us, substeps=1, intensity=oracle.LINEAR,
+                   ref_mode=oracle.RESET, c_pos_q16=C, c_neg_q16=C,
+                   event_time=oracle.T_CROSSING)
+    want = []
+    for i in range(1, F):
+        d = (frames[i].astype(np.int64) - frames[i - 1]) * Q
+        dt = int(t_us[i] - t_us[i - 1])
+        for yy in range(H):
+            for xx in range(W):
+                if abs(d[yy, xx]) > C:
+                    want.append((int(t_us[i - 1]) + dt * C // abs(int(d[yy, xx])), xx, yy,
+                                 1 if d[yy, xx] > 0 else -1))
+    t, x, y, p = oracle.unpack(r["events"])
+    assert list(zip(t.tolist(), x.tolist(), y.tolist(), p.tolist())) == want
+
+
+def test_crossing_time_primitive_properties():
+    """orc_crossing_time: the level at the end value gives the end time, the
+    level at (or behind) the start value the start time; times are monotone in
+    the level; falling is rising mirrored; a level halfway along a line of
+    even duration gives the midpoint."""
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        t0 = int(rng.integers(0, 10 ** 6))
+        t1 = t0 + int(rng.integers(1, 10 ** 5))
+        a = int(rng.integers(-10 ** 6, 10 ** 6))
+        b = a + int(rng.integers(1, 10 ** 6))
+        assert oracle.crossing_time(t0, t1, a, b, b, True) == t1
+        assert oracle.crossing_time(t0, t1, a, b, a, True) == t0
+        assert oracle.crossing_time(t0, t1, a, b, a - 5, True) == t0
+        lv = sorted(int(v) for v in rng.integers(a, b + 1, size=5))
+        ts = [oracle.crossing_time(t0, t1, a, b, v, True) for v in lv]
+        assert ts == sorted(ts) and t0 <= ts[0] and ts[-1] <= t1
+        for v in lv:
+            assert (oracle.crossing_time(t0, t1, a, b, v, True)
+                    == oracle.crossing_time(t0, t1, -a, -b, -v, False))
+        assert oracle.crossing_time(0, 2 * (t1 - t0), 0, 2 * (b - a), b - a, True) == t1 - t0
+
+
+@pytest.mark.parametrize("mode", [oracle.DENSE, oracle.SPARSE])
+@pytest.mark.parametrize("ref", [oracle.ACCUM, oracle.RESET])
+def test_crossing_times_keep_events_and_stay_inside_their_substep(mode, ref):
+    """With flow, log intensity and per-pixel noise-free thresholds: the
+    per-crossing run emits the same events in the same order as the
+    substep-time run (only t differs); each time lies in [t_{k-1}, t_k] of
+    the event's substep; a pixel's repeated crossings in one substep have
+    non-decreasing times."""
+    rng = np.random.default_rng(11 + mode * 2 + ref)
+    F, H, W = 5, 10, 13
+    frames = np.clip(np.cumsum(rng.integers(-25, 26, size=(F, H, W)), axis=0) + 128, 0,
+                     255).astype(np.uint8)
+    flows = rng.uniform(-2.5, 2.5, size=(F, H, W, 2)).astype(np.float32)
+    t_us = np.concatenate([[0], np.cumsum(rng.integers(2000, 40000, size=F - 1))]).astype(np.int64)
+    kw = dict(mode=mode, substeps=0, max_substeps=8, ref_mode=ref, c_pos_q16=9000,
+              c_neg_q16=11000, c_act_q16=4000)
+    a = oracle.run(frames, flows, t_us, **kw)
+    b = oracle.run(frames, flows, t_us, event_time=oracle.T_CROSSING, **kw)
+    assert len(a["events"]) == len(b["events"]) > 100
+    assert np.array_equal(a["events"]["x"], b["events"]["x"])
+    assert np.array_equal(a["events"]["yp"], b["events"]["yp"])
+    assert np.array_equal(a["R"], b["R"])
+    ta = a["events"]["t"].astype(np.int64)
+    tb = b["events"]["t"].astype(np.int64)
+    # t_{k-1} of each event from its frame's substep times
+    start = 0
+    lo = np.zeros_like(ta)
+    for i in range(1, F):
+        n_i = int(a["ev_per_frame"][i])
+        N = int(a["n_per_frame"][i])
+        dt = int(t_us[i] - t_us[i - 1])
+        tk = [int(t_us[i - 1]) + (k * dt) // N for k in range(N + 1)]
+        for e in range(start, start + n_i):
+            k = tk.index(int(ta[e]))
+            assert k >= 1
+            lo[e] = tk[k - 1]
+        start += n_i
+    assert np.all(tb <= ta) and np.all(tb >= lo)
+    assert np.any(tb < ta)
+    same = (np.diff(ta) == 0) & (np.diff(b["events"]["x"].astype(np.int64)) == 0) & \
+        (np.diff(b["events"]["yp"].astype(np.int64)) == 0)
+    assert np.all(np.diff(tb)[same] >= 0)
+
+
+@pytest.mark.parametrize("case", range(60))
+def test_crossing_times_second_restatement_on_random_8x8(case):
+    """orc_run with per-crossing times (substep-major C) and exact.simulate
+    (pixel-major Python, exact rationals) agree event for event."""
+    rng = np.random.default_rng(5000 + case)
+    F = int(rng.integers(2, 4))
+    H = W = 8
+    frames = rng.integers(0, 256, size=(F, H, W), dtype=np.uint8)
+    if case % 3 == 0:
+        frames = np.clip(np.cumsum(rng.integers(-30, 31, size=(F, H, W)), axis=0) + 128,
+                         0, 255).astype(np.uint8)
+    flows = rng.uniform(-3, 3, size=(F, H, W, 2)).astype(np.float32)
+    N = int(rng.integers(0, 7))
+    linear = bool(case % 3 == 1)
+    reset = bool(case % 4 == 2)
+    sparse = bool(case % 2)
+    if linear:
+        cp, cn = int(rng.integers(Q, 40 * Q)), int(rng.integers(Q, 40 * Q))
+    else:
+        cp, cn = int(rng.integers(2000, 40000)), int(rng.integers(2000, 40000))
+    cact = int(rng.integers(0, 30000)) if case % 5 == 1 else -1
+    t_us = np.cumsum(rng.integers(1, 50000, size=F)).astype(np.int64)
+    r = oracle.run(frames, flows, t_us, mode=oracle.SPARSE if sparse else oracle.DENSE,
+                   substeps=N, max_substeps=6, intensity=oracle.LINEAR if linear else oracle.LOG,
+                   ref_mode=oracle.RESET if reset else oracle.ACCUM, c_pos_q16=cp, c_neg_q16=cn,
+                   c_act_q16=cact, event_time=oracle.T_CROSSING)
+    fq = [[[(int(np.rint(np.float64(flows[i, y, x, 0]) * Q)),
+             int(np.rint(np.float64(flows[i, y, x, 1]) * Q))) for x in range(W)]
+           for y in range(H)] for i in range(F)]
+    ev, R = exact.simulate([f.tolist() for f in frames], fq, t_us.tolist(), n_sub=N, cp=cp,
+                           cn=cn, linear=linear, reset=reset, sparse=sparse, c_act=cact,
+                           max_sub=6, crossing=True)
+    t, x, y, p = oracle.unpack(r["events"])
+    assert list(zip(t.tolist(), x.tolist(), y.tolist(), p.tolist())) == ev
