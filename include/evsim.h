@@ -115,8 +115,31 @@ typedef struct {
   int32_t tile_height;       /* batch kernel tile shape: SIM_TILE_AUTO, SIM_TILE_TUNE, 8 or
                                 16 (64 x 8 tiles of 256 threads / 64 x 16 of 512); see
                                 sim_autotune.  Group members always use 16. */
-  int32_t reserved0;
+  int32_t event_time;        /* SIM_TIME_SUBSTEP | SIM_TIME_CROSSING (see below) */
 } sim_config;
+
+/* Event times (sim_config.event_time).  The paper's events carry a time t
+ * (Sec. III) without fixing where inside an interpolation step a crossing
+ * falls.
+ *   SIM_TIME_SUBSTEP : every crossing of substep k gets t_k = t_{i-1} +
+ *                      floor(k (t_i - t_{i-1}) / N) (the default).
+ *   SIM_TIME_CROSSING: between substeps k-1 and k (substep 0 = frame i-1) a
+ *                      pixel's value is taken to move linearly in time; the
+ *                      j-th level crossed, R + j C_pos (rising) or
+ *                      R - j C_neg (falling), R the reference before the
+ *                      substep (in reset mode the value of substep k-1), is
+ *                      reached at t_{k-1} + floor((t_k - t_{k-1})
+ *                      (level - I_{k-1}) / (I_k - I_{k-1})); a level at or
+ *                      behind I_{k-1} (a sparse pixel whose reference stayed
+ *                      behind while it was inactive) gets t_{k-1}.  Events keep
+ *                      their (frame, substep, row, column) order, so times are
+ *                      non-decreasing from substep to substep but not inside
+ *                      one.  Dense and sparse only (SIM_ERR_ARG for SIM_DIFF);
+ *                      single handles only (simb_admit and
+ *                      sim_step_pair_static refuse it); the batch kernel runs
+ *                      in 64 x 16 tiles, every row with an event staging its
+ *                      events. */
+enum { SIM_TIME_SUBSTEP = 0, SIM_TIME_CROSSING = 1 };
 
 /* Tile shape choices of sim_config.tile_height. */
 enum {

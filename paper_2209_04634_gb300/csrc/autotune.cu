@@ -67,6 +67,7 @@ int time_shape(const sim_config& c, int th, int order, int count, const void* co
                double* us) {
   sim_config tc = c;
   tc.tile_height = th;
+  tc.event_time = SIM_TIME_SUBSTEP;  // the table serves the substep-time kernels only
   tc.cuda_stream = nullptr;
   tc.max_batch = count - 1;
   tc.event_capacity = std::min<long long>((long long)c.width * c.height * 2 * count, 1LL << 27);

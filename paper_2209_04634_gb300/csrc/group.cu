@@ -339,7 +339,8 @@ int simb_state_bytes(const simb_t* g, const sim_config* cfg, int64_t* bytes) {
 
 int simb_admit(simb_t* g, const sim_config* cfg, int32_t* id) {
   if (!g || !cfg || !id) return SIM_ERR_ARG;
-  if (cfg->mode == SIM_DIFF) return SIM_ERR_ARG;  // single handles only
+  // single handles only
+  if (cfg->mode == SIM_DIFF || cfg->event_time != SIM_TIME_SUBSTEP) return SIM_ERR_ARG;
   int64_t bytes = 0;
   int rc = simb_state_bytes(g, cfg, &bytes);
   if (rc) return rc;

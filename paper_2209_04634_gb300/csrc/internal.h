@@ -113,6 +113,8 @@ struct SimParams {
   int sms;                      // SMs of the device (block placement of the batch kernel)
   int block_order;              // batch kernel: 0 tiles in block order, 1 serpentine,
                                 // 2 balanced by the previous batch's tile costs
+  int xtime;                    // 1: per-crossing event times (64 x 16 tiles, every row
+                                // with an event staged)
   unsigned int* tile_cost;      // balanced order: [tiles] cycles of each tile's last batch
   int* tile_order;              // balanced order: [tiles] tile of each block
   const unsigned short* cpmap;
@@ -230,6 +232,10 @@ cudaError_t configure_kernels(int n_max);
 // limits of their k_tile instances for batches of up to n_max substeps.
 cudaError_t configure_dense_kernels(int n_max);
 cudaError_t configure_sparse_kernels(int n_max);
+// Per-crossing event times (tile_xtime.cu): the tile kernel instances of both
+// modes; launch_dense / launch_sparse route to launch_xtime when p.xtime.
+cudaError_t configure_xtime_kernels(int n_max);
+cudaError_t launch_xtime(const SimParams& p, const BatchArg& b, bool sparse, cudaStream_t st);
 int tile_class(const SimParams& p);
 cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st);
 cudaError_t launch_tile_multi(const GroupArg& g, int cls, const ActiveTile* act, int grid,

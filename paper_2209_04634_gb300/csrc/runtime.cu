@@ -115,7 +115,9 @@ evsim::SimParams make_params(const sim_t* s) {
   p.sms = s->sms;
   p.block_order = s->block_order;
   p.tile_cost = s->block_order == 2 ? s->d_tile_cost : nullptr;
-  p.tile_order = s->d_tile_order;  p.mode = s->cfg.mode;
+  p.tile_order = s->d_tile_order;
+  p.xtime = s->cfg.event_time == SIM_TIME_CROSSING;
+  p.mode = s->cfg.mode;
   p.ref_mode = s->cfg.ref_mode;
   p.intensity = s->cfg.intensity;
   p.n_fixed = s->cfg.substeps;
@@ -344,6 +346,9 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   if (c.tile_height != SIM_TILE_AUTO && c.tile_height != SIM_TILE_TUNE && c.tile_height != 8 &&
       c.tile_height != 16)
     return SIM_ERR_ARG;
+  if (c.event_time != SIM_TIME_SUBSTEP && c.event_time != SIM_TIME_CROSSING) return SIM_ERR_ARG;
+  const bool xtime = c.event_time == SIM_TIME_CROSSING;
+  if (xtime && c.mode == SIM_DIFF) return SIM_ERR_ARG;  // no crossings: no reference
 
   int lut[256];
   build_lut(c.intensity, lut);
@@ -367,8 +372,10 @@ int sim_create(const sim_config* cfg, sim_t** out) {
 
   // tile shape: fixed, or the autotuner's choice for this configuration
   int th = c.tile_height, order = 0, tth = 16, torder = 0;
-  const bool tuned = tuned_tile_height(c, &tth, &torder);
-  if (th != 8 && th != 16) {
+  const bool tuned = !xtime && tuned_tile_height(c, &tth, &torder);
+  if (xtime) {
+    th = 16;  // the per-crossing-time kernel has the 64 x 16 shape only
+  } else if (th != 8 && th != 16) {
     if (tuned) {
       th = tth;
       order = torder;

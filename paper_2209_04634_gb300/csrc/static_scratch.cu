@@ -122,6 +122,7 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   if (c.substeps < 0 || c.substeps > SIM_MAX_SUBSTEPS) return SIM_ERR_ARG;
   if (c.substeps == 0 && (c.max_substeps < 1 || c.max_substeps > SIM_MAX_SUBSTEPS)) return SIM_ERR_ARG;
   if (c.c_pos_map || c.c_neg_map) return SIM_ERR_ARG;  // threshold maps: sim_create only
+  if (c.event_time != SIM_TIME_SUBSTEP) return SIM_ERR_ARG;  // per-crossing times: sim_create only
   if (event_capacity < 0 || event_capacity > evsim::MAX_EVENTS) return SIM_ERR_ARG;
   if (!prev_frame || !frame || !flow || (event_capacity > 0 && !events)) return SIM_ERR_ARG;
   if (misaligned(flow, 8) || misaligned(events, 8)) return SIM_ERR_ARG;

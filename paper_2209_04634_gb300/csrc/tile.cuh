@@ -513,11 +513,67 @@ __device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_l
             make_event(tk, tx0 + col_hi, y, n_hi > 0));
 }
 
+// Per-crossing event time (SIM_TIME_CROSSING).  Between two consecutive
+// substeps a pixel's value is taken to move linearly in time, from ip (the
+// previous substep's value; substep 0 is frame i-1 itself) at t0 to i at
+// t0 + dt.  The m-th level the substep crosses, rb + m c rising or rb - m c
+// falling (rb the reference before the substep), is reached at
+// t0 + floor(dt (level - ip) / (i - ip)); a level at or behind ip (a sparse
+// pixel whose reference stayed behind while it was inactive) gives t0.
+struct Crossing {
+  int ip, i, rb, c;
+};
+
+__device__ __forceinline__ unsigned crossing_time(unsigned t0, unsigned dt, const Crossing& x,
+                                                  bool rising, int m) {
+  const int num = rising ? x.rb + m * x.c - x.ip : x.ip - (x.rb - m * x.c);
+  const int den = rising ? x.i - x.ip : x.ip - x.i;
+  if (num <= 0 || den <= 0) return t0;
+  // num <= den: the levels crossed lie at or before i; dt num < 2^57
+  return t0 + (unsigned)(((unsigned long long)dt * (unsigned)num) / (unsigned)den);
+}
+
+// Publish the segment of one (substep, tile row) with per-crossing times:
+// every row with an event stages its events (column order, a pixel's
+// crossings adjacent in crossing order), each with its own time; lanes hold
+// the counts n_lo (column col_lo) and n_hi (col_hi) as in publish_row, t0 /
+// t1 are the times of the previous and this substep.  All 32 lanes must call
+// this.
+__device__ __forceinline__ void publish_row_xt(const SimParams& p, Seg* sg, int n_lo, int col_lo,
+                                               int n_hi, int col_hi, unsigned t0, unsigned t1,
+                                               int tx0, int y, WarpStage* ws,
+                                               const Crossing& x_lo, const Crossing& x_hi) {
+  const int lane = threadIdx.x & 31;
+  const int a_lo = abs(n_lo), a_hi = abs(n_hi);
+  if (!__any_sync(FULL, (a_lo | a_hi) != 0)) {
+    if (lane == 0) *sg = Seg{0ull, 0ull, 0, -1};
+    return;
+  }
+  const int i_lo = warp_incl_scan(a_lo);
+  const int t_lo = __shfl_sync(FULL, i_lo, 31);
+  const int i_hi = warp_incl_scan(a_hi);
+  const int total = t_lo + __shfl_sync(FULL, i_hi, 31);
+  long long base = 0;
+  if (lane == 0) base = stage_take(p, *ws, total);
+  base = __shfl_sync(FULL, base, 0);
+  if (base >= 0) {
+    const unsigned dt = t1 - t0;
+    for (int m = 0; m < a_lo; ++m)
+      p.staging[base + i_lo - a_lo + m] =
+          make_event(crossing_time(t0, dt, x_lo, n_lo > 0, m + 1), tx0 + col_lo, y, n_lo > 0);
+    for (int m = 0; m < a_hi; ++m)
+      p.staging[base + t_lo + i_hi - a_hi + m] =
+          make_event(crossing_time(t0, dt, x_hi, n_hi > 0, m + 1), tx0 + col_hi, y, n_hi > 0);
+  }
+  if (lane == 0) *sg = Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1};
+}
+
 // The substeps of the (up to) two pixels of this thread.  `lx, ly` are the
 // pixels' tile coordinates, `nk_at` their columns in the per-substep record.
 // DENSE: the two pixels are columns lane, lane + 32 of tile row `warp`, and the
-// row's segment is published from the loop.
-template <bool RESET, bool WIDE, bool FAST, bool DENSE, int TH_ = 16>
+// row's segment is published from the loop.  XT (DENSE only): per-crossing
+// event times, t_frame the time of frame i-1.
+template <bool RESET, bool WIDE, bool FAST, bool DENSE, int TH_ = 16, bool XT = false>
 __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
                                               unsigned mN, int tx0, int ty0, unsigned b0, unsigned b1,
                                               const FrameRef& prv, const FrameDesc& cur,
@@ -525,9 +581,11 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
                                               const int (&nk_at)[2], const bool (&act)[2],
                                               const int (&Fx)[2], const int (&Fy)[2],
                                               int (&R)[2], const int (&Cp)[2],
-                                              const int (&Cn)[2], WarpStage* ws) {
+                                              const int (&Cn)[2], WarpStage* ws,
+                                              unsigned t_frame = 0) {
   constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
   (void)TH; (void)NTD; (void)TP; (void)SH;
+  static_assert(!XT || DENSE, "per-crossing times use the dense row mapping");
   const int warp = threadIdx.x >> 5;
   int px[2], py[2], ax[2], ay[2], qx[2], rx[2], qy[2], ry[2];
 #pragma unroll
@@ -542,6 +600,17 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
     ax[j] = 0;
     ay[j] = 0;
   }
+  // XT: the value of the previous substep; substep 0 is frame i-1 at the
+  // pixel (zero offset)
+  int Ip[2] = {0, 0};
+  Crossing cx[2];
+  if (XT) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      Ip[j] = FAST ? tap_shared<WIDE>(b0, px[j], py[j])
+                   : tap_global<WIDE>(prv.ptr, prv.pitch, prv.ch, p.W, p.H, L.slut, px[j], py[j]);
+  }
+  unsigned t_last = t_frame;
   const int y = ty0 + warp;
   const bool row_in = !DENSE || y < p.H;
   for (int k = 0; k < N; ++k) {
@@ -565,13 +634,24 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
                               py[j] + Fy[j]);
       }
       const int I = lerp12<WIDE>(s0, s1, w);
+      if (XT) cx[j] = Crossing{Ip[j], I, R[j], 0};
       n[j] = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
       if (!act[j]) n[j] = 0;
+      if (XT) {
+        cx[j].c = n[j] > 0 ? Cp[j] : Cn[j];
+        Ip[j] = I;
+      }
       if (!DENSE) L.snk[k * TP + nk_at[j]] = (short)n[j];
     }
-    if (DENSE && row_in)  // warp-uniform
+    if (XT) {
+      if (row_in)  // warp-uniform
+        publish_row_xt(p, segf + (long long)k * p.segs_per_k + warp * p.tiles_x, n[0], lx[0],
+                       n[1], lx[1], t_last, L.stk[k], tx0, y, ws, cx[0], cx[1]);
+      t_last = L.stk[k];
+    } else if (DENSE && row_in) {  // warp-uniform
       publish_row(p, segf + (long long)k * p.segs_per_k + warp * p.tiles_x, n[0], lx[0], true,
                   n[1], lx[1], true, L.stk[k], tx0, y, ws);
+    }
   }
 }
 
@@ -1235,7 +1315,7 @@ __device__ __forceinline__ void substep_tables(const SimParams& p, unsigned long
   }
 }
 
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_>
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_, bool XT = false>
 __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b, int tile) {
   constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
   (void)TH; (void)NTD; (void)TP; (void)SH;
@@ -1382,7 +1462,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     // sparse tiles with at least 3/8 of their pixels active run the frame
     // through the dense loop (inactive pixels masked, their reference kept):
     // cheaper per pixel than compaction, per-slot records and mask atomics
-    const bool dsw = SPARSE && 8 * A >= 3 * TP;
+    // (per-crossing times: always, their rows are published by the dense loop)
+    const bool dsw = SPARSE && (XT || 8 * A >= 3 * TP);
 
     // 2. the simulated pixels of this thread and their (staged) flow; the
     // tile's reach
@@ -1484,7 +1565,23 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     V.snk = L.snk;
     const unsigned b0 = smem_addr(pb);
     const unsigned b1 = smem_addr(cb);
-    if (SPARSE && dsw && !(fast && N <= 32)) {
+    if (XT) {
+      const unsigned t_frame = (unsigned)(fi == 0 ? t_first : s_desc[(fi - 1) & 3].t_rel);
+      if (SPARSE && A == 0) {  // warp-uniform: nothing simulated, empty segments
+        if (ty0 + warp < H)
+          for (int k = lane; k < N; k += 32)
+            segf[(long long)k * p.segs_per_k + warp * p.tiles_x] = Seg{0ull, 0ull, 0, -1};
+      } else if (fast) {
+        tile_substeps<RESET, WIDE, true, true, TH_, true>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur,
+                                                          segf, lx, ly, nk_at, act, Fx, Fy, R,
+                                                          Cp, Cn, &s_stage[warp], t_frame);
+      } else {
+        tile_substeps<RESET, WIDE, false, true, TH_, true>(p, V, N, mN, tx0, ty0, b0, b1, prv,
+                                                           cur, segf, lx, ly, nk_at, act, Fx,
+                                                           Fy, R, Cp, Cn, &s_stage[warp],
+                                                           t_frame);
+      }
+    } else if (SPARSE && dsw && !(fast && N <= 32)) {
       if (fast)
         tile_substeps<RESET, WIDE, true, true, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
                                                     lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
@@ -1641,35 +1738,36 @@ __device__ __forceinline__ int serpentine_tile(int b, int T, int S) {
   return r * S + ((r & 1) ? size - 1 - j : j);
 }
 
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_>
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_, bool XT = false>
 __global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile(SimParams p, BatchArg b) {
   const int bi = blockIdx.x;
   const int tile = p.block_order == 2 ? p.tile_order[bi]
                    : p.block_order == 1 ? serpentine_tile(bi, gridDim.x, p.sms)
                                         : bi;
   const long long c0 = clock64();
-  tile_batch<RESET, MAPS, WIDE, SPARSE, TH_>(p, b, tile);
+  tile_batch<RESET, MAPS, WIDE, SPARSE, TH_, XT>(p, b, tile);
   if (p.tile_cost && threadIdx.x == 0) p.tile_cost[tile] = (unsigned)((clock64() - c0) >> 8);
 }
 
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, bool XT = false>
 void set_tile_attr(int n_max) {
-  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 16>,
+  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 16, XT>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)batch_smem_bytes(n_max, 3, SPARSE, 16));
-  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 8>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)batch_smem_bytes(n_max, 3, SPARSE, 8));
+  if (!XT)  // per-crossing times run in 64 x 16 tiles only
+    cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 8>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batch_smem_bytes(n_max, 3, SPARSE, 8));
 }
 
-template <bool SPARSE, int TH_>
+template <bool SPARSE, int TH_, bool XT = false>
 cudaError_t launch_tile_shape(const SimParams& p, const BatchArg& b, cudaStream_t st) {
   const int grid = p.tiles_x * p.tiles_y;
   const size_t sm = batch_smem_bytes(p.n_max, p.ch, SPARSE, TH_);
   const bool reset = p.ref_mode == SIM_REF_RESET;
   const bool maps = p.cpmap != nullptr;
   const bool wide = p.intensity == SIM_LINEAR;
-#define EVSIM_TILE(R, M, Wd) k_tile<R, M, Wd, SPARSE, TH_><<<grid, 32 * TH_, sm, st>>>(p, b)
+#define EVSIM_TILE(R, M, Wd) k_tile<R, M, Wd, SPARSE, TH_, XT><<<grid, 32 * TH_, sm, st>>>(p, b)
   if (!reset && !maps && !wide) EVSIM_TILE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_TILE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_TILE(false, false, true);

@@ -6,6 +6,7 @@
 namespace evsim {
 
 cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  if (p.xtime) return launch_xtime(p, b, false, st);
   return launch_tile_mode<false>(p, b, st);
 }
 

@@ -11,7 +11,8 @@ from paper_2209_04634_gb300 import synth
 
 def oracle_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, intensity=evsim.SIM_LOG,
                ref_mode=evsim.SIM_REF_ACCUM, c_act_q16: int = -1, substeps=None,
-               c_pos_q16=None, c_neg_q16=None, use_maps=True) -> dict:
+               c_pos_q16=None, c_neg_q16=None, use_maps=True,
+               event_time=evsim.SIM_TIME_SUBSTEP) -> dict:
     if mode == evsim.SIM_DIFF:
         return oracle.run_diff(seq.frames, seq.flows, seq.t_us,
                                substeps=seq.substeps if substeps is None else substeps,
@@ -28,14 +29,17 @@ def oracle_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, intensity=ev
                       c_neg_q16=evsim.q16(seq.c_neg) if c_neg_q16 is None else c_neg_q16,
                       c_act_q16=c_act_q16,
                       cpos_map=seq.cpos_map if use_maps else None,
-                      cneg_map=seq.cneg_map if use_maps else None)
+                      cneg_map=seq.cneg_map if use_maps else None,
+                      event_time=oracle.T_CROSSING if event_time == evsim.SIM_TIME_CROSSING
+                      else oracle.T_SUBSTEP)
 
 
 def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: bool = True,
             pop_every: int = 1, intensity=evsim.SIM_LOG, ref_mode=evsim.SIM_REF_ACCUM,
             c_act_q16: int = -1, substeps=None, c_pos_q16=None, c_neg_q16=None,
             use_maps=True, event_capacity: int = 0, stream=None, batch: int = 0,
-            max_batch: int = 0, tile_height: int = 0) -> dict:
+            max_batch: int = 0, tile_height: int = 0,
+            event_time: int = evsim.SIM_TIME_SUBSTEP) -> dict:
     """Push every frame of seq through the CUDA library; return the events,
     the committed reference and per-frame statistics."""
     import torch
@@ -54,6 +58,7 @@ def gpu_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, device_inputs: 
         kw["stream"] = stream
     kw["max_batch"] = max_batch
     kw["tile_height"] = tile_height
+    kw["event_time"] = event_time
     sim = evsim.simulator_for(seq, mode, **kw)
     if mode == evsim.SIM_DIFF:
         ref_mode = evsim.SIM_REF_RESET  # no reference state

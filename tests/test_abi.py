@@ -72,10 +72,22 @@ def _cfg(lib, w=64, h=48):
     ("width", 0), ("height", -3), ("width", 9000), ("pixel_format", 2), ("mode", 7),
     ("intensity", 5), ("ref_mode", 3), ("substeps", 65), ("substeps", -1),
     ("c_pos_q16", 0), ("c_neg_q16", 11), ("c_pos_q16", 1 << 30), ("event_capacity", -5),
+    ("event_time", 2), ("event_time", -1),
 ])
 def test_create_rejects_bad_config_before_touching_the_device(lib, field, value):
     c = _cfg(lib)
     setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(c), ctypes.byref(h)) == evsim.SIM_ERR_ARG
+    assert not h.value
+
+
+def test_crossing_times_need_a_reference(lib):
+    """Per-crossing event times are defined for the dense and sparse methods
+    only (the difference-frame method has no reference to cross)."""
+    c = _cfg(lib)
+    c.mode = evsim.SIM_DIFF
+    c.event_time = evsim.SIM_TIME_CROSSING
     h = ctypes.c_void_p()
     assert lib.sim_create(ctypes.byref(c), ctypes.byref(h)) == evsim.SIM_ERR_ARG
     assert not h.value

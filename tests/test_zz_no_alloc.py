@@ -116,6 +116,9 @@ def test_static_pair_argument_checks():
     cfg.c_neg_map = cp.ctypes.data
     assert _call(lib, cfg)[0] == evsim.SIM_ERR_ARG      # maps: handle API only
     cfg = _cfg(lib, 64, 32)
+    cfg.event_time = evsim.SIM_TIME_CROSSING
+    assert _call(lib, cfg)[0] == evsim.SIM_ERR_ARG      # per-crossing times: handle API only
+    cfg = _cfg(lib, 64, 32)
     assert _call(lib, cfg, flow=68)[0] == evsim.SIM_ERR_ARG    # flow not 8-byte aligned
     assert _call(lib, cfg, events=0)[0] == evsim.SIM_ERR_ARG   # no event buffer
     assert _call(lib, cfg, ref=None)[0] == evsim.SIM_ERR_ARG   # accumulate: ref_out needed
