@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--tile-height", type=int, default=0, choices=[0, 8, 16],
                     help="batch kernel tile height; 0: the library's autotuner chooses")
+    ap.add_argument("--substeps", type=int, default=0,
+                    help="fixed substeps per frame for profiling runs (splits a kernel's "
+                         "per-substep from its per-frame work); 0: the workload's adaptive N")
     return ap.parse_args()
 
 
@@ -228,6 +231,8 @@ def run_ours(args, ws, rank, local):
     evsim.load()
 
     seq = synth.warped_texture(frames=args.frames, seed=4209 + 1000 * rank)
+    if args.substeps:
+        seq.substeps = args.substeps
     F, H, W = seq.frames.shape
     P = W * H
     stream = torch.cuda.Stream()
@@ -325,7 +330,8 @@ def run_ours(args, ws, rank, local):
                    "pixel_substeps_per_step": work_step,
                    "active_pixel_substeps_per_step_sparse": active_work,
                    "l2": "inputs larger than L2 (277 MB resident), no flush",
-                   "parallelism": f"{ws} independent stream(s), one per GPU"},
+                   "parallelism": f"{ws} independent stream(s), one per GPU",
+                   "substeps": args.substeps if args.substeps else "adaptive"},
         "events_per_s": total_ev / (ms_max / 1e3),
         "wall_ms_per_step": wall / args.steps * 1e3,
         "kernel_us_per_launch": {k: v[0] / v[1] * 1e3 for k, v in ktimes.items()},

@@ -232,10 +232,13 @@ cudaError_t configure_kernels(int n_max);
 // limits of their k_tile instances for batches of up to n_max substeps.
 cudaError_t configure_dense_kernels(int n_max);
 cudaError_t configure_sparse_kernels(int n_max);
-// Per-crossing event times (tile_xtime.cu): the tile kernel instances of both
-// modes; launch_dense / launch_sparse route to launch_xtime when p.xtime.
-cudaError_t configure_xtime_kernels(int n_max);
-cudaError_t launch_xtime(const SimParams& p, const BatchArg& b, bool sparse, cudaStream_t st);
+// Per-crossing event times (tile_xtime_dense.cu, tile_xtime_sparse.cu): the
+// tile kernel instances of each mode; launch_dense / launch_sparse route to
+// them when p.xtime.
+cudaError_t configure_xtime_dense_kernels(int n_max);
+cudaError_t configure_xtime_sparse_kernels(int n_max);
+cudaError_t launch_xtime_dense(const SimParams& p, const BatchArg& b, cudaStream_t st);
+cudaError_t launch_xtime_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st);
 int tile_class(const SimParams& p);
 cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st);
 cudaError_t launch_tile_multi(const GroupArg& g, int cls, const ActiveTile* act, int grid,

@@ -920,7 +920,8 @@ int device_sm_count() {
 cudaError_t configure_kernels(int n_max) {
   configure_dense_kernels(n_max);
   configure_sparse_kernels(n_max);
-  configure_xtime_kernels(n_max);
+  configure_xtime_dense_kernels(n_max);
+  configure_xtime_sparse_kernels(n_max);
   return cudaGetLastError();
 }
 

@@ -2,8 +2,9 @@
 // the shared helpers of every kernel (bilinear taps, threshold step, scans,
 // segment publishing, staging) and the batch-persistent tile kernel k_tile
 // with its launch templates.  The translation units tile_dense.cu,
-// tile_sparse.cu and tile_xtime.cu instantiate k_tile for their mode, so the
-// instances compile in parallel; kernels.cu holds the other kernels.
+// tile_sparse.cu, tile_xtime_dense.cu and tile_xtime_sparse.cu instantiate
+// k_tile for their mode, so the instances compile in parallel; kernels.cu
+// holds the other kernels.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -529,8 +530,22 @@ __device__ __forceinline__ unsigned crossing_time(unsigned t0, unsigned dt, cons
   const int num = rising ? x.rb + m * x.c - x.ip : x.ip - (x.rb - m * x.c);
   const int den = rising ? x.i - x.ip : x.ip - x.i;
   if (num <= 0 || den <= 0) return t0;
-  // num <= den: the levels crossed lie at or before i; dt num < 2^57
-  return t0 + (unsigned)(((unsigned long long)dt * (unsigned)num) / (unsigned)den);
+  // num <= den (the levels crossed lie at or before i) and den < 2^24 (the
+  // range of the intensity tables), so both are exact floats and dt num < 2^56
+  const unsigned long long want = (unsigned long long)dt * (unsigned)num;
+  unsigned q;
+  if (dt <= (1u << 20)) {
+    // single-precision estimate of dt num / den: relative error below 2^-21,
+    // so within 0.32 of the exact quotient and its truncation within one of
+    // the floor; one exact integer comparison each way corrects it
+    q = (unsigned)(__fdividef((float)num, (float)den) * (float)dt);
+    const unsigned long long got = (unsigned long long)q * (unsigned)den;
+    if (got > want) --q;
+    else if (got + (unsigned)den <= want) ++q;
+  } else {
+    q = (unsigned)(want / (unsigned)den);
+  }
+  return t0 + q;
 }
 
 // Publish the segment of one (substep, tile row) with per-crossing times:
@@ -572,8 +587,10 @@ __device__ __forceinline__ void publish_row_xt(const SimParams& p, Seg* sg, int 
 // pixels' tile coordinates, `nk_at` their columns in the per-substep record.
 // DENSE: the two pixels are columns lane, lane + 32 of tile row `warp`, and the
 // row's segment is published from the loop.  XT (DENSE only): per-crossing
-// event times, t_frame the time of frame i-1.
-template <bool RESET, bool WIDE, bool FAST, bool DENSE, int TH_ = 16, bool XT = false>
+// event times, t_frame the time of frame i-1.  MK (N <= 32): the offsets'
+// carries come from the frame's carry table cmask, as in dense_substeps.
+template <bool RESET, bool WIDE, bool FAST, bool DENSE, int TH_ = 16, bool XT = false,
+          bool MK = false>
 __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayout& L, int N,
                                               unsigned mN, int tx0, int ty0, unsigned b0, unsigned b1,
                                               const FrameRef& prv, const FrameDesc& cur,
@@ -582,7 +599,8 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
                                               const int (&Fx)[2], const int (&Fy)[2],
                                               int (&R)[2], const int (&Cp)[2],
                                               const int (&Cn)[2], WarpStage* ws,
-                                              unsigned t_frame = 0) {
+                                              unsigned t_frame = 0,
+                                              const unsigned* cmask = nullptr) {
   constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
   (void)TH; (void)NTD; (void)TP; (void)SH;
   static_assert(!XT || DENSE, "per-crossing times use the dense row mapping");
@@ -597,12 +615,12 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
     // F = q N + r with 0 <= r < N: offset_k = q k + floor(r k / N)
     divmod_n(Fx[j], N, mN, qx[j], rx[j]);
     divmod_n(Fy[j], N, mN, qy[j], ry[j]);
-    ax[j] = 0;
-    ay[j] = 0;
+    ax[j] = MK ? (int)cmask[rx[j]] : 0;
+    ay[j] = MK ? (int)cmask[ry[j]] : 0;
   }
   // XT: the value of the previous substep; substep 0 is frame i-1 at the
   // pixel (zero offset)
-  int Ip[2] = {0, 0};
+  int Ip[2] = {0, 0}, Iold[2] = {0, 0};
   Crossing cx[2];
   if (XT) {
 #pragma unroll
@@ -618,12 +636,19 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
     int n[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      px[j] -= qx[j];
-      ax[j] += rx[j];
-      if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
-      py[j] -= qy[j];
-      ay[j] += ry[j];
-      if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
+      if (MK) {  // the carry of substep k is the table's next bit, from bit 31 down
+        px[j] -= qx[j] - (ax[j] >> 31);
+        ax[j] = (int)((unsigned)ax[j] << 1);
+        py[j] -= qy[j] - (ay[j] >> 31);
+        ay[j] = (int)((unsigned)ay[j] << 1);
+      } else {
+        px[j] -= qx[j];
+        ax[j] += rx[j];
+        if (ax[j] >= N) { ax[j] -= N; px[j] -= 1; }
+        py[j] -= qy[j];
+        ay[j] += ry[j];
+        if (ay[j] >= N) { ay[j] -= N; py[j] -= 1; }
+      }
       int s0, s1;
       if (FAST) {
         s0 = tap_shared<WIDE>(b0, px[j], py[j]);
@@ -634,19 +659,27 @@ __device__ __forceinline__ void tile_substeps(const SimParams& p, const TileLayo
                               py[j] + Fy[j]);
       }
       const int I = lerp12<WIDE>(s0, s1, w);
-      if (XT) cx[j] = Crossing{Ip[j], I, R[j], 0};
-      n[j] = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
-      if (!act[j]) n[j] = 0;
       if (XT) {
-        cx[j].c = n[j] > 0 ? Cp[j] : Cn[j];
+        Iold[j] = Ip[j];
         Ip[j] = I;
       }
+      n[j] = threshold_step<RESET>(I, R[j], Cp[j], Cn[j]);
+      if (!act[j]) n[j] = 0;
       if (!DENSE) L.snk[k * TP + nk_at[j]] = (short)n[j];
     }
     if (XT) {
-      if (row_in)  // warp-uniform
+      if (row_in) {  // warp-uniform
+        // the reference before the substep: reset mode, the previous value;
+        // else the reference after it less the levels crossed
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int c = n[j] > 0 ? Cp[j] : Cn[j];
+          const int rb = RESET ? Iold[j] : R[j] - n[j] * c;
+          cx[j] = Crossing{Iold[j], Ip[j], rb, c};
+        }
         publish_row_xt(p, segf + (long long)k * p.segs_per_k + warp * p.tiles_x, n[0], lx[0],
                        n[1], lx[1], t_last, L.stk[k], tx0, y, ws, cx[0], cx[1]);
+      }
       t_last = L.stk[k];
     } else if (DENSE && row_in) {  // warp-uniform
       publish_row(p, segf + (long long)k * p.segs_per_k + warp * p.tiles_x, n[0], lx[0], true,
@@ -1571,15 +1604,19 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         if (ty0 + warp < H)
           for (int k = lane; k < N; k += 32)
             segf[(long long)k * p.segs_per_k + warp * p.tiles_x] = Seg{0ull, 0ull, 0, -1};
-      } else if (fast) {
-        tile_substeps<RESET, WIDE, true, true, TH_, true>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur,
-                                                          segf, lx, ly, nk_at, act, Fx, Fy, R,
-                                                          Cp, Cn, &s_stage[warp], t_frame);
       } else {
-        tile_substeps<RESET, WIDE, false, true, TH_, true>(p, V, N, mN, tx0, ty0, b0, b1, prv,
-                                                           cur, segf, lx, ly, nk_at, act, Fx,
-                                                           Fy, R, Cp, Cn, &s_stage[warp],
-                                                           t_frame);
+#define EVSIM_XT(FA, MK)                                                                      \
+  tile_substeps<RESET, WIDE, FA, true, TH_, true, MK>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, \
+                                                      segf, lx, ly, nk_at, act, Fx, Fy, R, Cp, \
+                                                      Cn, &s_stage[warp], t_frame, s_cmask[par])
+        if (fast) {
+          if (N <= 32) EVSIM_XT(true, true);
+          else EVSIM_XT(true, false);
+        } else {
+          if (N <= 32) EVSIM_XT(false, true);
+          else EVSIM_XT(false, false);
+        }
+#undef EVSIM_XT
       }
     } else if (SPARSE && dsw && !(fast && N <= 32)) {
       if (fast)

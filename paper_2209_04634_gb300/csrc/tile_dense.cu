@@ -6,7 +6,7 @@
 namespace evsim {
 
 cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st) {
-  if (p.xtime) return launch_xtime(p, b, false, st);
+  if (p.xtime) return launch_xtime_dense(p, b, st);
   return launch_tile_mode<false>(p, b, st);
 }
 

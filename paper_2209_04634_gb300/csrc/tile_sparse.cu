@@ -6,7 +6,7 @@
 namespace evsim {
 
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st) {
-  if (p.xtime) return launch_xtime(p, b, true, st);
+  if (p.xtime) return launch_xtime_sparse(p, b, st);
   return launch_tile_mode<true>(p, b, st);
 }
 

@@ -1,5 +1,5 @@
 // The tile kernel with per-crossing event times (SIM_TIME_CROSSING), dense
-// and sparse, 64x16 tiles: every pixel runs the dense row mapping (sparse:
+// instances, 64x16 tiles: every pixel runs the dense row mapping (sparse:
 // inactive pixels masked) and every row with an event stages its events,
 // each at the time the line between the values of consecutive substeps meets
 // the level it crosses.
@@ -7,12 +7,11 @@
 
 namespace evsim {
 
-cudaError_t launch_xtime(const SimParams& p, const BatchArg& b, bool sparse, cudaStream_t st) {
-  return sparse ? launch_tile_shape<true, 16, true>(p, b, st)
-                : launch_tile_shape<false, 16, true>(p, b, st);
+cudaError_t launch_xtime_dense(const SimParams& p, const BatchArg& b, cudaStream_t st) {
+  return launch_tile_shape<false, 16, true>(p, b, st);
 }
 
-cudaError_t configure_xtime_kernels(int n_max) {
+cudaError_t configure_xtime_dense_kernels(int n_max) {
   set_tile_attr<false, false, false, false, true>(n_max);
   set_tile_attr<false, true, false, false, true>(n_max);
   set_tile_attr<false, false, true, false, true>(n_max);
@@ -21,14 +20,6 @@ cudaError_t configure_xtime_kernels(int n_max) {
   set_tile_attr<true, true, false, false, true>(n_max);
   set_tile_attr<true, false, true, false, true>(n_max);
   set_tile_attr<true, true, true, false, true>(n_max);
-  set_tile_attr<false, false, false, true, true>(n_max);
-  set_tile_attr<false, true, false, true, true>(n_max);
-  set_tile_attr<false, false, true, true, true>(n_max);
-  set_tile_attr<false, true, true, true, true>(n_max);
-  set_tile_attr<true, false, false, true, true>(n_max);
-  set_tile_attr<true, true, false, true, true>(n_max);
-  set_tile_attr<true, false, true, true, true>(n_max);
-  set_tile_attr<true, true, true, true, true>(n_max);
   return cudaGetLastError();
 }
 
