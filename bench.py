@@ -85,24 +85,40 @@ def barrier(ws):
         dist.barrier()
 
 
+def _reduce(v: float, op) -> float:
+    import torch
+    import torch.distributed as dist
+    # NCCL reduces device tensors; gloo (the CPU tests of this path) host ones
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
 def max_over_ranks(ws, v: float) -> float:
     if ws == 1:
         return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _reduce(v, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(ws, v: float) -> float:
     if ws == 1:
         return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(v, dist.ReduceOp.SUM)
+
+
+def weak_scaling_value(ws, units: float, ms: float) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: the units every rank
+    processed over the slowest rank's time (Gunits/s), and that time (ms)."""
+    ms_max = max_over_ranks(ws, ms)
+    return sum_over_ranks(ws, units) / (ms_max / 1e3) / 1e9, ms_max
+
+
+def stream_seed(rank: int) -> int:
+    """Seed of rank's stream: every replica simulates its own sequence."""
+    return 4209 + 1000 * rank
 
 
 class ClockSampler:
@@ -230,7 +246,7 @@ def run_ours(args, ws, rank, local):
     build.build()
     evsim.load()
 
-    seq = synth.warped_texture(frames=args.frames, seed=4209 + 1000 * rank)
+    seq = synth.warped_texture(frames=args.frames, seed=stream_seed(rank))
     if args.substeps:
         seq.substeps = args.substeps
     F, H, W = seq.frames.shape
@@ -305,7 +321,7 @@ def run_ours(args, ws, rank, local):
     barrier(ws)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ws, ms)
+    value, ms_max = weak_scaling_value(ws, work_step * args.steps, ms)
     ktimes = {}
     launches = 0
     for m, sim in sims.items():
@@ -315,9 +331,7 @@ def run_ours(args, ws, rank, local):
                 ktimes[("dense" if m == evsim.SIM_DENSE else "sparse") + "." + name] = (t, c)
                 launches += c
         sim.set_profiling(False)
-    total_work = sum_over_ranks(ws, work_step * args.steps)
     total_ev = sum_over_ranks(ws, n_ev)
-    value = total_work / (ms_max / 1e3) / 1e9
     line_roofline = roofline_dense(seq, ktimes, work[evsim.SIM_DENSE],
                                    tune["dense"]["tile_height"])
 
