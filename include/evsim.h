@@ -171,7 +171,8 @@ enum { SIM_K_INIT = 0, SIM_K_FLOWMAX = 1, SIM_K_DENSE = 2, SIM_K_MASK = 3,
        SIM_K_SPARSE = 4, SIM_K_ORDER = 5, SIM_K_COPY = 6, SIM_K_COUNT = 7 };
 
 /* Fill *cfg with defaults for a width x height luma stream: dense, N = 8,
- * log intensity, accumulate mode, C = 0.2, library-owned stream. */
+ * log intensity, accumulate mode, C = 0.2, substep event times, autotuned
+ * tile shape, library-owned stream. */
 int sim_config_default(sim_config* cfg, int32_t width, int32_t height);
 
 /* Create a simulator.  Allocates all device state (frame ring, reference,

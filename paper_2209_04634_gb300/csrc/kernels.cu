@@ -308,9 +308,9 @@ __global__ void k_accumulate(const Ev* ev, long long n, int W, int H, long long 
 
 // Balanced block order for the next batch (one block): tiles ranked by the
 // cycles their blocks took in the last batch (heaviest first, ties by tile
-// index), laid out in serpentine order over the ranks - round 0 of one block
-// per SM takes the heaviest tiles, round 1 the lightest in reverse - so the
-// heaviest tile shares its SM with the lightest.  An order of the tiles like
+// index), laid out in serpentine order over the ranks - the first wave of
+// one block per SM takes the heaviest tiles, the second wave the lightest in
+// reverse - so the heaviest tile shares its SM with the lightest.  An order of the tiles like
 // any other: it changes only the schedule.
 __global__ void k_plan(int T, int S, const unsigned* cost, int* order) {
   __shared__ unsigned sc[PLAN_MAX_TILES];
