@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--tile-height", type=int, default=0, choices=[0, 8, 16],
                     help="batch kernel tile height; 0: the library's autotuner chooses")
+    ap.add_argument("--max-flow", type=float, default=8.0,
+                    help="largest flow of the workload in px/frame (profiling runs: it sets "
+                         "the tile kernel's halo size); the workload's is 8")
     ap.add_argument("--substeps", type=int, default=0,
                     help="fixed substeps per frame for profiling runs (splits a kernel's "
                          "per-substep from its per-frame work); 0: the workload's adaptive N")
@@ -246,7 +249,7 @@ def run_ours(args, ws, rank, local):
     build.build()
     evsim.load()
 
-    seq = synth.warped_texture(frames=args.frames, seed=stream_seed(rank))
+    seq = synth.warped_texture(frames=args.frames, seed=stream_seed(rank), max_flow=args.max_flow)
     if args.substeps:
         seq.substeps = args.substeps
     F, H, W = seq.frames.shape
@@ -345,7 +348,8 @@ def run_ours(args, ws, rank, local):
                    "active_pixel_substeps_per_step_sparse": active_work,
                    "l2": "inputs larger than L2 (277 MB resident), no flush",
                    "parallelism": f"{ws} independent stream(s), one per GPU",
-                   "substeps": args.substeps if args.substeps else "adaptive"},
+                   "substeps": args.substeps if args.substeps else "adaptive",
+                   "max_flow_px": args.max_flow},
         "events_per_s": total_ev / (ms_max / 1e3),
         "wall_ms_per_step": wall / args.steps * 1e3,
         "kernel_us_per_launch": {k: v[0] / v[1] * 1e3 for k, v in ktimes.items()},
