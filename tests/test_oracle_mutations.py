@@ -68,6 +68,17 @@ MUTATIONS = {
     "accumulate_window_end_inclusive": ("if (t < t_begin || t >= t_end) continue;",
                                         "if (t < t_begin || t > t_end) continue;"),
     "accumulate_transposed": ("frame[(int64_t)y * W + x] +=", "frame[(int64_t)x * H + y] +="),
+    "activity_default_uses_the_larger_threshold": ("(cp < cn ? cp : cn);", "(cp > cn ? cp : cn);"),
+    "no_horizontal_neighbour": ("int64_t x1 = ix + 1 < W ? ix + 1 : W - 1;", "int64_t x1 = ix;"),
+    "threshold_maps_swapped": ("          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n"
+                               "          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n"
+                               "          int64_t D = I - R[p];",
+                               "          int32_t cp = pixel_threshold(cneg_map, c->c_pos_q16, p);\n"
+                               "          int32_t cn = pixel_threshold(cpos_map, c->c_neg_q16, p);\n"
+                               "          int64_t D = I - R[p];"),
+    "luma_rounding_dropped": ("(77 * r + 150 * g + 29 * b + 128) >> 8", "(77 * r + 150 * g + 29 * b) >> 8"),
+    "linear_table_scale": ("lut[v] = v * 65536;", "lut[v] = v * 65535;"),
+    "nan_flow_not_zeroed": ("  if (d != d) return 0;\n", "\n"),
     # per-crossing event times (orc_crossing_time and its callers)
     "crossing_level_counted_from_zero": ("orc_crossing_time(tk1, tk, ip, I, Rb + j * cp, 1)",
                                          "orc_crossing_time(tk1, tk, ip, I, Rb + (j - 1) * cp, 1)"),
@@ -133,6 +144,7 @@ def battery():
                 pins.test_crossing_times_of_monotone_ramps_follow_the_exact_line(N, cp, cn)
     yield lambda: pins.test_crossing_times_reset_one_substep(5 * 65536 + 123)
     yield pins.test_crossing_time_primitive_properties
+    yield pins.test_sparse_default_activity_threshold_is_the_smaller_threshold
     yield lambda: pins.test_crossing_times_keep_events_and_stay_inside_their_substep(
         oracle.SPARSE, oracle.ACCUM)
 

@@ -946,3 +946,20 @@ def test_crossing_times_second_restatement_on_random_8x8(case):
                            max_sub=6, crossing=True)
     t, x, y, p = oracle.unpack(r["events"])
     assert list(zip(t.tolist(), x.tolist(), y.tolist(), p.tolist())) == ev
+
+
+def test_sparse_default_activity_threshold_is_the_smaller_threshold():
+    """Sec. III-B with the default activity threshold min(C_pos, C_neg)
+    (reading O10): a uniform linear ramp of 2 grey levels per frame with
+    C_neg = 1 < 2 < C_pos = 3 levels is active at every pixel and frame, so
+    the sparse run equals the dense one: one positive event per pixel when
+    the accumulated rise reaches 3 levels (frame 2), none before."""
+    F, H, W = 3, 6, 9
+    frames = np.stack([np.full((H, W), 100 + 2 * i, np.uint8) for i in range(F)])
+    kw = dict(substeps=1, intensity=oracle.LINEAR, c_pos_q16=3 * Q, c_neg_q16=1 * Q)
+    d = oracle.run(frames, zero_flows(frames), times(F), mode=oracle.DENSE, **kw)
+    s = oracle.run(frames, zero_flows(frames), times(F), mode=oracle.SPARSE, **kw)
+    assert list(s["active_per_frame"][1:]) == [H * W, H * W]
+    assert np.array_equal(s["events"].view(np.uint64), d["events"].view(np.uint64))
+    t, x, y, p = oracle.unpack(s["events"])
+    assert len(t) == H * W and np.all(p == 1) and np.all(t == 2 * 1000)
