@@ -79,6 +79,15 @@ MUTATIONS = {
     "luma_rounding_dropped": ("(77 * r + 150 * g + 29 * b + 128) >> 8", "(77 * r + 150 * g + 29 * b) >> 8"),
     "linear_table_scale": ("lut[v] = v * 65536;", "lut[v] = v * 65535;"),
     "nan_flow_not_zeroed": ("  if (d != d) return 0;\n", "\n"),
+    "activity_against_the_reference": ("int64_t d = (int64_t)Lcur[p] - Lprev[p];",
+                                       "int64_t d = (int64_t)Lcur[p] - R[p];"),
+    "adaptive_n_over_inactive_pixels": ("        if (!act[p]) continue;\n        int64_t f2",
+                                        "        int64_t f2"),
+    "accum_negative_strict": ("} else if (-D >= cn) {", "} else if (-D > cn) {"),
+    "reset_negative_non_strict": ("else if (D < -(int64_t)cn)", "else if (D <= -(int64_t)cn)"),
+    "accumulate_window_start_exclusive": ("if (t < t_begin || t >= t_end) continue;",
+                                          "if (t <= t_begin || t >= t_end) continue;"),
+    "diff_starts_at_the_second_frame": ("    if (i < 2) continue;", "    if (i < 1) continue;"),
     # per-crossing event times (orc_crossing_time and its callers)
     "crossing_level_counted_from_zero": ("orc_crossing_time(tk1, tk, ip, I, Rb + j * cp, 1)",
                                          "orc_crossing_time(tk1, tk, ip, I, Rb + (j - 1) * cp, 1)"),
@@ -145,6 +154,8 @@ def battery():
     yield lambda: pins.test_crossing_times_reset_one_substep(5 * 65536 + 123)
     yield pins.test_crossing_time_primitive_properties
     yield pins.test_sparse_default_activity_threshold_is_the_smaller_threshold
+    yield pins.test_sparse_disregards_slow_drift_below_the_activity_threshold
+    yield pins.test_sparse_adaptive_substeps_follow_the_active_pixels_only
     yield lambda: pins.test_crossing_times_keep_events_and_stay_inside_their_substep(
         oracle.SPARSE, oracle.ACCUM)
 

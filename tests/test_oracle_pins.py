@@ -963,3 +963,37 @@ def test_sparse_default_activity_threshold_is_the_smaller_threshold():
     assert np.array_equal(s["events"].view(np.uint64), d["events"].view(np.uint64))
     t, x, y, p = oracle.unpack(s["events"])
     assert len(t) == H * W and np.all(p == 1) and np.all(t == 2 * 1000)
+
+
+def test_sparse_disregards_slow_drift_below_the_activity_threshold():
+    """Sec. III-B: a pixel whose value changes less than the activity
+    threshold from one frame to the next is disregarded, however far it has
+    drifted from its reference.  A uniform drift of 1 grey level per frame
+    with C = 3 levels: the dense method emits one event per pixel every three
+    frames, the sparse method none."""
+    F, H, W = 7, 4, 5
+    frames = np.stack([np.full((H, W), 100 + i, np.uint8) for i in range(F)])
+    kw = dict(substeps=2, intensity=oracle.LINEAR, c_pos_q16=3 * Q, c_neg_q16=3 * Q)
+    d = oracle.run(frames, zero_flows(frames), times(F), mode=oracle.DENSE, **kw)
+    s = oracle.run(frames, zero_flows(frames), times(F), mode=oracle.SPARSE, **kw)
+    assert len(d["events"]) == 2 * H * W
+    assert len(s["events"]) == 0 and not np.any(s["active_per_frame"])
+    assert np.array_equal(s["R"], np.full((H, W), 100 * Q))
+
+
+def test_sparse_adaptive_substeps_follow_the_active_pixels_only():
+    """Sec. III-B with adaptive N (reading O8): the substep count of a sparse
+    frame comes from the flow of its active pixels; a larger flow at pixels
+    that did not change does not raise it (the dense method takes every
+    pixel's flow)."""
+    F, H, W = 2, 12, 16
+    frames = np.full((F, H, W), 90, np.uint8)
+    frames[1, 3:6, 4:8] = 150                       # the only pixels that change
+    flows = np.zeros((F, H, W, 2), np.float32)
+    flows[1] = (7.0, 0.0)                           # a large flow everywhere ...
+    flows[1, 3:6, 4:8] = (2.0, -0.5)                # ... but 2.06 px at the active ones
+    kw = dict(substeps=0, max_substeps=16, c_pos_q16=13107, c_neg_q16=13107)
+    s = oracle.run(frames, flows, times(F), mode=oracle.SPARSE, **kw)
+    d = oracle.run(frames, flows, times(F), mode=oracle.DENSE, **kw)
+    assert s["active_per_frame"][1] == 12
+    assert s["n_per_frame"][1] == 3 and d["n_per_frame"][1] == 7
