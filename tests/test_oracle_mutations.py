@@ -88,6 +88,16 @@ MUTATIONS = {
     "accumulate_window_start_exclusive": ("if (t < t_begin || t >= t_end) continue;",
                                           "if (t <= t_begin || t >= t_end) continue;"),
     "diff_starts_at_the_second_frame": ("    if (i < 2) continue;", "    if (i < 1) continue;"),
+    "diff_flow_of_the_previous_frame": ("    const float* fl = flows + (int64_t)i * P * 2;\n    int64_t m = 0;",
+                                        "    const float* fl = flows + (int64_t)(i - 1) * P * 2;\n    int64_t m = 0;"),
+    "diff_negative_threshold_uses_cp": ("else if (I < -(int64_t)cn) emit(", "else if (I < -(int64_t)cp) emit("),
+    "diff_time_from_the_frame_before_last": ("    int64_t t_prev = t_us[i - 1] - t_us[0];\n    int64_t dt = t_us[i] - t_us[i - 1];\n    for (int32_t k = 1; k <= N; ++k) {\n      int64_t w = ((int64_t)k * 8192 + N) / (2 * (int64_t)N);\n      uint32_t tk = (uint32_t)(t_prev + floordiv((int64_t)k * dt, N));\n      for (int32_t y = 0; y < H; ++y) {\n        for (int32_t x = 0; x < W; ++x) {\n          int64_t p = (int64_t)y * W + x;\n          /* interpolated difference",
+                                             "    int64_t t_prev = t_us[i - 2] - t_us[0];\n    int64_t dt = t_us[i] - t_us[i - 1];\n    for (int32_t k = 1; k <= N; ++k) {\n      int64_t w = ((int64_t)k * 8192 + N) / (2 * (int64_t)N);\n      uint32_t tk = (uint32_t)(t_prev + floordiv((int64_t)k * dt, N));\n      for (int32_t y = 0; y < H; ++y) {\n        for (int32_t x = 0; x < W; ++x) {\n          int64_t p = (int64_t)y * W + x;\n          /* interpolated difference"),
+    "fraction_has_thirteen_bits": ("int64_t fx = (px & 0xFFFF) >> 4,", "int64_t fx = (px & 0xFFFF) >> 3,"),
+    "interval_from_the_first_frame": ("    int64_t dt = t_us[i] - t_us[i - 1];\n    if (dt <= 0)",
+                                      "    int64_t dt = t_us[i] - t_us[0];\n    if (dt <= 0)"),
+    "sparse_inactive_pixels_simulated": ("          if (!act[p]) continue;\n          /* Interpolated frame",
+                                         "          /* Interpolated frame"),
     # per-crossing event times (orc_crossing_time and its callers)
     "crossing_level_counted_from_zero": ("orc_crossing_time(tk1, tk, ip, I, Rb + j * cp, 1)",
                                          "orc_crossing_time(tk1, tk, ip, I, Rb + (j - 1) * cp, 1)"),
