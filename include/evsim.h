@@ -324,7 +324,9 @@ const char* sim_version(void);
  * *tile_height_out (if not NULL) receives 8 or 16; us_out (if not NULL, 2
  * doubles) the kernel time per frame in microseconds of shapes 16 and 8
  * (each in its faster order).  sim_get_stats reports a handle's shape and
- * order.
+ * order.  The table serves substep-time handles (cfg->event_time is not
+ * part of its key and is not timed); SIM_TIME_CROSSING handles run 64 x 16
+ * tiles in block order.
  * Allocates two temporary simulators and the probe's frames on the current
  * device and frees them before returning; blocks until done.  Errors:
  * SIM_ERR_ARG (bad configuration or frames), SIM_ERR_OOM, SIM_ERR_CUDA. */
