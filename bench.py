@@ -231,7 +231,10 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dts / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": args.frames, "width": seq.width,
+                   "height": seq.height, "substeps": "adaptive", "max_flow_px": 8.0,
+                   "parallelism": "the CPU oracle on rank 0", "sample": sample},
         "events_per_s": evs / dts,
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                          "sample": sample},
