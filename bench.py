@@ -203,8 +203,8 @@ def cpu_baseline(seq, frames_sample: int):
     t0 = time.perf_counter()
     for mode in (oracle.DENSE, oracle.SPARSE):
         r = oracle.run(s.frames, s.flows, s.t_us, mode=mode, substeps=s.substeps,
-                       max_substeps=s.max_substeps, c_pos_q16=evsim.q16(s.c_pos),
-                       c_neg_q16=evsim.q16(s.c_neg), cpos_map=s.cpos_map, cneg_map=s.cneg_map)
+                       max_substeps=s.max_substeps, c_pos_q16=oracle.q16(s.c_pos),
+                       c_neg_q16=oracle.q16(s.c_neg), cpos_map=s.cpos_map, cneg_map=s.cneg_map)
         work += int((r["n_per_frame"][1:].astype("int64") * s.width * s.height).sum())
         nev += len(r["events"])
     dt = time.perf_counter() - t0

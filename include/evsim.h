@@ -170,19 +170,34 @@ typedef struct {
 enum { SIM_K_INIT = 0, SIM_K_FLOWMAX = 1, SIM_K_DENSE = 2, SIM_K_MASK = 3,
        SIM_K_SPARSE = 4, SIM_K_ORDER = 5, SIM_K_COPY = 6, SIM_K_COUNT = 7 };
 
+/* A threshold in log units (SIM_LOG) or 8-bit intensity units (SIM_LINEAR,
+ * Table I's C = 2 / 10 / 20) as the Q16 integer that sim_config carries:
+ * round-half-even(|c| 65536).  The sign is dropped (Table I lists C_neg as a
+ * negative number; the library takes magnitudes).  Returns SIM_ERR_ARG for a
+ * value that is not finite or whose Q16 form is 2^30 or more.  Thresholds
+ * cross this boundary as Q16 integers so that the library and any checker
+ * compare them exactly. */
+int32_t sim_threshold_q16(double c);
+
 /* Fill *cfg with defaults for a width x height luma stream: dense, N = 8,
  * log intensity, accumulate mode, C = 0.2, substep event times, autotuned
  * tile shape, library-owned stream. */
 int sim_config_default(sim_config* cfg, int32_t width, int32_t height);
 
-/* Create a simulator.  Allocates all device state (frame ring, reference,
+/* Create a simulator (the per-stream state of the methods of Sec. III-A /
+ * III-B: the reference each pixel's interpolated log intensity is compared
+ * with, the previous frame, the thresholds C_pos / C_neg of the two-case
+ * equations of Sec. III-A).  Allocates all device state (frame ring, reference,
  * staging and event buffers) and copies the optional threshold maps.
  * Thresholds must be >= 1; in accumulate mode they must also be at least
  * (LUT[255] - LUT[0]) / 32766 (12 for SIM_LOG, 511 for SIM_LINEAR) so that one
  * substep emits at most 32767 events per pixel.  *out is set on SIM_OK only. */
 int sim_create(const sim_config* cfg, sim_t** out);
 
-/* Push camera frame i with the flow from frame i-1 to frame i.
+/* Push camera frame i with the flow from frame i-1 to frame i: the
+ * interpolation of N frames along the flow between frames i-1 and i and the
+ * threshold test of each against the reference (Sec. III, Sec. III-A; Sec.
+ * III-B for SIM_SPARSE).
  *   frame : height rows of pitch_bytes bytes, width * pixel_format bytes used.
  *   flow  : height * width * 2 floats (dx, dy) in px per frame interval,
  *           row-major, 8-byte aligned; ignored (may be NULL) on the first push.
@@ -212,7 +227,8 @@ int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float
 int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t pitch_bytes,
                     const float* const* flows, const int64_t* t_us, int32_t mem);
 
-/* Copy up to cap committed events, in output order, into out (host or device
+/* The output of the method: events <x, y, t, p> (Fig. 1 caption), here
+ * sim_event records.  Copy up to cap committed events, in output order, into out (host or device
  * memory per mem) and set *n_out.  Returns SIM_MORE if events remain (the next
  * call continues where this one stopped).  Waits for the handle's stream.
  * If a pushed frame failed on the device, returns that error code and
@@ -243,7 +259,8 @@ int sim_kernel_time(sim_t* s, int32_t kind, double* ms, int64_t* launches, int32
  * Waits for the handle's stream. */
 int sim_reset(sim_t* s);
 
-/* Release every resource of the handle (waits for its stream). */
+/* End of a stream (the paper's simulators run over a finite frame sequence,
+ * Sec. IV-A).  Release every resource of the handle (waits for its stream). */
 int sim_destroy(sim_t* s);
 
 /* Static English description of a return code. */
@@ -617,22 +634,33 @@ int sim_serve_run(const sim_serve_config* cfg, sim_serve_result* res);
  * SIM_ERR_TIME_RANGE, SIM_ERR_TOO_LARGE when the problem does not fit the
  * scratch array (checked before any device work), SIM_ERR_EVENT_OVERFLOW
  * when the events exceed event_capacity or the 8-byte staging that remains
- * after the other parts (then ref_out has already been updated and the
- * events buffer holds no usable result), SIM_ERR_DEVICE_TIMEOUT,
- * SIM_ERR_CUDA / SIM_ERR_NO_DEVICE.
+ * after the other parts, SIM_ERR_DEVICE_TIMEOUT, SIM_ERR_CUDA /
+ * SIM_ERR_NO_DEVICE.
+ * A failed step changes no reference the caller can still need: ref_in is
+ * never written; ref_out is written only by a step that returns SIM_OK when
+ * it equals ref_in or ref_in is NULL (the new reference is built in the
+ * scratch array and copied to ref_out once the step has been checked), so
+ * the same call can be repeated, e.g. with a larger event buffer.  With
+ * distinct ref_in and ref_out, ref_out is undefined after an error.  The
+ * events buffer holds no usable result after an error.
  *
  * Scratch: the array needs about 2 W H + 24.3 N_max H ceil(W / 64) bytes
- * (N_max = substeps, or max_substeps when adaptive), plus 2 KB, plus at
- * least 1 MiB of staging; larger problems get SIM_ERR_TOO_LARGE.  The 32 MiB
- * array admits 1280 x 720 at any N_max, 1920 x 1080 up to N_max = 36 and
- * 3840 x 2160 up to N_max = 5.
- * The first call on a device, with that device current, looks the array's
- * address up (cudaGetSymbolAddress): make that first call before any stream
- * capture begins on the device.  Each call clears the parts that must start
- * at zero.  Every call on a device shares the one array: calls whose device
- * work overlaps (two streams, or two host threads) race and corrupt each
- * other's results; order them on one stream or serialise them.  The call
- * waits for its stream before returning (it reads the event count back). */
+ * (N_max = substeps, or max_substeps when adaptive), plus 4 W H more for an
+ * in-place or stream-starting accumulate step (ref_in == ref_out or NULL),
+ * plus 2 KB, plus at least 1 MiB of staging; larger problems get
+ * SIM_ERR_TOO_LARGE.  The 32 MiB array admits 1280 x 720 at any N_max and
+ * 1920 x 1080 up to N_max = 36 (in place: 25); 3840 x 2160 up to N_max = 5
+ * (in place: does not fit).
+ * Set-up: on the first call on a device (and again after the device's
+ * context changes, e.g. after cudaDeviceReset) the call looks the array's
+ * address up in the current context (cudaGetSymbolAddress) and sets the
+ * kernels' shared-memory limits.  Each call clears the parts of the array
+ * that must start at zero.  Every call on a device shares the one array:
+ * calls whose device work overlaps (two streams, or two host threads) race
+ * and corrupt each other's results; order them on one stream or serialise
+ * them.  The call is synchronous: it waits for its stream before returning
+ * (it reads the step's status and event count back into host memory), so it
+ * must not be called while its stream is being captured into a CUDA graph. */
 #define SIM_STATIC_SCRATCH_BYTES (32LL << 20)
 int sim_step_pair_static(const sim_config* cfg, const void* prev_frame, int64_t prev_pitch,
                          const void* frame, int64_t pitch, const float* flow, int64_t t_prev_us,

@@ -881,9 +881,9 @@ __global__ void __launch_bounds__(NT) k_drain(GroupArg g, DrainArg d) {
   }
 }
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
-void set_tile_multi_attr(size_t bytes) {
-  cudaFuncSetAttribute(k_tile_multi<RESET, MAPS, WIDE, SPARSE>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t set_tile_multi_attr(size_t bytes) {
+  return cudaFuncSetAttribute(k_tile_multi<RESET, MAPS, WIDE, SPARSE>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <bool SPARSE>
@@ -917,12 +917,15 @@ int device_sm_count() {
   return n;
 }
 
+// Returns the first failing cudaFuncSetAttribute's error (each call's return
+// code is checked; an error left pending by the caller is neither reported
+// nor cleared here).
 cudaError_t configure_kernels(int n_max) {
-  configure_dense_kernels(n_max);
-  configure_sparse_kernels(n_max);
-  configure_xtime_dense_kernels(n_max);
-  configure_xtime_sparse_kernels(n_max);
-  return cudaGetLastError();
+  cudaError_t e = configure_dense_kernels(n_max);
+  if (e == cudaSuccess) e = configure_sparse_kernels(n_max);
+  if (e == cudaSuccess) e = configure_xtime_dense_kernels(n_max);
+  if (e == cudaSuccess) e = configure_xtime_sparse_kernels(n_max);
+  return e;
 }
 
 cudaError_t launch_init(const SimParams& p, const FrameDesc& f, cudaStream_t st) {
@@ -987,23 +990,26 @@ int tile_class(const SimParams& p) {
 }
 
 cudaError_t configure_group_kernels(size_t t) {
-  set_tile_multi_attr<false, false, false, false>(t);
-  set_tile_multi_attr<false, true, false, false>(t);
-  set_tile_multi_attr<false, false, true, false>(t);
-  set_tile_multi_attr<false, true, true, false>(t);
-  set_tile_multi_attr<true, false, false, false>(t);
-  set_tile_multi_attr<true, true, false, false>(t);
-  set_tile_multi_attr<true, false, true, false>(t);
-  set_tile_multi_attr<true, true, true, false>(t);
-  set_tile_multi_attr<false, false, false, true>(t);
-  set_tile_multi_attr<false, true, false, true>(t);
-  set_tile_multi_attr<false, false, true, true>(t);
-  set_tile_multi_attr<false, true, true, true>(t);
-  set_tile_multi_attr<true, false, false, true>(t);
-  set_tile_multi_attr<true, true, false, true>(t);
-  set_tile_multi_attr<true, false, true, true>(t);
-  set_tile_multi_attr<true, true, true, true>(t);
-  return cudaGetLastError();
+  const cudaError_t es[16] = {
+      set_tile_multi_attr<false, false, false, false>(t),
+      set_tile_multi_attr<false, true, false, false>(t),
+      set_tile_multi_attr<false, false, true, false>(t),
+      set_tile_multi_attr<false, true, true, false>(t),
+      set_tile_multi_attr<true, false, false, false>(t),
+      set_tile_multi_attr<true, true, false, false>(t),
+      set_tile_multi_attr<true, false, true, false>(t),
+      set_tile_multi_attr<true, true, true, false>(t),
+      set_tile_multi_attr<false, false, false, true>(t),
+      set_tile_multi_attr<false, true, false, true>(t),
+      set_tile_multi_attr<false, false, true, true>(t),
+      set_tile_multi_attr<false, true, true, true>(t),
+      set_tile_multi_attr<true, false, false, true>(t),
+      set_tile_multi_attr<true, true, false, true>(t),
+      set_tile_multi_attr<true, false, true, true>(t),
+      set_tile_multi_attr<true, true, true, true>(t)};
+  for (cudaError_t e : es)
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 cudaError_t launch_pre_multi(const GroupArg& g, int grid, cudaStream_t st) {

@@ -314,6 +314,13 @@ const char* sim_strerror(int code) {
   }
 }
 
+int32_t sim_threshold_q16(double c) {
+  if (!std::isfinite(c)) return SIM_ERR_ARG;
+  const double q = std::nearbyint(std::fabs(c) * 65536.0);  // ties to even
+  if (q >= 1073741824.0) return SIM_ERR_ARG;
+  return (int32_t)q;
+}
+
 int sim_config_default(sim_config* cfg, int32_t width, int32_t height) {
   if (!cfg) return SIM_ERR_ARG;
   std::memset(cfg, 0, sizeof(*cfg));

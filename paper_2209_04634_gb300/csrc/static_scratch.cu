@@ -15,7 +15,10 @@
 // The array is shared by every call on a device: it is re-initialised at the
 // start of each call (control block, tile progress words, look-back words
 // and flow maxima are cleared there), and two calls whose GPU work overlaps
-// race on it.
+// race on it.  An accumulate step that updates its reference in place (or
+// starts one) builds the new reference in the array and copies it out only
+// after the step has been checked, so a failed step leaves the caller's
+// reference as it was.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -37,7 +40,47 @@ static __device__ __align__(256) unsigned char g_scratch[SIM_STATIC_SCRATCH_BYTE
 
 constexpr int MAX_DEVICES = 256;
 std::mutex g_setup_mu;
-unsigned char* g_base[MAX_DEVICES] = {};  // address of g_scratch on each device (set-up done)
+
+// Set-up of one device, valid for one CUDA context on it: the array's address
+// in that context and the tile kernels' shared-memory permission.  A context
+// is recognised by its unique id (cuCtxGetId, reached through the runtime's
+// driver entry points), so a cudaDeviceReset, or another context made current
+// on the same device, leads to a fresh set-up instead of a stale address.
+struct DeviceSetup {
+  unsigned long long ctx_id;  // 0: not set up
+  unsigned char* base;        // address of g_scratch in that context
+};
+DeviceSetup g_dev[MAX_DEVICES] = {};
+
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// Unique id of the calling thread's current context, or 0 when it cannot be
+// told (no current context, or a driver without the query).  Call under
+// g_setup_mu.
+unsigned long long current_context_id() {
+  if (!g_ctx_fns_tried) {
+    g_ctx_fns_tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_ctx_current = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_ctx_id = (CtxGetIdFn)f;
+  }
+  if (!g_ctx_current || !g_ctx_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&ctx) != 0 || !ctx) return 0;
+  if (g_ctx_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 // Start of the array: uploaded by every call in one copy.
 struct alignas(256) Header {
@@ -59,13 +102,14 @@ struct Layout {
   long long tdone;
   long long status;
   long long ring0, ring1;
+  long long rnew;      // in-place or new-stream accumulate steps: the new reference (4 P)
   long long seg;
   long long staging;
   long long stage_events;
   long long need;      // bytes up to and including the minimum staging
 };
 
-Layout layout(long long P, long long nseg, long long tiles) {
+Layout layout(long long P, long long nseg, long long tiles, bool rnew) {
   Layout l{};
   const long long nchunks = (nseg + evsim::OCHUNK - 1) / evsim::OCHUNK;
   l.zero = align256(sizeof(Header));
@@ -74,7 +118,8 @@ Layout layout(long long P, long long nseg, long long tiles) {
   l.zero_len = l.status - l.zero + nchunks * 8;
   l.ring0 = align256(l.zero + l.zero_len);
   l.ring1 = align256(l.ring0 + P);
-  l.seg = align256(l.ring1 + P);
+  l.rnew = align256(l.ring1 + P);
+  l.seg = align256(l.rnew + (rnew ? 4 * P : 0));
   l.staging = align256(l.seg + nseg * (long long)sizeof(Seg));
   l.need = l.staging + STAGE_MIN;
   l.stage_events = (SIM_STATIC_SCRATCH_BYTES - l.staging) / (long long)sizeof(Ev);
@@ -89,16 +134,26 @@ int fail(cudaError_t e) {
              : SIM_ERR_CUDA;
 }
 
-// Once per device, with that device current: look up the array's address.
-int scratch_base(int dev, unsigned char** out) {
+// With device `dev` current: the array's address in the current context and
+// the kernels' shared-memory permission, set up once per device and context
+// (again after a cudaDeviceReset).  Every return code is checked.
+int device_setup(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> g(g_setup_mu);
-  if (!g_base[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
-    if (e != cudaSuccess) return fail(e);
-    g_base[dev] = (unsigned char*)ptr;
+  unsigned long long id = current_context_id();
+  if (id != 0 && g_dev[dev].ctx_id == id) {
+    *out = g_dev[dev].base;
+    return SIM_OK;
   }
-  *out = g_base[dev];
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);  // creates the context if needed
+  if (e != cudaSuccess) return fail(e);
+  // shared-memory permission of the tile kernels, at the largest substep cap
+  // (never below what any handle needs)
+  e = evsim::configure_kernels(SIM_MAX_SUBSTEPS);
+  if (e != cudaSuccess) return fail(e);
+  if (id == 0) id = current_context_id();
+  g_dev[dev] = DeviceSetup{id, (unsigned char*)ptr};  // id 0: set up again next call
+  *out = (unsigned char*)ptr;
   return SIM_OK;
 }
 
@@ -149,7 +204,13 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   const long long P = (long long)c.width * c.height;
   const long long segs_per_k = (long long)c.height * tiles_x;
   const long long nseg = (long long)n_max * segs_per_k;
-  const Layout L = layout(P, nseg, (long long)tiles_x * tiles_y);
+  // The reference is replaced only when the step succeeds: with ref_in given
+  // and distinct from ref_out the kernels read ref_in and write ref_out
+  // directly; in place (ref_in == ref_out) or with a fresh reference
+  // (ref_in = NULL), the new reference goes to the array first and is copied
+  // to ref_out after the step has been checked.
+  const bool staged_ref = accum && (!ref_in || ref_in == ref_out);
+  const Layout L = layout(P, nseg, (long long)tiles_x * tiles_y, staged_ref);
   if (L.need > SIM_STATIC_SCRATCH_BYTES) return SIM_ERR_TOO_LARGE;
 
   int dev = 0;
@@ -157,12 +218,8 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   if (e != cudaSuccess) return fail(e);
   if (dev < 0 || dev >= MAX_DEVICES) return SIM_ERR_NO_DEVICE;
   unsigned char* base = nullptr;
-  const int rc = scratch_base(dev, &base);
+  const int rc = device_setup(dev, &base);
   if (rc) return rc;
-  // shared-memory permission of the tile kernels, at the largest substep cap
-  // (never below what any handle needs)
-  e = evsim::configure_kernels(SIM_MAX_SUBSTEPS);
-  if (e != cudaSuccess) return fail(e);
   const int sms = evsim::device_sm_count();
   cudaStream_t st = c.cuda_stream ? (cudaStream_t)c.cuda_stream : cudaStreamLegacy;
 
@@ -213,16 +270,17 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   FrameDesc f0{};
   f0.frame = (const unsigned char*)prev_frame;
   f0.pitch = prev_pitch;
+  int32_t* rstage = (int32_t*)(base + L.rnew);
   if (accum && !ref_in) {
-    pi.R0 = ref_out;
+    pi.R0 = rstage;
   } else {
     pi.ref_mode = SIM_REF_RESET;  // ring only
   }
   e = evsim::launch_init(pi, f0, st);
   if (e != cudaSuccess) return fail(e);
   if (accum) {
-    p.R0 = ref_in ? const_cast<int32_t*>(ref_in) : ref_out;  // read (sel = 0)
-    p.R1 = ref_out;                                          // written
+    p.R0 = ref_in ? const_cast<int32_t*>(ref_in) : rstage;  // read (sel = 0)
+    p.R1 = staged_ref ? rstage : ref_out;                   // written
   }
 
   evsim::BatchArg b{};
@@ -247,6 +305,11 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(e);
   if (out.err) return out.err;
+  if (staged_ref) {
+    e = cudaMemcpyAsync(ref_out, rstage, (size_t)(4 * P), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(e);
+  }
   *n_events = out.cursor;
   return SIM_OK;
 }

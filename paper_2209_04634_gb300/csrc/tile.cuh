@@ -1786,15 +1786,35 @@ __global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile(SimParams p, BatchA
   if (p.tile_cost && threadIdx.x == 0) p.tile_cost[tile] = (unsigned)((clock64() - c0) >> 8);
 }
 
+// Dynamic shared-memory permission of one k_tile instance in both shapes;
+// returns the first failing call's error.
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, bool XT = false>
-void set_tile_attr(int n_max) {
-  cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 16, XT>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)batch_smem_bytes(n_max, 3, SPARSE, 16));
-  if (!XT)  // per-crossing times run in 64 x 16 tiles only
-    cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 8>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)batch_smem_bytes(n_max, 3, SPARSE, 8));
+cudaError_t set_tile_attr(int n_max) {
+  cudaError_t e = cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 16, XT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_smem_bytes(n_max, 3, SPARSE, 16));
+  if (e == cudaSuccess && !XT)  // per-crossing times run in 64 x 16 tiles only
+    e = cudaFuncSetAttribute(k_tile<RESET, MAPS, WIDE, SPARSE, 8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem_bytes(n_max, 3, SPARSE, 8));
+  return e;
+}
+
+// The eight (reset, maps, wide) instances of one mode.
+template <bool SPARSE, bool XT = false>
+cudaError_t set_mode_attrs(int n_max) {
+  const cudaError_t es[8] = {
+      set_tile_attr<false, false, false, SPARSE, XT>(n_max),
+      set_tile_attr<false, true, false, SPARSE, XT>(n_max),
+      set_tile_attr<false, false, true, SPARSE, XT>(n_max),
+      set_tile_attr<false, true, true, SPARSE, XT>(n_max),
+      set_tile_attr<true, false, false, SPARSE, XT>(n_max),
+      set_tile_attr<true, true, false, SPARSE, XT>(n_max),
+      set_tile_attr<true, false, true, SPARSE, XT>(n_max),
+      set_tile_attr<true, true, true, SPARSE, XT>(n_max)};
+  for (cudaError_t e : es)
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 template <bool SPARSE, int TH_, bool XT = false>

@@ -11,15 +11,7 @@ cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st)
 }
 
 cudaError_t configure_dense_kernels(int n_max) {
-  set_tile_attr<false, false, false, false>(n_max);
-  set_tile_attr<false, true, false, false>(n_max);
-  set_tile_attr<false, false, true, false>(n_max);
-  set_tile_attr<false, true, true, false>(n_max);
-  set_tile_attr<true, false, false, false>(n_max);
-  set_tile_attr<true, true, false, false>(n_max);
-  set_tile_attr<true, false, true, false>(n_max);
-  set_tile_attr<true, true, true, false>(n_max);
-  return cudaGetLastError();
+  return set_mode_attrs<false>(n_max);
 }
 
 }  // namespace evsim

@@ -11,15 +11,7 @@ cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st
 }
 
 cudaError_t configure_sparse_kernels(int n_max) {
-  set_tile_attr<false, false, false, true>(n_max);
-  set_tile_attr<false, true, false, true>(n_max);
-  set_tile_attr<false, false, true, true>(n_max);
-  set_tile_attr<false, true, true, true>(n_max);
-  set_tile_attr<true, false, false, true>(n_max);
-  set_tile_attr<true, true, false, true>(n_max);
-  set_tile_attr<true, false, true, true>(n_max);
-  set_tile_attr<true, true, true, true>(n_max);
-  return cudaGetLastError();
+  return set_mode_attrs<true>(n_max);
 }
 
 }  // namespace evsim

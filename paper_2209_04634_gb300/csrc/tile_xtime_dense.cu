@@ -12,15 +12,7 @@ cudaError_t launch_xtime_dense(const SimParams& p, const BatchArg& b, cudaStream
 }
 
 cudaError_t configure_xtime_dense_kernels(int n_max) {
-  set_tile_attr<false, false, false, false, true>(n_max);
-  set_tile_attr<false, true, false, false, true>(n_max);
-  set_tile_attr<false, false, true, false, true>(n_max);
-  set_tile_attr<false, true, true, false, true>(n_max);
-  set_tile_attr<true, false, false, false, true>(n_max);
-  set_tile_attr<true, true, false, false, true>(n_max);
-  set_tile_attr<true, false, true, false, true>(n_max);
-  set_tile_attr<true, true, true, false, true>(n_max);
-  return cudaGetLastError();
+  return set_mode_attrs<false, true>(n_max);
 }
 
 }  // namespace evsim

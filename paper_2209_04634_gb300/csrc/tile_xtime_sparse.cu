@@ -12,15 +12,7 @@ cudaError_t launch_xtime_sparse(const SimParams& p, const BatchArg& b, cudaStrea
 }
 
 cudaError_t configure_xtime_sparse_kernels(int n_max) {
-  set_tile_attr<false, false, false, true, true>(n_max);
-  set_tile_attr<false, true, false, true, true>(n_max);
-  set_tile_attr<false, false, true, true, true>(n_max);
-  set_tile_attr<false, true, true, true, true>(n_max);
-  set_tile_attr<true, false, false, true, true>(n_max);
-  set_tile_attr<true, true, false, true, true>(n_max);
-  set_tile_attr<true, false, true, true, true>(n_max);
-  set_tile_attr<true, true, true, true, true>(n_max);
-  return cudaGetLastError();
+  return set_mode_attrs<true, true>(n_max);
 }
 
 }  // namespace evsim

@@ -101,6 +101,7 @@ class simb_stats(ctypes.Structure):
 # (name, restype, argtypes) of every function that include/evsim.h declares
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 SIGNATURES = [
+    ("sim_threshold_q16", _I32, [ctypes.c_double]),
     ("sim_config_default", ctypes.c_int, [ctypes.POINTER(sim_config), _I32, _I32]),
     ("sim_create", ctypes.c_int, [ctypes.POINTER(sim_config), ctypes.POINTER(_VP)]),
     ("sim_push_frame", ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I32]),
@@ -198,8 +199,8 @@ def check(code: int, what: str) -> int:
 
 
 def q16(c: float) -> int:
-    """Threshold in log (or 8-bit) units -> Q16 integer."""
-    return int(round(abs(float(c)) * 65536.0))
+    """Threshold in log (or 8-bit) units -> Q16 integer (sim_threshold_q16)."""
+    return check(int(load().sim_threshold_q16(float(c))), "sim_threshold_q16")
 
 
 def _ptr(a) -> int:

@@ -17,16 +17,16 @@ def oracle_run(seq: synth.Sequence, mode: int = evsim.SIM_DENSE, *, intensity=ev
         return oracle.run_diff(seq.frames, seq.flows, seq.t_us,
                                substeps=seq.substeps if substeps is None else substeps,
                                max_substeps=seq.max_substeps, intensity=intensity,
-                               c_pos_q16=evsim.q16(seq.c_pos) if c_pos_q16 is None else c_pos_q16,
-                               c_neg_q16=evsim.q16(seq.c_neg) if c_neg_q16 is None else c_neg_q16,
+                               c_pos_q16=oracle.q16(seq.c_pos) if c_pos_q16 is None else c_pos_q16,
+                               c_neg_q16=oracle.q16(seq.c_neg) if c_neg_q16 is None else c_neg_q16,
                                cpos_map=seq.cpos_map if use_maps else None,
                                cneg_map=seq.cneg_map if use_maps else None)
     return oracle.run(seq.frames, seq.flows, seq.t_us,
                       mode=oracle.SPARSE if mode == evsim.SIM_SPARSE else oracle.DENSE,
                       substeps=seq.substeps if substeps is None else substeps,
                       max_substeps=seq.max_substeps, intensity=intensity, ref_mode=ref_mode,
-                      c_pos_q16=evsim.q16(seq.c_pos) if c_pos_q16 is None else c_pos_q16,
-                      c_neg_q16=evsim.q16(seq.c_neg) if c_neg_q16 is None else c_neg_q16,
+                      c_pos_q16=oracle.q16(seq.c_pos) if c_pos_q16 is None else c_pos_q16,
+                      c_neg_q16=oracle.q16(seq.c_neg) if c_neg_q16 is None else c_neg_q16,
                       c_act_q16=c_act_q16,
                       cpos_map=seq.cpos_map if use_maps else None,
                       cneg_map=seq.cneg_map if use_maps else None,

@@ -196,3 +196,18 @@ def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.strip().count(".") == 2
+
+
+def test_threshold_conversion_matches_the_oracles(lib):
+    # the library's float -> Q16 threshold conversion and the oracle's own
+    # (computed independently) agree, ties included
+    import oracle
+    vals = [0.0, 0.15, 0.2, 0.03, 2.0, 10.0, 20.0, -0.2, -2.0, 1.0 / 65536, 1e-7]
+    vals += [(k + 0.5) / 65536 for k in range(0, 40)]  # exact ties: round half even
+    vals += [(k + 0.5) / 65536 for k in range(13100, 13120)]
+    for c in vals:
+        assert evsim.q16(c) == oracle.q16(c), c
+    assert lib.sim_threshold_q16(float("nan")) == evsim.SIM_ERR_ARG
+    assert lib.sim_threshold_q16(float("inf")) == evsim.SIM_ERR_ARG
+    assert lib.sim_threshold_q16(16384.0) == evsim.SIM_ERR_ARG  # 2^30 in Q16
+    assert lib.sim_threshold_q16(16383.99) > 0

@@ -101,7 +101,7 @@ def test_moving_rectangles_full_length_invariants(mode):
     w = seq.frames.astype(np.int64)
     luma0 = (77 * w[0, ..., 0] + 150 * w[0, ..., 1] + 29 * w[0, ..., 2] + 128) >> 8
     lumaL = (77 * w[-1, ..., 0] + 150 * w[-1, ..., 1] + 29 * w[-1, ..., 2] + 128) >> 8
-    C = evsim.q16(seq.c_pos)
+    C = oracle.q16(seq.c_pos)
     pos = np.zeros(luma0.shape, np.int64)
     neg = np.zeros(luma0.shape, np.int64)
     np.add.at(pos, (y[p > 0], x[p > 0]), 1)
