@@ -55,6 +55,8 @@ class OrcConfig(ctypes.Structure):
         ("c_neg_q16", ctypes.c_int32),
         ("c_act_q16", ctypes.c_int32),
         ("event_time", ctypes.c_int32),
+        ("row_begin", ctypes.c_int32),
+        ("row_end", ctypes.c_int32),
     ]
 
 
@@ -160,12 +162,14 @@ def run(frames: np.ndarray, flows: np.ndarray | None, t_us, *, mode: int = DENSE
         ref_mode: int = ACCUM, c_pos_q16: int = 13107, c_neg_q16: int = 13107,
         c_act_q16: int = -1, cpos_map: np.ndarray | None = None,
         cneg_map: np.ndarray | None = None, cap: int | None = None,
-        event_time: int = T_SUBSTEP) -> dict:
+        event_time: int = T_SUBSTEP, rows: tuple[int, int] | None = None) -> dict:
     """Run the oracle over a whole sequence.
 
     frames: (F, H, W) uint8 luma or (F, H, W, 3) uint8 RGB.
     flows : (F, H, W, 2) float32, index i holds the flow of frame i-1 -> i
             (entry 0 unused); may be None when F == 1.
+    rows  : (begin, end): simulate only these rows (a band of run_bands);
+            the other rows' R entries are not meaningful.
     Returns a dict with 'events' (structured array, EVENT_DTYPE), 'R' (H, W)
     int32, 'n_per_frame', 'ev_per_frame', 'active_per_frame', 'clamped'.
     """
@@ -179,7 +183,8 @@ def run(frames: np.ndarray, flows: np.ndarray | None, t_us, *, mode: int = DENSE
         flows = np.ascontiguousarray(flows, dtype=np.float32)
         assert flows.shape == (F, H, W, 2), flows.shape
     cfg = OrcConfig(W, H, ch, mode, substeps, max_substeps, intensity, ref_mode,
-                    c_pos_q16, c_neg_q16, c_act_q16, event_time)
+                    c_pos_q16, c_neg_q16, c_act_q16, event_time,
+                    rows[0] if rows else 0, rows[1] if rows else 0)
     maps = []
     for m in (cpos_map, cneg_map):
         if m is None:
@@ -214,6 +219,40 @@ def run(frames: np.ndarray, flows: np.ndarray | None, t_us, *, mode: int = DENSE
         raise ValueError(f"oracle rejected the input (code {n})")
     return {"events": ev[:n].copy(), "R": R, "n_per_frame": npf, "ev_per_frame": epf,
             "active_per_frame": apf, "clamped": int(clamped.value)}
+
+
+def run_bands(frames: np.ndarray, flows: np.ndarray | None, t_us, *, threads: int,
+              substeps: int = 8, max_substeps: int = 64, **kw) -> dict:
+    """``run`` split into `threads` row bands run concurrently (the C call
+    releases the interpreter lock), merged into the single run's output: the
+    events of every (frame, substep) in band order, the reference by rows,
+    the per-frame counts summed.  The merge orders events by time, so it
+    needs substep times that strictly increase, i.e. every frame interval at
+    least N_max microseconds (checked); per-crossing times are refused."""
+    import concurrent.futures as cf
+    if kw.get("event_time", T_SUBSTEP) != T_SUBSTEP:
+        raise ValueError("run_bands merges substep times only")
+    t = np.asarray(t_us, dtype=np.int64)
+    nmax = substeps if substeps > 0 else max_substeps
+    if len(t) > 1 and int(np.diff(t).min()) < nmax:
+        raise ValueError("run_bands needs frame intervals of at least N_max microseconds")
+    H = frames.shape[1]
+    threads = max(1, min(int(threads), H))
+    edges = [H * j // threads for j in range(threads + 1)]
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda j: run(frames, flows, t_us, substeps=substeps,
+                                          max_substeps=max_substeps,
+                                          rows=(edges[j], edges[j + 1]), **kw),
+                            range(threads)))
+    ev = np.concatenate([p["events"] for p in parts])
+    ev = ev[np.argsort(ev["t"], kind="stable")]
+    R = parts[0]["R"].copy()
+    for j, p in enumerate(parts):
+        R[edges[j]:edges[j + 1]] = p["R"][edges[j]:edges[j + 1]]
+    return {"events": ev, "R": R, "n_per_frame": parts[0]["n_per_frame"],
+            "ev_per_frame": sum(p["ev_per_frame"] for p in parts),
+            "active_per_frame": sum(p["active_per_frame"] for p in parts),
+            "clamped": sum(p["clamped"] for p in parts), "threads": threads}
 
 
 def run_diff(frames: np.ndarray, flows: np.ndarray | None, t_us, *, substeps: int = 8,

@@ -153,6 +153,14 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
   const int32_t W = c->width, H = c->height;
   const int64_t P = (int64_t)W * H;
   const int64_t fbytes = P * c->channels;
+  /* the simulated rows [y0, y1) (a row band of a parallel run, or all rows) */
+  const int32_t y0 = c->row_begin < 0 ? 0 : (c->row_begin > H ? H : c->row_begin);
+  const int32_t y1 = c->row_end <= 0 || c->row_end > H ? H : c->row_end;
+  const int64_t p_begin = (int64_t)y0 * W, p_end = (int64_t)(y1 > y0 ? y1 : y0) * W;
+  /* the adaptive N is a maximum over the whole frame: then the flow and the
+   * activity of every pixel are needed, else only those of the band */
+  const int64_t q_begin = c->substeps == 0 ? 0 : p_begin;
+  const int64_t q_end = c->substeps == 0 ? P : p_end;
 
   int32_t lut[256];
   orc_lut(c->intensity, lut);
@@ -191,17 +199,17 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
 
     /* Flow of frame i (i-1 -> i), read at the target pixel. */
     const float* fl = flows + (int64_t)i * P * 2;
-    for (int64_t p = 0; p < P; ++p) {
+    for (int64_t p = q_begin; p < q_end; ++p) {
       int32_t cl = 0;
       Fx[p] = orc_flow_q16(fl[2 * p], &cl);
       Fy[p] = orc_flow_q16(fl[2 * p + 1], &cl);
-      clamped += cl;
+      if (p >= p_begin && p < p_end) clamped += cl;
     }
 
     /* Sec. III-B: pixels whose change from frame i-1 to frame i stays under
      * the activity threshold are disregarded (dense: every pixel counts). */
     int64_t n_active = 0;
-    for (int64_t p = 0; p < P; ++p) {
+    for (int64_t p = q_begin; p < q_end; ++p) {
       int32_t a = 1;
       if (c->mode == ORC_SPARSE) {
         int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);
@@ -212,7 +220,7 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
         a = d >= cact;
       }
       act[p] = (uint8_t)a;
-      n_active += a;
+      if (p >= p_begin && p < p_end) n_active += a;
     }
 
     int32_t N = c->substeps;
@@ -237,7 +245,7 @@ int64_t orc_run(const orc_config* c, int32_t n_frames, const uint8_t* frames,
       int64_t w = ((int64_t)k * 8192 + N) / (2 * (int64_t)N);
       uint32_t tk = (uint32_t)(t_prev + floordiv((int64_t)k * dt, N));
       int64_t tk1 = t_prev + floordiv((int64_t)(k - 1) * dt, N);  /* t_{k-1} */
-      for (int32_t y = 0; y < H; ++y) {
+      for (int32_t y = y0; y < y1; ++y) {
         for (int32_t x = 0; x < W; ++x) {
           int64_t p = (int64_t)y * W + x;
           if (!act[p]) continue;

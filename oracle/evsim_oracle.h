@@ -53,6 +53,12 @@ typedef struct {
   int32_t event_time;    /* ORC_T_SUBSTEP: every crossing of substep k at t_k;
                             ORC_T_CROSSING: each crossing at its own time between
                             t_{k-1} and t_k (see orc_crossing_time) */
+  int32_t row_begin;     /* orc_run simulates rows [row_begin, row_end) only (the other */
+  int32_t row_end;       /* rows' events are not produced, their R is not meaningful);
+                            row_end <= 0: through the last row.  Frames, flows and the
+                            adaptive N are still read / computed over the whole image,
+                            so the events of consecutive row bands, merged per
+                            (frame, substep) in band order, are those of one run. */
 } orc_config;
 
 typedef struct {

@@ -42,8 +42,8 @@ MUTATIONS = {
     "adaptive_off_by_one": ("(int64_t)n * n * 4294967296LL < max_f2",
                             "(int64_t)n * n * 4294967296LL <= max_f2"),
     "y_fraction_from_x": ("fy = (py & 0xFFFF) >> 4", "fy = (px & 0xFFFF) >> 4"),
-    "column_major_order": ("for (int32_t y = 0; y < H; ++y) {\n        for (int32_t x = 0; x < W; ++x) {",
-                           "for (int32_t x = 0; x < W; ++x) {\n        for (int32_t y = 0; y < H; ++y) {"),
+    "column_major_order": ("for (int32_t y = y0; y < y1; ++y) {\n        for (int32_t x = 0; x < W; ++x) {",
+                           "for (int32_t x = 0; x < W; ++x) {\n        for (int32_t y = y0; y < y1; ++y) {"),
     "polarity_bit_inverted": ("(y << 1) | (pos ? 1 : 0)", "(y << 1) | (pos ? 0 : 1)"),
     "flow_floored": ("(int32_t)nearbyint(d * 65536.0)", "(int32_t)floor(d * 65536.0)"),
     "reset_starts_from_new_frame": ("if (c->ref_mode == ORC_RESET) memcpy(R, Lprev,",
