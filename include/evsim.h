@@ -164,6 +164,8 @@ typedef struct {
   int32_t tile_height;       /* tile height of the batch kernel (8 or 16) */
   int32_t block_order;       /* its tile order: 0 linear, 1 serpentine, 2 balanced
                                 (see sim_autotune) */
+  int64_t active_pixels;     /* sum over committed frames of the pixels simulated (dense:
+                                width * height per frame; sparse: the active pixels) */
 } sim_stats;
 
 /* Kernel kinds for sim_kernel_time. */

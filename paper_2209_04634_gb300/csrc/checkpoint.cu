@@ -19,7 +19,7 @@ struct CkHeader {
   int32_t W, H, ch, mode, intensity, ref_mode, substeps, max_substeps;
   int32_t c_pos, c_neg, c_act, maps;
   int32_t have_first, last_n;
-  int64_t t0, committed, t_prev, pushed, work_px, work_active, batch_events;
+  int64_t t0, committed, t_prev, pushed, work_px, work_active, batch_events, work_pixels;
   uint64_t clamped;
   int64_t ring_bytes, ring2_bytes, ref_bytes;
 };
@@ -64,7 +64,7 @@ int sim_get_state(sim_t* s, void* buf, int64_t bytes) {
   CkHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, kMagic, sizeof(kMagic));
-  h.version = 1;
+  h.version = 2;  // 2: the header carries the simulated-pixel count
   h.W = s->W;
   h.H = s->H;
   h.ch = s->ch;
@@ -85,6 +85,7 @@ int sim_get_state(sim_t* s, void* buf, int64_t bytes) {
   h.pushed = s->pushed;
   h.work_px = c.work_px;
   h.work_active = c.work_active;
+  h.work_pixels = c.work_pixels;
   h.batch_events = c.batch_events;
   h.clamped = c.clamped;
   h.ring_bytes = s->P;
@@ -114,7 +115,7 @@ int sim_set_state(sim_t* s, const void* buf, int64_t bytes) {
   if (!s || !buf || bytes != total_bytes(s)) return SIM_ERR_ARG;
   CkHeader h;
   std::memcpy(&h, buf, sizeof(h));
-  if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != 1) return SIM_ERR_ARG;
+  if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != 2) return SIM_ERR_ARG;
   if (!same_config(h, s) || h.ring_bytes != s->P || h.ring2_bytes != ring2_bytes(s) ||
       h.ref_bytes != ref_bytes(s) || h.committed < 0 || h.t_prev < 0)
     return SIM_ERR_ARG;
@@ -128,6 +129,7 @@ int sim_set_state(sim_t* s, const void* buf, int64_t bytes) {
   c.committed = h.committed;
   c.work_px = h.work_px;
   c.work_active = h.work_active;
+  c.work_pixels = h.work_pixels;
   c.batch_events = h.batch_events;
   c.clamped = h.clamped;
   const unsigned char* in = (const unsigned char*)buf + sizeof(h);

@@ -63,6 +63,7 @@ struct Ctl {
   unsigned int order_exit;       // order kernel: blocks that left the ticket loop
   unsigned int pad0;
   long long drained;             // group delivery: events of the buffer already delivered
+  long long work_pixels;         // committed: sum over frames of the pixels simulated
 };
 
 // Per-frame arguments of a batch (device-resident table).
@@ -228,6 +229,11 @@ cudaError_t launch_plan(const SimParams& p, cudaStream_t st);
 constexpr int PLAN_MAX_TILES = 4096;  // tiles a balanced plan covers
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);
+// Raise the tile kernels' shared-memory limits on the current device to what
+// n_max substeps need, never lowering them (the limits are shared by every
+// handle and entry point); again = true sets them even if recorded as done
+// (a new CUDA context on the device).
+cudaError_t raise_kernel_limits(int n_max, bool again);
 // Per-mode tile kernels (tile_dense.cu, tile_sparse.cu): dynamic shared-memory
 // limits of their k_tile instances for batches of up to n_max substeps.
 cudaError_t configure_dense_kernels(int n_max);

@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "../../include/evsim.h"
 #include "internal.h"
@@ -600,6 +601,7 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
           ctl->work_px += P * nsum;
           ctl->work_active += p.mode == SIM_SPARSE ? ctl->active_n : P * nsum;
           ctl->last_active = p.mode == SIM_SPARSE ? ctl->active : P * b.count;
+          ctl->work_pixels += ctl->last_active;
         }
       }
       ctl->active = 0;
@@ -925,6 +927,27 @@ cudaError_t configure_kernels(int n_max) {
   if (e == cudaSuccess) e = configure_sparse_kernels(n_max);
   if (e == cudaSuccess) e = configure_xtime_dense_kernels(n_max);
   if (e == cudaSuccess) e = configure_xtime_sparse_kernels(n_max);
+  return e;
+}
+
+namespace {
+constexpr int LIMIT_DEVICES = 256;
+std::mutex g_limit_mu;
+int g_limit_nmax[LIMIT_DEVICES] = {};  // substep cap the current device's kernels allow
+}  // namespace
+
+// The limits are process-wide per kernel, so they only ever grow: a handle
+// with a small substep cap must not shrink what another caller set up.
+cudaError_t raise_kernel_limits(int n_max, bool again) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= LIMIT_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_limit_mu);
+  if (!again && n_max <= g_limit_nmax[dev]) return cudaSuccess;
+  const int want = std::max(n_max, again ? 0 : g_limit_nmax[dev]);
+  e = configure_kernels(want);
+  if (e == cudaSuccess) g_limit_nmax[dev] = want;
   return e;
 }
 

@@ -16,8 +16,6 @@
 
 namespace evsim_rt {
 
-std::mutex g_attr_mu;
-int g_attr_nmax = 0;
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 
 // Sizes of a handle's device buffers.
@@ -489,11 +487,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
     chk(cudaMemset(s->d_tdone, 0, (size_t)s->tiles_x * s->tiles_y * sizeof(unsigned long long)));
   }
   if (e == cudaSuccess) {
-    std::lock_guard<std::mutex> g(g_attr_mu);
-    if (s->n_max > g_attr_nmax) {
-      chk(evsim::configure_kernels(s->n_max));
-      if (e == cudaSuccess) g_attr_nmax = s->n_max;
-    }
+    chk(evsim::raise_kernel_limits(s->n_max, false));
   }
   if (e != cudaSuccess) {
     const int rc = cuda_rc(e);
@@ -650,6 +644,7 @@ int sim_get_stats(sim_t* s, sim_stats* st) {
   st->max_batch = s->bmax;
   st->pixel_substeps = c.work_px;
   st->active_substeps = c.work_active;
+  st->active_pixels = c.work_pixels;
   st->tile_height = s->tile_h;
   st->block_order = s->block_order;
   return SIM_OK;

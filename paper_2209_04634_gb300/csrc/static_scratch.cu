@@ -149,7 +149,7 @@ int device_setup(int dev, unsigned char** out) {
   if (e != cudaSuccess) return fail(e);
   // shared-memory permission of the tile kernels, at the largest substep cap
   // (never below what any handle needs)
-  e = evsim::configure_kernels(SIM_MAX_SUBSTEPS);
+  e = evsim::raise_kernel_limits(SIM_MAX_SUBSTEPS, true);
   if (e != cudaSuccess) return fail(e);
   if (id == 0) id = current_context_id();
   g_dev[dev] = DeviceSetup{id, (unsigned char*)ptr};  // id 0: set up again next call

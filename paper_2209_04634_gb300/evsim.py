@@ -63,6 +63,7 @@ class sim_stats(ctypes.Structure):
         ("max_batch", ctypes.c_int32), ("pixel_substeps", ctypes.c_int64),
         ("active_substeps", ctypes.c_int64),
         ("tile_height", ctypes.c_int32), ("block_order", ctypes.c_int32),
+        ("active_pixels", ctypes.c_int64),
     ]
 
 
