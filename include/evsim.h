@@ -144,7 +144,13 @@ enum { SIM_TIME_SUBSTEP = 0, SIM_TIME_CROSSING = 1 };
 /* Tile shape choices of sim_config.tile_height. */
 enum {
   SIM_TILE_AUTO = 0,    /* the shape the autotuner table holds for this configuration, else 16 */
-  SIM_TILE_TUNE = -1    /* as SIM_TILE_AUTO, but run sim_autotune first on a table miss */
+  SIM_TILE_TUNE = -1,   /* as SIM_TILE_AUTO, but run sim_autotune first on a table miss */
+  SIM_TILE_ROWS = 1     /* the row kernel: warps take 64 x 1 row units by ticket and carry
+                           each through the batch; frames are sampled in global memory,
+                           unit-frames with nothing to simulate (sparse: no active pixel;
+                           both modes: every pixel quiet, i.e. zero flow and both end values
+                           strictly inside the threshold band) cost one flag byte.  Dense and
+                           sparse substep-time streams (SIM_DIFF and SIM_TIME_CROSSING use 16) */
 };
 
 typedef struct {

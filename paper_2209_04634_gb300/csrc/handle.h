@@ -24,7 +24,7 @@ struct sim_s {
   long long P = 0;
   int n_max = 0;
   int tiles_x = 0, tiles_y = 0;
-  int tile_h = 16;             // batch kernel tile height (8 or 16)
+  int tile_h = 16;             // batch kernel tile height (8 or 16; 1: the row kernel)
   int block_order = 0;         // batch kernel tile order: 0 linear, 1 serpentine, 2 balanced
   unsigned int* d_tile_cost = nullptr;  // balanced order: cycles per tile of the last batch
   int* d_tile_order = nullptr;          // balanced order: tile of each block
@@ -44,6 +44,7 @@ struct sim_s {
   Ev* d_staging = nullptr;
   Ev* d_events = nullptr;
   evsim::Seg* d_seg = nullptr;
+  unsigned char* d_segflag = nullptr;       // row kernel: per (frame, row unit) written flags
   unsigned long long* d_tdone = nullptr;    // per tile progress words
   unsigned long long* d_order_status = nullptr;
   evsim::FrameDesc* d_desc = nullptr;       // bmax descriptors of the batch in flight

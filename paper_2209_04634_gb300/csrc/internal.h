@@ -61,7 +61,7 @@ struct Ctl {
   unsigned int order_ticket;     // order kernel: chunk tickets
   unsigned int order_done;       // order kernel: chunks finished
   unsigned int order_exit;       // order kernel: blocks that left the ticket loop
-  unsigned int pad0;
+  unsigned int unit_ticket;      // row kernel: next unit (reset when the batch finishes)
   long long drained;             // group delivery: events of the buffer already delivered
   long long work_pixels;         // committed: sum over frames of the pixels simulated
 };
@@ -137,6 +137,9 @@ struct SimParams {
   unsigned long long* order_status;
   Ev* events;
   long long event_cap;
+  unsigned char* segflag;       // row kernel: per (frame, row, 64-column unit) 1 when the
+                                // unit-frame's segments are written, 0 when it emitted
+                                // nothing and wrote none; null: every segment is written
 };
 
 // ---- multi-stream step (one launch per kernel for every member of a group)
@@ -221,6 +224,9 @@ cudaError_t launch_dense(const SimParams& p, const BatchArg& b, cudaStream_t st)
 cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_sparse(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_diff(const SimParams& p, const BatchArg& b, cudaStream_t st);
+// Row kernel (rows.cu): dense or sparse batch in 64-pixel row units taken by
+// ticket (p.tile_h == 1; needs p.segflag).
+cudaError_t launch_rows(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_accumulate(const Ev* ev, long long n, int W, int H, long long t_begin,
                               long long t_end, int* frame, cudaStream_t st);
 // Balanced block order: rank the tiles by their last batch's cost and lay

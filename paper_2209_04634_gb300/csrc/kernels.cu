@@ -481,11 +481,15 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
       }
       const int k = (int)(q - o.FN[fi]);
       const int N = o.N[fi];
-      const Seg sg = p.seg[((long long)fi * p.n_max + k) * S + rs];
-      cnt = sg.cnt;
-      src = sg.src;
-      mask = sg.mask;
-      pol = sg.pol;
+      // a unit-frame of the row kernel that emitted nothing wrote a flag
+      // instead of its segments
+      if (!p.segflag || p.segflag[(long long)fi * S + rs]) {
+        const Seg sg = p.seg[((long long)fi * p.n_max + k) * S + rs];
+        cnt = sg.cnt;
+        src = sg.src;
+        mask = sg.mask;
+        pol = sg.pol;
+      }
       const int y = rs / p.tiles_x, tc = rs - y * p.tiles_x;
       xy = (unsigned)(tc * TW) | ((unsigned)y << 16);
       const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
@@ -607,6 +611,7 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
       ctl->active = 0;
       ctl->active_n = 0;
       ctl->stage_top = 0;
+      ctl->unit_ticket = 0;
       ctl->order_done = 0;
       ctl->batch_fail = 0;
     }

@@ -56,6 +56,7 @@ long long state_bytes(const sim_config& c) {
   if (c.mode == SIM_DIFF) b += 2 * z.P;  // the second frame ring
   b += (z.stage + z.cap) * (long long)sizeof(Ev);       // staging + events
   b += z.seg_cap * (long long)sizeof(evsim::Seg) + 8 * z.ochunks;
+  b += (long long)z.bmax * z.segs_per_k;                 // row kernel: segment flags
   b += 8LL * z.tiles_x * ((c.height + 7) / 8);                     // tile progress words
   b += (long long)z.bmax * sizeof(evsim::FrameDesc);
   b += z.P * c.pixel_format;                             // host-frame staging (one frame)
@@ -89,6 +90,7 @@ void free_all(sim_t* s) {
   cudaFree(s->d_staging);
   cudaFree(s->d_events);
   cudaFree(s->d_seg);
+  cudaFree(s->d_segflag);
   cudaFree(s->d_tdone);
   cudaFree(s->d_order_status);
   cudaFree(s->d_desc);
@@ -114,6 +116,7 @@ evsim::SimParams make_params(const sim_t* s) {
   p.block_order = s->block_order;
   p.tile_cost = s->block_order == 2 ? s->d_tile_cost : nullptr;
   p.tile_order = s->d_tile_order;
+  p.segflag = s->tile_h == 1 ? s->d_segflag : nullptr;
   p.xtime = s->cfg.event_time == SIM_TIME_CROSSING;
   p.mode = s->cfg.mode;
   p.ref_mode = s->cfg.ref_mode;
@@ -265,17 +268,22 @@ cudaError_t enqueue_batch(sim_t* s, int n) {
     }
     if (s->cfg.mode == SIM_DIFF)
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_diff(p, b, s->stream); });
+    else if (p.segflag)
+      e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_rows(p, b, s->stream); });
     else
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, b, s->stream); });
-    if (e == cudaSuccess && s->block_order == 2 && s->cfg.mode != SIM_DIFF)
+    if (e == cudaSuccess && s->block_order == 2 && s->cfg.mode != SIM_DIFF && !p.segflag)
       e = evsim::launch_plan(p, s->stream);
   } else {
     if (adaptive) {
       e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, b, s->stream); });
       if (e != cudaSuccess) return e;
     }
-    e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, b, s->stream); });
-    if (e == cudaSuccess && s->block_order == 2) e = evsim::launch_plan(p, s->stream);
+    if (p.segflag)
+      e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_rows(p, b, s->stream); });
+    else
+      e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, b, s->stream); });
+    if (e == cudaSuccess && s->block_order == 2 && !p.segflag) e = evsim::launch_plan(p, s->stream);
   }
   if (e != cudaSuccess) return e;
   return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, b, s->stream, s->order_grid); });
@@ -349,7 +357,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   if (c.event_capacity < 0 || c.event_capacity > evsim::MAX_EVENTS) return SIM_ERR_ARG;
   if (c.max_batch < 0 || c.max_batch > SIM_MAX_BATCH) return SIM_ERR_ARG;
   if (c.tile_height != SIM_TILE_AUTO && c.tile_height != SIM_TILE_TUNE && c.tile_height != 8 &&
-      c.tile_height != 16)
+      c.tile_height != 16 && c.tile_height != SIM_TILE_ROWS)
     return SIM_ERR_ARG;
   if (c.event_time != SIM_TIME_SUBSTEP && c.event_time != SIM_TIME_CROSSING) return SIM_ERR_ARG;
   const bool xtime = c.event_time == SIM_TIME_CROSSING;
@@ -378,9 +386,9 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   // tile shape: fixed, or the autotuner's choice for this configuration
   int th = c.tile_height, order = 0, tth = 16, torder = 0;
   const bool tuned = !xtime && tuned_tile_height(c, &tth, &torder);
-  if (xtime) {
-    th = 16;  // the per-crossing-time kernel has the 64 x 16 shape only
-  } else if (th != 8 && th != 16) {
+  if (xtime || (c.mode == SIM_DIFF && th == SIM_TILE_ROWS)) {
+    th = 16;  // the per-crossing-time and difference kernels have the 64 x 16 shape only
+  } else if (th != 8 && th != 16 && th != SIM_TILE_ROWS) {
     if (tuned) {
       th = tth;
       order = torder;
@@ -467,6 +475,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   chk(dalloc(&s->d_staging, z.stage));
   chk(dalloc(&s->d_events, cap));
   chk(dalloc(&s->d_seg, seg_cap));
+  if (th == SIM_TILE_ROWS) chk(dalloc(&s->d_segflag, (size_t)s->bmax * s->segs_per_k));
   chk(dalloc(&s->d_tdone, (size_t)s->tiles_x * s->tiles_y));
   chk(dalloc(&s->d_order_status, ochunks));
   chk(dalloc(&s->d_desc, s->bmax));

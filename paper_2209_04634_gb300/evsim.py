@@ -32,7 +32,7 @@ SIM_REF_ACCUM, SIM_REF_RESET = 0, 1
 SIM_HOST, SIM_DEVICE = 0, 1
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 SIM_MAX_BATCH = 1024
-SIM_TILE_AUTO, SIM_TILE_TUNE = 0, -1
+SIM_TILE_AUTO, SIM_TILE_TUNE, SIM_TILE_ROWS = 0, -1, 1
 SIM_TIME_SUBSTEP, SIM_TIME_CROSSING = 0, 1
 SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
 KERNEL_NAMES = ["init", "flowmax", "dense", "mask", "sparse", "order", "copy"]
