@@ -245,11 +245,13 @@ class Passes:
                 th, tune = tile_height, {"tile_height": tile_height, "fixed": True}
             else:
                 n = min(tune_frames, len(seq.t_us))
-                th, us16, us8 = evsim.autotune_sample(
+                th, us16, us8, usr = evsim.autotune_sample(
                     W, H, self.frames[:n], self.flows[:n], seq.t_us[:n],
                     **evsim.seq_options(seq, mode=m, **extra))
-                tune = {"tile_height": th, "sample": f"first {n} frames",
-                        "us_per_frame_64x16": us16, "us_per_frame_64x8": us8}
+                tune = {"tile_height": th, "kernel": "rows" if th == evsim.SIM_TILE_ROWS
+                        else f"tiles 64x{th}", "sample": f"first {n} frames",
+                        "us_per_frame_64x16": us16, "us_per_frame_64x8": us8,
+                        "us_per_frame_rows": usr}
             sim = evsim.simulator_for(seq, m, event_capacity=cap, stream=stream, tile_height=th,
                                       **extra)
             st = sim.stats()

@@ -112,9 +112,10 @@ typedef struct {
   int64_t event_capacity;    /* device event buffer (events); 0: default max(2^20, 8 W H) */
   void* cuda_stream;         /* cudaStream_t to order work on; NULL: library-owned stream;
                                 cudaStreamLegacy for the legacy default stream */
-  int32_t tile_height;       /* batch kernel tile shape: SIM_TILE_AUTO, SIM_TILE_TUNE, 8 or
-                                16 (64 x 8 tiles of 256 threads / 64 x 16 of 512); see
-                                sim_autotune.  Group members always use 16. */
+  int32_t tile_height;       /* batch kernel: SIM_TILE_AUTO, SIM_TILE_TUNE, 8 or 16 (64 x 8
+                                tiles of 256 threads / 64 x 16 of 512), or SIM_TILE_ROWS (the
+                                row kernel, below); see sim_autotune.  Group members always
+                                use 16. */
   int32_t event_time;        /* SIM_TIME_SUBSTEP | SIM_TIME_CROSSING (see below) */
 } sim_config;
 
@@ -167,7 +168,7 @@ typedef struct {
   int32_t max_batch;         /* frames per device batch */
   int64_t pixel_substeps;    /* sum over committed frames of width * height * N */
   int64_t active_substeps;   /* sum over committed frames of (pixels simulated) * N */
-  int32_t tile_height;       /* tile height of the batch kernel (8 or 16) */
+  int32_t tile_height;       /* the batch kernel: tile height 8 or 16, or SIM_TILE_ROWS */
   int32_t block_order;       /* its tile order: 0 linear, 1 serpentine, 2 balanced
                                 (see sim_autotune) */
   int64_t active_pixels;     /* sum over committed frames of the pixels simulated (dense:
@@ -228,8 +229,12 @@ int sim_push_frame(sim_t* s, const void* frame, int64_t pitch_bytes, const float
  * three kernel launches per batch: each tile (or raster chunk) is carried
  * through every frame of the batch by one block.  A batch commits as a whole:
  * if its events do not fit, none of its frames commit (SIM_ERR_EVENT_OVERFLOW
- * at the next sim_sync / sim_pop_events).  Host-memory batches are first
- * copied into a device staging area that grows to fit.  Timestamps are
+ * at the next sim_sync / sim_pop_events).  Host-memory frames are copied
+ * into a device staging area (two slots, grown to fit) in chunks of
+ * max(4, ceil(count / 8)) frames (at most max_batch), each chunk a device
+ * batch of its own: the next chunk is copied on a library-owned copy stream
+ * while the previous one is simulated (pinned host memory lets the copies
+ * run asynchronously; pageable memory is still correct).  Timestamps are
  * validated for the whole call before anything is enqueued.  The event
  * stream equals that of count sim_push_frame calls. */
 int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t pitch_bytes,
@@ -346,9 +351,11 @@ const char* sim_version(void);
  * table keyed by (width, height, pixel_format, mode, substeps,
  * max_substeps, intensity, ref_mode, threshold maps present).  sim_create
  * consults the table when cfg->tile_height is SIM_TILE_AUTO or SIM_TILE_TUNE.
- * *tile_height_out (if not NULL) receives 8 or 16; us_out (if not NULL, 2
- * doubles) the kernel time per frame in microseconds of shapes 16 and 8
- * (each in its faster order).  sim_get_stats reports a handle's shape and
+ * The row kernel (SIM_TILE_ROWS) is timed too (dense and sparse modes) and
+ * is chosen on the same 5 % rule.
+ * *tile_height_out (if not NULL) receives 16, 8 or SIM_TILE_ROWS; us_out (if
+ * not NULL, 3 doubles) the kernel time per frame in microseconds of shapes 16
+ * and 8 (each in its faster order) and of the row kernel (0 when not timed).  sim_get_stats reports a handle's shape and
  * order.  The table serves substep-time handles (cfg->event_time is not
  * part of its key and is not timed); SIM_TIME_CROSSING handles run 64 x 16
  * tiles in block order.
@@ -372,7 +379,7 @@ int sim_autotune_sample(const sim_config* cfg, int32_t count, const void* const*
                         int32_t mem, int32_t* tile_height_out, double* us_out);
 
 /* Write the autotuner table to a text file (one line per configuration:
- * the key's nine fields, the chosen tile height and block order, the two
+ * the key's nine fields, the chosen tile height and block order, the three
  * per-frame times),
  * or merge such a file into the table (later lines win).  Return SIM_OK or
  * SIM_ERR_ARG (NULL path, unreadable or malformed file: nothing merged). */

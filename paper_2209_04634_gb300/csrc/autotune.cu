@@ -1,6 +1,6 @@
-// Autotuner of the batch kernel's tile shape (sim_autotune): both shapes run
-// the same synthetic frames, the faster one is recorded per configuration in
-// a process-wide table that sim_create consults.  The paper has no
+// Autotuner of the batch kernel's tile shape (sim_autotune): both tile shapes
+// and the row kernel run the same frames, the fastest is recorded per
+// configuration in a process-wide table that sim_create consults.  The paper has no
 // counterpart; the choice changes only how the work is launched, never the
 // events (both shapes compute the same integer arithmetic).
 #include <cuda_runtime.h>
@@ -24,7 +24,8 @@ using Key = std::tuple<int, int, int, int, int, int, int, int, int>;
 
 struct Entry {
   int th, order;
-  double us16, us8;  // best per-frame time of each shape over the block orders
+  double us16, us8;  // best per-frame time of each tile shape over the block orders
+  double us_rows;    // per-frame time of the row kernel (0: not timed)
 };
 
 std::mutex g_tune_mu;
@@ -113,6 +114,13 @@ int tune(const sim_config& c, int count, const void* const* frames, int64_t pitc
          const float* const* flows, const int64_t* t_us, int32_t mem, int32_t* th_out,
          double* us_out) {
   const int shapes[2] = {16, 8};
+  // the row kernel serves dense and sparse interpolation
+  double us_rows = 0;
+  if (c.mode != SIM_DIFF) {
+    const int rc = time_shape(c, SIM_TILE_ROWS, 0, count, frames, pitch, flows, t_us, mem,
+                              &us_rows);
+    if (rc) return rc;
+  }
   const long long T16 = ((c.width + 63) / 64) * (long long)((c.height + 15) / 16);
   const int norders = T16 * 2 <= evsim::PLAN_MAX_TILES ? 3 : 2;  // balanced needs a plan
   double us[2][3] = {{0, 0, 0}, {0, 0, 0}};
@@ -125,7 +133,14 @@ int tune(const sim_config& c, int count, const void* const* frames, int64_t pitc
   for (int a = 0; a < 2; ++a)
     for (int o = 0; o < norders; ++o)
       if (us[a][o] < us[ba][bo]) { ba = a; bo = o; }
-  if (!(us[ba][bo] < kMargin * us[0][0])) { ba = 0; bo = 0; }
+  int th = shapes[ba];
+  double best = us[ba][bo];
+  if (us_rows > 0 && us_rows < best) {
+    th = SIM_TILE_ROWS;
+    bo = 0;
+    best = us_rows;
+  }
+  if (!(best < kMargin * us[0][0])) { th = 16; bo = 0; }
   double us16 = us[0][0], us8 = us[1][0];
   for (int o = 1; o < norders; ++o) {
     us16 = std::min(us16, us[0][o]);
@@ -133,12 +148,13 @@ int tune(const sim_config& c, int count, const void* const* frames, int64_t pitc
   }
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_table[key_of(c)] = Entry{shapes[ba], bo, us16, us8};
+    g_table[key_of(c)] = Entry{th, bo, us16, us8, us_rows};
   }
-  if (th_out) *th_out = shapes[ba];
+  if (th_out) *th_out = th;
   if (us_out) {
     us_out[0] = us16;
     us_out[1] = us8;
+    us_out[2] = us_rows;
   }
   return SIM_OK;
 }
@@ -208,10 +224,10 @@ int sim_autotune_save(const char* path) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   for (const auto& kv : g_table) {
     const Key& k = kv.first;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.3f %.3f\n", std::get<0>(k),
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.3f %.3f %.3f\n", std::get<0>(k),
                  std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k),
                  std::get<6>(k), std::get<7>(k), std::get<8>(k), kv.second.th, kv.second.order,
-                 kv.second.us16, kv.second.us8);
+                 kv.second.us16, kv.second.us8, kv.second.us_rows);
   }
   const bool ok = std::fclose(f) == 0;
   return ok ? SIM_OK : SIM_ERR_ARG;
@@ -226,14 +242,14 @@ int sim_autotune_load(const char* path) {
   bool bad = false;
   while (std::fgets(line, sizeof(line), f)) {
     int v[11];
-    double a = 0, b = 0;
-    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %lf %lf", &v[0], &v[1], &v[2], &v[3],
-                    &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10], &a, &b) != 13 ||
-        (v[9] != 8 && v[9] != 16) || v[10] < 0 || v[10] > 2) {
+    double a = 0, b = 0, r = 0;
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %lf %lf %lf", &v[0], &v[1], &v[2],
+                    &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10], &a, &b, &r) != 14 ||
+        (v[9] != 8 && v[9] != 16 && v[9] != SIM_TILE_ROWS) || v[10] < 0 || v[10] > 2) {
       bad = true;
       break;
     }
-    add[Key{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]}] = Entry{v[9], v[10], a, b};
+    add[Key{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]}] = Entry{v[9], v[10], a, b, r};
   }
   std::fclose(f);
   if (bad) return SIM_ERR_ARG;

@@ -51,6 +51,12 @@ struct sim_s {
   unsigned char* d_stage_frames = nullptr;  // host batches: staged frames and flows
   float2* d_stage_flows = nullptr;
   long long stage_frames = 0;               // frames the host staging holds
+  // host batches: chunks are copied on copy_stream into two alternating
+  // staging slots while the previous chunk simulates on `stream`
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t slot_copied[2] = {nullptr, nullptr};  // a slot's copies are done
+  cudaEvent_t slot_free[2] = {nullptr, nullptr};    // a slot's kernels are done
+  cudaEvent_t stage_ready = nullptr;                // earlier work on `stream` is done
   long long event_cap = 0;
   long long stage_cap = 0;     // staging events (event capacity plus chunk slack)
   long long segs_per_k = 0;

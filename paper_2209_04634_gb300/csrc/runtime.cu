@@ -101,6 +101,12 @@ void free_all(sim_t* s) {
     cudaEventDestroy(r.b);
   }
   for (auto e : s->pool) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k) {
+    if (s->slot_copied[k]) cudaEventDestroy(s->slot_copied[k]);
+    if (s->slot_free[k]) cudaEventDestroy(s->slot_free[k]);
+  }
+  if (s->stage_ready) cudaEventDestroy(s->stage_ready);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -536,32 +542,67 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
   }
   cudaError_t e = cudaSuccess;
   std::vector<evsim::FrameDesc> desc;
-  while (i0 < count) {
-    const int n = std::min(count - i0, s->bmax);
-    desc.assign(n, evsim::FrameDesc{});
-    if (mem == SIM_HOST && s->stage_frames < n) {
-      e = cudaStreamSynchronize(s->stream);  // earlier batches may still read the old area
+  // Host frames go through device staging in chunks of m frames (about an
+  // eighth of the call, at least 4, at most a device batch), each chunk a
+  // device batch of its own: chunk j + 1 is copied on the copy stream into
+  // the other of two staging slots while chunk j simulates, so the copies
+  // overlap the kernels.  Device frames are read in place, in device batches
+  // of max_batch frames.
+  const int rest = count - i0;
+  const int m = mem == SIM_HOST ? std::min(s->bmax, std::max(4, (rest + 7) / 8)) : s->bmax;
+  if (mem == SIM_HOST && rest > 0) {
+    if (!s->copy_stream) {
+      e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&s->slot_copied[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->slot_free[k], cudaEventDisableTiming);
+      }
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->stage_ready, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_rc(e);
+    }
+    const int slots = std::min(2 * m, 2 * rest);
+    if (s->stage_frames < slots) {
+      // earlier batches may still read the old area
+      e = cudaStreamSynchronize(s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
       if (e != cudaSuccess) return cuda_rc(e);
       cudaFree(s->d_stage_frames);
       cudaFree(s->d_stage_flows);
       s->d_stage_frames = nullptr;
       s->d_stage_flows = nullptr;
       s->stage_frames = 0;
-      e = dalloc(&s->d_stage_frames, (size_t)n * s->P * s->ch);
-      if (e == cudaSuccess) e = dalloc(&s->d_stage_flows, (size_t)n * s->P);
+      e = dalloc(&s->d_stage_frames, (size_t)slots * s->P * s->ch);
+      if (e == cudaSuccess) e = dalloc(&s->d_stage_flows, (size_t)slots * s->P);
       if (e != cudaSuccess) return cuda_rc(e);
-      s->stage_frames = n;
+      s->stage_frames = slots;
+    }
+    // the copies wait for whatever the handle's stream did with the staging
+    // area before this call (a first frame, earlier batches)
+    e = cudaEventRecord(s->stage_ready, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, s->stage_ready, 0);
+    if (e != cudaSuccess) return cuda_rc(e);
+  }
+  int slot = 0;
+  while (i0 < count) {
+    const int n = std::min(count - i0, m);
+    desc.assign(n, evsim::FrameDesc{});
+    if (mem == SIM_HOST) {
+      // the slot's previous chunk must have been simulated before it is overwritten
+      e = cudaStreamWaitEvent(s->copy_stream, s->slot_free[slot], 0);
+      if (e != cudaSuccess) return cuda_rc(e);
     }
     for (int j = 0; j < n; ++j) {
       const int i = i0 + j;
       evsim::FrameDesc& d = desc[j];
       if (mem == SIM_HOST) {
-        unsigned char* fd = s->d_stage_frames + (size_t)j * s->P * s->ch;
-        float2* fl = s->d_stage_flows + (size_t)j * s->P;
+        const size_t f = (size_t)slot * m + j;
+        unsigned char* fd = s->d_stage_frames + f * s->P * s->ch;
+        float2* fl = s->d_stage_flows + f * s->P;
         e = cudaMemcpy2DAsync(fd, row, frames[i], pitch_bytes, row, s->H, cudaMemcpyHostToDevice,
-                              s->stream);
+                              s->copy_stream);
         if (e == cudaSuccess)
-          e = cudaMemcpyAsync(fl, flows[i], s->P * sizeof(float2), cudaMemcpyHostToDevice, s->stream);
+          e = cudaMemcpyAsync(fl, flows[i], s->P * sizeof(float2), cudaMemcpyHostToDevice,
+                              s->copy_stream);
         if (e != cudaSuccess) return cuda_rc(e);
         d.frame = fd;
         d.pitch = row;
@@ -573,13 +614,20 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
       }
       d.t_rel = t_us[i] - s->t0;
     }
+    if (mem == SIM_HOST) {
+      e = cudaEventRecord(s->slot_copied[slot], s->copy_stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->slot_copied[slot], 0);
+      if (e != cudaSuccess) return cuda_rc(e);
+    }
     e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
                         cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = enqueue_batch(s, n);
+    if (e == cudaSuccess && mem == SIM_HOST) e = cudaEventRecord(s->slot_free[slot], s->stream);
     if (e != cudaSuccess) return cuda_rc(e);
     s->t_last = t_us[i0 + n - 1];
     s->pushed += n;
     i0 += n;
+    slot ^= 1;
   }
   return SIM_OK;
 }

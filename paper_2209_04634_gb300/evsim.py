@@ -410,18 +410,20 @@ def make_config(width: int, height: int, *, pixel_format: int = SIM_LUMA8,
     return cfg, keep
 
 
-def autotune(width: int, height: int, frames: int = 8, **kw) -> tuple[int, float, float]:
+def autotune(width: int, height: int, frames: int = 8, **kw) -> tuple[int, float, float, float]:
     """sim_autotune for a configuration (make_config keywords): returns the
-    chosen tile height and the per-frame kernel times (us) of heights 16 and 8."""
+    chosen tile height (16, 8 or SIM_TILE_ROWS) and the per-frame kernel
+    times (us) of heights 16 and 8 and of the row kernel."""
     cfg, keep = make_config(width, height, **kw)
     th = ctypes.c_int32(0)
-    us = (ctypes.c_double * 2)()
+    us = (ctypes.c_double * 3)()
     check(load().sim_autotune(ctypes.byref(cfg), frames, ctypes.byref(th), us), "sim_autotune")
     del keep
-    return int(th.value), float(us[0]), float(us[1])
+    return int(th.value), float(us[0]), float(us[1]), float(us[2])
 
 
-def autotune_sample(width: int, height: int, frames, flows, t_us, **kw) -> tuple[int, float, float]:
+def autotune_sample(width: int, height: int, frames, flows, t_us,
+                    **kw) -> tuple[int, float, float, float]:
     """sim_autotune_sample on a sample of a stream: frames (F, H, W[, 3]) uint8
     and flows (F, H, W, 2) float32, numpy (host) or torch CUDA tensors
     (device), t_us (F,) int64; make_config keywords for the rest."""
@@ -436,12 +438,12 @@ def autotune_sample(width: int, height: int, frames, flows, t_us, **kw) -> tuple
     t = (ctypes.c_int64 * F)(*[int(v) for v in t_us])
     pitch = width * (3 if getattr(frames, "ndim", len(frames.shape)) == 4 else 1)
     th = ctypes.c_int32(0)
-    us = (ctypes.c_double * 2)()
+    us = (ctypes.c_double * 3)()
     check(load().sim_autotune_sample(ctypes.byref(cfg), F, fr, pitch, fl, t,
                                      SIM_DEVICE if dev else SIM_HOST, ctypes.byref(th), us),
           "sim_autotune_sample")
     del keep
-    return int(th.value), float(us[0]), float(us[1])
+    return int(th.value), float(us[0]), float(us[1]), float(us[2])
 
 
 def accumulate(events, n: int, width: int, height: int, t_begin: int, t_end: int, frame,

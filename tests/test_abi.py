@@ -130,16 +130,18 @@ def test_autotune_arguments_and_table_file(lib, tmp_path):
     h = ctypes.c_void_p()
     assert lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)) == evsim.SIM_ERR_ARG
     src = tmp_path / "tune.txt"
-    src.write_text("64 32 1 0 8 0 0 0 0 8 0 10.000 9.000\n"
-                   "640 480 1 1 0 8 0 0 1 16 1 900.000 950.000\n")
+    src.write_text("64 32 1 0 8 0 0 0 0 8 0 10.000 9.000 11.000\n"
+                   "640 480 1 1 0 8 0 0 1 16 1 900.000 950.000 0.000\n"
+                   "1280 720 3 1 10 0 0 0 0 1 0 900.000 950.000 400.000\n")
     assert lib.sim_autotune_load(str(src).encode()) == evsim.SIM_OK
     out = tmp_path / "out.txt"
     assert lib.sim_autotune_save(str(out).encode()) == evsim.SIM_OK
     text = out.read_text()
-    assert "64 32 1 0 8 0 0 0 0 8 0 10.000 9.000" in text
-    assert "640 480 1 1 0 8 0 0 1 16 1 900.000 950.000" in text
+    assert "64 32 1 0 8 0 0 0 0 8 0 10.000 9.000 11.000" in text
+    assert "640 480 1 1 0 8 0 0 1 16 1 900.000 950.000 0.000" in text
+    assert "1280 720 3 1 10 0 0 0 0 1 0 900.000 950.000 400.000" in text
     bad = tmp_path / "bad.txt"
-    bad.write_text("64 32 1 0 8 0 0 0 0 12 0 1 1\n")  # tile height must be 8 or 16
+    bad.write_text("64 32 1 0 8 0 0 0 0 12 0 1 1 1\n")  # tile height must be 1, 8 or 16
     assert lib.sim_autotune_load(str(bad).encode()) == evsim.SIM_ERR_ARG
     assert lib.sim_autotune_load(str(tmp_path / "missing.txt").encode()) == evsim.SIM_ERR_ARG
     assert lib.sim_autotune_load(None) == evsim.SIM_ERR_ARG

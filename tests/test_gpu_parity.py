@@ -417,9 +417,8 @@ def test_tile_shapes_agree_on_the_workloads(mode):
 
 
 def test_autotune_chooses_a_shape_that_sim_create_uses():
-    th, us16, us8 = evsim.autotune(240, 180, frames=6, substeps=0, max_substeps=8)
-    assert th in (8, 16) and us16 > 0 and us8 > 0
-    assert th in (8, 16)
+    th, us16, us8, us_rows = evsim.autotune(240, 180, frames=6, substeps=0, max_substeps=8)
+    assert th in (8, 16, evsim.SIM_TILE_ROWS) and us16 > 0 and us8 > 0 and us_rows > 0
     sim = evsim.Simulator(240, 180, substeps=0, max_substeps=8)  # SIM_TILE_AUTO
     assert sim.stats().tile_height == th
     sim.close()
@@ -428,7 +427,7 @@ def test_autotune_chooses_a_shape_that_sim_create_uses():
     sim.close()
     # a configuration the table does not hold: tuned at create (SIM_TILE_TUNE)
     sim = evsim.Simulator(200, 100, substeps=3, tile_height=evsim.SIM_TILE_TUNE)
-    assert sim.stats().tile_height in (8, 16)
+    assert sim.stats().tile_height in (8, 16, evsim.SIM_TILE_ROWS)
     sim.close()
 
 
@@ -439,8 +438,9 @@ def test_autotune_on_a_sample_of_the_stream(device):
     if device:
         fr, fl = torch.from_numpy(fr).cuda(), torch.from_numpy(fl).cuda()
     opts = evsim.seq_options(seq, mode=evsim.SIM_SPARSE)
-    th, us16, us8 = evsim.autotune_sample(seq.width, seq.height, fr, fl, seq.t_us, **opts)
-    assert th in (8, 16) and us16 > 0 and us8 > 0
+    th, us16, us8, us_rows = evsim.autotune_sample(seq.width, seq.height, fr, fl, seq.t_us,
+                                                   **opts)
+    assert th in (8, 16, evsim.SIM_TILE_ROWS) and us16 > 0 and us8 > 0 and us_rows > 0
     sim = evsim.simulator_for(seq, evsim.SIM_SPARSE)  # SIM_TILE_AUTO: the table's entry
     assert sim.stats().tile_height == th
     sim.close()
@@ -457,7 +457,7 @@ def test_block_orders_give_the_oracle_events(order, mode, tmp_path):
     several batches (the balanced order's plan comes from the batch before)."""
     seq = random_seq(90, 200, F=7, seed=31 + order, substeps=3)
     f = tmp_path / "table.txt"
-    f.write_text(f"200 90 1 {mode} 3 0 0 0 0 16 {order} 1.0 1.0\n")
+    f.write_text(f"200 90 1 {mode} 3 0 0 0 0 16 {order} 1.0 1.0 0.0\n")
     evsim.autotune_load(str(f))
     g = gpu_run(seq, mode, use_maps=False, batch=2)
     assert g["stats"].block_order == order and g["stats"].tile_height == 16
