@@ -10,7 +10,9 @@ it, and the two share no code: this package holds its own C source
 Sec. III-A / III-B of Ziegler et al., arXiv 2209.04634, as restated in
 ``evsim_oracle.c``; ``event_time=T_CROSSING`` gives each threshold crossing
 its own time inside its interpolation step, ``orc_crossing_time``); ``run_diff()`` wraps ``orc_run_diff`` (the
-difference-frame interpolation of Sec. III-C).  ``exact.py`` is a second, pixel-major restatement in
+difference-frame interpolation of Sec. III-C); ``flow_lk()`` wraps
+``orc_flow_lk`` (the pyramidal Lucas-Kanade flow the paper's sparse and
+difference simulators take their flow from).  ``exact.py`` is a second, pixel-major restatement in
 pure Python integers for tiny inputs.
 
 Parity status of each function is pinned by ``tests/test_oracle_pins.py``
@@ -58,6 +60,12 @@ class OrcConfig(ctypes.Structure):
         ("row_begin", ctypes.c_int32),
         ("row_end", ctypes.c_int32),
     ]
+
+
+class LkConfig(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("min_eig", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -114,6 +122,9 @@ def _load():
             lib.orc_accumulate.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int64, ctypes.c_int64, vp]
             lib.orc_accumulate.restype = None
+            lib.orc_flow_lk.argtypes = [ctypes.POINTER(LkConfig), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, vp, vp, vp]
+            lib.orc_flow_lk.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -296,6 +307,24 @@ def run_diff(frames: np.ndarray, flows: np.ndarray | None, t_us, *, substeps: in
         raise ValueError(f"oracle rejected the input (code {n})")
     return {"events": ev[:n].copy(), "n_per_frame": npf, "ev_per_frame": epf,
             "clamped": int(clamped.value)}
+
+
+def flow_lk(f0: np.ndarray, f1: np.ndarray, *, levels: int = 3, radius: int = 3,
+            iterations: int = 3, min_eig: float = 64.0) -> np.ndarray:
+    """orc_flow_lk: pyramidal Lucas-Kanade flow from f0 to f1 ((H, W) or
+    (H, W, 3) uint8); returns (H, W, 2) int32, Q16 px."""
+    f0 = np.ascontiguousarray(f0, dtype=np.uint8)
+    f1 = np.ascontiguousarray(f1, dtype=np.uint8)
+    assert f0.shape == f1.shape
+    H, W = f0.shape[:2]
+    ch = 3 if f0.ndim == 3 else 1
+    out = np.zeros((H, W, 2), dtype=np.int32)
+    cfg = LkConfig(levels, radius, iterations, 0, float(min_eig))
+    rc = _load().orc_flow_lk(ctypes.byref(cfg), W, H, ch, f0.ctypes.data, f1.ctypes.data,
+                             out.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the input (code {rc})")
+    return out
 
 
 def accumulate(events: np.ndarray, W: int, H: int, t_begin: int, t_end: int,

@@ -424,3 +424,189 @@ void orc_accumulate(const orc_event* ev, int64_t n, int32_t W, int32_t H, int64_
     frame[(int64_t)y * W + x] += (ev[i].yp & 1) ? 1 : -1;
   }
 }
+
+/*
+ * Pyramidal Lucas-Kanade optical flow.  The paper computes the flow between
+ * consecutive frames with OpenCV; its sparse and difference-frame
+ * simulators use Lucas-Kanade (Sec. III-B: "any sparse optical flow
+ * algorithm" on the selected pixels; Sec. IV-A, Figs. 3 and 4: "Sparse int.
+ * w. LK", "Difference int. w. LK").  Lucas and Kanade (1981) take the flow
+ * of a pixel as the least-squares solution of the linearised brightness
+ * constancy equations Ix u + Iy v + It = 0 over a window around it,
+ * iterated with the second frame resampled at the current estimate, and
+ * coarse to fine over image pyramids for motions beyond the window.  The
+ * paper fixes no parameters or precision; the reading here (O17):
+ *   - images: 8-bit luma (BT.601 for RGB) times 16 (4 fractional bits);
+ *     level l+1 is the 2 x 2 box average of level l, rounded half up, of
+ *     size ((W_l + 1) / 2, (H_l + 1) / 2), reads clamped to the image;
+ *   - gradients of the first frame: Ix = I(x+1, y) - I(x-1, y),
+ *     Iy = I(x, y+1) - I(x, y-1) (twice the central difference), reads
+ *     clamped; window: the (2r+1)^2 pixels p + (i, j), each coordinate
+ *     clamped to the image;
+ *   - G = sum of [Ix Ix, Ix Iy; Ix Iy, Iy Iy] over the window (int64);
+ *     the pixel is tracked only if the smaller eigenvalue of G divided by
+ *     the window area is at least min_eig, else its flow is its guess;
+ *   - iteration: It(q) = J(q + g + v) - I(q), J sampled with the clamped
+ *     bilinear of the simulator (Q16 position, 12-bit fractions, blends
+ *     rounded half up); b = sum of (Ix It, Iy It) (int64); the update is
+ *     -2 G^-1 b px (the factor 2: Ix is twice the derivative), evaluated
+ *     in IEEE double in the order written below and rounded to Q16 (ties to
+ *     even); v += update;
+ *   - coarse to fine: the guess g of a pixel of level l is twice the flow
+ *     of its parent (x / 2, y / 2) at level l + 1 (zero at the top);
+ *     the flow of level 0 is the output, Q16 px, clamped to +-1024 px.
+ */
+static int32_t lk_at(const int32_t* P, int32_t W, int32_t H, int64_t x, int64_t y) {
+  if (x < 0) x = 0;
+  if (x > W - 1) x = W - 1;
+  if (y < 0) y = 0;
+  if (y > H - 1) y = H - 1;
+  return P[y * W + x];
+}
+
+/* Clamp-to-edge bilinear sample of a Q4 level image at a Q16 position
+ * (the same rounding as orc_bilinear). */
+static int64_t lk_bilinear(const int32_t* P, int32_t W, int32_t H, int64_t px, int64_t py) {
+  return orc_bilinear(P, W, H, px, py);
+}
+
+int orc_flow_lk(const orc_lk_config* c, int32_t W, int32_t H, int32_t channels,
+                const uint8_t* f0, const uint8_t* f1, int32_t* flow) {
+  if (!c || !f0 || !f1 || !flow || W < 1 || H < 1) return -1;
+  if (channels != 1 && channels != 3) return -1;
+  if (c->levels < 1 || c->levels > 8 || c->radius < 1 || c->radius > 7) return -1;
+  if (c->iterations < 1 || c->iterations > 16) return -1;
+  const int L = c->levels, r = c->radius;
+  int32_t Ws[8], Hs[8];
+  int32_t* I[8];
+  int32_t* J[8];
+  int64_t* D[8]; /* flow of each level, Q16, 2 per pixel */
+  Ws[0] = W;
+  Hs[0] = H;
+  for (int l = 1; l < L; ++l) {
+    Ws[l] = (Ws[l - 1] + 1) / 2;
+    Hs[l] = (Hs[l - 1] + 1) / 2;
+  }
+  int fail = 0;
+  for (int l = 0; l < L; ++l) {
+    const int64_t n = (int64_t)Ws[l] * Hs[l];
+    I[l] = (int32_t*)malloc(n * sizeof(int32_t));
+    J[l] = (int32_t*)malloc(n * sizeof(int32_t));
+    D[l] = (int64_t*)malloc(2 * n * sizeof(int64_t));
+    if (!I[l] || !J[l] || !D[l]) fail = 1;
+  }
+  if (!fail) {
+    /* level 0: luma times 16 */
+    for (int64_t p = 0; p < (int64_t)W * H; ++p) {
+      int32_t a, b;
+      if (channels == 1) {
+        a = f0[p];
+        b = f1[p];
+      } else {
+        a = orc_luma(f0[3 * p], f0[3 * p + 1], f0[3 * p + 2]);
+        b = orc_luma(f1[3 * p], f1[3 * p + 1], f1[3 * p + 2]);
+      }
+      I[0][p] = 16 * a;
+      J[0][p] = 16 * b;
+    }
+    /* pyramids: 2 x 2 box averages, rounded half up */
+    for (int l = 1; l < L; ++l) {
+      for (int32_t y = 0; y < Hs[l]; ++y)
+        for (int32_t x = 0; x < Ws[l]; ++x) {
+          const int32_t* Pi = I[l - 1];
+          const int32_t* Pj = J[l - 1];
+          const int32_t w = Ws[l - 1], h = Hs[l - 1];
+          int64_t si = (int64_t)lk_at(Pi, w, h, 2 * x, 2 * y) + lk_at(Pi, w, h, 2 * x + 1, 2 * y) +
+                       lk_at(Pi, w, h, 2 * x, 2 * y + 1) + lk_at(Pi, w, h, 2 * x + 1, 2 * y + 1);
+          int64_t sj = (int64_t)lk_at(Pj, w, h, 2 * x, 2 * y) + lk_at(Pj, w, h, 2 * x + 1, 2 * y) +
+                       lk_at(Pj, w, h, 2 * x, 2 * y + 1) + lk_at(Pj, w, h, 2 * x + 1, 2 * y + 1);
+          I[l][(int64_t)y * Ws[l] + x] = (int32_t)((si + 2) >> 2);
+          J[l][(int64_t)y * Ws[l] + x] = (int32_t)((sj + 2) >> 2);
+        }
+    }
+    const double area = (double)((2 * r + 1) * (2 * r + 1));
+    const int64_t lim = (int64_t)1024 * 65536;
+    /* coarse to fine */
+    for (int l = L - 1; l >= 0; --l) {
+      const int32_t w = Ws[l], h = Hs[l];
+      const int32_t* Il = I[l];
+      const int32_t* Jl = J[l];
+      for (int32_t y = 0; y < h; ++y)
+        for (int32_t x = 0; x < w; ++x) {
+          int64_t gx = 0, gy = 0;
+          if (l < L - 1) {
+            const int64_t* Dp = D[l + 1];
+            const int64_t pp = (int64_t)(y / 2) * Ws[l + 1] + (x / 2);
+            gx = 2 * Dp[2 * pp];
+            gy = 2 * Dp[2 * pp + 1];
+          }
+          /* structure tensor of the window */
+          int64_t sxx = 0, sxy = 0, syy = 0;
+          for (int j = -r; j <= r; ++j)
+            for (int i = -r; i <= r; ++i) {
+              int64_t qx = x + i, qy = y + j;
+              if (qx < 0) qx = 0;
+              if (qx > w - 1) qx = w - 1;
+              if (qy < 0) qy = 0;
+              if (qy > h - 1) qy = h - 1;
+              const int64_t ix = (int64_t)lk_at(Il, w, h, qx + 1, qy) - lk_at(Il, w, h, qx - 1, qy);
+              const int64_t iy = (int64_t)lk_at(Il, w, h, qx, qy + 1) - lk_at(Il, w, h, qx, qy - 1);
+              sxx += ix * ix;
+              sxy += ix * iy;
+              syy += iy * iy;
+            }
+          const double a = (double)sxx, b = (double)sxy, d = (double)syy;
+          const double det = a * d - b * b;
+          const double tr = a + d, df = a - d;
+          const double disc = sqrt(df * df + (4.0 * b) * b);
+          const double lmin = (tr - disc) * 0.5;
+          int64_t vx = 0, vy = 0;
+          if (lmin / area >= c->min_eig && det > 0.0) {
+            for (int k = 0; k < c->iterations; ++k) {
+              int64_t bx = 0, by = 0;
+              for (int j = -r; j <= r; ++j)
+                for (int i = -r; i <= r; ++i) {
+                  int64_t qx = x + i, qy = y + j;
+                  if (qx < 0) qx = 0;
+                  if (qx > w - 1) qx = w - 1;
+                  if (qy < 0) qy = 0;
+                  if (qy > h - 1) qy = h - 1;
+                  const int64_t ix =
+                      (int64_t)lk_at(Il, w, h, qx + 1, qy) - lk_at(Il, w, h, qx - 1, qy);
+                  const int64_t iy =
+                      (int64_t)lk_at(Il, w, h, qx, qy + 1) - lk_at(Il, w, h, qx, qy - 1);
+                  const int64_t jv =
+                      lk_bilinear(Jl, w, h, qx * 65536 + gx + vx, qy * 65536 + gy + vy);
+                  const int64_t it = jv - lk_at(Il, w, h, qx, qy);
+                  bx += ix * it;
+                  by += iy * it;
+                }
+              const double ex = (double)bx, ey = (double)by;
+              const double nx = d * ex - b * ey;
+              const double ny = a * ey - b * ex;
+              vx += (int64_t)nearbyint((-131072.0 * nx) / det);
+              vy += (int64_t)nearbyint((-131072.0 * ny) / det);
+              if (vx > lim) vx = lim;
+              if (vx < -lim) vx = -lim;
+              if (vy > lim) vy = lim;
+              if (vy < -lim) vy = -lim;
+            }
+          }
+          int64_t ox = gx + vx, oy = gy + vy;
+          if (ox > lim) ox = lim;
+          if (ox < -lim) ox = -lim;
+          if (oy > lim) oy = lim;
+          if (oy < -lim) oy = -lim;
+          D[l][2 * ((int64_t)y * w + x)] = ox;
+          D[l][2 * ((int64_t)y * w + x) + 1] = oy;
+        }
+    }
+    for (int64_t p = 0; p < 2 * (int64_t)W * H; ++p) flow[p] = (int32_t)D[0][p];
+  }
+  for (int l = 0; l < L; ++l) {
+    free(I[l]);
+    free(J[l]);
+    free(D[l]);
+  }
+  return fail ? -4 : 0;
+}

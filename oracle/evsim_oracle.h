@@ -127,6 +127,26 @@ int64_t orc_run_diff(const orc_config* cfg, int32_t n_frames, const uint8_t* fra
 void orc_accumulate(const orc_event* ev, int64_t n, int32_t W, int32_t H, int64_t t_begin,
                     int64_t t_end, int32_t* frame);
 
+/* Pyramidal Lucas-Kanade optical flow (the flow the paper's sparse and
+ * difference simulators use, Sec. III-B, Sec. IV-A); the reading O17 is
+ * stated in evsim_oracle.c.  levels 1..8, radius 1..7 (window 2r+1 square),
+ * iterations 1..16 per level, min_eig: the smallest eigenvalue of the
+ * window's gradient matrix per window pixel below which a pixel keeps its
+ * guess (gradients in Q4 units, twice the derivative). */
+typedef struct {
+  int32_t levels;
+  int32_t radius;
+  int32_t iterations;
+  int32_t pad;
+  double min_eig;
+} orc_lk_config;
+
+/* Flow from frame f0 to frame f1 (W x H, 1 or 3 channels, rows packed):
+ * flow[2 (y W + x) + {0, 1}] = (dx, dy) in Q16 px.  Returns 0, -1 on bad
+ * arguments, -4 when out of memory. */
+int orc_flow_lk(const orc_lk_config* c, int32_t W, int32_t H, int32_t channels,
+                const uint8_t* f0, const uint8_t* f1, int32_t* flow);
+
 #ifdef __cplusplus
 }
 #endif

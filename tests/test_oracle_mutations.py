@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 
+from . import test_oracle_lk as lk_pins
 from . import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "evsim_oracle.c")
@@ -112,6 +113,27 @@ MUTATIONS = {
                                         "orc_crossing_time(tk1, tk, ip, I, Rb - j * cp, 0)"),
     "diff_blend_reversed": ("int64_t I = lerp_q12(s0, s1, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)",
                             "int64_t I = lerp_q12(s1, s0, w);\n          int32_t cp = pixel_threshold(cpos_map, c->c_pos_q16, p);\n          int32_t cn = pixel_threshold(cneg_map, c->c_neg_q16, p);\n          if (I > cp)"),
+    # pyramidal Lucas-Kanade flow (orc_flow_lk)
+    "lk_gradient_sign_in_the_window_matrix": (
+        "const int64_t ix = (int64_t)lk_at(Il, w, h, qx + 1, qy) - lk_at(Il, w, h, qx - 1, qy);",
+        "const int64_t ix = (int64_t)lk_at(Il, w, h, qx - 1, qy) - lk_at(Il, w, h, qx + 1, qy);"),
+    "lk_guess_not_doubled": [("gx = 2 * Dp[2 * pp];", "gx = Dp[2 * pp];"),
+                             ("gy = 2 * Dp[2 * pp + 1];", "gy = Dp[2 * pp + 1];")],
+    "lk_update_sign": [("vx += (int64_t)nearbyint((-131072.0 * nx) / det);",
+                        "vx += (int64_t)nearbyint((131072.0 * nx) / det);"),
+                       ("vy += (int64_t)nearbyint((-131072.0 * ny) / det);",
+                        "vy += (int64_t)nearbyint((131072.0 * ny) / det);")],
+    "lk_components_swapped": [("vx += (int64_t)nearbyint((-131072.0 * nx) / det);",
+                               "vx += (int64_t)nearbyint((-131072.0 * ny) / det);"),
+                              ("vy += (int64_t)nearbyint((-131072.0 * ny) / det);",
+                               "vy += (int64_t)nearbyint((-131072.0 * nx) / det);")],
+    "lk_window_short_by_one": ("          for (int j = -r; j <= r; ++j)\n            for (int i = -r; i <= r; ++i) {",
+                               "          for (int j = -r; j < r; ++j)\n            for (int i = -r; i <= r; ++i) {"),
+    "lk_temporal_difference_sign": ("const int64_t it = jv - lk_at(Il, w, h, qx, qy);",
+                                    "const int64_t it = lk_at(Il, w, h, qx, qy) - jv;"),
+    "lk_eigenvalue_test_dropped": ("if (lmin / area >= c->min_eig && det > 0.0) {", "if (det > 0.0) {"),
+    "lk_second_frame_not_sampled": ("lk_bilinear(Jl, w, h, qx * 65536 + gx + vx, qy * 65536 + gy + vy);",
+                                    "lk_bilinear(Il, w, h, qx * 65536 + gx + vx, qy * 65536 + gy + vy);"),
 }
 
 
@@ -168,6 +190,18 @@ def battery():
     yield pins.test_sparse_adaptive_substeps_follow_the_active_pixels_only
     yield lambda: pins.test_crossing_times_keep_events_and_stay_inside_their_substep(
         oracle.SPARSE, oracle.ACCUM)
+    # Lucas-Kanade flow
+    yield lk_pins.test_identical_frames_give_zero_flow
+    yield lk_pins.test_untextured_frames_are_not_tracked
+    for u, v in [(2, 0), (0, -2), (2, -2), (-4, 2)]:
+        yield lambda u=u, v=v: lk_pins.test_exactly_linear_motion_is_recovered_exactly(u, v)
+    yield lk_pins.test_transposed_frames_give_the_transposed_flow_at_one_step
+    yield lk_pins.test_mirrored_frames_give_the_mirrored_flow_at_one_step
+    yield lk_pins.test_one_dimensional_texture_is_not_tracked
+    yield lk_pins.test_translation_is_recovered_to_a_fraction_of_a_pixel
+    yield lk_pins.test_motion_beyond_the_window_needs_the_pyramid
+    yield lk_pins.test_rgb_frames_give_the_flow_of_their_luma
+    yield lk_pins.test_no_window_passes_an_unreachable_eigenvalue_threshold
 
 
 def test_battery_passes_on_the_real_oracle():
