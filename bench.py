@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the paper-mode, accumulate, difference and crossing-time objects")
+    ap.add_argument("--no-flow", action="store_true",
+                    help="skip the device optical-flow object")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the 640x480 and 240x180 workload objects")
     ap.add_argument("--only", default="",
@@ -349,7 +351,7 @@ def workload_object(name, desc, seq, stream, args, cap, key):
            "pixel_substeps_per_step": work,
            "active_pixel_substeps_per_step_sparse": units["sparse"]["active_substeps"],
            "kernel_us_per_launch": {k: v[0] / v[1] * 1e3 for k, v in kt.items()},
-           "rooflines": rooflines(seq, kt, units, key), "autotune": ps.tune}
+           "rooflines": rooflines(seq, kt, units, key, steps), "autotune": ps.tune}
     ps.close()
     return out
 
@@ -495,7 +497,7 @@ def run_ours(args, ws, rank, local):
     kt = ps.kernel_times()
     launches = sum(c for _, c in kt.values())
     total_ev = sum_over_ranks(ws, n_ev)
-    roofs = rooflines(seq, kt, units, "moving_rectangles_1280x720")
+    roofs = rooflines(seq, kt, units, "moving_rectangles_1280x720", args.steps)
     dom = max(roofs, key=lambda k: roofs[k]["total_ms"]) if roofs else None
 
     line = {
@@ -548,6 +550,8 @@ def run_ours(args, ws, rank, local):
         line["crossing_time"] = run_crossing_time(args, c2, frames, flows, stream, ccap, cout)
         del frames, flows, cout
         torch.cuda.empty_cache()
+    if rank == 0 and not args.no_flow:
+        line["lk_flow"] = run_flow(args, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = run_batched(args)
     if rank == 0 and not args.no_serve:
@@ -807,11 +811,12 @@ def kernel_model(kind: str, seq, u: dict, launches: int):
     return 0, 0
 
 
-def rooflines(seq, kt: dict, units: dict, key: str) -> dict:
+def rooflines(seq, kt: dict, units: dict, key: str, steps: int) -> dict:
     """Per kernel of a step: achieved integer issue rate and HBM bandwidth
     against the measured (HBM) and derived (issue) peaks, from the kernel's
-    algorithmic work and its CUDA-event device time; the binding resource
-    is the larger fraction."""
+    algorithmic work and its CUDA-event device time over `steps` steps (kt:
+    total time and launches over those steps; units: one step's); the
+    binding resource is the larger fraction."""
     import torch
     pk = measured_peaks()
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -824,7 +829,8 @@ def rooflines(seq, kt: dict, units: dict, key: str) -> dict:
         u = units.get(pass_name)
         if u is None or kind == "copy":
             continue
-        bytes_, ops = kernel_model(kind, seq, u, n)
+        b1, o1 = kernel_model(kind, seq, u, n / steps)
+        bytes_, ops = b1 * steps, o1 * steps
         s = t_ms / 1e3
         hbm = bytes_ / s / 1e9 if s > 0 else 0.0
         alu = ops / s / 1e12 if s > 0 else 0.0
@@ -847,6 +853,83 @@ def rooflines(seq, kt: dict, units: dict, key: str) -> dict:
             r.update(bound="hbm", achieved=hbm, peak=hbm_peak, unit="GB/s", frac=hf)
         out[name] = r
     return out
+
+def run_flow(args, stream):
+    """Pyramidal Lucas-Kanade flow on the device (the flow the paper's sparse
+    and difference simulators use, Sec. III-B, Sec. IV-A), on the 640x480
+    and 1280x720 workloads: time per frame pair (CUDA events), accuracy
+    against the generators' flow, and the whole pipeline - frames to device
+    flow to the dense and sparse simulators - in Gpix-substeps/s."""
+    import numpy as np
+    import torch
+
+    from paper_2209_04634_gb300 import evsim, synth
+    out = {"method": "pyramidal Lucas-Kanade, 3 levels, 7x7 window, 3 iterations, min_eig 64"}
+    cases = (("warped_texture_640x480", synth.warped_texture(seed=C2_SEED)),
+             ("moving_rectangles_1280x720", synth.moving_rectangles(seed=C3_SEED, frames=60)))
+    for name, seq in cases:
+        F, H, W = seq.frames.shape[:3]
+        frames = torch.from_numpy(seq.frames).cuda()
+        est = torch.zeros((F, H, W, 2), dtype=torch.float32, device="cuda")
+        fl = evsim.Flow(W, H, pixel_format=seq.channels, stream=stream)
+
+        def flow_pass():
+            for i in range(1, F):
+                fl.compute(frames[i - 1], frames[i], est[i])
+
+        for _ in range(2):
+            flow_pass()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            flow_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps / (F - 1)
+        e = np.hypot(*(est[1:].cpu().numpy() - seq.flows[1:]).transpose(3, 0, 1, 2))
+        # the pipeline: device flow into the simulators (dense + sparse)
+        sims = [evsim.simulator_for(seq, m, stream=stream, event_capacity=40_000_000)
+                for m in (evsim.SIM_DENSE, evsim.SIM_SPARSE)]
+        ev_out = torch.empty(40_000_000 * 8, dtype=torch.uint8, device="cuda")
+
+        def pipeline():
+            flow_pass()
+            n = 0
+            for sim in sims:
+                sim.reset()
+                sim.push_many(frames, est, seq.t_us)
+                k, rc = sim.pop_into(ev_out, 40_000_000)
+                assert rc == evsim.SIM_OK, rc
+                n += k
+            return n
+
+        pipeline()
+        work = sum(sim.stats().pixel_substeps for sim in sims)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        n_ev = 0
+        for _ in range(reps):
+            n_ev += pipeline()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        for sim in sims:
+            sim.close()
+        fl.close()
+        out[name] = {"us_per_frame_pair": us, "mpix_per_s": H * W / us,
+                     "endpoint_error_px": {"median": float(np.median(e)),
+                                           "p90": float(np.percentile(e, 90))},
+                     "pipeline": {"value": work / (ms / 1e3) / 1e9, "unit": METRIC,
+                                  "ms_per_step": ms, "ms_per_frame": ms / (F - 1),
+                                  "events_per_s": n_ev / reps / (ms / 1e3),
+                                  "frames": F}}
+        del frames, est, ev_out
+        torch.cuda.empty_cache()
+    return out
+
 
 BATCHED_WORKLOAD = ("64 concurrent streams (32 x 240x180, 24 x 640x480, 8 x 1280x720), warped "
                     "texture + smooth flow <= 8 px/frame, adaptive N <= 8, C = 0.2 with "

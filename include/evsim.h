@@ -609,6 +609,61 @@ typedef struct {
  * Uses the current device; allocates and frees all state itself. */
 int sim_serve_run(const sim_serve_config* cfg, sim_serve_result* res);
 
+/* ---- optical flow on the device -------------------------------------------
+ * Pyramidal Lucas-Kanade flow between two consecutive frames: the flow the
+ * paper's sparse and difference simulators use (Sec. III-B: the selected
+ * pixels' flow from "any sparse optical flow algorithm"; Sec. IV-A, Figs. 3
+ * and 4: "Sparse int. w. LK", "Difference int. w. LK"; the paper runs
+ * OpenCV's).  Computed on the device, its output is a flow buffer that
+ * sim_push_frame(s) takes as it is.
+ *
+ * Arithmetic (bit-exact across runs and devices): level 0 is the 8-bit luma
+ * (BT.601 for RGB) times 16; level l+1 the 2 x 2 box average of level l,
+ * rounded half up, of size ((W+1)/2, (H+1)/2); gradients of the first
+ * frame are twice the central differences (reads clamped); the window of a
+ * pixel is the (2r+1)^2 pixels around it, coordinates clamped; a pixel is
+ * tracked when the smaller eigenvalue of its window's gradient matrix, per
+ * window pixel, is at least min_eig (gradient units: twice the derivative
+ * in 1/16 intensity levels); each of `iterations` updates resamples the
+ * second frame with the simulator's clamped Q16 bilinear at the current
+ * estimate and adds -2 G^-1 b (G the gradient matrix, b the sums of
+ * gradient times temporal difference), solved in IEEE double with every
+ * operation rounded in a fixed order, rounded to Q16; the guess of a pixel
+ * is twice its parent's flow one level up; flows are clamped to +-1024 px.
+ * Untracked pixels keep their guess (zero at the top level). */
+typedef struct sim_flow_s sim_flow_t;  /* opaque, owned by the library */
+
+typedef struct {
+  int32_t width, height;   /* 1..SIM_MAX_DIM */
+  int32_t pixel_format;    /* SIM_LUMA8 | SIM_RGB8 */
+  int32_t levels;          /* pyramid levels, 1..8 (default 3) */
+  int32_t radius;          /* window radius r, 1..7: (2r+1)^2 pixels (default 3) */
+  int32_t iterations;      /* updates per level, 1..16 (default 3) */
+  double min_eig;          /* tracking threshold >= 0 (default 64) */
+  void* cuda_stream;       /* cudaStream_t to order work on; NULL: library-owned stream */
+} sim_flow_config;
+
+/* Defaults for a width x height luma stream (see the field comments). */
+int sim_flow_config_default(sim_flow_config* cfg, int32_t width, int32_t height);
+
+/* Allocate the pyramids of both frames and the per-level flows on the
+ * current device.  *out is set on SIM_OK only.  Errors: SIM_ERR_ARG,
+ * SIM_ERR_OOM, SIM_ERR_NO_DEVICE, SIM_ERR_CUDA. */
+int sim_flow_create(const sim_flow_config* cfg, sim_flow_t** out);
+
+/* Flow from frame prev (i-1) to frame cur (i), both device memory (rows of
+ * the given pitch, width * pixel_format bytes used), into flow (device,
+ * height * width * 2 floats (dx, dy) in px, 8-byte aligned) - the layout
+ * sim_push_frame reads.  Asynchronous on the handle's stream; the buffers
+ * must stay valid until the stream passes the call.  One handle must not
+ * be used from two host threads at once, and its calls are ordered on its
+ * stream. */
+int sim_flow_compute(sim_flow_t* f, const void* prev, int64_t prev_pitch, const void* cur,
+                     int64_t cur_pitch, float* flow);
+
+/* Release the handle (waits for its stream). */
+int sim_flow_destroy(sim_flow_t* f);
+
 /* ---- allocation-free frame pair ------------------------------------------
  * The paper has no counterpart: this is a library service for callers that
  * must not allocate device memory while they run, such as code whose device

@@ -122,7 +122,9 @@ evsim::SimParams make_params(const sim_t* s) {
   p.block_order = s->block_order;
   p.tile_cost = s->block_order == 2 ? s->d_tile_cost : nullptr;
   p.tile_order = s->d_tile_order;
-  p.segflag = s->tile_h == 1 ? s->d_segflag : nullptr;
+  // segment flags: the row kernel, and the dense tile kernel (which skips
+  // rows whose pixels are all quiet)
+  p.segflag = s->d_segflag;
   p.xtime = s->cfg.event_time == SIM_TIME_CROSSING;
   p.mode = s->cfg.mode;
   p.ref_mode = s->cfg.ref_mode;
@@ -274,22 +276,24 @@ cudaError_t enqueue_batch(sim_t* s, int n) {
     }
     if (s->cfg.mode == SIM_DIFF)
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_diff(p, b, s->stream); });
-    else if (p.segflag)
+    else if (s->tile_h == SIM_TILE_ROWS)
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_rows(p, b, s->stream); });
     else
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, b, s->stream); });
-    if (e == cudaSuccess && s->block_order == 2 && s->cfg.mode != SIM_DIFF && !p.segflag)
+    if (e == cudaSuccess && s->block_order == 2 && s->cfg.mode != SIM_DIFF &&
+        s->tile_h != SIM_TILE_ROWS)
       e = evsim::launch_plan(p, s->stream);
   } else {
     if (adaptive) {
       e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, b, s->stream); });
       if (e != cudaSuccess) return e;
     }
-    if (p.segflag)
+    if (s->tile_h == SIM_TILE_ROWS)
       e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_rows(p, b, s->stream); });
     else
       e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, b, s->stream); });
-    if (e == cudaSuccess && s->block_order == 2 && !p.segflag) e = evsim::launch_plan(p, s->stream);
+    if (e == cudaSuccess && s->block_order == 2 && s->tile_h != SIM_TILE_ROWS)
+      e = evsim::launch_plan(p, s->stream);
   }
   if (e != cudaSuccess) return e;
   return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, b, s->stream, s->order_grid); });
@@ -481,7 +485,9 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   chk(dalloc(&s->d_staging, z.stage));
   chk(dalloc(&s->d_events, cap));
   chk(dalloc(&s->d_seg, seg_cap));
-  if (th == SIM_TILE_ROWS) chk(dalloc(&s->d_segflag, (size_t)s->bmax * s->segs_per_k));
+  // segment flags (row kernel; dense tile kernel with substep times)
+  if (th == SIM_TILE_ROWS || (c.mode == SIM_DENSE && !xtime))
+    chk(dalloc(&s->d_segflag, (size_t)s->bmax * s->segs_per_k));
   chk(dalloc(&s->d_tdone, (size_t)s->tiles_x * s->tiles_y));
   chk(dalloc(&s->d_order_status, ochunks));
   chk(dalloc(&s->d_desc, s->bmax));

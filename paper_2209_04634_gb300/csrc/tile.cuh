@@ -1540,13 +1540,36 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         mfy = max(mfy, (unsigned)abs(Fy[q]));
       }
     }
+    // dense, substep times, segment flags on: a pixel is quiet when its flow
+    // is zero and both end values lie strictly inside its threshold band
+    // (reset mode: its change is within both thresholds).  With zero flow the
+    // interpolated values lie between the end values (every Q12 blend stays
+    // between its operands), so a quiet pixel emits nothing and keeps R; a
+    // row of quiet pixels skips its substeps and writes a flag instead of its
+    // segments, and a tile without a busy row builds no halo.
+    bool quiet = false;
+    if (!SPARSE && !XT && p.segflag) {
+      quiet = true;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!act[q]) continue;
+        if ((Fx[q] | Fy[q]) != 0) {
+          quiet = false;
+          continue;
+        }
+        const int Lp = L.slut[raw_luma(rawp, chp, ly[q] + HMAX, lx[q] + HMAX)];
+        const int Lc = L.slut[raw_luma(rawc, ch, ly[q] + HMAX, lx[q] + HMAX)];
+        if (RESET) quiet = quiet && Lc - Lp <= Cp[q] && Lp - Lc <= Cn[q];
+        else quiet = quiet && max(Lp, Lc) - R[q] < Cp[q] && R[q] - min(Lp, Lc) < Cn[q];
+      }
+    }
     mfx = __reduce_max_sync(FULL, mfx);
     mfy = __reduce_max_sync(FULL, mfy);
     if (lane == 0) {
       atomicMax(&s_fx, (int)mfx);
       atomicMax(&s_fy, (int)mfy);
     }
-    __syncthreads();
+    const bool busy = __syncthreads_or(quiet ? 0 : 1) != 0;
     const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
     const bool fast = hx <= HMAX && hy <= HMAX;
     // sparse fast path: row masks in the current flow buffer (its flows are
@@ -1557,7 +1580,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       for (int i = tid; i < N * TH * 4; i += NTD) rowm[i] = 0u;
       if (tid < N) s_multi[tid] = 0u;
     }
-    if (fast && A > 0) {
+    if (fast && A > 0 && busy) {
       hfx = max(hfx, hx);
       hfy = max(hfy, hy);
       if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
@@ -1628,7 +1651,11 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
                                                      segf, lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
                                                      &s_stage[warp]);
     } else if ((!SPARSE || dsw) && fast) {
-      if (ty0 + warp < H) {  // warp-uniform: rows below the image publish nothing
+      const bool skip = !SPARSE && p.segflag && __all_sync(FULL, quiet);
+      if (!SPARSE && p.segflag && ty0 + warp < H && lane == 0)
+        p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] =
+            skip ? 0 : 1;
+      if (ty0 + warp < H && !skip) {  // warp-uniform: rows below the image publish nothing
         // the row's 64 pixels are in the image (and, sparse, all simulated)
         const bool fullt = !SPARSE && tx0 + TW <= W;
 #define EVSIM_DENSE(FT, MK)                                                                    \
@@ -1654,6 +1681,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
                                         Fx, Fy, R, Cp, Cn);
       }
     } else if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
+      if (!SPARSE && p.segflag && ty0 + warp < H && lane == 0)  // every row simulated
+        p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 1;
       if (fast)
         tile_substeps<RESET, WIDE, true, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
@@ -1727,7 +1756,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       }
     }
     // frame i's halo becomes the previous-frame halo of frame i + 1
-    if (fast && A > 0) {
+    if (fast && A > 0 && busy) {
       int* t = pb;
       pb = cb;
       cb = t;

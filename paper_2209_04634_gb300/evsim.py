@@ -99,6 +99,14 @@ class simb_stats(ctypes.Structure):
     ]
 
 
+class sim_flow_config(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pixel_format", ctypes.c_int32),
+        ("levels", ctypes.c_int32), ("radius", ctypes.c_int32), ("iterations", ctypes.c_int32),
+        ("min_eig", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
 # (name, restype, argtypes) of every function that include/evsim.h declares
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 SIGNATURES = [
@@ -149,6 +157,10 @@ SIGNATURES = [
     ("simb_get_stats", ctypes.c_int, [_VP, ctypes.POINTER(simb_stats)]),
     ("simb_destroy", ctypes.c_int, [_VP]),
     ("sim_serve_run", ctypes.c_int, [_VP, _VP]),
+    ("sim_flow_config_default", ctypes.c_int, [ctypes.POINTER(sim_flow_config), _I32, _I32]),
+    ("sim_flow_create", ctypes.c_int, [ctypes.POINTER(sim_flow_config), ctypes.POINTER(_VP)]),
+    ("sim_flow_compute", ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _VP]),
+    ("sim_flow_destroy", ctypes.c_int, [_VP]),
     ("sim_step_pair_static", ctypes.c_int, [ctypes.POINTER(sim_config), _VP, _I64, _VP, _I64, _VP,
                                             _I64, _I64, _VP, _VP, _VP, _I64,
                                             ctypes.POINTER(_I64)]),
@@ -665,3 +677,47 @@ def step_pair_static(prev_frame, frame, flow, t_prev_us: int, t_us: int, ref_in,
         None if ref_out is None else _ptr(ref_out), _ptr(events), events.numel() // 8,
         ctypes.byref(n)), "sim_step_pair_static")
     return int(n.value)
+
+
+class Flow:
+    """sim_flow_* handle: pyramidal Lucas-Kanade flow between consecutive
+    frames on the device.  compute(prev, cur, out) takes torch CUDA uint8
+    frames ((H, W) or (H, W, 3), contiguous) and writes the flow into out, a
+    float32 CUDA tensor of shape (H, W, 2), asynchronously on the handle's
+    stream."""
+
+    def __init__(self, width: int, height: int, *, pixel_format: int = SIM_LUMA8,
+                 levels: int = 3, radius: int = 3, iterations: int = 3,
+                 min_eig: float = 64.0, stream=None):
+        self._lib = load()
+        cfg = sim_flow_config()
+        check(self._lib.sim_flow_config_default(ctypes.byref(cfg), width, height),
+              "sim_flow_config_default")
+        cfg.pixel_format = pixel_format
+        cfg.levels = levels
+        cfg.radius = radius
+        cfg.iterations = iterations
+        cfg.min_eig = float(min_eig)
+        if stream is not None:
+            handle = int(getattr(stream, "cuda_stream", stream))
+            cfg.cuda_stream = handle if handle else CUDA_STREAM_LEGACY
+        self.width, self.height, self.pixel_format = width, height, pixel_format
+        h = ctypes.c_void_p()
+        check(self._lib.sim_flow_create(ctypes.byref(cfg), ctypes.byref(h)), "sim_flow_create")
+        self.h = h
+
+    def compute(self, prev, cur, out) -> None:
+        pitch = self.width * self.pixel_format
+        check(self._lib.sim_flow_compute(self.h, _ptr(prev), pitch, _ptr(cur), pitch, _ptr(out)),
+              "sim_flow_compute")
+
+    def close(self) -> None:
+        if self.h:
+            check(self._lib.sim_flow_destroy(self.h), "sim_flow_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -2,8 +2,10 @@
 CPU oracle: bit-exact events, references and per-frame counts, dense and
 sparse, on the three workloads, every mode combination, ragged shapes, far
 and invalid flows, multi-crossing rows, N above 32, threshold maps, batches,
-overflow, and the exact skip of quiet pixels (zero flow, both end values
-inside the threshold band) at its bound and one unit either side."""
+overflow; and the exact skip of quiet pixels (zero flow, both end values
+inside the threshold band) at its bound and one unit either side and in
+quiet, moving and mixed rows, for the row kernel and both tile shapes (the
+dense tile kernel skips rows whose pixels are all quiet)."""
 import numpy as np
 import pytest
 
@@ -28,9 +30,9 @@ def _lib():
     evsim.load()
 
 
-def rows_parity(seq, mode, what, **kw):
-    g, o = check_parity(seq, mode, what + " (row kernel)", tile_height=ROWS, **kw)
-    assert g["stats"].tile_height == ROWS
+def rows_parity(seq, mode, what, th=ROWS, **kw):
+    g, o = check_parity(seq, mode, what + f" (tile height {th})", tile_height=th, **kw)
+    assert g["stats"].tile_height == th
     return g, o
 
 
@@ -163,11 +165,12 @@ def _plateau(v0, v1, H=8, W=70, F=3):
     return synth.Sequence("plateau", fr, flows, t, 6, 8, 0.2, 0.2)
 
 
+@pytest.mark.parametrize("th", [ROWS, 16, 8])
 @pytest.mark.parametrize("intensity", [evsim.SIM_LOG, evsim.SIM_LINEAR])
 @pytest.mark.parametrize("ref", [evsim.SIM_REF_ACCUM, evsim.SIM_REF_RESET])
 @pytest.mark.parametrize("delta", [-1, 0, 1])
 @pytest.mark.parametrize("mode", MODES)
-def test_quiet_pixel_skip_at_its_bound(intensity, ref, delta, mode):
+def test_quiet_pixel_skip_at_its_bound(intensity, ref, delta, mode, th):
     # zero-flow pixels whose change is the threshold, one unit below or one
     # unit above: the skip must decide exactly as the simulation would
     lut = oracle.lut(oracle.LINEAR if intensity == evsim.SIM_LINEAR else oracle.LOG)
@@ -179,12 +182,13 @@ def test_quiet_pixel_skip_at_its_bound(intensity, ref, delta, mode):
         cp, cn = (D + delta, big) if rising else (big, D + delta)
         # activity threshold 0: every pixel is active, so the skip decides alone
         rows_parity(s, mode, f"skip bound {delta:+d} ({'rising' if rising else 'falling'})",
-                    intensity=intensity, ref_mode=ref, use_maps=False, c_pos_q16=cp,
+                    th=th, intensity=intensity, ref_mode=ref, use_maps=False, c_pos_q16=cp,
                     c_neg_q16=cn, c_act_q16=0)
 
 
+@pytest.mark.parametrize("th", [ROWS, 16, 8])
 @pytest.mark.parametrize("mode", MODES)
-def test_quiet_moving_and_mixed_rows(mode):
+def test_quiet_moving_and_mixed_rows(mode, th):
     # static rows (skipped), rows with one moving pixel, rows half static
     rng = np.random.default_rng(3)
     H, W, F = 24, 200, 6
@@ -195,10 +199,13 @@ def test_quiet_moving_and_mixed_rows(mode):
         flows[i, 8:12] = (3.0, 0.0)
         fr[i, 16, 100:] = np.roll(fr[i - 1, 16, 100:], 2)    # half a row moving
         flows[i, 16, 100:] = (2.0, 0.0)
-        fr[i, 20, 7] = (fr[i - 1, 20, 7] + 60) % 256          # one pixel changing in place
+        fr[i, 20, 7] = (int(fr[i - 1, 20, 7]) + 60) % 256     # one pixel changing in place
     t = np.arange(F, dtype=np.int64) * 16_667
     seq = synth.Sequence("mixed", fr, flows, t, 10, 10, 0.15, 0.15)
-    g, _ = rows_parity(seq, mode, "quiet, moving and mixed rows", use_maps=False)
+    g, _ = rows_parity(seq, mode, "quiet, moving and mixed rows", th=th, use_maps=False)
+    # a second batch after a batch of quiet frames (the kept halo is rebuilt)
+    g2 = gpu_run(seq, mode, use_maps=False, batch=3, tile_height=th)
+    assert_same_events(g2["events"], g["events"], "quiet rows across batches")
     assert len(g["events"]) > 0
 
 
