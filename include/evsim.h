@@ -609,6 +609,22 @@ typedef struct {
  * Uses the current device; allocates and frees all state itself. */
 int sim_serve_run(const sim_serve_config* cfg, sim_serve_result* res);
 
+/* Diagnostic of failure detection (the paper has no counterpart): runs one
+ * of the library's bounded device-side waits on the current device with a
+ * poll limit of spin_limit (1 .. 2^22; the kernels use 2^22):
+ *   which = 0: the order kernel's single-pass scan waiting for its
+ *              predecessor chunk's prefix (look-back);
+ *   which = 1: a group tile waiting for the tile's earlier frames.
+ * publish = 1 prepares the awaited word as published (the wait ends at
+ * once), 0 leaves it unpublished: the wait must give up after spin_limit
+ * polls and return, leaving SIM_ERR_DEVICE_TIMEOUT in the stream's error
+ * word instead of hanging the GPU.  *device_status receives that word
+ * (SIM_OK or SIM_ERR_DEVICE_TIMEOUT).  Allocates and frees a few bytes of
+ * device memory; synchronises the device.  Returns SIM_OK, SIM_ERR_ARG,
+ * SIM_ERR_CUDA or SIM_ERR_NO_DEVICE. */
+int sim_selftest_bounded_wait(int32_t which, int32_t publish, int32_t spin_limit,
+                              int32_t* device_status);
+
 /* ---- optical flow on the device -------------------------------------------
  * Pyramidal Lucas-Kanade flow between two consecutive frames: the flow the
  * paper's sparse and difference simulators use (Sec. III-B: the selected

@@ -36,7 +36,9 @@ constexpr unsigned long long LB_AGG = 1ull << 30;
 constexpr unsigned long long LB_INC = 2ull << 30;
 constexpr unsigned long long LB_VALUE = (1ull << 30) - 1;
 constexpr int MAX_EVENTS = (1 << 30) - 2;  // per batch (and event buffer capacity)
-// Bounded spin: polls before a look-back gives up and flags a timeout.
+// Bounded spin: polls before a look-back (or a tile's wait for its earlier
+// frames) gives up and flags a timeout; SimParams.spin_limit overrides it
+// (0: this default).
 constexpr int SPIN_LIMIT = 1 << 22;
 
 // Device-resident control block of one stream.  Fields marked "committed"
@@ -137,6 +139,7 @@ struct SimParams {
   unsigned long long* order_status;
   Ev* events;
   long long event_cap;
+  int spin_limit;               // polls of a bounded device wait (0: SPIN_LIMIT)
   unsigned char* segflag;       // row kernel: per (frame, row, 64-column unit) 1 when the
                                 // unit-frame's segments are written, 0 when it emitted
                                 // nothing and wrote none; null: every segment is written

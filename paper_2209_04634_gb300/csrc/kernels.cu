@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "../../include/evsim.h"
@@ -521,7 +522,8 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
     ex += cnts[u];
   }
   if (tid < 32) {
-    const long long ex0 = lookback_warp(p.order_status, c, b.serial, total, &ctl->err);
+    const long long ex0 = lookback_warp(p.order_status, c, b.serial, total, &ctl->err,
+                                        p.spin_limit > 0 ? p.spin_limit : SPIN_LIMIT);
     if (tid == 0) o.prefix = ex0;
   }
   __syncthreads();
@@ -1061,4 +1063,64 @@ cudaError_t launch_drain(const GroupArg& g, const DrainArg& d, int grid, cudaStr
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Diagnostic of the bounded device waits (sim_selftest_bounded_wait): one
+// warp runs the order kernel's look-back for chunk 1 (which = 0) or a group
+// tile's wait for its earlier frames (which = 1) on words the host prepared;
+// when the awaited word is never published the wait gives up after
+// p.spin_limit polls and leaves SIM_ERR_DEVICE_TIMEOUT in the control block.
+
+__global__ void k_selftest_wait(SimParams p, int which, unsigned epoch) {
+  if (which == 0) {
+    lookback_warp(p.order_status, 1, epoch, 5, &p.ctl->err, p.spin_limit);
+  } else if (threadIdx.x == 0) {
+    wait_tile(p, 0, ((unsigned long long)epoch << 32) | 1u);
+  }
+}
+
 }  // namespace evsim
+
+extern "C" int sim_selftest_bounded_wait(int32_t which, int32_t publish, int32_t spin_limit,
+                                         int32_t* device_status) {
+  using namespace evsim;
+  if (!device_status || (which != 0 && which != 1) || (publish != 0 && publish != 1) ||
+      spin_limit < 1 || spin_limit > SPIN_LIMIT)
+    return SIM_ERR_ARG;
+  *device_status = SIM_OK;
+  struct Words {
+    Ctl ctl;
+    unsigned long long status[2];
+    unsigned long long tdone[1];
+  };
+  Words h;
+  std::memset(&h, 0, sizeof(h));
+  const unsigned epoch = 3;
+  if (publish) {
+    h.status[0] = ((unsigned long long)epoch << 32) | LB_INC | 7ull;
+    h.tdone[0] = ((unsigned long long)epoch << 32) | 1ull;
+  }
+  Words* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(Words));
+  if (e == cudaSuccess) e = cudaMemcpy(d, &h, sizeof(Words), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    SimParams p{};
+    p.ctl = &d->ctl;
+    p.order_status = d->status;
+    p.tdone = d->tdone;
+    p.spin_limit = spin_limit;
+    k_selftest_wait<<<1, 32>>>(p, which, epoch);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(Words), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    note_cuda_error(e);
+    return e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
+                   e == cudaErrorNoKernelImageForDevice
+               ? SIM_ERR_NO_DEVICE
+               : SIM_ERR_CUDA;
+  }
+  *device_status = h.ctl.err;
+  return SIM_OK;
+}

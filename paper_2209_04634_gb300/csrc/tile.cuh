@@ -206,7 +206,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // chunk c's inclusive prefix and returns its exclusive prefix (all lanes).
 // Values saturate at LB_VALUE, which callers treat as an overflow.
 __device__ long long lookback_warp(unsigned long long* status, int c, unsigned epoch,
-                                   long long agg, int* err) {
+                                   long long agg, int* err, int limit = SPIN_LIMIT) {
   const int lane = threadIdx.x & 31;
   const unsigned long long hi = (unsigned long long)epoch << 32;
   if (agg > (long long)LB_VALUE) agg = LB_VALUE;
@@ -248,7 +248,7 @@ __device__ long long lookback_warp(unsigned long long* status, int c, unsigned e
       j -= 32;
       continue;
     }
-    if (++spins > SPIN_LIMIT) {
+    if (++spins > limit) {
       if (lane == 0) atomicCAS(err, 0, SIM_ERR_DEVICE_TIMEOUT);
       break;
     }
@@ -864,8 +864,9 @@ __device__ __forceinline__ void sparse_substeps(const int* swk, int N, unsigned 
 // or after SPIN_LIMIT polls (then flags a timeout).
 __device__ __forceinline__ void wait_tile(const SimParams& p, int tile, unsigned long long want) {
   int spins = 0;
+  const int limit = p.spin_limit > 0 ? p.spin_limit : SPIN_LIMIT;
   while (ld_volatile(&p.tdone[tile]) < want) {
-    if (++spins > SPIN_LIMIT) {
+    if (++spins > limit) {
       atomicCAS(&p.ctl->err, 0, SIM_ERR_DEVICE_TIMEOUT);
       break;
     }

@@ -157,6 +157,7 @@ SIGNATURES = [
     ("simb_get_stats", ctypes.c_int, [_VP, ctypes.POINTER(simb_stats)]),
     ("simb_destroy", ctypes.c_int, [_VP]),
     ("sim_serve_run", ctypes.c_int, [_VP, _VP]),
+    ("sim_selftest_bounded_wait", ctypes.c_int, [_I32, _I32, _I32, ctypes.POINTER(_I32)]),
     ("sim_flow_config_default", ctypes.c_int, [ctypes.POINTER(sim_flow_config), _I32, _I32]),
     ("sim_flow_create", ctypes.c_int, [ctypes.POINTER(sim_flow_config), ctypes.POINTER(_VP)]),
     ("sim_flow_compute", ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _VP]),
