@@ -485,8 +485,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   chk(dalloc(&s->d_staging, z.stage));
   chk(dalloc(&s->d_events, cap));
   chk(dalloc(&s->d_seg, seg_cap));
-  // segment flags (row kernel; dense tile kernel with substep times)
-  if (th == SIM_TILE_ROWS || (c.mode == SIM_DENSE && !xtime))
+  // segment flags (row kernel; tile kernel with substep times)
+  if (th == SIM_TILE_ROWS || (c.mode != SIM_DIFF && !xtime))
     chk(dalloc(&s->d_segflag, (size_t)s->bmax * s->segs_per_k));
   chk(dalloc(&s->d_tdone, (size_t)s->tiles_x * s->tiles_y));
   chk(dalloc(&s->d_order_status, ochunks));

@@ -1497,7 +1497,10 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     // through the dense loop (inactive pixels masked, their reference kept):
     // cheaper per pixel than compaction, per-slot records and mask atomics
     // (per-crossing times: always, their rows are published by the dense loop)
-    const bool dsw = SPARSE && (XT || 8 * A >= 3 * TP);
+    // with segment flags (substep-time streams) always: rows without a
+    // pixel to simulate are then skipped whole, which beats compaction on
+    // both sparse workloads measured
+    const bool dsw = SPARSE && (XT || 8 * A >= 3 * TP || p.segflag != nullptr);
 
     // 2. the simulated pixels of this thread and their (staged) flow; the
     // tile's reach
@@ -1541,15 +1544,16 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         mfy = max(mfy, (unsigned)abs(Fy[q]));
       }
     }
-    // dense, substep times, segment flags on: a pixel is quiet when its flow
-    // is zero and both end values lie strictly inside its threshold band
+    // substep times, segment flags on (dense, and sparse in the dense row
+    // mapping): a simulated pixel is quiet when its flow is zero and both end
+    // values lie strictly inside its threshold band
     // (reset mode: its change is within both thresholds).  With zero flow the
     // interpolated values lie between the end values (every Q12 blend stays
     // between its operands), so a quiet pixel emits nothing and keeps R; a
     // row of quiet pixels skips its substeps and writes a flag instead of its
     // segments, and a tile without a busy row builds no halo.
     bool quiet = false;
-    if (!SPARSE && !XT && p.segflag) {
+    if (!XT && p.segflag) {  // sparse: inactive pixels count as quiet
       quiet = true;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -1643,6 +1647,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 #undef EVSIM_XT
       }
     } else if (SPARSE && dsw && !(fast && N <= 32)) {
+      if (p.segflag && ty0 + warp < H && lane == 0)  // every row simulated
+        p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 1;
       if (fast)
         tile_substeps<RESET, WIDE, true, true, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
                                                     lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
@@ -1652,8 +1658,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
                                                      segf, lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
                                                      &s_stage[warp]);
     } else if ((!SPARSE || dsw) && fast) {
-      const bool skip = !SPARSE && p.segflag && __all_sync(FULL, quiet);
-      if (!SPARSE && p.segflag && ty0 + warp < H && lane == 0)
+      const bool skip = p.segflag && __all_sync(FULL, quiet);
+      if (p.segflag && ty0 + warp < H && lane == 0)
         p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] =
             skip ? 0 : 1;
       if (ty0 + warp < H && !skip) {  // warp-uniform: rows below the image publish nothing

@@ -1,13 +1,14 @@
 """Checkpoint and restore of a stream (sim_get_state / sim_set_state): a
 stream saved after some frames and restored into a fresh handle of the same
 configuration continues bit-exactly - the events of the two halves are the
-events of the uninterrupted run, and the reference ends equal."""
+CPU oracle's events of the whole sequence (and those of the uninterrupted
+GPU run), and the reference ends equal to the oracle's."""
 import numpy as np
 import pytest
 
 from paper_2209_04634_gb300 import build, evsim, synth
 
-from .helpers import assert_same_events, gpu_run
+from .helpers import assert_same_events, gpu_run, oracle_run
 
 torch = pytest.importorskip("torch")
 
@@ -48,6 +49,7 @@ def test_restored_stream_continues_bit_exactly(mode, ref, maps, split):
     frames = torch.from_numpy(seq.frames).cuda()
     flows = torch.from_numpy(seq.flows).cuda()
     full = gpu_run(seq, mode, ref_mode=ref, use_maps=maps)
+    want = oracle_run(seq, mode, ref_mode=ref, use_maps=maps)
     a = evsim.simulator_for(seq, mode, **_options(seq, mode, ref, maps))
     ev_a = _push(a, seq, frames, flows, 0, split + 1)
     state = a.get_state()
@@ -55,12 +57,15 @@ def test_restored_stream_continues_bit_exactly(mode, ref, maps, split):
     b = evsim.simulator_for(seq, mode, **_options(seq, mode, ref, maps))
     b.set_state(state)
     ev_b = _push(b, seq, frames, flows, split + 1, seq.frames.shape[0])
-    assert_same_events(np.concatenate([ev_a, ev_b]), full["events"], f"split after {split}")
+    spliced = np.concatenate([ev_a, ev_b])
+    assert len(want["events"]) > 0
+    assert_same_events(spliced, want["events"], f"split after {split} vs the oracle")
+    assert_same_events(spliced, full["events"], f"split after {split} vs the GPU run")
     st = b.stats()
     assert st.frames_committed == seq.frames.shape[0]
     assert st.pixel_substeps == full["stats"].pixel_substeps
     if ref == evsim.SIM_REF_ACCUM and mode != evsim.SIM_DIFF:
-        assert np.array_equal(b.reference(), full["R"])
+        assert np.array_equal(b.reference(), want["R"])
     b.close()
 
 
@@ -73,7 +78,7 @@ def test_state_of_a_fresh_handle_and_mismatched_restores():
     frames = torch.from_numpy(seq.frames).cuda()
     flows = torch.from_numpy(seq.flows).cuda()
     ev = _push(b, seq, frames, flows, 0, 4)
-    assert_same_events(ev, gpu_run(seq, evsim.SIM_DENSE)["events"], "fresh state")
+    assert_same_events(ev, oracle_run(seq, evsim.SIM_DENSE)["events"], "fresh state")
     c = evsim.simulator_for(seq, evsim.SIM_SPARSE)
     with pytest.raises(evsim.SimError):
         c.set_state(empty)  # another mode
