@@ -71,6 +71,9 @@ def parse():
                     help="skip the paper-mode, accumulate, difference and crossing-time objects")
     ap.add_argument("--no-flow", action="store_true",
                     help="skip the device optical-flow object")
+    ap.add_argument("--profile-flow", type=int, default=0,
+                    help="profiling: only compute the device flow of this many frame pairs of "
+                         "the 640x480 workload, then exit")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the 640x480 and 240x180 workload objects")
     ap.add_argument("--only", default="",
@@ -460,6 +463,18 @@ def run_ours(args, ws, rank, local):
     from paper_2209_04634_gb300 import build, evsim, synth
     build.build()
     evsim.load()
+    if args.profile_flow:
+        s = synth.warped_texture(seed=C2_SEED, frames=args.profile_flow + 1)
+        fr = torch.from_numpy(s.frames).cuda()
+        out = torch.empty((s.height, s.width, 2), dtype=torch.float32, device="cuda")
+        fl = evsim.Flow(s.width, s.height)
+        for i in range(1, args.profile_flow + 1):
+            fl.compute(fr[i - 1], fr[i], out)
+        torch.cuda.synchronize()
+        fl.close()
+        print(json.dumps({"profile_flow": args.profile_flow, "width": s.width,
+                          "height": s.height}))
+        return 0
 
     seq = synth.moving_rectangles(seed=stream_seed(rank, C3_SEED), frames=args.frames)
     F, H, W = seq.frames.shape[:3]
@@ -1063,9 +1078,12 @@ def run_serving(args):
 
 
 def run_e2e(args, ps, work_step):
-    """Same metric through the C ABI with host buffers: frames and flows from
-    pinned host memory copied in by the library, events read back to pinned
-    host memory, every step."""
+    """Same metric through the C ABI with host buffers in pinned memory, every
+    step: the step's frames and flows cross from the host (read in place by
+    the kernels through their device mapping, the library's default for
+    pinned buffers; and, as `staged`, copied into device staging chunk by
+    chunk, overlapping the kernels) and the events are read back to pinned
+    host memory."""
     import torch
 
     from paper_2209_04634_gb300 import evsim
@@ -1075,34 +1093,47 @@ def run_e2e(args, ps, work_step):
     cap = ps.cap
     out_h = torch.empty(cap * 8, dtype=torch.uint8).pin_memory()
     fr_np, fl_np, out_np = frames_h.numpy(), flows_h.numpy(), out_h.numpy().view(evsim.EVENT_DTYPE)
-
-    def step():
-        d2h = 0
-        for sim in ps.sims.values():
-            sim.reset()
-            sim.push_many(fr_np, fl_np, seq.t_us)
-            n, rc = sim.pop_into(out_np, cap)
-            assert rc == evsim.SIM_OK, rc
-            d2h += n * 8
-        return d2h
-
-    for _ in range(2):
-        step()
-    steps = max(3, args.steps // 4)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(ps.stream)
-    d2h = 0
-    for _ in range(steps):
-        d2h += step()
-    e1.record(ps.stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
     h2d = len(ps.sims) * (seq.frames.nbytes + seq.flows[1:].nbytes)
-    return {"value": work_step * steps / (ms / 1e3) / 1e9, "unit": METRIC,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // steps),
-            "steps": steps, "ms_per_step": ms / steps}
+
+    def measure(sims):
+        def step():
+            d2h = 0
+            for sim in sims:
+                sim.reset()
+                sim.push_many(fr_np, fl_np, seq.t_us)
+                n, rc = sim.pop_into(out_np, cap)
+                assert rc == evsim.SIM_OK, rc
+                d2h += n * 8
+            return d2h
+
+        for _ in range(2):
+            step()
+        steps = max(3, args.steps // 4)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ps.stream)
+        d2h = 0
+        for _ in range(steps):
+            d2h += step()
+        e1.record(ps.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"value": work_step * steps / (ms / 1e3) / 1e9, "unit": METRIC,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // steps),
+                "steps": steps, "ms_per_step": ms / steps}
+
+    line = measure(list(ps.sims.values()))
+    line["host_inputs"] = "pinned, read in place by the kernels"
+    staged = [evsim.simulator_for(seq, m, event_capacity=cap, stream=ps.stream,
+                                  tile_height=ps.tune[PASS_NAMES[m]]["tile_height"],
+                                  host_inputs=evsim.SIM_HOST_STAGE)
+              for m in (0, 1) if PASS_NAMES[m] in ps.sims]
+    line["staged"] = measure(staged)
+    for sim in staged:
+        sim.close()
+    return line
+
 
 def main():
     args = parse()

@@ -370,6 +370,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
       c.tile_height != 16 && c.tile_height != SIM_TILE_ROWS)
     return SIM_ERR_ARG;
   if (c.event_time != SIM_TIME_SUBSTEP && c.event_time != SIM_TIME_CROSSING) return SIM_ERR_ARG;
+  if (c.host_inputs != SIM_HOST_AUTO && c.host_inputs != SIM_HOST_STAGE) return SIM_ERR_ARG;
   const bool xtime = c.event_time == SIM_TIME_CROSSING;
   if (xtime && c.mode == SIM_DIFF) return SIM_ERR_ARG;  // no crossings: no reference
 
@@ -548,6 +549,38 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
   }
   cudaError_t e = cudaSuccess;
   std::vector<evsim::FrameDesc> desc;
+  // Pinned host buffers are read in place through their device mapping
+  // (SIM_HOST_AUTO): the kernels pull the bytes over the host link as they
+  // stage each frame, so no copy precedes the kernels.
+  std::vector<const void*> mfr;
+  std::vector<const float*> mfl;
+  if (mem == SIM_HOST && s->cfg.host_inputs == SIM_HOST_AUTO && i0 < count) {
+    bool mapped = true;
+    mfr.assign(count, nullptr);
+    mfl.assign(count, nullptr);
+    for (int i = i0; i < count && mapped; ++i) {
+      void* dp[2] = {nullptr, nullptr};
+      const void* hp[2] = {frames[i], flows[i]};
+      for (int k = 0; k < 2 && mapped; ++k) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, hp[k]) != cudaSuccess) {
+          cudaGetLastError();  // an unregistered pointer is not an error here
+          mapped = false;
+        } else if (a.type != cudaMemoryTypeHost || !a.devicePointer) {
+          mapped = false;
+        } else {
+          dp[k] = a.devicePointer;
+        }
+      }
+      mfr[i] = dp[0];
+      mfl[i] = (const float*)dp[1];
+    }
+    if (mapped) {
+      frames = mfr.data();
+      flows = mfl.data();
+      mem = SIM_DEVICE;
+    }
+  }
   // Host frames go through device staging in chunks of m frames (about an
   // eighth of the call, at least 4, at most a device batch), each chunk a
   // device batch of its own: chunk j + 1 is copied on the copy stream into

@@ -33,6 +33,7 @@ SIM_HOST, SIM_DEVICE = 0, 1
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 SIM_MAX_BATCH = 1024
 SIM_TILE_AUTO, SIM_TILE_TUNE, SIM_TILE_ROWS = 0, -1, 1
+SIM_HOST_AUTO, SIM_HOST_STAGE = 0, 1
 SIM_TIME_SUBSTEP, SIM_TIME_CROSSING = 0, 1
 SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
 KERNEL_NAMES = ["init", "flowmax", "dense", "mask", "sparse", "order", "copy"]
@@ -51,6 +52,7 @@ class sim_config(ctypes.Structure):
         ("c_pos_map", ctypes.c_void_p), ("c_neg_map", ctypes.c_void_p),
         ("event_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
         ("tile_height", ctypes.c_int32), ("event_time", ctypes.c_int32),
+        ("host_inputs", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -241,7 +243,7 @@ class Simulator:
                  c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
                  c_pos_map=None, c_neg_map=None, event_capacity: int = 0, stream=None,
                  max_batch: int = 0, tile_height: int = SIM_TILE_AUTO,
-                 event_time: int = SIM_TIME_SUBSTEP):
+                 event_time: int = SIM_TIME_SUBSTEP, host_inputs: int = SIM_HOST_AUTO):
         lib = load()
         cfg = sim_config()
         check(lib.sim_config_default(ctypes.byref(cfg), width, height), "sim_config_default")
@@ -265,6 +267,7 @@ class Simulator:
         cfg.max_batch = max_batch
         cfg.tile_height = tile_height
         cfg.event_time = event_time
+        cfg.host_inputs = host_inputs
         if stream is not None:
             handle = int(getattr(stream, "cuda_stream", stream))
             # handle 0 is the legacy default stream (torch's default stream):
