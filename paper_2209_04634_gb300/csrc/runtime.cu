@@ -290,6 +290,8 @@ cudaError_t enqueue_batch(sim_t* s, int n) {
     }
     if (s->tile_h == SIM_TILE_ROWS)
       e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_rows(p, b, s->stream); });
+    else if (p.segflag && !p.xtime)  // the dense tile kernel with activity masks
+      e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_dense(p, b, s->stream); });
     else
       e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, b, s->stream); });
     if (e == cudaSuccess && s->block_order == 2 && s->tile_h != SIM_TILE_ROWS)

@@ -1376,6 +1376,10 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   const int tx0 = tcx * TW, ty0 = tcy * TH;
   const int W = p.W, H = p.H, count = b.count;
   const bool adaptive = p.n_fixed <= 0;
+  // a sparse stream with segment flags runs in this dense instance: its
+  // pixels' activity masks the dense row loop, rows without a pixel to
+  // simulate are skipped (no compaction, the reference stays in registers)
+  const bool spm = !SPARSE && p.mode == SIM_SPARSE;
 
   if (tid < 256) L.slut[tid] = p.lut[tid];
   const int sel = ctl->sel;
@@ -1455,19 +1459,22 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     const unsigned mN = s_mN[par];
     Seg* segf = p.seg + (long long)fi * nmax * p.segs_per_k + (long long)ty0 * p.tiles_x + tcx;
 
-    // 1. the pixels to simulate (the previous and current bytes are staged)
+    // 1. the pixels to simulate (the previous and current bytes are staged);
+    // spm: a sparse stream run by this dense instance - each pixel's
+    // activity is tested in the dense mapping and masks its substeps
     int A = 0;
     int sel_flag[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int lx = own[q] & (TW - 1), ly = own[q] / TW;
       bool a = inimg[q];
-      if (inimg[q] && (SPARSE || fi == count - 1)) {
+      if (inimg[q] && (SPARSE || spm || fi == count - 1)) {
         const int vc = raw_luma(rawc, ch, ly + HMAX, lx + HMAX);
         if (fi == count - 1) ringn[(long long)(ty0 + ly) * W + tx0 + lx] = (unsigned char)vc;
-        if (SPARSE) {
+        if (SPARSE || spm) {
           const int vp = raw_luma(rawp, chp, ly + HMAX, lx + HMAX);
-          const int cp = MAPS ? (int)L.sCp[own[q]] : p.cp, cn = MAPS ? (int)L.sCn[own[q]] : p.cn;
+          const int cp = MAPS ? (SPARSE ? (int)L.sCp[own[q]] : Cpd[q]) : p.cp;
+          const int cn = MAPS ? (SPARSE ? (int)L.sCn[own[q]] : Cnd[q]) : p.cn;
           a = abs(L.slut[vc] - L.slut[vp]) >= activity_threshold(p, cp, cn);
         }
       }
@@ -1491,16 +1498,20 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     } else {
       A = TP;
     }
-    act_sum += A;
-    act_n += (long long)A * N;
+    if (SPARSE) {
+      act_sum += A;
+      act_n += (long long)A * N;
+    } else if (spm) {  // per warp; lane 0 adds the warp's count at the end
+      const int na = __popc(__ballot_sync(FULL, sel_flag[0] != 0)) +
+                     __popc(__ballot_sync(FULL, sel_flag[1] != 0));
+      act_sum += na;
+      act_n += (long long)na * N;
+    }
     // sparse tiles with at least 3/8 of their pixels active run the frame
     // through the dense loop (inactive pixels masked, their reference kept):
     // cheaper per pixel than compaction, per-slot records and mask atomics
     // (per-crossing times: always, their rows are published by the dense loop)
-    // with segment flags (substep-time streams) always: rows without a
-    // pixel to simulate are then skipped whole, which beats compaction on
-    // both sparse workloads measured
-    const bool dsw = SPARSE && (XT || 8 * A >= 3 * TP || p.segflag != nullptr);
+    const bool dsw = SPARSE && (XT || 8 * A >= 3 * TP);
 
     // 2. the simulated pixels of this thread and their (staged) flow; the
     // tile's reach
@@ -1521,7 +1532,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         slot = act[q] ? L.sslot[j] : 0;
         nk_at[q] = j;
       } else {
-        act[q] = inimg[q];
+        act[q] = sel_flag[q] != 0;  // dense: in the image; spm: active
         slot = own[q];
         nk_at[q] = own[q];
       }
@@ -1664,7 +1675,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
             skip ? 0 : 1;
       if (ty0 + warp < H && !skip) {  // warp-uniform: rows below the image publish nothing
         // the row's 64 pixels are in the image (and, sparse, all simulated)
-        const bool fullt = !SPARSE && tx0 + TW <= W;
+        const bool fullt = !SPARSE && !spm && tx0 + TW <= W;
 #define EVSIM_DENSE(FT, MK)                                                                    \
   dense_substeps<RESET, WIDE, FT, MK>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp, b0, \
                                       b1, segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy,  \
@@ -1704,7 +1715,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       for (int q = 0; q < 2; ++q) {
         if (SPARSE) {
           if (act[q]) L.sR[lx[q] + ly[q] * TW] = R[q];
-        } else {
+        } else if (act[q]) {  // spm: inactive pixels keep their reference
           Rd[q] = R[q];
         }
       }
@@ -1788,6 +1799,10 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   }
   clamps = __reduce_add_sync(FULL, clamps);
   if (lane == 0 && clamps) atomicAdd(&ctl->clamped, (unsigned long long)clamps);
+  if (spm && lane == 0 && act_sum) {
+    atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)act_sum);
+    atomicAdd((unsigned long long*)&ctl->active_n, (unsigned long long)act_n);
+  }
   if (SPARSE && tid == 0 && act_sum) {
     atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)act_sum);
     atomicAdd((unsigned long long*)&ctl->active_n, (unsigned long long)act_n);
