@@ -450,8 +450,9 @@ void orc_accumulate(const orc_event* ev, int64_t n, int32_t W, int32_t H, int64_
  *     bilinear of the simulator (Q16 position, 12-bit fractions, blends
  *     rounded half up); b = sum of (Ix It, Iy It) (int64); the update is
  *     -2 G^-1 b px (the factor 2: Ix is twice the derivative), evaluated
- *     in IEEE double in the order written below and rounded to Q16 (ties to
- *     even); v += update;
+ *     in IEEE double in the order written below - the scale -2^17 / det G
+ *     once per pixel and level, then each component's numerator times it -
+ *     and rounded to Q16 (ties to even); v += update;
  *   - coarse to fine: the guess g of a pixel of level l is twice the flow
  *     of its parent (x / 2, y / 2) at level l + 1 (zero at the top);
  *     the flow of level 0 is the output, Q16 px, clamped to +-1024 px.
@@ -562,6 +563,7 @@ int orc_flow_lk(const orc_lk_config* c, int32_t W, int32_t H, int32_t channels,
           const double lmin = (tr - disc) * 0.5;
           int64_t vx = 0, vy = 0;
           if (lmin / area >= c->min_eig && det > 0.0) {
+            const double scale = -131072.0 / det;
             for (int k = 0; k < c->iterations; ++k) {
               int64_t bx = 0, by = 0;
               for (int j = -r; j <= r; ++j)
@@ -584,8 +586,8 @@ int orc_flow_lk(const orc_lk_config* c, int32_t W, int32_t H, int32_t channels,
               const double ex = (double)bx, ey = (double)by;
               const double nx = d * ex - b * ey;
               const double ny = a * ey - b * ex;
-              vx += (int64_t)nearbyint((-131072.0 * nx) / det);
-              vy += (int64_t)nearbyint((-131072.0 * ny) / det);
+              vx += (int64_t)nearbyint(nx * scale);
+              vy += (int64_t)nearbyint(ny * scale);
               if (vx > lim) vx = lim;
               if (vx < -lim) vx = -lim;
               if (vy > lim) vy = lim;

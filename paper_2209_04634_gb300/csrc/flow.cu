@@ -22,7 +22,8 @@
 //   - per iteration: It(q) = J(q + g + v) - I(q) with J sampled by the
 //     clamped bilinear of the simulator (Q16 position, 12-bit fractions,
 //     blends rounded half up); the update -2 G^-1 b, b = sums of (Ix It,
-//     Iy It), rounded to Q16; v is clamped to +-1024 px;
+//     Iy It), as each numerator times -2^17 / det G (one division per pixel
+//     and level), rounded to Q16; v is clamped to +-1024 px;
 //   - the guess of a level-l pixel is twice the flow of its parent
 //     (x / 2, y / 2) at level l + 1; the level-0 flow, Q16 px, is written
 //     as float pixels.
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(LBX * LBY) k_lk_level(LevelArg a) {
   const long long lim = 1024LL * 65536;
   long long vx = 0, vy = 0;
   if (__ddiv_rn(lmin, a.area) >= a.min_eig && det > 0.0) {
+    const double scale = __ddiv_rn(-131072.0, det);
     for (int k = 0; k < a.iters; ++k) {
       long long bxs = 0, bys = 0;
       for (int j = 0; j <= 2 * r; ++j) {
@@ -171,8 +173,8 @@ __global__ void __launch_bounds__(LBX * LBY) k_lk_level(LevelArg a) {
       const double ex = (double)bxs, ey = (double)bys;
       const double nx = __dsub_rn(__dmul_rn(Dd, ex), __dmul_rn(B, ey));
       const double ny = __dsub_rn(__dmul_rn(A, ey), __dmul_rn(B, ex));
-      vx += __double2ll_rn(__ddiv_rn(__dmul_rn(-131072.0, nx), det));
-      vy += __double2ll_rn(__ddiv_rn(__dmul_rn(-131072.0, ny), det));
+      vx += __double2ll_rn(__dmul_rn(nx, scale));
+      vy += __double2ll_rn(__dmul_rn(ny, scale));
       vx = vx > lim ? lim : (vx < -lim ? -lim : vx);
       vy = vy > lim ? lim : (vy < -lim ? -lim : vy);
     }

@@ -119,14 +119,12 @@ MUTATIONS = {
         "const int64_t ix = (int64_t)lk_at(Il, w, h, qx - 1, qy) - lk_at(Il, w, h, qx + 1, qy);"),
     "lk_guess_not_doubled": [("gx = 2 * Dp[2 * pp];", "gx = Dp[2 * pp];"),
                              ("gy = 2 * Dp[2 * pp + 1];", "gy = Dp[2 * pp + 1];")],
-    "lk_update_sign": [("vx += (int64_t)nearbyint((-131072.0 * nx) / det);",
-                        "vx += (int64_t)nearbyint((131072.0 * nx) / det);"),
-                       ("vy += (int64_t)nearbyint((-131072.0 * ny) / det);",
-                        "vy += (int64_t)nearbyint((131072.0 * ny) / det);")],
-    "lk_components_swapped": [("vx += (int64_t)nearbyint((-131072.0 * nx) / det);",
-                               "vx += (int64_t)nearbyint((-131072.0 * ny) / det);"),
-                              ("vy += (int64_t)nearbyint((-131072.0 * ny) / det);",
-                               "vy += (int64_t)nearbyint((-131072.0 * nx) / det);")],
+    "lk_update_sign": ("const double scale = -131072.0 / det;",
+                       "const double scale = 131072.0 / det;"),
+    "lk_components_swapped": [("vx += (int64_t)nearbyint(nx * scale);",
+                               "vx += (int64_t)nearbyint(ny * scale);"),
+                              ("vy += (int64_t)nearbyint(ny * scale);",
+                               "vy += (int64_t)nearbyint(nx * scale);")],
     "lk_window_short_by_one": ("          for (int j = -r; j <= r; ++j)\n            for (int i = -r; i <= r; ++i) {",
                                "          for (int j = -r; j < r; ++j)\n            for (int i = -r; i <= r; ++i) {"),
     "lk_temporal_difference_sign": ("const int64_t it = jv - lk_at(Il, w, h, qx, qy);",
