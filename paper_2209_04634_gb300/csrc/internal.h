@@ -80,6 +80,10 @@ struct BatchArg {
   const FrameDesc* frames;      // count descriptors (device)
   int count;
   unsigned int serial;          // batch serial: epoch of the look-back words
+  int host_mapped;              // 1: the frames are pinned host memory read in place (the
+                                // batch kernel then stages them with cp.async only, no
+                                // bulk copies)
+  int pad;
 };
 
 struct Ev {  // same layout as sim_event

@@ -663,6 +663,7 @@ __device__ __forceinline__ void load_stream(const GroupArg& g, int s, SimParams&
     sb.frames = g.gs[s].frames;
     sb.count = g.steps[s].count;
     sb.serial = g.steps[s].serial;
+    sb.host_mapped = 1;  // group tiles stage with cp.async
   }
 }
 

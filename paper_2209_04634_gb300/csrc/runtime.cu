@@ -261,12 +261,13 @@ int push_first(sim_t* s, const void* frame, long long pitch, int64_t t_us, int32
 }
 
 // Enqueue one batch whose descriptors are already in d_desc.
-cudaError_t enqueue_batch(sim_t* s, int n) {
+cudaError_t enqueue_batch(sim_t* s, int n, bool host_mapped) {
   const evsim::SimParams p = make_params(s);
   evsim::BatchArg b{};
   b.frames = s->d_desc;
   b.count = n;
   b.serial = ++s->serial;
+  b.host_mapped = host_mapped ? 1 : 0;
   cudaError_t e;
   const bool adaptive = s->cfg.substeps == 0;
   if (s->cfg.mode == SIM_DENSE || s->cfg.mode == SIM_DIFF) {
@@ -372,7 +373,7 @@ int sim_create(const sim_config* cfg, sim_t** out) {
       c.tile_height != 16 && c.tile_height != SIM_TILE_ROWS)
     return SIM_ERR_ARG;
   if (c.event_time != SIM_TIME_SUBSTEP && c.event_time != SIM_TIME_CROSSING) return SIM_ERR_ARG;
-  if (c.host_inputs != SIM_HOST_AUTO && c.host_inputs != SIM_HOST_STAGE) return SIM_ERR_ARG;
+  if (c.host_inputs != SIM_HOST_STAGE && c.host_inputs != SIM_HOST_MAPPED) return SIM_ERR_ARG;
   const bool xtime = c.event_time == SIM_TIME_CROSSING;
   if (xtime && c.mode == SIM_DIFF) return SIM_ERR_ARG;  // no crossings: no reference
 
@@ -551,12 +552,13 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
   }
   cudaError_t e = cudaSuccess;
   std::vector<evsim::FrameDesc> desc;
-  // Pinned host buffers are read in place through their device mapping
-  // (SIM_HOST_AUTO): the kernels pull the bytes over the host link as they
+  // SIM_HOST_MAPPED: pinned host buffers are read in place through their
+  // device mapping - the kernels pull the bytes over the host link as they
   // stage each frame, so no copy precedes the kernels.
   std::vector<const void*> mfr;
   std::vector<const float*> mfl;
-  if (mem == SIM_HOST && s->cfg.host_inputs == SIM_HOST_AUTO && i0 < count) {
+  bool host_mapped = false;
+  if (mem == SIM_HOST && s->cfg.host_inputs == SIM_HOST_MAPPED && i0 < count) {
     bool mapped = true;
     mfr.assign(count, nullptr);
     mfl.assign(count, nullptr);
@@ -581,6 +583,7 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
       frames = mfr.data();
       flows = mfl.data();
       mem = SIM_DEVICE;
+      host_mapped = true;
     }
   }
   // Host frames go through device staging in chunks of m frames (about an
@@ -662,7 +665,7 @@ int sim_push_frames(sim_t* s, int32_t count, const void* const* frames, int64_t 
     }
     e = cudaMemcpyAsync(s->d_desc, desc.data(), n * sizeof(evsim::FrameDesc),
                         cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = enqueue_batch(s, n);
+    if (e == cudaSuccess) e = enqueue_batch(s, n, host_mapped);
     if (e == cudaSuccess && mem == SIM_HOST) e = cudaEventRecord(s->slot_free[slot], s->stream);
     if (e != cudaSuccess) return cuda_rc(e);
     s->t_last = t_us[i0 + n - 1];

@@ -33,7 +33,7 @@ SIM_HOST, SIM_DEVICE = 0, 1
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 SIM_MAX_BATCH = 1024
 SIM_TILE_AUTO, SIM_TILE_TUNE, SIM_TILE_ROWS = 0, -1, 1
-SIM_HOST_AUTO, SIM_HOST_STAGE = 0, 1
+SIM_HOST_STAGE, SIM_HOST_MAPPED = 0, 1
 SIM_TIME_SUBSTEP, SIM_TIME_CROSSING = 0, 1
 SIM_K_INIT, SIM_K_FLOWMAX, SIM_K_DENSE, SIM_K_MASK, SIM_K_SPARSE, SIM_K_ORDER, SIM_K_COPY = range(7)
 KERNEL_NAMES = ["init", "flowmax", "dense", "mask", "sparse", "order", "copy"]
@@ -243,7 +243,7 @@ class Simulator:
                  c_pos_q16: int = 13107, c_neg_q16: int = 13107, c_act_q16: int = -1,
                  c_pos_map=None, c_neg_map=None, event_capacity: int = 0, stream=None,
                  max_batch: int = 0, tile_height: int = SIM_TILE_AUTO,
-                 event_time: int = SIM_TIME_SUBSTEP, host_inputs: int = SIM_HOST_AUTO):
+                 event_time: int = SIM_TIME_SUBSTEP, host_inputs: int = SIM_HOST_STAGE):
         lib = load()
         cfg = sim_config()
         check(lib.sim_config_default(ctypes.byref(cfg), width, height), "sim_config_default")

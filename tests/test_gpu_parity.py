@@ -469,13 +469,13 @@ def test_block_orders_give_the_oracle_events(order, mode, tmp_path):
 @pytest.mark.parametrize("mode", [evsim.SIM_DENSE, evsim.SIM_SPARSE])
 def test_pinned_host_inputs_read_in_place_equal_the_oracle(mode):
     """Host frames and flows in pinned memory are read by the kernels through
-    their device mapping (SIM_HOST_AUTO) or staged (SIM_HOST_STAGE): both give
-    the oracle's events; pageable arrays are staged."""
+    their device mapping (SIM_HOST_MAPPED) or staged (SIM_HOST_STAGE): both
+    give the oracle's events; pageable arrays are staged either way."""
     seq = synth.warped_texture(frames=12, width=200, height=120)
     fr = torch.from_numpy(seq.frames).pin_memory()
     fl = torch.from_numpy(seq.flows).pin_memory()
     o = oracle_run(seq, mode)
-    for how in (evsim.SIM_HOST_AUTO, evsim.SIM_HOST_STAGE):
+    for how in (evsim.SIM_HOST_MAPPED, evsim.SIM_HOST_STAGE):
         for frames, flows in ((fr.numpy(), fl.numpy()), (seq.frames, seq.flows)):
             sim = evsim.simulator_for(seq, mode, host_inputs=how)
             sim.push(frames[0], None, int(seq.t_us[0]))
