@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=50)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=12.0)
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving object (e.g. with --serve-seconds 120) and print it")
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the paper-mode, accumulate, difference and crossing-time objects")
     ap.add_argument("--no-flow", action="store_true",
@@ -463,6 +465,9 @@ def run_ours(args, ws, rank, local):
     from paper_2209_04634_gb300 import build, evsim, synth
     build.build()
     evsim.load()
+    if args.serving_only:
+        print(json.dumps({"serving": run_serving(args)}))
+        return 0
     if args.profile_flow:
         s = synth.warped_texture(seed=C2_SEED, frames=args.profile_flow + 1)
         fr = torch.from_numpy(s.frames).cuda()
@@ -980,9 +985,9 @@ def run_batched(args):
     def caps(s):
         return (32 if s.width * s.height <= 640 * 480 else 24) * s.width * s.height
 
-    def group_run(mode, timed):
+    def group_run(mode, timed, th=0):
         g = evsim.Group(max_streams=len(seqs), frames_per_step=1, hbm_budget_bytes=64 << 30)
-        ids = [g.admit(s.width, s.height, **evsim.seq_options(s, mode=mode,
+        ids = [g.admit(s.width, s.height, **evsim.seq_options(s, mode=mode, tile_height=th,
                                                                event_capacity=caps(s)))
                for s in seqs]
         assert all(i is not None for i in ids)
@@ -1024,7 +1029,23 @@ def run_batched(args):
         return wall, work, ev
 
     out = {"workload": BATCHED_WORKLOAD, "steps": T, "streams": len(seqs),
-           "pixels_per_step": int(sum(s.width * s.height for s in seqs))}
+           "pixels_per_step": int(sum(s.width * s.height for s in seqs)), "autotune": {}}
+    # the library's autotuner on a sample of each member configuration (its
+    # first 6 frames); members admitted with the automatic shape take the
+    # table's tile shape (the row kernel's choice maps to 64 x 16 tiles)
+    sizes = {}
+    for i, s in enumerate(seqs):
+        sizes.setdefault((s.width, s.height), i)
+    for mode, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
+        for (w, h), i in sizes.items():
+            fr, fl, _ = dev[i]
+            th, u16, u8, ur = evsim.autotune_sample(
+                w, h, fr[:U], fl[:U], (np.arange(U) * 50_000).astype(np.int64),
+                **evsim.seq_options(seqs[i], mode=mode, event_capacity=caps(seqs[i])))
+            out["autotune"][f"{name}.{w}x{h}"] = {
+                "choice": "rows" if th == evsim.SIM_TILE_ROWS else f"64x{th}",
+                "member_tiles": "64x16" if th == evsim.SIM_TILE_ROWS else f"64x{th}",
+                "us_per_frame_64x16": u16, "us_per_frame_64x8": u8, "us_per_frame_rows": ur}
     for mode, name in ((evsim.SIM_DENSE, "dense"), (evsim.SIM_SPARSE, "sparse")):
         # parity of the two launch patterns on the same frames
         _w, _wk, _st, ev_g = group_run(mode, False)
@@ -1033,12 +1054,17 @@ def run_batched(args):
                    for a, b in zip(ev_g, ev_s))
         n_events = int(sum(len(a) for a in ev_g))
         gw, work, st, _ = group_run(mode, True)
+        g16, _w16, _st16, _ = group_run(mode, True, th=16)
+        g8, _w8, _st8, _ = group_run(mode, True, th=8)
         sw, work_s, _ = single_run(mode, True)
         assert work == work_s
         out[name] = {
             "group": {"value": work / gw / 1e9, "unit": METRIC, "ms_per_step": gw / T * 1e3,
                       "kernel_launches_per_step": st.kernel_launches / max(1, st.steps),
-                      "graph_launches": st.graph_launches, "tile_classes": st.tile_classes},
+                      "graph_launches": st.graph_launches, "tile_classes": st.tile_classes,
+                      "tiles": "autotuned per member configuration"},
+            "group_all_64x16": {"value": work / g16 / 1e9, "ms_per_step": g16 / T * 1e3},
+            "group_all_64x8": {"value": work / g8 / 1e9, "ms_per_step": g8 / T * 1e3},
             "per_stream": {"value": work / sw / 1e9, "unit": METRIC,
                            "ms_per_step": sw / T * 1e3},
             "speedup": sw / gw,

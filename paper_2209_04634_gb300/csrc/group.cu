@@ -99,8 +99,8 @@ struct simb_s {
 
 namespace {
 
-static_assert(sizeof(GroupTotals) <= 256, "totals fit their slot");
-size_t off_steps() { return 256; }
+static_assert(sizeof(GroupTotals) <= 512, "totals fit their slot");
+size_t off_steps() { return 512; }
 size_t off_act(const simb_t* g) {
   return (off_steps() + sizeof(StreamStep) * g->cfg.max_streams + 255) & ~(size_t)255;
 }
@@ -143,7 +143,8 @@ int rebuild(simb_t* g) {
     const Member* m = g->members[i];
     g->cls_tiles[m->cls] += m->tiles;
     cls_members[m->cls] += 1;
-    g->cls_smem[m->cls] = std::max(g->cls_smem[m->cls], evsim::tile_smem_bytes(m->s->n_max));
+    g->cls_smem[m->cls] =
+        std::max(g->cls_smem[m->cls], evsim::tile_smem_bytes(m->s->n_max, m->s->tile_h));
     g->any_adaptive |= m->adaptive;
     max_chunks += order_chunks(m->s, g->fmax);
     gs[i].p = evsim_rt::make_params(m->s);
@@ -156,8 +157,10 @@ int rebuild(simb_t* g) {
   for (int c = 0; c < evsim::TILE_CLASSES; ++c) {
     g->cls_moff[c] = moff;
     moff += cls_members[c];
-    // persistent tile grid: two blocks per SM (the kernel's residency)
-    g->cls_grid[c] = std::min(g->cls_tiles[c] * g->fmax, 2 * g->sms);
+    // persistent tile grid: the kernel's residency per SM (two 512-thread
+    // blocks of 64 x 16 tiles, four 256-thread blocks of 64 x 8)
+    const int per_sm = (c & evsim::TILE_TH8) ? 4 : 2;
+    g->cls_grid[c] = std::min(g->cls_tiles[c] * g->fmax, per_sm * g->sms);
     if (g->cls_tiles[c]) ++g->n_classes;
   }
   std::vector<int> ids(std::max(n, 1));
@@ -257,11 +260,20 @@ void free_group(simb_t* g) {
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
 }
 
+// A member's configuration: its tile shape is the one asked for (8 or 16),
+// else the autotuner table's choice for its configuration when that is a
+// tile shape, else 64 x 16 (the group's tile kernel has the two tile shapes;
+// the row kernel and block orders do not apply to its ticketed launches).
 sim_config member_config(const simb_t* g, const sim_config& c) {
   sim_config mc = c;
   mc.cuda_stream = g->stream;
   mc.max_batch = g->fmax;
-  mc.tile_height = 16;  // the group's tile kernel has the 64 x 16 shape only
+  int th = 16, order = 0;
+  if (c.tile_height == 8 || c.tile_height == 16)
+    th = c.tile_height;
+  else if (evsim_rt::tuned_tile_height(c, &th, &order) && th != 8 && th != 16)
+    th = 16;
+  mc.tile_height = th;
   return mc;
 }
 

@@ -80,9 +80,7 @@ struct BatchArg {
   const FrameDesc* frames;      // count descriptors (device)
   int count;
   unsigned int serial;          // batch serial: epoch of the look-back words
-  int host_mapped;              // 1: the frames are pinned host memory read in place (the
-                                // batch kernel then stages them with cp.async only, no
-                                // bulk copies)
+  int host_mapped;              // 1: the frames are pinned host memory read in place
   int pad;
 };
 
@@ -152,7 +150,9 @@ struct SimParams {
 // ---- multi-stream step (one launch per kernel for every member of a group)
 constexpr int MAX_GROUP = 1024;  // members of one group
 // Tile kernel classes (template flags); members of one class share a launch.
-enum { TILE_RESET = 1, TILE_MAPS = 2, TILE_WIDE = 4, TILE_SPARSE = 8, TILE_CLASSES = 16 };
+// TILE_TH8: the member's tiles are 64 x 8 (256-thread blocks), else 64 x 16.
+enum { TILE_RESET = 1, TILE_MAPS = 2, TILE_WIDE = 4, TILE_SPARSE = 8, TILE_TH8 = 16,
+       TILE_CLASSES = 32 };
 
 struct GroupStream {            // per member; changes only when members change
   SimParams p;
@@ -220,8 +220,9 @@ struct GroupArg {
   int n;
 };
 
-// Shared-memory bytes of the tile kernel (dense and sparse) for a substep cap.
-size_t tile_smem_bytes(int n_max);
+// Shared-memory bytes of the multi-stream tile kernel (dense and sparse) for a
+// substep cap and a tile height (8 or 16).
+size_t tile_smem_bytes(int n_max, int th);
 
 // Launchers (kernels.cu; launch_dense in tile_dense.cu, launch_sparse in
 // tile_sparse.cu).  Each returns the cudaError_t of the launch.

@@ -712,9 +712,11 @@ __global__ void __launch_bounds__(NT) k_pre_multi(GroupArg g) {
 // work list (act: members in table order with their first item; frames in
 // order within a member) by ticket, so members without frames cost nothing
 // and items of unequal cost balance across the SMs.
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
-__global__ void __launch_bounds__(NTD, 2) k_tile_multi(GroupArg g, const ActiveTile* act,
-                                                       int cls) {
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, int TH_>
+__global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile_multi(GroupArg g,
+                                                                   const ActiveTile* act,
+                                                                   int cls) {
+  constexpr int NTD = 32 * TH_;
   __shared__ SimParams sp;
   __shared__ BatchArg sb;
   __shared__ int s_begin[MAX_GROUP];
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(NTD, 2) k_tile_multi(GroupArg g, const ActiveT
       __syncthreads();
     }
     const int T = sp.tiles_x * sp.tiles_y, r = t - s_begin[k], fi = r / T;
-    tile_frames<RESET, MAPS, WIDE, SPARSE, true>(sp, sb, r - fi * T, fi, fi + 1);
+    tile_frames<RESET, MAPS, WIDE, SPARSE, true, TH_>(sp, sb, r - fi * T, fi, fi + 1);
   }
   if (threadIdx.x == 0) {
     __threadfence();  // this block's ticket increments precede its exit count
@@ -892,7 +894,11 @@ __global__ void __launch_bounds__(NT) k_drain(GroupArg g, DrainArg d) {
 }
 template <bool RESET, bool MAPS, bool WIDE, bool SPARSE>
 cudaError_t set_tile_multi_attr(size_t bytes) {
-  return cudaFuncSetAttribute(k_tile_multi<RESET, MAPS, WIDE, SPARSE>,
+  const cudaError_t e = cudaFuncSetAttribute(k_tile_multi<RESET, MAPS, WIDE, SPARSE, 16>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tile_multi<RESET, MAPS, WIDE, SPARSE, 8>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -900,7 +906,9 @@ template <bool SPARSE>
 cudaError_t launch_tile_multi_mode(const GroupArg& g, int cls, const ActiveTile* act, int grid,
                                    size_t sm, cudaStream_t st) {
   const bool reset = cls & TILE_RESET, maps = cls & TILE_MAPS, wide = cls & TILE_WIDE;
-#define EVSIM_TILE(R, M, Wd) k_tile_multi<R, M, Wd, SPARSE><<<grid, NTD, sm, st>>>(g, act, cls)
+#define EVSIM_TILE(R, M, Wd)                                                                 \
+  if (cls & TILE_TH8) k_tile_multi<R, M, Wd, SPARSE, 8><<<grid, 256, sm, st>>>(g, act, cls);    \
+  else k_tile_multi<R, M, Wd, SPARSE, 16><<<grid, 512, sm, st>>>(g, act, cls)
   if (!reset && !maps && !wide) EVSIM_TILE(false, false, false);
   else if (!reset && maps && !wide) EVSIM_TILE(false, true, false);
   else if (!reset && !maps && wide) EVSIM_TILE(false, false, true);
@@ -916,8 +924,9 @@ cudaError_t launch_tile_multi_mode(const GroupArg& g, int cls, const ActiveTile*
 }  // namespace
 
 
-size_t tile_smem_bytes(int n_max) {
-  return (size_t)(2 * SH * SW + 256 + TP + 2 * n_max) * 4 + (size_t)(n_max * TP + 3 * TP) * 2;
+size_t tile_smem_bytes(int n_max, int th) {
+  const int tp = TW * th, sh = th + 2 * HMAX;
+  return (size_t)(2 * sh * SW + 256 + tp + 2 * n_max) * 4 + (size_t)(n_max * tp + 3 * tp) * 2;
 }
 
 int device_sm_count() {
@@ -1017,7 +1026,8 @@ cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st,
 
 int tile_class(const SimParams& p) {
   return (p.ref_mode == SIM_REF_RESET ? TILE_RESET : 0) | (p.cpmap ? TILE_MAPS : 0) |
-         (p.intensity == SIM_LINEAR ? TILE_WIDE : 0) | (p.mode == SIM_SPARSE ? TILE_SPARSE : 0);
+         (p.intensity == SIM_LINEAR ? TILE_WIDE : 0) | (p.mode == SIM_SPARSE ? TILE_SPARSE : 0) |
+         (p.tile_h == 8 ? TILE_TH8 : 0);
 }
 
 cudaError_t configure_group_kernels(size_t t) {

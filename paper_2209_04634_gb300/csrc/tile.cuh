@@ -334,7 +334,9 @@ struct TileLayout {
   unsigned short* sCn;
 };
 
+template <int TH_ = TH>
 __device__ __forceinline__ TileLayout tile_layout(unsigned char* raw, int nmax) {
+  constexpr int TP = TW * TH_, SH = TH_ + 2 * HMAX;
   TileLayout L;
   L.sLa = (int*)raw;
   L.sLb = L.sLa + SH * SW;
@@ -352,8 +354,10 @@ __device__ __forceinline__ TileLayout tile_layout(unsigned char* raw, int nmax) 
 // Fill a replicate-padded halo buffer (LUT'd) of one frame with reach (hx, hy)
 // around the tile.  The region is walked as a flat index (row = e / ncols by
 // a multiply-high with ceil(2^32 / ncols), exact for e < 2^16).
+template <int TH_ = TH>
 __device__ __forceinline__ void fill_halo(int* dst, const int* slut, const FrameRef& f, int W,
                                           int H, int tx0, int ty0, int hx, int hy) {
+  constexpr int TH = TH_, NTD = 32 * TH_;
   constexpr int FILL = 4;
   const int tid = threadIdx.x;
   const int c0 = HMAX - hx, ncols = TW + 2 * hx;
@@ -882,9 +886,11 @@ __device__ __forceinline__ void wait_tile(const SimParams& p, int tile, unsigned
 // f0 > 0: the tile's earlier frames were simulated by another block; wait for
 // them.  Publishes the tile's progress word at the end.  ONE: a single frame
 // (f1 = f0 + 1), which needs no state carried from frame to frame.
-template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, bool ONE = false>
+template <bool RESET, bool MAPS, bool WIDE, bool SPARSE, bool ONE = false, int TH_ = TH>
 __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& b, int tile, int f0,
                                             int f1) {
+  constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
+  (void)SH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NTD / 32 + 1];
   __shared__ int s_fx, s_fy;
@@ -897,7 +903,7 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max;
-  const TileLayout L = tile_layout(smem_raw, nmax);
+  const TileLayout L = tile_layout<TH_>(smem_raw, nmax);
   const int tcx = tile % p.tiles_x, tcy = tile / p.tiles_x;
   const int tx0 = tcx * TW, ty0 = tcy * TH;
   const int W = p.W, H = p.H;
@@ -1063,11 +1069,11 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
       hfx = max(hfx, hx);
       hfy = max(hfy, hy);
       if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
-        fill_halo(pb, L.slut, prv, W, H, tx0, ty0, hfx, hfy);
+        fill_halo<TH_>(pb, L.slut, prv, W, H, tx0, ty0, hfx, hfy);
         phx = hfx;
         phy = hfy;
       }
-      fill_halo(cb, L.slut, curf, W, H, tx0, ty0, hfx, hfy);
+      fill_halo<TH_>(cb, L.slut, curf, W, H, tx0, ty0, hfx, hfy);
     }
     __syncthreads();
     if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
@@ -1078,11 +1084,13 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
     const unsigned b1 = (unsigned)__cvta_generic_to_shared(cb);
     if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
       if (fast)
-        tile_substeps<RESET, WIDE, true, !SPARSE>(p, L, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
-                                                  lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn, &s_stage[warp]);
+        tile_substeps<RESET, WIDE, true, !SPARSE, TH_>(p, L, N, mN, tx0, ty0, b0, b1, prv, cur,
+                                                       segf, lx, ly, nk_at, act, Fx, Fy, R, Cp,
+                                                       Cn, &s_stage[warp]);
       else
-        tile_substeps<RESET, WIDE, false, !SPARSE>(p, L, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
-                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn, &s_stage[warp]);
+        tile_substeps<RESET, WIDE, false, !SPARSE, TH_>(p, L, N, mN, tx0, ty0, b0, b1, prv, cur,
+                                                        segf, lx, ly, nk_at, act, Fx, Fy, R, Cp,
+                                                        Cn, &s_stage[warp]);
     }
     if (!RESET) {
 #pragma unroll
@@ -1291,107 +1299,6 @@ __device__ __forceinline__ void stage_flow(float2* sf, const float2* flow, int W
   }
 }
 
-// Bulk staging: where every copy can be 16-byte aligned with a size that is a
-// multiple of 16 bytes (frame base and pitch multiples of 16, W * ch a
-// multiple of 16; flow base a multiple of 16, W even), the lanes of warp 0
-// copy the window's rows and the tile's flow rows as whole rows with
-// cp.async.bulk (one instruction per row), completing on the block's
-// mbarrier by transaction bytes, instead of every thread issuing 4- and
-// 8-byte cp.async copies.  A stage (the copies of one frame) registers its
-// bytes with expect_tx before its copies are issued and ends with one
-// arrive; consumers wait on the stage's phase parity, bounded.
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for phase `parity` of the stage barrier; gives up (and flags
-// a timeout in the stream's error word) after MBAR_SPIN_LIMIT polls.
-constexpr int MBAR_SPIN_LIMIT = 1 << 20;
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int* err) {
-  for (int spins = 0; !mbar_try_wait(bar, parity); ) {
-    if (++spins > MBAR_SPIN_LIMIT) {
-      atomicCAS(err, 0, SIM_ERR_DEVICE_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
-                                         unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-// Generic-proxy accesses of shared memory before this point (ordered by a
-// preceding barrier) precede the bulk copies issued after it.
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ bool frame_bulk_ok(const FrameRef& f, int W) {
-  return (((unsigned long long)f.ptr | (unsigned long long)f.pitch) & 15) == 0 &&
-         ((W * f.ch) & 15) == 0;
-}
-__device__ __forceinline__ bool flow_bulk_ok(const float2* flow, int W) {
-  return ((unsigned long long)flow & 15) == 0 && (W & 1) == 0;
-}
-
-// stage_raw's rows as bulk copies, issued by the 32 lanes of one warp.
-template <int TH_>
-__device__ __forceinline__ void stage_raw_bulk(unsigned char* raw, const FrameRef& f, int W,
-                                               int H, int tx0, int ty0, unsigned bar) {
-  constexpr int SH = TH_ + 2 * HMAX;
-  const int lane = threadIdx.x & 31;
-  const int ch = f.ch, RW = SW * ch;
-  const int r0 = max(0, HMAX - ty0), r1 = min(SH, H - ty0 + HMAX);
-  const int cx0 = max(0, tx0 - HMAX), cx1 = min(W, tx0 + TW + HMAX);
-  const int b0 = (cx0 - (tx0 - HMAX)) * ch;
-  const int nb = (cx1 - cx0) * ch;
-  if (lane == 0) mbar_expect_tx(bar, (unsigned)(max(0, r1 - r0) * nb));
-  __syncwarp();
-  fence_proxy_async();
-  const unsigned d0 = smem_addr(raw) + (unsigned)b0;
-  for (int r = r0 + lane; r < r1; r += 32)
-    bulk_g2s(d0 + (unsigned)(r * RW),
-             f.ptr + (long long)(ty0 - HMAX + r) * f.pitch + (long long)cx0 * ch, (unsigned)nb,
-             bar);
-}
-
-// stage_flow's rows (64 flows, 512 bytes, per tile row) as bulk copies.
-template <int TH_>
-__device__ __forceinline__ void stage_flow_bulk(float2* sf, const float2* flow, int W, int H,
-                                                int tx0, int ty0, unsigned bar) {
-  const int lane = threadIdx.x & 31;
-  const int rows = min(TH_, H - ty0), cols = min(TW, W - tx0);
-  if (lane == 0) mbar_expect_tx(bar, (unsigned)(rows * cols * 8));
-  __syncwarp();
-  fence_proxy_async();
-  const unsigned d0 = smem_addr(sf);
-  for (int ly = lane; ly < rows; ly += 32)
-    bulk_g2s(d0 + (unsigned)(ly * TW * 8), flow + (long long)(ty0 + ly) * W + tx0,
-             (unsigned)(cols * 8), bar);
-}
-
 // 8-bit luma of window pixel (row rr, column rc) of a staged frame.
 __device__ __forceinline__ int raw_luma(const unsigned char* raw, int ch, int rr, int rc) {
   const unsigned char* q = raw + rr * (SW * ch) + rc * ch;
@@ -1466,11 +1373,9 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   __shared__ __align__(16) FrameDesc s_desc[4];     // frame fi at fi & 3
   __shared__ __align__(8) unsigned long long s_mf[4];  // its squared flow maximum
   __shared__ WarpStage s_stage[NTD / 32];
-  __shared__ __align__(8) unsigned long long s_bar;  // bulk staging: one phase per frame
   Ctl* ctl = p.ctl;
   if (block_error(&ctl->err)) return;
   if ((threadIdx.x & 31) == 0) s_stage[threadIdx.x >> 5] = WarpStage{0, 0, p.stage_chunk};
-  const unsigned bar = smem_addr(&s_bar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nmax = p.n_max, ch = p.ch, RW = SW * ch;
@@ -1521,50 +1426,18 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     s_desc[tid] = b.frames[tid];
     s_mf[tid] = adaptive ? p.maxf2[tid] : 0ull;
   }
-  if (tid == 0) {
-    s_fx = 0;
-    s_fy = 0;
-    mbar_init(bar, 1);
-  }
+  if (tid == 0) { s_fx = 0; s_fy = 0; }
   __syncthreads();
-  // one stage: a frame's window bytes and flow rows, as bulk copies issued
-  // by warp 0 where aligned, else as cp.async copies by every thread; warp
-  // 0 closes the stage with the barrier's arrive
-  auto stage_frame = [&](unsigned char* dst, const FrameRef& f) {
-    if (!b.host_mapped && frame_bulk_ok(f, W)) {
-      if (warp == 0) stage_raw_bulk<TH_>(dst, f, W, H, tx0, ty0, bar);
-    } else {
-      stage_raw<TH_>(dst, f, W, H, tx0, ty0);
-    }
-  };
-  auto stage_flows = [&](float2* dst, const float2* fl) {
-    if (!b.host_mapped && flow_bulk_ok(fl, W)) {
-      if (warp == 0) stage_flow_bulk<TH_>(dst, fl, W, H, tx0, ty0, bar);
-    } else {
-      stage_flow<TH_>(dst, fl, W, H, tx0, ty0);
-    }
-  };
-  auto close_stage = [&]() {
-    if (warp == 0) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar);
-    }
-  };
-  unsigned phase = 0;  // parity of the stage in flight
-  bool pending = false;
   {
     const FrameRef ring{ringp, (long long)W, 1};
     const FrameDesc d0 = s_desc[0];
-    stage_frame(L.raw, ring);
-    stage_frame(L.raw + SH * RW, FrameRef{d0.frame, d0.pitch, ch});
-    stage_flows(L.sflow, d0.flow);
-    close_stage();
+    stage_raw<TH_>(L.raw, ring, W, H, tx0, ty0);
+    stage_raw<TH_>(L.raw + SH * RW, FrameRef{d0.frame, d0.pitch, ch}, W, H, tx0, ty0);
+    stage_flow<TH_>(L.sflow, d0.flow, W, H, tx0, ty0);
     cp_async_commit();
     if (tid < 64)
       substep_tables(p, s_mf[0], t_first, d0.t_rel, L.swk, L.stk, &s_N[0], &s_mN[0], s_cmask[0]);
     cp_async_wait_all();
-    pending = !mbar_wait(bar, phase, &ctl->err);
-    phase ^= 1;
   }
   __syncthreads();
 
@@ -1749,9 +1622,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     // substep tables
     if (fi + 1 < count) {
       const FrameDesc nd = s_desc[(fi + 1) & 3];
-      stage_frame(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch});
-      stage_flows(L.sflow + (par ^ 1) * TP, nd.flow);
-      close_stage();
+      stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
+      stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
       if (fi + 2 < count && tid < 2) {
         // descriptors are 32-byte, 16-byte aligned records
         cp_async16(smem_addr(&s_desc[(fi + 2) & 3]) + 16u * tid,
@@ -1922,15 +1794,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     }
     rb = 1 - rb;
     cp_async_wait_all();
-    if (fi + 1 < count) {
-      pending = !mbar_wait(bar, phase, &ctl->err) || pending;
-      phase ^= 1;
-    }
     __syncthreads();
   }
-  // a stage whose wait gave up (timeout flagged): wait once more, bounded,
-  // so that no copy is still writing this block's shared memory at exit
-  if (pending) mbar_wait(bar, phase ^ 1, &ctl->err);
 
   if (!RESET) {
 #pragma unroll

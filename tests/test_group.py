@@ -276,3 +276,47 @@ def test_group_delivery_matches_single_stream_handles(delivery_events, depth):
                                delivery_events=delivery_events, depth=depth)
     for (name, _s, _o), gv, wv in zip(mix, got, want):
         assert_same_events(gv, wv, name)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("th", [8, 16])
+def test_group_members_in_either_tile_shape_match_the_oracle(th):
+    """Members whose configuration asks for 64 x 8 (or 64 x 16) tiles run in
+    the group's kernel of that shape; a mixed-size group of dense and sparse
+    members, with threshold maps and adaptive N, equals the oracle."""
+    mix = [(n, s, dict(o, tile_height=th)) for n, s, o in _mix()]
+    got, st = _run_group(mix, use_graphs=True, fmax=2, schedule=lambda i, s: 1 + (i + s) % 2)
+    for (name, seq, opts), ev in zip(mix, got):
+        assert_same_events(ev, _oracle_events(seq, opts), f"{name} in 64x{th} tiles")
+
+
+def _oracle_events(seq, opts):
+    """The oracle's events for a member admitted with these options."""
+    import oracle
+    return oracle.run(
+        seq.frames, seq.flows, seq.t_us,
+        mode=oracle.SPARSE if opts.get("mode") == evsim.SIM_SPARSE else oracle.DENSE,
+        substeps=opts.get("substeps", seq.substeps),
+        max_substeps=opts.get("max_substeps", seq.max_substeps),
+        intensity=oracle.LINEAR if opts.get("intensity") == evsim.SIM_LINEAR else oracle.LOG,
+        ref_mode=oracle.RESET if opts.get("ref_mode") == evsim.SIM_REF_RESET else oracle.ACCUM,
+        c_pos_q16=opts.get("c_pos_q16", oracle.q16(seq.c_pos)),
+        c_neg_q16=opts.get("c_neg_q16", oracle.q16(seq.c_neg)),
+        cpos_map=opts.get("c_pos_map", seq.cpos_map),
+        cneg_map=opts.get("c_neg_map", seq.cneg_map))["events"]
+
+
+@pytest.mark.gpu
+def test_group_member_takes_the_autotuned_tile_shape(tmp_path):
+    """A member admitted with the automatic tile shape takes the shape the
+    autotuner table holds for its configuration (64 x 8 here), and its events
+    equal the oracle's."""
+    seq = synth.blob_translation(seed=93, frames=5, width=200, height=90)
+    f = tmp_path / "table.txt"
+    f.write_text(f"200 90 1 0 {seq.substeps} 0 0 0 0 8 0 1.0 2.0 0.0\\n")
+    evsim.autotune_load(str(f))
+    got, _ = _run_group([("blob", seq, dict(mode=evsim.SIM_DENSE, c_pos_map=None,
+                                            c_neg_map=None))],
+                        use_graphs=False, fmax=2, schedule=lambda i, s: 2)
+    assert_same_events(got[0], _oracle_events(seq, dict(mode=evsim.SIM_DENSE, c_pos_map=None,
+                                                         c_neg_map=None)), "tuned 64x8 member")
