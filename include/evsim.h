@@ -72,6 +72,7 @@ extern "C" {
 #define SIM_ERR_ADMIT (-9)         /* batch: admission refused (memory budget / slots) */
 #define SIM_ERR_NO_DEVICE (-10)    /* no usable CUDA device / kernel image */
 #define SIM_ERR_TOO_LARGE (-11)    /* sim_step_pair_static: problem exceeds its scratch */
+#define SIM_ERR_BOUNDS (-12)       /* debug builds only: a kernel index left its buffer */
 
 /* ---- enumerations ------------------------------------------------------- */
 enum { SIM_LUMA8 = 1, SIM_RGB8 = 3 };          /* bytes per input pixel */

@@ -36,6 +36,16 @@ constexpr unsigned long long LB_AGG = 1ull << 30;
 constexpr unsigned long long LB_INC = 2ull << 30;
 constexpr unsigned long long LB_VALUE = (1ull << 30) - 1;
 constexpr int MAX_EVENTS = (1 << 30) - 2;  // per batch (and event buffer capacity)
+// Debug builds (compiled with EVSIM_BOUNDS_CHECK): the kernels check the
+// indices of their global writes, of the order kernel's segment and staging
+// reads and of the shared-memory halo writes, record the first violation as
+// SIM_ERR_BOUNDS in the stream's error word and skip the access.  Release
+// builds compile the checks away.
+#ifdef EVSIM_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
 // Bounded spin: polls before a look-back (or a tile's wait for its earlier
 // frames) gives up and flags a timeout; SimParams.spin_limit overrides it
 // (0: this default).
@@ -138,6 +148,7 @@ struct SimParams {
   unsigned long long* tdone;    // per tile: [batch serial:32][frames of the batch done:32]
   Seg* seg;                     // per (frame, substep, tile row)
   long long segs_per_k;         // segments per substep of one frame
+  long long seg_cap;            // segments the table holds (debug bounds checks)
   unsigned long long* order_status;
   Ev* events;
   long long event_cap;

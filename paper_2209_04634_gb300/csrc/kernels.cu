@@ -485,7 +485,9 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
       // a unit-frame of the row kernel that emitted nothing wrote a flag
       // instead of its segments
       if (!p.segflag || p.segflag[(long long)fi * S + rs]) {
-        const Seg sg = p.seg[((long long)fi * p.n_max + k) * S + rs];
+        const long long si2 = ((long long)fi * p.n_max + k) * S + rs;
+        Seg sg{0ull, 0ull, 0, -1};
+        if (in_bounds(ctl, si2, p.seg_cap)) sg = p.seg[si2];
         cnt = sg.cnt;
         src = sg.src;
         mask = sg.mask;
@@ -540,6 +542,7 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
     const int m = jj - o.ex[lo];
     Ev ev;
     if (o.src[lo] >= 0) {
+      if (!in_bounds(ctl, (long long)o.src[lo] + m, p.stage_cap)) continue;
       ev = p.staging[(long long)o.src[lo] + m];
     } else {
       const int bit = nth_set_bit(o.mask[lo], m);
@@ -555,7 +558,9 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
     const int lane = tid & 31;
     for (int q = tid >> 5; q < o.ncblk; q += NWARP) {
       const int sidx = o.cblk[q];
-      const unsigned wd = ((const unsigned*)(p.staging + (-2LL - o.src[sidx])))[lane];
+      const long long cb = -2LL - o.src[sidx];
+      const unsigned wd = in_bounds(ctl, cb + 15, p.stage_cap)
+                              ? ((const unsigned*)(p.staging + cb))[lane] : 0u;
       const int a_lo = (int)(wd & 0xFFFFu), a_hi = (int)(wd >> 16);
       const int i_lo = warp_incl_scan(a_lo);
       const int t_lo = __shfl_sync(FULL, i_lo, 31);

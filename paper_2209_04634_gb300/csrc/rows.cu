@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(RT, 4) k_rows(SimParams p, BatchArg b) {
         const int x = x0 + lane + 32 * j;
         const int vc = load_luma(cur.ptr, cur.pitch, cur.ch, y, x);
         const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
-        if (fi == count - 1) ringn[(long long)y * W + x] = (unsigned char)vc;
+        if (fi == count - 1 && in_bounds(ctl, (long long)y * W + x, (long long)W * H))
+          ringn[(long long)y * W + x] = (unsigned char)vc;
         const int Lc = slut[vc], Lp = slut[vp];
         act[j] = !SPARSE || abs(Lc - Lp) >= cact[j];
         if (RESET) R[j] = Lp;
@@ -272,7 +273,8 @@ __global__ void __launch_bounds__(RT, 4) k_rows(SimParams p, BatchArg b) {
       }
       Seg* segr = p.seg + (long long)fi * p.n_max * S + u;
       const bool any = __any_sync(FULL, sim[0] || sim[1]);
-      if (lane == 0) p.segflag[(long long)fi * S + u] = any ? 1 : 0;
+      if (lane == 0 && in_bounds(ctl, (long long)fi * S + u, p.seg_cap / p.n_max))
+        p.segflag[(long long)fi * S + u] = any ? 1 : 0;
       if (any) {
         // 2. substeps; the unit-frame's segments are written
         const RowTab T = row_tables(N, tprev, cd.t_rel);
@@ -288,7 +290,8 @@ __global__ void __launch_bounds__(RT, 4) k_rows(SimParams p, BatchArg b) {
     if (!RESET) {
 #pragma unroll
       for (int j = 0; j < 2; ++j)
-        if (inimg[j]) Rout[(long long)y * W + x0 + lane + 32 * j] = R[j];
+        if (inimg[j] && in_bounds(ctl, (long long)y * W + x0 + lane + 32 * j, (long long)W * H))
+          Rout[(long long)y * W + x0 + lane + 32 * j] = R[j];
     }
   }
   clamps = __reduce_add_sync(FULL, clamps);

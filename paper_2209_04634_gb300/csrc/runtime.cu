@@ -152,6 +152,7 @@ evsim::SimParams make_params(const sim_t* s) {
   p.seg = s->d_seg;
   p.tdone = s->d_tdone;
   p.segs_per_k = s->segs_per_k;
+  p.seg_cap = (long long)s->bmax * s->n_max * s->segs_per_k;
   p.order_status = s->d_order_status;
   p.events = s->d_events;
   p.event_cap = s->event_cap;
@@ -329,6 +330,7 @@ const char* sim_strerror(int code) {
     case SIM_ERR_ADMIT: return "admission refused";
     case SIM_ERR_NO_DEVICE: return "no usable CUDA device";
     case SIM_ERR_TOO_LARGE: return "problem too large for the fixed scratch array";
+    case SIM_ERR_BOUNDS: return "a kernel index left its buffer (debug build bounds check)";
     default: return "unknown error";
   }
 }

@@ -249,6 +249,7 @@ extern "C" int sim_step_pair_static(const sim_config* cfg, const void* prev_fram
   p.stage_cap = L.stage_events;
   p.seg = (Seg*)(base + L.seg);
   p.segs_per_k = segs_per_k;
+  p.seg_cap = nseg;
   p.order_status = (unsigned long long*)(base + L.status);
   p.tdone = (unsigned long long*)(base + L.tdone);
   p.events = (Ev*)events;

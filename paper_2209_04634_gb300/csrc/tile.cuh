@@ -37,6 +37,16 @@ __device__ __forceinline__ bool block_error(const int* err) {
   return s_err != 0;
 }
 
+// Debug builds: whether index i lies in [0, n); a violation is recorded once
+// as SIM_ERR_BOUNDS in the stream's error word and the caller skips the
+// access.  Release builds: true, no code.
+__device__ __forceinline__ bool in_bounds(Ctl* ctl, long long i, long long n) {
+  if (!kBoundsCheck) return true;
+  if (i >= 0 && i < n) return true;
+  if (ctl) atomicCAS(&ctl->err, 0, SIM_ERR_BOUNDS);
+  return false;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -356,8 +366,9 @@ __device__ __forceinline__ TileLayout tile_layout(unsigned char* raw, int nmax) 
 // a multiply-high with ceil(2^32 / ncols), exact for e < 2^16).
 template <int TH_ = TH>
 __device__ __forceinline__ void fill_halo(int* dst, const int* slut, const FrameRef& f, int W,
-                                          int H, int tx0, int ty0, int hx, int hy) {
-  constexpr int TH = TH_, NTD = 32 * TH_;
+                                          int H, int tx0, int ty0, int hx, int hy,
+                                          Ctl* ctl = nullptr) {
+  constexpr int TH = TH_, NTD = 32 * TH_, SH = TH_ + 2 * HMAX;
   constexpr int FILL = 4;
   const int tid = threadIdx.x;
   const int c0 = HMAX - hx, ncols = TW + 2 * hx;
@@ -381,8 +392,13 @@ __device__ __forceinline__ void fill_halo(int* dst, const int* slut, const Frame
     }
 #pragma unroll
     for (int q = 0; q < FILL; ++q)
-      if (at[q] >= 0) dst[at[q]] = slut[v[q]];
+      if (at[q] >= 0 && in_bounds(ctl, at[q], SH * SW)) dst[at[q]] = slut[v[q]];
   }
+}
+
+// A segment write, checked in debug builds.
+__device__ __forceinline__ void put_seg(const SimParams& p, Seg* sg, const Seg& v) {
+  if (in_bounds(p.ctl, sg - p.seg, p.seg_cap)) *sg = v;
 }
 
 // Staging space of one warp: multi-crossing rows take their events' space
@@ -433,10 +449,10 @@ __device__ __forceinline__ void stage_row(const SimParams& p, WarpStage* ws, Seg
   if (lane == 0) base = stage_take(p, *ws, total);
   base = __shfl_sync(FULL, base, 0);
   if (base >= 0) {
-    for (int m = 0; m < a_lo; ++m) p.staging[base + i_lo - a_lo + m] = e_lo;
-    for (int m = 0; m < a_hi; ++m) p.staging[base + t_lo + i_hi - a_hi + m] = e_hi;
+    for (int m = 0; m < a_lo; ++m) if (in_bounds(p.ctl, base + i_lo - a_lo + m, p.stage_cap)) p.staging[base + i_lo - a_lo + m] = e_lo;
+    for (int m = 0; m < a_hi; ++m) if (in_bounds(p.ctl, base + t_lo + i_hi - a_hi + m, p.stage_cap)) p.staging[base + t_lo + i_hi - a_hi + m] = e_hi;
   }
-  if (lane == 0) *sg = Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1};
+  if (lane == 0) put_seg(p, sg, Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1});
 }
 
 // Publish the segment of one (substep, tile row) of a dense tile: lane l
@@ -447,16 +463,16 @@ __device__ __forceinline__ void publish_row_dense(const SimParams& p, Seg* sg, i
   const int lane = threadIdx.x & 31;
   const unsigned e0 = __ballot_sync(FULL, n0 != 0), e1 = __ballot_sync(FULL, n1 != 0);
   if ((e0 | e1) == 0) {
-    if (lane == 0) *sg = Seg{0ull, 0ull, 0, -1};
+    if (lane == 0) put_seg(p, sg, Seg{0ull, 0ull, 0, -1});
     return;
   }
   const unsigned multi = __ballot_sync(FULL, (unsigned)(n0 + 1) > 2u || (unsigned)(n1 + 1) > 2u);
   if (multi == 0) {
     const unsigned p0 = __ballot_sync(FULL, n0 > 0), p1 = __ballot_sync(FULL, n1 > 0);
     if (lane == 0)
-      *sg = Seg{(unsigned long long)e0 | ((unsigned long long)e1 << 32),
+      put_seg(p, sg, Seg{(unsigned long long)e0 | ((unsigned long long)e1 << 32),
                 (unsigned long long)p0 | ((unsigned long long)p1 << 32), __popc(e0) + __popc(e1),
-                -1};
+                -1});
     return;
   }
   // a pixel crossed two or more thresholds: rows of at least 16 events
@@ -474,12 +490,13 @@ __device__ __forceinline__ void publish_row_dense(const SimParams& p, Seg* sg, i
   long long base = 0;
   if (lane == 0) base = stage_take(p, *ws, 16);
   base = __shfl_sync(FULL, base, 0);
-  if (base >= 0) ((unsigned*)(p.staging + base))[lane] = (unsigned)a0 | ((unsigned)a1 << 16);
+  if (base >= 0 && in_bounds(p.ctl, base + 15, p.stage_cap))
+    ((unsigned*)(p.staging + base))[lane] = (unsigned)a0 | ((unsigned)a1 << 16);
   if (lane == 0)
-    *sg = base >= 0 ? Seg{(unsigned long long)e0 | ((unsigned long long)e1 << 32),
+    put_seg(p, sg, base >= 0 ? Seg{(unsigned long long)e0 | ((unsigned long long)e1 << 32),
                           (unsigned long long)p0 | ((unsigned long long)p1 << 32), total,
                           -2 - (int)base}
-                    : Seg{0ull, 0ull, 0, -1};
+                    : Seg{0ull, 0ull, 0, -1});
 }
 
 // Publish the segment of one (substep, tile row) from a warp that holds the
@@ -497,7 +514,7 @@ __device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_l
   const bool lo_in_low = col_lo < 32, hi_in_low = col_hi < 32;
   const unsigned m_any = __ballot_sync(FULL, (v_lo && n_lo) || (v_hi && n_hi));
   if (m_any == 0) {
-    if (lane == 0) *sg = Seg{0ull, 0ull, 0, -1};
+    if (lane == 0) put_seg(p, sg, Seg{0ull, 0ull, 0, -1});
     return;
   }
   const unsigned low = __reduce_or_sync(FULL, (lo_in_low ? b_lo : 0u) | (hi_in_low ? b_hi : 0u));
@@ -509,9 +526,9 @@ __device__ __forceinline__ void publish_row(const SimParams& p, Seg* sg, int n_l
   const int a_lo = v_lo ? abs(n_lo) : 0, a_hi = v_hi ? abs(n_hi) : 0;
   if (!__any_sync(FULL, a_lo > 1 || a_hi > 1)) {
     if (lane == 0)
-      *sg = Seg{(unsigned long long)low | ((unsigned long long)high << 32),
+      put_seg(p, sg, Seg{(unsigned long long)low | ((unsigned long long)high << 32),
                 (unsigned long long)plow | ((unsigned long long)phigh << 32),
-                __popc(low) + __popc(high), -1};
+                __popc(low) + __popc(high), -1});
     return;
   }
   stage_row(p, ws, sg, a_lo, a_hi, make_event(tk, tx0 + col_lo, y, n_lo > 0),
@@ -565,7 +582,7 @@ __device__ __forceinline__ void publish_row_xt(const SimParams& p, Seg* sg, int 
   const int lane = threadIdx.x & 31;
   const int a_lo = abs(n_lo), a_hi = abs(n_hi);
   if (!__any_sync(FULL, (a_lo | a_hi) != 0)) {
-    if (lane == 0) *sg = Seg{0ull, 0ull, 0, -1};
+    if (lane == 0) put_seg(p, sg, Seg{0ull, 0ull, 0, -1});
     return;
   }
   const int i_lo = warp_incl_scan(a_lo);
@@ -578,13 +595,13 @@ __device__ __forceinline__ void publish_row_xt(const SimParams& p, Seg* sg, int 
   if (base >= 0) {
     const unsigned dt = t1 - t0;
     for (int m = 0; m < a_lo; ++m)
-      p.staging[base + i_lo - a_lo + m] =
+      if (in_bounds(p.ctl, base + i_lo - a_lo + m, p.stage_cap)) p.staging[base + i_lo - a_lo + m] =
           make_event(crossing_time(t0, dt, x_lo, n_lo > 0, m + 1), tx0 + col_lo, y, n_lo > 0);
     for (int m = 0; m < a_hi; ++m)
-      p.staging[base + t_lo + i_hi - a_hi + m] =
+      if (in_bounds(p.ctl, base + t_lo + i_hi - a_hi + m, p.stage_cap)) p.staging[base + t_lo + i_hi - a_hi + m] =
           make_event(crossing_time(t0, dt, x_hi, n_hi > 0, m + 1), tx0 + col_hi, y, n_hi > 0);
   }
-  if (lane == 0) *sg = Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1};
+  if (lane == 0) put_seg(p, sg, Seg{0ull, 0ull, base >= 0 ? total : 0, base >= 0 ? (int)base : -1});
 }
 
 // The substeps of the (up to) two pixels of this thread.  `lx, ly` are the
@@ -988,7 +1005,10 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
       bool a = inimg[q];
       if (inimg[q] && (SPARSE || fi == b.count - 1)) {
         const int vc = load_luma(cur.frame, cur.pitch, p.ch, y, x);
-        if (fi == b.count - 1) ringn[(long long)y * W + x] = (unsigned char)vc;
+        if (fi == b.count - 1) {
+          const long long ri = (long long)y * W + x;
+          if (in_bounds(p.ctl, ri, (long long)p.W * p.H)) ringn[ri] = (unsigned char)vc;
+        }
         if (SPARSE) {
           const int vp = load_luma(prv.ptr, prv.pitch, prv.ch, y, x);
           const int cp = MAPS ? (int)L.sCp[own[q]] : p.cp, cn = MAPS ? (int)L.sCn[own[q]] : p.cn;
@@ -1069,11 +1089,11 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
       hfx = max(hfx, hx);
       hfy = max(hfy, hy);
       if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
-        fill_halo<TH_>(pb, L.slut, prv, W, H, tx0, ty0, hfx, hfy);
+        fill_halo<TH_>(pb, L.slut, prv, W, H, tx0, ty0, hfx, hfy, ctl);
         phx = hfx;
         phy = hfy;
       }
-      fill_halo<TH_>(cb, L.slut, curf, W, H, tx0, ty0, hfx, hfy);
+      fill_halo<TH_>(cb, L.slut, curf, W, H, tx0, ty0, hfx, hfy, ctl);
     }
     __syncthreads();
     if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
@@ -1112,8 +1132,7 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
       const int y = ty0 + r;
       if (y < H) {
         if (s1 == s0) {
-          for (int k = lane; k < N; k += 32) segf[(long long)k * p.segs_per_k + r * p.tiles_x] =
-              Seg{0ull, 0ull, 0, -1};
+          for (int k = lane; k < N; k += 32) put_seg(p, &segf[(long long)k * p.segs_per_k + r * p.tiles_x], Seg{0ull, 0ull, 0, -1});
         } else {
           const int j_lo = s0 + lane, j_hi = s0 + 32 + lane;
           const bool v_lo = j_lo < s1, v_hi = j_hi < s1;
@@ -1147,8 +1166,8 @@ __device__ __forceinline__ void tile_frames(const SimParams& p, const BatchArg& 
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!inimg[q]) continue;
-      Rout[(long long)(ty0 + own[q] / TW) * W + tx0 + (own[q] & (TW - 1))] =
-          SPARSE ? L.sR[own[q]] : Rd[q];
+      const long long ri = (long long)(ty0 + own[q] / TW) * W + tx0 + (own[q] & (TW - 1));
+      if (in_bounds(p.ctl, ri, (long long)W * H)) Rout[ri] = SPARSE ? L.sR[own[q]] : Rd[q];
     }
   }
   clamps = __reduce_add_sync(FULL, clamps);
@@ -1311,7 +1330,7 @@ __device__ __forceinline__ int raw_luma(const unsigned char* raw, int ch, int rr
 template <int TH_>
 __device__ __forceinline__ void fill_halo_raw(int* dst, const int* slut, const unsigned char* raw,
                                               int ch, int W, int H, int tx0, int ty0, int hx,
-                                              int hy) {
+                                              int hy, Ctl* ctl = nullptr) {
   constexpr int TH = TH_, NTD = 32 * TH_, TP = TW * TH_, SH = TH_ + 2 * HMAX;
   (void)TH; (void)NTD; (void)TP; (void)SH;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1325,7 +1344,7 @@ __device__ __forceinline__ void fill_halo_raw(int* dst, const int* slut, const u
       const int gx = min(max(tx0 - hx + sc, 0), W - 1);
       const unsigned char* q = src + (gx - (tx0 - HMAX)) * ch;
       const int v = ch == 1 ? q[0] : (77 * q[0] + 150 * q[1] + 29 * q[2] + 128) >> 8;
-      d[sc] = slut[v];
+      if (in_bounds(ctl, (HMAX - hy + sr) * SW + (HMAX - hx) + sc, SH * SW)) d[sc] = slut[v];
     }
   }
 }
@@ -1478,7 +1497,10 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       bool a = inimg[q];
       if (inimg[q] && (SPARSE || spm || fi == count - 1)) {
         const int vc = raw_luma(rawc, ch, ly + HMAX, lx + HMAX);
-        if (fi == count - 1) ringn[(long long)(ty0 + ly) * W + tx0 + lx] = (unsigned char)vc;
+        if (fi == count - 1) {
+          const long long ri = (long long)(ty0 + ly) * W + tx0 + lx;
+          if (in_bounds(p.ctl, ri, (long long)p.W * p.H)) ringn[ri] = (unsigned char)vc;
+        }
         if (SPARSE || spm) {
           const int vp = raw_luma(rawp, chp, ly + HMAX, lx + HMAX);
           const int cp = MAPS ? (SPARSE ? (int)L.sCp[own[q]] : Cpd[q]) : p.cp;
@@ -1608,11 +1630,11 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       hfx = max(hfx, hx);
       hfy = max(hfy, hy);
       if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
-        fill_halo_raw<TH_>(pb, L.slut, rawp, chp, W, H, tx0, ty0, hfx, hfy);
+        fill_halo_raw<TH_>(pb, L.slut, rawp, chp, W, H, tx0, ty0, hfx, hfy, ctl);
         phx = hfx;
         phy = hfy;
       }
-      fill_halo_raw<TH_>(cb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy);
+      fill_halo_raw<TH_>(cb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy, ctl);
     }
     __syncthreads();
     if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
@@ -1650,7 +1672,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       if (SPARSE && A == 0) {  // warp-uniform: nothing simulated, empty segments
         if (ty0 + warp < H)
           for (int k = lane; k < N; k += 32)
-            segf[(long long)k * p.segs_per_k + warp * p.tiles_x] = Seg{0ull, 0ull, 0, -1};
+            put_seg(p, &segf[(long long)k * p.segs_per_k + warp * p.tiles_x], Seg{0ull, 0ull, 0, -1});
       } else {
 #define EVSIM_XT(FA, MK)                                                                      \
   tile_substeps<RESET, WIDE, FA, true, TH_, true, MK>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, \
@@ -1667,7 +1689,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       }
     } else if (SPARSE && dsw && !(fast && N <= 32)) {
       if (p.segflag && ty0 + warp < H && lane == 0)  // every row simulated
-        p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 1;
+        if (in_bounds(p.ctl, (long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx, p.seg_cap / p.n_max))
+          p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 1;
       if (fast)
         tile_substeps<RESET, WIDE, true, true, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
                                                     lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
@@ -1679,7 +1702,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     } else if ((!SPARSE || dsw) && fast) {
       const bool skip = p.segflag && __all_sync(FULL, quiet);
       if (p.segflag && ty0 + warp < H && lane == 0)
-        p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] =
+        if (in_bounds(p.ctl, (long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx, p.seg_cap / p.n_max))
+          p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] =
             skip ? 0 : 1;
       if (ty0 + warp < H && !skip) {  // warp-uniform: rows below the image publish nothing
         // the row's 64 pixels are in the image (and, sparse, all simulated)
@@ -1708,7 +1732,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       }
     } else if (!SPARSE || warp * 32 < A || warp * 32 + NTD < A) {  // warp-uniform
       if (!SPARSE && p.segflag && ty0 + warp < H && lane == 0)  // every row simulated
-        p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 1;
+        if (in_bounds(p.ctl, (long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx, p.seg_cap / p.n_max))
+          p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 1;
       if (fast)
         tile_substeps<RESET, WIDE, true, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
@@ -1739,10 +1764,10 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         if (ty0 + r >= H || ((s_multi[k] >> r) & 1u)) continue;
         const unsigned* m = rowm + t * 4;
         const int cnt = __popc(m[0]) + __popc(m[1]);
-        segf[(long long)k * p.segs_per_k + r * p.tiles_x] =
-            cnt ? Seg{(unsigned long long)m[0] | ((unsigned long long)m[1] << 32),
-                      (unsigned long long)m[2] | ((unsigned long long)m[3] << 32), cnt, -1}
-                : Seg{0ull, 0ull, 0, -1};
+        put_seg(p, &segf[(long long)k * p.segs_per_k + r * p.tiles_x],
+                cnt ? Seg{(unsigned long long)m[0] | ((unsigned long long)m[1] << 32),
+                          (unsigned long long)m[2] | ((unsigned long long)m[3] << 32), cnt, -1}
+                    : Seg{0ull, 0ull, 0, -1});
       }
       const int r = warp, s0 = s_rs[r], s1 = s_rs[r + 1];
       const int y = ty0 + r;
@@ -1765,8 +1790,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       const int y = ty0 + r;
       if (y < H) {
         if (s1 == s0) {
-          for (int k = lane; k < N; k += 32) segf[(long long)k * p.segs_per_k + r * p.tiles_x] =
-              Seg{0ull, 0ull, 0, -1};
+          for (int k = lane; k < N; k += 32) put_seg(p, &segf[(long long)k * p.segs_per_k + r * p.tiles_x], Seg{0ull, 0ull, 0, -1});
         } else {
           const int j_lo = s0 + lane, j_hi = s0 + 32 + lane;
           const bool v_lo = j_lo < s1, v_hi = j_hi < s1;
@@ -1801,8 +1825,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!inimg[q]) continue;
-      Rout[(long long)(ty0 + own[q] / TW) * W + tx0 + (own[q] & (TW - 1))] =
-          SPARSE ? L.sR[own[q]] : Rd[q];
+      const long long ri = (long long)(ty0 + own[q] / TW) * W + tx0 + (own[q] & (TW - 1));
+      if (in_bounds(p.ctl, ri, (long long)W * H)) Rout[ri] = SPARSE ? L.sR[own[q]] : Rd[q];
     }
   }
   clamps = __reduce_add_sync(FULL, clamps);

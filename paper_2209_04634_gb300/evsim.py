@@ -178,11 +178,13 @@ def library_path() -> str:
 
 
 def load(path: str | None = None):
-    """Load libevsim.so (raises if it has not been built)."""
+    """Load libevsim.so (raises if it has not been built); the EVSIM_LIBRARY
+    environment variable may name another build of it (the bounds-checked
+    debug build)."""
     global _lib
     with _lock:
         if _lib is None:
-            p = path or _build.LIB
+            p = path or os.environ.get("EVSIM_LIBRARY") or _build.LIB
             if not os.path.exists(p):
                 raise RuntimeError(f"evsim CUDA library not built ({p}); run "
                                    "paper_2209_04634_gb300.build.build() first")
