@@ -143,6 +143,31 @@ def stream_seed(rank: int, base: int = C2_SEED) -> int:
     return base + 1000 * rank
 
 
+def bind_host_to_gpu(gpu_index: int) -> dict:
+    """Run this process on the host CPUs local to its GPU (sysfs
+    local_cpulist of the GPU's PCI device), so that host memory it allocates
+    from now on - pinned buffers included - is placed on the GPU's own
+    memory node (first touch).  Returns what was done."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().splitlines()[0].strip()
+        dom, rest = out.split(":", 1)
+        dev = f"{int(dom, 16):04x}:{rest}".lower()
+        base = f"/sys/bus/pci/devices/{dev}"
+        node = open(base + "/numa_node").read().strip()
+        cpus = set()
+        for part in open(base + "/local_cpulist").read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        return {"pci": dev, "numa_node": node, "cpus": len(cpus)}
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError) as e:
+        return {"unbound": str(e)[:120]}
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -543,7 +568,13 @@ def run_ours(args, ws, rank, local):
         "autotune": ps.tune,
     }
     if rank == 0 and not args.no_e2e:
+        # pinned buffers on the GPU's own memory node: run on its local CPUs
+        # while they are allocated and used, then restore the affinity
+        saved = os.sched_getaffinity(0)
+        binding = bind_host_to_gpu(local)
         line["e2e"] = run_e2e(args, ps, work_step)
+        line["e2e"]["host_binding"] = binding
+        os.sched_setaffinity(0, saved)
     ps.close()
     del ps
     torch.cuda.empty_cache()

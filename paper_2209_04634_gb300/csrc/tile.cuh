@@ -1226,7 +1226,7 @@ struct BatchLayout {
   int* sR;              // [TP] sparse
   unsigned* stk;        // [2][nmax] substep times (frame parity)
   int* swk;             // [2][nmax] substep weights
-  unsigned char* raw;   // [2][SH][SW * ch]
+  unsigned char* raw;   // [2 sparse, 3 dense][SH][SW * ch]
   short* snk;           // [nmax][TP] sparse
   short* sslot;         // [TP] sparse
   unsigned short* sCp;  // [TP] sparse maps
@@ -1237,7 +1237,7 @@ __host__ __device__ inline size_t batch_smem_bytes(int n_max, int ch, bool spars
   const int TP = TW * th, SH = th + 2 * HMAX;
   size_t b = (size_t)2 * TP * sizeof(float2);
   b += (size_t)(2 * SH * SW + 256 + (sparse ? TP : 0) + 4 * n_max) * 4;
-  b += (size_t)2 * SH * SW * ch;
+  b += (size_t)(sparse ? 2 : 3) * SH * SW * ch;  // raw frame buffers
   if (sparse) b += (size_t)(n_max * TP + 3 * TP) * 2;
   return b;
 }
@@ -1255,7 +1255,7 @@ __device__ __forceinline__ BatchLayout batch_layout(unsigned char* base, int nma
   L.stk = (unsigned*)(L.sR + (SPARSE ? TP : 0));
   L.swk = (int*)(L.stk + 2 * nmax);
   L.raw = (unsigned char*)(L.swk + 2 * nmax);
-  L.snk = (short*)(L.raw + 2 * SH * SW * ch);
+  L.snk = (short*)(L.raw + (SPARSE ? 2 : 3) * SH * SW * ch);
   L.sslot = L.snk + nmax * TP;
   L.sCp = (unsigned short*)(L.sslot + TP);
   L.sCn = L.sCp + TP;
@@ -1462,7 +1462,12 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 
   int clamps = 0;
   long long act_sum = 0, act_n = 0;
-  int rb = 1;  // raw buffer of the current frame; 1 - rb holds the previous frame
+  // raw frame buffers: sparse instances two (rb holds the current frame, 1 - rb
+  // the previous one, the next frame is staged over the previous one after
+  // its last read, mid-frame); dense instances three (frame f in buffer
+  // (f + 1) mod 3, the next frame staged at the start of each frame, so its
+  // copies overlap the whole frame's work)
+  int rb = 1;
   int* cb = L.sLb;
   int* pb = L.sLa;
   int phx = -1, phy = -1;
@@ -1479,8 +1484,16 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       prv = FrameRef{d.frame, d.pitch, ch};
     }
     const FrameRef curf{cur.frame, cur.pitch, ch};
-    const unsigned char* rawc = L.raw + rb * SH * RW;
-    const unsigned char* rawp = L.raw + (1 - rb) * SH * RW;
+    const unsigned char* rawc = L.raw + (SPARSE ? rb : (fi + 1) % 3) * SH * RW;
+    const unsigned char* rawp = L.raw + (SPARSE ? 1 - rb : fi % 3) * SH * RW;
+    // dense: the next frame's bytes and flow, into the buffers of frames
+    // i - 2 and i - 1 (read for the last time during frame i - 1)
+    if (!SPARSE && fi + 1 < count) {
+      const FrameDesc nd = s_desc[(fi + 1) & 3];
+      stage_raw<TH_>(L.raw + ((fi + 2) % 3) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H,
+                     tx0, ty0);
+      stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
+    }
     const int chp = fi == 0 ? 1 : ch;  // the ring holds luma
     const int N = s_N[par];
     const unsigned mN = s_mN[par];
@@ -1639,13 +1652,17 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     __syncthreads();
     if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
 
-    // 3. the next frame's inputs: its bytes over the previous frame's raw
-    // buffer (read by now), its flow, the descriptor two frames ahead; its
-    // substep tables
+    // 3. the next frame's inputs (sparse: its bytes over the previous
+    // frame's raw buffer, read by now, and its flow; dense: staged at the
+    // start of the frame), the descriptor two frames ahead; its substep
+    // tables
     if (fi + 1 < count) {
       const FrameDesc nd = s_desc[(fi + 1) & 3];
-      stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
-      stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
+      if (SPARSE) {
+        stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0,
+                       ty0);
+        stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
+      }
       if (fi + 2 < count && tid < 2) {
         // descriptors are 32-byte, 16-byte aligned records
         cp_async16(smem_addr(&s_desc[(fi + 2) & 3]) + 16u * tid,
