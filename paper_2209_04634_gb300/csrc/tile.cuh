@@ -1226,7 +1226,7 @@ struct BatchLayout {
   int* sR;              // [TP] sparse
   unsigned* stk;        // [2][nmax] substep times (frame parity)
   int* swk;             // [2][nmax] substep weights
-  unsigned char* raw;   // [2 sparse, 3 dense][SH][SW * ch]
+  unsigned char* raw;   // [2][SH][SW * ch]
   short* snk;           // [nmax][TP] sparse
   short* sslot;         // [TP] sparse
   unsigned short* sCp;  // [TP] sparse maps
@@ -1237,7 +1237,7 @@ __host__ __device__ inline size_t batch_smem_bytes(int n_max, int ch, bool spars
   const int TP = TW * th, SH = th + 2 * HMAX;
   size_t b = (size_t)2 * TP * sizeof(float2);
   b += (size_t)(2 * SH * SW + 256 + (sparse ? TP : 0) + 4 * n_max) * 4;
-  b += (size_t)(sparse ? 2 : 3) * SH * SW * ch;  // raw frame buffers
+  b += (size_t)2 * SH * SW * ch;
   if (sparse) b += (size_t)(n_max * TP + 3 * TP) * 2;
   return b;
 }
@@ -1255,7 +1255,7 @@ __device__ __forceinline__ BatchLayout batch_layout(unsigned char* base, int nma
   L.stk = (unsigned*)(L.sR + (SPARSE ? TP : 0));
   L.swk = (int*)(L.stk + 2 * nmax);
   L.raw = (unsigned char*)(L.swk + 2 * nmax);
-  L.snk = (short*)(L.raw + (SPARSE ? 2 : 3) * SH * SW * ch);
+  L.snk = (short*)(L.raw + 2 * SH * SW * ch);
   L.sslot = L.snk + nmax * TP;
   L.sCp = (unsigned short*)(L.sslot + TP);
   L.sCn = L.sCp + TP;
@@ -1358,16 +1358,25 @@ __device__ __forceinline__ void substep_tables(const SimParams& p, unsigned long
                                                unsigned* stk, int* sN, unsigned* smN,
                                                unsigned* cmask) {
   const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(maxf2, p.n_max);
-  if ((int)threadIdx.x < N) {
-    const int k = threadIdx.x + 1;
-    swk[threadIdx.x] = (k * 8192 + N) / (2 * N);
-    stk[threadIdx.x] = (unsigned)(t_prev + (k * (t_cur - t_prev)) / N);
-    if (N <= 32) {  // carry table of remainder r = threadIdx.x
-      const int r = threadIdx.x;
+  const int t = threadIdx.x;
+  if (t < N) {
+    const int k = t + 1;
+    swk[t] = (k * 8192 + N) / (2 * N);
+    // k dt / N (dt > 0): a 32-bit division when the product fits
+    const unsigned long long kd = (unsigned long long)k * (unsigned long long)(t_cur - t_prev);
+    const unsigned long long q = kd < 0x100000000ull ? (unsigned)kd / (unsigned)N : kd / (unsigned)N;
+    stk[t] = (unsigned)(t_prev + (long long)q);
+    if (N <= 32) {  // carry table of remainder r = t: (r j) mod N stepped without divisions
       unsigned m = 0;
-      for (int j = 1; j <= N; ++j)
-        if ((r * j) / N != (r * (j - 1)) / N) m |= 1u << (32 - j);
-      cmask[r] = m;
+      int acc = 0;
+      for (int j = 1; j <= N; ++j) {
+        acc += t;
+        if (acc >= N) {
+          acc -= N;
+          m |= 1u << (32 - j);
+        }
+      }
+      cmask[t] = m;
     }
   }
   if (threadIdx.x == 0) {
@@ -1382,7 +1391,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   (void)TH; (void)NTD; (void)TP; (void)SH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_warp[NTD / 32 + 1];
-  __shared__ int s_fx, s_fy;
+  __shared__ int s_fx[2], s_fy[2];  // the tile's flow reach, per frame parity
   __shared__ int s_rs[TH + 1];
   __shared__ int s_N[2];
   __shared__ unsigned s_mN[2];
@@ -1445,7 +1454,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     s_desc[tid] = b.frames[tid];
     s_mf[tid] = adaptive ? p.maxf2[tid] : 0ull;
   }
-  if (tid == 0) { s_fx = 0; s_fy = 0; }
+  if (tid < 2) { s_fx[tid] = 0; s_fy[tid] = 0; }
   __syncthreads();
   {
     const FrameRef ring{ringp, (long long)W, 1};
@@ -1462,12 +1471,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
 
   int clamps = 0;
   long long act_sum = 0, act_n = 0;
-  // raw frame buffers: sparse instances two (rb holds the current frame, 1 - rb
-  // the previous one, the next frame is staged over the previous one after
-  // its last read, mid-frame); dense instances three (frame f in buffer
-  // (f + 1) mod 3, the next frame staged at the start of each frame, so its
-  // copies overlap the whole frame's work)
-  int rb = 1;
+  int rb = 1;  // raw buffer of the current frame; 1 - rb holds the previous frame
   int* cb = L.sLb;
   int* pb = L.sLa;
   int phx = -1, phy = -1;
@@ -1484,16 +1488,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       prv = FrameRef{d.frame, d.pitch, ch};
     }
     const FrameRef curf{cur.frame, cur.pitch, ch};
-    const unsigned char* rawc = L.raw + (SPARSE ? rb : (fi + 1) % 3) * SH * RW;
-    const unsigned char* rawp = L.raw + (SPARSE ? 1 - rb : fi % 3) * SH * RW;
-    // dense: the next frame's bytes and flow, into the buffers of frames
-    // i - 2 and i - 1 (read for the last time during frame i - 1)
-    if (!SPARSE && fi + 1 < count) {
-      const FrameDesc nd = s_desc[(fi + 1) & 3];
-      stage_raw<TH_>(L.raw + ((fi + 2) % 3) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H,
-                     tx0, ty0);
-      stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
-    }
+    const unsigned char* rawc = L.raw + rb * SH * RW;
+    const unsigned char* rawp = L.raw + (1 - rb) * SH * RW;
     const int chp = fi == 0 ? 1 : ch;  // the ring holds luma
     const int N = s_N[par];
     const unsigned mN = s_mN[par];
@@ -1625,11 +1621,14 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     mfx = __reduce_max_sync(FULL, mfx);
     mfy = __reduce_max_sync(FULL, mfy);
     if (lane == 0) {
-      atomicMax(&s_fx, (int)mfx);
-      atomicMax(&s_fy, (int)mfy);
+      atomicMax(&s_fx[par], (int)mfx);
+      atomicMax(&s_fy[par], (int)mfy);
     }
     const bool busy = __syncthreads_or(quiet ? 0 : 1) != 0;
-    const int hx = (s_fx >> 16) + 1, hy = (s_fy >> 16) + 1;
+    const int hx = (s_fx[par] >> 16) + 1, hy = (s_fy[par] >> 16) + 1;
+    // the other parity's maxima (read during the previous frame, before its
+    // closing barrier) start the next frame from zero
+    if (tid == 0) { s_fx[par ^ 1] = 0; s_fy[par ^ 1] = 0; }
     const bool fast = hx <= HMAX && hy <= HMAX;
     // sparse fast path: row masks in the current flow buffer (its flows are
     // in registers by now), cleared here
@@ -1649,20 +1648,17 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       }
       fill_halo_raw<TH_>(cb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy, ctl);
     }
-    __syncthreads();
-    if (tid == 0) { s_fx = 0; s_fy = 0; }  // hx, hy are read by now
+    // the halos (and, sparse, the cleared row masks) are complete before any
+    // substep reads them; a dense tile that built no halo needs no barrier
+    if (SPARSE || (fast && busy)) __syncthreads();
 
-    // 3. the next frame's inputs (sparse: its bytes over the previous
-    // frame's raw buffer, read by now, and its flow; dense: staged at the
-    // start of the frame), the descriptor two frames ahead; its substep
-    // tables
+    // 3. the next frame's inputs: its bytes over the previous frame's raw
+    // buffer (read by now), its flow, the descriptor two frames ahead; its
+    // substep tables
     if (fi + 1 < count) {
       const FrameDesc nd = s_desc[(fi + 1) & 3];
-      if (SPARSE) {
-        stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0,
-                       ty0);
-        stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
-      }
+      stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
+      stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
       if (fi + 2 < count && tid < 2) {
         // descriptors are 32-byte, 16-byte aligned records
         cp_async16(smem_addr(&s_desc[(fi + 2) & 3]) + 16u * tid,
