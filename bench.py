@@ -213,7 +213,7 @@ class ClockSampler:
 
 KERNEL_SOURCES = {  # kernel kind -> the sources that define it
     "dense": ("internal.h", "tile.cuh", "tile_dense.cu"),
-    "sparse": ("internal.h", "tile.cuh", "tile_sparse.cu"),
+    "sparse": ("internal.h", "tile.cuh", "tile_dense.cu", "tile_sparse.cu"),
     "order": ("internal.h", "tile.cuh", "kernels.cu"),
     "mask": ("internal.h", "tile.cuh", "kernels.cu"),
     "flowmax": ("internal.h", "tile.cuh", "kernels.cu"),

@@ -465,21 +465,33 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
   // warp's loads are contiguous) into the chunk's arrays, then scanned with
   // each thread owning OSEG consecutive segments
   if (tid == 0) o.ncblk = 0;
+  // the chunk's first segment: frame-substep q0, row-segment rs0, frame fi0;
+  // a segment ls of the chunk lies (rs0 + ls) / S frame-substeps further
+  // (32-bit: S and OCHUNK are far below 2^31) and a few frames at most
+  const long long si0 = (long long)c * OCHUNK;
+  const long long q0 = si0 / S;
+  const int rs0 = (int)(si0 - q0 * S);
+  int fi0 = 0;
+  {
+    int hi = b.count;
+    while (hi - fi0 > 1) {
+      const int mid = (fi0 + hi) >> 1;
+      if (o.FN[mid] <= q0) fi0 = mid; else hi = mid;
+    }
+  }
 #pragma unroll
   for (int u = 0; u < OSEG; ++u) {
     const int ls = u * NT + tid;  // segment of the chunk
-    const long long si = (long long)c * OCHUNK + ls;
+    const long long si = si0 + ls;
     int cnt = 0, src = -1;
     unsigned long long mask = 0, pol = 0;
     unsigned tk = 0, xy = 0;
     if (si < nlive) {
-      const long long q = si / S;  // frame-substep of the batch
-      const int rs = (int)(si - q * S);
-      int fi = 0, hi = b.count;
-      while (hi - fi > 1) {
-        const int mid = (fi + hi) >> 1;
-        if (o.FN[mid] <= q) fi = mid; else hi = mid;
-      }
+      const unsigned dq = (unsigned)(rs0 + ls) / (unsigned)S;
+      const long long q = q0 + dq;  // frame-substep of the batch
+      const int rs = rs0 + ls - (int)(dq * (unsigned)S);
+      int fi = fi0;
+      while (o.FN[fi + 1] <= q) ++fi;  // FN[count] exceeds every live q
       const int k = (int)(q - o.FN[fi]);
       const int N = o.N[fi];
       // a unit-frame of the row kernel that emitted nothing wrote a flag
@@ -497,7 +509,10 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
       xy = (unsigned)(tc * TW) | ((unsigned)y << 16);
       const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
       const long long dt = b.frames[fi].t_rel - tp;
-      tk = (unsigned)(tp + ((long long)(k + 1) * dt) / N);
+      // (k + 1) dt / N (dt > 0): a 32-bit division when the product fits
+      const unsigned long long kd = (unsigned long long)(k + 1) * (unsigned long long)dt;
+      tk = (unsigned)(tp + (long long)(kd < 0x100000000ull ? (unsigned)kd / (unsigned)N
+                                                              : kd / (unsigned)N));
     }
     o.ex[ls] = cnt;
     o.src[ls] = src;

@@ -1206,11 +1206,48 @@ __device__ __forceinline__ void cp_async8(unsigned dst, const void* src) {
 __device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// 16-byte copy of which the first src_bytes (0..16) are read, the rest of
+// the destination zero-filled.
+__device__ __forceinline__ void cp_async16z(unsigned dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// The batch kernel's rarely taken substep loops, out of line: the general
+// loop (frames whose flow reach exceeds the shared halo; sparse tiles
+// without the fast path) and the dense loop for N > 32 (no carry tables).
+// Inlined, their registers would weigh on the allocation of the whole
+// kernel, and the spills that follow reach the per-frame path that every
+// frame runs.  The per-pixel arrays travel in one record (local memory of
+// the calling thread, on these paths only); R comes back through it.
+struct PixArgs {
+  int lx[2], ly[2], nk[2], Fx[2], Fy[2], R[2], Cp[2], Cn[2];
+  bool act[2];
+};
+
+template <bool RESET, bool WIDE, bool FAST, bool DENSE, int TH_>
+__device__ __noinline__ void tile_substeps_cold(const SimParams p, const TileLayout V, int N,
+                                                unsigned mN, int tx0, int ty0, unsigned b0,
+                                                unsigned b1, const FrameRef prv,
+                                                const FrameDesc cur, Seg* segf, PixArgs& a,
+                                                WarpStage* ws) {
+  tile_substeps<RESET, WIDE, FAST, DENSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf, a.lx,
+                                               a.ly, a.nk, a.act, a.Fx, a.Fy, a.R, a.Cp, a.Cn, ws);
+}
+
+template <bool RESET, bool WIDE, bool FULLT>
+__device__ __noinline__ void dense_substeps_cold(const SimParams p, const int* swk,
+                                                 const unsigned* stk, int N, unsigned mN, int tx0,
+                                                 int y, unsigned b0, unsigned b1, Seg* segr,
+                                                 WarpStage* ws, PixArgs& a) {
+  dense_substeps<RESET, WIDE, FULLT, false>(p, swk, stk, nullptr, N, mN, tx0, y, b0, b1, segr, ws,
+                                            a.act, a.Fx, a.Fy, a.R, a.Cp, a.Cn);
 }
 
 // Shared memory of the batch kernel.  `raw` holds two frames' bytes over the
@@ -1224,8 +1261,6 @@ struct BatchLayout {
   int* sLb;
   int* slut;
   int* sR;              // [TP] sparse
-  unsigned* stk;        // [2][nmax] substep times (frame parity)
-  int* swk;             // [2][nmax] substep weights
   unsigned char* raw;   // [2][SH][SW * ch]
   short* snk;           // [nmax][TP] sparse
   short* sslot;         // [TP] sparse
@@ -1236,7 +1271,7 @@ struct BatchLayout {
 __host__ __device__ inline size_t batch_smem_bytes(int n_max, int ch, bool sparse, int th) {
   const int TP = TW * th, SH = th + 2 * HMAX;
   size_t b = (size_t)2 * TP * sizeof(float2);
-  b += (size_t)(2 * SH * SW + 256 + (sparse ? TP : 0) + 4 * n_max) * 4;
+  b += (size_t)(2 * SH * SW + 256 + (sparse ? TP : 0)) * 4;
   b += (size_t)2 * SH * SW * ch;
   if (sparse) b += (size_t)(n_max * TP + 3 * TP) * 2;
   return b;
@@ -1252,9 +1287,7 @@ __device__ __forceinline__ BatchLayout batch_layout(unsigned char* base, int nma
   L.sLb = L.sLa + SH * SW;
   L.slut = L.sLb + SH * SW;
   L.sR = L.slut + 256;
-  L.stk = (unsigned*)(L.sR + (SPARSE ? TP : 0));
-  L.swk = (int*)(L.stk + 2 * nmax);
-  L.raw = (unsigned char*)(L.swk + 2 * nmax);
+  L.raw = (unsigned char*)(L.sR + (SPARSE ? TP : 0));  // 16-byte aligned, at a fixed offset
   L.snk = (short*)(L.raw + 2 * SH * SW * ch);
   L.sslot = L.snk + nmax * TP;
   L.sCp = (unsigned short*)(L.sslot + TP);
@@ -1277,7 +1310,19 @@ __device__ __forceinline__ void stage_raw(unsigned char* raw, const FrameRef& f,
   const int b0 = (cx0 - (tx0 - HMAX)) * ch;  // byte offset of column cx0 in a window row
   const int nb = (cx1 - cx0) * ch;            // bytes per row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if ((((unsigned long long)f.ptr | (unsigned long long)f.pitch) & 3) == 0) {
+  if ((((unsigned long long)f.ptr | (unsigned long long)f.pitch) & 15) == 0) {
+    // cx0 * ch and every window row's start in raw are multiples of 16
+    // bytes, so each 16-byte chunk is aligned on both sides; the last chunk
+    // of a row reads only the row's remaining bytes and zero-fills the rest,
+    // which stays inside the window row (its stride is a multiple of 16)
+    const int nw = (nb + 15) >> 4;
+    const unsigned dst0 = smem_addr(raw) + (unsigned)b0;
+    for (int r = r0 + warp; r < r1; r += NTD / 32) {
+      const unsigned char* src = f.ptr + (long long)(ty0 - HMAX + r) * f.pitch + (long long)cx0 * ch;
+      for (int w = lane; w < nw; w += 32)
+        cp_async16z(dst0 + (unsigned)(r * RW + 16 * w), src + 16 * w, min(16, nb - 16 * w));
+    }
+  } else if ((((unsigned long long)f.ptr | (unsigned long long)f.pitch) & 3) == 0) {
     // cx0 * ch is a multiple of 16, so every word starts 4-byte aligned; the
     // last word of a row copies only the row's remaining bytes (zero fill
     // within the window row)
@@ -1305,6 +1350,16 @@ __device__ __forceinline__ void stage_flow(float2* sf, const float2* flow, int W
   (void)TH; (void)NTD; (void)TP; (void)SH;
   const bool al = ((unsigned long long)flow & 7) == 0;
   const unsigned d0 = smem_addr(sf);
+  if (((unsigned long long)flow & 15) == 0 && (W & 1) == 0) {
+    // pixel pairs (2t, 2t + 1) of a tile row: both in the image or both
+    // out (x even, W even), 16-byte aligned in the flow and in sf
+    static_assert(TP / 2 == NTD, "one pixel pair per thread");
+    const int t = threadIdx.x;
+    const int lx = (2 * t) & (TW - 1), ly = (2 * t) / TW;
+    const int x = tx0 + lx, y = ty0 + ly;
+    if (x < W && y < H) cp_async16(d0 + (unsigned)t * 16u, flow + (long long)y * W + x);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < TP / NTD; ++q) {
     const int t = threadIdx.x + q * NTD;
@@ -1349,37 +1404,44 @@ __device__ __forceinline__ void fill_halo_raw(int* dst, const int* slut, const u
   }
 }
 
-// Substep weights and times of one frame (threads k < N) into the parity's
-// tables, and for N <= 32 its carry table (dense_substeps); thread 0
-// publishes N and its division multiplier (divmod_n).  Called by threads
-// 0..63 only.
+// Substep tables of one frame into a frame parity's buffers, by warp 0:
+// the substep times (lanes t < N), and - only when N differs from the N
+// these buffers last held, since they depend on N alone - the substep
+// weights, for N <= 32 the carry table (dense_substeps), and N with its
+// division multiplier (divmod_n).  *sN is read by the whole warp before
+// lane 0 rewrites it.
 __device__ __forceinline__ void substep_tables(const SimParams& p, unsigned long long maxf2,
                                                long long t_prev, long long t_cur, int* swk,
                                                unsigned* stk, int* sN, unsigned* smN,
                                                unsigned* cmask) {
   const int N = p.n_fixed > 0 ? p.n_fixed : adaptive_n(maxf2, p.n_max);
-  const int t = threadIdx.x;
-  if (t < N) {
+  const int lane = threadIdx.x & 31;
+  const bool same = *sN == N;
+  __syncwarp();
+  const unsigned long long dt = (unsigned long long)(t_cur - t_prev);
+  for (int t = lane; t < N; t += 32) {
     const int k = t + 1;
-    swk[t] = (k * 8192 + N) / (2 * N);
     // k dt / N (dt > 0): a 32-bit division when the product fits
-    const unsigned long long kd = (unsigned long long)k * (unsigned long long)(t_cur - t_prev);
+    const unsigned long long kd = (unsigned long long)k * dt;
     const unsigned long long q = kd < 0x100000000ull ? (unsigned)kd / (unsigned)N : kd / (unsigned)N;
     stk[t] = (unsigned)(t_prev + (long long)q);
-    if (N <= 32) {  // carry table of remainder r = t: (r j) mod N stepped without divisions
-      unsigned m = 0;
-      int acc = 0;
-      for (int j = 1; j <= N; ++j) {
-        acc += t;
-        if (acc >= N) {
-          acc -= N;
-          m |= 1u << (32 - j);
+    if (!same) {
+      swk[t] = (k * 8192 + N) / (2 * N);
+      if (N <= 32) {  // carry table of remainder r = t: (r j) mod N stepped without divisions
+        unsigned m = 0;
+        int acc = 0;
+        for (int j = 1; j <= N; ++j) {
+          acc += t;
+          if (acc >= N) {
+            acc -= N;
+            m |= 1u << (32 - j);
+          }
         }
+        cmask[t] = m;
       }
-      cmask[t] = m;
     }
   }
-  if (threadIdx.x == 0) {
+  if (lane == 0 && !same) {
     *sN = N;
     *smN = N > 1 ? (unsigned)(0x100000000ull / (unsigned)N) + 1u : 0u;
   }
@@ -1394,6 +1456,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   __shared__ int s_fx[2], s_fy[2];  // the tile's flow reach, per frame parity
   __shared__ int s_rs[TH + 1];
   __shared__ int s_N[2];
+  __shared__ unsigned s_stk[2][MAXN];  // substep times and weights of the frame parities
+  __shared__ int s_swk[2][MAXN];
   __shared__ unsigned s_mN[2];
   __shared__ unsigned s_cmask[2][32];  // carry tables of the frame parities
   __shared__ unsigned s_multi[32];  // sparse: rows with multi-crossings, per substep
@@ -1418,11 +1482,11 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   const bool spm = !SPARSE && p.mode == SIM_SPARSE;
 
   if (tid < 256) L.slut[tid] = p.lut[tid];
+  // the state buffers' double-buffer selector; the pointers are formed where
+  // they are used (kept live across the frame loop they cost registers)
   const int sel = ctl->sel;
   const int* Rin = (sel & 1) ? p.R1 : p.R0;
-  int* Rout = (sel & 1) ? p.R0 : p.R1;
   const unsigned char* ringp = (sel & 2) ? p.ring1 : p.ring0;
-  unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
   const long long t_first = ctl->t_prev;
 
   // Dense: thread (warp w, lane l) owns tile pixels (l, w) and (l + 32, w);
@@ -1454,7 +1518,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     s_desc[tid] = b.frames[tid];
     s_mf[tid] = adaptive ? p.maxf2[tid] : 0ull;
   }
-  if (tid < 2) { s_fx[tid] = 0; s_fy[tid] = 0; }
+  if (tid < 2) { s_fx[tid] = 0; s_fy[tid] = 0; s_N[tid] = 0; }
   __syncthreads();
   {
     const FrameRef ring{ringp, (long long)W, 1};
@@ -1463,17 +1527,16 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     stage_raw<TH_>(L.raw + SH * RW, FrameRef{d0.frame, d0.pitch, ch}, W, H, tx0, ty0);
     stage_flow<TH_>(L.sflow, d0.flow, W, H, tx0, ty0);
     cp_async_commit();
-    if (tid < 64)
-      substep_tables(p, s_mf[0], t_first, d0.t_rel, L.swk, L.stk, &s_N[0], &s_mN[0], s_cmask[0]);
+    if (warp == 0)
+      substep_tables(p, s_mf[0], t_first, d0.t_rel, s_swk[0], s_stk[0], &s_N[0], &s_mN[0], s_cmask[0]);
     cp_async_wait_all();
   }
   __syncthreads();
 
   int clamps = 0;
-  long long act_sum = 0, act_n = 0;
+  unsigned act_sum = 0, act_n = 0;  // < 2^26: at most 1024 pixels x 64 substeps x 1024 frames
   int rb = 1;  // raw buffer of the current frame; 1 - rb holds the previous frame
-  int* cb = L.sLb;
-  int* pb = L.sLa;
+  int hsel = 0;  // halo of the current frame: sLb (0) or sLa (1); the other holds frame i-1
   int phx = -1, phy = -1;
   int hfx = 1, hfy = 1;  // halo extents only grow within a batch
 
@@ -1482,7 +1545,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     const FrameDesc cur = s_desc[fi & 3];
     FrameRef prv;
     if (fi == 0) {
-      prv = FrameRef{ringp, (long long)W, 1};
+      prv = FrameRef{(sel & 2) ? p.ring1 : p.ring0, (long long)W, 1};
     } else {
       const FrameDesc d = s_desc[(fi - 1) & 3];
       prv = FrameRef{d.frame, d.pitch, ch};
@@ -1494,6 +1557,80 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     const int N = s_N[par];
     const unsigned mN = s_mN[par];
     Seg* segf = p.seg + (long long)fi * nmax * p.segs_per_k + (long long)ty0 * p.tiles_x + tcx;
+    auto stage_next = [&]() {
+      if (fi + 1 < count) {
+        const FrameDesc nd = s_desc[(fi + 1) & 3];
+        stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
+        stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
+        if (fi + 2 < count && tid < 2) {
+          // descriptors are 32-byte, 16-byte aligned records
+          cp_async16(smem_addr(&s_desc[(fi + 2) & 3]) + 16u * tid,
+                     (const unsigned char*)&b.frames[fi + 2] + 16 * tid);
+          if (tid == 0 && adaptive) cp_async8(smem_addr(&s_mf[(fi + 2) & 3]), &p.maxf2[fi + 2]);
+        }
+        cp_async_commit();
+        if (warp == 0)
+          substep_tables(p, s_mf[(fi + 1) & 3], cur.t_rel, nd.t_rel, s_swk[par ^ 1], s_stk[par ^ 1],
+                         &s_N[par ^ 1], &s_mN[par ^ 1], s_cmask[par ^ 1]);
+      }
+    };
+
+    // 0. quiet frame (dense mapping, segment flags on): when every simulated
+    // pixel of the tile has an exactly zero flow and both end values strictly
+    // inside its threshold band (reset mode: a change within both
+    // thresholds), the frame emits nothing and leaves every reference as it
+    // was; the tile flags its rows empty, stages the next frame and moves
+    // on.  A sufficient test: flows that round to zero in Q16 without being
+    // zero take the full path below, which applies the exact test.
+    if (!SPARSE && !XT && p.segflag) {
+      const float2* sfq = L.sflow + par * TP;
+      bool calm = true;
+      bool av[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        av[q] = false;
+        if (!inimg[q]) continue;
+        const int qx = lane + 32 * q + HMAX, qy = warp + HMAX;
+        const int Lp = L.slut[raw_luma(rawp, chp, qy, qx)];
+        const int Lc = L.slut[raw_luma(rawc, ch, qy, qx)];
+        const int cp = MAPS ? Cpd[q] : p.cp, cn = MAPS ? Cnd[q] : p.cn;
+        av[q] = !spm || abs(Lc - Lp) >= activity_threshold(p, cp, cn);
+        if (!av[q]) continue;  // sparse: an inactive pixel keeps R and emits nothing
+        const float2 fl = sfq[own[q]];
+        const bool still = ((__float_as_uint(fl.x) | __float_as_uint(fl.y)) << 1) == 0u;
+        const bool band = RESET ? (Lc - Lp <= cp && Lp - Lc <= cn)
+                                : (max(Lp, Lc) - Rd[q] < cp && Rd[q] - min(Lp, Lc) < cn);
+        calm = calm && still && band;
+      }
+      if (!__syncthreads_or(calm ? 0 : 1)) {
+        if (fi == count - 1) {  // the last frame's luma into the ring
+          unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            if (!inimg[q]) continue;
+            const long long ri = (long long)(ty0 + warp) * W + tx0 + lane + 32 * q;
+            if (in_bounds(p.ctl, ri, (long long)p.W * p.H))
+              ringn[ri] = (unsigned char)raw_luma(rawc, ch, warp + HMAX, lane + 32 * q + HMAX);
+          }
+        }
+        if (spm) {
+          const int na = __popc(__ballot_sync(FULL, av[0])) + __popc(__ballot_sync(FULL, av[1]));
+          act_sum += na;
+          act_n += na * N;
+        }
+        if (tid == 0) { s_fx[par ^ 1] = 0; s_fy[par ^ 1] = 0; }
+        stage_next();
+        if (ty0 + warp < H && lane == 0)
+          if (in_bounds(p.ctl, (long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx, p.seg_cap / p.n_max))
+            p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 0;
+        phx = -1;
+        phy = -1;
+        rb = 1 - rb;
+        cp_async_wait_all();
+        __syncthreads();
+        continue;
+      }
+    }
 
     // 1. the pixels to simulate (the previous and current bytes are staged);
     // spm: a sparse stream run by this dense instance - each pixel's
@@ -1508,6 +1645,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         const int vc = raw_luma(rawc, ch, ly + HMAX, lx + HMAX);
         if (fi == count - 1) {
           const long long ri = (long long)(ty0 + ly) * W + tx0 + lx;
+          unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
           if (in_bounds(p.ctl, ri, (long long)p.W * p.H)) ringn[ri] = (unsigned char)vc;
         }
         if (SPARSE || spm) {
@@ -1539,12 +1677,12 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     }
     if (SPARSE) {
       act_sum += A;
-      act_n += (long long)A * N;
+      act_n += A * N;
     } else if (spm) {  // per warp; lane 0 adds the warp's count at the end
       const int na = __popc(__ballot_sync(FULL, sel_flag[0] != 0)) +
                      __popc(__ballot_sync(FULL, sel_flag[1] != 0));
       act_sum += na;
-      act_n += (long long)na * N;
+      act_n += na * N;
     }
     // sparse tiles with at least 3/8 of their pixels active run the frame
     // through the dense loop (inactive pixels masked, their reference kept):
@@ -1642,11 +1780,11 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       hfx = max(hfx, hx);
       hfy = max(hfy, hy);
       if (phx < hx || phy < hy) {  // the kept halo of frame i-1 does not reach far enough
-        fill_halo_raw<TH_>(pb, L.slut, rawp, chp, W, H, tx0, ty0, hfx, hfy, ctl);
+        fill_halo_raw<TH_>(hsel ? L.sLb : L.sLa, L.slut, rawp, chp, W, H, tx0, ty0, hfx, hfy, ctl);
         phx = hfx;
         phy = hfy;
       }
-      fill_halo_raw<TH_>(cb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy, ctl);
+      fill_halo_raw<TH_>(hsel ? L.sLa : L.sLb, L.slut, rawc, ch, W, H, tx0, ty0, hfx, hfy, ctl);
     }
     // the halos (and, sparse, the cleared row masks) are complete before any
     // substep reads them; a dense tile that built no halo needs no barrier
@@ -1655,31 +1793,17 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     // 3. the next frame's inputs: its bytes over the previous frame's raw
     // buffer (read by now), its flow, the descriptor two frames ahead; its
     // substep tables
-    if (fi + 1 < count) {
-      const FrameDesc nd = s_desc[(fi + 1) & 3];
-      stage_raw<TH_>(L.raw + (1 - rb) * SH * RW, FrameRef{nd.frame, nd.pitch, ch}, W, H, tx0, ty0);
-      stage_flow<TH_>(L.sflow + (par ^ 1) * TP, nd.flow, W, H, tx0, ty0);
-      if (fi + 2 < count && tid < 2) {
-        // descriptors are 32-byte, 16-byte aligned records
-        cp_async16(smem_addr(&s_desc[(fi + 2) & 3]) + 16u * tid,
-                   (const unsigned char*)&b.frames[fi + 2] + 16 * tid);
-        if (tid == 0 && adaptive) cp_async8(smem_addr(&s_mf[(fi + 2) & 3]), &p.maxf2[fi + 2]);
-      }
-      cp_async_commit();
-      if (tid < 64)
-        substep_tables(p, s_mf[(fi + 1) & 3], cur.t_rel, nd.t_rel, L.swk + (par ^ 1) * nmax,
-                       L.stk + (par ^ 1) * nmax, &s_N[par ^ 1], &s_mN[par ^ 1], s_cmask[par ^ 1]);
-    }
+    stage_next();
 
     // 4. substeps (sparse: warps without a compacted pixel skip them); dense
     // rows publish their segments from the loop
     TileLayout V;
     V.slut = L.slut;
-    V.stk = L.stk + par * nmax;
-    V.swk = L.swk + par * nmax;
+    V.stk = s_stk[par];
+    V.swk = s_swk[par];
     V.snk = L.snk;
-    const unsigned b0 = smem_addr(pb);
-    const unsigned b1 = smem_addr(cb);
+    const unsigned b0 = smem_addr(hsel ? L.sLb : L.sLa);
+    const unsigned b1 = smem_addr(hsel ? L.sLa : L.sLb);
     if (XT) {
       const unsigned t_frame = (unsigned)(fi == 0 ? t_first : s_desc[(fi - 1) & 3].t_rel);
       if (SPARSE && A == 0) {  // warp-uniform: nothing simulated, empty segments
@@ -1721,16 +1845,24 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       if (ty0 + warp < H && !skip) {  // warp-uniform: rows below the image publish nothing
         // the row's 64 pixels are in the image (and, sparse, all simulated)
         const bool fullt = !SPARSE && !spm && tx0 + TW <= W;
-#define EVSIM_DENSE(FT, MK)                                                                    \
-  dense_substeps<RESET, WIDE, FT, MK>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp, b0, \
-                                      b1, segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy,  \
-                                      R, Cp, Cn)
+#define EVSIM_DENSE(FT)                                                                        \
+  dense_substeps<RESET, WIDE, FT, true>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp, b0, \
+                                        b1, segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy,  \
+                                        R, Cp, Cn)
         if (N <= 32) {
-          if (fullt) EVSIM_DENSE(true, true);
-          else EVSIM_DENSE(false, true);
+          if (fullt) EVSIM_DENSE(true);
+          else EVSIM_DENSE(false);
         } else {
-          if (fullt) EVSIM_DENSE(true, false);
-          else EVSIM_DENSE(false, false);
+          PixArgs a{{lx[0], lx[1]}, {ly[0], ly[1]}, {nk_at[0], nk_at[1]}, {Fx[0], Fx[1]},
+                    {Fy[0], Fy[1]}, {R[0], R[1]}, {Cp[0], Cp[1]}, {Cn[0], Cn[1]}, {act[0], act[1]}};
+          if (fullt)
+            dense_substeps_cold<RESET, WIDE, true>(p, V.swk, V.stk, N, mN, tx0, ty0 + warp, b0, b1,
+                                                   segf + warp * p.tiles_x, &s_stage[warp], a);
+          else
+            dense_substeps_cold<RESET, WIDE, false>(p, V.swk, V.stk, N, mN, tx0, ty0 + warp, b0, b1,
+                                                    segf + warp * p.tiles_x, &s_stage[warp], a);
+          R[0] = a.R[0];
+          R[1] = a.R[1];
         }
 #undef EVSIM_DENSE
       }
@@ -1747,14 +1879,16 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       if (!SPARSE && p.segflag && ty0 + warp < H && lane == 0)  // every row simulated
         if (in_bounds(p.ctl, (long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx, p.seg_cap / p.n_max))
           p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] = 1;
+      PixArgs a{{lx[0], lx[1]}, {ly[0], ly[1]}, {nk_at[0], nk_at[1]}, {Fx[0], Fx[1]},
+                {Fy[0], Fy[1]}, {R[0], R[1]}, {Cp[0], Cp[1]}, {Cn[0], Cn[1]}, {act[0], act[1]}};
       if (fast)
-        tile_substeps<RESET, WIDE, true, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
-                                                  lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
-                                                  &s_stage[warp]);
+        tile_substeps_cold<RESET, WIDE, true, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur,
+                                                            segf, a, &s_stage[warp]);
       else
-        tile_substeps<RESET, WIDE, false, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur, segf,
-                                                   lx, ly, nk_at, act, Fx, Fy, R, Cp, Cn,
-                                                   &s_stage[warp]);
+        tile_substeps_cold<RESET, WIDE, false, !SPARSE, TH_>(p, V, N, mN, tx0, ty0, b0, b1, prv, cur,
+                                                             segf, a, &s_stage[warp]);
+      R[0] = a.R[0];
+      R[1] = a.R[1];
     }
     if (!RESET) {
 #pragma unroll
@@ -1820,9 +1954,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     }
     // frame i's halo becomes the previous-frame halo of frame i + 1
     if (fast && A > 0 && busy) {
-      int* t = pb;
-      pb = cb;
-      cb = t;
+      hsel ^= 1;
       phx = hfx;
       phy = hfy;
     } else {
@@ -1835,6 +1967,7 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
   }
 
   if (!RESET) {
+    int* Rout = (sel & 1) ? p.R0 : p.R1;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!inimg[q]) continue;
