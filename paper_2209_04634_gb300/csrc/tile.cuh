@@ -1314,13 +1314,26 @@ __device__ __forceinline__ void stage_raw(unsigned char* raw, const FrameRef& f,
     // cx0 * ch and every window row's start in raw are multiples of 16
     // bytes, so each 16-byte chunk is aligned on both sides; the last chunk
     // of a row reads only the row's remaining bytes and zero-fills the rest,
-    // which stays inside the window row (its stride is a multiple of 16)
+    // which stays inside the window row (its stride is a multiple of 16).
+    // The window's chunks are dealt to the block's threads as one flat list
+    // (at most SH x 18 < 1024 chunks: one or two per thread), the chunk's row
+    // e / nw taken as (e * (floor(2^16 / nw) + 1)) >> 16, exact for e < 1024
+    // and nw <= 18 (the error stays below 1024 / 2^16 < 1 / nw; checked
+    // exhaustively).  A loop of a warp per row cost three times the
+    // instructions (6 of 32 lanes busy on 8-bit frames).
+    static_assert(SH * 18 < 1024 && SW * 3 <= 18 * 16, "flat chunk list of the staging window");
     const int nw = (nb + 15) >> 4;
-    const unsigned dst0 = smem_addr(raw) + (unsigned)b0;
-    for (int r = r0 + warp; r < r1; r += NTD / 32) {
-      const unsigned char* src = f.ptr + (long long)(ty0 - HMAX + r) * f.pitch + (long long)cx0 * ch;
-      for (int w = lane; w < nw; w += 32)
-        cp_async16z(dst0 + (unsigned)(r * RW + 16 * w), src + 16 * w, min(16, nb - 16 * w));
+    const unsigned mw = 65536u / (unsigned)nw + 1u;
+    const unsigned dst0 = smem_addr(raw) + (unsigned)b0 + (unsigned)(r0 * RW);
+    const unsigned char* src0 = f.ptr + (long long)(ty0 - HMAX + r0) * f.pitch + (long long)cx0 * ch;
+    const int tot = (r1 - r0) * nw;
+    for (int e = threadIdx.x; e < tot; e += NTD) {
+      const int rr = (int)(((unsigned)e * mw) >> 16), w = e - rr * nw;
+      const int left = nb - 16 * w;
+      const unsigned d = dst0 + (unsigned)(rr * RW + 16 * w);
+      const unsigned char* sp = src0 + (long long)rr * f.pitch + 16 * w;
+      if (left >= 16) cp_async16(d, sp);
+      else cp_async16z(d, sp, left);
     }
   } else if ((((unsigned long long)f.ptr | (unsigned long long)f.pitch) & 3) == 0) {
     // cx0 * ch is a multiple of 16, so every word starts 4-byte aligned; the
