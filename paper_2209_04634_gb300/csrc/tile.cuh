@@ -1595,22 +1595,33 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     // was; the tile flags its rows empty, stages the next frame and moves
     // on.  A sufficient test: flows that round to zero in Q16 without being
     // zero take the full path below, which applies the exact test.
+    // Dense mapping: each owned pixel's log end values and staged flow, read
+    // once per frame for the quiet tests, the activity test and the flow
+    // conversion below.
+    int Lpo[2] = {0, 0}, Lco[2] = {0, 0};
+    float2 flo[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (!SPARSE) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!inimg[q]) continue;
+        const int qx = lane + 32 * q + HMAX, qy = warp + HMAX;
+        Lpo[q] = L.slut[raw_luma(rawp, chp, qy, qx)];
+        Lco[q] = L.slut[raw_luma(rawc, ch, qy, qx)];
+        flo[q] = L.sflow[par * TP + own[q]];
+      }
+    }
     if (!SPARSE && !XT && p.segflag) {
-      const float2* sfq = L.sflow + par * TP;
       bool calm = true;
       bool av[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         av[q] = false;
         if (!inimg[q]) continue;
-        const int qx = lane + 32 * q + HMAX, qy = warp + HMAX;
-        const int Lp = L.slut[raw_luma(rawp, chp, qy, qx)];
-        const int Lc = L.slut[raw_luma(rawc, ch, qy, qx)];
+        const int Lp = Lpo[q], Lc = Lco[q];
         const int cp = MAPS ? Cpd[q] : p.cp, cn = MAPS ? Cnd[q] : p.cn;
         av[q] = !spm || abs(Lc - Lp) >= activity_threshold(p, cp, cn);
         if (!av[q]) continue;  // sparse: an inactive pixel keeps R and emits nothing
-        const float2 fl = sfq[own[q]];
-        const bool still = ((__float_as_uint(fl.x) | __float_as_uint(fl.y)) << 1) == 0u;
+        const bool still = ((__float_as_uint(flo[q].x) | __float_as_uint(flo[q].y)) << 1) == 0u;
         const bool band = RESET ? (Lc - Lp <= cp && Lp - Lc <= cn)
                                 : (max(Lp, Lc) - Rd[q] < cp && Rd[q] - min(Lp, Lc) < cn);
         calm = calm && still && band;
@@ -1655,17 +1666,19 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       const int lx = own[q] & (TW - 1), ly = own[q] / TW;
       bool a = inimg[q];
       if (inimg[q] && (SPARSE || spm || fi == count - 1)) {
-        const int vc = raw_luma(rawc, ch, ly + HMAX, lx + HMAX);
         if (fi == count - 1) {
           const long long ri = (long long)(ty0 + ly) * W + tx0 + lx;
           unsigned char* ringn = (sel & 2) ? p.ring0 : p.ring1;
-          if (in_bounds(p.ctl, ri, (long long)p.W * p.H)) ringn[ri] = (unsigned char)vc;
+          if (in_bounds(p.ctl, ri, (long long)p.W * p.H))
+            ringn[ri] = (unsigned char)raw_luma(rawc, ch, ly + HMAX, lx + HMAX);
         }
         if (SPARSE || spm) {
-          const int vp = raw_luma(rawp, chp, ly + HMAX, lx + HMAX);
           const int cp = MAPS ? (SPARSE ? (int)L.sCp[own[q]] : Cpd[q]) : p.cp;
           const int cn = MAPS ? (SPARSE ? (int)L.sCn[own[q]] : Cnd[q]) : p.cn;
-          a = abs(L.slut[vc] - L.slut[vp]) >= activity_threshold(p, cp, cn);
+          const int dl = SPARSE ? L.slut[raw_luma(rawc, ch, ly + HMAX, lx + HMAX)] -
+                                      L.slut[raw_luma(rawp, chp, ly + HMAX, lx + HMAX)]
+                                : Lco[q] - Lpo[q];
+          a = abs(dl) >= activity_threshold(p, cp, cn);
         }
       }
       sel_flag[q] = a ? 1 : 0;
@@ -1733,14 +1746,14 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
       Cp[q] = SPARSE ? p.cp : Cpd[q];
       Cn[q] = SPARSE ? p.cn : Cnd[q];
       if (act[q]) {
-        const float2 fl = sfl[slot];
+        const float2 fl = SPARSE ? sfl[slot] : flo[q];
         Fx[q] = flow_q16(fl.x, clamps);
         Fy[q] = flow_q16(fl.y, clamps);
         if (SPARSE) {
           if (MAPS) { Cp[q] = L.sCp[slot]; Cn[q] = L.sCn[slot]; }
           if (!RESET) R[q] = L.sR[slot];
         }
-        if (RESET) R[q] = L.slut[raw_luma(rawp, chp, ly[q] + HMAX, lx[q] + HMAX)];
+        if (RESET) R[q] = SPARSE ? L.slut[raw_luma(rawp, chp, ly[q] + HMAX, lx[q] + HMAX)] : Lpo[q];
         mfx = max(mfx, (unsigned)abs(Fx[q]));
         mfy = max(mfy, (unsigned)abs(Fy[q]));
       }
@@ -1763,8 +1776,8 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
           quiet = false;
           continue;
         }
-        const int Lp = L.slut[raw_luma(rawp, chp, ly[q] + HMAX, lx[q] + HMAX)];
-        const int Lc = L.slut[raw_luma(rawc, ch, ly[q] + HMAX, lx[q] + HMAX)];
+        const int Lp = SPARSE ? L.slut[raw_luma(rawp, chp, ly[q] + HMAX, lx[q] + HMAX)] : Lpo[q];
+        const int Lc = SPARSE ? L.slut[raw_luma(rawc, ch, ly[q] + HMAX, lx[q] + HMAX)] : Lco[q];
         if (RESET) quiet = quiet && Lc - Lp <= Cp[q] && Lp - Lc <= Cn[q];
         else quiet = quiet && max(Lp, Lc) - R[q] < Cp[q] && R[q] - min(Lp, Lc) < Cn[q];
       }
@@ -1856,8 +1869,9 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
           p.segflag[(long long)fi * p.segs_per_k + (long long)(ty0 + warp) * p.tiles_x + tcx] =
             skip ? 0 : 1;
       if (ty0 + warp < H && !skip) {  // warp-uniform: rows below the image publish nothing
-        // the row's 64 pixels are in the image (and, sparse, all simulated)
-        const bool fullt = !SPARSE && !spm && tx0 + TW <= W;
+        // the row's 64 pixels are in the image (and, sparse, all active)
+        const bool fullt =
+            !SPARSE && tx0 + TW <= W && (!spm || __all_sync(FULL, act[0] && act[1]));
 #define EVSIM_DENSE(FT)                                                                        \
   dense_substeps<RESET, WIDE, FT, true>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp, b0, \
                                         b1, segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy,  \
