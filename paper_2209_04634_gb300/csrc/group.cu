@@ -149,6 +149,7 @@ int rebuild(simb_t* g) {
     max_chunks += order_chunks(m->s, g->fmax);
     gs[i].p = evsim_rt::make_params(m->s);
     gs[i].p.segflag = nullptr;  // group tile launches write every segment
+    gs[i].p.units = nullptr;
     gs[i].frames = d_desc(g) + (size_t)i * g->fmax;
     gs[i].pre_blocks = m->pre_blocks;
   }

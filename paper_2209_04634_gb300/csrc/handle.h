@@ -45,6 +45,8 @@ struct sim_s {
   Ev* d_events = nullptr;
   evsim::Seg* d_seg = nullptr;
   unsigned char* d_segflag = nullptr;       // row kernel: per (frame, row unit) written flags
+  int* d_units = nullptr;                   // per frame: its flagged units (order kernel)
+  int* d_unit_count = nullptr;              // [bmax] flagged units per frame
   unsigned long long* d_tdone = nullptr;    // per tile progress words
   unsigned long long* d_order_status = nullptr;
   evsim::FrameDesc* d_desc = nullptr;       // bmax descriptors of the batch in flight

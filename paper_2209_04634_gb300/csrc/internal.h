@@ -156,6 +156,9 @@ struct SimParams {
   unsigned char* segflag;       // row kernel: per (frame, row, 64-column unit) 1 when the
                                 // unit-frame's segments are written, 0 when it emitted
                                 // nothing and wrote none; null: every segment is written
+  int* units;                   // with segflag (null: none): per frame, the indices of its
+                                // flagged units in raster order (segs_per_k slots a frame)
+  int* unit_count;              // [bmax] flagged units of each frame
 };
 
 // ---- multi-stream step (one launch per kernel for every member of a group)

@@ -409,7 +409,9 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long mask, int m) {
   return 32 + (int)__fns(hi, 0, m - c + 1);
 }
 
-// Shared memory of an order block.
+// Shared memory of an order block (the multi-stream order kernel adds a
+// member's parameters: both stay within the 48 KB of static shared memory).
+static_assert(SIM_MAX_SUBSTEPS <= 255, "substep counts are kept in bytes");
 struct OrderSmem {
   int ex[OCHUNK];
   int src[OCHUNK];
@@ -417,8 +419,10 @@ struct OrderSmem {
   unsigned long long pol[OCHUNK];
   unsigned t[OCHUNK];
   unsigned xy[OCHUNK];  // x0 | (y << 16)
-  int N[SIM_MAX_BATCH];  // substeps of each frame of the batch
-  int FN[SIM_MAX_BATCH + 1];  // substeps of the frames before each frame
+  unsigned char N[SIM_MAX_BATCH];  // substeps of each frame of the batch (<= 64)
+  int B[SIM_MAX_BATCH];  // flagged units of each frame (p.units set)
+  int FN[SIM_MAX_BATCH + 1];  // live segments of the frames before each frame, in
+                              // substeps (p.units null: x segs_per_k) or segments
   int warp[NWARP + 1];
   short cblk[OCHUNK];    // segments of the chunk with per-pixel counts
   int ncblk;
@@ -426,25 +430,31 @@ struct OrderSmem {
   long long prefix;
 };
 
-// Substep counts of the batch's frames into o.N and their exclusive prefix
-// into o.FN (FN[count] = all substeps of the batch); returns the number of
-// chunks of the batch's live segments (those of substeps k < N of their
-// frame).  All threads; contains barriers.
+// Substep counts of the batch's frames into o.N and the exclusive prefix of
+// their live segments into o.FN; returns the number of chunks of the
+// batch's live segments.  Live: the segments of substeps k < N of their
+// frame, and with unit lists (p.units) only those of the frame's flagged
+// units (FN counts segments: N_f x units_f per frame; the table holds fewer
+// than 2^31 segments); without, every unit's (FN counts substeps, a frame's
+// segments being N_f x segs_per_k).  All threads; contains barriers.
 __device__ __forceinline__ int order_fill_n(const SimParams& p, const BatchArg& b, OrderSmem& o) {
-  for (int i = threadIdx.x; i < b.count; i += NT)
-    o.N[i] = p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[i], p.n_max);
+  for (int i = threadIdx.x; i < b.count; i += NT) {
+    o.N[i] = (unsigned char)(p.n_fixed > 0 ? p.n_fixed : adaptive_n(p.maxf2[i], p.n_max));
+    o.B[i] = p.units ? p.unit_count[i] : 0;
+  }
   __syncthreads();
   int carry = 0;
   for (int base = 0; base < b.count; base += NT) {
     const int i = base + threadIdx.x;
     int tot;
-    const int ex = block_excl_scan(i < b.count ? o.N[i] : 0, o.warp, &tot);
+    const int v = i < b.count ? (p.units ? o.N[i] * o.B[i] : o.N[i]) : 0;
+    const int ex = block_excl_scan(v, o.warp, &tot);
     if (i < b.count) o.FN[i] = carry + ex;
     carry += tot;
   }
   if (threadIdx.x == 0) o.FN[b.count] = carry;
   __syncthreads();
-  const long long live = (long long)carry * p.segs_per_k;
+  const long long live = p.units ? (long long)carry : (long long)carry * p.segs_per_k;
   return (int)max(1LL, (live + OCHUNK - 1) / OCHUNK);
 }
 
@@ -459,67 +469,84 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
   const long long S = p.segs_per_k;
   // live segments only: (frame, substep k < N of the frame, row); a chunk
   // index beyond them (a ticket range sized for n_max substeps) is empty
-  const long long nlive = (long long)o.FN[b.count] * S;
-  if ((long long)c * OCHUNK >= nlive) return;
+  const long long nlive = p.units ? (long long)o.FN[b.count] : (long long)o.FN[b.count] * S;
+  // chunk 0 always runs: a batch without a live segment (no flagged unit
+  // in any frame) is still committed by it
+  if (c > 0 && (long long)c * OCHUNK >= nlive) return;
   // OSEG segments per thread: loaded interleaved (segment u * NT + tid, so a
   // warp's loads are contiguous) into the chunk's arrays, then scanned with
   // each thread owning OSEG consecutive segments
   if (tid == 0) o.ncblk = 0;
-  // the chunk's first segment: frame-substep q0, row-segment rs0, frame fi0;
-  // a segment ls of the chunk lies (rs0 + ls) / S frame-substeps further
-  // (32-bit: S and OCHUNK are far below 2^31) and a few frames at most
+  // the chunk's first segment: without unit lists, frame-substep q0 and
+  // row-segment rs0 (a segment ls of the chunk lies (rs0 + ls) / S
+  // frame-substeps further: 32-bit, S and OCHUNK are far below 2^31); with
+  // them, segment si0 of the live list; in both, frame fi0 and a few frames
+  // further at most
   const long long si0 = (long long)c * OCHUNK;
-  const long long q0 = si0 / S;
-  const int rs0 = (int)(si0 - q0 * S);
+  const long long q0 = p.units ? 0 : si0 / S;
+  const int rs0 = p.units ? 0 : (int)(si0 - q0 * S);
+  const long long key0 = p.units ? si0 : q0;
   int fi0 = 0;
   {
     int hi = b.count;
     while (hi - fi0 > 1) {
       const int mid = (fi0 + hi) >> 1;
-      if (o.FN[mid] <= q0) fi0 = mid; else hi = mid;
+      if (o.FN[mid] <= key0) fi0 = mid; else hi = mid;
     }
   }
 #pragma unroll
   for (int u = 0; u < OSEG; ++u) {
     const int ls = u * NT + tid;  // segment of the chunk
     const long long si = si0 + ls;
+    // a segment's masks, row position and time are needed only when it has
+    // events (the scan reads the counts and sources of all)
     int cnt = 0, src = -1;
-    unsigned long long mask = 0, pol = 0;
-    unsigned tk = 0, xy = 0;
     if (si < nlive) {
-      const unsigned dq = (unsigned)(rs0 + ls) / (unsigned)S;
-      const long long q = q0 + dq;  // frame-substep of the batch
-      const int rs = rs0 + ls - (int)(dq * (unsigned)S);
-      int fi = fi0;
-      while (o.FN[fi + 1] <= q) ++fi;  // FN[count] exceeds every live q
-      const int k = (int)(q - o.FN[fi]);
+      int fi = fi0, k, rs;
+      bool written;
+      if (p.units) {
+        // live segment rem of frame fi: substep rem / units_f of the frame's
+        // flagged unit rem mod units_f (frames without one hold no segment)
+        while (o.FN[fi + 1] <= si) ++fi;
+        const int rem = (int)(si - o.FN[fi]);
+        const int nu = o.B[fi];
+        k = (int)((unsigned)rem / (unsigned)nu);
+        const long long ui = (long long)fi * S + (rem - k * nu);
+        rs = in_bounds(ctl, ui, (long long)p.bmax * S) ? p.units[ui] : 0;
+        written = true;
+      } else {
+        const unsigned dq = (unsigned)(rs0 + ls) / (unsigned)S;
+        const long long q = q0 + dq;  // frame-substep of the batch
+        rs = rs0 + ls - (int)(dq * (unsigned)S);
+        while (o.FN[fi + 1] <= q) ++fi;  // FN[count] exceeds every live q
+        k = (int)(q - o.FN[fi]);
+        // a unit-frame that emitted nothing wrote a flag instead of its
+        // segments
+        written = !p.segflag || p.segflag[(long long)fi * S + rs];
+      }
       const int N = o.N[fi];
-      // a unit-frame of the row kernel that emitted nothing wrote a flag
-      // instead of its segments
-      if (!p.segflag || p.segflag[(long long)fi * S + rs]) {
+      if (written) {
         const long long si2 = ((long long)fi * p.n_max + k) * S + rs;
         Seg sg{0ull, 0ull, 0, -1};
         if (in_bounds(ctl, si2, p.seg_cap)) sg = p.seg[si2];
         cnt = sg.cnt;
         src = sg.src;
-        mask = sg.mask;
-        pol = sg.pol;
+        if (cnt > 0) {
+          const int y = rs / p.tiles_x, tc = rs - y * p.tiles_x;
+          const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
+          const long long dt = b.frames[fi].t_rel - tp;
+          // (k + 1) dt / N (dt > 0): a 32-bit division when the product fits
+          const unsigned long long kd = (unsigned long long)(k + 1) * (unsigned long long)dt;
+          o.mask[ls] = sg.mask;
+          o.pol[ls] = sg.pol;
+          o.t[ls] = (unsigned)(tp + (long long)(kd < 0x100000000ull ? (unsigned)kd / (unsigned)N
+                                                                      : kd / (unsigned)N));
+          o.xy[ls] = (unsigned)(tc * TW) | ((unsigned)y << 16);
+        }
       }
-      const int y = rs / p.tiles_x, tc = rs - y * p.tiles_x;
-      xy = (unsigned)(tc * TW) | ((unsigned)y << 16);
-      const long long tp = fi == 0 ? t_first : b.frames[fi - 1].t_rel;
-      const long long dt = b.frames[fi].t_rel - tp;
-      // (k + 1) dt / N (dt > 0): a 32-bit division when the product fits
-      const unsigned long long kd = (unsigned long long)(k + 1) * (unsigned long long)dt;
-      tk = (unsigned)(tp + (long long)(kd < 0x100000000ull ? (unsigned)kd / (unsigned)N
-                                                              : kd / (unsigned)N));
     }
     o.ex[ls] = cnt;
     o.src[ls] = src;
-    o.mask[ls] = mask;
-    o.pol[ls] = pol;
-    o.t[ls] = tk;
-    o.xy[ls] = xy;
   }
   __syncthreads();
   int mine = 0;
@@ -545,8 +572,9 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
   }
   __syncthreads();
   const long long base = cursor + o.prefix;
+  int lo = 0;  // the thread's events only move forward: each search starts at the last hit
   for (int jj = tid; jj < total; jj += NT) {
-    int lo = 0, hi = OCHUNK;
+    int hi = OCHUNK;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (o.ex[mid] <= jj) lo = mid; else hi = mid;
@@ -640,6 +668,29 @@ __device__ __forceinline__ void order_chunk(const SimParams& p, const BatchArg& 
     for (int i = tid; i < b.count; i += NT) p.maxf2[i] = 0;
   }
   __syncthreads();
+}
+
+// The flagged units of each frame of the batch in raster order (their
+// segments are the only ones written), one block per frame: the order pass
+// then walks live segments only instead of every (substep, unit) slot.
+constexpr int UNT = 1024;
+__global__ void __launch_bounds__(UNT) k_units(SimParams p, int count) {
+  __shared__ int s_warp[UNT / 32 + 1];
+  const int fi = blockIdx.x;
+  if (fi >= count || block_error(&p.ctl->err)) return;
+  const long long S = p.segs_per_k;
+  const unsigned char* f = p.segflag + (long long)fi * S;
+  int* u = p.units + (long long)fi * S;
+  int carry = 0;
+  for (long long base = 0; base < S; base += UNT) {
+    const long long i = base + threadIdx.x;
+    const int flag = i < S && f[i] ? 1 : 0;
+    int tot;
+    const int ex = block_excl_scan<UNT>(flag, s_warp, &tot);
+    if (flag) u[carry + ex] = (int)i;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) p.unit_count[fi] = carry;
 }
 
 __global__ void __launch_bounds__(NT) k_order(SimParams p, BatchArg b) {
@@ -1040,6 +1091,11 @@ cudaError_t launch_sparse_pre(const SimParams& p, const BatchArg& b, cudaStream_
 }
 
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid) {
+  if (p.units) {
+    k_units<<<b.count, UNT, 0, st>>>(p, b.count);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_order<<<grid, NT, 0, st>>>(p, b);
   return cudaGetLastError();
 }

@@ -56,7 +56,7 @@ long long state_bytes(const sim_config& c) {
   if (c.mode == SIM_DIFF) b += 2 * z.P;  // the second frame ring
   b += (z.stage + z.cap) * (long long)sizeof(Ev);       // staging + events
   b += z.seg_cap * (long long)sizeof(evsim::Seg) + 8 * z.ochunks;
-  b += (long long)z.bmax * z.segs_per_k;                 // row kernel: segment flags
+  b += (long long)z.bmax * z.segs_per_k * 5 + 4LL * z.bmax;  // segment flags, flagged units
   b += 8LL * z.tiles_x * ((c.height + 7) / 8);                     // tile progress words
   b += (long long)z.bmax * sizeof(evsim::FrameDesc);
   b += z.P * c.pixel_format;                             // host-frame staging (one frame)
@@ -91,6 +91,8 @@ void free_all(sim_t* s) {
   cudaFree(s->d_events);
   cudaFree(s->d_seg);
   cudaFree(s->d_segflag);
+  cudaFree(s->d_units);
+  cudaFree(s->d_unit_count);
   cudaFree(s->d_tdone);
   cudaFree(s->d_order_status);
   cudaFree(s->d_desc);
@@ -125,6 +127,8 @@ evsim::SimParams make_params(const sim_t* s) {
   // segment flags: the row kernel, and the dense tile kernel (which skips
   // rows whose pixels are all quiet)
   p.segflag = s->d_segflag;
+  p.units = s->d_units;
+  p.unit_count = s->d_unit_count;
   p.xtime = s->cfg.event_time == SIM_TIME_CROSSING;
   p.mode = s->cfg.mode;
   p.ref_mode = s->cfg.ref_mode;
@@ -492,8 +496,15 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   chk(dalloc(&s->d_events, cap));
   chk(dalloc(&s->d_seg, seg_cap));
   // segment flags (row kernel; tile kernel with substep times)
-  if (th == SIM_TILE_ROWS || (c.mode != SIM_DIFF && !xtime))
+  if (th == SIM_TILE_ROWS || (c.mode != SIM_DIFF && !xtime)) {
     chk(dalloc(&s->d_segflag, (size_t)s->bmax * s->segs_per_k));
+    // the order pass walks the flagged units only (its 32-bit segment
+    // counts need a table below 2^31 segments)
+    if (seg_cap < (1LL << 31)) {
+      chk(dalloc(&s->d_units, (size_t)s->bmax * s->segs_per_k));
+      chk(dalloc(&s->d_unit_count, (size_t)s->bmax));
+    }
+  }
   chk(dalloc(&s->d_tdone, (size_t)s->tiles_x * s->tiles_y));
   chk(dalloc(&s->d_order_status, ochunks));
   chk(dalloc(&s->d_desc, s->bmax));
