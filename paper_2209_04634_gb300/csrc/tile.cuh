@@ -815,6 +815,87 @@ __device__ __forceinline__ void dense_substeps(const SimParams& p, const int* sw
   }
 }
 
+// Dense loop over a row whose pixels to simulate number at most 32 (sparse
+// activity masks, or pixels that are quiet: both emit nothing and keep R),
+// compacted one per lane: lane j runs column col (has: j holds a pixel),
+// the row's column layout (lane l: columns l and l + 32) is restored for
+// publishing by taking column l's count from lane s0 and column l + 32's from
+// lane s1 (-1: not simulated, count 0).  Same arithmetic as dense_substeps,
+// half the pixel work of its two-pixel lanes.
+template <bool RESET, bool WIDE, bool MASKS>
+__device__ __forceinline__ void dense_substeps1(const SimParams& p, const int* swk,
+                                                const unsigned* stk, const unsigned* cmask,
+                                                int N, unsigned mN, int tx0, int y, unsigned b0,
+                                                unsigned b1, Seg* segr, WarpStage* ws, bool has,
+                                                int col, int Fx, int Fy, int& R, int Cp, int Cn,
+                                                int s0, int s1) {
+  const int warp = threadIdx.x >> 5;
+  int px = (col + HMAX) << 16, py = (warp + HMAX) << 16;
+  int qx, qy, r_x, r_y;
+  unsigned ax, ay, rx = 0, ry = 0;
+  divmod_n(Fx, N, mN, qx, r_x);
+  divmod_n(Fy, N, mN, qy, r_y);
+  if (MASKS) {
+    ax = cmask[r_x];
+    ay = cmask[r_y];
+    qx = -qx;
+    qy = -qy;
+  } else {
+    rx = (unsigned)r_x;
+    ry = (unsigned)r_y;
+    ax = 0;
+    ay = 0;
+  }
+  const int l0 = s0 & 31, l1 = s1 & 31;
+  for (int k = 0; k < N; ++k) {
+    const int w = swk[k];
+    if (MASKS) {
+      px += qx + ((int)ax >> 31);
+      ax <<= 1;
+      py += qy + ((int)ay >> 31);
+      ay <<= 1;
+    } else {
+      px -= qx;
+      ax += rx;
+      if (ax >= (unsigned)N) { ax -= N; px -= 1; }
+      py -= qy;
+      ay += ry;
+      if (ay >= (unsigned)N) { ay -= N; py -= 1; }
+    }
+    const int v0 = tap_shared<WIDE>(b0, px, py);
+    const int v1 = tap_shared<WIDE>(b1, px + Fx, py + Fy);
+    const int I = lerp12<WIDE>(v0, v1, w);
+    const int d = I - R;
+    int n;
+    bool multi = false;
+    if (RESET) {
+      if (has) R = I;
+      n = d > Cp ? 1 : (d < -Cn ? -1 : 0);
+    } else {
+      n = d >= Cp ? 1 : (d <= -Cn ? -1 : 0);
+      if (has) R += n > 0 ? Cp : (n < 0 ? -Cn : 0);
+      const int d2 = I - R;
+      multi = has && (d2 >= Cp || d2 <= -Cn);
+    }
+    if (!has) n = 0;
+    if (!RESET && __any_sync(FULL, multi)) {
+      if (has && d >= 2 * Cp) {
+        const int m = floordiv_pos<WIDE>(d, Cp);
+        R += (m - 1) * Cp;
+        n = m;
+      } else if (has && d <= -2 * Cn) {
+        const int m = floordiv_pos<WIDE>(-d, Cn);
+        R -= (m - 1) * Cn;
+        n = -m;
+      }
+    }
+    int n0 = __shfl_sync(FULL, n, l0), n1 = __shfl_sync(FULL, n, l1);
+    if (s0 < 0) n0 = 0;
+    if (s1 < 0) n1 = 0;
+    publish_row_dense(p, segr + (long long)k * p.segs_per_k, n0, n1, stk[k], tx0, y, ws);
+  }
+}
+
 // Sparse fast path: the substeps of this thread's compacted pixels (slots
 // tid and, NPX = 2, tid + NTD; `act` says which exist), sampling the shared
 // halos.  Each pixel's count per substep goes to snk (slot order) and, when
@@ -1767,20 +1848,22 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
     // row of quiet pixels skips its substeps and writes a flag instead of its
     // segments, and a tile without a busy row builds no halo.
     bool quiet = false;
+    bool qp[2] = {false, false};  // per pixel (dense mapping): nothing to simulate
     if (!XT && p.segflag) {  // sparse: inactive pixels count as quiet
-      quiet = true;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
+        qp[q] = true;
         if (!act[q]) continue;
         if ((Fx[q] | Fy[q]) != 0) {
-          quiet = false;
+          qp[q] = false;
           continue;
         }
         const int Lp = SPARSE ? L.slut[raw_luma(rawp, chp, ly[q] + HMAX, lx[q] + HMAX)] : Lpo[q];
         const int Lc = SPARSE ? L.slut[raw_luma(rawc, ch, ly[q] + HMAX, lx[q] + HMAX)] : Lco[q];
-        if (RESET) quiet = quiet && Lc - Lp <= Cp[q] && Lp - Lc <= Cn[q];
-        else quiet = quiet && max(Lp, Lc) - R[q] < Cp[q] && R[q] - min(Lp, Lc) < Cn[q];
+        if (RESET) qp[q] = Lc - Lp <= Cp[q] && Lp - Lc <= Cn[q];
+        else qp[q] = max(Lp, Lc) - R[q] < Cp[q] && R[q] - min(Lp, Lc) < Cn[q];
       }
+      quiet = qp[0] && qp[1];
     }
     mfx = __reduce_max_sync(FULL, mfx);
     mfy = __reduce_max_sync(FULL, mfy);
@@ -1872,11 +1955,36 @@ __device__ __forceinline__ void tile_batch(const SimParams& p, const BatchArg& b
         // the row's 64 pixels are in the image (and, sparse, all active)
         const bool fullt =
             !SPARSE && tx0 + TW <= W && (!spm || __all_sync(FULL, act[0] && act[1]));
+        // the row's pixels to simulate: active and not quiet
+        const bool sim0 = act[0] && !qp[0], sim1 = act[1] && !qp[1];
+        const unsigned m0 = __ballot_sync(FULL, sim0), m1 = __ballot_sync(FULL, sim1);
+        const int c0 = __popc(m0), nsim = c0 + __popc(m1);
 #define EVSIM_DENSE(FT)                                                                        \
   dense_substeps<RESET, WIDE, FT, true>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp, b0, \
                                         b1, segf + warp * p.tiles_x, &s_stage[warp], act, Fx, Fy,  \
                                         R, Cp, Cn)
-        if (N <= 32) {
+        if (!SPARSE && N <= 32 && nsim <= 32) {  // warp-uniform: one pixel per lane
+          const unsigned lt = lanemask_lt();
+          const int s0 = sim0 ? __popc(m0 & lt) : -1, s1 = sim1 ? c0 + __popc(m1 & lt) : -1;
+          const bool has = lane < nsim;
+          const int col = !has ? 0
+                          : lane < c0 ? (int)__fns(m0, 0, lane + 1)
+                                      : 32 + (int)__fns(m1, 0, lane - c0 + 1);
+          const int src = col & 31;
+          const bool hi = col >= 32;
+          auto take = [&](const int (&v)[2]) {
+            const int a0 = __shfl_sync(FULL, v[0], src), a1 = __shfl_sync(FULL, v[1], src);
+            return has ? (hi ? a1 : a0) : 0;
+          };
+          int Rj = take(R);
+          dense_substeps1<RESET, WIDE, true>(p, V.swk, V.stk, s_cmask[par], N, mN, tx0, ty0 + warp,
+                                             b0, b1, segf + warp * p.tiles_x, &s_stage[warp], has,
+                                             col, take(Fx), take(Fy), Rj,
+                                             MAPS ? take(Cp) : p.cp, MAPS ? take(Cn) : p.cn, s0, s1);
+          const int r0 = __shfl_sync(FULL, Rj, s0 & 31), r1 = __shfl_sync(FULL, Rj, s1 & 31);
+          if (s0 >= 0) R[0] = r0;
+          if (s1 >= 0) R[1] = r1;
+        } else if (N <= 32) {
           if (fullt) EVSIM_DENSE(true);
           else EVSIM_DENSE(false);
         } else {
