@@ -541,8 +541,16 @@ def run_ours(args, ws, rank, local):
     value, ms_max = weak_scaling_value(ws, work_step * args.steps, ms)
     kt = ps.kernel_times()
     # every order call of these passes is two kernels: k_units (the frames'
-    # flagged row units) and k_order
-    launches = sum(c * (2 if k.endswith(".order") else 1) for k, (_, c) in kt.items())
+    # flagged row units) and k_order; a tile call in the balanced order is
+    # preceded by two more (k_predict: the tiles' cost estimates, k_plan)
+    def calls(k, c):
+        pass_name, kind = k.split(".", 1)
+        if kind == "order":
+            return 2 * c
+        if kind in ("dense", "sparse") and ps.tune.get(pass_name, {}).get("block_order") == "balanced":
+            return 3 * c
+        return c
+    launches = sum(calls(k, c) for k, (_, c) in kt.items())
     total_ev = sum_over_ranks(ws, n_ev)
     roofs = rooflines(seq, kt, units, "moving_rectangles_1280x720", args.steps)
     dom = max(roofs, key=lambda k: roofs[k]["total_ms"]) if roofs else None

@@ -343,8 +343,9 @@ const char* sim_version(void);
  * block (two blocks per SM) and 64 x 8 per 256-thread block (four per SM),
  * and takes its tiles in one of three block orders: linear; serpentine (odd
  * rounds of one block per SM reversed, so that the blocks sharing an SM hold
- * tiles from opposite ends of the image); or balanced (each batch records
- * how long each tile's block took, and the next batch places the tiles in
+ * tiles from opposite ends of the image); or balanced (before each batch a
+ * pre-pass estimates every tile's cost from samples of the batch's flows -
+ * frames in which the tile moves cost more - and the tiles are placed in
  * serpentine order over that ranking, so that the heaviest tile shares its
  * SM with the lightest; frames up to 4096 tiles).
  * The smaller shape has twice the blocks for a frame of a given size - more

@@ -108,8 +108,8 @@ int valid_cfg(const sim_config& c) {
 // Time both shapes in each block order (linear, serpentine, balanced) on the
 // frames and record the fastest; the default (64x16, linear order) unless
 // another choice is at least 5 % faster (a sample's timings scatter by a few
-// percent).  The balanced order's timed pass runs on the plan its warm-up
-// pass measured.
+// percent).  The balanced order plans each batch from samples of its own
+// flows, as in a stream.
 int tune(const sim_config& c, int count, const void* const* frames, int64_t pitch,
          const float* const* flows, const int64_t* t_us, int32_t mem, int32_t* th_out,
          double* us_out) {

@@ -251,9 +251,10 @@ cudaError_t launch_diff(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_rows(const SimParams& p, const BatchArg& b, cudaStream_t st);
 cudaError_t launch_accumulate(const Ev* ev, long long n, int W, int H, long long t_begin,
                               long long t_end, int* frame, cudaStream_t st);
-// Balanced block order: rank the tiles by their last batch's cost and lay
-// them out for the next batch (one block).
-cudaError_t launch_plan(const SimParams& p, cudaStream_t st);
+// Balanced block order for the batch about to run: estimate every tile's
+// cost from samples of the batch's flows (one block per tile), rank the
+// tiles and lay them out (one block).
+cudaError_t launch_plan(const SimParams& p, const BatchArg& b, cudaStream_t st);
 constexpr int PLAN_MAX_TILES = 4096;  // tiles a balanced plan covers
 cudaError_t launch_order(const SimParams& p, const BatchArg& b, cudaStream_t st, int grid);
 cudaError_t configure_kernels(int n_max);

@@ -280,18 +280,23 @@ cudaError_t enqueue_batch(sim_t* s, int n, bool host_mapped) {
       e = timed(s, SIM_K_FLOWMAX, [&] { return evsim::launch_flowmax(p, b, s->stream); });
       if (e != cudaSuccess) return e;
     }
+    if (s->block_order == 2 && s->cfg.mode != SIM_DIFF && s->tile_h != SIM_TILE_ROWS) {
+      e = evsim::launch_plan(p, b, s->stream);  // the balanced order of this batch's tiles
+      if (e != cudaSuccess) return e;
+    }
     if (s->cfg.mode == SIM_DIFF)
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_diff(p, b, s->stream); });
     else if (s->tile_h == SIM_TILE_ROWS)
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_rows(p, b, s->stream); });
     else
       e = timed(s, SIM_K_DENSE, [&] { return evsim::launch_dense(p, b, s->stream); });
-    if (e == cudaSuccess && s->block_order == 2 && s->cfg.mode != SIM_DIFF &&
-        s->tile_h != SIM_TILE_ROWS)
-      e = evsim::launch_plan(p, s->stream);
   } else {
     if (adaptive) {
       e = timed(s, SIM_K_MASK, [&] { return evsim::launch_sparse_pre(p, b, s->stream); });
+      if (e != cudaSuccess) return e;
+    }
+    if (s->block_order == 2 && s->tile_h != SIM_TILE_ROWS) {
+      e = evsim::launch_plan(p, b, s->stream);
       if (e != cudaSuccess) return e;
     }
     if (s->tile_h == SIM_TILE_ROWS)
@@ -300,8 +305,6 @@ cudaError_t enqueue_batch(sim_t* s, int n, bool host_mapped) {
       e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_dense(p, b, s->stream); });
     else
       e = timed(s, SIM_K_SPARSE, [&] { return evsim::launch_sparse(p, b, s->stream); });
-    if (e == cudaSuccess && s->block_order == 2 && s->tile_h != SIM_TILE_ROWS)
-      e = evsim::launch_plan(p, s->stream);
   }
   if (e != cudaSuccess) return e;
   return timed(s, SIM_K_ORDER, [&] { return evsim::launch_order(p, b, s->stream, s->order_grid); });
@@ -475,8 +478,8 @@ int sim_create(const sim_config* cfg, sim_t** out) {
   }
   chk(dalloc(&s->d_ctl, 1));
   {
-    // balanced block order: per-tile costs of the last batch and the plan,
-    // identity until a batch has been measured
+    // balanced block order: per-tile cost estimates of the batch and the
+    // plan made from them before each batch
     const int T = s->tiles_x * s->tiles_y;
     if (T <= evsim::PLAN_MAX_TILES) {
       chk(dalloc(&s->d_tile_cost, T));

@@ -2145,9 +2145,7 @@ __global__ void __launch_bounds__(32 * TH_, 32 / TH_) k_tile(SimParams p, BatchA
   const int tile = p.block_order == 2 ? p.tile_order[bi]
                    : p.block_order == 1 ? serpentine_tile(bi, gridDim.x, p.sms)
                                         : bi;
-  const long long c0 = clock64();
   tile_batch<RESET, MAPS, WIDE, SPARSE, TH_, XT>(p, b, tile);
-  if (p.tile_cost && threadIdx.x == 0) p.tile_cost[tile] = (unsigned)((clock64() - c0) >> 8);
 }
 
 // Dynamic shared-memory permission of one k_tile instance in both shapes;

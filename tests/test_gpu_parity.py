@@ -454,7 +454,8 @@ def test_autotune_on_a_sample_of_the_stream(device):
 def test_block_orders_give_the_oracle_events(order, mode, tmp_path):
     """The serpentine and the balanced block orders (set through an autotuner
     table) only reschedule the tiles: the events stay the oracle's, over
-    several batches (the balanced order's plan comes from the batch before)."""
+    several batches (the balanced order plans each batch from samples of its
+    own flows)."""
     seq = random_seq(90, 200, F=7, seed=31 + order, substeps=3)
     f = tmp_path / "table.txt"
     f.write_text(f"200 90 1 {mode} 3 0 0 0 0 16 {order} 1.0 1.0 0.0\n")
