@@ -314,53 +314,67 @@ __global__ void k_accumulate(const Ev* ev, long long n, int W, int H, long long 
 // about four quiet ones (measured on moving content: 20 against 8 us per
 // 1280x720 frame with about half the tiles busy), so a tile's cost is
 // count + 3 x its busy frames.  The samples only steer the schedule, never
-// the events.  One block per tile; warp w takes frames 2w and 2w + 1 of
-// every 16 (a half warp per frame).
+// the events.  One block per tile: the batch's flow pointers are read into
+// shared memory once, then every thread loads its (frame, sample) pairs -
+// independent loads, four in flight - and marks the frames found moving.
+constexpr int PRED_UNROLL = 4;
 __global__ void __launch_bounds__(NT) k_predict(SimParams p, BatchArg b) {
-  __shared__ int s_busy;
-  const int tile = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ const float2* s_flow[SIM_MAX_BATCH];
+  __shared__ unsigned char s_busy[SIM_MAX_BATCH];
+  __shared__ int s_n;
+  const int tile = blockIdx.x, count = b.count;
   const int th = p.tile_h == 8 ? 8 : 16;
   const int x0 = (tile % p.tiles_x) * TW, y0 = (tile / p.tiles_x) * th;
-  const int half = lane >> 4, sm = lane & 15;
-  const int sx = x0 + 4 + 8 * (sm & 7), sy = y0 + (th >> 2) + (th >> 1) * (sm >> 3);
-  const bool in = sx < p.W && sy < p.H;
-  if (threadIdx.x == 0) s_busy = 0;
-  __syncthreads();
-  int busy = 0;
-  for (int f0 = 2 * warp; f0 < b.count; f0 += 2 * NWARP) {  // warp-uniform trip count
-    const int f = f0 + half;
-    bool nz = false;
-    if (in && f < b.count) {
-      const float2 v = b.frames[f].flow[(long long)sy * p.W + sx];
-      nz = ((__float_as_uint(v.x) | __float_as_uint(v.y)) << 1) != 0u;
-    }
-    const unsigned m = __ballot_sync(FULL, nz);
-    if (sm == 0 && ((m >> (16 * half)) & 0xFFFFu)) ++busy;
+  for (int f = threadIdx.x; f < count; f += NT) {
+    s_flow[f] = b.frames[f].flow;
+    s_busy[f] = 0;
   }
-  if (sm == 0 && busy) atomicAdd(&s_busy, busy);
+  if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
-  if (threadIdx.x == 0) p.tile_cost[tile] = (unsigned)(b.count + 3 * s_busy);
+  const int total = count * 16;
+  for (int e0 = threadIdx.x; e0 < total; e0 += NT * PRED_UNROLL) {
+    float2 v[PRED_UNROLL];
+    bool ok[PRED_UNROLL];
+#pragma unroll
+    for (int u = 0; u < PRED_UNROLL; ++u) {
+      const int e = e0 + u * NT, f = e >> 4, sm = e & 15;
+      const int sx = x0 + 4 + 8 * (sm & 7), sy = y0 + (th >> 2) + (th >> 1) * (sm >> 3);
+      ok[u] = e < total && sx < p.W && sy < p.H;
+      v[u] = ok[u] ? s_flow[f][(long long)sy * p.W + sx] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < PRED_UNROLL; ++u)
+      if (ok[u] && ((__float_as_uint(v[u].x) | __float_as_uint(v[u].y)) << 1) != 0u)
+        s_busy[(e0 + u * NT) >> 4] = 1;
+  }
+  __syncthreads();
+  int n = 0;
+  for (int f = threadIdx.x; f < count; f += NT) n += s_busy[f];
+  n = __reduce_add_sync(FULL, n);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(&s_n, n);
+  __syncthreads();
+  if (threadIdx.x == 0) p.tile_cost[tile] = (unsigned)(count + 3 * s_n);
 }
 
-// Balanced block order (one block): tiles ranked by their estimated cost
-// (heaviest first, ties by tile index), laid out in serpentine order over
-// the ranks - the first wave of one block per SM takes the heaviest tiles,
-// the second wave the lightest in reverse - so the heaviest tile shares its
-// SM with the lightest.  An order of the tiles like any other: it changes
-// only the schedule.
-__global__ void k_plan(int T, int S, const unsigned* cost, int* order) {
+// Balanced block order: tiles ranked by their estimated cost (heaviest
+// first, ties by tile index), laid out in serpentine order over the ranks -
+// the first wave of one block per SM takes the heaviest tiles, the second
+// wave the lightest in reverse - so the heaviest tile shares its SM with the
+// lightest.  An order of the tiles like any other: it changes only the
+// schedule.  Every block ranks NT tiles against all T (costs in shared
+// memory) and writes each tile to the block that takes its rank:
+// serpentine_tile maps a block to a rank and is its own inverse (it reverses
+// odd rounds only).
+__global__ void __launch_bounds__(NT) k_plan(int T, int S, const unsigned* cost, int* order) {
   __shared__ unsigned sc[PLAN_MAX_TILES];
-  __shared__ int sorted[PLAN_MAX_TILES];
-  for (int t = threadIdx.x; t < T; t += blockDim.x) sc[t] = cost[t];
+  for (int t = threadIdx.x; t < T; t += NT) sc[t] = cost[t];
   __syncthreads();
-  for (int t = threadIdx.x; t < T; t += blockDim.x) {
-    const unsigned c = sc[t];
-    int rank = 0;
-    for (int u = 0; u < T; ++u) rank += sc[u] > c || (sc[u] == c && u < t);
-    sorted[rank] = t;
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < T; b += blockDim.x) order[b] = sorted[serpentine_tile(b, T, S)];
+  const int t = blockIdx.x * NT + threadIdx.x;
+  if (t >= T) return;
+  const unsigned c = sc[t];
+  int rank = 0;
+  for (int u = 0; u < T; ++u) rank += (sc[u] > c) | ((sc[u] == c) & (u < t));
+  order[serpentine_tile(rank, T, S)] = t;
 }
 
 // Adaptive N for the sparse method: max squared flow over the active pixels
@@ -1101,7 +1115,7 @@ cudaError_t launch_plan(const SimParams& p, const BatchArg& b, cudaStream_t st) 
   const int T = p.tiles_x * p.tiles_y;
   if (T > PLAN_MAX_TILES || !p.tile_cost || !p.tile_order || b.count < 1) return cudaSuccess;
   k_predict<<<T, NT, 0, st>>>(p, b);
-  k_plan<<<1, 1024, 0, st>>>(T, p.sms, p.tile_cost, p.tile_order);
+  k_plan<<<(T + NT - 1) / NT, NT, 0, st>>>(T, p.sms, p.tile_cost, p.tile_order);
   return cudaGetLastError();
 }
 
