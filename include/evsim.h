@@ -753,13 +753,13 @@ int sim_flow_destroy(sim_flow_t* f);
  * Set-up: on the first call on a device (and again after the device's
  * context changes, e.g. after cudaDeviceReset) the call looks the array's
  * address up in the current context (cudaGetSymbolAddress) and sets the
- * kernels' shared-memory limits.  Each call clears the parts of the array
+ * kernels' shared-memory limits; make that first call before any stream
+ * capture begins.  Each call clears the parts of the array
  * that must start at zero.  Every call on a device shares the one array:
  * calls whose device work overlaps (two streams, or two host threads) race
  * and corrupt each other's results; order them on one stream or serialise
  * them.  The call is synchronous: it waits for its stream before returning
- * (it reads the step's status and event count back into host memory), so it
- * must not be called while its stream is being captured into a CUDA graph. */
+ * (it reads the step's status and event count back into host memory). */
 #define SIM_STATIC_SCRATCH_BYTES (32LL << 20)
 int sim_step_pair_static(const sim_config* cfg, const void* prev_frame, int64_t prev_pitch,
                          const void* frame, int64_t pitch, const float* flow, int64_t t_prev_us,
