@@ -212,9 +212,10 @@ void prof_collect(sim_t* s) {
 
 // Read the control block (after the stream is idle).
 int read_ctl(sim_t* s, Ctl* c) {
-  cudaError_t e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return cuda_rc(e);
-  e = cudaMemcpy(c, s->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+  // on the handle's stream: a copy on the legacy default stream would also
+  // wait for other streams' work
+  cudaError_t e = cudaMemcpyAsync(c, s->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_rc(e);
 }
 
@@ -726,9 +727,14 @@ int sim_pop_events(sim_t* s, sim_event* out, int64_t cap, int64_t* n_out, int32_
   int status = SIM_OK;
   const long long avail = c.cursor - s->popped;
   const long long m = std::min<long long>(avail, cap);
+  // the copies run on the handle's stream (not the legacy default stream,
+  // which would also wait for other streams' work) and are waited for here
   if (m > 0) {
-    cudaError_t e = cudaMemcpy(out, s->d_events + s->popped, (size_t)m * sizeof(Ev),
-                               mem == SIM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    cudaError_t e = cudaMemcpyAsync(out, s->d_events + s->popped, (size_t)m * sizeof(Ev),
+                                    mem == SIM_HOST ? cudaMemcpyDeviceToHost
+                                                    : cudaMemcpyDeviceToDevice,
+                                    s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_rc(e);
   }
   s->popped += m;
@@ -736,7 +742,9 @@ int sim_pop_events(sim_t* s, sim_event* out, int64_t cap, int64_t* n_out, int32_
   *n_out = m;
   if (s->popped == c.cursor && c.cursor > 0) {
     const long long zero = 0;
-    cudaError_t e = cudaMemcpy(&s->d_ctl->cursor, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(&s->d_ctl->cursor, &zero, sizeof(zero),
+                                    cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_rc(e);
     s->popped = 0;
   }
