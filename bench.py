@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--profile-flow", type=int, default=0,
                     help="profiling: only compute the device flow of this many frame pairs of "
                          "the 640x480 workload, then exit")
+    ap.add_argument("--profile-adaptive", type=int, default=0,
+                    help="profiling: only run this many dense + sparse steps of the 640x480 "
+                         "warped-texture workload (adaptive N: flow-maximum and activity "
+                         "pre-passes), 64x16 tiles in block order, then exit")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the 640x480 and 240x180 workload objects")
     ap.add_argument("--only", default="",
@@ -525,6 +529,14 @@ def run_ours(args, ws, rank, local):
         fl.close()
         print(json.dumps({"profile_flow": args.profile_flow, "width": s.width,
                           "height": s.height}))
+        return 0
+
+    if args.profile_adaptive:
+        c2 = synth.warped_texture(seed=C2_SEED)
+        pp = Passes(c2, torch.cuda.Stream(), 40_000_000, tile_height=16)
+        n = sum(pp.step(serial=True) for _ in range(args.profile_adaptive))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_adaptive": args.profile_adaptive, "events": n}))
         return 0
 
     seq = synth.moving_rectangles(seed=stream_seed(rank, C3_SEED), frames=args.frames)
