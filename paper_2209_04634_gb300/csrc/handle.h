@@ -26,7 +26,7 @@ struct sim_s {
   int tiles_x = 0, tiles_y = 0;
   int tile_h = 16;             // batch kernel tile height (8 or 16; 1: the row kernel)
   int block_order = 0;         // batch kernel tile order: 0 linear, 1 serpentine, 2 balanced
-  unsigned int* d_tile_cost = nullptr;  // balanced order: cycles per tile of the last batch
+  unsigned int* d_tile_cost = nullptr;  // balanced order: estimated cost per tile of the batch
   int* d_tile_order = nullptr;          // balanced order: tile of each block
   cudaStream_t stream = nullptr;
   bool own_stream = false;

@@ -127,10 +127,10 @@ struct SimParams {
   int tile_h;                   // batch kernel tile height: 16 (512 threads) or 8 (256)
   int sms;                      // SMs of the device (block placement of the batch kernel)
   int block_order;              // batch kernel: 0 tiles in block order, 1 serpentine,
-                                // 2 balanced by the previous batch's tile costs
+                                // 2 balanced by the batch's estimated tile costs
   int xtime;                    // 1: per-crossing event times (64 x 16 tiles, every row
                                 // with an event staged)
-  unsigned int* tile_cost;      // balanced order: [tiles] cycles of each tile's last batch
+  unsigned int* tile_cost;      // balanced order: [tiles] each tile's estimated cost (k_predict)
   int* tile_order;              // balanced order: [tiles] tile of each block
   const unsigned short* cpmap;
   const unsigned short* cnmap;

@@ -2,8 +2,9 @@
 //
 // Frames are simulated in batches (a single push is a batch of one).  One
 // batch runs, on the handle's stream:
-//   dense : [flowmax, adaptive N only] -> dense -> order
-//   sparse: [sparse_pre, adaptive N only] -> sparse -> order
+//   dense : [flowmax, adaptive N] -> [predict, plan: balanced order] -> dense
+//           -> [units: rows flagged] -> order
+//   sparse: [sparse_pre, adaptive N] -> [predict, plan] -> sparse -> [units] -> order
 // The method (Ziegler et al., arXiv 2209.04634, Sec. III-A / III-B) and its
 // integer arithmetic are described in include/evsim.h.  Every kernel checks
 // the stream's sticky error word first and does nothing once it is set.
